@@ -1,0 +1,327 @@
+"""Benchmark of the compress + decompress hot path on GB300.
+
+Workload: the 3D 100x500x500 FP32 field (sum of 64 Gaussian blobs plus
+k^-11/3 turbulence, seed 2) at value-range-relative bound 1e-4, 1-layer
+prediction, adaptive m -- the stand-in for the paper's Hurricane fields.
+A step compresses the device-resident field and decompresses the stream.
+
+Prints one JSON line.  `value` = input bytes compressed + input bytes
+decompressed per second of device time (CUDA events on the library's
+stream), L2 flushed (256 MiB write) before every timed step because the
+100 MB input fits in the 129 MB L2.  `e2e` repeats the step through the C
+ABI with pinned host buffers (host->device and device->host copies inside
+the timed region).  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "compress & decompress GB/s of FP32 input (fraction of HBM roofline) at rel eb 1e-4; p50/p99"
+WORKLOAD = "3d-blobs-100x500x500-fp32-releb1e-4-n1-adaptive-m"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else "/tmp/szgb_clocks.csv"
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def pct(v, q):
+    v = sorted(v)
+    if not v:
+        return None
+    k = min(len(v) - 1, max(0, int(round(q / 100.0 * (len(v) - 1)))))
+    return v[k]
+
+
+def run_reference(args):
+    """The CPU oracle, as it stands, on the host cores: bounded sample of the
+    same workload (a 20-plane slab of the field, compress + decompress)."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import szo
+    from synthetic import fields
+    x = fields.workload_3d()
+    slab = np.ascontiguousarray(x[:20])
+    nbytes = slab.nbytes
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        s = szo.compress(slab, eb_rel=1e-4, n=1, m=0)
+        szo.decompress(s)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    val = 2 * nbytes * len(times) / tot / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "planes 0-19 of the 100x500x500 field",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": val, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": "20x500x500 slab, compress+decompress, single thread"},
+            "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample():
+    import numpy as np
+    from oracle import szo
+    from synthetic import fields
+    x = fields.workload_3d()
+    slab = np.ascontiguousarray(x[:10])
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        s = szo.compress(slab, eb_rel=1e-4, n=1, m=0)
+        szo.decompress(s)
+        reps += 1
+        if time.perf_counter() - t0 > 8.0:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": 2 * slab.nbytes * reps / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": "10x500x500 slab of the field, compress+decompress, %d reps, single thread" % reps}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--layers", type=int, default=1)
+    ap.add_argument("--ebrel", type=float, default=1e-4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1706_03791_gb300 import build as B
+    if rank == 0 or ws == 1:
+        B.build()
+    if ws > 1:
+        dist.barrier()
+    from paper_1706_03791_gb300 import szgb
+    from synthetic import fields
+
+    x_np = fields.workload_3d()
+    N = x_np.size
+    nbytes = x_np.nbytes
+    x = torch.from_numpy(x_np).to(dev)
+    ctx = szgb.Context(local)
+    stream = torch.cuda.Stream(device=dev)
+    ctx.set_stream(stream.cuda_stream)
+    kw = dict(eb_rel=args.ebrel, layers=args.layers, m=0)
+    bound = szgb.compress_bound(x_np.shape, **kw)
+    sbuf = torch.empty(bound, dtype=torch.uint8, device=dev)
+    y = torch.empty_like(x)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(prof=False):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e2 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s, st = ctx.compress(x, out=sbuf, **kw)
+            e1.record(stream)
+            ctx.decompress(s, out=y)
+            e2.record(stream)
+        return e0, e1, e2, s, st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # correctness guard on the timed configuration: every point within eb
+    s0, st0 = ctx.compress(x, out=sbuf, **kw)
+    yv = ctx.decompress(s0, out=y)
+    torch.cuda.synchronize()
+    maxerr = float((yv.double() - x.double()).abs().max())
+    assert maxerr < st0.eb_f, "error bound violated"
+    stream_bytes = int(s0.numel())
+
+    clocks = ClockSampler(local)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ctx.set_profiling(True)
+    ctx.phase_times(reset=True)
+    tc, td = [], []
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        e0, e1, e2, s, st = step()
+        e2.synchronize()
+        tc.append(e0.elapsed_time(e1))
+        td.append(e1.elapsed_time(e2))
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    ctx.set_profiling(False)
+    phases = ctx.phase_times(reset=True)
+    clk = clocks.stop()
+    # the profiled run adds event synchronisations per phase; time the same
+    # steps again without profiling for the headline numbers
+    tc2, td2 = [], []
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        e0, e1, e2, s, st = step()
+        e2.synchronize()
+        tc2.append(e0.elapsed_time(e1))
+        td2.append(e1.elapsed_time(e2))
+    torch.cuda.synchronize()
+    tot_ms = sum(tc2) + sum(td2)
+    if ws > 1:
+        t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    ms_step = tot_ms / args.steps
+    value = ws * 2 * nbytes * args.steps / (tot_ms / 1e3) / 1e9
+    comp_gbs = [nbytes / (t / 1e3) / 1e9 for t in tc2]
+    dec_gbs = [nbytes / (t / 1e3) / 1e9 for t in td2]
+
+    # end to end through the C ABI with pinned host buffers
+    xh = torch.from_numpy(x_np).pin_memory()
+    sh = torch.empty(bound, dtype=torch.uint8).pin_memory()
+    yh = torch.empty(x_np.shape, dtype=torch.float32).pin_memory()
+    e2e_t = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n, _ = ctx.compress_host_ptr(xh.data_ptr(), x_np.shape, sh.data_ptr(), bound, **kw)
+        rc = ctx.decompress_ptr(sh.data_ptr(), n, False, yh.data_ptr(), N, False)
+        assert rc == 0
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            e2e_t.append(dt)
+    e2e_val = ws * 2 * nbytes * len(e2e_t) / sum(e2e_t) / 1e9
+
+    # roofline of the dominant kernel: live CUDA-event phase times
+    peak, peak_kind = peaks()
+    bits_pp = stream_bytes * 8.0 / N
+    algo = {"wave_compress": 4.0 + 2.0, "wave_decompress": bits_pp / 8.0 + 4.0}
+    dom = max(algo, key=lambda k: phases.get(k, (0, 0))[0])
+    ms_dom, calls_dom = phases[dom]
+    achieved = algo[dom] * N / (ms_dom / calls_dom / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+            "algorithmic_bytes_per_point": algo[dom]}
+    phase_ms = {k: v[0] / max(v[1], 1) for k, v in phases.items() if v[1]}
+
+    if rank != 0:
+        if ws > 1:
+            dist.barrier()
+        return
+    cpu = None if args.no_cpu_baseline else cpu_baseline_sample()
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "shape": list(x_np.shape), "eb_rel": args.ebrel,
+                   "layers": args.layers, "m": "adaptive", "m_chosen": int(st0.m),
+                   "l2": "flushed (256 MiB write) before every step",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "compress_gbs": {"p50": pct(comp_gbs, 50), "p99": pct(comp_gbs, 1)},
+        "decompress_gbs": {"p50": pct(dec_gbs, 50), "p99": pct(dec_gbs, 1)},
+        "compression_factor": nbytes / stream_bytes, "bits_per_value": bits_pp,
+        "n_unpred": int(st0.n_unpred), "max_error_over_eb": maxerr / float(st0.eb_f),
+        "phase_ms": phase_ms,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": nbytes + stream_bytes,
+                "d2h_bytes_per_step": stream_bytes + nbytes},
+        "gpu_launches": 17 * args.steps,
+        "clocks": clk,
+        "wall_s_timed": t_wall,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+
+
+if __name__ == "__main__":
+    main()

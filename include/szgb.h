@@ -1,0 +1,139 @@
+/*
+ * szgb.h -- C ABI of the GB300 (sm_103a) error-bounded lossy compressor for
+ * FP32 1D/2D/3D arrays: multilayer prediction from preceding decompressed
+ * values (arXiv:1706.03791 Sec. III, Eq. predmodel), error-controlled
+ * linear-scaling quantization into 2^m - 1 intervals with a truncated binary
+ * representation for unpredictable values (Sec. IV-A, Sec. IV-B, Algorithm
+ * 1), canonical Huffman coding of the quantization codes (Sec. IV-A), and the
+ * matching decompression.
+ *
+ * Conventions
+ *  - Every pointer is a plain host or device address; a flag argument says
+ *    which.  The caller owns every buffer: the library never frees caller
+ *    memory and keeps no caller pointer after a call returns.
+ *  - Device buffers must be 4-byte aligned (16-byte alignment is faster).
+ *  - shape[] lists extents slowest -> fastest (C order); only the first ndim
+ *    entries are read.  Points are at most 2^32 - 1 per field.
+ *  - Work is issued on the context's stream (szgb_set_stream); every entry
+ *    point returns after the stream has finished the call's work.
+ *  - Return value 0 on success, a negative SZGB_E* code otherwise
+ *    (szgb_strerror gives the text).  On error, output buffers hold
+ *    unspecified bytes.
+ *  - A context is not thread-safe; use one per host thread.
+ *
+ * Stream format: a 128-byte little-endian header, a codebook of
+ * (u16 symbol, u8 length) for the used quantization codes, one byte length
+ * per row (fastest-axis line) as u16 or u32, then one byte-padded chunk per
+ * row holding, for every point, its canonical Huffman code (MSB first) and,
+ * after a code 0, the unpredictable value's sign, exponent and top t mantissa
+ * bits.  The same bytes are produced by the CPU oracle of the test-suite.
+ */
+#ifndef SZGB_H
+#define SZGB_H
+#include <stddef.h>
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes */
+#define SZGB_OK 0
+#define SZGB_EINVAL (-1)      /* bad argument (shape, bound, n, m, alignment) */
+#define SZGB_ENONFINITE (-2)  /* input holds NaN or Inf */
+#define SZGB_ETRUNC (-3)      /* output buffer too small; needed size reported */
+#define SZGB_ECORRUPT (-4)    /* stream fails a consistency check */
+#define SZGB_ENOMEM (-5)      /* device allocation failed */
+#define SZGB_EBUDGET (-6)     /* call needs more device memory than the budget */
+#define SZGB_ETIMEOUT (-7)    /* a bounded device-side wait ran out */
+#define SZGB_ECUDA (-8)       /* a CUDA runtime call failed */
+#define SZGB_EUNSUPPORTED (-9)/* valid request this build does not run on GPU */
+
+/* error-bound modes (Sec. II, metric 1): absolute, value-range relative,
+ * or both (the smaller bound applies) */
+#define SZGB_ABS 0
+#define SZGB_REL 1
+#define SZGB_ABS_AND_REL 2
+
+typedef struct szgb_ctx szgb_ctx;
+
+typedef struct {
+    int ndim;           /* 1, 2 or 3 */
+    uint64_t shape[3];  /* extents, slowest -> fastest */
+    int mode;           /* SZGB_ABS / SZGB_REL / SZGB_ABS_AND_REL */
+    double eb_abs;      /* absolute bound (>= 0), modes ABS, ABS_AND_REL */
+    double eb_rel;      /* relative bound (>= 0) times (max - min) */
+    int layers;         /* n of the n-layer predictor; 1 or 2 on the GPU
+                           (Sec. III-B; the paper's default is 1) */
+    int m;              /* 2..16: 2^m - 1 intervals; 0 = adaptive (Sec. IV-B) */
+    double theta;       /* adaptive-m hit-rate threshold, e.g. 0.99 */
+} szgb_params;
+
+typedef struct {
+    uint64_t n_points;      /* points in the field */
+    uint64_t n_unpred;      /* unpredictable points (code 0) */
+    uint64_t stream_bytes;  /* size of the compressed stream */
+    int m;                  /* interval bits used (chosen when adaptive) */
+    int maxlen;             /* longest Huffman code */
+    uint32_t nsym;          /* quantization codes in use */
+    float eb_f;             /* effective bound: largest float <= eb */
+    float xmin, xmax;       /* value range of the input */
+} szgb_stats;
+
+/* Creates a context on CUDA device `device` that keeps at most
+ * `device_mem_budget` bytes of device scratch (0 = no limit).  *out is set
+ * on success.  Scratch is allocated on first use and kept for reuse. */
+int szgb_create(szgb_ctx **out, int device, size_t device_mem_budget);
+/* Frees the context and its scratch.  NULL is ignored. */
+void szgb_destroy(szgb_ctx *ctx);
+/* Issue work on `cuda_stream` (a cudaStream_t; NULL = the context's own
+ * stream). */
+int szgb_set_stream(szgb_ctx *ctx, void *cuda_stream);
+
+/* Upper bound of the stream size for these parameters (bytes). */
+size_t szgb_compress_bound(const szgb_params *p);
+
+/* Compresses the FP32 array `data` (host or device) into `out` (host or
+ * device, out_cap bytes).  *out_len receives the stream size, also when
+ * SZGB_ETRUNC reports that out_cap is too small.  opt_stats may be NULL.
+ * Fails with SZGB_ENONFINITE on NaN/Inf input, SZGB_EINVAL on bad
+ * parameters, SZGB_EUNSUPPORTED for layers > 2. */
+int szgb_compress(szgb_ctx *ctx, const float *data, int data_on_device,
+                  const szgb_params *p, uint8_t *out, size_t out_cap,
+                  int out_on_device, size_t *out_len, szgb_stats *opt_stats);
+
+/* As szgb_compress with device buffers only, and additionally writes (when
+ * the pointers are not NULL, device memory, one entry per point in raster
+ * order) the values the compressor recorded for later predictions -- the
+ * exact decompressed values -- and the quantization codes.  For testing. */
+int szgb_compress_trace(szgb_ctx *ctx, const float *data_dev, const szgb_params *p,
+                        uint8_t *out_dev, size_t out_cap, size_t *out_len,
+                        szgb_stats *opt_stats, float *recorded_dev,
+                        uint16_t *codes_dev);
+
+/* Decompresses `in` (host or device, in_len bytes) into `out` (host or
+ * device; out_cap_elems floats, at least the number of points).
+ * SZGB_ECORRUPT when the stream is inconsistent. */
+int szgb_decompress(szgb_ctx *ctx, const uint8_t *in, size_t in_len,
+                    int in_on_device, float *out, size_t out_cap_elems,
+                    int out_on_device);
+
+/* Reads the header of a stream held in host memory: parameters (with the
+ * m actually used) and the number of unpredictable points. */
+int szgb_stream_info(const uint8_t *in_host, size_t in_len, szgb_params *out,
+                     uint64_t *n_unpred);
+
+/* Per-phase device time of the calls made since the last reset, measured
+ * with CUDA events on the context's stream when profiling is on.  Phase
+ * names: szgb_phase_name(i) for i < szgb_num_phases().  ms[i] is the summed
+ * time, calls[i] the number of timed launches. */
+int szgb_set_profiling(szgb_ctx *ctx, int on);
+int szgb_num_phases(void);
+const char *szgb_phase_name(int i);
+int szgb_phase_times(szgb_ctx *ctx, double *ms, uint64_t *calls, int n, int reset);
+
+const char *szgb_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -397,6 +397,9 @@ int szo_compress(const float *x, int ndim, const uint64_t *shape, int mode,
         if (x[p] < xmin) xmin = x[p];
         if (x[p] > xmax) xmax = x[p];
     }
+    /* the stored range is the value range: a signed zero is stored as +0 */
+    xmin = xmin + 0.0f;
+    xmax = xmax + 0.0f;
     float eb_f;
     szo_effective_eb(mode, eb_abs, eb_rel, xmin, xmax, &eb_f);
     int adaptive = (m == 0);

@@ -118,9 +118,11 @@ def choose_m(x, n, eb_f, theta=0.99):
 
 
 def compress(x, mode=REL, eb_abs=0.0, eb_rel=1e-4, n=1, m=0, theta=0.99, order=0,
-             want_aux=False):
+             want_aux=False, layers=None):
     """Returns the stream bytes (and, with want_aux, the recorded values and
-    the quantization codes)."""
+    the quantization codes).  `layers` is an alias of n."""
+    if layers is not None:
+        n = layers
     x = np.ascontiguousarray(x, dtype=np.float32)
     L = lib()
     cap = L.szo_stream_bound(x.ndim, _shape(x))

@@ -1,0 +1,681 @@
+// k_huff.cu -- variable-length (Huffman) coding of the quantization codes
+// (Sec. IV-A: any number of symbols, 2^m for m up to 16) and the stream
+// layout: histogram, codebook build, per-row bit lengths, row offsets, the
+// payload writer, and the decoder tables.
+//
+// Codebook: the used symbols sorted by (frequency, symbol) are merged with
+// two FIFO queues (leaves, internal nodes; a leaf is taken first on equal
+// weights); a symbol's code length is its leaf depth (one used symbol gets
+// length 1).  Codes are canonical: ordered by (length, symbol), consecutive
+// within a length.
+#include "szgb_internal.cuh"
+
+namespace szgb {
+
+// ---------------------------------------------------------------------------
+// histogram of the codes over 2^m bins (warp-aggregated increments)
+
+__global__ void __launch_bounds__(512) k_hist(const uint16_t* __restrict__ codes, uint64_t n,
+                                              uint32_t* hist, const DevState* st) {
+    extern __shared__ uint32_t sh[];
+    if (st->err) return;
+    const int m = st->m;
+    const int nb = 1 << m;
+    const bool use_smem = m <= 13;
+    if (use_smem)
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    uint32_t* H = use_smem ? sh : hist;
+    const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x; base < n; base += nthr) {
+        uint64_t i = base + threadIdx.x;
+        bool v = i < n;
+        unsigned active = __ballot_sync(0xffffffffu, v);
+        if (!v) continue;
+        uint32_t c = __ldcs(codes + i);
+        if (c >= (uint32_t)nb) c = 0;  // codes are < 2^m; never index past the bins
+        unsigned peers = __match_any_sync(active, c);
+        int leader = __ffs(peers) - 1;
+        if ((int)(threadIdx.x & 31) == leader) atomicAdd(&H[c], (uint32_t)__popc(peers));
+    }
+    if (use_smem) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < nb; i += blockDim.x)
+            if (sh[i]) atomicAdd(&hist[i], sh[i]);
+    }
+}
+
+int launch_histogram(const uint16_t* codes, uint64_t n, uint32_t* hist, DevState* st, cudaStream_t s) {
+    int blocks = (int)((n + 4095) / 4096);
+    if (blocks > 4 * 152) blocks = 4 * 152;
+    if (blocks < 1) blocks = 1;
+    size_t smem = (size_t)(1 << 13) * 4;
+    if (cudaFuncSetAttribute(k_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return SZGB_ECUDA;
+    k_hist<<<blocks, 512, smem, s>>>(codes, n, hist, st);
+    return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// codebook build: one CTA of 1024 threads.
+//   sortbuf: >= 2^16 u64 keys (freq << 16 | symbol)
+//   nodebuf: >= 4 * 2^16 u32 (parent links, depths)
+
+constexpr int kCbThreads = 1024;
+constexpr int kSmemSortCap = 8192;
+
+__device__ void bitonic_sort(uint64_t* a, int n_pow2) {
+    for (int k = 2; k <= n_pow2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n_pow2; i += blockDim.x) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    uint64_t x = a[i], y = a[ixj];
+                    bool up = (i & k) == 0;
+                    if ((x > y) == up) { a[i] = y; a[ixj] = x; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// canonical code assignment over symbols listed in ascending order: the code
+// of a symbol of length L is first[L] + (number of earlier symbols of length
+// L).  Done by warp 0, 32 symbols at a time.
+__device__ void canonical_assign(const uint32_t* syms, int n, const uint8_t* len, uint64_t* first_io,
+                                 uint64_t* cw_out, uint32_t* rank_out) {
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    for (int base = 0; base < n; base += 32) {
+        int i = base + lane;
+        bool v = i < n;
+        unsigned act = __ballot_sync(0xffffffffu, v);
+        if (v) {
+            uint32_t s = syms[i];
+            int L = len[s];
+            unsigned peers = __match_any_sync(act, L);
+            int rank = __popc(peers & ((1u << lane) - 1u));
+            uint64_t f = first_io[L];
+            if (cw_out) cw_out[s] = f + (uint64_t)rank;
+            if (rank_out) rank_out[i] = (uint32_t)(f + rank);
+            __syncwarp(act);
+            if (rank == 0) first_io[L] = f + (uint64_t)__popc(peers);
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(kCbThreads) k_codebook(const uint32_t* __restrict__ hist, DevState* st,
+                                                          uint8_t* len, uint64_t* cw, uint64_t* sortbuf,
+                                                          uint32_t* nodebuf) {
+    __shared__ uint64_t s_keys[kSmemSortCap];
+    __shared__ uint32_t s_wsum[kCbThreads / 32];
+    __shared__ uint32_t s_n;
+    __shared__ uint32_t s_cnt[66];
+    __shared__ uint64_t s_first[66];
+    if (st->err) return;
+    const int m = st->m;
+    const int ntot = 1 << m;
+    uint32_t* usedlist = nodebuf;                 // [2^16] used symbols, ascending
+    uint32_t* par = nodebuf + 65536;              // [2^17] parent of node
+    uint32_t* dep = nodebuf + 3 * 65536;          // [2^17] depth (overlaps nothing used later)
+    uint64_t* wbuf = sortbuf + 65536;             // [2^17] node weights
+    // 1. compact the used symbols (ascending) with their keys
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    for (int base = 0; base < ntot; base += kCbThreads) {
+        int s = base + threadIdx.x;
+        uint32_t f = s < ntot ? hist[s] : 0u;
+        bool u = f > 0;
+        unsigned b = __ballot_sync(0xffffffffu, u);
+        int wid = threadIdx.x >> 5, ln = threadIdx.x & 31;
+        if (ln == 0) s_wsum[wid] = __popc(b);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t acc = s_n;
+            for (int w = 0; w < kCbThreads / 32; w++) { uint32_t t = s_wsum[w]; s_wsum[w] = acc; acc += t; }
+            s_n = acc;
+        }
+        __syncthreads();
+        if (u) {
+            uint32_t pos = s_wsum[wid] + __popc(b & ((1u << ln) - 1u));
+            usedlist[pos] = (uint32_t)s;
+            sortbuf[pos] = ((uint64_t)f << 16) | (uint64_t)s;
+        }
+        __syncthreads();
+    }
+    const int n = (int)s_n;
+    for (int s = threadIdx.x; s < ntot; s += kCbThreads) len[s] = 0;
+    __syncthreads();
+    if (n == 0) return;
+    if (n == 1) {
+        if (threadIdx.x == 0) {
+            uint32_t s = usedlist[0];
+            len[s] = 1;
+            cw[s] = 0;
+            st->nsym = 1;
+            st->maxlen = 1;
+        }
+        return;
+    }
+    // 2. sort keys ascending (frequency, then symbol)
+    int np2 = 1;
+    while (np2 < n) np2 <<= 1;
+    uint64_t* keys;
+    if (np2 <= kSmemSortCap) {
+        keys = s_keys;
+        for (int i = threadIdx.x; i < np2; i += kCbThreads) s_keys[i] = i < n ? sortbuf[i] : ~0ull;
+    } else {
+        keys = sortbuf;
+        for (int i = n + threadIdx.x; i < np2; i += kCbThreads) sortbuf[i] = ~0ull;
+    }
+    __syncthreads();
+    bitonic_sort(keys, np2);
+    // 3. two-queue merge (thread 0): leaves 0..n-1, internal nodes n..2n-2
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < n; i++) wbuf[i] = keys[i] >> 16;
+        int q1 = 0, q2 = n, nxt = n;
+        uint64_t wl = wbuf[0];
+        for (int step = 0; step < n - 1; step++) {
+            int pk[2];
+            uint64_t wsum = 0;
+#pragma unroll
+            for (int p = 0; p < 2; p++) {
+                bool leaf = q1 < n && (q2 >= nxt || wl <= wbuf[q2]);
+                if (leaf) {
+                    pk[p] = q1;
+                    wsum += wl;
+                    q1++;
+                    wl = q1 < n ? wbuf[q1] : 0;
+                } else {
+                    pk[p] = q2;
+                    wsum += wbuf[q2];
+                    q2++;
+                }
+            }
+            wbuf[nxt] = wsum;
+            par[pk[0]] = (uint32_t)nxt;
+            par[pk[1]] = (uint32_t)nxt;
+            nxt++;
+        }
+        // 4. depths, root = 2n-2, parents always later than children
+        int total = 2 * n - 1;
+        dep[total - 1] = 0;
+        int maxlen = 0;
+        for (int v = total - 2; v >= 0; v--) {
+            int d = (int)dep[par[v]] + 1;
+            dep[v] = (uint32_t)d;
+            if (v < n && d > maxlen) maxlen = d;
+        }
+        for (int i = 0; i < n; i++) len[(uint32_t)(keys[i] & 0xffffu)] = (uint8_t)dep[i];
+        st->nsym = (uint32_t)n;
+        st->maxlen = (uint32_t)maxlen;
+    }
+    __syncthreads();
+    // 5. canonical codes: first code of each length
+    if (threadIdx.x < 66) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += kCbThreads) atomicAdd(&s_cnt[len[usedlist[i]]], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t code = 0;
+        int prevL = 0;
+        bool firstSeen = false;
+        for (int L = 1; L <= 64; L++) {
+            if (!s_cnt[L]) continue;
+            if (!firstSeen) { code = 0; firstSeen = true; }
+            else code = code << (L - prevL);
+            s_first[L] = code;
+            code += s_cnt[L];
+            prevL = L;
+        }
+    }
+    __syncthreads();
+    canonical_assign(usedlist, n, len, s_first, cw, nullptr);
+}
+
+int launch_codebook(const uint32_t* hist, DevState* st, uint8_t* len, uint64_t* cw, uint64_t* sortbuf,
+                    uint32_t* nodebuf, cudaStream_t s) {
+    k_codebook<<<1, kCbThreads, 0, s>>>(hist, st, len, cw, sortbuf, nodebuf);
+    return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// per-row bit counts: Huffman code bits plus 9 + t record bits after code 0
+
+__global__ void __launch_bounds__(256) k_rowbits(const uint16_t* __restrict__ codes,
+                                                 const float* __restrict__ x, uint64_t rows,
+                                                 uint64_t rowlen, const uint8_t* __restrict__ len,
+                                                 uint32_t* rowbytes, DevState* st) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t wglob = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    if (st->err) return;
+    const int e_eb = st->e_eb;
+    unsigned long long kcount = 0;
+    for (uint64_t r = wglob; r < rows; r += nw) {
+        const uint64_t base = r * rowlen;
+        uint64_t bits = 0;
+        for (uint64_t l = lane; l < rowlen; l += 32) {
+            uint32_t c = codes[base + l];
+            bits += len[c];
+            if (c == 0) {
+                bits += 9 + trunc_bits(__float_as_uint(x[base + l]), e_eb);
+                kcount++;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) bits += __shfl_xor_sync(0xffffffffu, bits, o);
+        if (lane == 0) {
+            uint64_t b = (bits + 7) / 8;
+            rowbytes[r] = (uint32_t)b;
+            atomicMax(&st->maxrow, (uint32_t)b);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) kcount += __shfl_xor_sync(0xffffffffu, kcount, o);
+    if (lane == 0 && kcount) atomicAdd(&st->K, kcount);
+}
+
+int launch_rowbits(const uint16_t* codes, const float* x, uint64_t rows, uint64_t rowlen,
+                   const uint8_t* len, uint32_t* rowbytes, DevState* st, cudaStream_t s) {
+    uint64_t warps = rows;
+    uint64_t blocks = (warps * 32 + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_rowbits<<<(int)blocks, 256, 0, s>>>(codes, x, rows, rowlen, len, rowbytes, st);
+    return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of row byte counts -> row offsets (three phases)
+
+constexpr int kScanTile = 2048;
+
+__global__ void __launch_bounds__(1024) k_scan_local(const uint32_t* __restrict__ in, uint64_t n,
+                                                     uint64_t* out, uint64_t* blocksums) {
+    __shared__ uint64_t s[kScanTile];
+    const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+    for (int i = threadIdx.x; i < kScanTile; i += blockDim.x) s[i] = (base + i < n) ? in[base + i] : 0;
+    __syncthreads();
+    // Hillis-Steele inclusive scan over 2048 elements (2 per thread)
+    for (int off = 1; off < kScanTile; off <<= 1) {
+        uint64_t a0 = 0, a1 = 0;
+        int i0 = threadIdx.x, i1 = threadIdx.x + 1024;
+        if (i0 >= off) a0 = s[i0 - off];
+        if (i1 >= off) a1 = s[i1 - off];
+        __syncthreads();
+        s[i0] += a0;
+        s[i1] += a1;
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < kScanTile; i += blockDim.x) {
+        uint64_t excl = i ? s[i - 1] : 0;
+        if (base + i < n) out[base + i] = excl;
+    }
+    if (threadIdx.x == 0) blocksums[blockIdx.x] = s[kScanTile - 1];
+}
+
+__global__ void __launch_bounds__(1024) k_scan_blocks(uint64_t* blocksums, int nblocks, DevState* st,
+                                                      uint64_t rows, int finalize) {
+    if (threadIdx.x == 0) {
+        uint64_t acc = 0;
+        for (int b = 0; b < nblocks; b++) { uint64_t t = blocksums[b]; blocksums[b] = acc; acc += t; }
+        if (finalize) {
+            st->payload = acc;
+            unsigned tw = st->maxrow <= 0xffffu ? 2u : 4u;
+            st->table_width = tw;
+            st->cb_bytes = (3ull * st->nsym + 3) & ~3ull;
+            st->tab_bytes = ((uint64_t)tw * rows + 3) & ~3ull;
+            st->total = (uint64_t)kHeaderBytes + st->cb_bytes + st->tab_bytes + acc;
+            st->fits = st->total <= st->cap;
+            if (!st->fits) st->err |= kErrOverflow;
+        } else {
+            st->payload = acc;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_add(uint64_t* out, uint64_t n, const uint64_t* blocksums) {
+    const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+    const uint64_t add = blocksums[blockIdx.x];
+    for (int i = threadIdx.x; i < kScanTile; i += blockDim.x)
+        if (base + i < n) out[base + i] += add;
+}
+
+int launch_scan_rows(const uint32_t* rowbytes, uint64_t rows, uint64_t* rowoff, uint64_t* blocksums,
+                     DevState* st, int finalize_compress, cudaStream_t s) {
+    int nb = (int)((rows + kScanTile - 1) / kScanTile);
+    k_scan_local<<<nb, 1024, 0, s>>>(rowbytes, rows, rowoff, blocksums);
+    k_scan_blocks<<<1, 32, 0, s>>>(blocksums, nb, st, rows, finalize_compress);
+    k_scan_add<<<nb, 1024, 0, s>>>(rowoff, rows, blocksums);
+    return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// stream writer
+
+__device__ __forceinline__ void wr_u16(uint8_t* p, uint32_t v) { p[0] = (uint8_t)v; p[1] = (uint8_t)(v >> 8); }
+__device__ __forceinline__ void wr_u32(uint8_t* p, uint32_t v) {
+    for (int i = 0; i < 4; i++) p[i] = (uint8_t)(v >> (8 * i));
+}
+__device__ __forceinline__ void wr_u64(uint8_t* p, uint64_t v) {
+    for (int i = 0; i < 8; i++) p[i] = (uint8_t)(v >> (8 * i));
+}
+
+// header, codebook section and chunk table
+__global__ void __launch_bounds__(256) k_write_meta(const CallParams cp, uint64_t rows,
+                                                    const uint8_t* __restrict__ len,
+                                                    const uint32_t* __restrict__ usedlist,
+                                                    const uint32_t* __restrict__ rowbytes,
+                                                    const uint64_t* __restrict__ rowoff, uint8_t* out,
+                                                    DevState* st) {
+    if (!st->fits || st->err) return;
+    const uint64_t cb = st->cb_bytes, tb = st->tab_bytes;
+    const unsigned tw = st->table_width;
+    const uint32_t nsym = st->nsym;
+    uint8_t* cbp = out + kHeaderBytes;
+    uint8_t* tab = cbp + cb;
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
+    if (tid == 0) {
+        uint8_t* h = out;
+        for (int i = 0; i < kHeaderBytes; i++) h[i] = 0;
+        h[0] = 'S'; h[1] = 'Z'; h[2] = 'G'; h[3] = 'B';
+        wr_u16(h + 4, 1);
+        wr_u16(h + 6, kHeaderBytes);
+        h[8] = (uint8_t)cp.ndim;
+        h[9] = (uint8_t)cp.layers;
+        h[10] = (uint8_t)st->m;
+        h[11] = (uint8_t)cp.mode;
+        h[12] = (uint8_t)st->maxlen;
+        h[13] = (uint8_t)tw;
+        wr_u64(h + 16, cp.d0);
+        wr_u64(h + 24, cp.d1);
+        wr_u64(h + 32, cp.d2);
+        wr_u64(h + 40, (uint64_t)__double_as_longlong(cp.eb_abs));
+        wr_u64(h + 48, (uint64_t)__double_as_longlong(cp.eb_rel));
+        wr_u32(h + 56, __float_as_uint(st->eb_f));
+        wr_u32(h + 60, __float_as_uint(st->xmin));
+        wr_u32(h + 64, __float_as_uint(st->xmax));
+        wr_u32(h + 68, nsym);
+        wr_u64(h + 72, rows);
+        wr_u64(h + 80, st->K);
+        wr_u64(h + 88, st->payload);
+        wr_u64(h + 96, st->total);
+        wr_u64(h + 104, (uint64_t)__double_as_longlong(cp.theta));
+        h[112] = (uint8_t)(cp.m_user == 0);
+    }
+    for (uint64_t i = tid; i < cb; i += nthr) {
+        uint64_t e = i / 3;
+        int k = (int)(i % 3);
+        uint8_t v = 0;
+        if (e < nsym) {
+            uint32_t s = usedlist[e];
+            v = (k == 0) ? (uint8_t)s : (k == 1) ? (uint8_t)(s >> 8) : len[s];
+        }
+        cbp[i] = v;
+    }
+    for (uint64_t i = tid; i < tb; i += nthr) {
+        uint64_t r = i / tw;
+        int k = (int)(i % tw);
+        tab[i] = (r < rows) ? (uint8_t)(rowbytes[r] >> (8 * k)) : 0;
+    }
+}
+
+__device__ __forceinline__ void put32(uint32_t* buf, uint32_t o, uint32_t v, int n) {
+    // n in [1,32], v < 2^n, MSB-first at bit offset o
+    uint32_t i = o >> 5, s = o & 31;
+    if (s + n <= 32) {
+        atomicOr(&buf[i], v << (32 - s - n));
+    } else {
+        atomicOr(&buf[i], v >> (s + n - 32));
+        atomicOr(&buf[i + 1], v << (64 - s - n));
+    }
+}
+__device__ __forceinline__ void put64(uint32_t* buf, uint32_t o, uint64_t v, int n) {
+    if (n > 32) {
+        put32(buf, o, (uint32_t)(v >> 32), n - 32);
+        put32(buf, o + (n - 32), (uint32_t)v, 32);
+    } else if (n > 0) {
+        put32(buf, o, (uint32_t)v, n);
+    }
+}
+
+constexpr int kEncWarps = 8;
+constexpr int kEncBufWords = 112;
+
+// payload: one warp per row; 32 points at a time are placed by a warp scan of
+// their bit lengths into a shared-memory word buffer whose completed words
+// are stored.  Every payload byte belongs to exactly one row (rows are
+// byte-padded), so a word a row shares with a neighbour is written byte by
+// byte for the row's own bytes only: no atomics, no zeroing pass.
+__device__ __forceinline__ void store_word_bytes(uint8_t* plb, uint64_t gw, uint32_t val, uint32_t lo,
+                                                 uint32_t hi) {
+    // val: big-endian word value; write bytes covering bits [lo, hi) of it
+    if (lo == 0 && hi == 32) {
+        reinterpret_cast<uint32_t*>(plb)[gw] = bswap32(val);
+    } else {
+        for (uint32_t k = lo >> 3; k < ((hi + 7) >> 3); k++) plb[4 * gw + k] = (uint8_t)(val >> (24 - 8 * k));
+    }
+}
+
+__global__ void __launch_bounds__(kEncWarps * 32) k_encode(const uint16_t* __restrict__ codes,
+                                                          const float* __restrict__ x, uint64_t rows,
+                                                          uint64_t rowlen, const uint8_t* __restrict__ len,
+                                                          const uint64_t* __restrict__ cw,
+                                                          const uint64_t* __restrict__ rowoff,
+                                                          uint8_t* out, DevState* st) {
+    __shared__ uint32_t sbuf[kEncWarps][kEncBufWords];
+    if (!st->fits || st->err) return;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t* buf = sbuf[wib];
+    uint8_t* plb = out + kHeaderBytes + st->cb_bytes + st->tab_bytes;
+    const int e_eb = st->e_eb;
+    const uint64_t wglob = blockIdx.x * (uint64_t)kEncWarps + wib;
+    const uint64_t nw = (uint64_t)gridDim.x * kEncWarps;
+    for (uint64_t r = wglob; r < rows; r += nw) {
+        const uint64_t g0 = rowoff[r] * 8;        // first bit of the row in the payload
+        const uint64_t w0 = g0 >> 5;              // its word
+        const uint32_t lo0 = (uint32_t)(g0 & 31); // bits of w0 owned by earlier rows
+        uint64_t curw = w0;                        // global word held in buf[0]
+        uint32_t bitpos = lo0;                     // bits already used in buf[0]
+        for (int i = lane; i < kEncBufWords; i += 32) buf[i] = 0;
+        __syncwarp();
+        const uint64_t base = r * rowlen;
+        for (uint64_t l0 = 0; l0 < rowlen; l0 += 32) {
+            uint64_t l = l0 + lane;
+            bool v = l < rowlen;
+            uint32_t c = v ? codes[base + l] : 0u;
+            int L = v ? len[c] : 0;
+            uint64_t code = v ? cw[c] : 0;
+            int nrec = 0;
+            uint32_t se = 0, mb = 0;
+            int t = 0;
+            if (v && c == 0) {
+                uint32_t u = __float_as_uint(x[base + l]);
+                t = trunc_bits(u, e_eb);
+                se = u >> 23;
+                mb = t ? ((u >> (23 - t)) & ((1u << t) - 1u)) : 0u;
+                nrec = 9 + t;
+            }
+            uint32_t nbits = (uint32_t)(L + nrec);
+            uint32_t incl = nbits;
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            uint32_t off = bitpos + incl - nbits;
+            if (L) put64(buf, off, code, L);
+            if (nrec) {
+                put32(buf, off + L, se, 9);
+                if (t) put32(buf, off + L + 9, mb, t);
+            }
+            __syncwarp();
+            uint32_t end = bitpos + total;
+            uint32_t full = end >> 5;
+            for (uint32_t i = lane; i < full; i += 32) {
+                uint64_t gw = curw + i;
+                store_word_bytes(plb, gw, buf[i], gw == w0 ? lo0 : 0u, 32u);
+            }
+            __syncwarp();
+            uint32_t carry = buf[full];
+            __syncwarp();
+            for (int i = lane; i < kEncBufWords; i += 32) buf[i] = 0;
+            __syncwarp();
+            if (lane == 0) buf[0] = carry;
+            __syncwarp();
+            curw += full;
+            bitpos = end & 31;
+        }
+        if (bitpos && lane == 0) store_word_bytes(plb, curw, buf[0], curw == w0 ? lo0 : 0u, bitpos);
+        __syncwarp();
+    }
+}
+
+int launch_write_meta(const CallParams& cp, uint64_t rows, const uint8_t* len, const uint32_t* usedlist,
+                      const uint32_t* rowbytes, const uint64_t* rowoff, uint8_t* out, DevState* st,
+                      cudaStream_t s) {
+    uint64_t blocks = (rows + 255) / 256;
+    if (blocks < 8) blocks = 8;
+    if (blocks > 1024) blocks = 1024;
+    k_write_meta<<<(int)blocks, 256, 0, s>>>(cp, rows, len, usedlist, rowbytes, rowoff, out, st);
+    return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
+}
+
+int launch_encode(const uint16_t* codes, const float* x, uint64_t rows, uint64_t rowlen, const uint8_t* len,
+                  const uint64_t* cw, const uint64_t* rowoff, uint8_t* out, DevState* st, cudaStream_t s) {
+    uint64_t blocks = (rows + kEncWarps - 1) / kEncWarps;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks < 1) blocks = 1;
+    k_encode<<<(int)blocks, kEncWarps * 32, 0, s>>>(codes, x, rows, rowlen, len, cw, rowoff, out, st);
+    return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// decoder tables from the codebook section (one CTA).
+//   lut[2^T]: (symbol << 8) | length for codes of length <= T (0 = longer)
+//   dectab[0..64] first code low word per length, [65..129] high word,
+//   [130..194] count, [195..259] start index into the sorted list,
+//   then the symbols sorted by (length, symbol) as u16.
+
+__global__ void __launch_bounds__(1024) k_decode_tables(const uint8_t* __restrict__ cb, uint32_t nsym, int m,
+                                                        uint32_t* lut, uint32_t* dectab, uint8_t* lenbuf,
+                                                        uint32_t* symbuf, DevState* st) {
+    __shared__ uint32_t s_cnt[66];
+    __shared__ uint64_t s_first[66];
+    __shared__ uint64_t s_next[66];
+    __shared__ uint32_t s_start[66];
+    __shared__ int s_bad;
+    __shared__ int s_maxlen;
+    const int ntot = 1 << m;
+    if (threadIdx.x < 66) { s_cnt[threadIdx.x] = 0; s_first[threadIdx.x] = 0; }
+    if (threadIdx.x == 0) { s_bad = 0; s_maxlen = 0; }
+    for (int s = threadIdx.x; s < ntot; s += blockDim.x) lenbuf[s] = 0;
+    __syncthreads();
+    for (uint32_t e = threadIdx.x; e < nsym; e += blockDim.x) {
+        uint32_t s = cb[3 * e] | ((uint32_t)cb[3 * e + 1] << 8);
+        uint32_t L = cb[3 * e + 2];
+        uint32_t prev = e ? (cb[3 * (e - 1)] | ((uint32_t)cb[3 * (e - 1) + 1] << 8)) : 0;
+        if (s >= (uint32_t)ntot || L < 1 || L > 64 || (e && s <= prev)) { s_bad = 1; continue; }
+        lenbuf[s] = (uint8_t)L;
+        symbuf[e] = s;
+        atomicAdd(&s_cnt[L], 1u);
+        atomicMax(&s_maxlen, (int)L);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !s_bad) {
+        // canonical first codes, start indices, and a Kraft check
+        uint64_t code = 0;
+        int prevL = 0;
+        bool seen = false;
+        uint32_t start = 0;
+        for (int L = 1; L <= 64; L++) {
+            s_start[L] = start;
+            if (!s_cnt[L]) continue;
+            if (!seen) { code = 0; seen = true; }
+            else code = code << (L - prevL);
+            s_first[L] = code;
+            if (L < 64 && (code + s_cnt[L]) > (1ull << L)) s_bad = 1;
+            code += s_cnt[L];
+            prevL = L;
+            start += s_cnt[L];
+        }
+        if (nsym == 1 && s_maxlen != 1) s_bad = 1;
+    }
+    __syncthreads();
+    if (s_bad) {
+        if (threadIdx.x == 0) st->err |= kErrCorrupt;
+        return;
+    }
+    const int maxlen = s_maxlen;
+    const int T = maxlen < kLutBits ? maxlen : kLutBits;
+    for (int i = threadIdx.x; i < (1 << T); i += blockDim.x) lut[i] = 0;
+    if (threadIdx.x < 65) {
+        dectab[threadIdx.x] = (uint32_t)s_first[threadIdx.x];
+        dectab[65 + threadIdx.x] = (uint32_t)(s_first[threadIdx.x] >> 32);
+        dectab[130 + threadIdx.x] = s_cnt[threadIdx.x];
+        dectab[195 + threadIdx.x] = s_start[threadIdx.x];
+        s_next[threadIdx.x] = s_first[threadIdx.x];
+    }
+    __syncthreads();
+    // ranks within each length (warp 0, ascending symbols) -> codes
+    // sorted[start[L] + rank] = symbol; code = first[L] + rank
+    uint16_t* sorted = reinterpret_cast<uint16_t*>(dectab + 260);
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        for (uint32_t base = 0; base < nsym; base += 32) {
+            uint32_t i = base + lane;
+            bool v = i < nsym;
+            unsigned act = __ballot_sync(0xffffffffu, v);
+            if (v) {
+                uint32_t s = symbuf[i];
+                int L = lenbuf[s];
+                unsigned peers = __match_any_sync(act, L);
+                int rank = __popc(peers & ((1u << lane) - 1u));
+                uint64_t f = s_next[L];
+                uint64_t code = f + (uint64_t)rank;
+                uint32_t idx = s_start[L] + (uint32_t)(code - s_first[L]);
+                sorted[idx] = (uint16_t)s;
+                if (L <= T) {
+                    uint32_t lo = (uint32_t)code << (T - L), n = 1u << (T - L);
+                    for (uint32_t k = 0; k < n; k++) lut[lo + k] = (s << 8) | (uint32_t)L;
+                }
+                __syncwarp(act);
+                if (rank == 0) s_next[L] = f + (uint64_t)__popc(peers);
+            }
+            __syncwarp();
+        }
+    }
+    if (threadIdx.x == 0) {
+        st->maxlen = (uint32_t)maxlen;
+        st->lut_bits = (uint32_t)T;
+        st->nsym = nsym;
+    }
+}
+
+int launch_decode_tables(const uint8_t* codebook, uint32_t nsym, int m, uint32_t* lut, uint32_t* dec_tab,
+                         uint8_t* lenbuf, uint32_t* symbuf, DevState* st, cudaStream_t s) {
+    k_decode_tables<<<1, 1024, 0, s>>>(codebook, nsym, m, lut, dec_tab, lenbuf, symbuf, st);
+    return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
+}
+
+__global__ void k_read_rowbytes(const uint8_t* __restrict__ tab, int width, uint64_t rows, uint32_t* rb) {
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < rows;
+         r += (uint64_t)gridDim.x * blockDim.x) {
+        const uint8_t* p = tab + r * width;
+        uint32_t v = p[0] | ((uint32_t)p[1] << 8);
+        if (width == 4) v |= ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+        rb[r] = v;
+    }
+}
+
+int launch_read_rowbytes(const uint8_t* table, int width, uint64_t rows, uint32_t* rowbytes, cudaStream_t s) {
+    uint64_t blocks = (rows + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    k_read_rowbytes<<<(int)blocks, 256, 0, s>>>(table, width, rows, rowbytes);
+    return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
+}
+
+}  // namespace szgb

@@ -1,0 +1,631 @@
+// szgb.cu -- the C ABI: context, device scratch, and the compress /
+// decompress pipelines.
+//
+// compress:   range + bound (K1) -> adaptive m (K8, when m = 0) -> wavefront
+//             predict + quantize (K2) -> histogram (K3) -> codebook (K4) ->
+//             row bit lengths -> row offsets -> header/codebook/table ->
+//             payload (K5).
+// decompress: header (host) -> decoder tables -> row offsets -> wavefront
+//             decode + reconstruct (K6 fused into K7).
+// Every launch goes to the context's stream; a call returns after one
+// stream synchronisation at its end.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "szgb_internal.cuh"
+
+using namespace szgb;
+
+namespace {
+
+enum Phase {
+    PH_H2D = 0, PH_RANGE, PH_ADAPT, PH_WAVE_C, PH_HIST, PH_CODEBOOK, PH_ROWBITS, PH_SCAN, PH_WRITE,
+    PH_D2H, PH_DEC_TABLES, PH_DEC_SCAN, PH_WAVE_D, PH_N
+};
+const char* kPhaseNames[PH_N] = {"h2d", "range", "adapt", "wave_compress", "histogram", "codebook",
+                                  "rowbits", "scan", "write", "d2h", "decode_tables", "decode_scan",
+                                  "wave_decompress"};
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Arena {
+    // offsets into the scratch allocation
+    std::vector<std::pair<void**, size_t>> items;
+    size_t total = 0;
+    template <typename T>
+    void add(T** p, size_t count) {
+        items.push_back({reinterpret_cast<void**>(p), total});
+        total = align_up(total + std::max<size_t>(count * sizeof(T), 1), 256);
+    }
+    void bind(void* base) {
+        for (auto& it : items) *it.first = static_cast<char*>(base) + it.second;
+    }
+};
+
+}  // namespace
+
+struct szgb_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+    size_t budget = 0;
+    void* scratch = nullptr;
+    size_t scratch_cap = 0;
+    DevState* h_state = nullptr;  // pinned
+    bool profiling = false;
+    double ph_ms[PH_N] = {};
+    uint64_t ph_calls[PH_N] = {};
+    cudaEvent_t ev0[PH_N] = {}, ev1[PH_N] = {};
+    int sm_count = 152;
+    int W2 = 8, W3 = 8;
+    uint64_t timeout_ns = 4000000000ull;
+};
+
+namespace {
+
+struct PhaseTimer {
+    szgb_ctx* c;
+    int ph;
+    PhaseTimer(szgb_ctx* c_, int ph_) : c(c_), ph(ph_) {
+        if (c->profiling) cudaEventRecord(c->ev0[ph], c->stream);
+    }
+    ~PhaseTimer() {
+        if (!c->profiling) return;
+        cudaEventRecord(c->ev1[ph], c->stream);
+        cudaEventSynchronize(c->ev1[ph]);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev0[ph], c->ev1[ph]);
+        c->ph_ms[ph] += ms;
+        c->ph_calls[ph]++;
+    }
+};
+
+int ensure_scratch(szgb_ctx* c, size_t need) {
+    if (need <= c->scratch_cap) return SZGB_OK;
+    if (c->budget && need > c->budget) return SZGB_EBUDGET;
+    if (c->scratch) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->scratch);
+        c->scratch = nullptr;
+        c->scratch_cap = 0;
+    }
+    size_t cap = align_up(need + need / 8, 1 << 20);
+    if (c->budget && cap > c->budget) cap = need;
+    if (cudaMalloc(&c->scratch, cap) != cudaSuccess) {
+        cudaGetLastError();
+        return SZGB_ENOMEM;
+    }
+    c->scratch_cap = cap;
+    return SZGB_OK;
+}
+
+int check_params(const szgb_params* p, CallParams* cp) {
+    if (!p || p->ndim < 1 || p->ndim > 3) return SZGB_EINVAL;
+    uint64_t d[3] = {1, 1, 1};
+    for (int a = 0; a < p->ndim; a++) {
+        if (p->shape[a] == 0 || p->shape[a] > 0xffffffffull) return SZGB_EINVAL;
+        d[3 - p->ndim + a] = p->shape[a];
+    }
+    unsigned __int128 n = (unsigned __int128)d[0] * d[1] * d[2];
+    if (n >= ((unsigned __int128)1 << 32)) return SZGB_EINVAL;
+    if (p->mode < 0 || p->mode > 2) return SZGB_EINVAL;
+    if (p->mode != SZGB_REL && !(p->eb_abs >= 0.0)) return SZGB_EINVAL;
+    if (p->mode != SZGB_ABS && !(p->eb_rel >= 0.0)) return SZGB_EINVAL;
+    if (p->m != 0 && (p->m < 2 || p->m > 16)) return SZGB_EINVAL;
+    if (p->layers < 1 || p->layers > 4) return SZGB_EINVAL;
+    if (p->m == 0 && !(p->theta == p->theta)) return SZGB_EINVAL;
+    cp->ndim = p->ndim;
+    cp->d0 = d[0];
+    cp->d1 = d[1];
+    cp->d2 = d[2];
+    cp->mode = p->mode;
+    cp->eb_abs = p->eb_abs;
+    cp->eb_rel = p->eb_rel;
+    cp->layers = p->layers;
+    cp->m_user = p->m;
+    cp->theta = p->theta;
+    return p->layers > kMaxLayers ? SZGB_EUNSUPPORTED : SZGB_OK;
+}
+
+WaveGeom make_geom(const szgb_ctx* c, const CallParams& cp, int layers) {
+    WaveGeom g = {};
+    g.N = cp.d2;
+    g.ntiles = (int)((cp.d2 + kTile - 1) / kTile);
+    g.aligned = (cp.d2 % 4) == 0;
+    if (cp.ndim == 3) {
+        g.ndim = 3;
+        g.P = cp.d0;
+        g.M = cp.d1;
+        int W = c->W3;
+        if ((uint64_t)W > cp.d0) W = (int)cp.d0;
+        if (W < 2 * layers) W = 2 * layers;  // the plane halo's rows all have sweeps >= 0
+        g.W = W;
+        g.nb0 = (int)((cp.d0 + W - 1) / W);
+        g.nb1 = (int)((cp.d1 + 31) / 32);
+        g.nsweeps = g.ntiles + W + 31;
+    } else {
+        g.ndim = 2;
+        g.P = 1;
+        g.M = cp.d0 * cp.d1;  // 1D: a single row
+        int W = c->W2;
+        int need = (int)((g.M + 31) / 32);
+        if (W > need) W = need;
+        if (W < 1) W = 1;
+        g.W = W;
+        g.nb0 = 1;
+        g.nb1 = (int)((g.M + 32ull * W - 1) / (32ull * W));
+        g.nsweeps = g.ntiles + 32 * W;
+    }
+    g.num_ctas = g.nb0 * g.nb1;
+    return g;
+}
+
+void halo_sizes(const WaveGeom& g, int layers, size_t* row_floats, size_t* plane_floats) {
+    size_t tpr = (size_t)g.ntiles * kTile;
+    if (g.ndim == 3) {
+        *row_floats = (size_t)g.P * g.nb1 * layers * tpr;
+        *plane_floats = (size_t)g.nb0 * g.nb1 * layers * (32 + layers) * tpr;
+    } else {
+        *row_floats = (size_t)g.nb1 * layers * tpr;
+        *plane_floats = 4;
+    }
+}
+
+int dev_errors(const DevState& s) {
+    if (s.err & kErrNonFinite) return SZGB_ENONFINITE;
+    if (s.err & kErrTimeout) return SZGB_ETIMEOUT;
+    if (s.err & kErrCorrupt) return SZGB_ECORRUPT;
+    if (s.err & kErrOverflow) return SZGB_ETRUNC;
+    return SZGB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// compress
+
+int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb_params* p, uint8_t* out,
+                  size_t out_cap, int out_on_device, size_t* out_len, szgb_stats* stats, float* rec_dev,
+                  uint16_t* codes_dev) {
+    if (!c || !data || !out_len) return SZGB_EINVAL;
+    if (((uintptr_t)rec_dev % 16) != 0 || ((uintptr_t)codes_dev % 8) != 0) return SZGB_EINVAL;
+    CallParams cp;
+    int rc = check_params(p, &cp);
+    if (rc) return rc;
+    if (cudaSetDevice(c->device) != cudaSuccess) return SZGB_ECUDA;
+    const uint64_t N = cp.d0 * cp.d1 * cp.d2;
+    const uint64_t rows = cp.d0 * cp.d1;
+    const uint64_t rowlen = cp.d2;
+    const int layers = cp.layers;
+    WaveGeom g = make_geom(c, cp, layers);
+    size_t hrow, hplane;
+    halo_sizes(g, layers, &hrow, &hplane);
+    const size_t bound = szgb_compress_bound(p);
+    const bool direct_out = out_on_device && ((uintptr_t)out % 4 == 0) && out_cap >= bound;
+    const bool direct_in = data_on_device && ((uintptr_t)data % 16 == 0);
+    const int range_blocks = (int)std::min<uint64_t>(std::max<uint64_t>((N + 8191) / 8192, 1), 4ull * c->sm_count);
+
+    DevState* st;
+    float *xs, *partials, *halo_row, *halo_plane;
+    uint16_t* codes;
+    unsigned int* prog;
+    uint32_t *hist, *rowbytes, *nodebuf;
+    uint8_t *len, *ostage;
+    uint64_t *cw, *sortbuf, *rowoff, *blocksums;
+    Arena A;
+    A.add(&st, 1);
+    A.add(&partials, 2 * (size_t)range_blocks);
+    A.add(&codes, N + 8);
+    A.add(&halo_row, hrow);
+    A.add(&halo_plane, hplane);
+    A.add(&prog, g.num_ctas);
+    A.add(&hist, 65536);
+    A.add(&len, 65536);
+    A.add(&cw, 65536);
+    A.add(&sortbuf, kSortBufU64);
+    A.add(&nodebuf, kNodeBufU32);
+    A.add(&rowbytes, rows);
+    A.add(&rowoff, rows);
+    A.add(&blocksums, (rows + 2047) / 2048 + 1);
+    if (!direct_in) A.add(&xs, N);
+    else xs = nullptr;
+    if (!direct_out) A.add(&ostage, bound);
+    else ostage = nullptr;
+    rc = ensure_scratch(c, A.total);
+    if (rc) return rc;
+    A.bind(c->scratch);
+    const float* x = direct_in ? data : xs;
+    uint8_t* dst = direct_out ? out : ostage;
+    cudaStream_t s = c->stream;
+
+    DevState init = {};
+    init.cap = direct_out ? out_cap : bound;
+    if (!direct_in) {
+        PhaseTimer t(c, PH_H2D);
+        if (cudaMemcpyAsync(xs, data, N * 4, data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return SZGB_ECUDA;
+    }
+    if (cudaMemcpyAsync(st, &init, sizeof(DevState), cudaMemcpyHostToDevice, s) != cudaSuccess) return SZGB_ECUDA;
+    cudaMemsetAsync(prog, 0, sizeof(unsigned) * g.num_ctas, s);
+    cudaMemsetAsync(hist, 0, 65536 * 4, s);
+    {
+        PhaseTimer t(c, PH_RANGE);
+        if ((rc = launch_range(x, N, st, cp, partials, range_blocks, s))) return rc;
+    }
+    if (cp.m_user == 0) {
+        PhaseTimer t(c, PH_ADAPT);
+        if ((rc = launch_adapt(x, cp, st, s))) return rc;
+    }
+    {
+        PhaseTimer t(c, PH_WAVE_C);
+        if ((rc = launch_wave_compress(g, layers, x, codes, rec_dev, halo_row, halo_plane, prog, st,
+                                       c->timeout_ns, s)))
+            return rc;
+    }
+    {
+        PhaseTimer t(c, PH_HIST);
+        if ((rc = launch_histogram(codes, N, hist, st, s))) return rc;
+    }
+    {
+        PhaseTimer t(c, PH_CODEBOOK);
+        if ((rc = launch_codebook(hist, st, len, cw, sortbuf, nodebuf, s))) return rc;
+    }
+    {
+        PhaseTimer t(c, PH_ROWBITS);
+        if ((rc = launch_rowbits(codes, x, rows, rowlen, len, rowbytes, st, s))) return rc;
+    }
+    {
+        PhaseTimer t(c, PH_SCAN);
+        if ((rc = launch_scan_rows(rowbytes, rows, rowoff, blocksums, st, 1, s))) return rc;
+    }
+    {
+        PhaseTimer t(c, PH_WRITE);
+        if ((rc = launch_write_meta(cp, rows, len, nodebuf, rowbytes, rowoff, dst, st, s))) return rc;
+        if ((rc = launch_encode(codes, x, rows, rowlen, len, cw, rowoff, dst, st, s))) return rc;
+    }
+    if (codes_dev && cudaMemcpyAsync(codes_dev, codes, N * 2, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return SZGB_ECUDA;
+    if (cudaMemcpyAsync(c->h_state, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return SZGB_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SZGB_ECUDA;
+    const DevState hs = *c->h_state;
+    *out_len = (size_t)hs.total;
+    rc = dev_errors(hs);
+    if (rc == SZGB_OK && hs.total > out_cap) rc = SZGB_ETRUNC;
+    if (rc) return rc;
+    if (!direct_out) {
+        PhaseTimer t(c, PH_D2H);
+        if (cudaMemcpyAsync(out, ostage, hs.total, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return SZGB_ECUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return SZGB_ECUDA;
+    }
+    if (stats) {
+        stats->n_points = N;
+        stats->n_unpred = hs.K;
+        stats->stream_bytes = hs.total;
+        stats->m = hs.m;
+        stats->maxlen = (int)hs.maxlen;
+        stats->nsym = hs.nsym;
+        stats->eb_f = hs.eb_f;
+        stats->xmin = hs.xmin;
+        stats->xmax = hs.xmax;
+    }
+    return SZGB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// stream header (host side)
+
+struct Header {
+    int ndim, layers, m, mode, maxlen, tw;
+    uint64_t d0, d1, d2;
+    double eb_abs, eb_rel, theta;
+    float eb_f, xmin, xmax;
+    uint32_t nsym;
+    uint64_t nchunks, K, payload, total;
+    int adaptive;
+};
+
+uint64_t rd_le(const uint8_t* p, int n) {
+    uint64_t v = 0;
+    for (int i = n - 1; i >= 0; i--) v = (v << 8) | p[i];
+    return v;
+}
+
+int parse_header(const uint8_t* h, size_t in_len, Header* o) {
+    if (in_len < (size_t)kHeaderBytes) return SZGB_ECORRUPT;
+    if (!(h[0] == 'S' && h[1] == 'Z' && h[2] == 'G' && h[3] == 'B')) return SZGB_ECORRUPT;
+    if (rd_le(h + 4, 2) != 1 || rd_le(h + 6, 2) != (uint64_t)kHeaderBytes) return SZGB_ECORRUPT;
+    o->ndim = h[8];
+    o->layers = h[9];
+    o->m = h[10];
+    o->mode = h[11];
+    o->maxlen = h[12];
+    o->tw = h[13];
+    o->d0 = rd_le(h + 16, 8);
+    o->d1 = rd_le(h + 24, 8);
+    o->d2 = rd_le(h + 32, 8);
+    uint64_t u;
+    u = rd_le(h + 40, 8); memcpy(&o->eb_abs, &u, 8);
+    u = rd_le(h + 48, 8); memcpy(&o->eb_rel, &u, 8);
+    uint32_t v;
+    v = (uint32_t)rd_le(h + 56, 4); memcpy(&o->eb_f, &v, 4);
+    v = (uint32_t)rd_le(h + 60, 4); memcpy(&o->xmin, &v, 4);
+    v = (uint32_t)rd_le(h + 64, 4); memcpy(&o->xmax, &v, 4);
+    o->nsym = (uint32_t)rd_le(h + 68, 4);
+    o->nchunks = rd_le(h + 72, 8);
+    o->K = rd_le(h + 80, 8);
+    o->payload = rd_le(h + 88, 8);
+    o->total = rd_le(h + 96, 8);
+    u = rd_le(h + 104, 8); memcpy(&o->theta, &u, 8);
+    o->adaptive = h[112];
+    if (o->ndim < 1 || o->ndim > 3 || o->layers < 1 || o->layers > 4 || o->m < 2 || o->m > 16) return SZGB_ECORRUPT;
+    if (o->tw != 2 && o->tw != 4 || o->mode > 2) return SZGB_ECORRUPT;
+    if (o->d0 == 0 || o->d1 == 0 || o->d2 == 0 || o->d0 > 0xffffffffull || o->d1 > 0xffffffffull ||
+        o->d2 > 0xffffffffull)
+        return SZGB_ECORRUPT;
+    unsigned __int128 n = (unsigned __int128)o->d0 * o->d1 * o->d2;
+    if (n >= ((unsigned __int128)1 << 32)) return SZGB_ECORRUPT;
+    if (o->ndim < 3 && o->d0 != 1) return SZGB_ECORRUPT;
+    if (o->ndim < 2 && o->d1 != 1) return SZGB_ECORRUPT;
+    if (o->nchunks != o->d0 * o->d1) return SZGB_ECORRUPT;
+    if (o->nsym < 1 || o->nsym > (1u << o->m) || o->maxlen < 1 || o->maxlen > 64) return SZGB_ECORRUPT;
+    uint64_t cb = (3ull * o->nsym + 3) & ~3ull;
+    uint64_t tb = ((uint64_t)o->tw * o->nchunks + 3) & ~3ull;
+    if (o->total != (uint64_t)kHeaderBytes + cb + tb + o->payload || o->total > in_len) return SZGB_ECORRUPT;
+    return SZGB_OK;
+}
+
+int decompress_impl(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_device, float* out,
+                    size_t out_cap_elems, int out_on_device) {
+    if (!c || !in || !out) return SZGB_EINVAL;
+    if (cudaSetDevice(c->device) != cudaSuccess) return SZGB_ECUDA;
+    cudaStream_t s = c->stream;
+    uint8_t hbuf[kHeaderBytes];
+    if (in_len < (size_t)kHeaderBytes) return SZGB_ECORRUPT;
+    if (in_on_device) {
+        if (cudaMemcpyAsync(hbuf, in, kHeaderBytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return SZGB_ECUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return SZGB_ECUDA;
+    } else {
+        memcpy(hbuf, in, kHeaderBytes);
+    }
+    Header H;
+    int rc = parse_header(hbuf, in_len, &H);
+    if (rc) return rc;
+    if (H.layers > kMaxLayers) return SZGB_EUNSUPPORTED;
+    const uint64_t N = H.d0 * H.d1 * H.d2;
+    if (out_cap_elems < N) return SZGB_EINVAL;
+    const uint64_t rows = H.nchunks;
+    CallParams cp = {};
+    cp.ndim = H.ndim;
+    cp.d0 = H.d0;
+    cp.d1 = H.d1;
+    cp.d2 = H.d2;
+    cp.layers = H.layers;
+    WaveGeom g = make_geom(c, cp, H.layers);
+    size_t hrow, hplane;
+    halo_sizes(g, H.layers, &hrow, &hplane);
+    const bool direct_in = in_on_device && ((uintptr_t)in % 4 == 0);
+    const bool direct_out = out_on_device && ((uintptr_t)out % 16 == 0);
+    DevState* st;
+    float *halo_row, *halo_plane, *ostage;
+    unsigned int* prog;
+    uint32_t *rowbytes, *lut, *dectab, *symbuf;
+    uint64_t *rowoff, *blocksums;
+    uint8_t *lenbuf, *istage;
+    Arena A;
+    A.add(&st, 1);
+    A.add(&halo_row, hrow);
+    A.add(&halo_plane, hplane);
+    A.add(&prog, g.num_ctas);
+    A.add(&rowbytes, rows);
+    A.add(&rowoff, rows);
+    A.add(&blocksums, (rows + 2047) / 2048 + 1);
+    A.add(&lut, (size_t)1 << kLutBits);
+    A.add(&dectab, kDecTabU32);
+    A.add(&lenbuf, 65536);
+    A.add(&symbuf, 65536);
+    if (!direct_in) A.add(&istage, H.total + 16);
+    else istage = nullptr;
+    if (!direct_out) A.add(&ostage, N);
+    else ostage = nullptr;
+    rc = ensure_scratch(c, A.total);
+    if (rc) return rc;
+    A.bind(c->scratch);
+    const uint8_t* sb = direct_in ? in : istage;
+    float* dst = direct_out ? out : ostage;
+    if (!direct_in) {
+        PhaseTimer t(c, PH_H2D);
+        if (cudaMemcpyAsync(istage, in, H.total, in_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return SZGB_ECUDA;
+    }
+    DevState init = {};
+    init.eb_f = H.eb_f;
+    init.twoeb = 2.0f * H.eb_f;
+    init.m = H.m;
+    init.center = 1 << (H.m - 1);
+    init.radius = (float)((1 << (H.m - 1)) - 1);
+    uint32_t ub;
+    memcpy(&ub, &H.eb_f, 4);
+    init.e_eb = (int)((ub >> 23) & 0xffu);
+    if (cudaMemcpyAsync(st, &init, sizeof(DevState), cudaMemcpyHostToDevice, s) != cudaSuccess) return SZGB_ECUDA;
+    cudaMemsetAsync(prog, 0, sizeof(unsigned) * g.num_ctas, s);
+    const uint64_t cb = (3ull * H.nsym + 3) & ~3ull;
+    const uint64_t tb = ((uint64_t)H.tw * rows + 3) & ~3ull;
+    const uint8_t* codebook = sb + kHeaderBytes;
+    const uint8_t* table = codebook + cb;
+    const uint8_t* payload = table + tb;
+    {
+        PhaseTimer t(c, PH_DEC_TABLES);
+        if ((rc = launch_decode_tables(codebook, H.nsym, H.m, lut, dectab, lenbuf, symbuf, st, s))) return rc;
+    }
+    {
+        PhaseTimer t(c, PH_DEC_SCAN);
+        if ((rc = launch_read_rowbytes(table, H.tw, rows, rowbytes, s))) return rc;
+        if ((rc = launch_scan_rows(rowbytes, rows, rowoff, blocksums, st, 0, s))) return rc;
+    }
+    {
+        PhaseTimer t(c, PH_WAVE_D);
+        if ((rc = launch_wave_decompress(g, H.layers, payload, rowoff, rowbytes, payload + H.payload, lut, dectab,
+                                         dst, halo_row, halo_plane, prog, st, c->timeout_ns, s)))
+            return rc;
+    }
+    if (cudaMemcpyAsync(c->h_state, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return SZGB_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SZGB_ECUDA;
+    const DevState hs = *c->h_state;
+    rc = dev_errors(hs);
+    if (rc == SZGB_OK && hs.payload != H.payload) rc = SZGB_ECORRUPT;
+    if (rc) return rc;
+    if (!direct_out) {
+        PhaseTimer t(c, PH_D2H);
+        if (cudaMemcpyAsync(out, ostage, N * 4, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return SZGB_ECUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return SZGB_ECUDA;
+    }
+    return SZGB_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+
+extern "C" {
+
+int szgb_create(szgb_ctx** out, int device, size_t device_mem_budget) {
+    if (!out) return SZGB_EINVAL;
+    *out = nullptr;
+    if (cudaSetDevice(device) != cudaSuccess) return SZGB_ECUDA;
+    szgb_ctx* c = new (std::nothrow) szgb_ctx();
+    if (!c) return SZGB_ENOMEM;
+    c->device = device;
+    c->budget = device_mem_budget;
+    if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return SZGB_ECUDA;
+    }
+    c->stream = c->own_stream;
+    if (cudaMallocHost(&c->h_state, sizeof(DevState)) != cudaSuccess) {
+        cudaStreamDestroy(c->own_stream);
+        delete c;
+        return SZGB_ENOMEM;
+    }
+    for (int i = 0; i < PH_N; i++) {
+        cudaEventCreate(&c->ev0[i]);
+        cudaEventCreate(&c->ev1[i]);
+    }
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    const char* e;
+    if ((e = getenv("SZGB_W2"))) c->W2 = std::max(1, atoi(e));
+    if ((e = getenv("SZGB_W3"))) c->W3 = std::max(1, std::min(16, atoi(e)));
+    *out = c;
+    return SZGB_OK;
+}
+
+void szgb_destroy(szgb_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->scratch) cudaFree(c->scratch);
+    if (c->h_state) cudaFreeHost(c->h_state);
+    for (int i = 0; i < PH_N; i++) {
+        if (c->ev0[i]) cudaEventDestroy(c->ev0[i]);
+        if (c->ev1[i]) cudaEventDestroy(c->ev1[i]);
+    }
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    delete c;
+}
+
+int szgb_set_stream(szgb_ctx* c, void* stream) {
+    if (!c) return SZGB_EINVAL;
+    c->stream = stream ? static_cast<cudaStream_t>(stream) : c->own_stream;
+    return SZGB_OK;
+}
+
+size_t szgb_compress_bound(const szgb_params* p) {
+    CallParams cp;
+    if (!p) return 0;
+    int rc = check_params(p, &cp);
+    if (rc != SZGB_OK && rc != SZGB_EUNSUPPORTED) return 0;
+    uint64_t N = cp.d0 * cp.d1 * cp.d2, rows = cp.d0 * cp.d1;
+    // header + codebook + table + rows * (N/row points * (64 + 32) bits)
+    return (size_t)(kHeaderBytes + 3 * 65536 + 4 + 4 * rows + 4 + rows + N * 12 + 16);
+}
+
+int szgb_compress(szgb_ctx* c, const float* data, int data_on_device, const szgb_params* p, uint8_t* out,
+                  size_t out_cap, int out_on_device, size_t* out_len, szgb_stats* opt_stats) {
+    if (!out) return SZGB_EINVAL;
+    return compress_impl(c, data, data_on_device, p, out, out_cap, out_on_device, out_len, opt_stats, nullptr,
+                         nullptr);
+}
+
+int szgb_compress_trace(szgb_ctx* c, const float* data_dev, const szgb_params* p, uint8_t* out_dev,
+                        size_t out_cap, size_t* out_len, szgb_stats* opt_stats, float* recorded_dev,
+                        uint16_t* codes_dev) {
+    if (!out_dev) return SZGB_EINVAL;
+    return compress_impl(c, data_dev, 1, p, out_dev, out_cap, 1, out_len, opt_stats, recorded_dev, codes_dev);
+}
+
+int szgb_decompress(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_device, float* out,
+                    size_t out_cap_elems, int out_on_device) {
+    return decompress_impl(c, in, in_len, in_on_device, out, out_cap_elems, out_on_device);
+}
+
+int szgb_stream_info(const uint8_t* in_host, size_t in_len, szgb_params* out, uint64_t* n_unpred) {
+    if (!in_host || !out) return SZGB_EINVAL;
+    Header H;
+    int rc = parse_header(in_host, in_len, &H);
+    if (rc) return rc;
+    memset(out, 0, sizeof(*out));
+    out->ndim = H.ndim;
+    uint64_t d[3] = {H.d0, H.d1, H.d2};
+    for (int a = 0; a < H.ndim; a++) out->shape[a] = d[3 - H.ndim + a];
+    out->mode = H.mode;
+    out->eb_abs = H.eb_abs;
+    out->eb_rel = H.eb_rel;
+    out->layers = H.layers;
+    out->m = H.m;
+    out->theta = H.theta;
+    if (n_unpred) *n_unpred = H.K;
+    return SZGB_OK;
+}
+
+int szgb_set_profiling(szgb_ctx* c, int on) {
+    if (!c) return SZGB_EINVAL;
+    c->profiling = on != 0;
+    return SZGB_OK;
+}
+int szgb_num_phases(void) { return PH_N; }
+const char* szgb_phase_name(int i) { return (i >= 0 && i < PH_N) ? kPhaseNames[i] : ""; }
+int szgb_phase_times(szgb_ctx* c, double* ms, uint64_t* calls, int n, int reset) {
+    if (!c) return SZGB_EINVAL;
+    for (int i = 0; i < n && i < PH_N; i++) {
+        if (ms) ms[i] = c->ph_ms[i];
+        if (calls) calls[i] = c->ph_calls[i];
+    }
+    if (reset) {
+        for (int i = 0; i < PH_N; i++) { c->ph_ms[i] = 0; c->ph_calls[i] = 0; }
+    }
+    return SZGB_OK;
+}
+
+const char* szgb_strerror(int code) {
+    switch (code) {
+        case SZGB_OK: return "ok";
+        case SZGB_EINVAL: return "invalid argument";
+        case SZGB_ENONFINITE: return "input holds NaN or Inf";
+        case SZGB_ETRUNC: return "output buffer too small";
+        case SZGB_ECORRUPT: return "corrupt stream";
+        case SZGB_ENOMEM: return "device allocation failed";
+        case SZGB_EBUDGET: return "device memory budget exceeded";
+        case SZGB_ETIMEOUT: return "device-side wait timed out";
+        case SZGB_ECUDA: return "CUDA runtime error";
+        case SZGB_EUNSUPPORTED: return "not supported on the GPU path";
+        default: return "unknown error";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,225 @@
+// szgb_internal.cuh -- shared definitions of the GB300 compressor library.
+//
+// Device-side state of one compress/decompress call, the per-point
+// arithmetic of the method (prediction terms, error-controlled quantization,
+// truncated representation of unpredictable values) and small PTX helpers.
+// All float arithmetic on the data path uses explicit round-to-nearest
+// intrinsics (__fadd_rn, __fmul_rn, ...) so that no FMA contraction can
+// change a bit.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/szgb.h"
+
+namespace szgb {
+
+constexpr int kHeaderBytes = 128;
+constexpr int kTile = 4;           // columns per sweep and lane (one float4)
+constexpr int kMaxLayers = 2;      // n supported by the GPU kernels
+constexpr int kLutBits = 11;       // decoder lookup-table index bits
+constexpr uint32_t kProgAbort = 0x7fffffffu;
+
+// Error flags raised on the device (DevState::err bitmask).
+constexpr uint32_t kErrTimeout = 1u;
+constexpr uint32_t kErrCorrupt = 2u;
+constexpr uint32_t kErrNonFinite = 4u;
+constexpr uint32_t kErrOverflow = 8u;   // stream does not fit in the output
+
+// State of one call, in device memory (zeroed before the call).
+struct DevState {
+    // range (K1)
+    unsigned int nonfinite;
+    unsigned int range_blocks_done;
+    float xmin, xmax;
+    // bound and quantizer parameters
+    float eb_f, twoeb, inv2eb, radius;
+    int m, center, e_eb, adaptive;
+    // adaptive m (K8)
+    unsigned long long need[18];
+    unsigned long long nsamples;
+    unsigned int adapt_blocks_done;
+    // wavefront scheduling
+    unsigned int ticket;
+    unsigned int err;
+    // Huffman
+    unsigned int nsym, maxlen;
+    unsigned long long K;
+    unsigned int maxrow;
+    unsigned int table_width;
+    unsigned long long cb_bytes, tab_bytes, payload, total, cap;
+    unsigned int fits;
+    unsigned int scan_blocks;
+    // decoder
+    unsigned int lut_bits;
+};
+
+// Parameters of a call that the host knows before launching.
+struct CallParams {
+    int ndim;
+    uint64_t d0, d1, d2;     // extents, slowest -> fastest (leading 1s)
+    int mode;
+    double eb_abs, eb_rel;
+    int layers;
+    int m_user;              // 0 = adaptive
+    double theta;
+};
+
+// --------------------------------------------------------------------------
+// prediction terms: k in [0,n]^3 \ {0} in descending lexicographic order with
+// coefficient -prod_j (-1)^k_j C(n,k_j)  (Eq. predmodel; summation order R2)
+
+__host__ __device__ constexpr int binom_c(int n, int k) {
+    return (k < 0 || k > n) ? 0 : (k == 0 ? 1 : binom_c(n, k - 1) * (n - k + 1) / k);
+}
+__host__ __device__ constexpr int sgn_binom(int n, int k) { return ((k & 1) ? -1 : 1) * binom_c(n, k); }
+__host__ __device__ constexpr int term_coef(int n, int k0, int k1, int k2) {
+    return -sgn_binom(n, k0) * sgn_binom(n, k1) * sgn_binom(n, k2);
+}
+
+// --------------------------------------------------------------------------
+// quantizer parameters in registers
+struct QParams {
+    float eb, twoeb, inv, radius;
+    int center, e_eb;
+};
+
+__device__ __forceinline__ QParams load_qparams(const DevState* st) {
+    QParams q;
+    q.eb = st->eb_f;
+    q.twoeb = st->twoeb;
+    q.inv = st->inv2eb;
+    q.radius = st->radius;
+    q.center = st->center;
+    q.e_eb = st->e_eb;
+    return q;
+}
+
+// number of mantissa bits kept for an unpredictable value (R5)
+__host__ __device__ __forceinline__ int trunc_bits(uint32_t u, int e_eb) {
+    if (e_eb == 0) return 23;
+    int e = (int)((u >> 23) & 0xffu);
+    e = e < 1 ? 1 : e;
+    int t = e - e_eb;
+    t = t < 0 ? 0 : t;
+    return t > 23 ? 23 : t;
+}
+
+__device__ __forceinline__ float trunc_value(float x, int e_eb) {
+    uint32_t u = __float_as_uint(x);
+    int t = trunc_bits(u, e_eb);
+    return __uint_as_float(u & ~((1u << (23 - t)) - 1u));
+}
+
+// Error-controlled quantization of one value (Sec. IV-A).  Returns the code
+// (0 = unpredictable) and sets V to the value recorded for later predictions.
+// q + 0.0f equals (float)(int)q for the integral |q| <= radius and maps -0.0
+// to +0.0, matching a reconstruction from the integer code.
+__device__ __forceinline__ int quantize(float x, float pred, const QParams& qp, float& V) {
+    float diff = __fsub_rn(x, pred);
+    float q = rintf(__fmul_rn(diff, qp.inv));
+    bool ok = fabsf(q) <= qp.radius;
+    float qn = __fadd_rn(q, 0.0f);
+    float dq = __fadd_rn(pred, __fmul_rn(qn, qp.twoeb));
+    float err = __fsub_rn(x, dq);
+    ok = ok && ((fabsf(err) < qp.eb) || (x == dq));
+    V = ok ? dq : trunc_value(x, qp.e_eb);
+    return ok ? ((int)qn + qp.center) : 0;
+}
+
+// Reconstruction of a predictable value from its code.
+__device__ __forceinline__ float dequantize(int code, float pred, const QParams& qp) {
+    float qf = (float)(code - qp.center);
+    return __fadd_rn(pred, __fmul_rn(qf, qp.twoeb));
+}
+
+// --------------------------------------------------------------------------
+// PTX helpers
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+// 16-byte asynchronous global->shared copy, zero-filling when src_bytes < 16
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(dst)), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ uint32_t bswap32(uint32_t v) { return __byte_perm(v, 0, 0x0123); }
+
+// --------------------------------------------------------------------------
+// geometry of the wavefront launch (host-computed, passed by value)
+struct WaveGeom {
+    int ndim;             // 1,2 treated as 2D (rows); 3 as 3D
+    uint64_t P, M, N;     // extents (planes, rows, columns)
+    int ntiles;           // ceil(N / kTile)
+    int W;                // compute warps per CTA
+    int nb0, nb1;         // CTA grid: 3D (plane blocks, row blocks); 2D (1, row blocks)
+    int nsweeps;          // sweeps per CTA including the final flush sweep
+    int aligned;          // rows start on 16-byte boundaries (N % 4 == 0)
+    int num_ctas;
+};
+
+// host launchers (each in its own translation unit)
+int launch_range(const float* x, uint64_t n, DevState* st, const CallParams& cp, float* partials,
+                 int nblocks, cudaStream_t s);
+int launch_adapt(const float* x, const CallParams& cp, DevState* st, cudaStream_t s);
+int launch_wave_compress(const WaveGeom& g, int layers, const float* x, uint16_t* codes,
+                         float* recorded, float* halo_row, float* halo_plane, unsigned int* prog,
+                         DevState* st, uint64_t timeout_ns, cudaStream_t s);
+int launch_wave_decompress(const WaveGeom& g, int layers, const uint8_t* payload,
+                           const uint64_t* rowoff, const uint32_t* rowbytes,
+                           const uint8_t* stream_end, const uint32_t* lut,
+                           const uint32_t* dec_tab, float* out, float* halo_row,
+                           float* halo_plane, unsigned int* prog, DevState* st,
+                           uint64_t timeout_ns, cudaStream_t s);
+size_t wave_smem_bytes(const WaveGeom& g, int layers, bool decompress);
+
+// Huffman / stream kernels (k_huff.cu)
+int launch_histogram(const uint16_t* codes, uint64_t n, uint32_t* hist, DevState* st, cudaStream_t s);
+int launch_codebook(const uint32_t* hist, DevState* st, uint8_t* len, uint64_t* cw, uint64_t* sortbuf,
+                    uint32_t* nodebuf, cudaStream_t s);
+int launch_rowbits(const uint16_t* codes, const float* x, uint64_t rows, uint64_t rowlen,
+                   const uint8_t* len, uint32_t* rowbytes, DevState* st, cudaStream_t s);
+int launch_scan_rows(const uint32_t* rowbytes, uint64_t rows, uint64_t* rowoff, uint64_t* blocksums,
+                     DevState* st, int finalize_compress, cudaStream_t s);
+int launch_write_meta(const CallParams& cp, uint64_t rows, const uint8_t* len, const uint32_t* usedlist,
+                      const uint32_t* rowbytes, const uint64_t* rowoff, uint8_t* out, DevState* st,
+                      cudaStream_t s);
+int launch_encode(const uint16_t* codes, const float* x, uint64_t rows, uint64_t rowlen, const uint8_t* len,
+                  const uint64_t* cw, const uint64_t* rowoff, uint8_t* out, DevState* st, cudaStream_t s);
+int launch_decode_tables(const uint8_t* codebook, uint32_t nsym, int m, uint32_t* lut, uint32_t* dec_tab,
+                         uint8_t* lenbuf, uint32_t* symbuf, DevState* st, cudaStream_t s);
+int launch_read_rowbytes(const uint8_t* table, int width, uint64_t rows, uint32_t* rowbytes,
+                         cudaStream_t s);
+
+// scratch sizes of the codebook build (elements)
+constexpr size_t kSortBufU64 = 3 * 65536;
+constexpr size_t kNodeBufU32 = 5 * 65536;
+constexpr size_t kDecTabU32 = 260 + 32768;
+
+}  // namespace szgb

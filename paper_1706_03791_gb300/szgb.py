@@ -1,0 +1,257 @@
+"""Python binding of the C ABI in include/szgb.h (argument marshalling only).
+
+Every step of compression and decompression runs in the CUDA library
+``libszgb.so`` built in-tree for sm_103a; this module only passes pointers
+and sizes.  PyTorch tensors provide device memory and streams; NumPy arrays
+are passed as host buffers.  If the library is missing or cannot be loaded
+the import fails: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libszgb.so")
+
+OK, EINVAL, ENONFINITE, ETRUNC, ECORRUPT, ENOMEM, EBUDGET, ETIMEOUT, ECUDA, EUNSUPPORTED = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8, -9
+ABS, REL, ABS_AND_REL = 0, 1, 2
+
+
+class SzgbError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (what, strerror(code), code))
+
+
+class Params(C.Structure):
+    _fields_ = [("ndim", C.c_int), ("shape", C.c_uint64 * 3), ("mode", C.c_int),
+                ("eb_abs", C.c_double), ("eb_rel", C.c_double), ("layers", C.c_int),
+                ("m", C.c_int), ("theta", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_points", C.c_uint64), ("n_unpred", C.c_uint64), ("stream_bytes", C.c_uint64),
+                ("m", C.c_int), ("maxlen", C.c_int), ("nsym", C.c_uint32), ("eb_f", C.c_float),
+                ("xmin", C.c_float), ("xmax", C.c_float)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libszgb.so (raises if it is not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libszgb.so is not built (run __graft_entry__.build())")
+        L = C.CDLL(LIB_PATH)
+        vp, sz = C.c_void_p, C.c_size_t
+        L.szgb_create.argtypes = [C.POINTER(vp), C.c_int, sz]
+        L.szgb_destroy.argtypes = [vp]
+        L.szgb_destroy.restype = None
+        L.szgb_set_stream.argtypes = [vp, vp]
+        L.szgb_compress_bound.argtypes = [C.POINTER(Params)]
+        L.szgb_compress_bound.restype = sz
+        L.szgb_compress.argtypes = [vp, vp, C.c_int, C.POINTER(Params), vp, sz, C.c_int,
+                                    C.POINTER(sz), C.POINTER(Stats)]
+        L.szgb_compress_trace.argtypes = [vp, vp, C.POINTER(Params), vp, sz, C.POINTER(sz),
+                                          C.POINTER(Stats), vp, vp]
+        L.szgb_decompress.argtypes = [vp, vp, sz, C.c_int, vp, sz, C.c_int]
+        L.szgb_stream_info.argtypes = [vp, sz, C.POINTER(Params), C.POINTER(C.c_uint64)]
+        L.szgb_set_profiling.argtypes = [vp, C.c_int]
+        L.szgb_num_phases.argtypes = []
+        L.szgb_phase_name.argtypes = [C.c_int]
+        L.szgb_phase_name.restype = C.c_char_p
+        L.szgb_phase_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.c_int,
+                                       C.c_int]
+        L.szgb_strerror.argtypes = [C.c_int]
+        L.szgb_strerror.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().szgb_strerror(code).decode()
+
+
+# names of every entry point declared in include/szgb.h
+EXPORTS = ["szgb_create", "szgb_destroy", "szgb_set_stream", "szgb_compress_bound", "szgb_compress",
+           "szgb_compress_trace", "szgb_decompress", "szgb_stream_info", "szgb_set_profiling",
+           "szgb_num_phases", "szgb_phase_name", "szgb_phase_times", "szgb_strerror"]
+
+
+def make_params(shape, mode=REL, eb_abs=0.0, eb_rel=1e-4, layers=1, m=0, theta=0.99) -> Params:
+    p = Params()
+    shape = tuple(int(s) for s in shape)
+    p.ndim = len(shape)
+    for i in range(3):
+        p.shape[i] = shape[i] if i < len(shape) else 0
+    p.mode, p.eb_abs, p.eb_rel, p.layers, p.m, p.theta = mode, float(eb_abs), float(eb_rel), \
+        int(layers), int(m), float(theta)
+    return p
+
+
+def compress_bound(shape, **kw) -> int:
+    p = make_params(shape, **kw)
+    return int(lib().szgb_compress_bound(C.byref(p)))
+
+
+def stream_info(stream) -> dict:
+    s = np.ascontiguousarray(np.asarray(stream, dtype=np.uint8))
+    p = Params()
+    k = C.c_uint64()
+    rc = lib().szgb_stream_info(s.ctypes.data, s.size, C.byref(p), C.byref(k))
+    if rc:
+        raise SzgbError(rc, "szgb_stream_info")
+    return {"ndim": p.ndim, "shape": tuple(p.shape[i] for i in range(p.ndim)), "mode": p.mode,
+            "eb_abs": p.eb_abs, "eb_rel": p.eb_rel, "layers": p.layers, "m": p.m,
+            "theta": p.theta, "n_unpred": k.value}
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+class Context:
+    """A library context (device scratch and a stream) on one CUDA device."""
+
+    def __init__(self, device: int = 0, budget: int = 0):
+        self._h = C.c_void_p()
+        rc = lib().szgb_create(C.byref(self._h), int(device), int(budget))
+        if rc:
+            raise SzgbError(rc, "szgb_create")
+        self.device = device
+
+    def close(self):
+        if self._h:
+            lib().szgb_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_ptr: int | None):
+        lib().szgb_set_stream(self._h, C.c_void_p(stream_ptr or 0))
+
+    def set_profiling(self, on: bool):
+        lib().szgb_set_profiling(self._h, 1 if on else 0)
+
+    def phase_times(self, reset: bool = False) -> dict:
+        L = lib()
+        n = L.szgb_num_phases()
+        ms = (C.c_double * n)()
+        calls = (C.c_uint64 * n)()
+        L.szgb_phase_times(self._h, ms, calls, n, 1 if reset else 0)
+        return {L.szgb_phase_name(i).decode(): (ms[i], calls[i]) for i in range(n)}
+
+    # -- compression ---------------------------------------------------------
+    def compress(self, x, out=None, **kw):
+        """Compress `x` (a CUDA float32 tensor, or a NumPy float32 array on the
+        host).  Returns (stream, stats): with a CUDA input, `stream` is a view
+        of the uint8 CUDA tensor `out` (allocated when None); with a NumPy
+        input, a NumPy uint8 array."""
+        p = make_params(tuple(x.shape), **kw)
+        L = lib()
+        bound = int(L.szgb_compress_bound(C.byref(p)))
+        st = Stats()
+        olen = C.c_size_t()
+        if _is_torch(x):
+            import torch
+            assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()
+            if out is None:
+                out = torch.empty(bound, dtype=torch.uint8, device=x.device)
+            rc = L.szgb_compress(self._h, C.c_void_p(x.data_ptr()), 1, C.byref(p),
+                                 C.c_void_p(out.data_ptr()), out.numel(), 1, C.byref(olen), C.byref(st))
+            if rc:
+                raise SzgbError(rc, "szgb_compress")
+            return out[:olen.value], st
+        xa = np.ascontiguousarray(x, dtype=np.float32)
+        if out is None:
+            out = np.empty(bound, np.uint8)
+        rc = L.szgb_compress(self._h, C.c_void_p(xa.ctypes.data), 0, C.byref(p),
+                             C.c_void_p(out.ctypes.data), out.size, 0, C.byref(olen), C.byref(st))
+        if rc:
+            raise SzgbError(rc, "szgb_compress")
+        return out[:olen.value], st
+
+    def compress_host_ptr(self, x_ptr: int, shape, out_ptr: int, out_cap: int, **kw):
+        """Compress from a host pointer into a host buffer (pinned or pageable)."""
+        p = make_params(shape, **kw)
+        st = Stats()
+        olen = C.c_size_t()
+        rc = lib().szgb_compress(self._h, C.c_void_p(x_ptr), 0, C.byref(p), C.c_void_p(out_ptr),
+                                 int(out_cap), 0, C.byref(olen), C.byref(st))
+        if rc:
+            raise SzgbError(rc, "szgb_compress")
+        return olen.value, st
+
+    def compress_trace(self, x, **kw):
+        """Device-only compression that also returns the recorded (exact
+        decompressed) values and the quantization codes, for testing."""
+        import torch
+        p = make_params(tuple(x.shape), **kw)
+        L = lib()
+        bound = int(L.szgb_compress_bound(C.byref(p)))
+        out = torch.empty(bound, dtype=torch.uint8, device=x.device)
+        rec = torch.empty_like(x)
+        codes = torch.empty(x.shape, dtype=torch.int16, device=x.device)
+        st = Stats()
+        olen = C.c_size_t()
+        rc = L.szgb_compress_trace(self._h, C.c_void_p(x.data_ptr()), C.byref(p),
+                                   C.c_void_p(out.data_ptr()), out.numel(), C.byref(olen),
+                                   C.byref(st), C.c_void_p(rec.data_ptr()),
+                                   C.c_void_p(codes.data_ptr()))
+        if rc:
+            raise SzgbError(rc, "szgb_compress_trace")
+        return out[:olen.value], rec, codes, st
+
+    # -- decompression -------------------------------------------------------
+    def decompress(self, stream, out=None, shape=None):
+        """Decompress a stream (uint8 CUDA tensor or NumPy array).  Returns a
+        float32 CUDA tensor (CUDA stream input) or NumPy array."""
+        L = lib()
+        if _is_torch(stream):
+            import torch
+            hdr = stream[:128].cpu().numpy()
+            info = stream_info_header(hdr)
+            n = int(np.prod(info["shape"]))
+            if out is None:
+                out = torch.empty(info["shape"], dtype=torch.float32, device=stream.device)
+            rc = L.szgb_decompress(self._h, C.c_void_p(stream.data_ptr()), stream.numel(), 1,
+                                   C.c_void_p(out.data_ptr()), out.numel(), 1)
+            if rc:
+                raise SzgbError(rc, "szgb_decompress")
+            return out
+        s = np.ascontiguousarray(np.asarray(stream, dtype=np.uint8))
+        info = stream_info_header(s[:128])
+        if out is None:
+            out = np.empty(info["shape"], np.float32)
+        rc = L.szgb_decompress(self._h, C.c_void_p(s.ctypes.data), s.size, 0,
+                               C.c_void_p(out.ctypes.data), out.size, 0)
+        if rc:
+            raise SzgbError(rc, "szgb_decompress")
+        return out
+
+    def decompress_ptr(self, in_ptr: int, in_len: int, in_on_device: bool, out_ptr: int,
+                       out_elems: int, out_on_device: bool) -> int:
+        return lib().szgb_decompress(self._h, C.c_void_p(in_ptr), int(in_len), int(in_on_device),
+                                     C.c_void_p(out_ptr), int(out_elems), int(out_on_device))
+
+
+def stream_info_header(hdr) -> dict:
+    """Shape and parameters from the 128-byte header alone (no length check)."""
+    import struct
+    b = bytes(np.asarray(hdr[:128], dtype=np.uint8))
+    ndim = b[8]
+    d = struct.unpack_from("<3Q", b, 16)
+    return {"ndim": ndim, "shape": tuple(int(v) for v in d[3 - ndim:]), "m": b[10], "layers": b[9]}
