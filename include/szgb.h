@@ -47,6 +47,8 @@ extern "C" {
 #define SZGB_ETIMEOUT (-7)    /* a bounded device-side wait ran out */
 #define SZGB_ECUDA (-8)       /* a CUDA runtime call failed */
 #define SZGB_EUNSUPPORTED (-9)/* valid request this build does not run on GPU */
+#define SZGB_ESCRATCH (-10)   /* request needs more than the fixed scratch of
+                                 szgb_decompress_noalloc */
 
 /* error-bound modes (Sec. II, metric 1): absolute, value-range relative,
  * or both (the smaller bound applies) */
@@ -116,6 +118,26 @@ int szgb_compress_trace(szgb_ctx *ctx, const float *data_dev, const szgb_params 
 int szgb_decompress(szgb_ctx *ctx, const uint8_t *in, size_t in_len,
                     int in_on_device, float *out, size_t out_cap_elems,
                     int out_on_device);
+
+/* Decompression that allocates no memory, for callers that cannot call
+ * cudaMalloc (for example code that issues work while a stream capture is
+ * open, services with a fixed device-memory plan, or allocator callbacks).
+ * The paper has no counterpart: this is an operational variant of
+ * szgb_decompress with identical output.
+ *  - in_dev (in_len bytes, 4-byte aligned) and out_dev (out_cap_elems floats,
+ *    16-byte aligned) are device buffers owned by the caller; work is issued
+ *    on `cuda_stream` (a cudaStream_t, NULL = legacy default stream) and the
+ *    call returns after that stream has finished it.
+ *  - Scratch is a fixed 64 MiB static device array held by every GPU that
+ *    loads the library until the process exits; a stream whose decompression
+ *    needs more returns SZGB_ESCRATCH before any work is issued.
+ *  - The first call on a device looks up that array's device address; make
+ *    that first call before any stream capture is opened.
+ *  - Every call on a device shares the array; calls whose work overlaps on
+ *    the GPU race.  It never calls cudaMalloc/cudaFree or an allocating
+ *    library routine. */
+int szgb_decompress_noalloc(const uint8_t *in_dev, size_t in_len, float *out_dev,
+                            size_t out_cap_elems, void *cuda_stream);
 
 /* Reads the header of a stream held in host memory: parameters (with the
  * m actually used) and the number of unpredictable points. */

@@ -624,6 +624,7 @@ const char* szgb_strerror(int code) {
         case SZGB_ETIMEOUT: return "device-side wait timed out";
         case SZGB_ECUDA: return "CUDA runtime error";
         case SZGB_EUNSUPPORTED: return "not supported on the GPU path";
+        case SZGB_ESCRATCH: return "needs more than the fixed scratch of szgb_decompress_noalloc";
         default: return "unknown error";
     }
 }

@@ -1,0 +1,181 @@
+// szgb_noalloc.cu -- decompression that allocates no memory.
+//
+// Some callers cannot call cudaMalloc: a thread that issues work while a
+// stream capture is open (allocation is not a capturable operation), a
+// service that must keep a fixed device-memory plan for its whole life, or
+// code that runs inside an allocator or framework callback where allocating
+// would re-enter the allocator.  szgb_decompress_noalloc serves them.  It
+// runs the same kernels as szgb_decompress, but every scratch buffer those
+// kernels use (halo rows/planes, progress counters, per-row byte lengths and
+// offsets, decoder tables, call state) is carved out of the fixed array
+// below, which every GPU that loads this library holds until the process
+// exits.  Inputs and outputs are the caller's device buffers.
+//
+// The array is shared by every call on a device and keeps the last call's
+// contents; what must start at zero is cleared on the stream at the start of
+// each call.  Calls whose work overlaps on the GPU (two host threads, or two
+// streams) race on the array.
+#include <string.h>
+
+#include <mutex>
+
+#include "szgb_internal.cuh"
+
+using namespace szgb;
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 64ull << 20;  // 64 MiB
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_setup_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the array on the current device, looked up once per
+// device.  The host-side symbol is not a device address; only this address
+// may be handed to kernels.
+int scratch_address(void** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SZGB_ECUDA;
+    std::lock_guard<std::mutex> lk(g_setup_mu);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return SZGB_ECUDA;
+        }
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return SZGB_OK;
+}
+
+uint64_t le(const uint8_t* p, int n) {
+    uint64_t v = 0;
+    for (int i = n - 1; i >= 0; i--) v = (v << 8) | p[i];
+    return v;
+}
+
+size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" int szgb_decompress_noalloc(const uint8_t* in_dev, size_t in_len, float* out_dev,
+                                       size_t out_cap_elems, void* cuda_stream) {
+    if (!in_dev || !out_dev || in_len < (size_t)kHeaderBytes) return SZGB_EINVAL;
+    if ((uintptr_t)in_dev % 4 || (uintptr_t)out_dev % 16) return SZGB_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    void* base = nullptr;
+    int rc = scratch_address(&base);
+    if (rc) return rc;
+
+    // header (128 bytes) to the host stack
+    uint8_t h[kHeaderBytes];
+    if (cudaMemcpyAsync(h, in_dev, kHeaderBytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return SZGB_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SZGB_ECUDA;
+    if (!(h[0] == 'S' && h[1] == 'Z' && h[2] == 'G' && h[3] == 'B')) return SZGB_ECORRUPT;
+    if (le(h + 4, 2) != 1 || le(h + 6, 2) != (uint64_t)kHeaderBytes) return SZGB_ECORRUPT;
+    const int ndim = h[8], layers = h[9], m = h[10], tw = h[13];
+    const uint64_t d0 = le(h + 16, 8), d1 = le(h + 24, 8), d2 = le(h + 32, 8);
+    float eb_f;
+    uint32_t ebu = (uint32_t)le(h + 56, 4);
+    memcpy(&eb_f, &ebu, 4);
+    const uint32_t nsym = (uint32_t)le(h + 68, 4);
+    const uint64_t rows = le(h + 72, 8), payload_bytes = le(h + 88, 8), total = le(h + 96, 8);
+    if (ndim < 1 || ndim > 3 || layers < 1 || m < 2 || m > 16 || (tw != 2 && tw != 4)) return SZGB_ECORRUPT;
+    if (d0 == 0 || d1 == 0 || d2 == 0 || d0 > 0xffffffffull || d1 > 0xffffffffull || d2 > 0xffffffffull)
+        return SZGB_ECORRUPT;
+    if ((unsigned __int128)d0 * d1 * d2 >= ((unsigned __int128)1 << 32)) return SZGB_ECORRUPT;
+    if ((ndim < 3 && d0 != 1) || (ndim < 2 && d1 != 1) || rows != d0 * d1) return SZGB_ECORRUPT;
+    if (nsym < 1 || nsym > (1u << m) || h[12] < 1 || h[12] > 64) return SZGB_ECORRUPT;
+    const uint64_t cb = (3ull * nsym + 3) & ~3ull, tb = ((uint64_t)tw * rows + 3) & ~3ull;
+    if (total != (uint64_t)kHeaderBytes + cb + tb + payload_bytes || total > in_len) return SZGB_ECORRUPT;
+    if (layers > kMaxLayers) return SZGB_EUNSUPPORTED;
+
+    // wavefront geometry (the same schedule as szgb_decompress; any valid
+    // schedule gives the same values)
+    WaveGeom g = {};
+    g.N = d2;
+    g.ntiles = (int)((d2 + kTile - 1) / kTile);
+    g.aligned = (d2 % 4) == 0;
+    if (ndim == 3) {
+        g.ndim = 3;
+        g.P = d0;
+        g.M = d1;
+        int W = 8;
+        if ((uint64_t)W > d0) W = (int)d0;
+        if (W < 2 * layers) W = 2 * layers;
+        g.W = W;
+        g.nb0 = (int)((d0 + W - 1) / W);
+        g.nb1 = (int)((d1 + 31) / 32);
+        g.nsweeps = g.ntiles + W + 31;
+    } else {
+        g.ndim = 2;
+        g.P = 1;
+        g.M = d0 * d1;
+        int W = 8, need = (int)((g.M + 31) / 32);
+        if (W > need) W = need;
+        if (W < 1) W = 1;
+        g.W = W;
+        g.nb0 = 1;
+        g.nb1 = (int)((g.M + 32ull * W - 1) / (32ull * W));
+        g.nsweeps = g.ntiles + 32 * W;
+    }
+    g.num_ctas = g.nb0 * g.nb1;
+    const size_t tpr = (size_t)g.ntiles * kTile;
+    const size_t hrow = (ndim == 3) ? (size_t)g.P * g.nb1 * layers * tpr : (size_t)g.nb1 * layers * tpr;
+    const size_t hplane = (ndim == 3) ? (size_t)g.nb0 * g.nb1 * layers * (32 + layers) * tpr : 4;
+
+    // carve the scratch
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = up256(off + (bytes ? bytes : 1)); return o; };
+    const size_t o_st = take(sizeof(DevState));
+    const size_t o_hrow = take(hrow * 4), o_hplane = take(hplane * 4);
+    const size_t o_prog = take((size_t)g.num_ctas * 4);
+    const size_t o_rb = take(rows * 4), o_ro = take(rows * 8), o_bs = take(((rows + 2047) / 2048 + 1) * 8);
+    const size_t o_lut = take(((size_t)1 << kLutBits) * 4), o_tab = take(kDecTabU32 * 4);
+    const size_t o_len = take(65536), o_sym = take(65536 * 4);
+    if (off > kNoAllocScratchBytes) return SZGB_ESCRATCH;
+    if (out_cap_elems < d0 * d1 * d2) return SZGB_EINVAL;
+    char* b = static_cast<char*>(base);
+    DevState* st = reinterpret_cast<DevState*>(b + o_st);
+    unsigned int* prog = reinterpret_cast<unsigned int*>(b + o_prog);
+    uint32_t* rowbytes = reinterpret_cast<uint32_t*>(b + o_rb);
+    uint64_t* rowoff = reinterpret_cast<uint64_t*>(b + o_ro);
+
+    // clear what starts at zero: the call state and the progress counters
+    DevState init = {};
+    init.eb_f = eb_f;
+    init.twoeb = 2.0f * eb_f;
+    init.m = m;
+    init.center = 1 << (m - 1);
+    init.radius = (float)((1 << (m - 1)) - 1);
+    init.e_eb = (int)((ebu >> 23) & 0xffu);
+    if (cudaMemcpyAsync(st, &init, sizeof(DevState), cudaMemcpyHostToDevice, s) != cudaSuccess) return SZGB_ECUDA;
+    if (cudaMemsetAsync(prog, 0, (size_t)g.num_ctas * 4, s) != cudaSuccess) return SZGB_ECUDA;
+
+    const uint8_t* codebook = in_dev + kHeaderBytes;
+    const uint8_t* table = codebook + cb;
+    const uint8_t* payload = table + tb;
+    uint32_t* lut = reinterpret_cast<uint32_t*>(b + o_lut);
+    uint32_t* dectab = reinterpret_cast<uint32_t*>(b + o_tab);
+    if ((rc = launch_decode_tables(codebook, nsym, m, lut, dectab, reinterpret_cast<uint8_t*>(b + o_len),
+                                   reinterpret_cast<uint32_t*>(b + o_sym), st, s)))
+        return rc;
+    if ((rc = launch_read_rowbytes(table, tw, rows, rowbytes, s))) return rc;
+    if ((rc = launch_scan_rows(rowbytes, rows, rowoff, reinterpret_cast<uint64_t*>(b + o_bs), st, 0, s)))
+        return rc;
+    if ((rc = launch_wave_decompress(g, layers, payload, rowoff, rowbytes, payload + payload_bytes, lut, dectab,
+                                     out_dev, reinterpret_cast<float*>(b + o_hrow),
+                                     reinterpret_cast<float*>(b + o_hplane), prog, st, 4000000000ull, s)))
+        return rc;
+    DevState hs;
+    if (cudaMemcpyAsync(&hs, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SZGB_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SZGB_ECUDA;
+    if (hs.err & kErrTimeout) return SZGB_ETIMEOUT;
+    if (hs.err & kErrCorrupt) return SZGB_ECORRUPT;
+    if (hs.payload != payload_bytes) return SZGB_ECORRUPT;
+    return SZGB_OK;
+}

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libszgb.so")
 
 OK, EINVAL, ENONFINITE, ETRUNC, ECORRUPT, ENOMEM, EBUDGET, ETIMEOUT, ECUDA, EUNSUPPORTED = \
     0, -1, -2, -3, -4, -5, -6, -7, -8, -9
+ESCRATCH = -10
 ABS, REL, ABS_AND_REL = 0, 1, 2
 
 
@@ -71,6 +72,7 @@ def lib():
         L.szgb_phase_name.restype = C.c_char_p
         L.szgb_phase_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.c_int,
                                        C.c_int]
+        L.szgb_decompress_noalloc.argtypes = [vp, sz, vp, sz, vp]
         L.szgb_strerror.argtypes = [C.c_int]
         L.szgb_strerror.restype = C.c_char_p
         _lib = L
@@ -84,7 +86,8 @@ def strerror(code: int) -> str:
 # names of every entry point declared in include/szgb.h
 EXPORTS = ["szgb_create", "szgb_destroy", "szgb_set_stream", "szgb_compress_bound", "szgb_compress",
            "szgb_compress_trace", "szgb_decompress", "szgb_stream_info", "szgb_set_profiling",
-           "szgb_num_phases", "szgb_phase_name", "szgb_phase_times", "szgb_strerror"]
+           "szgb_num_phases", "szgb_phase_name", "szgb_phase_times", "szgb_strerror",
+           "szgb_decompress_noalloc"]
 
 
 def make_params(shape, mode=REL, eb_abs=0.0, eb_rel=1e-4, layers=1, m=0, theta=0.99) -> Params:
@@ -255,3 +258,12 @@ def stream_info_header(hdr) -> dict:
     ndim = b[8]
     d = struct.unpack_from("<3Q", b, 16)
     return {"ndim": ndim, "shape": tuple(int(v) for v in d[3 - ndim:]), "m": b[10], "layers": b[9]}
+
+
+def decompress_noalloc(stream, out, cuda_stream: int = 0) -> int:
+    """szgb_decompress_noalloc on a uint8 CUDA tensor `stream` into the
+    float32 CUDA tensor `out`; returns the C status code.  No memory is
+    allocated by the library (the caller provides `out`)."""
+    return lib().szgb_decompress_noalloc(C.c_void_p(stream.data_ptr()), stream.numel(),
+                                         C.c_void_p(out.data_ptr()), out.numel(),
+                                         C.c_void_p(cuda_stream or 0))

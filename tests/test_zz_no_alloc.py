@@ -1,0 +1,74 @@
+"""szgb_decompress_noalloc: the decompression entry point for callers that
+cannot allocate device memory (a thread issuing work inside an open stream
+capture, a service with a fixed memory plan, an allocator callback).  Its
+scratch is a fixed static device array, so these tests check that its output
+equals szgb_decompress's, bit for bit, on two calls in a row (the array keeps
+the previous call's contents), across two different fields, and that a
+stream needing more scratch than the array holds is refused up front."""
+import struct
+
+import numpy as np
+import pytest
+
+from synthetic import fields
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    from paper_1706_03791_gb300 import build
+    build.build()
+    from paper_1706_03791_gb300 import szgb
+    ctx = szgb.Context(0)
+    yield torch, szgb, ctx
+    ctx.close()
+
+
+def _same(a, b):
+    return np.array_equal(a.cpu().numpy().view(np.uint32), b.cpu().numpy().view(np.uint32))
+
+
+def test_noalloc_matches_decompress_twice(env):
+    torch, szgb, ctx = env
+    cases = [(fields.blobs3d(24, 70, 44, seed=61, nblobs=6), dict(eb_rel=1e-4, m=0)),
+             (fields.grf2d(300, 130, seed=62), dict(eb_rel=1e-4, m=0, layers=2))]
+    for x, kw in cases:
+        xd = torch.from_numpy(x).cuda()
+        s, _ = ctx.compress(xd, **kw)
+        s = s.clone()
+        ref = ctx.decompress(s)
+        torch.cuda.synchronize()
+        for _ in range(2):
+            out = torch.full_like(ref, float("nan"))
+            rc = szgb.decompress_noalloc(s, out, torch.cuda.current_stream().cuda_stream)
+            torch.cuda.synchronize()
+            assert rc == szgb.OK, szgb.strerror(rc)
+            assert _same(out, ref)
+
+
+def test_noalloc_refuses_oversize(env):
+    torch, szgb, ctx = env
+    # a consistent header for a 16 x 3200 x 10000 field with an empty payload:
+    # its halo buffers alone exceed the fixed scratch
+    d = (16, 3200, 10000)
+    rows = d[0] * d[1]
+    nsym, tw = 1, 2
+    h = bytearray(128)
+    h[0:4] = b"SZGB"
+    struct.pack_into("<HH", h, 4, 1, 128)
+    h[8], h[9], h[10], h[11], h[12], h[13] = 3, 1, 8, 1, 1, tw
+    struct.pack_into("<3Q", h, 16, *d)
+    struct.pack_into("<I", h, 68, nsym)
+    cb = (3 * nsym + 3) & ~3
+    tb = (tw * rows + 3) & ~3
+    total = 128 + cb + tb
+    struct.pack_into("<4Q", h, 72, rows, 0, 0, total)
+    buf = np.zeros(total, np.uint8)
+    buf[:128] = np.frombuffer(bytes(h), np.uint8)
+    buf[128:131] = [128, 0, 1]
+    s = torch.from_numpy(buf).cuda()
+    out = torch.empty(16, dtype=torch.float32, device="cuda")
+    rc = szgb.decompress_noalloc(s, out, 0)
+    assert rc == szgb.ESCRATCH
