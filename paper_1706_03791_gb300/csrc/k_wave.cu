@@ -33,8 +33,8 @@
 
 namespace szgb {
 
-constexpr int kPFX = 8;  // x prefetch depth (sweeps)
-constexpr int kPFH = 4;  // halo prefetch depth (sweeps)
+constexpr int kPFX = 12;  // x prefetch depth (sweeps)
+constexpr int kPFH = 3;   // halo prefetch depth (sweeps)
 
 struct WaveArgs {
     WaveGeom g;
@@ -63,18 +63,25 @@ __device__ __forceinline__ int posmod(int a, int m) {
     return r < 0 ? r + m : r;
 }
 
-// Bounded wait until *p >= need.  Returns false on timeout.
-__device__ __forceinline__ bool wait_progress(const unsigned int* p, unsigned int need,
+// Bounded wait until *p >= need; `seen` caches the last value observed so
+// that a satisfied requirement costs no memory access.  Returns false on
+// timeout.
+__device__ __forceinline__ bool wait_progress(const unsigned int* p, unsigned int need, unsigned int& seen,
                                               uint64_t timeout_ns) {
-    if (ld_acquire_u32(p) >= need) return true;
+    if (seen >= need) return true;
+    seen = ld_acquire_u32(p);
+    if (seen >= need) return true;
     uint64_t t0 = globaltimer();
     for (unsigned it = 0; it < (1u << 28); it++) {
-        __nanosleep(128);
-        if (ld_acquire_u32(p) >= need) return true;
+        __nanosleep(64);
+        seen = ld_acquire_u32(p);
+        if (seen >= need) return true;
         if ((it & 63) == 63 && globaltimer() - t0 > timeout_ns) return false;
     }
     return false;
 }
+
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
 // Prediction of the 4 points of a tile from the series of neighbour values.
@@ -84,17 +91,20 @@ __device__ __forceinline__ bool wait_progress(const unsigned int* p, unsigned in
 // product initialising the sum (as the oracle does).
 
 template <int NL, int ND>
-__device__ __forceinline__ float predict_point(const float (&S)[NL + 1][NL + 1][NL + kTile], int k) {
+__device__ __forceinline__ float predict_partial(const float (&S)[NL + 1][NL + 1][NL + kTile], int k) {
+    // all terms with (a, b) != (0, 0): in descending lexicographic order they
+    // come before the own-line terms (0, 0, e)
     constexpr int A = (ND == 3) ? NL : 0;
+    constexpr int B = (ND >= 2) ? NL : 0;  // a 1D field has only own-line terms
     float pred = 0.0f;
     bool first = true;
 #pragma unroll
     for (int a = A; a >= 0; a--) {
 #pragma unroll
-        for (int b = NL; b >= 0; b--) {
+        for (int b = B; b >= 0; b--) {
+            if (a == 0 && b == 0) continue;
 #pragma unroll
             for (int e = NL; e >= 0; e--) {
-                if (a == 0 && b == 0 && e == 0) continue;
                 const float v = S[a][b][NL + k - e];
                 const int c = term_coef(NL, a, b, e);
                 if (NL == 1) {
@@ -106,6 +116,27 @@ __device__ __forceinline__ float predict_point(const float (&S)[NL + 1][NL + 1][
                 }
                 first = false;
             }
+        }
+    }
+    return pred;
+}
+
+// the own-line terms (0, 0, NL) ... (0, 0, 1) added last, in order; in 1D
+// they are the only terms and the first one initialises the sum
+template <int NL, int ND>
+__device__ __forceinline__ float predict_own(float part, const float (&S)[NL + 1][NL + 1][NL + kTile], int k) {
+    float pred = part;
+#pragma unroll
+    for (int e = NL; e >= 1; e--) {
+        const float v = S[0][0][NL + k - e];
+        const int c = term_coef(NL, 0, 0, e);
+        const bool first = (ND == 1 && e == NL);
+        if (NL == 1) {
+            if (first) pred = (c > 0) ? v : -v;
+            else pred = (c > 0) ? __fadd_rn(pred, v) : __fsub_rn(pred, v);
+        } else {
+            const float prod = __fmul_rn((float)c, v);
+            pred = first ? prod : __fadd_rn(pred, prod);
         }
     }
     return pred;
@@ -212,10 +243,31 @@ __device__ __forceinline__ int decode_symbol(BitReader& br, const uint32_t* s_lu
 
 // ---------------------------------------------------------------------------
 // The kernel.  ND = 2 (1D/2D fields) or 3; NL = layers; DEC = decompress.
+//
+// Ring: RD sweeps deep, each sweep slot holds one float4 (a tile of 4
+// recorded values) per (plane slot, row slot); plane/row slots 0..NL-1 are
+// the "virtual" lines that belong to neighbouring CTAs and are filled by the
+// halo warp with cp.async, kPFH sweeps ahead, straight into their slot.
+//
+// Global halos written by the compute lanes as soon as a tile is done:
+//   3D row halo   [P][nb1][NL][tpr]        the last NL rows of each row block
+//   3D plane halo [nb0][nb1][NL][32][tpr]  the last NL planes of each plane block
+//   2D row halo   [nb1][NL][tpr]
+// The corner lines a CTA needs (previous planes x previous rows) come from
+// the diagonal CTA's row halo.  Progress counters (sweeps completed) are
+// published every g.pub sweeps after a fence.
+
+template <int ND, int NL>
+struct Cfg {
+    static constexpr int RD = kPFH + (ND == 3 ? 2 * NL : NL) + 1;  // ring depth
+    static constexpr int MAXE = (ND == 3) ? (NL * (32 + NL) + NL * kMaxWaveWarps + 31) / 32 : 1;  // entries per halo lane
+};
 
 template <int ND, int NL, bool DEC>
-__global__ void __launch_bounds__(17 * 32) k_wave(WaveArgs A) {
+__global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32) k_wave(WaveArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
+    using C = Cfg<ND, NL>;
+    constexpr int RD = C::RD;
     const WaveGeom& g = A.g;
     const int W = g.W;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -236,189 +288,136 @@ __global__ void __launch_bounds__(17 * 32) k_wave(WaveArgs A) {
         return;
     }
 
-    constexpr int D = (ND == 3) ? (2 * NL + 1) : (NL + 1);
-    // ring geometry
     const int NP = (ND == 3) ? (W + NL) : 1;
     const int NR = (ND == 3) ? (32 + NL) : (32 * W + NL);
-    const int ringN = D * NP * NR;
-    const int NE = (ND == 3) ? (NL * (32 + NL) + NL * W) : NL;
+    const int slotsz = NP * NR;  // float4 entries per ring slot
     float4* ring = reinterpret_cast<float4*>(smem);
-    float4* hstage = ring + ringN;                      // [kPFH+1][NE]
-    float4* xstage = hstage + (kPFH + 1) * NE;          // [W][kPFX][32] (compress)
-    uint32_t* s_lut = reinterpret_cast<uint32_t*>(xstage);  // (decompress)
-    uint32_t* s_tab = s_lut + (1 << kLutBits);               // 260 words
+    float4* xstage = ring + RD * slotsz;                     // [W][kPFX][32] (compress)
+    uint32_t* s_lut = reinterpret_cast<uint32_t*>(xstage);   // (decompress)
+    uint32_t* s_tab = s_lut + (1 << kLutBits);
 
-    const int tpr = g.ntiles * kTile;  // padded halo row length (floats)
-    // global halo layouts
-    //   3D row halo  : [P][nb1][NL][tpr]        plane halo: [nb0][nb1][NL][32+NL][tpr]
-    //   2D row halo  : [nb1][NL][tpr]
-    const int r_last = (ND == 3) ? (g.ntiles - 1 + (W - 1) + 31) : (g.ntiles - 1 + 32 * W - 1);
+    const int tpr = g.ntiles * kTile;  // halo row length (floats)
+    const int r_last = g.nsweeps - 1;  // last compute sweep
     const unsigned final_prog = (unsigned)(r_last + 1);
     unsigned int* my_prog = A.prog + item;
-
     QParams qp = load_qparams(A.st);
 
     if (is_halo) {
         // ================= halo warp =================
-        // virtual entry e -> (ring plane slot, ring row slot, skew) and source
-        auto entry_info = [&](int e, int& wp, int& rs, int& skew) {
+        const int NE = (ND == 3) ? (NL * (32 + NL) + NL * W) : NL;
+        const int row_lag = (ND == 3) ? 33 : (32 * W + 1);
+        const int plane_lag = W + 1;
+        const int diag_lag = W + 33;
+        const unsigned* prog_row = nullptr;
+        const unsigned* prog_plane = nullptr;
+        const unsigned* prog_diag = nullptr;
+        if (ND == 3) {
+            if (jb > 0) prog_row = A.prog + ib * g.nb1 + jb - 1;
+            if (ib > 0) prog_plane = A.prog + (ib - 1) * g.nb1 + jb;
+            if (ib > 0 && jb > 0) prog_diag = A.prog + (ib - 1) * g.nb1 + jb - 1;
+        } else if (jb > 0) {
+            prog_row = A.prog + jb - 1;
+        }
+        // per-lane entries: ring offset within a slot, skew, source of tile 0
+        int e_off[C::MAXE], e_skew[C::MAXE];
+        const float* e_src[C::MAXE];
+#pragma unroll
+        for (int j = 0; j < C::MAXE; j++) {
+            const int e = lane + 32 * j;
+            e_off[j] = -1;
+            e_skew[j] = 0;
+            e_src[j] = nullptr;
+            if (e >= NE) continue;
+            int wp, rs;
+            const float* src = nullptr;
             if (ND == 3) {
                 if (e < NL * (32 + NL)) {
-                    wp = e / (32 + NL);
+                    const int p = e / (32 + NL);
+                    wp = p;
                     rs = e % (32 + NL);
-                    skew = (wp - NL) + (rs - NL);
+                    if (ib > 0) {
+                        if (rs >= NL) {
+                            size_t off = ((((size_t)(ib - 1) * g.nb1 + jb) * NL + p) * 32 + (rs - NL)) * tpr;
+                            src = A.halo_plane + off;
+                        } else if (jb > 0) {
+                            uint64_t plane = (uint64_t)(ib - 1) * W + W - NL + p;
+                            size_t off = (((size_t)plane * g.nb1 + (jb - 1)) * NL + rs) * tpr;
+                            src = A.halo_row + off;
+                        }
+                    }
                 } else {
-                    int e2 = e - NL * (32 + NL);
-                    wp = NL + e2 / NL;
-                    rs = e2 % NL;
-                    skew = (wp - NL) + (rs - NL);
+                    const int e2 = e - NL * (32 + NL);
+                    const int w = e2 / NL, q = e2 % NL;
+                    wp = NL + w;
+                    rs = q;
+                    const uint64_t plane = (uint64_t)ib * W + w;
+                    if (jb > 0 && plane < g.P) {
+                        size_t off = (((size_t)plane * g.nb1 + (jb - 1)) * NL + q) * tpr;
+                        src = A.halo_row + off;
+                    }
                 }
             } else {
                 wp = 0;
                 rs = e;
-                skew = e - NL;
+                if (jb > 0) src = A.halo_row + ((size_t)(jb - 1) * NL + e) * tpr;
             }
-        };
-        // source pointer of virtual entry e for tile c (nullptr = zeros)
-        auto entry_src = [&](int e, int c) -> const float* {
-            if (c < 0 || c >= g.ntiles) return nullptr;
-            if (ND == 3) {
-                if (e < NL * (32 + NL)) {
-                    if (ib == 0) return nullptr;
-                    int p = e / (32 + NL), rs = e % (32 + NL);
-                    size_t off = ((((size_t)(ib - 1) * g.nb1 + jb) * NL + p) * (32 + NL) + rs) * tpr;
-                    return A.halo_plane + off + (size_t)c * kTile;
-                } else {
-                    if (jb == 0) return nullptr;
-                    int e2 = e - NL * (32 + NL);
-                    int w = e2 / NL, q = e2 % NL;
-                    uint64_t plane = (uint64_t)ib * W + w;
-                    if (plane >= g.P) return nullptr;
-                    size_t off = (((size_t)plane * g.nb1 + (jb - 1)) * NL + q) * tpr;
-                    return A.halo_row + off + (size_t)c * kTile;
-                }
-            } else {
-                if (jb == 0) return nullptr;
-                size_t off = ((size_t)(jb - 1) * NL + e) * tpr;
-                return A.halo_row + off + (size_t)c * kTile;
-            }
-        };
-        const unsigned* prog_row = (jb > 0) ? (A.prog + ((ND == 3) ? (ib * g.nb1 + jb - 1) : (jb - 1))) : nullptr;
-        const unsigned* prog_plane = (ND == 3 && ib > 0) ? (A.prog + ((ib - 1) * g.nb1 + jb)) : nullptr;
-        const int row_lag = (ND == 3) ? 33 : (32 * W + 1);
-        const int plane_lag = W + 1;
+            e_off[j] = wp * NR + rs;
+            e_skew[j] = (ND == 3) ? (wp - NL) + (rs - NL) : (rs - NL);
+            e_src[j] = src;
+        }
         bool timed_out = false;
+        unsigned seen_row = 0, seen_plane = 0, seen_diag = 0;
+        const float* dummy = A.halo_row;  // a valid address for zero-fill copies
 
-        auto prefetch = [&](int rp) {  // issue loads of sweep rp's virtual entries
-            if (rp >= g.nsweeps) { cp_async_commit(); return; }
-            if (!timed_out && lane == 0) {
+        // issue the cp.async loads of the virtual entries of sweep rp into
+        // their ring slot, after the producers have published enough progress
+        auto issue = [&](int rp) {
+            if (lane == 0 && !timed_out) {
                 if (prog_row) {
-                    unsigned need = min((unsigned)(rp + row_lag), final_prog);
-                    if (!wait_progress(prog_row, need, A.timeout_ns)) timed_out = true;
+                    unsigned need = min((unsigned)max(rp + row_lag, 0), final_prog);
+                    if (!wait_progress(prog_row, need, seen_row, A.timeout_ns)) timed_out = true;
                 }
                 if (prog_plane && !timed_out) {
-                    unsigned need = min((unsigned)(rp + plane_lag), final_prog);
-                    if (!wait_progress(prog_plane, need, A.timeout_ns)) timed_out = true;
+                    unsigned need = min((unsigned)max(rp + plane_lag, 0), final_prog);
+                    if (!wait_progress(prog_plane, need, seen_plane, A.timeout_ns)) timed_out = true;
+                }
+                if (prog_diag && !timed_out) {
+                    unsigned need = min((unsigned)max(rp + diag_lag, 0), final_prog);
+                    if (!wait_progress(prog_diag, need, seen_diag, A.timeout_ns)) timed_out = true;
                 }
             }
             timed_out = __shfl_sync(0xffffffffu, timed_out ? 1 : 0, 0) != 0;
-            __syncwarp();
-            float4* dst = hstage + (rp % (kPFH + 1)) * NE;
-            for (int e = lane; e < NE; e += 32) {
-                int wp, rs, skew;
-                entry_info(e, wp, rs, skew);
-                const float* src = timed_out ? nullptr : entry_src(e, rp - skew);
-                if (src) cp_async16(dst + e, src, 16);
-                else dst[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+            float4* slot = ring + posmod(rp, RD) * slotsz;
+#pragma unroll
+            for (int j = 0; j < C::MAXE; j++) {
+                if (e_off[j] < 0) continue;
+                const int c = rp - e_skew[j];
+                const bool ok = e_src[j] && !timed_out && c >= 0 && c < g.ntiles;
+                cp_async16(slot + e_off[j], ok ? (const void*)(e_src[j] + (size_t)c * kTile) : (const void*)dummy,
+                           ok ? 16 : 0);
             }
             cp_async_commit();
         };
-        // Virtual entries with a negative sweep index (the first tiles of the
-        // halo rows/planes, whose skew is negative) are loaded synchronously
-        // before sweep 0 into their ring slots.
         const int min_sweep = (ND == 3) ? -2 * NL : -NL;
-        for (int rv = min_sweep; rv < 0; rv++) {
-            if (!timed_out && lane == 0) {
-                if (prog_row) {
-                    unsigned need = min((unsigned)max(rv + row_lag, 0), final_prog);
-                    if (!wait_progress(prog_row, need, A.timeout_ns)) timed_out = true;
-                }
-                if (prog_plane && !timed_out) {
-                    unsigned need = min((unsigned)max(rv + plane_lag, 0), final_prog);
-                    if (!wait_progress(prog_plane, need, A.timeout_ns)) timed_out = true;
-                }
-            }
-            timed_out = __shfl_sync(0xffffffffu, timed_out ? 1 : 0, 0) != 0;
-            __syncwarp();
-            const int slot = posmod(rv, D);
-            for (int e = lane; e < NE; e += 32) {
-                int wp, rs, skew;
-                entry_info(e, wp, rs, skew);
-                const float* src = timed_out ? nullptr : entry_src(e, rv - skew);
-                float4 v = src ? __ldcg(reinterpret_cast<const float4*>(src)) : make_float4(0.f, 0.f, 0.f, 0.f);
-                ring[(slot * NP + wp) * NR + rs] = v;
-            }
-        }
-        for (int rp = 0; rp < kPFH; rp++) prefetch(rp);
-        __syncthreads();  // prologue entries visible before sweep 0
+        for (int rv = min_sweep; rv < kPFH; rv++) issue(rv);
+        cp_async_wait<0>();
+        __syncthreads();  // prologue: virtual entries of sweeps < kPFH in place
 
-        for (int r = 0; r < g.nsweeps; r++) {
-            prefetch(r + kPFH);
-            cp_async_wait<kPFH>();
-            __syncwarp();
-            // virtual entries of sweep r -> ring slot r % D
-            const float4* src = hstage + (r % (kPFH + 1)) * NE;
-            const int slot = r % D;
-            for (int e = lane; e < NE; e += 32) {
-                int wp, rs, skew;
-                entry_info(e, wp, rs, skew);
-                ring[(slot * NP + wp) * NR + rs] = src[e];
-            }
-            // halo out: entries of sweep r-1
-            if (r >= 1) {
-                const int ps = (r - 1) % D;
-                if (ND == 3) {
-                    if (jb + 1 < g.nb1) {
-                        for (int e = lane; e < NL * W; e += 32) {
-                            int w = e / NL, q = e % NL;
-                            int t = 32 - NL + q;
-                            int c = (r - 1) - w - t;
-                            uint64_t plane = (uint64_t)ib * W + w;
-                            if (c < 0 || c >= g.ntiles || plane >= g.P) continue;
-                            size_t off = (((size_t)plane * g.nb1 + jb) * NL + q) * tpr + (size_t)c * kTile;
-                            *reinterpret_cast<float4*>(A.halo_row + off) = ring[(ps * NP + w + NL) * NR + t + NL];
-                        }
-                    }
-                    if (ib + 1 < g.nb0) {
-                        for (int e = lane; e < NL * (32 + NL); e += 32) {
-                            int p = e / (32 + NL), rs = e % (32 + NL);
-                            int w = W - NL + p, t = rs - NL;
-                            int c = (r - 1) - w - t;
-                            if (c < 0 || c >= g.ntiles) continue;
-                            size_t off = ((((size_t)ib * g.nb1 + jb) * NL + p) * (32 + NL) + rs) * tpr + (size_t)c * kTile;
-                            *reinterpret_cast<float4*>(A.halo_plane + off) = ring[(ps * NP + w + NL) * NR + rs];
-                        }
-                    }
-                } else {
-                    if (jb + 1 < g.nb1) {
-                        for (int q = lane; q < NL; q += 32) {
-                            int rho = 32 * W - NL + q;
-                            int c = (r - 1) - rho;
-                            if (c < 0 || c >= g.ntiles) continue;
-                            size_t off = ((size_t)jb * NL + q) * tpr + (size_t)c * kTile;
-                            *reinterpret_cast<float4*>(A.halo_row + off) = ring[ps * NR + rho + NL];
-                        }
-                    }
-                }
-                __threadfence();
+        for (int r = 0; r <= r_last; r++) {
+            if (r > 0 && r % g.pub == 0) {  // sweeps < r are complete: publish
+                fence_acq_rel_gpu();
                 __syncwarp();
                 if (lane == 0) st_release_u32(my_prog, (unsigned)r);
             }
+            issue(r + kPFH);
+            cp_async_wait<kPFH>();
             if (lane == 0 && timed_out) s_abort = 1;
             __syncthreads();
             if (s_abort) break;
         }
         cp_async_wait<0>();
+        fence_acq_rel_gpu();
+        __syncwarp();
         if (lane == 0) {
             if (s_abort) {
                 atomicOr(&A.st->err, kErrTimeout);
@@ -431,7 +430,6 @@ __global__ void __launch_bounds__(17 * 32) k_wave(WaveArgs A) {
     }
 
     // ================= compute warps =================
-    // lane -> row / plane and skew
     uint64_t plane, row;
     int skew, wp_own, rs_own;
     if (ND == 3) {
@@ -450,6 +448,22 @@ __global__ void __launch_bounds__(17 * 32) k_wave(WaveArgs A) {
     const bool valid = (plane < g.P) && (row < g.M);
     const uint64_t rowid = plane * g.M + row;
     const uint64_t rowbase = rowid * g.N;
+    const int own_off = wp_own * NR + rs_own;
+    // halo outputs written by this lane (null when the line has no consumer)
+    float* hout_row = nullptr;
+    float* hout_plane = nullptr;
+    if (valid) {
+        if (ND == 3) {
+            if (lane >= 32 - NL && jb + 1 < g.nb1)
+                hout_row = A.halo_row + (((size_t)plane * g.nb1 + jb) * NL + (lane - (32 - NL))) * tpr;
+            if (warp >= W - NL && ib + 1 < g.nb0)
+                hout_plane = A.halo_plane +
+                             ((((size_t)ib * g.nb1 + jb) * NL + (warp - (W - NL))) * 32 + lane) * tpr;
+        } else {
+            if (warp == W - 1 && lane >= 32 - NL && jb + 1 < g.nb1)
+                hout_row = A.halo_row + ((size_t)jb * NL + (lane - (32 - NL))) * tpr;
+        }
+    }
 
     // tails: the last NL values of the previous tile of every series
     float tail[NL + 1][NL + 1][NL];
@@ -460,13 +474,11 @@ __global__ void __launch_bounds__(17 * 32) k_wave(WaveArgs A) {
 #pragma unroll
             for (int j = 0; j < NL; j++) tail[a][b][j] = 0.0f;
 
-    // decompression state
     BitReader br;
     int T = 1, maxlen = 1;
     bool bad = false;
     uint64_t rowbits_avail = 0;
     if constexpr (DEC) {
-        // decoder tables to shared memory (all compute threads)
         T = (int)A.st->lut_bits;
         maxlen = (int)A.st->maxlen;
         const int nthr = W * 32;
@@ -479,25 +491,25 @@ __global__ void __launch_bounds__(17 * 32) k_wave(WaveArgs A) {
             br.init(A.payload, off, (uint64_t)(A.stream_end - A.payload));
         }
     }
+    const uint16_t* g_sorted = reinterpret_cast<const uint16_t*>(A.dectab + 260);
 
-    float4* xs = xstage + warp * kPFX * 32;
+    float4* xs = xstage + warp * kPFX * 32 + lane;
+    const float* xrow = A.x + rowbase;
     auto x_prefetch = [&](int rp) {
         if constexpr (!DEC) {
-            int c = rp - skew;
-            float4* dst = xs + (rp % kPFX) * 32 + lane;
-            if (valid && c >= 0 && c < g.ntiles) {
-                uint64_t col = (uint64_t)c * kTile;
-                const float* src = A.x + rowbase + col;
-                if (g.aligned) {
-                    int nbytes = (int)(min((uint64_t)kTile, g.N - col) * 4);
-                    cp_async16(dst, src, nbytes);
-                } else {
-                    float* d = reinterpret_cast<float*>(dst);
+            const int c = rp - skew;
+            float4* dst = xs + (rp % kPFX) * 32;
+            const bool ok = valid && c >= 0 && c < g.ntiles;
+            if (g.aligned) {
+                const uint64_t col = (uint64_t)c * kTile;
+                cp_async16(dst, ok ? (const void*)(xrow + col) : (const void*)A.x, ok ? 16 : 0);
+            } else {
+                float* d = reinterpret_cast<float*>(dst);
 #pragma unroll
-                    for (int k = 0; k < kTile; k++) {
-                        bool in = col + k < g.N;
-                        cp_async4(d + k, in ? src + k : src, in ? 4 : 0);
-                    }
+                for (int k = 0; k < kTile; k++) {
+                    const uint64_t col = (uint64_t)c * kTile + k;
+                    const bool in = ok && col < g.N;
+                    cp_async4(d + k, in ? (const void*)(xrow + col) : (const void*)A.x, in ? 4 : 0);
                 }
             }
             cp_async_commit();
@@ -506,18 +518,17 @@ __global__ void __launch_bounds__(17 * 32) k_wave(WaveArgs A) {
     if constexpr (!DEC) {
         for (int rp = 0; rp < kPFX - 1; rp++) x_prefetch(rp);
     }
-
-    const uint16_t* g_sorted = reinterpret_cast<const uint16_t*>(A.dectab + 260);
     __syncthreads();  // matches the halo warp's prologue barrier
 
-    for (int r = 0; r < g.nsweeps; r++) {
+    for (int r = 0; r <= r_last; r++) {
         if constexpr (!DEC) {
             x_prefetch(r + kPFX - 1);
             cp_async_wait<kPFX - 1>();
         }
         const int c = r - skew;
         if (c >= 0 && c < g.ntiles) {
-            // neighbour series of this tile
+            // neighbour series of this tile: tails + the ring entries written
+            // a + b sweeps ago by the lane at (plane - a, row - b)
             float S[NL + 1][NL + 1][NL + kTile];
 #pragma unroll
             for (int a = 0; a <= NL; a++)
@@ -525,28 +536,34 @@ __global__ void __launch_bounds__(17 * 32) k_wave(WaveArgs A) {
                 for (int b = 0; b <= NL; b++) {
 #pragma unroll
                     for (int j = 0; j < NL; j++) S[a][b][j] = tail[a][b][j];
-                    if ((ND == 2 && a > 0) || (a == 0 && b == 0)) {
+                    if ((ND != 3 && a > 0) || (a == 0 && b == 0)) {
 #pragma unroll
                         for (int k = 0; k < kTile; k++) S[a][b][NL + k] = 0.0f;
                         continue;
                     }
-                    int slot = posmod(r - a - b, D);
-                    float4 v = (ND == 3) ? ring[(slot * NP + wp_own - a) * NR + rs_own - b]
-                                         : ring[slot * NR + rs_own - b];
+                    const float4 v = ring[posmod(r - a - b, RD) * slotsz + own_off - a * NR - b];
                     S[a][b][NL + 0] = v.x;
                     S[a][b][NL + 1] = v.y;
                     S[a][b][NL + 2] = v.z;
                     S[a][b][NL + 3] = v.w;
                 }
+            // partial predictions: every term except the own-line ones,
+            // summed in the method's order (they precede the own-line terms)
+            float part[kTile];
+#pragma unroll
+            for (int k = 0; k < kTile; k++) part[k] = predict_partial<NL, ND>(S, k);
             int code[kTile];
             if constexpr (!DEC) {
-                float4 xv4 = xs[(r % kPFX) * 32 + lane];
-                float xv[kTile] = {xv4.x, xv4.y, xv4.z, xv4.w};
+                const float4 xv4 = xs[(r % kPFX) * 32];
+                const float xv[kTile] = {xv4.x, xv4.y, xv4.z, xv4.w};
+                float tr[kTile];
+#pragma unroll
+                for (int k = 0; k < kTile; k++) tr[k] = trunc_value(xv[k], qp.e_eb);
 #pragma unroll
                 for (int k = 0; k < kTile; k++) {
-                    float pred = predict_point<NL, ND>(S, k);
+                    const float pred = predict_own<NL, ND>(part[k], S, k);
                     float V;
-                    code[k] = quantize(xv[k], pred, qp, V);
+                    code[k] = quantize_tr(xv[k], pred, tr[k], qp, V);
                     S[0][0][NL + k] = V;
                 }
             } else {
@@ -569,13 +586,14 @@ __global__ void __launch_bounds__(17 * 32) k_wave(WaveArgs A) {
                 }
 #pragma unroll
                 for (int k = 0; k < kTile; k++) {
-                    float pred = predict_point<NL, ND>(S, k);
+                    const float pred = predict_own<NL, ND>(part[k], S, k);
                     S[0][0][NL + k] = code[k] ? dequantize(code[k], pred, qp) : uv[k];
                 }
             }
-            float4 vout = make_float4(S[0][0][NL], S[0][0][NL + 1], S[0][0][NL + 2], S[0][0][NL + 3]);
-            if (ND == 3) ring[((r % D) * NP + wp_own) * NR + rs_own] = vout;
-            else ring[(r % D) * NR + rs_own] = vout;
+            const float4 vout = make_float4(S[0][0][NL], S[0][0][NL + 1], S[0][0][NL + 2], S[0][0][NL + 3]);
+            ring[(r % RD) * slotsz + own_off] = vout;
+            if (hout_row) *reinterpret_cast<float4*>(hout_row + (size_t)c * kTile) = vout;
+            if (ND == 3 && hout_plane) *reinterpret_cast<float4*>(hout_plane + (size_t)c * kTile) = vout;
 #pragma unroll
             for (int a = 0; a <= NL; a++)
 #pragma unroll
@@ -593,7 +611,7 @@ __global__ void __launch_bounds__(17 * 32) k_wave(WaveArgs A) {
                         *reinterpret_cast<uint2*>(A.codes + rowbase + col) = pk;
                         if (A.recorded) *reinterpret_cast<float4*>(A.recorded + rowbase + col) = vout;
                     } else {
-                        float vv[kTile] = {vout.x, vout.y, vout.z, vout.w};
+                        const float vv[kTile] = {vout.x, vout.y, vout.z, vout.w};
 #pragma unroll
                         for (int k = 0; k < kTile; k++)
                             if (col + k < g.N) {
@@ -605,7 +623,7 @@ __global__ void __launch_bounds__(17 * 32) k_wave(WaveArgs A) {
                     if (full) {
                         *reinterpret_cast<float4*>(A.out + rowbase + col) = vout;
                     } else {
-                        float vv[kTile] = {vout.x, vout.y, vout.z, vout.w};
+                        const float vv[kTile] = {vout.x, vout.y, vout.z, vout.w};
 #pragma unroll
                         for (int k = 0; k < kTile; k++)
                             if (col + k < g.N) A.out[rowbase + col + k] = vv[k];
@@ -626,14 +644,14 @@ __global__ void __launch_bounds__(17 * 32) k_wave(WaveArgs A) {
 // host side
 
 size_t wave_smem_bytes(const WaveGeom& g, int layers, bool decompress) {
-    int NL = layers, W = g.W;
-    int D, NP, NR, NE;
+    const int NL = layers, W = g.W;
+    int RD, NP, NR;
     if (g.ndim == 3) {
-        D = 2 * NL + 1; NP = W + NL; NR = 32 + NL; NE = NL * (32 + NL) + NL * W;
+        RD = kPFH + 2 * NL + 1; NP = W + NL; NR = 32 + NL;
     } else {
-        D = NL + 1; NP = 1; NR = 32 * W + NL; NE = NL;
+        RD = kPFH + NL + 1; NP = 1; NR = 32 * W + NL;
     }
-    size_t b = (size_t)D * NP * NR * 16 + (size_t)(kPFH + 1) * NE * 16;
+    size_t b = (size_t)RD * NP * NR * 16;
     if (decompress) b += (size_t)(1 << kLutBits) * 4 + 260 * 4;
     else b += (size_t)W * kPFX * 32 * 16;
     return b;
@@ -651,10 +669,9 @@ static int launch_t(const WaveArgs& a, cudaStream_t s) {
 
 template <bool DEC>
 static int launch_any(const WaveArgs& a, int layers, cudaStream_t s) {
-    if (a.g.ndim == 3) {
-        return layers == 1 ? launch_t<3, 1, DEC>(a, s) : launch_t<3, 2, DEC>(a, s);
-    }
-    return layers == 1 ? launch_t<2, 1, DEC>(a, s) : launch_t<2, 2, DEC>(a, s);
+    if (a.g.ndim == 3) return layers == 1 ? launch_t<3, 1, DEC>(a, s) : launch_t<3, 2, DEC>(a, s);
+    if (a.g.ndim == 2) return layers == 1 ? launch_t<2, 1, DEC>(a, s) : launch_t<2, 2, DEC>(a, s);
+    return layers == 1 ? launch_t<1, 1, DEC>(a, s) : launch_t<1, 2, DEC>(a, s);
 }
 
 int launch_wave_compress(const WaveGeom& g, int layers, const float* x, uint16_t* codes,

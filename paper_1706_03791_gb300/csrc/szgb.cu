@@ -61,7 +61,7 @@ struct szgb_ctx {
     uint64_t ph_calls[PH_N] = {};
     cudaEvent_t ev0[PH_N] = {}, ev1[PH_N] = {};
     int sm_count = 152;
-    int W2 = 8, W3 = 8;
+    int W2 = 8, W3 = 8, pub = 8;
     uint64_t timeout_ns = 4000000000ull;
 };
 
@@ -146,9 +146,9 @@ WaveGeom make_geom(const szgb_ctx* c, const CallParams& cp, int layers) {
         g.W = W;
         g.nb0 = (int)((cp.d0 + W - 1) / W);
         g.nb1 = (int)((cp.d1 + 31) / 32);
-        g.nsweeps = g.ntiles + W + 31;
+        g.nsweeps = g.ntiles + W + 30;  // last sweep: tile ntiles-1 of warp W-1, lane 31
     } else {
-        g.ndim = 2;
+        g.ndim = cp.ndim;
         g.P = 1;
         g.M = cp.d0 * cp.d1;  // 1D: a single row
         int W = c->W2;
@@ -158,9 +158,10 @@ WaveGeom make_geom(const szgb_ctx* c, const CallParams& cp, int layers) {
         g.W = W;
         g.nb0 = 1;
         g.nb1 = (int)((g.M + 32ull * W - 1) / (32ull * W));
-        g.nsweeps = g.ntiles + 32 * W;
+        g.nsweeps = g.ntiles + 32 * W - 1;  // last sweep: tile ntiles-1 of row 32W-1
     }
     g.num_ctas = g.nb0 * g.nb1;
+    g.pub = c->pub;
     return g;
 }
 
@@ -168,7 +169,7 @@ void halo_sizes(const WaveGeom& g, int layers, size_t* row_floats, size_t* plane
     size_t tpr = (size_t)g.ntiles * kTile;
     if (g.ndim == 3) {
         *row_floats = (size_t)g.P * g.nb1 * layers * tpr;
-        *plane_floats = (size_t)g.nb0 * g.nb1 * layers * (32 + layers) * tpr;
+        *plane_floats = (size_t)g.nb0 * g.nb1 * layers * 32 * tpr;
     } else {
         *row_floats = (size_t)g.nb1 * layers * tpr;
         *plane_floats = 4;
@@ -519,8 +520,9 @@ int szgb_create(szgb_ctx** out, int device, size_t device_mem_budget) {
     }
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
     const char* e;
-    if ((e = getenv("SZGB_W2"))) c->W2 = std::max(1, atoi(e));
-    if ((e = getenv("SZGB_W3"))) c->W3 = std::max(1, std::min(16, atoi(e)));
+    if ((e = getenv("SZGB_W2"))) c->W2 = std::max(1, std::min(kMaxWaveWarps, atoi(e)));
+    if ((e = getenv("SZGB_W3"))) c->W3 = std::max(1, std::min(kMaxWaveWarps, atoi(e)));
+    if ((e = getenv("SZGB_PUB"))) c->pub = std::max(1, std::min(64, atoi(e)));
     *out = c;
     return SZGB_OK;
 }

@@ -18,6 +18,7 @@ constexpr int kHeaderBytes = 128;
 constexpr int kTile = 4;           // columns per sweep and lane (one float4)
 constexpr int kMaxLayers = 2;      // n supported by the GPU kernels
 constexpr int kLutBits = 11;       // decoder lookup-table index bits
+constexpr int kMaxWaveWarps = 8;   // compute warps per wavefront CTA (plus one halo warp)
 constexpr uint32_t kProgAbort = 0x7fffffffu;
 
 // Error flags raised on the device (DevState::err bitmask).
@@ -127,6 +128,19 @@ __device__ __forceinline__ int quantize(float x, float pred, const QParams& qp, 
     return ok ? ((int)qn + qp.center) : 0;
 }
 
+// As quantize, with the truncated representation of x computed beforehand
+// (it does not depend on the prediction, so it stays off the dependency chain).
+__device__ __forceinline__ int quantize_tr(float x, float pred, float tr, const QParams& qp, float& V) {
+    const float diff = __fsub_rn(x, pred);
+    const float q = rintf(__fmul_rn(diff, qp.inv));
+    const float qn = __fadd_rn(q, 0.0f);
+    const float dq = __fadd_rn(pred, __fmul_rn(qn, qp.twoeb));
+    const float err = __fsub_rn(x, dq);
+    const bool ok = (fabsf(q) <= qp.radius) & ((fabsf(err) < qp.eb) | (x == dq));
+    V = ok ? dq : tr;
+    return ok ? ((int)qn + qp.center) : 0;
+}
+
 // Reconstruction of a predictable value from its code.
 __device__ __forceinline__ float dequantize(int code, float pred, const QParams& qp) {
     float qf = (float)(code - qp.center);
@@ -174,7 +188,7 @@ __device__ __forceinline__ uint32_t bswap32(uint32_t v) { return __byte_perm(v, 
 // --------------------------------------------------------------------------
 // geometry of the wavefront launch (host-computed, passed by value)
 struct WaveGeom {
-    int ndim;             // 1,2 treated as 2D (rows); 3 as 3D
+    int ndim;             // 1 and 2 use the row topology, 3 the plane x row one
     uint64_t P, M, N;     // extents (planes, rows, columns)
     int ntiles;           // ceil(N / kTile)
     int W;                // compute warps per CTA
@@ -182,6 +196,7 @@ struct WaveGeom {
     int nsweeps;          // sweeps per CTA including the final flush sweep
     int aligned;          // rows start on 16-byte boundaries (N % 4 == 0)
     int num_ctas;
+    int pub;              // progress is published every `pub` sweeps
 };
 
 // host launchers (each in its own translation unit)
