@@ -9,32 +9,35 @@
 // the Huffman decode of each row fused in (a row is one stream chunk).
 //
 // Parallel schedule.  A point depends only on neighbours with smaller
-// (plane, row, column) offsets, so any order that respects that DAG gives
+// (plane, row, column) coordinates, so any order that respects that DAG gives
 // identical bits.  The field is cut into lines along the fastest axis
-// ("rows"); a lane owns one row and walks it in tiles of kTile = 4 columns,
-// one tile per "sweep".  Lanes are skewed by one sweep per row (2D) or per
-// row and per plane (3D), so every value a lane needs from another row or
-// plane was produced in an EARLIER sweep and sits in a shared-memory ring;
-// only the lane's own left neighbour chain is on the critical path.
+// ("rows"); a lane owns one row and computes one column per step.
+//   * Within a warp the 32 lanes hold 32 consecutive rows, lane t one column
+//     behind lane t-1: the value of the row above at the same column was made
+//     by lane t-1 in the previous step and arrives with one shfl.up.
+//   * Warps are skewed by whole sweeps of 4 steps: in 3D warp w holds plane
+//     i0+w (skew 4w), in 2D it holds the next 32 rows (skew 36w).  Their
+//     values pass through shared-memory rings, with one CTA barrier per
+//     sweep.  The plane ring is stored diagonally (row t at column l + t), so
+//     every lane reads and writes one aligned float4 per sweep.
+// Only the lane's own left neighbour and the shuffled upper neighbour are on
+// the critical path; the descending summation order puts them last.
 //
-//   2D: CTA = W warps = 32W consecutive rows, row rho processes tile
-//       c = r - rho in sweep r.
-//   3D: CTA = W warps (planes) x 32 lanes (rows), lane (w,t) processes tile
-//       c = r - w - t in sweep r.
-//
-// A CTA boundary is crossed through global "halo" buffers: an extra warp per
-// CTA copies the CTA's boundary rows/planes out of the ring after each sweep,
-// publishes a progress counter (release), and prefetches the neighbouring
-// CTAs' halos into the ring (acquire, cp.async), with bounded waits.  CTAs
-// take work items from a ticket counter in dependency order, so a CTA only
-// ever waits for CTAs that are already resident: forward progress holds for
-// any grid size.
+// CTA boundaries go through global "halo" buffers written by the lanes that
+// compute the boundary lines; an extra warp per CTA publishes a progress
+// counter every few sweeps (fence + st.release) and prefetches the
+// neighbouring CTAs' halos into the rings with cp.async after bounded
+// acquire-waits.  CTAs take work items from a ticket counter in dependency
+// order, so a CTA only waits for CTAs that are already resident.
 #include "szgb_internal.cuh"
 
 namespace szgb {
 
-constexpr int kPFX = 12;  // x prefetch depth (sweeps)
+constexpr int kPFX = 8;   // x prefetch depth (sweeps), power of two
 constexpr int kPFH = 3;   // halo prefetch depth (sweeps)
+constexpr int kRP = 32;   // plane ring: floats per row (8 blocks of 4 columns)
+constexpr int kRPS = 36;  // plane ring row stride (9 float4: conflict-free)
+constexpr int kRV = 64;   // virtual-row ring: floats per line
 
 struct WaveArgs {
     WaveGeom g;
@@ -82,65 +85,6 @@ __device__ __forceinline__ bool wait_progress(const unsigned int* p, unsigned in
 }
 
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
-
-// ---------------------------------------------------------------------------
-// Prediction of the 4 points of a tile from the series of neighbour values.
-// S[a][b][j]: values of the line at plane offset a, row offset b, for
-// columns (tile start - NL + j), j in [0, NL + 4); S[0][0] is the own line.
-// Terms are summed in descending lexicographic (a, b, e) order, the first
-// product initialising the sum (as the oracle does).
-
-template <int NL, int ND>
-__device__ __forceinline__ float predict_partial(const float (&S)[NL + 1][NL + 1][NL + kTile], int k) {
-    // all terms with (a, b) != (0, 0): in descending lexicographic order they
-    // come before the own-line terms (0, 0, e)
-    constexpr int A = (ND == 3) ? NL : 0;
-    constexpr int B = (ND >= 2) ? NL : 0;  // a 1D field has only own-line terms
-    float pred = 0.0f;
-    bool first = true;
-#pragma unroll
-    for (int a = A; a >= 0; a--) {
-#pragma unroll
-        for (int b = B; b >= 0; b--) {
-            if (a == 0 && b == 0) continue;
-#pragma unroll
-            for (int e = NL; e >= 0; e--) {
-                const float v = S[a][b][NL + k - e];
-                const int c = term_coef(NL, a, b, e);
-                if (NL == 1) {
-                    if (first) pred = (c > 0) ? v : -v;
-                    else pred = (c > 0) ? __fadd_rn(pred, v) : __fsub_rn(pred, v);
-                } else {
-                    float prod = __fmul_rn((float)c, v);
-                    pred = first ? prod : __fadd_rn(pred, prod);
-                }
-                first = false;
-            }
-        }
-    }
-    return pred;
-}
-
-// the own-line terms (0, 0, NL) ... (0, 0, 1) added last, in order; in 1D
-// they are the only terms and the first one initialises the sum
-template <int NL, int ND>
-__device__ __forceinline__ float predict_own(float part, const float (&S)[NL + 1][NL + 1][NL + kTile], int k) {
-    float pred = part;
-#pragma unroll
-    for (int e = NL; e >= 1; e--) {
-        const float v = S[0][0][NL + k - e];
-        const int c = term_coef(NL, 0, 0, e);
-        const bool first = (ND == 1 && e == NL);
-        if (NL == 1) {
-            if (first) pred = (c > 0) ? v : -v;
-            else pred = (c > 0) ? __fadd_rn(pred, v) : __fsub_rn(pred, v);
-        } else {
-            const float prod = __fmul_rn((float)c, v);
-            pred = first ? prod : __fadd_rn(pred, prod);
-        }
-    }
-    return pred;
-}
 
 // ---------------------------------------------------------------------------
 // Per-lane bit reader over one row chunk (MSB-first), for decompression.
@@ -242,32 +186,33 @@ __device__ __forceinline__ int decode_symbol(BitReader& br, const uint32_t* s_lu
 }
 
 // ---------------------------------------------------------------------------
-// The kernel.  ND = 2 (1D/2D fields) or 3; NL = layers; DEC = decompress.
+// The kernel.  ND = 1, 2 (row topology) or 3 (plane x row); NL = layers;
+// DEC = decompress.
 //
-// Ring: RD sweeps deep, each sweep slot holds one float4 (a tile of 4
-// recorded values) per (plane slot, row slot); plane/row slots 0..NL-1 are
-// the "virtual" lines that belong to neighbouring CTAs and are filled by the
-// halo warp with cp.async, kPFH sweeps ahead, straight into their slot.
-//
-// Global halos written by the compute lanes as soon as a tile is done:
-//   3D row halo   [P][nb1][NL][tpr]        the last NL rows of each row block
-//   3D plane halo [nb0][nb1][NL][32][tpr]  the last NL planes of each plane block
-//   2D row halo   [nb1][NL][tpr]
-// The corner lines a CTA needs (previous planes x previous rows) come from
-// the diagonal CTA's row halo.  Progress counters (sweeps completed) are
-// published every g.pub sweeps after a fence.
+// Shared memory:
+//   PR  [NL+W][32][kRPS] plane ring (3D): plane slot w+NL holds warp w's
+//       values, row t at diagonal column l+t; slots < NL are the previous
+//       plane block's last planes (virtual planes, loaded by the halo warp)
+//   VR  [NL+W][NL][kRV] virtual rows (3D): the NL rows above the CTA for
+//       every plane slot (from the row halo of the CTA above, or for the
+//       virtual planes from the diagonal CTA)
+//   VR  [W][NL][kRV] (1D/2D): the NL rows above warp w (warp w-1's last
+//       lanes; for warp 0 the CTA above, loaded by the halo warp)
+//   XS  [W][32][kPFX+1] float4 input staging (compress) / decoder tables
+// Global halos (written by the lanes computing the boundary lines):
+//   3D row halo   [P][nb1][NL][npad]          unshifted columns
+//   3D plane halo [nb0][nb1][NL][32][npad+32] diagonal columns l+t
+//   2D row halo   [nb1][NL][npad]
 
 template <int ND, int NL>
 struct Cfg {
-    static constexpr int RD = kPFH + (ND == 3 ? 2 * NL : NL) + 1;  // ring depth
-    static constexpr int MAXE = (ND == 3) ? (NL * (32 + NL) + NL * kMaxWaveWarps + 31) / 32 : 1;  // entries per halo lane
+    static constexpr int MAXE = (ND == 3) ? (NL * 32 + NL * kMaxWaveWarps + NL * NL + 31) / 32 : 1;
 };
 
 template <int ND, int NL, bool DEC>
-__global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32) k_wave(WaveArgs A) {
+__global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __grid_constant__ WaveArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     using C = Cfg<ND, NL>;
-    constexpr int RD = C::RD;
     const WaveGeom& g = A.g;
     const int W = g.W;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -288,29 +233,87 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32) k_wave(WaveArgs A) {
         return;
     }
 
-    const int NP = (ND == 3) ? (W + NL) : 1;
-    const int NR = (ND == 3) ? (32 + NL) : (32 * W + NL);
-    const int slotsz = NP * NR;  // float4 entries per ring slot
-    float4* ring = reinterpret_cast<float4*>(smem);
-    float4* xstage = ring + RD * slotsz;                     // [W][kPFX][32] (compress)
-    uint32_t* s_lut = reinterpret_cast<uint32_t*>(xstage);   // (decompress)
+    // shared-memory carve-up
+    const int npl = (ND == 3) ? (NL + W) : 0;         // plane ring slots
+    const int nvl = (ND == 3) ? (NL + W) : W;         // virtual-row line groups
+    float* PR = reinterpret_cast<float*>(smem);                       // npl*32*kRPS
+    float* VR = PR + (size_t)npl * 32 * kRPS;                         // nvl*NL*kRV
+    float4* XS = reinterpret_cast<float4*>(VR + (size_t)nvl * NL * kRV);  // W*32*(kPFX+1)
+    uint32_t* s_lut = reinterpret_cast<uint32_t*>(XS);
     uint32_t* s_tab = s_lut + (1 << kLutBits);
 
-    const int tpr = g.ntiles * kTile;  // halo row length (floats)
-    const int r_last = g.nsweeps - 1;  // last compute sweep
-    const unsigned final_prog = (unsigned)(r_last + 1);
+    const int npad = g.ntiles * kTile;     // row halo line length
+    const int nshift = npad + 32;          // plane halo line length (diagonal)
+    const int nsweeps = g.nsweeps;
+    const unsigned final_prog = (unsigned)nsweeps;
     unsigned int* my_prog = A.prog + item;
-    QParams qp = load_qparams(A.st);
+    const QParams qp = load_qparams(A.st);
 
     if (is_halo) {
         // ================= halo warp =================
-        const int NE = (ND == 3) ? (NL * (32 + NL) + NL * W) : NL;
-        const int row_lag = (ND == 3) ? 33 : (32 * W + 1);
-        const int plane_lag = W + 1;
-        const int diag_lag = W + 33;
-        const unsigned* prog_row = nullptr;
-        const unsigned* prog_plane = nullptr;
-        const unsigned* prog_diag = nullptr;
+        // entry kinds: 0 virtual plane line (PR slot p < NL, row t)
+        //              1 virtual row of a real plane (VR slot w+NL, row q)
+        //              2 virtual row of a virtual plane (VR slot p, row q)
+        //              3 (1D/2D) virtual row of warp 0 (VR group 0, row q)
+        int e_kind[C::MAXE], e_uoff[C::MAXE], e_nblk[C::MAXE];
+        float* e_dst[C::MAXE];  // shared address of block 0 of the line
+        int e_dmask[C::MAXE];   // ring blocks - 1
+        const float* e_src[C::MAXE];
+        const int NE = (ND == 3) ? (NL * 32 + NL * W + NL * NL) : NL;
+#pragma unroll
+        for (int j = 0; j < C::MAXE; j++) {
+            const int e = lane + 32 * j;
+            e_kind[j] = -1;
+            e_uoff[j] = 0;
+            e_nblk[j] = 0;
+            e_dst[j] = nullptr;
+            e_dmask[j] = 0;
+            e_src[j] = nullptr;
+            if (e >= NE) continue;
+            if (ND == 3) {
+                if (e < NL * 32) {
+                    const int p = e / 32, t = e % 32;
+                    e_kind[j] = 0;
+                    e_uoff[j] = 0;
+                    e_nblk[j] = nshift / 4;
+                    e_dst[j] = PR + ((size_t)p * 32 + t) * kRPS;
+                    e_dmask[j] = kRP / 4 - 1;
+                    if (ib > 0)
+                        e_src[j] = A.halo_plane + ((((size_t)(ib - 1) * g.nb1 + jb) * NL + p) * 32 + t) * nshift;
+                } else if (e < NL * 32 + NL * W) {
+                    const int e2 = e - NL * 32, w = e2 / NL, q = e2 % NL;
+                    e_kind[j] = 1;
+                    e_uoff[j] = w;
+                    e_nblk[j] = npad / 4;
+                    e_dst[j] = VR + ((size_t)(w + NL) * NL + q) * kRV;
+                    e_dmask[j] = kRV / 4 - 1;
+                    const uint64_t plane = (uint64_t)ib * W + w;
+                    if (jb > 0 && plane < g.P)
+                        e_src[j] = A.halo_row + (((size_t)plane * g.nb1 + (jb - 1)) * NL + q) * npad;
+                } else {
+                    const int e3 = e - NL * 32 - NL * W, p = e3 / NL, q = e3 % NL;
+                    e_kind[j] = 2;
+                    e_uoff[j] = p - NL;
+                    e_nblk[j] = npad / 4;
+                    e_dst[j] = VR + ((size_t)p * NL + q) * kRV;
+                    e_dmask[j] = kRV / 4 - 1;
+                    if (ib > 0 && jb > 0) {
+                        const uint64_t plane = (uint64_t)(ib - 1) * W + W - NL + p;
+                        e_src[j] = A.halo_row + (((size_t)plane * g.nb1 + (jb - 1)) * NL + q) * npad;
+                    }
+                }
+            } else {
+                e_kind[j] = 3;
+                e_uoff[j] = 0;
+                e_nblk[j] = npad / 4;
+                e_dst[j] = VR + (size_t)e * kRV;
+                e_dmask[j] = kRV / 4 - 1;
+                if (jb > 0) e_src[j] = A.halo_row + ((size_t)(jb - 1) * NL + e) * npad;
+            }
+        }
+        const unsigned* prog_row = nullptr;    // CTA above (same planes)
+        const unsigned* prog_plane = nullptr;  // previous plane block
+        const unsigned* prog_diag = nullptr;   // previous plane block, row block above
         if (ND == 3) {
             if (jb > 0) prog_row = A.prog + ib * g.nb1 + jb - 1;
             if (ib > 0) prog_plane = A.prog + (ib - 1) * g.nb1 + jb;
@@ -318,98 +321,55 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32) k_wave(WaveArgs A) {
         } else if (jb > 0) {
             prog_row = A.prog + jb - 1;
         }
-        // per-lane entries: ring offset within a slot, skew, source of tile 0
-        int e_off[C::MAXE], e_skew[C::MAXE];
-        const float* e_src[C::MAXE];
-#pragma unroll
-        for (int j = 0; j < C::MAXE; j++) {
-            const int e = lane + 32 * j;
-            e_off[j] = -1;
-            e_skew[j] = 0;
-            e_src[j] = nullptr;
-            if (e >= NE) continue;
-            int wp, rs;
-            const float* src = nullptr;
-            if (ND == 3) {
-                if (e < NL * (32 + NL)) {
-                    const int p = e / (32 + NL);
-                    wp = p;
-                    rs = e % (32 + NL);
-                    if (ib > 0) {
-                        if (rs >= NL) {
-                            size_t off = ((((size_t)(ib - 1) * g.nb1 + jb) * NL + p) * 32 + (rs - NL)) * tpr;
-                            src = A.halo_plane + off;
-                        } else if (jb > 0) {
-                            uint64_t plane = (uint64_t)(ib - 1) * W + W - NL + p;
-                            size_t off = (((size_t)plane * g.nb1 + (jb - 1)) * NL + rs) * tpr;
-                            src = A.halo_row + off;
-                        }
-                    }
-                } else {
-                    const int e2 = e - NL * (32 + NL);
-                    const int w = e2 / NL, q = e2 % NL;
-                    wp = NL + w;
-                    rs = q;
-                    const uint64_t plane = (uint64_t)ib * W + w;
-                    if (jb > 0 && plane < g.P) {
-                        size_t off = (((size_t)plane * g.nb1 + (jb - 1)) * NL + q) * tpr;
-                        src = A.halo_row + off;
-                    }
-                }
-            } else {
-                wp = 0;
-                rs = e;
-                if (jb > 0) src = A.halo_row + ((size_t)(jb - 1) * NL + e) * tpr;
-            }
-            e_off[j] = wp * NR + rs;
-            e_skew[j] = (ND == 3) ? (wp - NL) + (rs - NL) : (rs - NL);
-            e_src[j] = src;
-        }
+        // sweeps after which a block needed from sweep u is complete at the producer
+        const int row_lag = (ND == 3) ? 9 : 9 * W;
+        const int plane_lag = W;
+        const int diag_lag = W + 9;
         bool timed_out = false;
         unsigned seen_row = 0, seen_plane = 0, seen_diag = 0;
-        const float* dummy = A.halo_row;  // a valid address for zero-fill copies
+        const float* dummy = A.halo_row;
 
-        // issue the cp.async loads of the virtual entries of sweep rp into
-        // their ring slot, after the producers have published enough progress
-        auto issue = [&](int rp) {
+        // load the blocks first needed in sweep u (u may be negative)
+        auto issue = [&](int u) {
             if (lane == 0 && !timed_out) {
                 if (prog_row) {
-                    unsigned need = min((unsigned)max(rp + row_lag, 0), final_prog);
+                    unsigned need = min((unsigned)max(u + row_lag, 0), final_prog);
                     if (!wait_progress(prog_row, need, seen_row, A.timeout_ns)) timed_out = true;
                 }
                 if (prog_plane && !timed_out) {
-                    unsigned need = min((unsigned)max(rp + plane_lag, 0), final_prog);
+                    unsigned need = min((unsigned)max(u + plane_lag, 0), final_prog);
                     if (!wait_progress(prog_plane, need, seen_plane, A.timeout_ns)) timed_out = true;
                 }
                 if (prog_diag && !timed_out) {
-                    unsigned need = min((unsigned)max(rp + diag_lag, 0), final_prog);
+                    unsigned need = min((unsigned)max(u + diag_lag, 0), final_prog);
                     if (!wait_progress(prog_diag, need, seen_diag, A.timeout_ns)) timed_out = true;
                 }
             }
             timed_out = __shfl_sync(0xffffffffu, timed_out ? 1 : 0, 0) != 0;
-            float4* slot = ring + posmod(rp, RD) * slotsz;
 #pragma unroll
             for (int j = 0; j < C::MAXE; j++) {
-                if (e_off[j] < 0) continue;
-                const int c = rp - e_skew[j];
-                const bool ok = e_src[j] && !timed_out && c >= 0 && c < g.ntiles;
-                cp_async16(slot + e_off[j], ok ? (const void*)(e_src[j] + (size_t)c * kTile) : (const void*)dummy,
-                           ok ? 16 : 0);
+                if (e_kind[j] < 0) continue;
+                const int b = u - e_uoff[j];
+                if (b < 0) continue;  // columns before the line start are never read
+                float* dst = e_dst[j] + (size_t)((b & e_dmask[j]) * 4);
+                const bool ok = e_src[j] && !timed_out && b >= 0 && b < e_nblk[j];
+                cp_async16(dst, ok ? (const void*)(e_src[j] + (size_t)b * 4) : (const void*)dummy, ok ? 16 : 0);
             }
-            cp_async_commit();
         };
-        const int min_sweep = (ND == 3) ? -2 * NL : -NL;
-        for (int rv = min_sweep; rv < kPFH; rv++) issue(rv);
+        // prologue: every block needed up to sweep kPFH
+        for (int u = -2 * NL - 1; u <= kPFH; u++) issue(u);
+        cp_async_commit();
         cp_async_wait<0>();
-        __syncthreads();  // prologue: virtual entries of sweeps < kPFH in place
+        __syncthreads();
 
-        for (int r = 0; r <= r_last; r++) {
+        for (int r = 0; r < nsweeps; r++) {
             if (r > 0 && r % g.pub == 0) {  // sweeps < r are complete: publish
                 fence_acq_rel_gpu();
                 __syncwarp();
                 if (lane == 0) st_release_u32(my_prog, (unsigned)r);
             }
-            issue(r + kPFH);
+            issue(r + kPFH + 1);
+            cp_async_commit();
             cp_async_wait<kPFH>();
             if (lane == 0 && timed_out) s_abort = 1;
             __syncthreads();
@@ -431,48 +391,62 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32) k_wave(WaveArgs A) {
 
     // ================= compute warps =================
     uint64_t plane, row;
-    int skew, wp_own, rs_own;
+    int sig;  // warp skew in steps
     if (ND == 3) {
         plane = (uint64_t)ib * W + warp;
         row = (uint64_t)jb * 32 + lane;
-        skew = warp + lane;
-        wp_own = warp + NL;
-        rs_own = lane + NL;
+        sig = 4 * warp;
     } else {
         plane = 0;
         row = (uint64_t)jb * 32 * W + warp * 32 + lane;
-        skew = warp * 32 + lane;
-        wp_own = 0;
-        rs_own = warp * 32 + lane + NL;
+        sig = 36 * warp;
     }
     const bool valid = (plane < g.P) && (row < g.M);
     const uint64_t rowid = plane * g.M + row;
     const uint64_t rowbase = rowid * g.N;
-    const int own_off = wp_own * NR + rs_own;
-    // halo outputs written by this lane (null when the line has no consumer)
-    float* hout_row = nullptr;
-    float* hout_plane = nullptr;
+    const int N = (int)g.N;
+    // per-lane output pointers (the parameter block is read once)
+    uint16_t* const codes_row = DEC ? nullptr : A.codes + rowbase;
+    float* const rec_row = (!DEC && A.recorded) ? A.recorded + rowbase : nullptr;
+    float* const out_row = DEC ? A.out + rowbase : nullptr;
+    const int col0 = -lane - sig;  // column at step 0
+
+    // halo outputs of this lane (null when the line has no consumer)
+    float* hout_row = nullptr;    // unshifted
+    float* hout_plane = nullptr;  // diagonal
+    float* vr_next = nullptr;     // 2D: this lane's line for the next warp's virtual rows
     if (valid) {
         if (ND == 3) {
             if (lane >= 32 - NL && jb + 1 < g.nb1)
-                hout_row = A.halo_row + (((size_t)plane * g.nb1 + jb) * NL + (lane - (32 - NL))) * tpr;
+                hout_row = A.halo_row + (((size_t)plane * g.nb1 + jb) * NL + (lane - (32 - NL))) * npad;
             if (warp >= W - NL && ib + 1 < g.nb0)
-                hout_plane = A.halo_plane +
-                             ((((size_t)ib * g.nb1 + jb) * NL + (warp - (W - NL))) * 32 + lane) * tpr;
+                hout_plane = A.halo_plane + ((((size_t)ib * g.nb1 + jb) * NL + (warp - (W - NL))) * 32 + lane) * nshift;
         } else {
-            if (warp == W - 1 && lane >= 32 - NL && jb + 1 < g.nb1)
-                hout_row = A.halo_row + ((size_t)jb * NL + (lane - (32 - NL))) * tpr;
+            if (lane >= 32 - NL) {
+                if (warp + 1 < W) vr_next = VR + ((size_t)(warp + 1) * NL + (lane - (32 - NL))) * kRV;
+                else if (jb + 1 < g.nb1) hout_row = A.halo_row + ((size_t)jb * NL + (lane - (32 - NL))) * npad;
+            }
         }
     }
+    // this lane's virtual-row lines (lanes t < NL): own plane and planes - a
+    const float* vr_own = (ND == 3) ? VR + (size_t)(warp + NL) * NL * kRV : VR + (size_t)warp * NL * kRV;
 
-    // tails: the last NL values of the previous tile of every series
-    float tail[NL + 1][NL + 1][NL];
+    // neighbour histories: index [e] = column l - e
+    float oV[NL + 1];                       // own line
+    float Rr[NL + 1][NL + 1];               // rows above, own plane
+    float Pp[NL + 1][NL + 1];               // planes below, own row (3D)
+    float Qq[NL + 1][NL + 1][NL + 1];       // planes below, rows above (3D)
 #pragma unroll
-    for (int a = 0; a <= NL; a++)
+    for (int e = 0; e <= NL; e++) {
+        oV[e] = 0.0f;
 #pragma unroll
-        for (int b = 0; b <= NL; b++)
+        for (int b = 0; b <= NL; b++) {
+            Rr[b][e] = 0.0f;
+            Pp[b][e] = 0.0f;
 #pragma unroll
-            for (int j = 0; j < NL; j++) tail[a][b][j] = 0.0f;
+            for (int c = 0; c <= NL; c++) Qq[b][c][e] = 0.0f;
+        }
+    }
 
     BitReader br;
     int T = 1, maxlen = 1;
@@ -493,142 +467,171 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32) k_wave(WaveArgs A) {
     }
     const uint16_t* g_sorted = reinterpret_cast<const uint16_t*>(A.dectab + 260);
 
-    float4* xs = xstage + warp * kPFX * 32 + lane;
+    float4* xs = XS + (size_t)(warp * 32 + lane) * (kPFX + 1);
     const float* xrow = A.x + rowbase;
-    auto x_prefetch = [&](int rp) {
+    auto x_prefetch = [&](int q) {  // the 4 columns of sweep q
         if constexpr (!DEC) {
-            const int c = rp - skew;
-            float4* dst = xs + (rp % kPFX) * 32;
-            const bool ok = valid && c >= 0 && c < g.ntiles;
-            if (g.aligned) {
-                const uint64_t col = (uint64_t)c * kTile;
-                cp_async16(dst, ok ? (const void*)(xrow + col) : (const void*)A.x, ok ? 16 : 0);
-            } else {
-                float* d = reinterpret_cast<float*>(dst);
+            float* d = reinterpret_cast<float*>(xs + (q & (kPFX - 1)));
 #pragma unroll
-                for (int k = 0; k < kTile; k++) {
-                    const uint64_t col = (uint64_t)c * kTile + k;
-                    const bool in = ok && col < g.N;
-                    cp_async4(d + k, in ? (const void*)(xrow + col) : (const void*)A.x, in ? 4 : 0);
-                }
+            for (int k = 0; k < kTile; k++) {
+                const int l = 4 * q + k + col0;
+                const bool in = valid && l >= 0 && l < N;
+                cp_async4(d + k, in ? (const void*)(xrow + l) : (const void*)A.x, in ? 4 : 0);
             }
             cp_async_commit();
         }
     };
     if constexpr (!DEC) {
-        for (int rp = 0; rp < kPFX - 1; rp++) x_prefetch(rp);
+        for (int q = 0; q < kPFX - 1; q++) x_prefetch(q);
     }
     __syncthreads();  // matches the halo warp's prologue barrier
 
-    for (int r = 0; r <= r_last; r++) {
+    for (int q = 0; q < nsweeps; q++) {
         if constexpr (!DEC) {
-            x_prefetch(r + kPFX - 1);
+            x_prefetch(q + kPFX - 1);
             cp_async_wait<kPFX - 1>();
         }
-        const int c = r - skew;
-        if (c >= 0 && c < g.ntiles) {
-            // neighbour series of this tile: tails + the ring entries written
-            // a + b sweeps ago by the lane at (plane - a, row - b)
-            float S[NL + 1][NL + 1][NL + kTile];
+        const int lq = 4 * q + col0;  // this lane's column at step 0 of the sweep
+        const int wl0 = 4 * q - sig;  // lane 0's column at step 0 (warp-uniform)
+        // a warp is idle in sweeps where none of its lanes has a column
+        if (wl0 + 3 >= 0 && wl0 - 31 < N) {
+            float4 pr[NL + 1];
+            if (ND == 3) {
+                const int blk = (q - warp) & (kRP / 4 - 1);
 #pragma unroll
-            for (int a = 0; a <= NL; a++)
-#pragma unroll
-                for (int b = 0; b <= NL; b++) {
-#pragma unroll
-                    for (int j = 0; j < NL; j++) S[a][b][j] = tail[a][b][j];
-                    if ((ND != 3 && a > 0) || (a == 0 && b == 0)) {
-#pragma unroll
-                        for (int k = 0; k < kTile; k++) S[a][b][NL + k] = 0.0f;
-                        continue;
-                    }
-                    const float4 v = ring[posmod(r - a - b, RD) * slotsz + own_off - a * NR - b];
-                    S[a][b][NL + 0] = v.x;
-                    S[a][b][NL + 1] = v.y;
-                    S[a][b][NL + 2] = v.z;
-                    S[a][b][NL + 3] = v.w;
-                }
-            // partial predictions: every term except the own-line ones,
-            // summed in the method's order (they precede the own-line terms)
-            float part[kTile];
-#pragma unroll
-            for (int k = 0; k < kTile; k++) part[k] = predict_partial<NL, ND>(S, k);
-            int code[kTile];
+                for (int a = 1; a <= NL; a++)
+                    pr[a] = *reinterpret_cast<const float4*>(PR + ((size_t)(warp + NL - a) * 32 + lane) * kRPS + blk * 4);
+            }
+            float xv[kTile] = {0.f, 0.f, 0.f, 0.f};
             if constexpr (!DEC) {
-                const float4 xv4 = xs[(r % kPFX) * 32];
-                const float xv[kTile] = {xv4.x, xv4.y, xv4.z, xv4.w};
-                float tr[kTile];
+                const float4 x4 = xs[q & (kPFX - 1)];
+                xv[0] = x4.x; xv[1] = x4.y; xv[2] = x4.z; xv[3] = x4.w;
+            }
+            float vout[kTile];
 #pragma unroll
-                for (int k = 0; k < kTile; k++) tr[k] = trunc_value(xv[k], qp.e_eb);
+            for (int k = 0; k < kTile; k++) {
+                const int l = lq + k;
+                const bool act = (l >= 0) && (l < N);
+                // ---- new neighbour values at column l (shuffles first: they
+                // read the values of the previous step)
+                float nR[NL + 1], nP[NL + 1], nQ[NL + 1][NL + 1];
+                nR[1] = __shfl_up_sync(0xffffffffu, oV[1], 1);
+                if (NL >= 2) nR[2] = __shfl_up_sync(0xffffffffu, Rr[1][0], 1);
+                if (ND == 3) {
 #pragma unroll
-                for (int k = 0; k < kTile; k++) {
-                    const float pred = predict_own<NL, ND>(part[k], S, k);
-                    float V;
-                    code[k] = quantize_tr(xv[k], pred, tr[k], qp, V);
-                    S[0][0][NL + k] = V;
+                    for (int a = 1; a <= NL; a++) {
+                        nP[a] = (k == 0) ? pr[a].x : (k == 1) ? pr[a].y : (k == 2) ? pr[a].z : pr[a].w;
+                        nQ[a][1] = __shfl_up_sync(0xffffffffu, Pp[a][0], 1);
+                        if (NL >= 2) nQ[a][2] = __shfl_up_sync(0xffffffffu, Qq[a][1][0], 1);
+                    }
                 }
-            } else {
-                float uv[kTile];
-                const uint64_t col0 = (uint64_t)c * kTile;
+                // lanes next to the top of the block read the rows above
+                if (ND >= 2 && lane < NL) {
+                    const int cl = l & (kRV - 1);
 #pragma unroll
-                for (int k = 0; k < kTile; k++) {
-                    code[k] = 0;
-                    uv[k] = 0.0f;
-                    if (valid && col0 + k < g.N) {
-                        int sym = decode_symbol(br, s_lut, T, s_tab, g_sorted, maxlen, bad);
-                        code[k] = sym;
-                        if (sym == 0) {
-                            uint32_t se = br.take(9);
-                            int t = trunc_bits(se << 23, qp.e_eb);
-                            uint32_t mb = br.take(t);
-                            uv[k] = __uint_as_float((se << 23) | (t ? (mb << (23 - t)) : 0u));
+                    for (int b = 1; b <= NL; b++) {
+                        if (lane < b) {
+                            const int vr = NL + lane - b;
+                            nR[b] = vr_own[vr * kRV + cl];
+                            if (ND == 3) {
+#pragma unroll
+                                for (int a = 1; a <= NL; a++)
+                                    nQ[a][b] = VR[((size_t)(warp + NL - a) * NL + vr) * kRV + cl];
+                            }
                         }
                     }
                 }
+                // shift histories, insert (zeros outside the row)
 #pragma unroll
-                for (int k = 0; k < kTile; k++) {
-                    const float pred = predict_own<NL, ND>(part[k], S, k);
-                    S[0][0][NL + k] = code[k] ? dequantize(code[k], pred, qp) : uv[k];
+                for (int b = 1; b <= NL; b++) {
+#pragma unroll
+                    for (int e = NL; e >= 1; e--) Rr[b][e] = Rr[b][e - 1];
+                    Rr[b][0] = act ? nR[b] : 0.0f;
+                }
+                if (ND == 3) {
+#pragma unroll
+                    for (int a = 1; a <= NL; a++) {
+#pragma unroll
+                        for (int e = NL; e >= 1; e--) Pp[a][e] = Pp[a][e - 1];
+                        Pp[a][0] = act ? nP[a] : 0.0f;
+#pragma unroll
+                        for (int b = 1; b <= NL; b++) {
+#pragma unroll
+                            for (int e = NL; e >= 1; e--) Qq[a][b][e] = Qq[a][b][e - 1];
+                            Qq[a][b][0] = act ? nQ[a][b] : 0.0f;
+                        }
+                    }
+                }
+                // ---- prediction: terms in descending lexicographic (a, b, e)
+                float pred = 0.0f;
+                bool first = true;
+                constexpr int AA = (ND == 3) ? NL : 0;
+                constexpr int BB = (ND >= 2) ? NL : 0;
+#pragma unroll
+                for (int a = AA; a >= 0; a--) {
+#pragma unroll
+                    for (int b = BB; b >= 0; b--) {
+#pragma unroll
+                        for (int e = NL; e >= 0; e--) {
+                            if (a == 0 && b == 0 && e == 0) continue;
+                            const float v = (a > 0 && b > 0) ? Qq[a][b][e]
+                                          : (a > 0)          ? Pp[a][e]
+                                          : (b > 0)          ? Rr[b][e]
+                                                             : oV[e];
+                            const int c = term_coef(NL, a, b, e);
+                            if (NL == 1) {
+                                if (first) pred = (c > 0) ? v : -v;
+                                else pred = (c > 0) ? __fadd_rn(pred, v) : __fsub_rn(pred, v);
+                            } else {
+                                const float prod = __fmul_rn((float)c, v);
+                                pred = first ? prod : __fadd_rn(pred, prod);
+                            }
+                            first = false;
+                        }
+                    }
+                }
+                // ---- quantize (compress) / decode + dequantize (decompress)
+                float V;
+                int code = 0;
+                if constexpr (!DEC) {
+                    const float tr = trunc_value(xv[k], qp.e_eb);
+                    code = quantize_tr(xv[k], pred, tr, qp, V);
+                } else {
+                    float uv = 0.0f;
+                    if (valid && act) {
+                        code = decode_symbol(br, s_lut, T, s_tab, g_sorted, maxlen, bad);
+                        if (code == 0) {
+                            const uint32_t se = br.take(9);
+                            const int t = trunc_bits(se << 23, qp.e_eb);
+                            const uint32_t mb = br.take(t);
+                            uv = __uint_as_float((se << 23) | (t ? (mb << (23 - t)) : 0u));
+                        }
+                    }
+                    V = code ? dequantize(code, pred, qp) : uv;
+                }
+                V = act ? V : 0.0f;
+#pragma unroll
+                for (int e = NL; e >= 2; e--) oV[e] = oV[e - 1];
+                oV[1] = V;
+                vout[k] = V;
+                if (valid && act) {
+                    if constexpr (!DEC) {
+                        codes_row[l] = (uint16_t)code;
+                        if (rec_row) rec_row[l] = V;
+                    } else {
+                        out_row[l] = V;
+                    }
+                    if (hout_row) hout_row[l] = V;
+                    if (ND != 3 && vr_next) vr_next[l & (kRV - 1)] = V;
                 }
             }
-            const float4 vout = make_float4(S[0][0][NL], S[0][0][NL + 1], S[0][0][NL + 2], S[0][0][NL + 3]);
-            ring[(r % RD) * slotsz + own_off] = vout;
-            if (hout_row) *reinterpret_cast<float4*>(hout_row + (size_t)c * kTile) = vout;
-            if (ND == 3 && hout_plane) *reinterpret_cast<float4*>(hout_plane + (size_t)c * kTile) = vout;
-#pragma unroll
-            for (int a = 0; a <= NL; a++)
-#pragma unroll
-                for (int b = 0; b <= NL; b++)
-#pragma unroll
-                    for (int j = 0; j < NL; j++) tail[a][b][j] = S[a][b][kTile + j];
-            if (valid) {
-                const uint64_t col = (uint64_t)c * kTile;
-                const bool full = g.aligned && (col + kTile <= g.N);
-                if constexpr (!DEC) {
-                    if (full) {
-                        uint2 pk;
-                        pk.x = (uint32_t)code[0] | ((uint32_t)code[1] << 16);
-                        pk.y = (uint32_t)code[2] | ((uint32_t)code[3] << 16);
-                        *reinterpret_cast<uint2*>(A.codes + rowbase + col) = pk;
-                        if (A.recorded) *reinterpret_cast<float4*>(A.recorded + rowbase + col) = vout;
-                    } else {
-                        const float vv[kTile] = {vout.x, vout.y, vout.z, vout.w};
-#pragma unroll
-                        for (int k = 0; k < kTile; k++)
-                            if (col + k < g.N) {
-                                A.codes[rowbase + col + k] = (uint16_t)code[k];
-                                if (A.recorded) A.recorded[rowbase + col + k] = vv[k];
-                            }
-                    }
-                } else {
-                    if (full) {
-                        *reinterpret_cast<float4*>(A.out + rowbase + col) = vout;
-                    } else {
-                        const float vv[kTile] = {vout.x, vout.y, vout.z, vout.w};
-#pragma unroll
-                        for (int k = 0; k < kTile; k++)
-                            if (col + k < g.N) A.out[rowbase + col + k] = vv[k];
-                    }
-                }
+            // this sweep's 4 values, diagonal block q - warp: plane ring and plane halo
+            if (ND == 3) {
+                const int blk = q - warp;
+                const float4 v4 = make_float4(vout[0], vout[1], vout[2], vout[3]);
+                *reinterpret_cast<float4*>(PR + ((size_t)(warp + NL) * 32 + lane) * kRPS + (blk & (kRP / 4 - 1)) * 4) = v4;
+                if (hout_plane && blk >= 0 && blk < nshift / 4)
+                    *reinterpret_cast<float4*>(hout_plane + (size_t)blk * 4) = v4;
             }
         }
         __syncthreads();
@@ -645,15 +648,12 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32) k_wave(WaveArgs A) {
 
 size_t wave_smem_bytes(const WaveGeom& g, int layers, bool decompress) {
     const int NL = layers, W = g.W;
-    int RD, NP, NR;
-    if (g.ndim == 3) {
-        RD = kPFH + 2 * NL + 1; NP = W + NL; NR = 32 + NL;
-    } else {
-        RD = kPFH + NL + 1; NP = 1; NR = 32 * W + NL;
-    }
-    size_t b = (size_t)RD * NP * NR * 16;
+    const int npl = (g.ndim == 3) ? (NL + W) : 0;
+    const int nvl = (g.ndim == 3) ? (NL + W) : W;
+    size_t b = (size_t)npl * 32 * kRPS * 4 + (size_t)nvl * NL * kRV * 4;
+    b = (b + 15) & ~(size_t)15;
     if (decompress) b += (size_t)(1 << kLutBits) * 4 + 260 * 4;
-    else b += (size_t)W * kPFX * 32 * 16;
+    else b += (size_t)W * 32 * (kPFX + 1) * 16;
     return b;
 }
 

@@ -146,7 +146,7 @@ WaveGeom make_geom(const szgb_ctx* c, const CallParams& cp, int layers) {
         g.W = W;
         g.nb0 = (int)((cp.d0 + W - 1) / W);
         g.nb1 = (int)((cp.d1 + 31) / 32);
-        g.nsweeps = g.ntiles + W + 30;  // last sweep: tile ntiles-1 of warp W-1, lane 31
+        g.nsweeps = (int)((cp.d2 - 1 + 31 + 4 * (W - 1)) / 4) + 1;  // last step: column N-1 of warp W-1, lane 31
     } else {
         g.ndim = cp.ndim;
         g.P = 1;
@@ -158,7 +158,7 @@ WaveGeom make_geom(const szgb_ctx* c, const CallParams& cp, int layers) {
         g.W = W;
         g.nb0 = 1;
         g.nb1 = (int)((g.M + 32ull * W - 1) / (32ull * W));
-        g.nsweeps = g.ntiles + 32 * W - 1;  // last sweep: tile ntiles-1 of row 32W-1
+        g.nsweeps = (int)((cp.d2 - 1 + 31 + 36 * (W - 1)) / 4) + 1;  // last step: column N-1 of warp W-1, lane 31
     }
     g.num_ctas = g.nb0 * g.nb1;
     g.pub = c->pub;
@@ -169,7 +169,7 @@ void halo_sizes(const WaveGeom& g, int layers, size_t* row_floats, size_t* plane
     size_t tpr = (size_t)g.ntiles * kTile;
     if (g.ndim == 3) {
         *row_floats = (size_t)g.P * g.nb1 * layers * tpr;
-        *plane_floats = (size_t)g.nb0 * g.nb1 * layers * 32 * tpr;
+        *plane_floats = (size_t)g.nb0 * g.nb1 * layers * 32 * (tpr + 32);
     } else {
         *row_floats = (size_t)g.nb1 * layers * tpr;
         *plane_floats = 4;

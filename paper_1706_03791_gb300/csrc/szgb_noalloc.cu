@@ -110,7 +110,7 @@ extern "C" int szgb_decompress_noalloc(const uint8_t* in_dev, size_t in_len, flo
         g.W = W;
         g.nb0 = (int)((d0 + W - 1) / W);
         g.nb1 = (int)((d1 + 31) / 32);
-        g.nsweeps = g.ntiles + W + 30;  // last sweep: tile ntiles-1 of warp W-1, lane 31
+        g.nsweeps = (int)((d2 - 1 + 31 + 4 * (W - 1)) / 4) + 1;  // last step: column N-1 of warp W-1, lane 31
     } else {
         g.ndim = ndim;
         g.P = 1;
@@ -121,13 +121,13 @@ extern "C" int szgb_decompress_noalloc(const uint8_t* in_dev, size_t in_len, flo
         g.W = W;
         g.nb0 = 1;
         g.nb1 = (int)((g.M + 32ull * W - 1) / (32ull * W));
-        g.nsweeps = g.ntiles + 32 * W - 1;  // last sweep: tile ntiles-1 of row 32W-1
+        g.nsweeps = (int)((d2 - 1 + 31 + 36 * (W - 1)) / 4) + 1;  // last step: column N-1 of warp W-1, lane 31
     }
     g.num_ctas = g.nb0 * g.nb1;
     g.pub = 8;
     const size_t tpr = (size_t)g.ntiles * kTile;
     const size_t hrow = (ndim == 3) ? (size_t)g.P * g.nb1 * layers * tpr : (size_t)g.nb1 * layers * tpr;
-    const size_t hplane = (ndim == 3) ? (size_t)g.nb0 * g.nb1 * layers * 32 * tpr : 4;
+    const size_t hplane = (ndim == 3) ? (size_t)g.nb0 * g.nb1 * layers * 32 * (tpr + 32) : 4;
 
     // carve the scratch
     size_t off = 0;
