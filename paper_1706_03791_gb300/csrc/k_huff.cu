@@ -15,8 +15,10 @@ namespace szgb {
 // ---------------------------------------------------------------------------
 // histogram of the codes over 2^m bins (warp-aggregated increments)
 
-__global__ void __launch_bounds__(512) k_hist(const uint16_t* __restrict__ codes, uint64_t n,
-                                              uint32_t* hist, const DevState* st) {
+// codes are stored row by row with a row pitch of `pitch` entries (>= rowlen)
+__global__ void __launch_bounds__(512) k_hist(const uint16_t* __restrict__ codes, uint64_t rows,
+                                              uint64_t rowlen, uint64_t pitch, uint32_t* hist,
+                                              const DevState* st) {
     extern __shared__ uint32_t sh[];
     if (st->err) return;
     const int m = st->m;
@@ -26,17 +28,20 @@ __global__ void __launch_bounds__(512) k_hist(const uint16_t* __restrict__ codes
         for (int i = threadIdx.x; i < nb; i += blockDim.x) sh[i] = 0;
     __syncthreads();
     uint32_t* H = use_smem ? sh : hist;
-    const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x; base < n; base += nthr) {
-        uint64_t i = base + threadIdx.x;
-        bool v = i < n;
-        unsigned active = __ballot_sync(0xffffffffu, v);
-        if (!v) continue;
-        uint32_t c = __ldcs(codes + i);
-        if (c >= (uint32_t)nb) c = 0;  // codes are < 2^m; never index past the bins
-        unsigned peers = __match_any_sync(active, c);
-        int leader = __ffs(peers) - 1;
-        if ((int)(threadIdx.x & 31) == leader) atomicAdd(&H[c], (uint32_t)__popc(peers));
+    const int lane = threadIdx.x & 31;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t r = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; r < rows; r += nw) {
+        const uint16_t* row = codes + r * pitch;
+        for (uint64_t l0 = 0; l0 < rowlen; l0 += 32) {
+            const uint64_t l = l0 + lane;
+            const bool v = l < rowlen;
+            const unsigned active = __ballot_sync(0xffffffffu, v);
+            if (!v) continue;
+            uint32_t c = __ldcs(row + l);
+            if (c >= (uint32_t)nb) c = 0;  // codes are < 2^m; never index past the bins
+            const unsigned peers = __match_any_sync(active, c);
+            if (lane == __ffs(peers) - 1) atomicAdd(&H[c], (uint32_t)__popc(peers));
+        }
     }
     if (use_smem) {
         __syncthreads();
@@ -45,14 +50,16 @@ __global__ void __launch_bounds__(512) k_hist(const uint16_t* __restrict__ codes
     }
 }
 
-int launch_histogram(const uint16_t* codes, uint64_t n, uint32_t* hist, DevState* st, cudaStream_t s) {
+int launch_histogram(const uint16_t* codes, uint64_t rows, uint64_t rowlen, uint64_t pitch, uint32_t* hist,
+                     DevState* st, cudaStream_t s) {
+    const uint64_t n = rows * rowlen;
     int blocks = (int)((n + 4095) / 4096);
     if (blocks > 4 * 152) blocks = 4 * 152;
     if (blocks < 1) blocks = 1;
     size_t smem = (size_t)(1 << 13) * 4;
     if (cudaFuncSetAttribute(k_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return SZGB_ECUDA;
-    k_hist<<<blocks, 512, smem, s>>>(codes, n, hist, st);
+    k_hist<<<blocks, 512, smem, s>>>(codes, rows, rowlen, pitch, hist, st);
     return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
 }
 
@@ -244,7 +251,7 @@ int launch_codebook(const uint32_t* hist, DevState* st, uint8_t* len, uint64_t* 
 // ---------------------------------------------------------------------------
 // per-row bit counts: Huffman code bits plus 9 + t record bits after code 0
 
-__global__ void __launch_bounds__(256) k_rowbits(const uint16_t* __restrict__ codes,
+__global__ void __launch_bounds__(256) k_rowbits(const uint16_t* __restrict__ codes, uint64_t pitch,
                                                  const float* __restrict__ x, uint64_t rows,
                                                  uint64_t rowlen, const uint8_t* __restrict__ len,
                                                  uint32_t* rowbytes, DevState* st) {
@@ -256,9 +263,10 @@ __global__ void __launch_bounds__(256) k_rowbits(const uint16_t* __restrict__ co
     unsigned long long kcount = 0;
     for (uint64_t r = wglob; r < rows; r += nw) {
         const uint64_t base = r * rowlen;
+        const uint16_t* crow = codes + r * pitch;
         uint64_t bits = 0;
         for (uint64_t l = lane; l < rowlen; l += 32) {
-            uint32_t c = codes[base + l];
+            uint32_t c = crow[l];
             bits += len[c];
             if (c == 0) {
                 bits += 9 + trunc_bits(__float_as_uint(x[base + l]), e_eb);
@@ -276,13 +284,13 @@ __global__ void __launch_bounds__(256) k_rowbits(const uint16_t* __restrict__ co
     if (lane == 0 && kcount) atomicAdd(&st->K, kcount);
 }
 
-int launch_rowbits(const uint16_t* codes, const float* x, uint64_t rows, uint64_t rowlen,
+int launch_rowbits(const uint16_t* codes, uint64_t pitch, const float* x, uint64_t rows, uint64_t rowlen,
                    const uint8_t* len, uint32_t* rowbytes, DevState* st, cudaStream_t s) {
     uint64_t warps = rows;
     uint64_t blocks = (warps * 32 + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    k_rowbits<<<(int)blocks, 256, 0, s>>>(codes, x, rows, rowlen, len, rowbytes, st);
+    k_rowbits<<<(int)blocks, 256, 0, s>>>(codes, pitch, x, rows, rowlen, len, rowbytes, st);
     return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
 }
 
@@ -459,7 +467,7 @@ __device__ __forceinline__ void store_word_bytes(uint8_t* plb, uint64_t gw, uint
     }
 }
 
-__global__ void __launch_bounds__(kEncWarps * 32) k_encode(const uint16_t* __restrict__ codes,
+__global__ void __launch_bounds__(kEncWarps * 32) k_encode(const uint16_t* __restrict__ codes, uint64_t pitch,
                                                           const float* __restrict__ x, uint64_t rows,
                                                           uint64_t rowlen, const uint8_t* __restrict__ len,
                                                           const uint64_t* __restrict__ cw,
@@ -482,10 +490,11 @@ __global__ void __launch_bounds__(kEncWarps * 32) k_encode(const uint16_t* __res
         for (int i = lane; i < kEncBufWords; i += 32) buf[i] = 0;
         __syncwarp();
         const uint64_t base = r * rowlen;
+        const uint16_t* crow = codes + r * pitch;
         for (uint64_t l0 = 0; l0 < rowlen; l0 += 32) {
             uint64_t l = l0 + lane;
             bool v = l < rowlen;
-            uint32_t c = v ? codes[base + l] : 0u;
+            uint32_t c = v ? crow[l] : 0u;
             int L = v ? len[c] : 0;
             uint64_t code = v ? cw[c] : 0;
             int nrec = 0;
@@ -543,12 +552,12 @@ int launch_write_meta(const CallParams& cp, uint64_t rows, const uint8_t* len, c
     return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
 }
 
-int launch_encode(const uint16_t* codes, const float* x, uint64_t rows, uint64_t rowlen, const uint8_t* len,
+int launch_encode(const uint16_t* codes, uint64_t pitch, const float* x, uint64_t rows, uint64_t rowlen, const uint8_t* len,
                   const uint64_t* cw, const uint64_t* rowoff, uint8_t* out, DevState* st, cudaStream_t s) {
     uint64_t blocks = (rows + kEncWarps - 1) / kEncWarps;
     if (blocks > 152 * 32) blocks = 152 * 32;
     if (blocks < 1) blocks = 1;
-    k_encode<<<(int)blocks, kEncWarps * 32, 0, s>>>(codes, x, rows, rowlen, len, cw, rowoff, out, st);
+    k_encode<<<(int)blocks, kEncWarps * 32, 0, s>>>(codes, pitch, x, rows, rowlen, len, cw, rowoff, out, st);
     return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
 }
 

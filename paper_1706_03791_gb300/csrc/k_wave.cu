@@ -23,23 +23,40 @@
 // Only the lane's own left neighbour and the shuffled upper neighbour are on
 // the critical path; the descending summation order puts them last.
 //
+// Inputs and outputs are staged through shared memory: a warp's 32 rows are
+// cut into 32 x 32 tiles, which the extra warp below loads (x) and stores
+// (codes, or decompressed values) with coalesced accesses; a lane reads its x
+// and writes its result at the same tile position, bank-conflict-free.
+//
 // CTA boundaries go through global "halo" buffers written by the lanes that
 // compute the boundary lines; an extra warp per CTA publishes a progress
 // counter every few sweeps (fence + st.release) and prefetches the
 // neighbouring CTAs' halos into the rings with cp.async after bounded
 // acquire-waits.  CTAs take work items from a ticket counter in dependency
 // order, so a CTA only waits for CTAs that are already resident.
+#include <cuda.h>
+
+#include <mutex>
+
 #include "szgb_internal.cuh"
 
 namespace szgb {
 
-constexpr int kPFX = 8;   // x prefetch depth (sweeps), power of two
-constexpr int kPFH = 3;   // halo prefetch depth (sweeps)
+constexpr int kPFH = 3;   // halo / input prefetch depth (sweeps)
+constexpr int kTW = 32;   // staging tile: 32 rows x kTW columns
+constexpr int kTE = 32 * kTW;  // elements per staging tile
+constexpr int kTS = 3;    // staging ring slots per warp
 constexpr int kRP = 32;   // plane ring: floats per row (8 blocks of 4 columns)
 constexpr int kRPS = 36;  // plane ring row stride (9 float4: conflict-free)
 constexpr int kRV = 64;   // virtual-row ring: floats per line
 
 struct WaveArgs {
+    // TMA descriptors of the 32 x 32 staging tiles: x (compress) and the
+    // output (codes when compressing, values when decompressing)
+    CUtensorMap tm_x;
+    CUtensorMap tm_out;
+    int tma_x, tma_out;
+    uint64_t opitch;  // output row pitch (elements)
     WaveGeom g;
     // compress
     const float* x;
@@ -198,7 +215,11 @@ __device__ __forceinline__ int decode_symbol(BitReader& br, const uint32_t* s_lu
 //       virtual planes from the diagonal CTA)
 //   VR  [W][NL][kRV] (1D/2D): the NL rows above warp w (warp w-1's last
 //       lanes; for warp 0 the CTA above, loaded by the halo warp)
-//   XS  [W][32][kPFX+1] float4 input staging (compress) / decoder tables
+//   XR  [W][kTS][32][kTW] f32 staging ring of x (compress)
+//   OR  [W][kTS][32][kTW] staging ring of the outputs: u16 codes (compress)
+//       or f32 values (decompress)
+//   MB  [W][kTS] mbarriers of the TMA loads into XR
+//   decoder tables (decompress)
 // Global halos (written by the lanes computing the boundary lines):
 //   3D row halo   [P][nb1][NL][npad]          unshifted columns
 //   3D plane halo [nb0][nb1][NL][32][npad+32] diagonal columns l+t
@@ -209,10 +230,21 @@ struct Cfg {
     static constexpr int MAXE = (ND == 3) ? (NL * 32 + NL * kMaxWaveWarps + NL * NL + 31) / 32 : 1;
 };
 
+// output element: quantization code (compress) or decompressed value
+template <bool DEC>
+struct OutElem {
+    using T = uint16_t;
+};
+template <>
+struct OutElem<true> {
+    using T = float;
+};
+
 template <int ND, int NL, bool DEC>
 __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __grid_constant__ WaveArgs A) {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     using C = Cfg<ND, NL>;
+    using OT = typename OutElem<DEC>::T;
     const WaveGeom& g = A.g;
     const int W = g.W;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -220,9 +252,27 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
     __shared__ unsigned int s_ticket;
     __shared__ int s_abort;
 
+    // shared-memory carve-up from a 128-byte boundary (TMA destinations)
+    unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+    const int npl = (ND == 3) ? (NL + W) : 0;         // plane ring slots
+    const int nvl = (ND == 3) ? (NL + W) : W;         // virtual-row line groups
+    float* PR = reinterpret_cast<float*>(smem);                          // npl*32*kRPS
+    float* VR = PR + (size_t)npl * 32 * kRPS;                            // nvl*NL*kRV
+    float* XR = VR + (size_t)nvl * NL * kRV;                             // W*kTS*kTE (compress)
+    OT* OR = reinterpret_cast<OT*>(XR + (DEC ? 0 : (size_t)W * kTS * kTE));  // W*kTS*kTE
+    uint64_t* MB = reinterpret_cast<uint64_t*>(OR + (size_t)W * kTS * kTE);  // W*kTS
+    uint32_t* s_lut = reinterpret_cast<uint32_t*>(MB + W * kTS);
+    uint32_t* s_tab = s_lut + (1 << kLutBits);
+    const bool tma_x = !DEC && A.tma_x;
+    const bool tma_o = A.tma_out != 0;
+
     if (threadIdx.x == 0) {
         s_ticket = atomicAdd(&A.st->ticket, 1u);
         s_abort = 0;
+        if (tma_x) {
+            for (int i = 0; i < W * kTS; i++) mbar_init(MB + i, 1);
+            fence_mbar_init();
+        }
     }
     __syncthreads();
     const int item = (int)s_ticket;
@@ -233,21 +283,13 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
         return;
     }
 
-    // shared-memory carve-up
-    const int npl = (ND == 3) ? (NL + W) : 0;         // plane ring slots
-    const int nvl = (ND == 3) ? (NL + W) : W;         // virtual-row line groups
-    float* PR = reinterpret_cast<float*>(smem);                       // npl*32*kRPS
-    float* VR = PR + (size_t)npl * 32 * kRPS;                         // nvl*NL*kRV
-    float4* XS = reinterpret_cast<float4*>(VR + (size_t)nvl * NL * kRV);  // W*32*(kPFX+1)
-    uint32_t* s_lut = reinterpret_cast<uint32_t*>(XS);
-    uint32_t* s_tab = s_lut + (1 << kLutBits);
-
     const int npad = g.ntiles * kTile;     // row halo line length
     const int nshift = npad + 32;          // plane halo line length (diagonal)
     const int nsweeps = g.nsweeps;
     const unsigned final_prog = (unsigned)nsweeps;
     unsigned int* my_prog = A.prog + item;
     const QParams qp = load_qparams(A.st);
+    const int N = (int)g.N;
 
     if (is_halo) {
         // ================= halo warp =================
@@ -329,6 +371,102 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
         unsigned seen_row = 0, seen_plane = 0, seen_diag = 0;
         const float* dummy = A.halo_row;
 
+        // staging tiles of compute warp w: first row, valid rows, skew in
+        // sweeps, and TMA coordinates (row, plane)
+        auto tile_row0 = [&](int w) -> uint64_t {
+            return (ND == 3) ? ((uint64_t)ib * W + w) * g.M + (uint64_t)jb * 32
+                             : (uint64_t)jb * 32 * W + (uint64_t)w * 32;
+        };
+        auto tile_rows = [&](int w) -> int {
+            if (ND == 3) {
+                if ((uint64_t)ib * W + w >= g.P) return 0;
+                return (int)min((uint64_t)32, g.M - (uint64_t)jb * 32);
+            }
+            const uint64_t r0 = (uint64_t)jb * 32 * W + (uint64_t)w * 32;
+            return r0 >= g.M ? 0 : (int)min((uint64_t)32, g.M - r0);
+        };
+        unsigned wv_mask = 0;  // warps with valid rows
+        for (int w = 0; w < W; w++)
+            if (tile_rows(w) > 0) wv_mask |= 1u << w;
+        auto tile_s4 = [&](int w) { return (ND == 3) ? w : 9 * w; };
+        auto tma_row = [&](int w) { return (ND == 3) ? jb * 32 : (jb * W + w) * 32; };
+        auto tma_plane = [&](int w) { return (ND == 3) ? ib * W + w : 0; };
+        // Tile kt of warp w is read from sweep 8 kt + s4(w) on and, when
+        // full, complete after sweep 8 kt + 15 + s4(w).  s4(w) = w (mod 8)
+        // in both topologies, so for a given sweep only warp (sweep mod 8)
+        // can start or finish a tile.
+        // x tile first read in sweep u: issued kPFH + 1 sweeps ahead
+        auto issue_x = [&](int u) {
+            if constexpr (!DEC) {
+                if (u < 0) return;
+                const int w = u & 7;
+                if (!((wv_mask >> w) & 1u)) return;
+                const int d = u - tile_s4(w);
+                if (d < 0) return;
+                const int kt = d >> 3, c0 = kt * kTW;
+                if (c0 >= N) return;
+                float* slot = XR + ((size_t)w * kTS + kt % kTS) * kTE;
+                if (tma_x) {
+                    if (lane == 0) {
+                        uint64_t* bar = MB + w * kTS + kt % kTS;
+                        mbar_arrive_expect_tx(bar, kTE * 4);
+                        tma_load_3d(slot, &A.tm_x, c0, tma_row(w), tma_plane(w), bar);
+                    }
+                } else {
+                    const int nv = tile_rows(w);
+                    const float* xr = A.x + tile_row0(w) * g.N;
+                    const int col = c0 + lane;
+                    for (int t = 0; t < 32; t++) {
+                        const bool ok = t < nv && col < N;
+                        cp_async4(slot + t * kTW + lane,
+                                  ok ? (const void*)(xr + (uint64_t)t * g.N + col) : (const void*)A.x, ok ? 4 : 0);
+                    }
+                }
+            }
+        };
+        // store output tile kt of warp w
+        auto store_tile = [&](int w, int kt) {
+            const int c0 = kt * kTW;
+            const OT* slot = OR + ((size_t)w * kTS + kt % kTS) * kTE;
+            if (tma_o) {
+                if (lane == 0) tma_store_3d(&A.tm_out, c0, tma_row(w), tma_plane(w), slot);
+            } else {
+                const int nv = tile_rows(w);
+                const uint64_t base = tile_row0(w) * A.opitch + (uint64_t)c0;
+                const bool in = c0 + lane < N;
+                for (int t0 = 0; t0 < nv; t0 += 8) {
+                    OT v[8];
+#pragma unroll
+                    for (int i = 0; i < 8; i++) v[i] = slot[((t0 + i) & 31) * kTW + lane];
+#pragma unroll
+                    for (int i = 0; i < 8; i++) {
+                        if (!in || t0 + i >= nv) continue;
+                        const uint64_t idx = base + (uint64_t)(t0 + i) * A.opitch + lane;
+                        if constexpr (DEC) A.out[idx] = v[i];
+                        else A.codes[idx] = v[i];
+                    }
+                }
+            }
+        };
+        const int nfull = N / kTW;  // full tiles per row
+        // in iteration r (sweeps < r complete): the full tile completed in sweep r - 1
+        auto flush = [&](int r) {
+            const int v = r - 16;
+            if (v >= 0) {
+                const int w = v & 7;
+                if ((wv_mask >> w) & 1u) {
+                    const int d = v - tile_s4(w);
+                    if (d >= 0 && (d >> 3) < nfull) store_tile(w, d >> 3);
+                }
+            }
+            if (lane == 0) bulk_commit();
+        };
+        // full tiles of warp w stored inside the sweep loop
+        auto flushed_in_loop = [&](int w) {
+            const int lim = nsweeps - 17 - tile_s4(w);
+            return lim < 0 ? 0 : min(nfull, lim / 8 + 1);
+        };
+
         // load the blocks first needed in sweep u (u may be negative)
         auto issue = [&](int u) {
             if (lane == 0 && !timed_out) {
@@ -355,8 +493,10 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
                 const bool ok = e_src[j] && !timed_out && b >= 0 && b < e_nblk[j];
                 cp_async16(dst, ok ? (const void*)(e_src[j] + (size_t)b * 4) : (const void*)dummy, ok ? 16 : 0);
             }
+            issue_x(u);
         };
         // prologue: every block needed up to sweep kPFH
+        int u_issued = kPFH;  // latest sweep whose blocks were issued
         for (int u = -2 * NL - 1; u <= kPFH; u++) issue(u);
         cp_async_commit();
         cp_async_wait<0>();
@@ -368,14 +508,41 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
                 __syncwarp();
                 if (lane == 0) st_release_u32(my_prog, (unsigned)r);
             }
+            flush(r);
             issue(r + kPFH + 1);
+            u_issued = r + kPFH + 1;
             cp_async_commit();
             cp_async_wait<kPFH>();
+            // an output slot is rewritten 8 sweeps after its store was issued
+            if (lane == 0) bulk_wait_read<4>();
             if (lane == 0 && timed_out) s_abort = 1;
             __syncthreads();
             if (s_abort) break;
         }
         cp_async_wait<0>();
+        if (!s_abort) {
+            // the tiles not stored yet (every sweep is complete)
+            const int ntl = (N + kTW - 1) / kTW;
+            for (int w = 0; w < W; w++) {
+                if (!((wv_mask >> w) & 1u)) continue;
+                for (int kt = flushed_in_loop(w); kt < ntl; kt++) store_tile(w, kt);
+            }
+            if (lane == 0) bulk_commit();
+        }
+        if (lane == 0) bulk_wait<0>();
+        if (tma_x && s_abort && lane == 0) {
+            // loads still in flight land in this CTA's shared memory: wait
+            // for the latest load of every slot (the last 8 kTS sweeps issued
+            // hold it) before leaving
+            for (int u = max(0, u_issued - 8 * kTS + 1); u <= u_issued; u++) {
+                const int w = u & 7;
+                if (!((wv_mask >> w) & 1u)) continue;
+                const int d = u - tile_s4(w);
+                if (d < 0 || (d >> 3) * kTW >= N) continue;
+                const int kt = d >> 3;
+                mbar_wait_bounded(MB + w * kTS + kt % kTS, (unsigned)(kt / kTS) & 1u, A.timeout_ns);
+            }
+        }
         fence_acq_rel_gpu();
         __syncwarp();
         if (lane == 0) {
@@ -392,23 +559,26 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
     // ================= compute warps =================
     uint64_t plane, row;
     int sig;  // warp skew in steps
+    bool wvalid;  // the warp has valid rows
     if (ND == 3) {
         plane = (uint64_t)ib * W + warp;
         row = (uint64_t)jb * 32 + lane;
         sig = 4 * warp;
+        wvalid = plane < g.P;
     } else {
         plane = 0;
         row = (uint64_t)jb * 32 * W + warp * 32 + lane;
         sig = 36 * warp;
+        wvalid = (uint64_t)jb * 32 * W + warp * 32 < g.M;
     }
+    const int s4 = sig / 4;
     const bool valid = (plane < g.P) && (row < g.M);
     const uint64_t rowid = plane * g.M + row;
     const uint64_t rowbase = rowid * g.N;
-    const int N = (int)g.N;
-    // per-lane output pointers (the parameter block is read once)
-    uint16_t* const codes_row = DEC ? nullptr : A.codes + rowbase;
     float* const rec_row = (!DEC && A.recorded) ? A.recorded + rowbase : nullptr;
-    float* const out_row = DEC ? A.out + rowbase : nullptr;
+    const float* const xw = XR + (size_t)warp * kTS * kTE + lane * kTW;  // this lane's tile rows
+    OT* const ow = OR + (size_t)warp * kTS * kTE + lane * kTW;
+    const int qd_last = (N - 1 + 31 + sig) / 4;  // sweep completing the last output tile
     const int col0 = -lane - sig;  // column at step 0
 
     // halo outputs of this lane (null when the line has no consumer)
@@ -467,29 +637,21 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
     }
     const uint16_t* g_sorted = reinterpret_cast<const uint16_t*>(A.dectab + 260);
 
-    float4* xs = XS + (size_t)(warp * 32 + lane) * (kPFX + 1);
-    const float* xrow = A.x + rowbase;
-    auto x_prefetch = [&](int q) {  // the 4 columns of sweep q
-        if constexpr (!DEC) {
-            float* d = reinterpret_cast<float*>(xs + (q & (kPFX - 1)));
-#pragma unroll
-            for (int k = 0; k < kTile; k++) {
-                const int l = 4 * q + k + col0;
-                const bool in = valid && l >= 0 && l < N;
-                cp_async4(d + k, in ? (const void*)(xrow + l) : (const void*)A.x, in ? 4 : 0);
-            }
-            cp_async_commit();
-        }
-    };
-    if constexpr (!DEC) {
-        for (int q = 0; q < kPFX - 1; q++) x_prefetch(q);
-    }
     __syncthreads();  // matches the halo warp's prologue barrier
 
     for (int q = 0; q < nsweeps; q++) {
-        if constexpr (!DEC) {
-            x_prefetch(q + kPFX - 1);
-            cp_async_wait<kPFX - 1>();
+        // this warp's next x tile is first read in this sweep: wait for its load
+        if (tma_x && wvalid) {
+            const int d = q - s4;
+            if (d >= 0 && (d & 7) == 0 && (d >> 3) * kTW < N) {
+                const int kt = d >> 3;
+                if (!mbar_wait_bounded(MB + warp * kTS + kt % kTS, (unsigned)(kt / kTS) & 1u, A.timeout_ns)) {
+                    if (lane == 0) {
+                        atomicOr(&A.st->err, kErrTimeout);
+                        s_abort = 1;
+                    }
+                }
+            }
         }
         const int lq = 4 * q + col0;  // this lane's column at step 0 of the sweep
         const int wl0 = 4 * q - sig;  // lane 0's column at step 0 (warp-uniform)
@@ -502,16 +664,14 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
                 for (int a = 1; a <= NL; a++)
                     pr[a] = *reinterpret_cast<const float4*>(PR + ((size_t)(warp + NL - a) * 32 + lane) * kRPS + blk * 4);
             }
-            float xv[kTile] = {0.f, 0.f, 0.f, 0.f};
-            if constexpr (!DEC) {
-                const float4 x4 = xs[q & (kPFX - 1)];
-                xv[0] = x4.x; xv[1] = x4.y; xv[2] = x4.z; xv[3] = x4.w;
-            }
             float vout[kTile];
 #pragma unroll
             for (int k = 0; k < kTile; k++) {
                 const int l = lq + k;
                 const bool act = (l >= 0) && (l < N);
+                // position of column l in this lane's staging rows
+                const unsigned lc = act ? (unsigned)l : 0u;
+                const int ti = (int)(((lc >> 5) % kTS) * kTE + (lc & (kTW - 1)));
                 // ---- new neighbour values at column l (shuffles first: they
                 // read the values of the previous step)
                 float nR[NL + 1], nP[NL + 1], nQ[NL + 1][NL + 1];
@@ -594,8 +754,9 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
                 float V;
                 int code = 0;
                 if constexpr (!DEC) {
-                    const float tr = trunc_value(xv[k], qp.e_eb);
-                    code = quantize_tr(xv[k], pred, tr, qp, V);
+                    const float xv = act ? xw[ti] : 0.0f;
+                    const float tr = trunc_value(xv, qp.e_eb);
+                    code = quantize_tr(xv, pred, tr, qp, V);
                 } else {
                     float uv = 0.0f;
                     if (valid && act) {
@@ -614,12 +775,13 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
                 for (int e = NL; e >= 2; e--) oV[e] = oV[e - 1];
                 oV[1] = V;
                 vout[k] = V;
+                if (act) {
+                    if constexpr (DEC) ow[ti] = V;
+                    else ow[ti] = (uint16_t)code;
+                }
                 if (valid && act) {
                     if constexpr (!DEC) {
-                        codes_row[l] = (uint16_t)code;
                         if (rec_row) rec_row[l] = V;
-                    } else {
-                        out_row[l] = V;
                     }
                     if (hout_row) hout_row[l] = V;
                     if (ND != 3 && vr_next) vr_next[l & (kRV - 1)] = V;
@@ -634,10 +796,12 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
                     *reinterpret_cast<float4*>(hout_plane + (size_t)blk * 4) = v4;
             }
         }
+        // an output tile of this warp is complete after this sweep: make
+        // this thread's writes to it visible to the TMA store
+        if (tma_o && ((q >= 15 + s4 && ((q - 15 - s4) & 7) == 0) || q == qd_last)) fence_proxy_async_smem();
         __syncthreads();
         if (s_abort) break;
     }
-    if constexpr (!DEC) cp_async_wait<0>();
     if constexpr (DEC) {
         if (valid && (bad || br.consumed > rowbits_avail)) atomicOr(&A.st->err, kErrCorrupt);
     }
@@ -650,11 +814,55 @@ size_t wave_smem_bytes(const WaveGeom& g, int layers, bool decompress) {
     const int NL = layers, W = g.W;
     const int npl = (g.ndim == 3) ? (NL + W) : 0;
     const int nvl = (g.ndim == 3) ? (NL + W) : W;
-    size_t b = (size_t)npl * 32 * kRPS * 4 + (size_t)nvl * NL * kRV * 4;
-    b = (b + 15) & ~(size_t)15;
+    size_t b = 128;  // alignment slack
+    b += (size_t)npl * 32 * kRPS * 4 + (size_t)nvl * NL * kRV * 4;
+    if (!decompress) b += (size_t)W * kTS * kTE * 4;
+    b += (size_t)W * kTS * kTE * (decompress ? 4 : 2);
+    b += (size_t)W * kTS * 8;
     if (decompress) b += (size_t)(1 << kLutBits) * 4 + 260 * 4;
-    else b += (size_t)W * 32 * (kPFX + 1) * 16;
     return b;
+}
+
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link
+// dependency on the driver library)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// TMA descriptor of 32 x 32 tiles of a [P][M][N] array (row pitch `pitch`
+// elements, f32 or u16); false when the array does not meet TMA's rules
+// (16-byte aligned base and row pitch, int32 coordinates), in which case the
+// kernel uses plain loads and stores
+static bool encode_tiles(CUtensorMap* m, bool f32, const void* base, uint64_t N, uint64_t M, uint64_t P,
+                         uint64_t pitch) {
+    const uint64_t es = f32 ? 4 : 2;
+    if (!base || (reinterpret_cast<uintptr_t>(base) & 15) || (pitch * es) % 16) return false;
+    if (N >= (1ull << 31) || M * P >= (1ull << 31)) return false;
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {N, M, P};
+    cuuint64_t strides[2] = {pitch * es, pitch * es * M};
+    cuuint32_t box[3] = {(cuuint32_t)kTW, 32, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return fn(m, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<void*>(base),
+              dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <int ND, int NL, bool DEC>
@@ -674,19 +882,23 @@ static int launch_any(const WaveArgs& a, int layers, cudaStream_t s) {
     return layers == 1 ? launch_t<1, 1, DEC>(a, s) : launch_t<1, 2, DEC>(a, s);
 }
 
-int launch_wave_compress(const WaveGeom& g, int layers, const float* x, uint16_t* codes,
+int launch_wave_compress(const WaveGeom& g, int layers, const float* x, uint16_t* codes, uint64_t codes_pitch,
                          float* recorded, float* halo_row, float* halo_plane, unsigned int* prog,
                          DevState* st, uint64_t timeout_ns, cudaStream_t s) {
-    WaveArgs a = {};
+    WaveArgs a;
+    memset(&a, 0, sizeof(a));
     a.g = g;
     a.x = x;
     a.codes = codes;
+    a.opitch = codes_pitch;
     a.recorded = recorded;
     a.halo_row = halo_row;
     a.halo_plane = halo_plane;
     a.prog = prog;
     a.st = st;
     a.timeout_ns = timeout_ns;
+    a.tma_x = encode_tiles(&a.tm_x, true, x, g.N, g.M, g.P, g.N) ? 1 : 0;
+    a.tma_out = encode_tiles(&a.tm_out, false, codes, g.N, g.M, g.P, codes_pitch) ? 1 : 0;
     return launch_any<false>(a, layers, s);
 }
 
@@ -696,7 +908,8 @@ int launch_wave_decompress(const WaveGeom& g, int layers, const uint8_t* payload
                            const uint32_t* dec_tab, float* out, float* halo_row,
                            float* halo_plane, unsigned int* prog, DevState* st,
                            uint64_t timeout_ns, cudaStream_t s) {
-    WaveArgs a = {};
+    WaveArgs a;
+    memset(&a, 0, sizeof(a));
     a.g = g;
     a.payload = payload;
     a.rowoff = rowoff;
@@ -705,11 +918,13 @@ int launch_wave_decompress(const WaveGeom& g, int layers, const uint8_t* payload
     a.lut = lut;
     a.dectab = dec_tab;
     a.out = out;
+    a.opitch = g.N;
     a.halo_row = halo_row;
     a.halo_plane = halo_plane;
     a.prog = prog;
     a.st = st;
     a.timeout_ns = timeout_ns;
+    a.tma_out = encode_tiles(&a.tm_out, true, out, g.N, g.M, g.P, g.N) ? 1 : 0;
     return launch_any<true>(a, layers, s);
 }
 

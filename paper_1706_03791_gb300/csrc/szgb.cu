@@ -199,6 +199,7 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
     const uint64_t N = cp.d0 * cp.d1 * cp.d2;
     const uint64_t rows = cp.d0 * cp.d1;
     const uint64_t rowlen = cp.d2;
+    const uint64_t cpitch = (rowlen + 7) & ~(uint64_t)7;  // codes row pitch: 16-byte rows
     const int layers = cp.layers;
     WaveGeom g = make_geom(c, cp, layers);
     size_t hrow, hplane;
@@ -218,7 +219,7 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
     Arena A;
     A.add(&st, 1);
     A.add(&partials, 2 * (size_t)range_blocks);
-    A.add(&codes, N + 8);
+    A.add(&codes, rows * cpitch + 8);
     A.add(&halo_row, hrow);
     A.add(&halo_plane, hplane);
     A.add(&prog, g.num_ctas);
@@ -261,13 +262,13 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
     }
     {
         PhaseTimer t(c, PH_WAVE_C);
-        if ((rc = launch_wave_compress(g, layers, x, codes, rec_dev, halo_row, halo_plane, prog, st,
+        if ((rc = launch_wave_compress(g, layers, x, codes, cpitch, rec_dev, halo_row, halo_plane, prog, st,
                                        c->timeout_ns, s)))
             return rc;
     }
     {
         PhaseTimer t(c, PH_HIST);
-        if ((rc = launch_histogram(codes, N, hist, st, s))) return rc;
+        if ((rc = launch_histogram(codes, rows, rowlen, cpitch, hist, st, s))) return rc;
     }
     {
         PhaseTimer t(c, PH_CODEBOOK);
@@ -275,7 +276,7 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
     }
     {
         PhaseTimer t(c, PH_ROWBITS);
-        if ((rc = launch_rowbits(codes, x, rows, rowlen, len, rowbytes, st, s))) return rc;
+        if ((rc = launch_rowbits(codes, cpitch, x, rows, rowlen, len, rowbytes, st, s))) return rc;
     }
     {
         PhaseTimer t(c, PH_SCAN);
@@ -284,9 +285,10 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
     {
         PhaseTimer t(c, PH_WRITE);
         if ((rc = launch_write_meta(cp, rows, len, nodebuf, rowbytes, rowoff, dst, st, s))) return rc;
-        if ((rc = launch_encode(codes, x, rows, rowlen, len, cw, rowoff, dst, st, s))) return rc;
+        if ((rc = launch_encode(codes, cpitch, x, rows, rowlen, len, cw, rowoff, dst, st, s))) return rc;
     }
-    if (codes_dev && cudaMemcpyAsync(codes_dev, codes, N * 2, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    if (codes_dev && cudaMemcpy2DAsync(codes_dev, rowlen * 2, codes, cpitch * 2, rowlen * 2, rows,
+                                       cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return SZGB_ECUDA;
     if (cudaMemcpyAsync(c->h_state, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return SZGB_ECUDA;

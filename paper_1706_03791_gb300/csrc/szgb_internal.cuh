@@ -70,11 +70,16 @@ struct CallParams {
 // prediction terms: k in [0,n]^3 \ {0} in descending lexicographic order with
 // coefficient -prod_j (-1)^k_j C(n,k_j)  (Eq. predmodel; summation order R2)
 
-__host__ __device__ constexpr int binom_c(int n, int k) {
-    return (k < 0 || k > n) ? 0 : (k == 0 ? 1 : binom_c(n, k - 1) * (n - k + 1) / k);
+// Iterative (not recursive) so that, with constant arguments after loop
+// unrolling, the compiler folds it to a literal instead of emitting a call.
+__host__ __device__ __forceinline__ constexpr int binom_c(int n, int k) {
+    if (k < 0 || k > n) return 0;
+    int r = 1;
+    for (int i = 1; i <= k; i++) r = r * (n - i + 1) / i;
+    return r;
 }
-__host__ __device__ constexpr int sgn_binom(int n, int k) { return ((k & 1) ? -1 : 1) * binom_c(n, k); }
-__host__ __device__ constexpr int term_coef(int n, int k0, int k1, int k2) {
+__host__ __device__ __forceinline__ constexpr int sgn_binom(int n, int k) { return ((k & 1) ? -1 : 1) * binom_c(n, k); }
+__host__ __device__ __forceinline__ constexpr int term_coef(int n, int k0, int k1, int k2) {
     return -sgn_binom(n, k0) * sgn_binom(n, k1) * sgn_binom(n, k2);
 }
 
@@ -183,6 +188,68 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// mbarrier (shared memory, CTA scope)
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, uint64_t timeout_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (unsigned it = 0; it < (1u << 26); it++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 15) == 15 && globaltimer() - t0 > timeout_ns) return false;
+    }
+    return false;
+}
+// TMA: 3D tiled tensor load (global -> shared, completes on an mbarrier) and
+// store (shared -> global, bulk async-group); coordinates are element
+// indices, fastest first.
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int c0, int c1, int c2, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_addr(dst)), "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_store_3d(const void* tmap, int c0, int c1, int c2, const void* src) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];"
+                 ::"l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(src))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+template <int N>
+__device__ __forceinline__ void bulk_wait() {
+    asm volatile("cp.async.bulk.wait_group %0;" ::"n"(N) : "memory");
+}
+// orders this thread's generic-proxy shared-memory writes before later
+// async-proxy (TMA) reads of them
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void prefetch_tmap(const void* tmap) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(tmap) : "memory");
+}
+
 __device__ __forceinline__ uint32_t bswap32(uint32_t v) { return __byte_perm(v, 0, 0x0123); }
 
 // --------------------------------------------------------------------------
@@ -204,7 +271,7 @@ int launch_range(const float* x, uint64_t n, DevState* st, const CallParams& cp,
                  int nblocks, cudaStream_t s);
 int launch_adapt(const float* x, const CallParams& cp, DevState* st, cudaStream_t s);
 int launch_wave_compress(const WaveGeom& g, int layers, const float* x, uint16_t* codes,
-                         float* recorded, float* halo_row, float* halo_plane, unsigned int* prog,
+                         uint64_t codes_pitch, float* recorded, float* halo_row, float* halo_plane, unsigned int* prog,
                          DevState* st, uint64_t timeout_ns, cudaStream_t s);
 int launch_wave_decompress(const WaveGeom& g, int layers, const uint8_t* payload,
                            const uint64_t* rowoff, const uint32_t* rowbytes,
@@ -215,17 +282,18 @@ int launch_wave_decompress(const WaveGeom& g, int layers, const uint8_t* payload
 size_t wave_smem_bytes(const WaveGeom& g, int layers, bool decompress);
 
 // Huffman / stream kernels (k_huff.cu)
-int launch_histogram(const uint16_t* codes, uint64_t n, uint32_t* hist, DevState* st, cudaStream_t s);
+int launch_histogram(const uint16_t* codes, uint64_t rows, uint64_t rowlen, uint64_t pitch, uint32_t* hist,
+                     DevState* st, cudaStream_t s);
 int launch_codebook(const uint32_t* hist, DevState* st, uint8_t* len, uint64_t* cw, uint64_t* sortbuf,
                     uint32_t* nodebuf, cudaStream_t s);
-int launch_rowbits(const uint16_t* codes, const float* x, uint64_t rows, uint64_t rowlen,
+int launch_rowbits(const uint16_t* codes, uint64_t pitch, const float* x, uint64_t rows, uint64_t rowlen,
                    const uint8_t* len, uint32_t* rowbytes, DevState* st, cudaStream_t s);
 int launch_scan_rows(const uint32_t* rowbytes, uint64_t rows, uint64_t* rowoff, uint64_t* blocksums,
                      DevState* st, int finalize_compress, cudaStream_t s);
 int launch_write_meta(const CallParams& cp, uint64_t rows, const uint8_t* len, const uint32_t* usedlist,
                       const uint32_t* rowbytes, const uint64_t* rowoff, uint8_t* out, DevState* st,
                       cudaStream_t s);
-int launch_encode(const uint16_t* codes, const float* x, uint64_t rows, uint64_t rowlen, const uint8_t* len,
+int launch_encode(const uint16_t* codes, uint64_t pitch, const float* x, uint64_t rows, uint64_t rowlen, const uint8_t* len,
                   const uint64_t* cw, const uint64_t* rowoff, uint8_t* out, DevState* st, cudaStream_t s);
 int launch_decode_tables(const uint8_t* codebook, uint32_t nsym, int m, uint32_t* lut, uint32_t* dec_tab,
                          uint8_t* lenbuf, uint32_t* symbuf, DevState* st, cudaStream_t s);
