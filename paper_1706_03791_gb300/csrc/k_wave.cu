@@ -42,7 +42,10 @@
 
 namespace szgb {
 
-constexpr int kPFH = 3;   // halo / input prefetch depth (sweeps)
+constexpr int kPFH = 2;   // halo blocks are loaded this many sweeps ahead
+constexpr int kPFX = 4;   // x tiles are loaded this many sweeps ahead
+constexpr int kBarReady = 3;  // named barrier: the halo warp has made a sweep's inputs ready
+constexpr int kBarDone = 4;   // named barrier: the compute warps have finished a sweep
 constexpr int kTW = 32;   // staging tile: 32 rows x kTW columns
 constexpr int kTE = 32 * kTW;  // elements per staging tile
 constexpr int kTS = 3;    // staging ring slots per warp
@@ -240,7 +243,8 @@ struct OutElem<true> {
     using T = float;
 };
 
-template <int ND, int NL, bool DEC>
+// TR: also write the recorded (decompressed) values to A.recorded (tests)
+template <int ND, int NL, bool DEC, bool TR>
 __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __grid_constant__ WaveArgs A) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     using C = Cfg<ND, NL>;
@@ -250,15 +254,19 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool is_halo = (warp == W);
     __shared__ unsigned int s_ticket;
-    __shared__ int s_abort;
+    __shared__ int s_abort;    // written by the halo warp only; read after kBarReady
+    __shared__ int s_timeout;  // a compute warp's bounded wait ran out
+    __shared__ int s_err;      // an earlier stage failed (read once, by thread 0)
 
     // shared-memory carve-up from a 128-byte boundary (TMA destinations)
     unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     const int npl = (ND == 3) ? (NL + W) : 0;         // plane ring slots
-    const int nvl = (ND == 3) ? (NL + W) : W;         // virtual-row line groups
+    const int nvl = (ND == 3) ? (NL + W) : W + 1;     // virtual-row line groups
+    const int nhr = (ND == 3) ? W : 0;                 // bottom-row line groups (3D)
     float* PR = reinterpret_cast<float*>(smem);                          // npl*32*kRPS
     float* VR = PR + (size_t)npl * 32 * kRPS;                            // nvl*NL*kRV
-    float* XR = VR + (size_t)nvl * NL * kRV;                             // W*kTS*kTE (compress)
+    float* HR = VR + (size_t)nvl * NL * kRV;                             // nhr*NL*kRV
+    float* XR = HR + (size_t)nhr * NL * kRV;                             // W*kTS*kTE (compress)
     OT* OR = reinterpret_cast<OT*>(XR + (DEC ? 0 : (size_t)W * kTS * kTE));  // W*kTS*kTE
     uint64_t* MB = reinterpret_cast<uint64_t*>(OR + (size_t)W * kTS * kTE);  // W*kTS
     uint32_t* s_lut = reinterpret_cast<uint32_t*>(MB + W * kTS);
@@ -269,6 +277,8 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
     if (threadIdx.x == 0) {
         s_ticket = atomicAdd(&A.st->ticket, 1u);
         s_abort = 0;
+        s_timeout = 0;
+        s_err = *(volatile const unsigned*)&A.st->err != 0;
         if (tma_x) {
             for (int i = 0; i < W * kTS; i++) mbar_init(MB + i, 1);
             fence_mbar_init();
@@ -278,7 +288,7 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
     const int item = (int)s_ticket;
     const int ib = (ND == 3) ? item / g.nb1 : 0;
     const int jb = item % g.nb1;  // row block
-    if (A.st->err) {  // an earlier stage failed: publish an aborted state and leave
+    if (s_err) {  // an earlier stage failed: publish an aborted state and leave
         if (threadIdx.x == 0) st_release_u32(A.prog + item, kProgAbort);
         return;
     }
@@ -290,6 +300,7 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
     unsigned int* my_prog = A.prog + item;
     const QParams qp = load_qparams(A.st);
     const int N = (int)g.N;
+    const int nthr_all = (W + 1) * 32;  // threads of the per-sweep barriers
 
     if (is_halo) {
         // ================= halo warp =================
@@ -353,6 +364,67 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
                 if (jb > 0) e_src[j] = A.halo_row + ((size_t)(jb - 1) * NL + e) * npad;
             }
         }
+        // copy-out entries: the halo lines this CTA produces, moved from shared
+        // memory to the global halo buffers one 4-column block per sweep
+        //   3D row halo: warp w's bottom line q (HR), block b after sweep b+w+8
+        //   3D plane halo: the last NL warps' plane-ring rows (diagonal), block
+        //                  blk after sweep blk+w
+        //   2D row halo: the last warp's bottom lines (VR group W), block b
+        //                after sweep b+9W-1
+        constexpr int MAXC = (ND == 3) ? (NL * kMaxWaveWarps + NL * 32 + 31) / 32 : 1;
+        const float* c_src[MAXC];
+        float* c_dst[MAXC];
+        int c_off[MAXC], c_nblk[MAXC], c_smask[MAXC], c_sstride[MAXC];
+#pragma unroll
+        for (int j = 0; j < MAXC; j++) {
+            const int e = lane + 32 * j;
+            c_src[j] = nullptr;
+            c_dst[j] = nullptr;
+            c_off[j] = 0;
+            c_nblk[j] = 0;
+            c_smask[j] = 0;
+            c_sstride[j] = 0;
+            if (ND == 3) {
+                if (e < NL * W) {
+                    const int w = e / NL, q = e % NL;
+                    const uint64_t plane = (uint64_t)ib * W + w;
+                    if (plane < g.P && jb + 1 < g.nb1) {
+                        c_src[j] = HR + ((size_t)w * NL + q) * kRV;
+                        c_dst[j] = A.halo_row + (((size_t)plane * g.nb1 + jb) * NL + q) * npad;
+                        c_off[j] = w + 9;
+                        c_nblk[j] = npad / 4;
+                        c_smask[j] = kRV / 4 - 1;
+                    }
+                } else if (e < NL * W + NL * 32) {
+                    const int e2 = e - NL * W, p2 = e2 / 32, t = e2 % 32, w = W - NL + p2;
+                    const uint64_t plane = (uint64_t)ib * W + w, row = (uint64_t)jb * 32 + t;
+                    if (ib + 1 < g.nb0 && plane < g.P && row < g.M) {
+                        c_src[j] = PR + ((size_t)(w + NL) * 32 + t) * kRPS;
+                        c_dst[j] = A.halo_plane + ((((size_t)ib * g.nb1 + jb) * NL + p2) * 32 + t) * nshift;
+                        c_off[j] = w + 1;
+                        c_nblk[j] = nshift / 4;
+                        c_smask[j] = kRP / 4 - 1;
+                    }
+                }
+            } else if (e < NL && jb + 1 < g.nb1) {
+                c_src[j] = VR + ((size_t)W * NL + e) * kRV;
+                c_dst[j] = A.halo_row + ((size_t)jb * NL + e) * npad;
+                c_off[j] = 9 * W;
+                c_nblk[j] = npad / 4;
+                c_smask[j] = kRV / 4 - 1;
+            }
+        }
+        // in iteration r (sweeps < r complete): the blocks completed in sweep r - 1
+        auto copy_out = [&](int r) {
+#pragma unroll
+            for (int j = 0; j < MAXC; j++) {
+                if (!c_src[j]) continue;
+                const int b = r - c_off[j];
+                if (b < 0 || b >= c_nblk[j]) continue;
+                const float4 v = *reinterpret_cast<const float4*>(c_src[j] + (b & c_smask[j]) * 4);
+                *reinterpret_cast<float4*>(c_dst[j] + (size_t)b * 4) = v;
+            }
+        };
         const unsigned* prog_row = nullptr;    // CTA above (same planes)
         const unsigned* prog_plane = nullptr;  // previous plane block
         const unsigned* prog_diag = nullptr;   // previous plane block, row block above
@@ -368,7 +440,10 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
         const int plane_lag = W;
         const int diag_lag = W + 9;
         bool timed_out = false;
-        unsigned seen_row = 0, seen_plane = 0, seen_diag = 0;
+        // lanes 0, 1, 2 poll the row, plane and diagonal producer in parallel
+        const unsigned* my_src = (lane == 0) ? prog_row : (lane == 1) ? prog_plane : (lane == 2) ? prog_diag : nullptr;
+        const int my_lag = (lane == 0) ? row_lag : (lane == 1) ? plane_lag : diag_lag;
+        unsigned my_seen = 0;
         const float* dummy = A.halo_row;
 
         // staging tiles of compute warp w: first row, valid rows, skew in
@@ -395,7 +470,7 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
         // full, complete after sweep 8 kt + 15 + s4(w).  s4(w) = w (mod 8)
         // in both topologies, so for a given sweep only warp (sweep mod 8)
         // can start or finish a tile.
-        // x tile first read in sweep u: issued kPFH + 1 sweeps ahead
+        // x tile first read in sweep u: issued kPFX + 1 sweeps ahead
         auto issue_x = [&](int u) {
             if constexpr (!DEC) {
                 if (u < 0) return;
@@ -469,21 +544,11 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
 
         // load the blocks first needed in sweep u (u may be negative)
         auto issue = [&](int u) {
-            if (lane == 0 && !timed_out) {
-                if (prog_row) {
-                    unsigned need = min((unsigned)max(u + row_lag, 0), final_prog);
-                    if (!wait_progress(prog_row, need, seen_row, A.timeout_ns)) timed_out = true;
-                }
-                if (prog_plane && !timed_out) {
-                    unsigned need = min((unsigned)max(u + plane_lag, 0), final_prog);
-                    if (!wait_progress(prog_plane, need, seen_plane, A.timeout_ns)) timed_out = true;
-                }
-                if (prog_diag && !timed_out) {
-                    unsigned need = min((unsigned)max(u + diag_lag, 0), final_prog);
-                    if (!wait_progress(prog_diag, need, seen_diag, A.timeout_ns)) timed_out = true;
-                }
+            if (my_src && !timed_out) {
+                const unsigned need = min((unsigned)max(u + my_lag, 0), final_prog);
+                if (!wait_progress(my_src, need, my_seen, A.timeout_ns)) timed_out = true;
             }
-            timed_out = __shfl_sync(0xffffffffu, timed_out ? 1 : 0, 0) != 0;
+            timed_out = __any_sync(0xffffffffu, timed_out);
 #pragma unroll
             for (int j = 0; j < C::MAXE; j++) {
                 if (e_kind[j] < 0) continue;
@@ -493,34 +558,48 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
                 const bool ok = e_src[j] && !timed_out && b >= 0 && b < e_nblk[j];
                 cp_async16(dst, ok ? (const void*)(e_src[j] + (size_t)b * 4) : (const void*)dummy, ok ? 16 : 0);
             }
-            issue_x(u);
         };
-        // prologue: every block needed up to sweep kPFH
-        int u_issued = kPFH;  // latest sweep whose blocks were issued
+        // Iteration r: wait until the compute warps have finished the sweeps
+        // < r (barrier kBarDone), release sweep r (barrier kBarReady, whose
+        // halo blocks were loaded kPFH iterations earlier), then, while sweep
+        // r runs, copy out and publish the halo blocks of sweep r - 1, store
+        // the finished output tiles and load ahead.
+        // prologue: every halo block needed up to sweep kPFH, x tiles up to kPFX
+        int u_issued = kPFX;  // latest sweep whose x tiles were issued
         for (int u = -2 * NL - 1; u <= kPFH; u++) issue(u);
+        for (int u = 0; u <= kPFX; u++) issue_x(u);
         cp_async_commit();
         cp_async_wait<0>();
-        __syncthreads();
-
-        for (int r = 0; r < nsweeps; r++) {
-            if (r > 0 && r % g.pub == 0) {  // sweeps < r are complete: publish
+        if (lane == 0 && timed_out) s_abort = 1;
+        __syncwarp();
+        named_bar_arrive(kBarReady, nthr_all);  // sweep 0
+        bool stop = timed_out;
+        for (int r = 1; r <= nsweeps && !stop; r++) {
+            named_bar_sync(kBarDone, nthr_all);  // sweeps < r are complete
+            cp_async_wait<kPFH - 1>();           // halo blocks of sweep r
+            // output slots rewritten from sweep r on: their stores have read them
+            if (lane == 0) bulk_wait_read<4>();
+            stop = __any_sync(0xffffffffu, timed_out || *(volatile int*)&s_timeout != 0);
+            if (lane == 0 && stop) s_abort = 1;
+            __syncwarp();
+            if (r < nsweeps) named_bar_arrive(kBarReady, nthr_all);  // sweep r
+            if (stop) break;
+            copy_out(r);
+            if (r % g.pub == 0) {  // publish: sweeps < r are complete
                 fence_acq_rel_gpu();
                 __syncwarp();
                 if (lane == 0) st_release_u32(my_prog, (unsigned)r);
             }
             flush(r);
-            issue(r + kPFH + 1);
-            u_issued = r + kPFH + 1;
+            issue(r + kPFH);
+            issue_x(r + kPFX);
+            u_issued = r + kPFX;
             cp_async_commit();
-            cp_async_wait<kPFH>();
-            // an output slot is rewritten 8 sweeps after its store was issued
-            if (lane == 0) bulk_wait_read<4>();
-            if (lane == 0 && timed_out) s_abort = 1;
-            __syncthreads();
-            if (s_abort) break;
         }
         cp_async_wait<0>();
         if (!s_abort) {
+            // the halo blocks completed in the last sweeps
+            for (int r = nsweeps; r <= nsweeps + 9 * W + 9; r++) copy_out(r);
             // the tiles not stored yet (every sweep is complete)
             const int ntl = (N + kTW - 1) / kTW;
             for (int w = 0; w < W; w++) {
@@ -575,29 +654,20 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
     const bool valid = (plane < g.P) && (row < g.M);
     const uint64_t rowid = plane * g.M + row;
     const uint64_t rowbase = rowid * g.N;
-    float* const rec_row = (!DEC && A.recorded) ? A.recorded + rowbase : nullptr;
+    float* const rec_row = TR ? A.recorded + rowbase : nullptr;
     const float* const xw = XR + (size_t)warp * kTS * kTE + lane * kTW;  // this lane's tile rows
     OT* const ow = OR + (size_t)warp * kTS * kTE + lane * kTW;
     const int qd_last = (N - 1 + 31 + sig) / 4;  // sweep completing the last output tile
     const int col0 = -lane - sig;  // column at step 0
 
-    // halo outputs of this lane (null when the line has no consumer)
-    float* hout_row = nullptr;    // unshifted
-    float* hout_plane = nullptr;  // diagonal
-    float* vr_next = nullptr;     // 2D: this lane's line for the next warp's virtual rows
-    if (valid) {
-        if (ND == 3) {
-            if (lane >= 32 - NL && jb + 1 < g.nb1)
-                hout_row = A.halo_row + (((size_t)plane * g.nb1 + jb) * NL + (lane - (32 - NL))) * npad;
-            if (warp >= W - NL && ib + 1 < g.nb0)
-                hout_plane = A.halo_plane + ((((size_t)ib * g.nb1 + jb) * NL + (warp - (W - NL))) * 32 + lane) * nshift;
-        } else {
-            if (lane >= 32 - NL) {
-                if (warp + 1 < W) vr_next = VR + ((size_t)(warp + 1) * NL + (lane - (32 - NL))) * kRV;
-                else if (jb + 1 < g.nb1) hout_row = A.halo_row + ((size_t)jb * NL + (lane - (32 - NL))) * npad;
-            }
-        }
-    }
+    // lanes of the last NL rows keep their values in a shared line: in 3D
+    // for the row halo (copied out by the halo warp), in 1D/2D as the next
+    // warp's virtual rows (the last warp's group W is copied out as the row
+    // halo).  The plane halo is copied out of the plane ring.
+    const bool has_hr = lane >= 32 - NL;
+    const int hr_q = has_hr ? lane - (32 - NL) : 0;
+    const uint32_t hr_addr = smem_addr((ND == 3) ? HR + ((size_t)warp * NL + hr_q) * kRV
+                                                 : VR + ((size_t)(warp + 1) * NL + hr_q) * kRV);
     // this lane's virtual-row lines (lanes t < NL): own plane and planes - a
     const float* vr_own = (ND == 3) ? VR + (size_t)(warp + NL) * NL * kRV : VR + (size_t)warp * NL * kRV;
 
@@ -637,9 +707,9 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
     }
     const uint16_t* g_sorted = reinterpret_cast<const uint16_t*>(A.dectab + 260);
 
-    __syncthreads();  // matches the halo warp's prologue barrier
-
     for (int q = 0; q < nsweeps; q++) {
+        named_bar_sync(kBarReady, nthr_all);  // this sweep's inputs are ready
+        if (*(volatile int*)&s_abort) break;
         // this warp's next x tile is first read in this sweep: wait for its load
         if (tma_x && wvalid) {
             const int d = q - s4;
@@ -648,7 +718,7 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
                 if (!mbar_wait_bounded(MB + warp * kTS + kt % kTS, (unsigned)(kt / kTS) & 1u, A.timeout_ns)) {
                     if (lane == 0) {
                         atomicOr(&A.st->err, kErrTimeout);
-                        s_abort = 1;
+                        s_timeout = 1;  // the halo warp stops the CTA after this sweep
                     }
                 }
             }
@@ -665,13 +735,17 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
                     pr[a] = *reinterpret_cast<const float4*>(PR + ((size_t)(warp + NL - a) * 32 + lane) * kRPS + blk * 4);
             }
             float vout[kTile];
+            // staging slots of this sweep's columns (a sweep spans at most two tiles)
+            const unsigned kt0 = lq > 0 ? (unsigned)lq >> 5 : 0u;
+            const int sl0 = (int)(kt0 % kTS) * kTE;
+            const int sl1 = (sl0 == (kTS - 1) * kTE) ? 0 : sl0 + kTE;
 #pragma unroll
             for (int k = 0; k < kTile; k++) {
                 const int l = lq + k;
                 const bool act = (l >= 0) && (l < N);
                 // position of column l in this lane's staging rows
-                const unsigned lc = act ? (unsigned)l : 0u;
-                const int ti = (int)(((lc >> 5) % kTS) * kTE + (lc & (kTW - 1)));
+                const bool cross = lq >= 0 && (lq & (kTW - 1)) + k >= kTW;
+                const int ti = (cross ? sl1 : sl0) + (l & (kTW - 1));
                 // ---- new neighbour values at column l (shuffles first: they
                 // read the values of the previous step)
                 float nR[NL + 1], nP[NL + 1], nQ[NL + 1][NL + 1];
@@ -686,17 +760,20 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
                     }
                 }
                 // lanes next to the top of the block read the rows above
-                if (ND >= 2 && lane < NL) {
+                // (every lane loads, from a clamped line; lanes >= b discard)
+                if (ND >= 2) {
                     const int cl = l & (kRV - 1);
 #pragma unroll
                     for (int b = 1; b <= NL; b++) {
-                        if (lane < b) {
-                            const int vr = NL + lane - b;
-                            nR[b] = vr_own[vr * kRV + cl];
-                            if (ND == 3) {
+                        const int vr = min(NL + lane - b, NL - 1);
+                        const bool top = lane < b;
+                        const float r_v = vr_own[vr * kRV + cl];
+                        nR[b] = top ? r_v : nR[b];
+                        if (ND == 3) {
 #pragma unroll
-                                for (int a = 1; a <= NL; a++)
-                                    nQ[a][b] = VR[((size_t)(warp + NL - a) * NL + vr) * kRV + cl];
+                            for (int a = 1; a <= NL; a++) {
+                                const float q_v = VR[((size_t)(warp + NL - a) * NL + vr) * kRV + cl];
+                                nQ[a][b] = top ? q_v : nQ[a][b];
                             }
                         }
                     }
@@ -779,12 +856,9 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
                     if constexpr (DEC) ow[ti] = V;
                     else ow[ti] = (uint16_t)code;
                 }
-                if (valid && act) {
-                    if constexpr (!DEC) {
-                        if (rec_row) rec_row[l] = V;
-                    }
-                    if (hout_row) hout_row[l] = V;
-                    if (ND != 3 && vr_next) vr_next[l & (kRV - 1)] = V;
+                st_shared_f32_if(has_hr && act, hr_addr + 4u * (uint32_t)(l & (kRV - 1)), V);
+                if constexpr (TR) {
+                    if (valid && act) rec_row[l] = V;
                 }
             }
             // this sweep's 4 values, diagonal block q - warp: plane ring and plane halo
@@ -792,15 +866,12 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
                 const int blk = q - warp;
                 const float4 v4 = make_float4(vout[0], vout[1], vout[2], vout[3]);
                 *reinterpret_cast<float4*>(PR + ((size_t)(warp + NL) * 32 + lane) * kRPS + (blk & (kRP / 4 - 1)) * 4) = v4;
-                if (hout_plane && blk >= 0 && blk < nshift / 4)
-                    *reinterpret_cast<float4*>(hout_plane + (size_t)blk * 4) = v4;
             }
         }
         // an output tile of this warp is complete after this sweep: make
         // this thread's writes to it visible to the TMA store
         if (tma_o && ((q >= 15 + s4 && ((q - 15 - s4) & 7) == 0) || q == qd_last)) fence_proxy_async_smem();
-        __syncthreads();
-        if (s_abort) break;
+        named_bar_arrive(kBarDone, nthr_all);  // this warp has finished the sweep
     }
     if constexpr (DEC) {
         if (valid && (bad || br.consumed > rowbits_avail)) atomicOr(&A.st->err, kErrCorrupt);
@@ -813,9 +884,10 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
 size_t wave_smem_bytes(const WaveGeom& g, int layers, bool decompress) {
     const int NL = layers, W = g.W;
     const int npl = (g.ndim == 3) ? (NL + W) : 0;
-    const int nvl = (g.ndim == 3) ? (NL + W) : W;
+    const int nvl = (g.ndim == 3) ? (NL + W) : W + 1;
+    const int nhr = (g.ndim == 3) ? W : 0;
     size_t b = 128;  // alignment slack
-    b += (size_t)npl * 32 * kRPS * 4 + (size_t)nvl * NL * kRV * 4;
+    b += (size_t)npl * 32 * kRPS * 4 + (size_t)(nvl + nhr) * NL * kRV * 4;
     if (!decompress) b += (size_t)W * kTS * kTE * 4;
     b += (size_t)W * kTS * kTE * (decompress ? 4 : 2);
     b += (size_t)W * kTS * 8;
@@ -865,21 +937,26 @@ static bool encode_tiles(CUtensorMap* m, bool f32, const void* base, uint64_t N,
               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int ND, int NL, bool DEC>
+template <int ND, int NL, bool DEC, bool TR>
 static int launch_t(const WaveArgs& a, cudaStream_t s) {
     size_t smem = wave_smem_bytes(a.g, NL, DEC);
-    auto fn = k_wave<ND, NL, DEC>;
+    auto fn = k_wave<ND, NL, DEC, TR>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return SZGB_ECUDA;
     fn<<<a.g.num_ctas, (a.g.W + 1) * 32, smem, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
 }
 
+template <bool DEC, bool TR>
+static int launch_nd(const WaveArgs& a, int layers, cudaStream_t s) {
+    if (a.g.ndim == 3) return layers == 1 ? launch_t<3, 1, DEC, TR>(a, s) : launch_t<3, 2, DEC, TR>(a, s);
+    if (a.g.ndim == 2) return layers == 1 ? launch_t<2, 1, DEC, TR>(a, s) : launch_t<2, 2, DEC, TR>(a, s);
+    return layers == 1 ? launch_t<1, 1, DEC, TR>(a, s) : launch_t<1, 2, DEC, TR>(a, s);
+}
 template <bool DEC>
 static int launch_any(const WaveArgs& a, int layers, cudaStream_t s) {
-    if (a.g.ndim == 3) return layers == 1 ? launch_t<3, 1, DEC>(a, s) : launch_t<3, 2, DEC>(a, s);
-    if (a.g.ndim == 2) return layers == 1 ? launch_t<2, 1, DEC>(a, s) : launch_t<2, 2, DEC>(a, s);
-    return layers == 1 ? launch_t<1, 1, DEC>(a, s) : launch_t<1, 2, DEC>(a, s);
+    if (!DEC && a.recorded) return launch_nd<false, true>(a, layers, s);
+    return launch_nd<DEC, false>(a, layers, s);
 }
 
 int launch_wave_compress(const WaveGeom& g, int layers, const float* x, uint16_t* codes, uint64_t codes_pitch,

@@ -61,7 +61,7 @@ struct szgb_ctx {
     uint64_t ph_calls[PH_N] = {};
     cudaEvent_t ev0[PH_N] = {}, ev1[PH_N] = {};
     int sm_count = 152;
-    int W2 = 8, W3 = 8, pub = 8;
+    int W2 = 8, W3 = 8, pub = 4;
     uint64_t timeout_ns = 4000000000ull;
 };
 

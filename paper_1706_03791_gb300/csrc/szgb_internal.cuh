@@ -250,6 +250,20 @@ __device__ __forceinline__ void prefetch_tmap(const void* tmap) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(tmap) : "memory");
 }
 
+// named CTA barriers (producer/consumer: one side arrives, the other syncs)
+__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+__device__ __forceinline__ void named_bar_arrive(int id, int nthreads) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// predicated 32-bit shared-memory store (shared-window address)
+__device__ __forceinline__ void st_shared_f32_if(bool p, uint32_t addr, float v) {
+    asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n @q st.shared.f32 [%1], %2;\n}" ::"r"((unsigned)p),
+                 "r"(addr), "f"(v));
+}
+
 __device__ __forceinline__ uint32_t bswap32(uint32_t v) { return __byte_perm(v, 0, 0x0123); }
 
 // --------------------------------------------------------------------------
