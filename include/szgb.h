@@ -139,6 +139,32 @@ int szgb_decompress(szgb_ctx *ctx, const uint8_t *in, size_t in_len,
 int szgb_decompress_noalloc(const uint8_t *in_dev, size_t in_len, float *out_dev,
                             size_t out_cap_elems, void *cuda_stream);
 
+/* Batched compression of `count` independent fields, all in device memory:
+ * field i is data_dev[i] with params[i], its stream goes to out_dev[i]
+ * (out_cap[i] bytes, 4-byte aligned; data 16-byte aligned).  The result of
+ * every field is the same as szgb_compress of that field alone.  The
+ * wavefronts of all fields run in one persistent launch (one per layer
+ * count present); the per-field range, histogram, codebook and encoding
+ * kernels overlap on auxiliary streams; the whole sequence is captured in a
+ * CUDA graph on the first call and replayed while the arguments (pointers,
+ * capacities, parameters) repeat (szgb_set_graphs(ctx, 0) launches directly
+ * instead).  out_len[i] receives each stream size, also on SZGB_ETRUNC;
+ * opt_stats is NULL or holds count entries.  Returns 0 or the error of the
+ * first field that failed. */
+int szgb_compress_batch(szgb_ctx *ctx, int count, const float *const *data_dev,
+                        const szgb_params *params, uint8_t *const *out_dev,
+                        const size_t *out_cap, size_t *out_len, szgb_stats *opt_stats);
+
+/* Batched decompression: stream i (in_dev[i], in_len[i] bytes, 4-byte
+ * aligned) into out_dev[i] (out_cap_elems[i] floats, 16-byte aligned), all
+ * device memory; one persistent wavefront launch as above. */
+int szgb_decompress_batch(szgb_ctx *ctx, int count, const uint8_t *const *in_dev,
+                          const size_t *in_len, float *const *out_dev,
+                          const size_t *out_cap_elems);
+
+/* Capture batches in CUDA graphs (1, the default) or launch them directly (0). */
+int szgb_set_graphs(szgb_ctx *ctx, int on);
+
 /* Reads the header of a stream held in host memory: parameters (with the
  * m actually used) and the number of unpredictable points. */
 int szgb_stream_info(const uint8_t *in_host, size_t in_len, szgb_params *out,

@@ -49,6 +49,7 @@ constexpr int kBarDone = 4;   // named barrier: the compute warps have finished 
 constexpr int kTW = 32;   // staging tile: 32 rows x kTW columns
 constexpr int kTE = 32 * kTW;  // elements per staging tile
 constexpr int kTS = 3;    // staging ring slots per warp
+constexpr int kMbarBytes = 256;  // room for kMaxWaveWarps * kTS mbarriers, 128-byte multiple
 constexpr int kRP = 32;   // plane ring: floats per row (8 blocks of 4 columns)
 constexpr int kRPS = 36;  // plane ring row stride (9 float4: conflict-free)
 constexpr int kRV = 64;   // virtual-row ring: floats per line
@@ -244,54 +245,64 @@ struct OutElem<true> {
 };
 
 // TR: also write the recorded (decompressed) values to A.recorded (tests)
+// Per-CTA control words of one work item.
+struct WaveCtl {
+    unsigned int ticket;
+    int abort;     // written by the halo warp only; read after kBarReady
+    int timeout;   // a compute warp's bounded wait ran out
+    int err;       // an earlier stage failed (read once, by thread 0)
+    int mbar_live; // the mbarriers hold a previous item's state
+};
+
+// One work item (a block of planes x rows, or of rows) of one field.  Every
+// thread of the CTA calls it; threads beyond the item's W + 1 warps return at
+// once.  The caller separates items with __syncthreads().
 template <int ND, int NL, bool DEC, bool TR>
-__global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __grid_constant__ WaveArgs A) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+__device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, unsigned char* smem_raw, WaveCtl& S) {
     using C = Cfg<ND, NL>;
     using OT = typename OutElem<DEC>::T;
     const WaveGeom& g = A.g;
     const int W = g.W;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool is_halo = (warp == W);
-    __shared__ unsigned int s_ticket;
-    __shared__ int s_abort;    // written by the halo warp only; read after kBarReady
-    __shared__ int s_timeout;  // a compute warp's bounded wait ran out
-    __shared__ int s_err;      // an earlier stage failed (read once, by thread 0)
 
-    // shared-memory carve-up from a 128-byte boundary (TMA destinations)
+    // shared-memory carve-up from a 128-byte boundary (TMA destinations);
+    // the mbarriers sit first, at a place that does not depend on W
     unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+    uint64_t* MB = reinterpret_cast<uint64_t*>(smem);  // kMaxWaveWarps*kTS
     const int npl = (ND == 3) ? (NL + W) : 0;         // plane ring slots
     const int nvl = (ND == 3) ? (NL + W) : W + 1;     // virtual-row line groups
     const int nhr = (ND == 3) ? W : 0;                 // bottom-row line groups (3D)
-    float* PR = reinterpret_cast<float*>(smem);                          // npl*32*kRPS
+    float* PR = reinterpret_cast<float*>(smem + kMbarBytes);             // npl*32*kRPS
     float* VR = PR + (size_t)npl * 32 * kRPS;                            // nvl*NL*kRV
     float* HR = VR + (size_t)nvl * NL * kRV;                             // nhr*NL*kRV
     float* XR = HR + (size_t)nhr * NL * kRV;                             // W*kTS*kTE (compress)
     OT* OR = reinterpret_cast<OT*>(XR + (DEC ? 0 : (size_t)W * kTS * kTE));  // W*kTS*kTE
-    uint64_t* MB = reinterpret_cast<uint64_t*>(OR + (size_t)W * kTS * kTE);  // W*kTS
-    uint32_t* s_lut = reinterpret_cast<uint32_t*>(MB + W * kTS);
+    uint32_t* s_lut = reinterpret_cast<uint32_t*>(OR + (size_t)W * kTS * kTE);
     uint32_t* s_tab = s_lut + (1 << kLutBits);
     const bool tma_x = !DEC && A.tma_x;
     const bool tma_o = A.tma_out != 0;
 
     if (threadIdx.x == 0) {
-        s_ticket = atomicAdd(&A.st->ticket, 1u);
-        s_abort = 0;
-        s_timeout = 0;
-        s_err = *(volatile const unsigned*)&A.st->err != 0;
+        S.abort = 0;
+        S.timeout = 0;
+        S.err = *(volatile const unsigned*)&A.st->err != 0;
         if (tma_x) {
-            for (int i = 0; i < W * kTS; i++) mbar_init(MB + i, 1);
+            if (S.mbar_live)
+                for (int i = 0; i < kMaxWaveWarps * kTS; i++) mbar_inval(MB + i);
+            for (int i = 0; i < kMaxWaveWarps * kTS; i++) mbar_init(MB + i, 1);
             fence_mbar_init();
+            S.mbar_live = 1;
         }
     }
     __syncthreads();
-    const int item = (int)s_ticket;
     const int ib = (ND == 3) ? item / g.nb1 : 0;
     const int jb = item % g.nb1;  // row block
-    if (s_err) {  // an earlier stage failed: publish an aborted state and leave
+    if (S.err) {  // an earlier stage failed: publish an aborted state and leave
         if (threadIdx.x == 0) st_release_u32(A.prog + item, kProgAbort);
         return;
     }
+    if (warp > W) return;  // a narrower item than the launch
 
     const int npad = g.ntiles * kTile;     // row halo line length
     const int nshift = npad + 32;          // plane halo line length (diagonal)
@@ -570,7 +581,7 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
         for (int u = 0; u <= kPFX; u++) issue_x(u);
         cp_async_commit();
         cp_async_wait<0>();
-        if (lane == 0 && timed_out) s_abort = 1;
+        if (lane == 0 && timed_out) S.abort = 1;
         __syncwarp();
         named_bar_arrive(kBarReady, nthr_all);  // sweep 0
         bool stop = timed_out;
@@ -579,8 +590,8 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
             cp_async_wait<kPFH - 1>();           // halo blocks of sweep r
             // output slots rewritten from sweep r on: their stores have read them
             if (lane == 0) bulk_wait_read<4>();
-            stop = __any_sync(0xffffffffu, timed_out || *(volatile int*)&s_timeout != 0);
-            if (lane == 0 && stop) s_abort = 1;
+            stop = __any_sync(0xffffffffu, timed_out || *(volatile int*)&S.timeout != 0);
+            if (lane == 0 && stop) S.abort = 1;
             __syncwarp();
             if (r < nsweeps) named_bar_arrive(kBarReady, nthr_all);  // sweep r
             if (stop) break;
@@ -597,7 +608,7 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
             cp_async_commit();
         }
         cp_async_wait<0>();
-        if (!s_abort) {
+        if (!S.abort) {
             // the halo blocks completed in the last sweeps
             for (int r = nsweeps; r <= nsweeps + 9 * W + 9; r++) copy_out(r);
             // the tiles not stored yet (every sweep is complete)
@@ -609,7 +620,7 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
             if (lane == 0) bulk_commit();
         }
         if (lane == 0) bulk_wait<0>();
-        if (tma_x && s_abort && lane == 0) {
+        if (tma_x && S.abort && lane == 0) {
             // loads still in flight land in this CTA's shared memory: wait
             // for the latest load of every slot (the last 8 kTS sweeps issued
             // hold it) before leaving
@@ -625,7 +636,7 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
         fence_acq_rel_gpu();
         __syncwarp();
         if (lane == 0) {
-            if (s_abort) {
+            if (S.abort) {
                 atomicOr(&A.st->err, kErrTimeout);
                 st_release_u32(my_prog, kProgAbort);
             } else {
@@ -709,7 +720,7 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
 
     for (int q = 0; q < nsweeps; q++) {
         named_bar_sync(kBarReady, nthr_all);  // this sweep's inputs are ready
-        if (*(volatile int*)&s_abort) break;
+        if (*(volatile int*)&S.abort) break;
         // this warp's next x tile is first read in this sweep: wait for its load
         if (tma_x && wvalid) {
             const int d = q - s4;
@@ -718,7 +729,7 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
                 if (!mbar_wait_bounded(MB + warp * kTS + kt % kTS, (unsigned)(kt / kTS) & 1u, A.timeout_ns)) {
                     if (lane == 0) {
                         atomicOr(&A.st->err, kErrTimeout);
-                        s_timeout = 1;  // the halo warp stops the CTA after this sweep
+                        S.timeout = 1;  // the halo warp stops the CTA after this sweep
                     }
                 }
             }
@@ -878,6 +889,44 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
     }
 }
 
+// one field, one work item per CTA (items from the field's ticket counter)
+template <int ND, int NL, bool DEC, bool TR>
+__global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __grid_constant__ WaveArgs A) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ WaveCtl S;
+    if (threadIdx.x == 0) {
+        S.ticket = atomicAdd(&A.st->ticket, 1u);
+        S.mbar_live = 0;
+    }
+    __syncthreads();
+    wave_item<ND, NL, DEC, TR>(A, (int)S.ticket, smem_raw, S);
+}
+
+// Many fields in one persistent launch: every CTA takes (field, item) pairs
+// from a global ticket over `order`, which lists each field's items in
+// dependency order (interleaved across fields), so a CTA only waits for
+// items that resident CTAs took earlier.
+template <int NL, bool DEC>
+__global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1)
+    k_wave_batch(const WaveArgs* __restrict__ F, const uint2* __restrict__ order, unsigned total, unsigned* ticket) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ WaveCtl S;
+    if (threadIdx.x == 0) S.mbar_live = 0;
+    for (;;) {
+        if (threadIdx.x == 0) S.ticket = atomicAdd(ticket, 1u);
+        __syncthreads();
+        const unsigned t = S.ticket;
+        if (t >= total) break;
+        const uint2 o = order[t];
+        const WaveArgs& A = F[o.x];
+        const int nd = A.g.ndim;
+        if (nd == 3) wave_item<3, NL, DEC, false>(A, (int)o.y, smem_raw, S);
+        else if (nd == 2) wave_item<2, NL, DEC, false>(A, (int)o.y, smem_raw, S);
+        else wave_item<1, NL, DEC, false>(A, (int)o.y, smem_raw, S);
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 
@@ -886,11 +935,10 @@ size_t wave_smem_bytes(const WaveGeom& g, int layers, bool decompress) {
     const int npl = (g.ndim == 3) ? (NL + W) : 0;
     const int nvl = (g.ndim == 3) ? (NL + W) : W + 1;
     const int nhr = (g.ndim == 3) ? W : 0;
-    size_t b = 128;  // alignment slack
+    size_t b = 128 + kMbarBytes;  // alignment slack, mbarriers
     b += (size_t)npl * 32 * kRPS * 4 + (size_t)(nvl + nhr) * NL * kRV * 4;
     if (!decompress) b += (size_t)W * kTS * kTE * 4;
     b += (size_t)W * kTS * kTE * (decompress ? 4 : 2);
-    b += (size_t)W * kTS * 8;
     if (decompress) b += (size_t)(1 << kLutBits) * 4 + 260 * 4;
     return b;
 }
@@ -959,10 +1007,9 @@ static int launch_any(const WaveArgs& a, int layers, cudaStream_t s) {
     return launch_nd<DEC, false>(a, layers, s);
 }
 
-int launch_wave_compress(const WaveGeom& g, int layers, const float* x, uint16_t* codes, uint64_t codes_pitch,
-                         float* recorded, float* halo_row, float* halo_plane, unsigned int* prog,
-                         DevState* st, uint64_t timeout_ns, cudaStream_t s) {
-    WaveArgs a;
+static void fill_compress(WaveArgs& a, const WaveGeom& g, const float* x, uint16_t* codes, uint64_t codes_pitch,
+                          float* recorded, float* halo_row, float* halo_plane, unsigned int* prog, DevState* st,
+                          uint64_t timeout_ns) {
     memset(&a, 0, sizeof(a));
     a.g = g;
     a.x = x;
@@ -976,16 +1023,12 @@ int launch_wave_compress(const WaveGeom& g, int layers, const float* x, uint16_t
     a.timeout_ns = timeout_ns;
     a.tma_x = encode_tiles(&a.tm_x, true, x, g.N, g.M, g.P, g.N) ? 1 : 0;
     a.tma_out = encode_tiles(&a.tm_out, false, codes, g.N, g.M, g.P, codes_pitch) ? 1 : 0;
-    return launch_any<false>(a, layers, s);
 }
 
-int launch_wave_decompress(const WaveGeom& g, int layers, const uint8_t* payload,
-                           const uint64_t* rowoff, const uint32_t* rowbytes,
-                           const uint8_t* stream_end, const uint32_t* lut,
-                           const uint32_t* dec_tab, float* out, float* halo_row,
-                           float* halo_plane, unsigned int* prog, DevState* st,
-                           uint64_t timeout_ns, cudaStream_t s) {
-    WaveArgs a;
+static void fill_decompress(WaveArgs& a, const WaveGeom& g, const uint8_t* payload, const uint64_t* rowoff,
+                            const uint32_t* rowbytes, const uint8_t* stream_end, const uint32_t* lut,
+                            const uint32_t* dec_tab, float* out, float* halo_row, float* halo_plane,
+                            unsigned int* prog, DevState* st, uint64_t timeout_ns) {
     memset(&a, 0, sizeof(a));
     a.g = g;
     a.payload = payload;
@@ -1002,7 +1045,67 @@ int launch_wave_decompress(const WaveGeom& g, int layers, const uint8_t* payload
     a.st = st;
     a.timeout_ns = timeout_ns;
     a.tma_out = encode_tiles(&a.tm_out, true, out, g.N, g.M, g.P, g.N) ? 1 : 0;
+}
+
+int launch_wave_compress(const WaveGeom& g, int layers, const float* x, uint16_t* codes, uint64_t codes_pitch,
+                         float* recorded, float* halo_row, float* halo_plane, unsigned int* prog,
+                         DevState* st, uint64_t timeout_ns, cudaStream_t s) {
+    WaveArgs a;
+    fill_compress(a, g, x, codes, codes_pitch, recorded, halo_row, halo_plane, prog, st, timeout_ns);
+    return launch_any<false>(a, layers, s);
+}
+
+int launch_wave_decompress(const WaveGeom& g, int layers, const uint8_t* payload,
+                           const uint64_t* rowoff, const uint32_t* rowbytes,
+                           const uint8_t* stream_end, const uint32_t* lut,
+                           const uint32_t* dec_tab, float* out, float* halo_row,
+                           float* halo_plane, unsigned int* prog, DevState* st,
+                           uint64_t timeout_ns, cudaStream_t s) {
+    WaveArgs a;
+    fill_decompress(a, g, payload, rowoff, rowbytes, stream_end, lut, dec_tab, out, halo_row, halo_plane, prog, st,
+                    timeout_ns);
     return launch_any<true>(a, layers, s);
+}
+
+// ---------------------------------------------------------------------------
+// batched launch
+
+size_t wave_args_bytes() { return sizeof(WaveArgs); }
+
+void wave_args_compress(void* dst, const WaveGeom& g, const float* x, uint16_t* codes, uint64_t codes_pitch,
+                        float* halo_row, float* halo_plane, unsigned int* prog, DevState* st, uint64_t timeout_ns) {
+    fill_compress(*static_cast<WaveArgs*>(dst), g, x, codes, codes_pitch, nullptr, halo_row, halo_plane, prog, st,
+                  timeout_ns);
+}
+
+void wave_args_decompress(void* dst, const WaveGeom& g, const uint8_t* payload, const uint64_t* rowoff,
+                          const uint32_t* rowbytes, const uint8_t* stream_end, const uint32_t* lut,
+                          const uint32_t* dec_tab, float* out, float* halo_row, float* halo_plane,
+                          unsigned int* prog, DevState* st, uint64_t timeout_ns) {
+    fill_decompress(*static_cast<WaveArgs*>(dst), g, payload, rowoff, rowbytes, stream_end, lut, dec_tab, out,
+                    halo_row, halo_plane, prog, st, timeout_ns);
+}
+
+int launch_wave_batch(const void* args_dev, const void* order_dev, unsigned total, unsigned* ticket_dev, int layers,
+                      bool decompress, size_t smem, int grid, cudaStream_t s) {
+    const WaveArgs* F = static_cast<const WaveArgs*>(args_dev);
+    const uint2* order = static_cast<const uint2*>(order_dev);
+    const int block = (kMaxWaveWarps + 1) * 32;
+    if (grid < 1) grid = 1;
+    cudaError_t e;
+    if (!decompress) {
+        auto fn = layers == 1 ? k_wave_batch<1, false> : k_wave_batch<2, false>;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return SZGB_ECUDA;
+        fn<<<grid, block, smem, s>>>(F, order, total, ticket_dev);
+    } else {
+        auto fn = layers == 1 ? k_wave_batch<1, true> : k_wave_batch<2, true>;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return SZGB_ECUDA;
+        fn<<<grid, block, smem, s>>>(F, order, total, ticket_dev);
+    }
+    e = cudaGetLastError();
+    return e == cudaSuccess ? 0 : SZGB_ECUDA;
 }
 
 }  // namespace szgb

@@ -48,6 +48,14 @@ struct Arena {
 
 }  // namespace
 
+constexpr int kAux = 8;  // auxiliary streams of the batched paths
+
+// A captured batch: the arguments it was captured with and its executable graph.
+struct BatchGraph {
+    std::vector<uint64_t> key;
+    cudaGraphExec_t exec = nullptr;
+};
+
 struct szgb_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -63,6 +71,13 @@ struct szgb_ctx {
     int sm_count = 152;
     int W2 = 8, W3 = 8, pub = 4;
     uint64_t timeout_ns = 4000000000ull;
+    // batched paths
+    cudaStream_t aux[kAux] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[kAux] = {};
+    void* h_batch = nullptr;  // pinned host tables of a batch
+    size_t h_batch_cap = 0;
+    bool use_graphs = true;
+    BatchGraph g_comp, g_dec;
 };
 
 namespace {
@@ -491,6 +506,468 @@ int decompress_impl(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_dev
     return SZGB_OK;
 }
 
+
+uint64_t header_hash(const Header& h) {
+    uint64_t v = 1469598103934665603ull;
+    auto mix = [&](uint64_t x) { v = (v ^ x) * 1099511628211ull; };
+    mix(h.ndim); mix(h.layers); mix(h.m); mix(h.tw); mix(h.d0); mix(h.d1); mix(h.d2); mix(h.nsym);
+    mix(h.payload); mix(h.total);
+    uint32_t e;
+    memcpy(&e, &h.eb_f, 4);
+    mix(e);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// batches of independent fields (device buffers): every field's wavefront in
+// one persistent launch, the per-field kernels spread over auxiliary streams,
+// the whole sequence captured once in a CUDA graph and replayed while the
+// arguments repeat
+
+int ensure_aux(szgb_ctx* c) {
+    if (c->ev_fork) return SZGB_OK;
+    for (int k = 0; k < kAux; k++) {
+        if (cudaStreamCreateWithFlags(&c->aux[k], cudaStreamNonBlocking) != cudaSuccess) return SZGB_ECUDA;
+        if (cudaEventCreateWithFlags(&c->ev_join[k], cudaEventDisableTiming) != cudaSuccess) return SZGB_ECUDA;
+    }
+    if (cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess) return SZGB_ECUDA;
+    return SZGB_OK;
+}
+
+int ensure_pinned(szgb_ctx* c, size_t need) {
+    if (need <= c->h_batch_cap) return SZGB_OK;
+    if (c->h_batch) {
+        cudaStreamSynchronize(c->stream);
+        cudaFreeHost(c->h_batch);
+        c->h_batch = nullptr;
+        c->h_batch_cap = 0;
+    }
+    size_t cap = align_up(need + need / 4, 1 << 16);
+    if (cudaMallocHost(&c->h_batch, cap) != cudaSuccess) {
+        cudaGetLastError();
+        return SZGB_ENOMEM;
+    }
+    c->h_batch_cap = cap;
+    return SZGB_OK;
+}
+
+// fork: every auxiliary stream waits for the main stream; join: the reverse
+void fork_aux(szgb_ctx* c) {
+    cudaEventRecord(c->ev_fork, c->stream);
+    for (int k = 0; k < kAux; k++) cudaStreamWaitEvent(c->aux[k], c->ev_fork, 0);
+}
+void join_aux(szgb_ctx* c) {
+    for (int k = 0; k < kAux; k++) {
+        cudaEventRecord(c->ev_join[k], c->aux[k]);
+        cudaStreamWaitEvent(c->stream, c->ev_join[k], 0);
+    }
+}
+
+void drop_graph(BatchGraph& G) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    G.exec = nullptr;
+    G.key.clear();
+}
+
+// Runs `enqueue` on the main stream: directly, or from the cached graph when
+// `key` matches, else captured into a new graph first.
+template <typename F>
+int run_batch(szgb_ctx* c, BatchGraph& G, const std::vector<uint64_t>& key, F enqueue) {
+    cudaStream_t s = c->stream;
+    if (!c->use_graphs) return enqueue();
+    if (!(G.exec && G.key == key)) {
+        drop_graph(G);
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) return SZGB_ECUDA;
+        int rc = enqueue();
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s, &graph);
+        if (rc || e != cudaSuccess || !graph) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return rc ? rc : SZGB_ECUDA;
+        }
+        e = cudaGraphInstantiate(&G.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            G.exec = nullptr;
+            cudaGetLastError();
+            return SZGB_ECUDA;
+        }
+        G.key = key;
+    }
+    return cudaGraphLaunch(G.exec, s) == cudaSuccess ? SZGB_OK : SZGB_ECUDA;
+}
+
+struct CompPlan {
+    CallParams cp;
+    WaveGeom g;
+    uint64_t n, rows, rowlen, cpitch;
+    size_t hrow, hplane;
+    int range_blocks;
+    // device scratch
+    float *partials, *halo_row, *halo_plane;
+    uint16_t* codes;
+    uint32_t *rowbytes, *nodebuf;
+    uint8_t* len;
+    uint64_t *cw, *sortbuf, *rowoff, *blocksums;
+    unsigned* prog;
+    uint32_t* hist;
+};
+
+// the (field, item) order of a batched wavefront: level i lists item i of
+// every field that has one, so each field's items stay in dependency order
+size_t build_order(const std::vector<int>& fields, const std::vector<int>& nitems, uint32_t* dst) {
+    int maxi = 0;
+    for (int f : fields) maxi = std::max(maxi, nitems[f]);
+    size_t t = 0;
+    for (int i = 0; i < maxi; i++)
+        for (int f : fields)
+            if (i < nitems[f]) {
+                dst[2 * t] = (uint32_t)f;
+                dst[2 * t + 1] = (uint32_t)i;
+                t++;
+            }
+    return t;
+}
+
+int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const szgb_params* params,
+                        uint8_t* const* out, const size_t* out_cap, size_t* out_len, szgb_stats* stats) {
+    if (!c || count < 1 || !data || !params || !out || !out_cap || !out_len) return SZGB_EINVAL;
+    if (cudaSetDevice(c->device) != cudaSuccess) return SZGB_ECUDA;
+    int rc = ensure_aux(c);
+    if (rc) return rc;
+    std::vector<CompPlan> P(count);
+    std::vector<int> nitems(count), by_layers[2];
+    size_t smem[2] = {0, 0};
+    for (int f = 0; f < count; f++) {
+        CompPlan& q = P[f];
+        if (!data[f] || !out[f] || ((uintptr_t)data[f] % 16) || ((uintptr_t)out[f] % 4)) return SZGB_EINVAL;
+        if ((rc = check_params(&params[f], &q.cp))) return rc;
+        q.n = q.cp.d0 * q.cp.d1 * q.cp.d2;
+        q.rows = q.cp.d0 * q.cp.d1;
+        q.rowlen = q.cp.d2;
+        q.cpitch = (q.rowlen + 7) & ~(uint64_t)7;
+        q.g = make_geom(c, q.cp, q.cp.layers);
+        halo_sizes(q.g, q.cp.layers, &q.hrow, &q.hplane);
+        q.range_blocks = (int)std::min<uint64_t>(std::max<uint64_t>((q.n + 8191) / 8192, 1), 4ull * c->sm_count);
+        nitems[f] = q.g.num_ctas;
+        const int li = q.cp.layers - 1;
+        by_layers[li].push_back(f);
+        smem[li] = std::max(smem[li], wave_smem_bytes(q.g, q.cp.layers, false));
+    }
+    const size_t wsz = wave_args_bytes();
+    size_t nprog = 0, total_items = 0;
+    for (int f = 0; f < count; f++) nprog += (size_t)nitems[f], total_items += (size_t)nitems[f];
+
+    // device scratch
+    DevState* st;
+    unsigned *tickets, *prog_all;
+    uint32_t *hist_all, *order;
+    char* wargs;
+    Arena A;
+    A.add(&st, count);
+    A.add(&tickets, 2);
+    A.add(&prog_all, nprog);
+    A.add(&hist_all, (size_t)count * 65536);
+    A.add(&wargs, (size_t)count * wsz);
+    A.add(&order, 2 * total_items);
+    for (int f = 0; f < count; f++) {
+        CompPlan& q = P[f];
+        A.add(&q.partials, 2 * (size_t)q.range_blocks);
+        A.add(&q.codes, q.rows * q.cpitch + 8);
+        A.add(&q.halo_row, q.hrow);
+        A.add(&q.halo_plane, q.hplane);
+        A.add(&q.len, 65536);
+        A.add(&q.cw, 65536);
+        A.add(&q.sortbuf, kSortBufU64);
+        A.add(&q.nodebuf, kNodeBufU32);
+        A.add(&q.rowbytes, q.rows);
+        A.add(&q.rowoff, q.rows);
+        A.add(&q.blocksums, (q.rows + 2047) / 2048 + 1);
+    }
+    if ((rc = ensure_scratch(c, A.total))) return rc;
+    A.bind(c->scratch);
+    {
+        size_t po = 0;
+        for (int f = 0; f < count; f++) {
+            P[f].prog = prog_all + po;
+            P[f].hist = hist_all + (size_t)f * 65536;
+            po += (size_t)nitems[f];
+        }
+    }
+    // pinned host tables: initial states, wavefront arguments, order; the
+    // final states come back to the same place
+    const size_t o_st = 0, o_w = align_up((size_t)count * sizeof(DevState), 256);
+    const size_t o_ord = align_up(o_w + (size_t)count * wsz, 256);
+    const size_t o_out = align_up(o_ord + 8 * total_items, 256);
+    if ((rc = ensure_pinned(c, o_out + (size_t)count * sizeof(DevState)))) return rc;
+    char* H = static_cast<char*>(c->h_batch);
+    DevState* h_init = reinterpret_cast<DevState*>(H + o_st);
+    DevState* h_fin = reinterpret_cast<DevState*>(H + o_out);
+    for (int f = 0; f < count; f++) {
+        h_init[f] = DevState{};
+        h_init[f].cap = out_cap[f];
+        wave_args_compress(H + o_w + (size_t)f * wsz, P[f].g, data[f], P[f].codes, P[f].cpitch, P[f].halo_row,
+                           P[f].halo_plane, P[f].prog, st + f, c->timeout_ns);
+    }
+    uint32_t* h_order = reinterpret_cast<uint32_t*>(H + o_ord);
+    size_t ord_at[2], ord_n[2];
+    ord_at[0] = 0;
+    ord_n[0] = build_order(by_layers[0], nitems, h_order);
+    ord_at[1] = ord_n[0];
+    ord_n[1] = build_order(by_layers[1], nitems, h_order + 2 * ord_n[0]);
+
+    std::vector<uint64_t> key;
+    key.push_back((uint64_t)count);
+    key.push_back((uint64_t)(uintptr_t)c->scratch);
+    key.push_back((uint64_t)(uintptr_t)c->h_batch);
+    key.push_back((uint64_t)c->W2 | ((uint64_t)c->W3 << 16) | ((uint64_t)c->pub << 32));
+    for (int f = 0; f < count; f++) {
+        key.push_back((uint64_t)(uintptr_t)data[f]);
+        key.push_back((uint64_t)(uintptr_t)out[f]);
+        key.push_back((uint64_t)out_cap[f]);
+        const uint64_t* pw = reinterpret_cast<const uint64_t*>(&params[f]);
+        for (size_t i = 0; i < sizeof(szgb_params) / 8; i++) key.push_back(pw[i]);
+    }
+    cudaStream_t s = c->stream;
+    auto enqueue = [&]() -> int {
+        int r;
+        if (cudaMemcpyAsync(st, h_init, (size_t)count * sizeof(DevState), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(wargs, H + o_w, (size_t)count * wsz, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(order, h_order, 8 * total_items, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemsetAsync(tickets, 0, 2 * sizeof(unsigned), s) != cudaSuccess ||
+            cudaMemsetAsync(prog_all, 0, nprog * sizeof(unsigned), s) != cudaSuccess ||
+            cudaMemsetAsync(hist_all, 0, (size_t)count * 65536 * 4, s) != cudaSuccess)
+            return SZGB_ECUDA;
+        fork_aux(c);
+        for (int f = 0; f < count; f++) {
+            CompPlan& q = P[f];
+            cudaStream_t a = c->aux[f % kAux];
+            if ((r = launch_range(data[f], q.n, st + f, q.cp, q.partials, q.range_blocks, a))) return r;
+            if (q.cp.m_user == 0 && (r = launch_adapt(data[f], q.cp, st + f, a))) return r;
+        }
+        join_aux(c);
+        for (int li = 0; li < 2; li++) {
+            if (!ord_n[li]) continue;
+            const int grid = (int)std::min<size_t>(ord_n[li], (size_t)c->sm_count);
+            if ((r = launch_wave_batch(wargs, order + 2 * ord_at[li], (unsigned)ord_n[li], tickets + li, li + 1, false,
+                                       smem[li], grid, s)))
+                return r;
+        }
+        fork_aux(c);
+        for (int f = 0; f < count; f++) {
+            CompPlan& q = P[f];
+            cudaStream_t a = c->aux[f % kAux];
+            if ((r = launch_histogram(q.codes, q.rows, q.rowlen, q.cpitch, q.hist, st + f, a))) return r;
+            if ((r = launch_codebook(q.hist, st + f, q.len, q.cw, q.sortbuf, q.nodebuf, a))) return r;
+            if ((r = launch_rowbits(q.codes, q.cpitch, data[f], q.rows, q.rowlen, q.len, q.rowbytes, st + f, a))) return r;
+            if ((r = launch_scan_rows(q.rowbytes, q.rows, q.rowoff, q.blocksums, st + f, 1, a))) return r;
+            if ((r = launch_write_meta(q.cp, q.rows, q.len, q.nodebuf, q.rowbytes, q.rowoff, out[f], st + f, a))) return r;
+            if ((r = launch_encode(q.codes, q.cpitch, data[f], q.rows, q.rowlen, q.len, q.cw, q.rowoff, out[f], st + f, a)))
+                return r;
+        }
+        join_aux(c);
+        if (cudaMemcpyAsync(h_fin, st, (size_t)count * sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return SZGB_ECUDA;
+        return SZGB_OK;
+    };
+    if ((rc = run_batch(c, c->g_comp, key, enqueue))) return rc;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SZGB_ECUDA;
+    int first = SZGB_OK;
+    for (int f = 0; f < count; f++) {
+        const DevState& hs = h_fin[f];
+        out_len[f] = (size_t)hs.total;
+        int r = dev_errors(hs);
+        if (r == SZGB_OK && hs.total > out_cap[f]) r = SZGB_ETRUNC;
+        if (r && !first) first = r;
+        if (stats) {
+            stats[f].n_points = P[f].n;
+            stats[f].n_unpred = hs.K;
+            stats[f].stream_bytes = hs.total;
+            stats[f].m = hs.m;
+            stats[f].maxlen = (int)hs.maxlen;
+            stats[f].nsym = hs.nsym;
+            stats[f].eb_f = hs.eb_f;
+            stats[f].xmin = hs.xmin;
+            stats[f].xmax = hs.xmax;
+        }
+    }
+    return first;
+}
+
+struct DecPlan {
+    Header H;
+    CallParams cp;
+    WaveGeom g;
+    uint64_t n, rows;
+    size_t hrow, hplane;
+    const uint8_t *codebook, *table, *payload;
+    float *halo_row, *halo_plane;
+    unsigned* prog;
+    uint32_t *rowbytes, *lut, *dectab, *symbuf;
+    uint64_t *rowoff, *blocksums;
+    uint8_t* lenbuf;
+};
+
+int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, const size_t* in_len,
+                          float* const* out, const size_t* out_cap) {
+    if (!c || count < 1 || !in || !in_len || !out || !out_cap) return SZGB_EINVAL;
+    if (cudaSetDevice(c->device) != cudaSuccess) return SZGB_ECUDA;
+    int rc = ensure_aux(c);
+    if (rc) return rc;
+    cudaStream_t s = c->stream;
+    // headers to the host (one small copy per field, one synchronisation)
+    const size_t hdr_bytes = (size_t)count * kHeaderBytes;
+    if ((rc = ensure_pinned(c, hdr_bytes))) return rc;
+    for (int f = 0; f < count; f++) {
+        if (!in[f] || !out[f] || ((uintptr_t)in[f] % 4) || ((uintptr_t)out[f] % 16) || in_len[f] < (size_t)kHeaderBytes)
+            return SZGB_EINVAL;
+        if (cudaMemcpyAsync(static_cast<char*>(c->h_batch) + (size_t)f * kHeaderBytes, in[f], kHeaderBytes,
+                            cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return SZGB_ECUDA;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SZGB_ECUDA;
+    std::vector<DecPlan> P(count);
+    std::vector<int> nitems(count), by_layers[2];
+    size_t smem[2] = {0, 0};
+    for (int f = 0; f < count; f++) {
+        DecPlan& q = P[f];
+        if ((rc = parse_header(static_cast<uint8_t*>(c->h_batch) + (size_t)f * kHeaderBytes, in_len[f], &q.H))) return rc;
+        if (q.H.layers > kMaxLayers) return SZGB_EUNSUPPORTED;
+        q.n = q.H.d0 * q.H.d1 * q.H.d2;
+        if (out_cap[f] < q.n) return SZGB_EINVAL;
+        q.rows = q.H.nchunks;
+        q.cp = CallParams{};
+        q.cp.ndim = q.H.ndim;
+        q.cp.d0 = q.H.d0;
+        q.cp.d1 = q.H.d1;
+        q.cp.d2 = q.H.d2;
+        q.cp.layers = q.H.layers;
+        q.g = make_geom(c, q.cp, q.H.layers);
+        halo_sizes(q.g, q.H.layers, &q.hrow, &q.hplane);
+        const uint64_t cb = (3ull * q.H.nsym + 3) & ~3ull, tb = ((uint64_t)q.H.tw * q.rows + 3) & ~3ull;
+        q.codebook = in[f] + kHeaderBytes;
+        q.table = q.codebook + cb;
+        q.payload = q.table + tb;
+        nitems[f] = q.g.num_ctas;
+        const int li = q.H.layers - 1;
+        by_layers[li].push_back(f);
+        smem[li] = std::max(smem[li], wave_smem_bytes(q.g, q.H.layers, true));
+    }
+    const size_t wsz = wave_args_bytes();
+    size_t nprog = 0, total_items = 0;
+    for (int f = 0; f < count; f++) nprog += (size_t)nitems[f], total_items += (size_t)nitems[f];
+    DevState* st;
+    unsigned *tickets, *prog_all;
+    uint32_t* order;
+    char* wargs;
+    Arena A;
+    A.add(&st, count);
+    A.add(&tickets, 2);
+    A.add(&prog_all, nprog);
+    A.add(&wargs, (size_t)count * wsz);
+    A.add(&order, 2 * total_items);
+    for (int f = 0; f < count; f++) {
+        DecPlan& q = P[f];
+        A.add(&q.halo_row, q.hrow);
+        A.add(&q.halo_plane, q.hplane);
+        A.add(&q.rowbytes, q.rows);
+        A.add(&q.rowoff, q.rows);
+        A.add(&q.blocksums, (q.rows + 2047) / 2048 + 1);
+        A.add(&q.lut, (size_t)1 << kLutBits);
+        A.add(&q.dectab, kDecTabU32);
+        A.add(&q.lenbuf, 65536);
+        A.add(&q.symbuf, 65536);
+    }
+    if ((rc = ensure_scratch(c, A.total))) return rc;
+    A.bind(c->scratch);
+    {
+        size_t po = 0;
+        for (int f = 0; f < count; f++) {
+            P[f].prog = prog_all + po;
+            po += (size_t)nitems[f];
+        }
+    }
+    const size_t o_st = 0, o_w = align_up((size_t)count * sizeof(DevState), 256);
+    const size_t o_ord = align_up(o_w + (size_t)count * wsz, 256);
+    const size_t o_out = align_up(o_ord + 8 * total_items, 256);
+    if ((rc = ensure_pinned(c, o_out + (size_t)count * sizeof(DevState)))) return rc;
+    char* Hb = static_cast<char*>(c->h_batch);
+    DevState* h_init = reinterpret_cast<DevState*>(Hb + o_st);
+    DevState* h_fin = reinterpret_cast<DevState*>(Hb + o_out);
+    for (int f = 0; f < count; f++) {
+        DecPlan& q = P[f];
+        DevState& d = h_init[f];
+        d = DevState{};
+        d.eb_f = q.H.eb_f;
+        d.twoeb = 2.0f * q.H.eb_f;
+        d.m = q.H.m;
+        d.center = 1 << (q.H.m - 1);
+        d.radius = (float)((1 << (q.H.m - 1)) - 1);
+        uint32_t ub;
+        memcpy(&ub, &q.H.eb_f, 4);
+        d.e_eb = (int)((ub >> 23) & 0xffu);
+        wave_args_decompress(Hb + o_w + (size_t)f * wsz, q.g, q.payload, q.rowoff, q.rowbytes, q.payload + q.H.payload,
+                             q.lut, q.dectab, out[f], q.halo_row, q.halo_plane, q.prog, st + f, c->timeout_ns);
+    }
+    uint32_t* h_order = reinterpret_cast<uint32_t*>(Hb + o_ord);
+    size_t ord_at[2], ord_n[2];
+    ord_at[0] = 0;
+    ord_n[0] = build_order(by_layers[0], nitems, h_order);
+    ord_at[1] = ord_n[0];
+    ord_n[1] = build_order(by_layers[1], nitems, h_order + 2 * ord_n[0]);
+    std::vector<uint64_t> key;
+    key.push_back((uint64_t)count);
+    key.push_back((uint64_t)(uintptr_t)c->scratch);
+    key.push_back((uint64_t)(uintptr_t)c->h_batch);
+    key.push_back((uint64_t)c->W2 | ((uint64_t)c->W3 << 16) | ((uint64_t)c->pub << 32));
+    for (int f = 0; f < count; f++) {
+        key.push_back((uint64_t)(uintptr_t)in[f]);
+        key.push_back((uint64_t)in_len[f]);
+        key.push_back((uint64_t)(uintptr_t)out[f]);
+        // the header fixes everything else the plan depends on
+        key.push_back(header_hash(P[f].H));
+    }
+    auto enqueue = [&]() -> int {
+        int r;
+        if (cudaMemcpyAsync(st, h_init, (size_t)count * sizeof(DevState), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(wargs, Hb + o_w, (size_t)count * wsz, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(order, h_order, 8 * total_items, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemsetAsync(tickets, 0, 2 * sizeof(unsigned), s) != cudaSuccess ||
+            cudaMemsetAsync(prog_all, 0, nprog * sizeof(unsigned), s) != cudaSuccess)
+            return SZGB_ECUDA;
+        fork_aux(c);
+        for (int f = 0; f < count; f++) {
+            DecPlan& q = P[f];
+            cudaStream_t a = c->aux[f % kAux];
+            if ((r = launch_decode_tables(q.codebook, q.H.nsym, q.H.m, q.lut, q.dectab, q.lenbuf, q.symbuf, st + f, a)))
+                return r;
+            if ((r = launch_read_rowbytes(q.table, q.H.tw, q.rows, q.rowbytes, a))) return r;
+            if ((r = launch_scan_rows(q.rowbytes, q.rows, q.rowoff, q.blocksums, st + f, 0, a))) return r;
+        }
+        join_aux(c);
+        for (int li = 0; li < 2; li++) {
+            if (!ord_n[li]) continue;
+            const int grid = (int)std::min<size_t>(ord_n[li], (size_t)c->sm_count);
+            if ((r = launch_wave_batch(wargs, order + 2 * ord_at[li], (unsigned)ord_n[li], tickets + li, li + 1, true,
+                                       smem[li], grid, s)))
+                return r;
+        }
+        if (cudaMemcpyAsync(h_fin, st, (size_t)count * sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return SZGB_ECUDA;
+        return SZGB_OK;
+    };
+    if ((rc = run_batch(c, c->g_dec, key, enqueue))) return rc;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SZGB_ECUDA;
+    int first = SZGB_OK;
+    for (int f = 0; f < count; f++) {
+        const DevState& hs = h_fin[f];
+        int r = dev_errors(hs);
+        if (r == SZGB_OK && hs.payload != P[f].H.payload) r = SZGB_ECORRUPT;
+        if (r && !first) first = r;
+    }
+    return first;
+}
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -539,13 +1016,46 @@ void szgb_destroy(szgb_ctx* c) {
         if (c->ev0[i]) cudaEventDestroy(c->ev0[i]);
         if (c->ev1[i]) cudaEventDestroy(c->ev1[i]);
     }
+    drop_graph(c->g_comp);
+    drop_graph(c->g_dec);
+    for (int k = 0; k < kAux; k++) {
+        if (c->aux[k]) cudaStreamDestroy(c->aux[k]);
+        if (c->ev_join[k]) cudaEventDestroy(c->ev_join[k]);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->h_batch) cudaFreeHost(c->h_batch);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
 }
 
+int szgb_compress_batch(szgb_ctx* c, int count, const float* const* data_dev, const szgb_params* params,
+                        uint8_t* const* out_dev, const size_t* out_cap, size_t* out_len, szgb_stats* opt_stats) {
+    return compress_batch_impl(c, count, data_dev, params, out_dev, out_cap, out_len, opt_stats);
+}
+
+int szgb_decompress_batch(szgb_ctx* c, int count, const uint8_t* const* in_dev, const size_t* in_len,
+                          float* const* out_dev, const size_t* out_cap_elems) {
+    return decompress_batch_impl(c, count, in_dev, in_len, out_dev, out_cap_elems);
+}
+
+int szgb_set_graphs(szgb_ctx* c, int on) {
+    if (!c) return SZGB_EINVAL;
+    c->use_graphs = on != 0;
+    if (!c->use_graphs) {
+        drop_graph(c->g_comp);
+        drop_graph(c->g_dec);
+    }
+    return SZGB_OK;
+}
+
 int szgb_set_stream(szgb_ctx* c, void* stream) {
     if (!c) return SZGB_EINVAL;
-    c->stream = stream ? static_cast<cudaStream_t>(stream) : c->own_stream;
+    cudaStream_t ns = stream ? static_cast<cudaStream_t>(stream) : c->own_stream;
+    if (ns != c->stream) {  // captured graphs were recorded on the old stream
+        drop_graph(c->g_comp);
+        drop_graph(c->g_dec);
+    }
+    c->stream = ns;
     return SZGB_OK;
 }
 

@@ -192,6 +192,9 @@ __device__ __forceinline__ void cp_async_wait() {
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
 __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -294,6 +297,17 @@ int launch_wave_decompress(const WaveGeom& g, int layers, const uint8_t* payload
                            float* halo_plane, unsigned int* prog, DevState* st,
                            uint64_t timeout_ns, cudaStream_t s);
 size_t wave_smem_bytes(const WaveGeom& g, int layers, bool decompress);
+// batched wavefront: a device table of per-field arguments (filled on the
+// host, wave_args_bytes() each, 64-byte aligned) and a (field, item) order
+size_t wave_args_bytes();
+void wave_args_compress(void* dst, const WaveGeom& g, const float* x, uint16_t* codes, uint64_t codes_pitch,
+                        float* halo_row, float* halo_plane, unsigned int* prog, DevState* st, uint64_t timeout_ns);
+void wave_args_decompress(void* dst, const WaveGeom& g, const uint8_t* payload, const uint64_t* rowoff,
+                          const uint32_t* rowbytes, const uint8_t* stream_end, const uint32_t* lut,
+                          const uint32_t* dec_tab, float* out, float* halo_row, float* halo_plane,
+                          unsigned int* prog, DevState* st, uint64_t timeout_ns);
+int launch_wave_batch(const void* args_dev, const void* order_dev, unsigned total, unsigned* ticket_dev, int layers,
+                      bool decompress, size_t smem, int grid, cudaStream_t s);
 
 // Huffman / stream kernels (k_huff.cu)
 int launch_histogram(const uint16_t* codes, uint64_t rows, uint64_t rowlen, uint64_t pitch, uint32_t* hist,

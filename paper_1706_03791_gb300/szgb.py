@@ -73,6 +73,11 @@ def lib():
         L.szgb_phase_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.c_int,
                                        C.c_int]
         L.szgb_decompress_noalloc.argtypes = [vp, sz, vp, sz, vp]
+        L.szgb_compress_batch.argtypes = [vp, C.c_int, C.POINTER(vp), C.POINTER(Params), C.POINTER(vp),
+                                          C.POINTER(sz), C.POINTER(sz), C.POINTER(Stats)]
+        L.szgb_decompress_batch.argtypes = [vp, C.c_int, C.POINTER(vp), C.POINTER(sz), C.POINTER(vp),
+                                            C.POINTER(sz)]
+        L.szgb_set_graphs.argtypes = [vp, C.c_int]
         L.szgb_strerror.argtypes = [C.c_int]
         L.szgb_strerror.restype = C.c_char_p
         _lib = L
@@ -87,7 +92,7 @@ def strerror(code: int) -> str:
 EXPORTS = ["szgb_create", "szgb_destroy", "szgb_set_stream", "szgb_compress_bound", "szgb_compress",
            "szgb_compress_trace", "szgb_decompress", "szgb_stream_info", "szgb_set_profiling",
            "szgb_num_phases", "szgb_phase_name", "szgb_phase_times", "szgb_strerror",
-           "szgb_decompress_noalloc"]
+           "szgb_decompress_noalloc", "szgb_compress_batch", "szgb_decompress_batch", "szgb_set_graphs"]
 
 
 def make_params(shape, mode=REL, eb_abs=0.0, eb_rel=1e-4, layers=1, m=0, theta=0.99) -> Params:
@@ -244,6 +249,57 @@ class Context:
         if rc:
             raise SzgbError(rc, "szgb_decompress")
         return out
+
+    # -- batches -------------------------------------------------------------
+    def set_graphs(self, on: bool):
+        lib().szgb_set_graphs(self._h, 1 if on else 0)
+
+    def compress_batch(self, xs, params, outs=None):
+        """Compress the CUDA float32 tensors `xs` in one batched call.
+        `params` is one dict of make_params keywords for all fields or a list
+        of them.  `outs` (optional) are uint8 CUDA tensors to write into.
+        Returns (streams, stats): views of the output tensors and a list of
+        Stats."""
+        import torch
+        n = len(xs)
+        if isinstance(params, dict):
+            params = [params] * n
+        P = (Params * n)()
+        for i, (x, kw) in enumerate(zip(xs, params)):
+            assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()
+            P[i] = make_params(tuple(x.shape), **kw)
+        L = lib()
+        if outs is None:
+            outs = [torch.empty(int(L.szgb_compress_bound(C.byref(P[i]))), dtype=torch.uint8, device=xs[i].device)
+                    for i in range(n)]
+        dp = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+        op = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+        cap = (C.c_size_t * n)(*[o.numel() for o in outs])
+        olen = (C.c_size_t * n)()
+        st = (Stats * n)()
+        rc = L.szgb_compress_batch(self._h, n, dp, P, op, cap, olen, st)
+        if rc:
+            raise SzgbError(rc, "szgb_compress_batch")
+        return [outs[i][:olen[i]] for i in range(n)], [st[i] for i in range(n)]
+
+    def decompress_batch(self, streams, outs=None):
+        """Decompress the uint8 CUDA tensors `streams` in one batched call into
+        float32 CUDA tensors (allocated from the headers when `outs` is None)."""
+        import torch
+        n = len(streams)
+        if outs is None:
+            outs = []
+            for s in streams:
+                info = stream_info_header(s[:128].cpu().numpy())
+                outs.append(torch.empty(info["shape"], dtype=torch.float32, device=s.device))
+        ip = (C.c_void_p * n)(*[s.data_ptr() for s in streams])
+        il = (C.c_size_t * n)(*[s.numel() for s in streams])
+        op = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+        oc = (C.c_size_t * n)(*[o.numel() for o in outs])
+        rc = lib().szgb_decompress_batch(self._h, n, ip, il, op, oc)
+        if rc:
+            raise SzgbError(rc, "szgb_decompress_batch")
+        return outs
 
     def decompress_ptr(self, in_ptr: int, in_len: int, in_on_device: bool, out_ptr: int,
                        out_elems: int, out_on_device: bool) -> int:

@@ -1,0 +1,92 @@
+"""Batched compression and decompression (one persistent wavefront launch for
+many fields, captured in a CUDA graph) against the CPU oracle: every field's
+stream is byte-identical to the oracle's stream of that field alone, and every
+reconstruction bit-identical -- the result of a field is the same alone and in
+the mix.  Fields of mixed dimension, size, layer count and bound."""
+import numpy as np
+import pytest
+
+from synthetic import fields
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    from paper_1706_03791_gb300 import build
+    build.build()
+    from paper_1706_03791_gb300 import szgb
+    assert torch.cuda.is_available()
+    c = szgb.Context(0)
+    yield c
+    c.close()
+
+
+def _bits(a):
+    return np.ascontiguousarray(a).view(np.uint32)
+
+
+MIX = [
+    (lambda: fields.grf2d(64, 72, seed=61), dict(eb_rel=1e-4, m=8)),
+    (lambda: fields.grf2d(301, 203, seed=62), dict(eb_rel=1e-4, m=0)),
+    (lambda: fields.blobs3d(19, 70, 37, seed=63, nblobs=8), dict(eb_rel=1e-4, m=0)),
+    (lambda: fields.grf2d(1, 900, seed=64).reshape(900), dict(eb_rel=1e-3, m=8)),
+    (lambda: fields.blobs3d(5, 33, 44, seed=65, nblobs=4), dict(mode=0, eb_abs=1e-3, m=6)),
+    (lambda: fields.grf2d(97, 140, seed=66), dict(eb_rel=1e-4, layers=2, m=0)),
+    (lambda: fields.blobs3d(21, 45, 36, seed=67, nblobs=6), dict(eb_rel=1e-5, layers=2, m=0)),
+    (lambda: fields.grf2d(700, 130, seed=68), dict(eb_rel=1e-3, m=0)),
+]
+
+
+def _run(ctx, szo, graphs, reps):
+    import torch
+    xs = [np.ascontiguousarray(g()) for g, _ in MIX]
+    kws = [kw for _, kw in MIX]
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    refs = [szo.compress(x, want_aux=True, **kw) for x, kw in zip(xs, kws)]
+    ctx.set_graphs(graphs)
+    for _ in range(reps):  # the second call replays the captured graph
+        streams, stats = ctx.compress_batch(xd, kws)
+        for i, (s, (sref, rec, _)) in enumerate(zip(streams, refs)):
+            sg = s.cpu().numpy()
+            assert sg.size == sref.size, "field %d: stream length %d vs %d" % (i, sg.size, sref.size)
+            assert np.array_equal(sg, sref), "field %d: stream bytes differ" % i
+            assert stats[i].stream_bytes == sref.size
+        ys = ctx.decompress_batch(streams)
+        for i, (y, (_, rec, _)) in enumerate(zip(ys, refs)):
+            assert np.array_equal(_bits(y.cpu().numpy()), _bits(rec)), "field %d: reconstruction differs" % i
+    ctx.set_graphs(True)
+
+
+def test_batch_graph(ctx, szo):
+    _run(ctx, szo, graphs=True, reps=2)
+
+
+def test_batch_direct(ctx, szo):
+    _run(ctx, szo, graphs=False, reps=1)
+
+
+def test_batch_matches_single(ctx):
+    import torch
+    x = [torch.from_numpy(fields.grf2d(256, 256, seed=1)).cuda(),
+         torch.from_numpy(fields.blobs3d(12, 36, 40, seed=38, nblobs=6)).cuda()]
+    kw = dict(eb_rel=1e-4, m=0)
+    sb, _ = ctx.compress_batch(x, kw)
+    for xi, si in zip(x, sb):
+        s1, _ = ctx.compress(xi, **kw)
+        assert torch.equal(s1.cpu(), si.cpu())
+
+
+def test_batch_error_reporting(ctx):
+    import torch
+    from paper_1706_03791_gb300 import szgb
+    good = torch.from_numpy(fields.grf2d(40, 50, seed=70)).cuda()
+    bad = good.clone()
+    bad[3, 7] = float("nan")
+    with pytest.raises(szgb.SzgbError) as e:
+        ctx.compress_batch([good, bad], dict(eb_rel=1e-4, m=8))
+    assert e.value.code == szgb.ENONFINITE
+    # the context stays usable
+    s, _ = ctx.compress_batch([good], dict(eb_rel=1e-4, m=8))
+    assert s[0].numel() > 128
