@@ -17,6 +17,14 @@ import os
 import numpy as np
 
 
+try:  # multithreaded FFTs (the same transform as numpy.fft)
+    import scipy.fft as _fft
+    _WORKERS = os.cpu_count() or 1
+except ImportError:  # pragma: no cover
+    _fft = None
+    _WORKERS = 1
+
+
 def sha256(a: np.ndarray) -> str:
     return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
 
@@ -29,7 +37,7 @@ def _spectral_noise(rng: np.random.Generator, shape, slope: float) -> np.ndarray
     with zero mean and unit standard deviation.
     """
     white = rng.standard_normal(shape)
-    f = np.fft.rfftn(white)
+    f = _fft.rfftn(white, workers=_WORKERS)
     ks = [np.fft.fftfreq(s) for s in shape[:-1]] + [np.fft.rfftfreq(shape[-1])]
     k2 = np.zeros(f.shape, dtype=np.float64)
     for ax, k in enumerate(ks):
@@ -39,7 +47,7 @@ def _spectral_noise(rng: np.random.Generator, shape, slope: float) -> np.ndarray
     k2.flat[0] = 1.0
     f *= k2 ** (-slope / 4.0)
     f.flat[0] = 0.0
-    g = np.fft.irfftn(f, s=shape, axes=tuple(range(len(shape))))
+    g = _fft.irfftn(f, s=shape, axes=tuple(range(len(shape))), workers=_WORKERS)
     g -= g.mean()
     sd = g.std()
     return g / sd if sd > 0 else g
@@ -123,6 +131,29 @@ def climate_batch(nfields: int = 79, n0: int = 1800, n1: int = 3600,
     for i in range(nfields):
         out.append(climate2d(seed0 + i, n0, n1, mask=i in masked,
                              front=i in fronts))
+    return out
+
+
+def uneven_batch(nfields: int = 512, seed: int = 4, seed0: int = 4000,
+                 side2=(64, 2048), side3=(32, 256), ebs=(1e-3, 1e-4, 1e-5)) -> list:
+    """The uneven batch: half 2D fields with side log-uniform in side2, half
+    3D fields with side log-uniform in side3 (sizes and bounds drawn from
+    `seed`), each a k^-3 Gaussian random field scaled to range 1 (field i
+    from seed seed0 + i), with a value-range-relative bound drawn from
+    `ebs`.  Returns a list of (array, eb_rel)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(nfields):
+        if i % 2 == 0:
+            n = int(round(np.exp(rng.uniform(np.log(side2[0]), np.log(side2[1])))))
+            shape = (n, n)
+        else:
+            n = int(round(np.exp(rng.uniform(np.log(side3[0]), np.log(side3[1])))))
+            shape = (n, n, n)
+        eb = float(ebs[int(rng.integers(0, len(ebs)))])
+        g = _spectral_noise(np.random.default_rng(seed0 + i), shape, 3.0)
+        g = (g - g.min()) / max(g.max() - g.min(), 1e-30)
+        out.append((g.astype(np.float32), eb))
     return out
 
 
