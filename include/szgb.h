@@ -79,6 +79,7 @@ typedef struct {
     uint32_t nsym;          /* quantization codes in use */
     float eb_f;             /* effective bound: largest float <= eb */
     float xmin, xmax;       /* value range of the input */
+    int status;             /* 0, or this field's SZGB_E* code (batches) */
 } szgb_stats;
 
 /* Creates a context on CUDA device `device` that keeps at most
@@ -157,13 +158,59 @@ int szgb_compress_batch(szgb_ctx *ctx, int count, const float *const *data_dev,
 
 /* Batched decompression: stream i (in_dev[i], in_len[i] bytes, 4-byte
  * aligned) into out_dev[i] (out_cap_elems[i] floats, 16-byte aligned), all
- * device memory; one persistent wavefront launch as above. */
+ * device memory; one persistent wavefront launch as above.  opt_status is
+ * NULL or receives count per-field codes. */
 int szgb_decompress_batch(szgb_ctx *ctx, int count, const uint8_t *const *in_dev,
                           const size_t *in_len, float *const *out_dev,
-                          const size_t *out_cap_elems);
+                          const size_t *out_cap_elems, int *opt_status);
 
 /* Capture batches in CUDA graphs (1, the default) or launch them directly (0). */
 int szgb_set_graphs(szgb_ctx *ctx, int on);
+
+/* ---- serving loop ------------------------------------------------------
+ * Requests are taken as they arrive and run by worker threads, each with its
+ * own context and stream, so that batches overlap on the device.  A worker
+ * admits the oldest pending requests whose device footprint (input + output
+ * + a scratch estimate) fits in the memory budget beside the requests in
+ * flight, at most max_batch at a time, and runs them as one batched
+ * compression and one batched decompression (continuous batching: requests
+ * arriving meanwhile join the next batch).  Buffers and codebook tables stay
+ * resident between batches.  The result of every request equals the result
+ * of the single-field call. */
+#define SZGB_OP_COMPRESS 0
+#define SZGB_OP_DECOMPRESS 1
+
+typedef struct szgb_server szgb_server;
+
+typedef struct {
+    int op;              /* SZGB_OP_COMPRESS or SZGB_OP_DECOMPRESS */
+    const void *in;      /* host: the FP32 array (compress) or the stream (decompress) */
+    size_t in_bytes;     /* bytes of `in` (compress: 4 x points of params.shape) */
+    szgb_params params;  /* compress: shape, bound, n, m (ignored for decompress) */
+    void *out;           /* host: room for the stream (compress) or the FP32 array */
+    size_t out_cap;      /* bytes of `out` */
+} szgb_request;
+
+/* Creates a server on CUDA device `device` with `workers` worker threads
+ * (1..16), admitting at most `device_mem_budget` bytes of request footprint
+ * at a time and at most `max_batch` requests per batch. */
+int szgb_server_create(szgb_server **out, int device, size_t device_mem_budget,
+                       int workers, int max_batch);
+/* Queues a request; the caller keeps `in` and `out` valid and untouched
+ * until the request is done.  *ticket identifies it.  SZGB_EBUDGET when the
+ * request alone exceeds the budget. */
+int szgb_submit(szgb_server *srv, const szgb_request *req, uint64_t *ticket);
+/* Non-blocking: *done = 1 once the request finished; then *status (its
+ * SZGB_E* code) and *out_len (stream bytes, or 4 x points) are set and the
+ * ticket is released. */
+int szgb_poll(szgb_server *srv, uint64_t ticket, int *done, int *status, size_t *out_len);
+/* Blocks until the request finished; then as szgb_poll with *done = 1. */
+int szgb_wait(szgb_server *srv, uint64_t ticket, int *status, size_t *out_len);
+/* Batches run, requests completed, and the peak admitted footprint. */
+int szgb_server_stats(szgb_server *srv, uint64_t *batches, uint64_t *completed,
+                      size_t *peak_reserved);
+/* Finishes the pending requests, stops the workers and frees the server. */
+void szgb_server_destroy(szgb_server *srv);
 
 /* Reads the header of a stream held in host memory: parameters (with the
  * m actually used) and the number of unpredictable points. */

@@ -329,6 +329,7 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
         stats->eb_f = hs.eb_f;
         stats->xmin = hs.xmin;
         stats->xmax = hs.xmax;
+        stats->status = SZGB_OK;
     }
     return SZGB_OK;
 }
@@ -790,6 +791,7 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
             stats[f].eb_f = hs.eb_f;
             stats[f].xmin = hs.xmin;
             stats[f].xmax = hs.xmax;
+            stats[f].status = r;
         }
     }
     return first;
@@ -810,7 +812,7 @@ struct DecPlan {
 };
 
 int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, const size_t* in_len,
-                          float* const* out, const size_t* out_cap) {
+                          float* const* out, const size_t* out_cap, int* status) {
     if (!c || count < 1 || !in || !in_len || !out || !out_cap) return SZGB_EINVAL;
     if (cudaSetDevice(c->device) != cudaSuccess) return SZGB_ECUDA;
     int rc = ensure_aux(c);
@@ -965,6 +967,7 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
         int r = dev_errors(hs);
         if (r == SZGB_OK && hs.payload != P[f].H.payload) r = SZGB_ECORRUPT;
         if (r && !first) first = r;
+        if (status) status[f] = r;
     }
     return first;
 }
@@ -1034,8 +1037,8 @@ int szgb_compress_batch(szgb_ctx* c, int count, const float* const* data_dev, co
 }
 
 int szgb_decompress_batch(szgb_ctx* c, int count, const uint8_t* const* in_dev, const size_t* in_len,
-                          float* const* out_dev, const size_t* out_cap_elems) {
-    return decompress_batch_impl(c, count, in_dev, in_len, out_dev, out_cap_elems);
+                          float* const* out_dev, const size_t* out_cap_elems, int* opt_status) {
+    return decompress_batch_impl(c, count, in_dev, in_len, out_dev, out_cap_elems, opt_status);
 }
 
 int szgb_set_graphs(szgb_ctx* c, int on) {

@@ -1,0 +1,342 @@
+// szgb_server.cu -- serving loop: compress / decompress requests taken as they
+// arrive, admitted by a device-memory budget, run as batches on several
+// worker contexts whose work overlaps on the GPU (continuous batching).
+//
+// Every worker thread owns a library context (its own stream, device scratch
+// and codebook tables, all kept resident between batches) and a resident
+// device I/O arena.  A worker takes the oldest pending requests that fit in
+// the budget (at most max_batch), copies their host inputs to the device,
+// runs one batched compression and one batched decompression, copies the
+// results back and completes the requests.  Requests that arrive while a
+// batch is on the GPU wait for the next free worker; with several workers,
+// the copies and kernels of different batches overlap.  A request's result
+// is exactly the result of the single-field calls: batches change the
+// schedule, never the bits.
+#include <string.h>
+
+#include <algorithm>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/szgb.h"
+
+namespace {
+
+size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
+constexpr int kNoStatus = -1000;  // a batch call returned before reaching the field
+
+struct Req {
+    szgb_request r;
+    uint64_t ticket = 0;
+    uint64_t n_points = 0;
+    size_t dev_in = 0, dev_out = 0;  // device bytes of input and output
+    size_t need = 0;                  // admitted bytes (I/O + scratch estimate)
+    int status = SZGB_OK;
+    size_t out_len = 0;
+    bool done = false;
+};
+
+}  // namespace
+
+struct szgb_server {
+    int device = 0;
+    size_t budget = 0;
+    int max_batch = 64;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Req*> pending;
+    std::unordered_map<uint64_t, Req*> reqs;
+    uint64_t next_ticket = 1;
+    size_t reserved = 0, peak_reserved = 0;
+    uint64_t batches = 0, completed = 0;
+    bool stop = false;
+    std::vector<std::thread> workers;
+};
+
+namespace {
+
+// device scratch the library needs for one field, beyond its I/O buffers
+// (codes 2 B/pt, halos, per-row tables; Huffman tables 3.6 MB per field)
+size_t scratch_estimate(int op, uint64_t n_points) {
+    if (op == SZGB_OP_COMPRESS) return (size_t)(2.3 * (double)n_points) + (4u << 20);
+    return (size_t)(0.3 * (double)n_points) + (1u << 20);
+}
+
+void run_batch(szgb_server* S, szgb_ctx* ctx, cudaStream_t st, void*& dbuf, size_t& dcap,
+               std::vector<Req*>& batch) {
+    // device I/O layout of the batch
+    std::vector<size_t> off_in(batch.size()), off_out(batch.size());
+    size_t total = 0;
+    for (size_t i = 0; i < batch.size(); i++) {
+        off_in[i] = total;
+        total += up256(batch[i]->dev_in);
+        off_out[i] = total;
+        total += up256(batch[i]->dev_out);
+    }
+    if (total > dcap) {
+        if (dbuf) cudaFree(dbuf);
+        dbuf = nullptr;
+        dcap = 0;
+        size_t cap = up256(total + total / 4);
+        if (cudaMalloc(&dbuf, cap) != cudaSuccess) {
+            cudaGetLastError();
+            for (Req* q : batch) q->status = SZGB_ENOMEM;
+            return;
+        }
+        dcap = cap;
+    }
+    char* D = static_cast<char*>(dbuf);
+    for (size_t i = 0; i < batch.size(); i++) {
+        if (cudaMemcpyAsync(D + off_in[i], batch[i]->r.in, batch[i]->r.in_bytes, cudaMemcpyHostToDevice, st) !=
+            cudaSuccess) {
+            for (Req* q : batch) q->status = SZGB_ECUDA;
+            return;
+        }
+    }
+    // one batched call per operation
+    std::vector<size_t> ci, di;
+    for (size_t i = 0; i < batch.size(); i++) (batch[i]->r.op == SZGB_OP_COMPRESS ? ci : di).push_back(i);
+    if (!ci.empty()) {
+        const int n = (int)ci.size();
+        std::vector<const float*> in(n);
+        std::vector<szgb_params> prm(n);
+        std::vector<uint8_t*> out(n);
+        std::vector<size_t> cap(n), len(n);
+        std::vector<szgb_stats> sts(n);
+        for (auto& x : sts) x.status = kNoStatus;
+        for (int k = 0; k < n; k++) {
+            const size_t i = ci[k];
+            in[k] = reinterpret_cast<const float*>(D + off_in[i]);
+            prm[k] = batch[i]->r.params;
+            out[k] = reinterpret_cast<uint8_t*>(D + off_out[i]);
+            cap[k] = batch[i]->dev_out;
+        }
+        int rc = szgb_compress_batch(ctx, n, in.data(), prm.data(), out.data(), cap.data(), len.data(), sts.data());
+        for (int k = 0; k < n; k++) {
+            Req* q = batch[ci[k]];
+            // a per-field code when the batch reached its fields, else the call's
+            q->status = sts[k].status != kNoStatus ? sts[k].status : (rc ? rc : SZGB_ECUDA);
+            q->out_len = len[k];
+            if (q->status == SZGB_OK && len[k] > q->r.out_cap) q->status = SZGB_ETRUNC;
+            if (q->status == SZGB_OK &&
+                cudaMemcpyAsync(q->r.out, D + off_out[ci[k]], len[k], cudaMemcpyDeviceToHost, st) != cudaSuccess)
+                q->status = SZGB_ECUDA;
+        }
+    }
+    if (!di.empty()) {
+        const int n = (int)di.size();
+        std::vector<const uint8_t*> in(n);
+        std::vector<size_t> inl(n), cap(n);
+        std::vector<float*> out(n);
+        std::vector<int> sts(n, kNoStatus);
+        for (int k = 0; k < n; k++) {
+            const size_t i = di[k];
+            in[k] = reinterpret_cast<const uint8_t*>(D + off_in[i]);
+            inl[k] = batch[i]->r.in_bytes;
+            out[k] = reinterpret_cast<float*>(D + off_out[i]);
+            cap[k] = batch[i]->n_points;
+        }
+        int rc = szgb_decompress_batch(ctx, n, in.data(), inl.data(), out.data(), cap.data(), sts.data());
+        for (int k = 0; k < n; k++) {
+            Req* q = batch[di[k]];
+            q->status = sts[k] != kNoStatus ? sts[k] : (rc ? rc : SZGB_ECUDA);
+            q->out_len = q->n_points * 4;
+            if (q->status == SZGB_OK &&
+                cudaMemcpyAsync(q->r.out, D + off_out[di[k]], q->out_len, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+                q->status = SZGB_ECUDA;
+        }
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess)
+        for (Req* q : batch) q->status = SZGB_ECUDA;
+}
+
+void worker_main(szgb_server* S) {
+    cudaSetDevice(S->device);
+    szgb_ctx* ctx = nullptr;
+    cudaStream_t st = nullptr;
+    int init_rc = szgb_create(&ctx, S->device, 0);
+    if (init_rc == SZGB_OK && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+        init_rc = SZGB_ECUDA;
+    if (init_rc == SZGB_OK) {
+        szgb_set_stream(ctx, st);
+        szgb_set_graphs(ctx, 0);  // every batch differs: launch directly
+    }
+    void* dbuf = nullptr;
+    size_t dcap = 0;
+    for (;;) {
+        std::vector<Req*> batch;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            for (;;) {
+                if (S->stop && S->pending.empty()) break;
+                // the oldest requests that fit in the budget, in arrival order
+                while (!S->pending.empty() && (int)batch.size() < S->max_batch) {
+                    Req* q = S->pending.front();
+                    if (S->reserved + q->need > S->budget) break;
+                    S->reserved += q->need;
+                    S->peak_reserved = std::max(S->peak_reserved, S->reserved);
+                    batch.push_back(q);
+                    S->pending.pop_front();
+                }
+                if (!batch.empty()) break;
+                S->cv_work.wait(lk);
+            }
+            if (batch.empty()) break;  // stopping, nothing pending
+        }
+        if (init_rc != SZGB_OK) {
+            for (Req* q : batch) q->status = init_rc;
+        } else {
+            run_batch(S, ctx, st, dbuf, dcap, batch);
+        }
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            for (Req* q : batch) {
+                q->done = true;
+                S->reserved -= q->need;
+            }
+            S->batches++;
+            S->completed += batch.size();
+        }
+        S->cv_done.notify_all();
+        S->cv_work.notify_all();  // memory came free
+    }
+    if (dbuf) cudaFree(dbuf);
+    if (ctx) szgb_destroy(ctx);
+    if (st) cudaStreamDestroy(st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int szgb_server_create(szgb_server** out, int device, size_t device_mem_budget, int workers, int max_batch) {
+    if (!out || workers < 1 || workers > 16 || max_batch < 1 || device_mem_budget == 0) return SZGB_EINVAL;
+    *out = nullptr;
+    szgb_server* S = new (std::nothrow) szgb_server();
+    if (!S) return SZGB_ENOMEM;
+    S->device = device;
+    S->budget = device_mem_budget;
+    S->max_batch = max_batch;
+    for (int i = 0; i < workers; i++) S->workers.emplace_back(worker_main, S);
+    *out = S;
+    return SZGB_OK;
+}
+
+int szgb_submit(szgb_server* S, const szgb_request* r, uint64_t* ticket) {
+    if (!S || !r || !ticket || !r->in || !r->out) return SZGB_EINVAL;
+    Req* q = new (std::nothrow) Req();
+    if (!q) return SZGB_ENOMEM;
+    q->r = *r;
+    if (r->op == SZGB_OP_COMPRESS) {
+        const szgb_params& p = r->params;
+        if (p.ndim < 1 || p.ndim > 3) {
+            delete q;
+            return SZGB_EINVAL;
+        }
+        uint64_t n = 1;
+        for (int a = 0; a < p.ndim; a++) n *= p.shape[a];
+        const size_t bound = szgb_compress_bound(&p);
+        if (bound == 0 || r->in_bytes != n * 4) {
+            delete q;
+            return SZGB_EINVAL;
+        }
+        q->n_points = n;
+        q->dev_in = r->in_bytes;
+        // the stream is written on the device first; it may not exceed the
+        // caller's capacity (SZGB_ETRUNC reports the size needed)
+        q->dev_out = std::min(bound, std::max(r->out_cap, (size_t)4096));
+    } else if (r->op == SZGB_OP_DECOMPRESS) {
+        szgb_params p;
+        uint64_t k = 0;
+        int rc = szgb_stream_info(static_cast<const uint8_t*>(r->in), r->in_bytes, &p, &k);
+        if (rc) {
+            delete q;
+            return rc;
+        }
+        uint64_t n = 1;
+        for (int a = 0; a < p.ndim; a++) n *= p.shape[a];
+        if (r->out_cap < n * 4) {
+            delete q;
+            return SZGB_EINVAL;
+        }
+        q->n_points = n;
+        q->dev_in = r->in_bytes;
+        q->dev_out = n * 4;
+    } else {
+        delete q;
+        return SZGB_EINVAL;
+    }
+    q->need = up256(q->dev_in) + up256(q->dev_out) + scratch_estimate(r->op, q->n_points);
+    if (q->need > S->budget) {
+        delete q;
+        return SZGB_EBUDGET;
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        q->ticket = S->next_ticket++;
+        S->reqs[q->ticket] = q;
+        S->pending.push_back(q);
+        *ticket = q->ticket;
+    }
+    S->cv_work.notify_one();
+    return SZGB_OK;
+}
+
+int szgb_poll(szgb_server* S, uint64_t ticket, int* done, int* status, size_t* out_len) {
+    if (!S || !done) return SZGB_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return SZGB_EINVAL;
+    Req* q = it->second;
+    *done = q->done ? 1 : 0;
+    if (q->done) {
+        if (status) *status = q->status;
+        if (out_len) *out_len = q->out_len;
+        S->reqs.erase(it);
+        delete q;
+    }
+    return SZGB_OK;
+}
+
+int szgb_wait(szgb_server* S, uint64_t ticket, int* status, size_t* out_len) {
+    if (!S) return SZGB_EINVAL;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return SZGB_EINVAL;
+    Req* q = it->second;
+    S->cv_done.wait(lk, [&] { return q->done; });
+    if (status) *status = q->status;
+    if (out_len) *out_len = q->out_len;
+    S->reqs.erase(it);
+    delete q;
+    return SZGB_OK;
+}
+
+int szgb_server_stats(szgb_server* S, uint64_t* batches, uint64_t* completed, size_t* peak_reserved) {
+    if (!S) return SZGB_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (batches) *batches = S->batches;
+    if (completed) *completed = S->completed;
+    if (peak_reserved) *peak_reserved = S->peak_reserved;
+    return SZGB_OK;
+}
+
+void szgb_server_destroy(szgb_server* S) {
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    for (auto& t : S->workers) t.join();
+    for (auto& kv : S->reqs) delete kv.second;
+    delete S;
+}
+
+}  // extern "C"

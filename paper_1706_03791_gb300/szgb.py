@@ -37,10 +37,18 @@ class Params(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("n_points", C.c_uint64), ("n_unpred", C.c_uint64), ("stream_bytes", C.c_uint64),
                 ("m", C.c_int), ("maxlen", C.c_int), ("nsym", C.c_uint32), ("eb_f", C.c_float),
-                ("xmin", C.c_float), ("xmax", C.c_float)]
+                ("xmin", C.c_float), ("xmax", C.c_float), ("status", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+OP_COMPRESS, OP_DECOMPRESS = 0, 1
+
+
+class Request(C.Structure):
+    _fields_ = [("op", C.c_int), ("in_", C.c_void_p), ("in_bytes", C.c_size_t), ("params", Params),
+                ("out", C.c_void_p), ("out_cap", C.c_size_t)]
 
 
 _lib = None
@@ -76,8 +84,15 @@ def lib():
         L.szgb_compress_batch.argtypes = [vp, C.c_int, C.POINTER(vp), C.POINTER(Params), C.POINTER(vp),
                                           C.POINTER(sz), C.POINTER(sz), C.POINTER(Stats)]
         L.szgb_decompress_batch.argtypes = [vp, C.c_int, C.POINTER(vp), C.POINTER(sz), C.POINTER(vp),
-                                            C.POINTER(sz)]
+                                            C.POINTER(sz), C.POINTER(C.c_int)]
         L.szgb_set_graphs.argtypes = [vp, C.c_int]
+        L.szgb_server_create.argtypes = [C.POINTER(vp), C.c_int, sz, C.c_int, C.c_int]
+        L.szgb_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]
+        L.szgb_poll.argtypes = [vp, C.c_uint64, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(sz)]
+        L.szgb_wait.argtypes = [vp, C.c_uint64, C.POINTER(C.c_int), C.POINTER(sz)]
+        L.szgb_server_stats.argtypes = [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(sz)]
+        L.szgb_server_destroy.argtypes = [vp]
+        L.szgb_server_destroy.restype = None
         L.szgb_strerror.argtypes = [C.c_int]
         L.szgb_strerror.restype = C.c_char_p
         _lib = L
@@ -92,7 +107,9 @@ def strerror(code: int) -> str:
 EXPORTS = ["szgb_create", "szgb_destroy", "szgb_set_stream", "szgb_compress_bound", "szgb_compress",
            "szgb_compress_trace", "szgb_decompress", "szgb_stream_info", "szgb_set_profiling",
            "szgb_num_phases", "szgb_phase_name", "szgb_phase_times", "szgb_strerror",
-           "szgb_decompress_noalloc", "szgb_compress_batch", "szgb_decompress_batch", "szgb_set_graphs"]
+           "szgb_decompress_noalloc", "szgb_compress_batch", "szgb_decompress_batch", "szgb_set_graphs",
+           "szgb_server_create", "szgb_submit", "szgb_poll", "szgb_wait", "szgb_server_stats",
+           "szgb_server_destroy"]
 
 
 def make_params(shape, mode=REL, eb_abs=0.0, eb_rel=1e-4, layers=1, m=0, theta=0.99) -> Params:
@@ -296,7 +313,7 @@ class Context:
         il = (C.c_size_t * n)(*[s.numel() for s in streams])
         op = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
         oc = (C.c_size_t * n)(*[o.numel() for o in outs])
-        rc = lib().szgb_decompress_batch(self._h, n, ip, il, op, oc)
+        rc = lib().szgb_decompress_batch(self._h, n, ip, il, op, oc, None)
         if rc:
             raise SzgbError(rc, "szgb_decompress_batch")
         return outs
@@ -323,3 +340,84 @@ def decompress_noalloc(stream, out, cuda_stream: int = 0) -> int:
     return lib().szgb_decompress_noalloc(C.c_void_p(stream.data_ptr()), stream.numel(),
                                          C.c_void_p(out.data_ptr()), out.numel(),
                                          C.c_void_p(cuda_stream or 0))
+
+
+class Server:
+    """The serving loop (szgb_server_*): host buffers in, host buffers out.
+    The buffers of a request are kept referenced here until it is done."""
+
+    def __init__(self, device: int = 0, budget: int = 100 << 30, workers: int = 2, max_batch: int = 64):
+        self._h = C.c_void_p()
+        rc = lib().szgb_server_create(C.byref(self._h), int(device), int(budget), int(workers), int(max_batch))
+        if rc:
+            raise SzgbError(rc, "szgb_server_create")
+        self._keep = {}
+
+    def close(self):
+        if self._h:
+            lib().szgb_server_destroy(self._h)
+            self._h = C.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _submit(self, req, keep):
+        t = C.c_uint64()
+        rc = lib().szgb_submit(self._h, C.byref(req), C.byref(t))
+        if rc:
+            raise SzgbError(rc, "szgb_submit")
+        self._keep[t.value] = keep
+        return t.value
+
+    def submit_compress(self, x: np.ndarray, out: np.ndarray, **kw) -> int:
+        """Queue compression of the host float32 array `x` into the host uint8
+        array `out`; returns the ticket."""
+        assert x.dtype == np.float32 and x.flags.c_contiguous and out.dtype == np.uint8
+        r = Request()
+        r.op = OP_COMPRESS
+        r.in_ = x.ctypes.data
+        r.in_bytes = x.nbytes
+        r.params = make_params(x.shape, **kw)
+        r.out = out.ctypes.data
+        r.out_cap = out.nbytes
+        return self._submit(r, (x, out))
+
+    def submit_decompress(self, stream: np.ndarray, out: np.ndarray) -> int:
+        """Queue decompression of the host stream into the host float32 array `out`."""
+        assert stream.dtype == np.uint8 and out.dtype == np.float32 and out.flags.c_contiguous
+        r = Request()
+        r.op = OP_DECOMPRESS
+        r.in_ = stream.ctypes.data
+        r.in_bytes = stream.nbytes
+        r.out = out.ctypes.data
+        r.out_cap = out.nbytes
+        return self._submit(r, (stream, out))
+
+    def poll(self, ticket: int):
+        """(done, status, out_len); status and out_len are None until done."""
+        d, st, n = C.c_int(), C.c_int(), C.c_size_t()
+        rc = lib().szgb_poll(self._h, C.c_uint64(ticket), C.byref(d), C.byref(st), C.byref(n))
+        if rc:
+            raise SzgbError(rc, "szgb_poll")
+        if d.value:
+            self._keep.pop(ticket, None)
+            return True, st.value, n.value
+        return False, None, None
+
+    def wait(self, ticket: int):
+        """(status, out_len) once the request is done."""
+        st, n = C.c_int(), C.c_size_t()
+        rc = lib().szgb_wait(self._h, C.c_uint64(ticket), C.byref(st), C.byref(n))
+        if rc:
+            raise SzgbError(rc, "szgb_wait")
+        self._keep.pop(ticket, None)
+        return st.value, n.value
+
+    def stats(self) -> dict:
+        b, c_, p = C.c_uint64(), C.c_uint64(), C.c_size_t()
+        lib().szgb_server_stats(self._h, C.byref(b), C.byref(c_), C.byref(p))
+        return {"batches": b.value, "completed": c_.value, "peak_reserved": p.value}

@@ -1,0 +1,64 @@
+"""Host-side behaviour of the serving loop (no GPU needed): argument checks,
+budget admission, tickets, and that every request completes -- on a machine
+without a GPU the workers cannot create a context and complete every request
+with SZGB_ECUDA, which exercises the queue and completion path."""
+import numpy as np
+import pytest
+
+
+@pytest.fixture(scope="module")
+def szgb():
+    from paper_1706_03791_gb300 import build
+    build.build()
+    from paper_1706_03791_gb300 import szgb as m
+    return m
+
+
+def _gpu():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def test_server_arguments(szgb):
+    import ctypes as C
+    h = C.c_void_p()
+    L = szgb.lib()
+    assert L.szgb_server_create(C.byref(h), 0, 0, 1, 4) == szgb.EINVAL      # no budget
+    assert L.szgb_server_create(C.byref(h), 0, 1 << 20, 0, 4) == szgb.EINVAL  # no worker
+    assert L.szgb_server_create(C.byref(h), 0, 1 << 20, 1, 0) == szgb.EINVAL  # no batch
+
+
+def test_server_budget_and_validation(szgb):
+    srv = szgb.Server(0, budget=8 << 20, workers=1, max_batch=4)
+    try:
+        big = np.zeros((1024, 1024), np.float32)          # footprint > 8 MiB
+        with pytest.raises(szgb.SzgbError) as e:
+            srv.submit_compress(big, np.empty(1 << 20, np.uint8), eb_rel=1e-4)
+        assert e.value.code == szgb.EBUDGET
+        bad = np.zeros(100, np.uint8)                      # not a stream
+        with pytest.raises(szgb.SzgbError) as e:
+            srv.submit_decompress(bad, np.empty(10, np.float32))
+        assert e.value.code == szgb.ECORRUPT
+    finally:
+        srv.close()
+
+
+@pytest.mark.skipif(_gpu(), reason="checks the no-GPU completion path")
+def test_server_completes_every_request_without_gpu(szgb):
+    srv = szgb.Server(0, budget=64 << 20, workers=2, max_batch=3)
+    try:
+        xs = [np.random.default_rng(i).standard_normal((40, 50)).astype(np.float32) for i in range(7)]
+        outs = [np.empty(1 << 16, np.uint8) for _ in xs]
+        tickets = [srv.submit_compress(x, o, eb_rel=1e-3) for x, o in zip(xs, outs)]
+        assert len(set(tickets)) == len(tickets)
+        for t in tickets:
+            st, n = srv.wait(t)
+            assert st == szgb.ECUDA
+        assert srv.stats()["completed"] == len(xs)
+        with pytest.raises(szgb.SzgbError):
+            srv.poll(tickets[0])  # released after completion
+    finally:
+        srv.close()
