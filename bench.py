@@ -278,6 +278,113 @@ def run_batch_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """Serving: Poisson arrivals of compress and decompress requests (half
+    each) of 2D fields (side log-uniform in [256, 4096]) and 3D fields (side
+    log-uniform in [64, 512]), k^-3 random fields, rel eb 1e-4, admitted under
+    a 100 GB device-memory budget; host buffers in and out.  Requests draw
+    their field from a seeded pool of fields generated with that recipe.
+    Reports p50/p99 latency (arrival to completion) and sustained GB/s."""
+    import numpy as np
+    import torch
+    from paper_1706_03791_gb300 import build as B
+    B.build()
+    from paper_1706_03791_gb300 import szgb
+    from synthetic import fields
+    rng = np.random.default_rng(5)
+    npool = 24
+    t0 = time.perf_counter()
+    pool = []
+    for i in range(npool):
+        if i % 2 == 0:
+            n = int(round(np.exp(rng.uniform(np.log(256), np.log(4096)))))
+            shape = (n, n)
+        else:
+            n = int(round(np.exp(rng.uniform(np.log(64), np.log(512)))))
+            shape = (n, n, n)
+        g = fields._spectral_noise(np.random.default_rng(5000 + i), shape, 3.0)
+        g = ((g - g.min()) / max(g.max() - g.min(), 1e-30)).astype(np.float32)
+        pool.append(torch.from_numpy(g).pin_memory())
+    gen_s = time.perf_counter() - t0
+    kw = dict(eb_rel=1e-4, layers=1, m=0)
+    # streams of the pool for the decompress requests
+    ctx = szgb.Context(0)
+    streams = []
+    for x in pool:
+        s_, _ = ctx.compress(x.numpy(), **kw)
+        streams.append(torch.from_numpy(np.ascontiguousarray(s_)).pin_memory())
+    ctx.close()
+    # output buffers: a few per pool entry and operation
+    nbuf = 3
+    cbufs = [[torch.empty(x.numel() * 4 + (1 << 16), dtype=torch.uint8).pin_memory() for _ in range(nbuf)] for x in pool]
+    dbufs = [[torch.empty(x.numel(), dtype=torch.float32).pin_memory() for _ in range(nbuf)] for x in pool]
+    free = {(op, i): list(range(nbuf)) for op in "cd" for i in range(npool)}
+    srv = szgb.Server(0, budget=100 << 30, workers=3, max_batch=32)
+    # warm-up: one request of each pool entry and operation
+    for i in range(npool):
+        t = srv.submit_compress(pool[i].numpy(), cbufs[i][0].numpy(), **kw)
+        assert srv.wait(t)[0] == 0
+        t = srv.submit_decompress(streams[i].numpy(), dbufs[i][0].numpy())
+        assert srv.wait(t)[0] == 0
+    nreq = int(args.rate * args.duration)
+    arr = np.cumsum(rng.exponential(1.0 / args.rate, nreq))
+    pick = rng.integers(0, npool, nreq)
+    ops = rng.integers(0, 2, nreq)
+    inflight = {}
+    lat, done_bytes = [], 0
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.1)
+    start = time.perf_counter()
+    k = 0
+    waiting = []  # arrived, no output buffer free yet
+    while k < nreq or inflight or waiting:
+        now = time.perf_counter() - start
+        while k < nreq and arr[k] <= now:
+            waiting.append(k)
+            k += 1
+        still = []
+        for j in waiting:
+            op = "c" if ops[j] == 0 else "d"
+            i = int(pick[j])
+            if not free[(op, i)]:
+                still.append(j)
+                continue
+            b = free[(op, i)].pop()
+            if op == "c":
+                t = srv.submit_compress(pool[i].numpy(), cbufs[i][b].numpy(), **kw)
+            else:
+                t = srv.submit_decompress(streams[i].numpy(), dbufs[i][b].numpy())
+            inflight[t] = (j, op, i, b)
+        waiting = still
+        for t in list(inflight):
+            d, st, n = srv.poll(t)
+            if d:
+                j, op, i, b = inflight.pop(t)
+                assert st == 0, szgb.strerror(st)
+                lat.append(time.perf_counter() - start - arr[j])
+                done_bytes += pool[i].numel() * 4
+                free[(op, i)].append(b)
+        time.sleep(0.0002)
+    wall = time.perf_counter() - start
+    clk = clocks.stop()
+    stats = srv.stats()
+    srv.close()
+    lat_ms = sorted(1e3 * v for v in lat)
+    mean_mb = float(np.mean([pool[int(i)].numel() * 4 for i in pick])) / 1e6
+    line = {"metric": "serving: p50/p99 latency and sustained GB/s of FP32 input at rel eb 1e-4",
+            "value": done_bytes / wall / 1e9, "unit": "GB/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serve-poisson%.0f-%.0fs-2d256-4096-3d64-512-fp32-releb1e-4" % (args.rate, args.duration),
+                       "requests": nreq, "pool_fields": npool, "mean_request_mb": mean_mb,
+                       "offered_gbs": args.rate * mean_mb / 1e3, "budget_gb": 100, "workers": 3,
+                       "max_batch": 32, "io": "pinned host buffers in and out"},
+            "latency_ms": {"p50": pct(lat_ms, 50), "p99": pct(lat_ms, 99), "max": lat_ms[-1]},
+            "batches": stats["batches"], "peak_reserved_gb": stats["peak_reserved"] / 1e9,
+            "wall_s": wall, "clocks": clk, "generate_s": gen_s}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -287,7 +394,9 @@ def main():
     ap.add_argument("--layers", type=int, default=1)
     ap.add_argument("--ebrel", type=float, default=1e-4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="3d", choices=["3d", "climate79", "uneven512"],
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
+    ap.add_argument("--duration", type=float, default=30.0, help="serve: seconds of arrivals")
+    ap.add_argument("--workload", default="3d", choices=["3d", "climate79", "uneven512", "serve"],
                     help="3d: the single 100x500x500 field (default); climate79 / uneven512: "
                          "batched many-field workloads, batched+graph vs one field per call")
     args = ap.parse_args()
@@ -295,6 +404,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serve":
+        return run_serve(args)
     if args.workload != "3d":
         return run_batch_workload(args)
 

@@ -8,6 +8,8 @@
 // weights); a symbol's code length is its leaf depth (one used symbol gets
 // length 1).  Codes are canonical: ordered by (length, symbol), consecutive
 // within a length.
+#include <mutex>
+
 #include "szgb_internal.cuh"
 
 namespace szgb {
@@ -113,33 +115,78 @@ __device__ void canonical_assign(const uint32_t* syms, int n, const uint8_t* len
     }
 }
 
+// block-wide exclusive scan of one value per thread (kCbThreads = 1024)
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_tmp, uint32_t* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_tmp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t t = s_tmp[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        s_tmp[lane] = t;
+    }
+    __syncthreads();
+    const uint32_t ex = (wid ? s_tmp[wid - 1] : 0u) + x - v;
+    *total = s_tmp[31];
+    __syncthreads();
+    return ex;
+}
+
+constexpr int kCbRing = 32768;                   // internal-node weight ring (>= n/2)
+constexpr size_t kCbSmem = 65536 + 4 * kCbRing;  // region A (64 KB) + ring (128 KB)
+
+// Codebook (R6).  Leaves sorted by (frequency, symbol): bitonic sort in shared
+// memory up to 8192 used symbols, else a stable LSD radix sort by frequency of
+// the symbol-ordered list.  The two-queue merge (one thread, the internal
+// nodes in a shared-memory ring: the queue never holds more than n/2 nodes)
+// gives every node its parent; depths follow top-down; canonical codes by
+// (length, symbol).
 __global__ void __launch_bounds__(kCbThreads) k_codebook(const uint32_t* __restrict__ hist, DevState* st,
                                                           uint8_t* len, uint64_t* cw, uint64_t* sortbuf,
                                                           uint32_t* nodebuf) {
-    __shared__ uint64_t s_keys[kSmemSortCap];
+    extern __shared__ __align__(16) unsigned char cb_smem[];
+    uint64_t* s_keys = reinterpret_cast<uint64_t*>(cb_smem);          // region A: 8192 keys
+    uint32_t* s_a32 = reinterpret_cast<uint32_t*>(cb_smem);           // region A: 16384 words
+    uint32_t* s_ring = reinterpret_cast<uint32_t*>(cb_smem + 65536);  // internal weights
+    uint8_t* s_dint = cb_smem + 65536;                                 // internal depths (after the merge)
     __shared__ uint32_t s_wsum[kCbThreads / 32];
-    __shared__ uint32_t s_n;
+    __shared__ uint32_t s_tmp[32];
+    __shared__ uint32_t s_rowbase[16];
+    __shared__ uint32_t s_n, s_maxf, s_maxlen;
     __shared__ uint32_t s_cnt[66];
     __shared__ uint64_t s_first[66];
     if (st->err) return;
+    const int tid = threadIdx.x;
     const int m = st->m;
     const int ntot = 1 << m;
     uint32_t* usedlist = nodebuf;                 // [2^16] used symbols, ascending
     uint32_t* par = nodebuf + 65536;              // [2^17] parent of node
-    uint32_t* dep = nodebuf + 3 * 65536;          // [2^17] depth (overlaps nothing used later)
-    uint64_t* wbuf = sortbuf + 65536;             // [2^17] node weights
+    uint32_t* leafw_g = nodebuf + 3 * 65536;      // [2^16] sorted leaf weights (large alphabets)
+    uint32_t* sortedsym = nodebuf + 4 * 65536;    // [2^16] symbols in leaf order
     // 1. compact the used symbols (ascending) with their keys
-    if (threadIdx.x == 0) s_n = 0;
+    if (tid == 0) {
+        s_n = 0;
+        s_maxf = 0;
+        s_maxlen = 0;
+    }
     __syncthreads();
     for (int base = 0; base < ntot; base += kCbThreads) {
-        int s = base + threadIdx.x;
+        int s = base + tid;
         uint32_t f = s < ntot ? hist[s] : 0u;
         bool u = f > 0;
         unsigned b = __ballot_sync(0xffffffffu, u);
-        int wid = threadIdx.x >> 5, ln = threadIdx.x & 31;
+        int wid = tid >> 5, ln = tid & 31;
         if (ln == 0) s_wsum[wid] = __popc(b);
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             uint32_t acc = s_n;
             for (int w = 0; w < kCbThreads / 32; w++) { uint32_t t = s_wsum[w]; s_wsum[w] = acc; acc += t; }
             s_n = acc;
@@ -149,15 +196,16 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const uint32_t* __restr
             uint32_t pos = s_wsum[wid] + __popc(b & ((1u << ln) - 1u));
             usedlist[pos] = (uint32_t)s;
             sortbuf[pos] = ((uint64_t)f << 16) | (uint64_t)s;
+            atomicMax(&s_maxf, f);
         }
         __syncthreads();
     }
     const int n = (int)s_n;
-    for (int s = threadIdx.x; s < ntot; s += kCbThreads) len[s] = 0;
+    for (int s = tid; s < ntot; s += kCbThreads) len[s] = 0;
     __syncthreads();
     if (n == 0) return;
     if (n == 1) {
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             uint32_t s = usedlist[0];
             len[s] = 1;
             cw[s] = 0;
@@ -166,66 +214,136 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const uint32_t* __restr
         }
         return;
     }
-    // 2. sort keys ascending (frequency, then symbol)
-    int np2 = 1;
-    while (np2 < n) np2 <<= 1;
-    uint64_t* keys;
-    if (np2 <= kSmemSortCap) {
-        keys = s_keys;
-        for (int i = threadIdx.x; i < np2; i += kCbThreads) s_keys[i] = i < n ? sortbuf[i] : ~0ull;
+    // 2. leaves in (frequency, symbol) order: weights to region A (or global), symbols to sortedsym
+    const bool leaves_smem = n <= 16384;
+    if (n <= kSmemSortCap) {
+        int np2 = 1;
+        while (np2 < n) np2 <<= 1;
+        for (int i = tid; i < np2; i += kCbThreads) s_keys[i] = i < n ? sortbuf[i] : ~0ull;
+        __syncthreads();
+        bitonic_sort(s_keys, np2);
+        uint64_t tmp[kSmemSortCap / kCbThreads];
+#pragma unroll
+        for (int k = 0; k < kSmemSortCap / kCbThreads; k++) {
+            const int i = tid + k * kCbThreads;
+            tmp[k] = i < n ? s_keys[i] : 0ull;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kSmemSortCap / kCbThreads; k++) {
+            const int i = tid + k * kCbThreads;
+            if (i < n) {
+                s_a32[i] = (uint32_t)(tmp[k] >> 16);
+                sortedsym[i] = (uint32_t)(tmp[k] & 0xffffu);
+            }
+        }
     } else {
-        keys = sortbuf;
-        for (int i = n + threadIdx.x; i < np2; i += kCbThreads) sortbuf[i] = ~0ull;
+        // stable LSD radix sort by frequency, 4-bit digits, counters [digit][thread] in region A
+        uint64_t* src = sortbuf;
+        uint64_t* dst = sortbuf + 65536;
+        const int chunk = (n + kCbThreads - 1) / kCbThreads;
+        const int lo = min(n, tid * chunk), hi = min(n, lo + chunk);
+        const int bits = 32 - __clz((int)s_maxf);
+        for (int sh = 16; sh < 16 + bits; sh += 4) {
+            for (int d = 0; d < 16; d++) s_a32[d * kCbThreads + tid] = 0;
+            for (int i = lo; i < hi; i++) s_a32[(int)((src[i] >> sh) & 15u) * kCbThreads + tid]++;
+            __syncthreads();
+            for (int d = 0; d < 16; d++) {
+                uint32_t tot;
+                const uint32_t ex = block_excl_scan(s_a32[d * kCbThreads + tid], s_tmp, &tot);
+                s_a32[d * kCbThreads + tid] = ex;
+                if (tid == 0) s_rowbase[d] = tot;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                uint32_t acc = 0;
+                for (int d = 0; d < 16; d++) { uint32_t t = s_rowbase[d]; s_rowbase[d] = acc; acc += t; }
+            }
+            __syncthreads();
+            for (int d = 0; d < 16; d++) s_a32[d * kCbThreads + tid] += s_rowbase[d];
+            __syncthreads();
+            for (int i = lo; i < hi; i++) {
+                const uint64_t key = src[i];
+                const int d = (int)((key >> sh) & 15u);
+                dst[s_a32[d * kCbThreads + tid]++] = key;
+            }
+            __syncthreads();
+            uint64_t* t = src;
+            src = dst;
+            dst = t;
+        }
+        for (int i = tid; i < n; i += kCbThreads) {
+            const uint64_t key = src[i];
+            sortedsym[i] = (uint32_t)(key & 0xffffu);
+            if (leaves_smem) s_a32[i] = (uint32_t)(key >> 16);
+            else leafw_g[i] = (uint32_t)(key >> 16);
+        }
     }
     __syncthreads();
-    bitonic_sort(keys, np2);
-    // 3. two-queue merge (thread 0): leaves 0..n-1, internal nodes n..2n-2
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < n; i++) wbuf[i] = keys[i] >> 16;
+    // 3. two-queue merge (thread 0): leaves 0..n-1, internal nodes n..2n-2;
+    //    a leaf is taken first on equal weight
+    if (tid == 0) {
+        const uint32_t* LW = leaves_smem ? s_a32 : leafw_g;
         int q1 = 0, q2 = n, nxt = n;
-        uint64_t wl = wbuf[0];
+        uint32_t wl = LW[0], wq = 0;
         for (int step = 0; step < n - 1; step++) {
-            int pk[2];
-            uint64_t wsum = 0;
-#pragma unroll
-            for (int p = 0; p < 2; p++) {
-                bool leaf = q1 < n && (q2 >= nxt || wl <= wbuf[q2]);
+            int pk0, pk1;
+            uint32_t w0, w1;
+            {
+                const bool leaf = q1 < n && (q2 >= nxt || wl <= wq);
                 if (leaf) {
-                    pk[p] = q1;
-                    wsum += wl;
-                    q1++;
-                    wl = q1 < n ? wbuf[q1] : 0;
+                    pk0 = q1; w0 = wl; q1++; wl = q1 < n ? LW[q1] : 0u;
                 } else {
-                    pk[p] = q2;
-                    wsum += wbuf[q2];
-                    q2++;
+                    pk0 = q2; w0 = wq; q2++; wq = q2 < nxt ? s_ring[q2 & (kCbRing - 1)] : 0u;
                 }
             }
-            wbuf[nxt] = wsum;
-            par[pk[0]] = (uint32_t)nxt;
-            par[pk[1]] = (uint32_t)nxt;
+            {
+                const bool leaf = q1 < n && (q2 >= nxt || wl <= wq);
+                if (leaf) {
+                    pk1 = q1; w1 = wl; q1++; wl = q1 < n ? LW[q1] : 0u;
+                } else {
+                    pk1 = q2; w1 = wq; q2++; wq = q2 < nxt ? s_ring[q2 & (kCbRing - 1)] : 0u;
+                }
+            }
+            const uint32_t sum = w0 + w1;
+            s_ring[nxt & (kCbRing - 1)] = sum;
+            if (q2 == nxt) wq = sum;  // the queue was empty: the new node is its head
+            par[pk0] = (uint32_t)nxt;
+            par[pk1] = (uint32_t)nxt;
             nxt++;
         }
-        // 4. depths, root = 2n-2, parents always later than children
-        int total = 2 * n - 1;
-        dep[total - 1] = 0;
-        int maxlen = 0;
-        for (int v = total - 2; v >= 0; v--) {
-            int d = (int)dep[par[v]] + 1;
-            dep[v] = (uint32_t)d;
-            if (v < n && d > maxlen) maxlen = d;
-        }
-        for (int i = 0; i < n; i++) len[(uint32_t)(keys[i] & 0xffffu)] = (uint8_t)dep[i];
-        st->nsym = (uint32_t)n;
-        st->maxlen = (uint32_t)maxlen;
     }
     __syncthreads();
+    // 4. depths: internal nodes top-down (parents have larger ids), then leaves
+    const int nint = n - 1;
+    const bool par_smem = nint <= 16384;
+    if (par_smem)
+        for (int i = tid; i < nint; i += kCbThreads) s_a32[i] = par[n + i];
+    __syncthreads();
+    if (tid == 0) {
+        s_dint[nint - 1] = 0;  // the root, node 2n-2
+        for (int v = nint - 2; v >= 0; v--) {
+            const uint32_t p = par_smem ? s_a32[v] : par[n + v];
+            s_dint[v] = (uint8_t)(s_dint[p - (uint32_t)n] + 1);
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += kCbThreads) {
+        const uint32_t d = (uint32_t)s_dint[par[i] - (uint32_t)n] + 1u;
+        len[sortedsym[i]] = (uint8_t)d;
+        atomicMax(&s_maxlen, d);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        st->nsym = (uint32_t)n;
+        st->maxlen = s_maxlen;
+    }
     // 5. canonical codes: first code of each length
-    if (threadIdx.x < 66) s_cnt[threadIdx.x] = 0;
+    if (tid < 66) s_cnt[tid] = 0;
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += kCbThreads) atomicAdd(&s_cnt[len[usedlist[i]]], 1u);
+    for (int i = tid; i < n; i += kCbThreads) atomicAdd(&s_cnt[len[usedlist[i]]], 1u);
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         uint64_t code = 0;
         int prevL = 0;
         bool firstSeen = false;
@@ -244,7 +362,15 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const uint32_t* __restr
 
 int launch_codebook(const uint32_t* hist, DevState* st, uint8_t* len, uint64_t* cw, uint64_t* sortbuf,
                     uint32_t* nodebuf, cudaStream_t s) {
-    k_codebook<<<1, kCbThreads, 0, s>>>(hist, st, len, cw, sortbuf, nodebuf);
+    static std::once_flag once;
+    static bool ok = false;
+    std::call_once(once, [] {
+        ok = cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbSmem) ==
+             cudaSuccess;
+        if (!ok) cudaGetLastError();
+    });
+    if (!ok) return SZGB_ECUDA;
+    k_codebook<<<1, kCbThreads, kCbSmem, s>>>(hist, st, len, cw, sortbuf, nodebuf);
     return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
 }
 

@@ -985,12 +985,35 @@ static bool encode_tiles(CUtensorMap* m, bool f32, const void* base, uint64_t N,
               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The dynamic shared-memory limit of a kernel is raised once, to the device
+// maximum, and never lowered: a per-launch value would race between host
+// threads launching the same kernel with different sizes.
+// (one flag per kernel: the template is instantiated per function)
+template <auto Fn>
+static int smem_limit_once(size_t need) {
+    static std::once_flag once;
+    static int limit = 0;
+    std::call_once(once, [] {
+        int dev = 0, mx = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, Fn) != cudaSuccess) {  // the limit covers static + dynamic
+            cudaGetLastError();
+            return;
+        }
+        const int dyn = mx - (int)fa.sharedSizeBytes;
+        if (cudaFuncSetAttribute(Fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) == cudaSuccess) limit = dyn;
+        else cudaGetLastError();
+    });
+    return (size_t)limit >= need ? 0 : SZGB_ECUDA;
+}
+
 template <int ND, int NL, bool DEC, bool TR>
 static int launch_t(const WaveArgs& a, cudaStream_t s) {
     size_t smem = wave_smem_bytes(a.g, NL, DEC);
     auto fn = k_wave<ND, NL, DEC, TR>;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return SZGB_ECUDA;
+    if (smem_limit_once<k_wave<ND, NL, DEC, TR>>(smem)) return SZGB_ECUDA;
     fn<<<a.g.num_ctas, (a.g.W + 1) * 32, smem, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
 }
@@ -1094,15 +1117,21 @@ int launch_wave_batch(const void* args_dev, const void* order_dev, unsigned tota
     if (grid < 1) grid = 1;
     cudaError_t e;
     if (!decompress) {
-        auto fn = layers == 1 ? k_wave_batch<1, false> : k_wave_batch<2, false>;
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return SZGB_ECUDA;
-        fn<<<grid, block, smem, s>>>(F, order, total, ticket_dev);
+        if (layers == 1) {
+            if (smem_limit_once<k_wave_batch<1, false>>(smem)) return SZGB_ECUDA;
+            k_wave_batch<1, false><<<grid, block, smem, s>>>(F, order, total, ticket_dev);
+        } else {
+            if (smem_limit_once<k_wave_batch<2, false>>(smem)) return SZGB_ECUDA;
+            k_wave_batch<2, false><<<grid, block, smem, s>>>(F, order, total, ticket_dev);
+        }
     } else {
-        auto fn = layers == 1 ? k_wave_batch<1, true> : k_wave_batch<2, true>;
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return SZGB_ECUDA;
-        fn<<<grid, block, smem, s>>>(F, order, total, ticket_dev);
+        if (layers == 1) {
+            if (smem_limit_once<k_wave_batch<1, true>>(smem)) return SZGB_ECUDA;
+            k_wave_batch<1, true><<<grid, block, smem, s>>>(F, order, total, ticket_dev);
+        } else {
+            if (smem_limit_once<k_wave_batch<2, true>>(smem)) return SZGB_ECUDA;
+            k_wave_batch<2, true><<<grid, block, smem, s>>>(F, order, total, ticket_dev);
+        }
     }
     e = cudaGetLastError();
     return e == cudaSuccess ? 0 : SZGB_ECUDA;

@@ -138,3 +138,16 @@ def test_errors(ctx, szo):
     assert e.value.code == szgb.EUNSUPPORTED
     # the context stays usable after errors
     _check(ctx, szo, x, eb_rel=1e-3, m=8)
+
+
+# large alphabets: white noise at a small absolute bound spreads the codes
+# over a 16-bit alphabet (> 8192 used symbols: radix-sorted leaves; > 16384:
+# leaf weights in global memory)
+WIDE = [((300, 300), 1e-4, 91), ((400, 400), 4e-5, 92)]
+
+
+@pytest.mark.parametrize("shape,eb,seed", WIDE, ids=["wide-radix", "wide-global"])
+def test_parity_large_alphabet(ctx, szo, shape, eb, seed):
+    x = np.random.default_rng(seed).random(shape).astype(np.float32)
+    st = _check(ctx, szo, x, mode=0, eb_abs=eb, m=16)
+    assert st.nsym > 8192
