@@ -211,6 +211,10 @@ def run_batch_workload(args):
     outs = [torch.empty(szgb.compress_bound(tuple(x.shape), **kw), dtype=torch.uint8, device=dev)
             for x, kw in zip(xs, kws)]
     ys = [torch.empty_like(x) for x in xs]
+    # autotune the wavefront shape of the batched pass
+    t0 = time.perf_counter()
+    tuned = ctx.autotune_batch(xs, kws, reps=1)
+    tune_s = time.perf_counter() - t0
 
     def batched():
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
@@ -274,6 +278,7 @@ def run_batch_workload(args):
                          "decompress_frac": ((stream_bytes + 4.0 * npts) / (bd / 1e3) / 1e9) / peaks()[0],
                          "note": "algorithmic bytes of the whole pass (compress 6 B/pt + range read; "
                                  "decompress stream + 4 B/pt) over the pass time"},
+            "autotune": {"W": tuned["W"], "pub": tuned["pub"], "seconds": tune_s},
             "clocks": clk, "generate_s": gen_s}
     print(json.dumps(line), flush=True)
 

@@ -164,6 +164,29 @@ int szgb_decompress_batch(szgb_ctx *ctx, int count, const uint8_t *const *in_dev
                           const size_t *in_len, float *const *out_dev,
                           const size_t *out_cap_elems, int *opt_status);
 
+/* Autotuner.  Times compression + decompression of the device field
+ * `data_dev` (params p) for every candidate wavefront shape (warps per CTA:
+ * 2,4,6,8 in 3D, 1,2,4,8 in 1D/2D; progress published every 2, 4 or 8
+ * sweeps), best of `reps` runs each, and keeps the fastest for the field's
+ * shape class (dimension, layers, bit lengths of planes/rows/columns); later
+ * calls on fields of that class use it.  The shape changes the schedule
+ * only: streams and reconstructions are identical for every candidate.
+ * *W_out, *pub_out, *ms_out (may be NULL) receive the choice and its time. */
+int szgb_autotune(szgb_ctx *ctx, const float *data_dev, const szgb_params *p, int reps,
+                  int *W_out, int *pub_out, double *ms_out);
+/* As szgb_autotune for a batch: times szgb_compress_batch +
+ * szgb_decompress_batch of the given device fields for every candidate
+ * shape (warps per CTA 1,2,4,6,8; publication every 2, 4, 8 sweeps) and
+ * keeps the fastest for every shape class in the batch: the shape that is
+ * best for one field alone is often not the one that fills the GPU best
+ * when many fields share it. */
+int szgb_autotune_batch(szgb_ctx *ctx, int count, const float *const *data_dev,
+                        const szgb_params *params, int reps, int *W_out, int *pub_out,
+                        double *ms_out);
+/* Save / load the autotuned table (a small text file). */
+int szgb_tune_save(szgb_ctx *ctx, const char *path);
+int szgb_tune_load(szgb_ctx *ctx, const char *path);
+
 /* Capture batches in CUDA graphs (1, the default) or launch them directly (0). */
 int szgb_set_graphs(szgb_ctx *ctx, int on);
 

@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <vector>
 
 #include "szgb_internal.cuh"
@@ -78,6 +79,13 @@ struct szgb_ctx {
     size_t h_batch_cap = 0;
     bool use_graphs = true;
     BatchGraph g_comp, g_dec;
+    // autotuned wavefront shapes per shape class (see shape_class)
+    struct Tune {
+        int W, pub;
+        double ms;
+    };
+    std::map<uint64_t, Tune> tune;
+    int force_W = 0, force_pub = 0;  // set while the autotuner times a candidate
 };
 
 namespace {
@@ -146,7 +154,25 @@ int check_params(const szgb_params* p, CallParams* cp) {
     return p->layers > kMaxLayers ? SZGB_EUNSUPPORTED : SZGB_OK;
 }
 
+// Shape class of a field for the autotuner: dimension, layers and the bit
+// lengths of the extents that set the wavefront's shape (3D: planes, rows,
+// columns; 1D/2D: rows, columns).
+uint64_t shape_class(const CallParams& cp, int layers) {
+    auto bl = [](uint64_t v) { uint64_t b = 0; while (v) { b++; v >>= 1; } return b; };
+    const uint64_t rows = cp.ndim == 3 ? cp.d1 : cp.d0 * cp.d1;
+    const uint64_t planes = cp.ndim == 3 ? cp.d0 : 1;
+    return ((uint64_t)cp.ndim << 56) | ((uint64_t)layers << 48) | (bl(planes) << 32) | (bl(rows) << 16) | bl(cp.d2);
+}
+
 WaveGeom make_geom(const szgb_ctx* c, const CallParams& cp, int layers) {
+    int W2 = c->W2, W3 = c->W3, pub = c->pub;
+    auto it = c->tune.find(shape_class(cp, layers));
+    if (it != c->tune.end()) {
+        W2 = W3 = it->second.W;
+        pub = it->second.pub;
+    }
+    if (c->force_W) W2 = W3 = c->force_W;
+    if (c->force_pub) pub = c->force_pub;
     WaveGeom g = {};
     g.N = cp.d2;
     g.ntiles = (int)((cp.d2 + kTile - 1) / kTile);
@@ -155,7 +181,7 @@ WaveGeom make_geom(const szgb_ctx* c, const CallParams& cp, int layers) {
         g.ndim = 3;
         g.P = cp.d0;
         g.M = cp.d1;
-        int W = c->W3;
+        int W = W3;
         if ((uint64_t)W > cp.d0) W = (int)cp.d0;
         if (W < 2 * layers) W = 2 * layers;  // the plane halo's rows all have sweeps >= 0
         g.W = W;
@@ -166,7 +192,7 @@ WaveGeom make_geom(const szgb_ctx* c, const CallParams& cp, int layers) {
         g.ndim = cp.ndim;
         g.P = 1;
         g.M = cp.d0 * cp.d1;  // 1D: a single row
-        int W = c->W2;
+        int W = W2;
         int need = (int)((g.M + 31) / 32);
         if (W > need) W = need;
         if (W < 1) W = 1;
@@ -176,7 +202,7 @@ WaveGeom make_geom(const szgb_ctx* c, const CallParams& cp, int layers) {
         g.nsweeps = (int)((cp.d2 - 1 + 31 + 36 * (W - 1)) / 4) + 1;  // last step: column N-1 of warp W-1, lane 31
     }
     g.num_ctas = g.nb0 * g.nb1;
-    g.pub = c->pub;
+    g.pub = pub;
     return g;
 }
 
@@ -1039,6 +1065,181 @@ int szgb_compress_batch(szgb_ctx* c, int count, const float* const* data_dev, co
 int szgb_decompress_batch(szgb_ctx* c, int count, const uint8_t* const* in_dev, const size_t* in_len,
                           float* const* out_dev, const size_t* out_cap_elems, int* opt_status) {
     return decompress_batch_impl(c, count, in_dev, in_len, out_dev, out_cap_elems, opt_status);
+}
+
+int szgb_autotune(szgb_ctx* c, const float* data_dev, const szgb_params* p, int reps, int* W_out, int* pub_out,
+                  double* ms_out) {
+    CallParams cp;
+    if (!c || !data_dev || !p) return SZGB_EINVAL;
+    int rc = check_params(p, &cp);
+    if (rc) return rc;
+    if (cudaSetDevice(c->device) != cudaSuccess) return SZGB_ECUDA;
+    if (reps < 1) reps = 1;
+    const uint64_t N = cp.d0 * cp.d1 * cp.d2;
+    const size_t bound = szgb_compress_bound(p);
+    uint8_t* sbuf = nullptr;
+    float* ybuf = nullptr;
+    cudaEvent_t e0, e1;
+    if (cudaMalloc(&sbuf, bound) != cudaSuccess || cudaMalloc(&ybuf, N * 4) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(sbuf);
+        return SZGB_ENOMEM;
+    }
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int Ws3[] = {2, 4, 6, 8}, Ws2[] = {1, 2, 4, 8}, pubs[] = {2, 4, 8};
+    const int* Ws = cp.ndim == 3 ? Ws3 : Ws2;
+    double best = 1e30;
+    int bW = c->W3, bP = c->pub;
+    const bool prof = c->profiling;
+    c->profiling = false;
+    for (int wi = 0; wi < 4 && !rc; wi++) {
+        if (cp.ndim == 3 && Ws[wi] < 2 * cp.layers) continue;
+        for (int pi = 0; pi < 3 && !rc; pi++) {
+            c->force_W = Ws[wi];
+            c->force_pub = pubs[pi];
+            double tmin = 1e30;
+            for (int r = 0; r <= reps && !rc; r++) {  // the first run warms up
+                size_t olen = 0;
+                cudaEventRecord(e0, c->stream);
+                rc = compress_impl(c, data_dev, 1, p, sbuf, bound, 1, &olen, nullptr, nullptr, nullptr);
+                if (!rc) rc = decompress_impl(c, sbuf, olen, 1, ybuf, N, 1);
+                cudaEventRecord(e1, c->stream);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (r > 0) tmin = std::min(tmin, (double)ms);
+            }
+            if (!rc && tmin < best) {
+                best = tmin;
+                bW = Ws[wi];
+                bP = pubs[pi];
+            }
+        }
+    }
+    c->force_W = c->force_pub = 0;
+    c->profiling = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sbuf);
+    cudaFree(ybuf);
+    if (rc) return rc;
+    c->tune[shape_class(cp, cp.layers)] = szgb_ctx::Tune{bW, bP, best};
+    drop_graph(c->g_comp);  // captured batches used the previous shapes
+    drop_graph(c->g_dec);
+    if (W_out) *W_out = bW;
+    if (pub_out) *pub_out = bP;
+    if (ms_out) *ms_out = best;
+    return SZGB_OK;
+}
+
+int szgb_autotune_batch(szgb_ctx* c, int count, const float* const* data_dev, const szgb_params* params, int reps,
+                        int* W_out, int* pub_out, double* ms_out) {
+    if (!c || count < 1 || !data_dev || !params) return SZGB_EINVAL;
+    if (cudaSetDevice(c->device) != cudaSuccess) return SZGB_ECUDA;
+    if (reps < 1) reps = 1;
+    std::vector<CallParams> cps(count);
+    std::vector<uint8_t*> sb(count, nullptr);
+    std::vector<float*> yb(count, nullptr);
+    std::vector<size_t> cap(count), len(count), ycap(count);
+    int rc = SZGB_OK;
+    bool any3 = false;
+    int maxl = 1;
+    for (int f = 0; f < count && !rc; f++) {
+        rc = check_params(&params[f], &cps[f]);
+        if (rc) break;
+        any3 |= cps[f].ndim == 3;
+        maxl = std::max(maxl, cps[f].layers);
+        cap[f] = szgb_compress_bound(&params[f]);
+        ycap[f] = cps[f].d0 * cps[f].d1 * cps[f].d2;
+        if (cudaMalloc(&sb[f], cap[f]) != cudaSuccess || cudaMalloc(&yb[f], ycap[f] * 4) != cudaSuccess) {
+            cudaGetLastError();
+            rc = SZGB_ENOMEM;
+        }
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const bool graphs = c->use_graphs;
+    c->use_graphs = false;
+    const int Ws[] = {1, 2, 4, 6, 8}, pubs[] = {2, 4, 8};
+    double best = 1e30;
+    int bW = c->W3, bP = c->pub;
+    for (int wi = 0; wi < 5 && !rc; wi++) {
+        if (any3 && Ws[wi] < 2 * maxl) continue;
+        for (int pi = 0; pi < 3 && !rc; pi++) {
+            c->force_W = Ws[wi];
+            c->force_pub = pubs[pi];
+            double tmin = 1e30;
+            for (int r = 0; r <= reps && !rc; r++) {
+                cudaEventRecord(e0, c->stream);
+                rc = compress_batch_impl(c, count, data_dev, params, sb.data(), cap.data(), len.data(), nullptr);
+                if (!rc)
+                    rc = decompress_batch_impl(c, count, sb.data(), len.data(), yb.data(), ycap.data(), nullptr);
+                cudaEventRecord(e1, c->stream);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (r > 0) tmin = std::min(tmin, (double)ms);
+            }
+            if (!rc && tmin < best) {
+                best = tmin;
+                bW = Ws[wi];
+                bP = pubs[pi];
+            }
+        }
+    }
+    c->force_W = c->force_pub = 0;
+    c->use_graphs = graphs;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int f = 0; f < count; f++) {
+        cudaFree(sb[f]);
+        cudaFree(yb[f]);
+    }
+    if (rc) return rc;
+    for (int f = 0; f < count; f++) c->tune[shape_class(cps[f], cps[f].layers)] = szgb_ctx::Tune{bW, bP, best};
+    drop_graph(c->g_comp);
+    drop_graph(c->g_dec);
+    if (W_out) *W_out = bW;
+    if (pub_out) *pub_out = bP;
+    if (ms_out) *ms_out = best;
+    return SZGB_OK;
+}
+
+int szgb_tune_save(szgb_ctx* c, const char* path) {
+    if (!c || !path) return SZGB_EINVAL;
+    FILE* f = fopen(path, "w");
+    if (!f) return SZGB_EINVAL;
+    fprintf(f, "# szgb autotune v1: shape_class W pub ms\n");
+    for (auto& kv : c->tune)
+        fprintf(f, "%016llx %d %d %.6f\n", (unsigned long long)kv.first, kv.second.W, kv.second.pub, kv.second.ms);
+    fclose(f);
+    return SZGB_OK;
+}
+
+int szgb_tune_load(szgb_ctx* c, const char* path) {
+    if (!c || !path) return SZGB_EINVAL;
+    FILE* f = fopen(path, "r");
+    if (!f) return SZGB_EINVAL;
+    char line[256];
+    int rc = SZGB_OK;
+    while (fgets(line, sizeof line, f)) {
+        if (line[0] == '#' || line[0] == '\n') continue;
+        unsigned long long k;
+        int W, pub;
+        double ms;
+        if (sscanf(line, "%llx %d %d %lf", &k, &W, &pub, &ms) != 4 || W < 1 || W > kMaxWaveWarps || pub < 1 ||
+            pub > 64) {
+            rc = SZGB_ECORRUPT;
+            break;
+        }
+        c->tune[(uint64_t)k] = szgb_ctx::Tune{W, pub, ms};
+    }
+    fclose(f);
+    drop_graph(c->g_comp);
+    drop_graph(c->g_dec);
+    return rc;
 }
 
 int szgb_set_graphs(szgb_ctx* c, int on) {

@@ -86,6 +86,12 @@ def lib():
         L.szgb_decompress_batch.argtypes = [vp, C.c_int, C.POINTER(vp), C.POINTER(sz), C.POINTER(vp),
                                             C.POINTER(sz), C.POINTER(C.c_int)]
         L.szgb_set_graphs.argtypes = [vp, C.c_int]
+        L.szgb_autotune.argtypes = [vp, vp, C.POINTER(Params), C.c_int, C.POINTER(C.c_int),
+                                    C.POINTER(C.c_int), C.POINTER(C.c_double)]
+        L.szgb_autotune_batch.argtypes = [vp, C.c_int, C.POINTER(vp), C.POINTER(Params), C.c_int,
+                                          C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]
+        L.szgb_tune_save.argtypes = [vp, C.c_char_p]
+        L.szgb_tune_load.argtypes = [vp, C.c_char_p]
         L.szgb_server_create.argtypes = [C.POINTER(vp), C.c_int, sz, C.c_int, C.c_int]
         L.szgb_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]
         L.szgb_poll.argtypes = [vp, C.c_uint64, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(sz)]
@@ -109,7 +115,7 @@ EXPORTS = ["szgb_create", "szgb_destroy", "szgb_set_stream", "szgb_compress_boun
            "szgb_num_phases", "szgb_phase_name", "szgb_phase_times", "szgb_strerror",
            "szgb_decompress_noalloc", "szgb_compress_batch", "szgb_decompress_batch", "szgb_set_graphs",
            "szgb_server_create", "szgb_submit", "szgb_poll", "szgb_wait", "szgb_server_stats",
-           "szgb_server_destroy"]
+           "szgb_server_destroy", "szgb_autotune", "szgb_autotune_batch", "szgb_tune_save", "szgb_tune_load"]
 
 
 def make_params(shape, mode=REL, eb_abs=0.0, eb_rel=1e-4, layers=1, m=0, theta=0.99) -> Params:
@@ -266,6 +272,43 @@ class Context:
         if rc:
             raise SzgbError(rc, "szgb_decompress")
         return out
+
+    # -- autotuner -----------------------------------------------------------
+    def autotune(self, x, reps: int = 2, **kw) -> dict:
+        """Pick the wavefront shape for the shape class of the CUDA tensor `x`."""
+        p = make_params(tuple(x.shape), **kw)
+        W, pub, ms = C.c_int(), C.c_int(), C.c_double()
+        rc = lib().szgb_autotune(self._h, C.c_void_p(x.data_ptr()), C.byref(p), int(reps), C.byref(W),
+                                 C.byref(pub), C.byref(ms))
+        if rc:
+            raise SzgbError(rc, "szgb_autotune")
+        return {"W": W.value, "pub": pub.value, "ms": ms.value}
+
+    def autotune_batch(self, xs, params, reps: int = 1) -> dict:
+        """Pick one wavefront shape for the batch of CUDA tensors `xs`
+        (timed as batched passes) and keep it for every shape class in it."""
+        n = len(xs)
+        if isinstance(params, dict):
+            params = [params] * n
+        P = (Params * n)()
+        for i, (x, kw) in enumerate(zip(xs, params)):
+            P[i] = make_params(tuple(x.shape), **kw)
+        dp = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+        W, pub, ms = C.c_int(), C.c_int(), C.c_double()
+        rc = lib().szgb_autotune_batch(self._h, n, dp, P, int(reps), C.byref(W), C.byref(pub), C.byref(ms))
+        if rc:
+            raise SzgbError(rc, "szgb_autotune_batch")
+        return {"W": W.value, "pub": pub.value, "ms": ms.value}
+
+    def tune_save(self, path: str):
+        rc = lib().szgb_tune_save(self._h, path.encode())
+        if rc:
+            raise SzgbError(rc, "szgb_tune_save")
+
+    def tune_load(self, path: str):
+        rc = lib().szgb_tune_load(self._h, path.encode())
+        if rc:
+            raise SzgbError(rc, "szgb_tune_load")
 
     # -- batches -------------------------------------------------------------
     def set_graphs(self, on: bool):
