@@ -129,7 +129,7 @@ int szgb_decompress(szgb_ctx *ctx, const uint8_t *in, size_t in_len,
  *    16-byte aligned) are device buffers owned by the caller; work is issued
  *    on `cuda_stream` (a cudaStream_t, NULL = legacy default stream) and the
  *    call returns after that stream has finished it.
- *  - Scratch is a fixed 64 MiB static device array held by every GPU that
+ *  - Scratch is a fixed 128 MiB static device array held by every GPU that
  *    loads the library until the process exits; a stream whose decompression
  *    needs more returns SZGB_ESCRATCH before any work is issued.
  *  - The first call on a device looks up that array's device address; make

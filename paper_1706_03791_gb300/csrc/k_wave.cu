@@ -207,6 +207,105 @@ __device__ __forceinline__ int decode_symbol(BitReader& br, const uint32_t* s_lu
 }
 
 // ---------------------------------------------------------------------------
+// Huffman decode of every row (a row is one stream chunk), before the
+// reconstruction wavefront: one lane per row, a warp's 32 lanes in lockstep
+// (one symbol per lane per step), codes staged through a shared tile and
+// stored coalesced into the row-pitched code array; the value of an
+// unpredictable point (code 0: sign, exponent and top t mantissa bits) goes
+// straight to its place in the output array.
+
+struct DecodeArgs {
+    const uint8_t* payload;
+    const uint64_t* rowoff;
+    const uint32_t* rowbytes;
+    const uint8_t* stream_end;
+    const uint32_t* lut;
+    const uint32_t* dectab;
+    uint16_t* codes;
+    uint64_t cpitch;
+    float* out;
+    uint64_t rows, N;
+    DevState* st;
+};
+
+constexpr int kDecWarps = 8;
+constexpr int kDecTileStride = 34;  // u16 per tile row: an odd word stride, conflict-free
+
+__global__ void __launch_bounds__(kDecWarps * 32) k_decode_rows(const __grid_constant__ DecodeArgs D) {
+    __shared__ uint32_t s_lut[1 << kLutBits];
+    __shared__ uint32_t s_tab[260];
+    __shared__ uint16_t s_tile[kDecWarps][32][kDecTileStride];
+    __shared__ int s_err;
+    if (threadIdx.x == 0) s_err = *(volatile const unsigned*)&D.st->err != 0;
+    __syncthreads();
+    if (s_err) return;
+    const int T = (int)D.st->lut_bits, maxlen = (int)D.st->maxlen, e_eb = D.st->e_eb;
+    for (int i = threadIdx.x; i < (1 << T); i += blockDim.x) s_lut[i] = D.lut[i];
+    for (int i = threadIdx.x; i < 260; i += blockDim.x) s_tab[i] = D.dectab[i];
+    __syncthreads();
+    const uint16_t* g_sorted = reinterpret_cast<const uint16_t*>(D.dectab + 260);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t row0 = ((uint64_t)blockIdx.x * kDecWarps + warp) * 32;
+    const uint64_t row = row0 + lane;
+    const bool valid = row < D.rows;
+    BitReader br;
+    bool bad = false;
+    uint64_t avail = 0;
+    if (valid) {
+        br.init(D.payload, D.rowoff[row], (uint64_t)(D.stream_end - D.payload));
+        avail = (uint64_t)D.rowbytes[row] * 8;
+    }
+    uint16_t(*tile)[kDecTileStride] = s_tile[warp];
+    float* const orow = D.out + row * D.N;
+    for (uint64_t l0 = 0; l0 < D.N; l0 += 32) {
+        const int ncol = (int)min((uint64_t)32, D.N - l0);
+        for (int j = 0; j < ncol; j++) {
+            int code = 0;
+            if (valid) {
+                code = decode_symbol(br, s_lut, T, s_tab, g_sorted, maxlen, bad);
+                if (code == 0) {
+                    const uint32_t se = br.take(9);
+                    const int t = trunc_bits(se << 23, e_eb);
+                    const uint32_t mb = br.take(t);
+                    orow[l0 + j] = __uint_as_float((se << 23) | (t ? (mb << (23 - t)) : 0u));
+                }
+            }
+            tile[lane][j] = (uint16_t)code;
+        }
+        __syncwarp();
+        for (int t = 0; t < 32; t++) {
+            const uint64_t r = row0 + t;
+            if (r < D.rows && lane < ncol) D.codes[r * D.cpitch + l0 + lane] = tile[t][lane];
+        }
+        __syncwarp();
+    }
+    if (valid && (bad || br.consumed > avail)) atomicOr(&D.st->err, kErrCorrupt);
+}
+
+int launch_decode_rows(const uint8_t* payload, const uint64_t* rowoff, const uint32_t* rowbytes,
+                       const uint8_t* stream_end, const uint32_t* lut, const uint32_t* dec_tab, uint16_t* codes,
+                       uint64_t cpitch, float* out, uint64_t rows, uint64_t N, DevState* st, cudaStream_t s) {
+    DecodeArgs d;
+    d.payload = payload;
+    d.rowoff = rowoff;
+    d.rowbytes = rowbytes;
+    d.stream_end = stream_end;
+    d.lut = lut;
+    d.dectab = dec_tab;
+    d.codes = codes;
+    d.cpitch = cpitch;
+    d.out = out;
+    d.rows = rows;
+    d.N = N;
+    d.st = st;
+    const uint64_t per = 32ull * kDecWarps;
+    const uint64_t blocks = (rows + per - 1) / per;
+    if (blocks == 0 || blocks > 0x7fffffffull) return SZGB_EINVAL;
+    k_decode_rows<<<(unsigned)blocks, kDecWarps * 32, 0, s>>>(d);
+    return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
 // The kernel.  ND = 1, 2 (row topology) or 3 (plane x row); NL = layers;
 // DEC = decompress.
 //
@@ -234,14 +333,17 @@ struct Cfg {
     static constexpr int MAXE = (ND == 3) ? (NL * 32 + NL * kMaxWaveWarps + NL * NL + 31) / 32 : 1;
 };
 
-// output element: quantization code (compress) or decompressed value
+// staging elements: compression reads x (f32) and writes codes (u16);
+// decompression reads the decoded codes (u16) and writes values (f32)
 template <bool DEC>
-struct OutElem {
-    using T = uint16_t;
+struct Elems {
+    using In = float;
+    using Out = uint16_t;
 };
 template <>
-struct OutElem<true> {
-    using T = float;
+struct Elems<true> {
+    using In = uint16_t;
+    using Out = float;
 };
 
 // TR: also write the recorded (decompressed) values to A.recorded (tests)
@@ -260,7 +362,8 @@ struct WaveCtl {
 template <int ND, int NL, bool DEC, bool TR>
 __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, unsigned char* smem_raw, WaveCtl& S) {
     using C = Cfg<ND, NL>;
-    using OT = typename OutElem<DEC>::T;
+    using IT = typename Elems<DEC>::In;
+    using OT = typename Elems<DEC>::Out;
     const WaveGeom& g = A.g;
     const int W = g.W;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -276,11 +379,9 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
     float* PR = reinterpret_cast<float*>(smem + kMbarBytes);             // npl*32*kRPS
     float* VR = PR + (size_t)npl * 32 * kRPS;                            // nvl*NL*kRV
     float* HR = VR + (size_t)nvl * NL * kRV;                             // nhr*NL*kRV
-    float* XR = HR + (size_t)nhr * NL * kRV;                             // W*kTS*kTE (compress)
-    OT* OR = reinterpret_cast<OT*>(XR + (DEC ? 0 : (size_t)W * kTS * kTE));  // W*kTS*kTE
-    uint32_t* s_lut = reinterpret_cast<uint32_t*>(OR + (size_t)W * kTS * kTE);
-    uint32_t* s_tab = s_lut + (1 << kLutBits);
-    const bool tma_x = !DEC && A.tma_x;
+    IT* XR = reinterpret_cast<IT*>(HR + (size_t)nhr * NL * kRV);         // W*kTS*kTE inputs
+    OT* OR = reinterpret_cast<OT*>(XR + (size_t)W * kTS * kTE);          // W*kTS*kTE outputs
+    const bool tma_x = A.tma_x != 0;
     const bool tma_o = A.tma_out != 0;
 
     if (threadIdx.x == 0) {
@@ -483,7 +584,7 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
         // can start or finish a tile.
         // x tile first read in sweep u: issued kPFX + 1 sweeps ahead
         auto issue_x = [&](int u) {
-            if constexpr (!DEC) {
+            {
                 if (u < 0) return;
                 const int w = u & 7;
                 if (!((wv_mask >> w) & 1u)) return;
@@ -491,14 +592,14 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
                 if (d < 0) return;
                 const int kt = d >> 3, c0 = kt * kTW;
                 if (c0 >= N) return;
-                float* slot = XR + ((size_t)w * kTS + kt % kTS) * kTE;
+                IT* slot = XR + ((size_t)w * kTS + kt % kTS) * kTE;
                 if (tma_x) {
                     if (lane == 0) {
                         uint64_t* bar = MB + w * kTS + kt % kTS;
-                        mbar_arrive_expect_tx(bar, kTE * 4);
+                        mbar_arrive_expect_tx(bar, kTE * (unsigned)sizeof(IT));
                         tma_load_3d(slot, &A.tm_x, c0, tma_row(w), tma_plane(w), bar);
                     }
-                } else {
+                } else if constexpr (!DEC) {  // decompression always has TMA (its code array is ours)
                     const int nv = tile_rows(w);
                     const float* xr = A.x + tile_row0(w) * g.N;
                     const int col = c0 + lane;
@@ -666,7 +767,8 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
     const uint64_t rowid = plane * g.M + row;
     const uint64_t rowbase = rowid * g.N;
     float* const rec_row = TR ? A.recorded + rowbase : nullptr;
-    const float* const xw = XR + (size_t)warp * kTS * kTE + lane * kTW;  // this lane's tile rows
+    const IT* const xw = XR + (size_t)warp * kTS * kTE + lane * kTW;  // this lane's tile rows
+    const float* const out_row = DEC ? A.out + rowbase : nullptr;       // unpredictable values (decompress)
     OT* const ow = OR + (size_t)warp * kTS * kTE + lane * kTW;
     const int qd_last = (N - 1 + 31 + sig) / 4;  // sweep completing the last output tile
     const int col0 = -lane - sig;  // column at step 0
@@ -699,24 +801,6 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
         }
     }
 
-    BitReader br;
-    int T = 1, maxlen = 1;
-    bool bad = false;
-    uint64_t rowbits_avail = 0;
-    if constexpr (DEC) {
-        T = (int)A.st->lut_bits;
-        maxlen = (int)A.st->maxlen;
-        const int nthr = W * 32;
-        for (int i = threadIdx.x; i < (1 << T); i += nthr) s_lut[i] = A.lut[i];
-        for (int i = threadIdx.x; i < 260; i += nthr) s_tab[i] = A.dectab[i];
-        asm volatile("bar.sync 1, %0;" ::"r"(nthr));
-        if (valid) {
-            uint64_t off = A.rowoff[rowid];
-            rowbits_avail = (uint64_t)A.rowbytes[rowid] * 8;
-            br.init(A.payload, off, (uint64_t)(A.stream_end - A.payload));
-        }
-    }
-    const uint16_t* g_sorted = reinterpret_cast<const uint16_t*>(A.dectab + 260);
 
     for (int q = 0; q < nsweeps; q++) {
         named_bar_sync(kBarReady, nthr_all);  // this sweep's inputs are ready
@@ -846,16 +930,11 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
                     const float tr = trunc_value(xv, qp.e_eb);
                     code = quantize_tr(xv, pred, tr, qp, V);
                 } else {
+                    // the decode pass left the code here and, for code 0, the
+                    // unpredictable value in the output array
+                    code = act ? (int)xw[ti] : 0;
                     float uv = 0.0f;
-                    if (valid && act) {
-                        code = decode_symbol(br, s_lut, T, s_tab, g_sorted, maxlen, bad);
-                        if (code == 0) {
-                            const uint32_t se = br.take(9);
-                            const int t = trunc_bits(se << 23, qp.e_eb);
-                            const uint32_t mb = br.take(t);
-                            uv = __uint_as_float((se << 23) | (t ? (mb << (23 - t)) : 0u));
-                        }
-                    }
+                    if (code == 0 && valid && act) uv = out_row[l];
                     V = code ? dequantize(code, pred, qp) : uv;
                 }
                 V = act ? V : 0.0f;
@@ -883,9 +962,6 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
         // this thread's writes to it visible to the TMA store
         if (tma_o && ((q >= 15 + s4 && ((q - 15 - s4) & 7) == 0) || q == qd_last)) fence_proxy_async_smem();
         named_bar_arrive(kBarDone, nthr_all);  // this warp has finished the sweep
-    }
-    if constexpr (DEC) {
-        if (valid && (bad || br.consumed > rowbits_avail)) atomicOr(&A.st->err, kErrCorrupt);
     }
 }
 
@@ -937,9 +1013,8 @@ size_t wave_smem_bytes(const WaveGeom& g, int layers, bool decompress) {
     const int nhr = (g.ndim == 3) ? W : 0;
     size_t b = 128 + kMbarBytes;  // alignment slack, mbarriers
     b += (size_t)npl * 32 * kRPS * 4 + (size_t)(nvl + nhr) * NL * kRV * 4;
-    if (!decompress) b += (size_t)W * kTS * kTE * 4;
-    b += (size_t)W * kTS * kTE * (decompress ? 4 : 2);
-    if (decompress) b += (size_t)(1 << kLutBits) * 4 + 260 * 4;
+    b += (size_t)W * kTS * kTE * (4 + 2);  // input and output rings (f32 + u16 either way)
+    (void)decompress;
     return b;
 }
 
@@ -1048,18 +1123,12 @@ static void fill_compress(WaveArgs& a, const WaveGeom& g, const float* x, uint16
     a.tma_out = encode_tiles(&a.tm_out, false, codes, g.N, g.M, g.P, codes_pitch) ? 1 : 0;
 }
 
-static void fill_decompress(WaveArgs& a, const WaveGeom& g, const uint8_t* payload, const uint64_t* rowoff,
-                            const uint32_t* rowbytes, const uint8_t* stream_end, const uint32_t* lut,
-                            const uint32_t* dec_tab, float* out, float* halo_row, float* halo_plane,
-                            unsigned int* prog, DevState* st, uint64_t timeout_ns) {
+static void fill_decompress(WaveArgs& a, const WaveGeom& g, const uint16_t* codes, uint64_t codes_pitch, float* out,
+                            float* halo_row, float* halo_plane, unsigned int* prog, DevState* st,
+                            uint64_t timeout_ns) {
     memset(&a, 0, sizeof(a));
     a.g = g;
-    a.payload = payload;
-    a.rowoff = rowoff;
-    a.rowbytes = rowbytes;
-    a.stream_end = stream_end;
-    a.lut = lut;
-    a.dectab = dec_tab;
+    a.codes = const_cast<uint16_t*>(codes);
     a.out = out;
     a.opitch = g.N;
     a.halo_row = halo_row;
@@ -1067,6 +1136,7 @@ static void fill_decompress(WaveArgs& a, const WaveGeom& g, const uint8_t* paylo
     a.prog = prog;
     a.st = st;
     a.timeout_ns = timeout_ns;
+    a.tma_x = encode_tiles(&a.tm_x, false, codes, g.N, g.M, g.P, codes_pitch) ? 1 : 0;
     a.tma_out = encode_tiles(&a.tm_out, true, out, g.N, g.M, g.P, g.N) ? 1 : 0;
 }
 
@@ -1078,15 +1148,12 @@ int launch_wave_compress(const WaveGeom& g, int layers, const float* x, uint16_t
     return launch_any<false>(a, layers, s);
 }
 
-int launch_wave_decompress(const WaveGeom& g, int layers, const uint8_t* payload,
-                           const uint64_t* rowoff, const uint32_t* rowbytes,
-                           const uint8_t* stream_end, const uint32_t* lut,
-                           const uint32_t* dec_tab, float* out, float* halo_row,
-                           float* halo_plane, unsigned int* prog, DevState* st,
+int launch_wave_decompress(const WaveGeom& g, int layers, const uint16_t* codes, uint64_t codes_pitch, float* out,
+                           float* halo_row, float* halo_plane, unsigned int* prog, DevState* st,
                            uint64_t timeout_ns, cudaStream_t s) {
     WaveArgs a;
-    fill_decompress(a, g, payload, rowoff, rowbytes, stream_end, lut, dec_tab, out, halo_row, halo_plane, prog, st,
-                    timeout_ns);
+    fill_decompress(a, g, codes, codes_pitch, out, halo_row, halo_plane, prog, st, timeout_ns);
+    if (!a.tma_x) return SZGB_ECUDA;  // the code array is row-pitched and aligned: never expected
     return launch_any<true>(a, layers, s);
 }
 
@@ -1101,12 +1168,11 @@ void wave_args_compress(void* dst, const WaveGeom& g, const float* x, uint16_t* 
                   timeout_ns);
 }
 
-void wave_args_decompress(void* dst, const WaveGeom& g, const uint8_t* payload, const uint64_t* rowoff,
-                          const uint32_t* rowbytes, const uint8_t* stream_end, const uint32_t* lut,
-                          const uint32_t* dec_tab, float* out, float* halo_row, float* halo_plane,
-                          unsigned int* prog, DevState* st, uint64_t timeout_ns) {
-    fill_decompress(*static_cast<WaveArgs*>(dst), g, payload, rowoff, rowbytes, stream_end, lut, dec_tab, out,
-                    halo_row, halo_plane, prog, st, timeout_ns);
+int wave_args_decompress(void* dst, const WaveGeom& g, const uint16_t* codes, uint64_t codes_pitch, float* out,
+                         float* halo_row, float* halo_plane, unsigned int* prog, DevState* st, uint64_t timeout_ns) {
+    WaveArgs& a = *static_cast<WaveArgs*>(dst);
+    fill_decompress(a, g, codes, codes_pitch, out, halo_row, halo_plane, prog, st, timeout_ns);
+    return a.tma_x ? 0 : SZGB_ECUDA;
 }
 
 int launch_wave_batch(const void* args_dev, const void* order_dev, unsigned total, unsigned* ticket_dev, int layers,

@@ -25,11 +25,11 @@ namespace {
 
 enum Phase {
     PH_H2D = 0, PH_RANGE, PH_ADAPT, PH_WAVE_C, PH_HIST, PH_CODEBOOK, PH_ROWBITS, PH_SCAN, PH_WRITE,
-    PH_D2H, PH_DEC_TABLES, PH_DEC_SCAN, PH_WAVE_D, PH_N
+    PH_D2H, PH_DEC_TABLES, PH_DEC_SCAN, PH_WAVE_D, PH_DEC_ROWS, PH_N
 };
 const char* kPhaseNames[PH_N] = {"h2d", "range", "adapt", "wave_compress", "histogram", "codebook",
                                   "rowbits", "scan", "write", "d2h", "decode_tables", "decode_scan",
-                                  "wave_decompress"};
+                                  "wave_decompress", "decode_rows"};
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -460,8 +460,11 @@ int decompress_impl(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_dev
     uint32_t *rowbytes, *lut, *dectab, *symbuf;
     uint64_t *rowoff, *blocksums;
     uint8_t *lenbuf, *istage;
+    uint16_t* codes;
+    const uint64_t cpitch = (H.d2 + 7) & ~(uint64_t)7;
     Arena A;
     A.add(&st, 1);
+    A.add(&codes, rows * cpitch + 8);
     A.add(&halo_row, hrow);
     A.add(&halo_plane, hplane);
     A.add(&prog, g.num_ctas);
@@ -512,9 +515,15 @@ int decompress_impl(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_dev
         if ((rc = launch_scan_rows(rowbytes, rows, rowoff, blocksums, st, 0, s))) return rc;
     }
     {
+        PhaseTimer t(c, PH_DEC_ROWS);
+        if ((rc = launch_decode_rows(payload, rowoff, rowbytes, payload + H.payload, lut, dectab, codes, cpitch, dst,
+                                     rows, H.d2, st, s)))
+            return rc;
+    }
+    {
         PhaseTimer t(c, PH_WAVE_D);
-        if ((rc = launch_wave_decompress(g, H.layers, payload, rowoff, rowbytes, payload + H.payload, lut, dectab,
-                                         dst, halo_row, halo_plane, prog, st, c->timeout_ns, s)))
+        if ((rc = launch_wave_decompress(g, H.layers, codes, cpitch, dst, halo_row, halo_plane, prog, st,
+                                         c->timeout_ns, s)))
             return rc;
     }
     if (cudaMemcpyAsync(c->h_state, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess)
@@ -827,7 +836,8 @@ struct DecPlan {
     Header H;
     CallParams cp;
     WaveGeom g;
-    uint64_t n, rows;
+    uint64_t n, rows, cpitch;
+    uint16_t* codes;
     size_t hrow, hplane;
     const uint8_t *codebook, *table, *payload;
     float *halo_row, *halo_plane;
@@ -865,6 +875,7 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
         q.n = q.H.d0 * q.H.d1 * q.H.d2;
         if (out_cap[f] < q.n) return SZGB_EINVAL;
         q.rows = q.H.nchunks;
+        q.cpitch = (q.H.d2 + 7) & ~(uint64_t)7;
         q.cp = CallParams{};
         q.cp.ndim = q.H.ndim;
         q.cp.d0 = q.H.d0;
@@ -897,6 +908,7 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
     A.add(&order, 2 * total_items);
     for (int f = 0; f < count; f++) {
         DecPlan& q = P[f];
+        A.add(&q.codes, q.rows * q.cpitch + 8);
         A.add(&q.halo_row, q.hrow);
         A.add(&q.halo_plane, q.hplane);
         A.add(&q.rowbytes, q.rows);
@@ -935,8 +947,9 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
         uint32_t ub;
         memcpy(&ub, &q.H.eb_f, 4);
         d.e_eb = (int)((ub >> 23) & 0xffu);
-        wave_args_decompress(Hb + o_w + (size_t)f * wsz, q.g, q.payload, q.rowoff, q.rowbytes, q.payload + q.H.payload,
-                             q.lut, q.dectab, out[f], q.halo_row, q.halo_plane, q.prog, st + f, c->timeout_ns);
+        if ((rc = wave_args_decompress(Hb + o_w + (size_t)f * wsz, q.g, q.codes, q.cpitch, out[f], q.halo_row,
+                                       q.halo_plane, q.prog, st + f, c->timeout_ns)))
+            return rc;
     }
     uint32_t* h_order = reinterpret_cast<uint32_t*>(Hb + o_ord);
     size_t ord_at[2], ord_n[2];
@@ -972,6 +985,9 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
                 return r;
             if ((r = launch_read_rowbytes(q.table, q.H.tw, q.rows, q.rowbytes, a))) return r;
             if ((r = launch_scan_rows(q.rowbytes, q.rows, q.rowoff, q.blocksums, st + f, 0, a))) return r;
+            if ((r = launch_decode_rows(q.payload, q.rowoff, q.rowbytes, q.payload + q.H.payload, q.lut, q.dectab,
+                                        q.codes, q.cpitch, out[f], q.rows, q.H.d2, st + f, a)))
+                return r;
         }
         join_aux(c);
         for (int li = 0; li < 2; li++) {

@@ -290,11 +290,13 @@ int launch_adapt(const float* x, const CallParams& cp, DevState* st, cudaStream_
 int launch_wave_compress(const WaveGeom& g, int layers, const float* x, uint16_t* codes,
                          uint64_t codes_pitch, float* recorded, float* halo_row, float* halo_plane, unsigned int* prog,
                          DevState* st, uint64_t timeout_ns, cudaStream_t s);
-int launch_wave_decompress(const WaveGeom& g, int layers, const uint8_t* payload,
-                           const uint64_t* rowoff, const uint32_t* rowbytes,
-                           const uint8_t* stream_end, const uint32_t* lut,
-                           const uint32_t* dec_tab, float* out, float* halo_row,
-                           float* halo_plane, unsigned int* prog, DevState* st,
+// decompression: rows decoded first (codes into a row-pitched array, the
+// values of unpredictable points into `out`), then the reconstruction wavefront
+int launch_decode_rows(const uint8_t* payload, const uint64_t* rowoff, const uint32_t* rowbytes,
+                       const uint8_t* stream_end, const uint32_t* lut, const uint32_t* dec_tab, uint16_t* codes,
+                       uint64_t cpitch, float* out, uint64_t rows, uint64_t N, DevState* st, cudaStream_t s);
+int launch_wave_decompress(const WaveGeom& g, int layers, const uint16_t* codes, uint64_t codes_pitch, float* out,
+                           float* halo_row, float* halo_plane, unsigned int* prog, DevState* st,
                            uint64_t timeout_ns, cudaStream_t s);
 size_t wave_smem_bytes(const WaveGeom& g, int layers, bool decompress);
 // batched wavefront: a device table of per-field arguments (filled on the
@@ -302,10 +304,8 @@ size_t wave_smem_bytes(const WaveGeom& g, int layers, bool decompress);
 size_t wave_args_bytes();
 void wave_args_compress(void* dst, const WaveGeom& g, const float* x, uint16_t* codes, uint64_t codes_pitch,
                         float* halo_row, float* halo_plane, unsigned int* prog, DevState* st, uint64_t timeout_ns);
-void wave_args_decompress(void* dst, const WaveGeom& g, const uint8_t* payload, const uint64_t* rowoff,
-                          const uint32_t* rowbytes, const uint8_t* stream_end, const uint32_t* lut,
-                          const uint32_t* dec_tab, float* out, float* halo_row, float* halo_plane,
-                          unsigned int* prog, DevState* st, uint64_t timeout_ns);
+int wave_args_decompress(void* dst, const WaveGeom& g, const uint16_t* codes, uint64_t codes_pitch, float* out,
+                         float* halo_row, float* halo_plane, unsigned int* prog, DevState* st, uint64_t timeout_ns);
 int launch_wave_batch(const void* args_dev, const void* order_dev, unsigned total, unsigned* ticket_dev, int layers,
                       bool decompress, size_t smem, int grid, cudaStream_t s);
 

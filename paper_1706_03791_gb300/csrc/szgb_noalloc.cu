@@ -25,7 +25,7 @@ using namespace szgb;
 
 namespace {
 
-constexpr size_t kNoAllocScratchBytes = 64ull << 20;  // 64 MiB
+constexpr size_t kNoAllocScratchBytes = 128ull << 20;  // 128 MiB
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
@@ -138,6 +138,8 @@ extern "C" int szgb_decompress_noalloc(const uint8_t* in_dev, size_t in_len, flo
     const size_t o_rb = take(rows * 4), o_ro = take(rows * 8), o_bs = take(((rows + 2047) / 2048 + 1) * 8);
     const size_t o_lut = take(((size_t)1 << kLutBits) * 4), o_tab = take(kDecTabU32 * 4);
     const size_t o_len = take(65536), o_sym = take(65536 * 4);
+    const uint64_t cpitch = (d2 + 7) & ~7ull;
+    const size_t o_codes = take((rows * cpitch + 8) * 2);
     if (off > kNoAllocScratchBytes) return SZGB_ESCRATCH;
     if (out_cap_elems < d0 * d1 * d2) return SZGB_EINVAL;
     char* b = static_cast<char*>(base);
@@ -168,8 +170,11 @@ extern "C" int szgb_decompress_noalloc(const uint8_t* in_dev, size_t in_len, flo
     if ((rc = launch_read_rowbytes(table, tw, rows, rowbytes, s))) return rc;
     if ((rc = launch_scan_rows(rowbytes, rows, rowoff, reinterpret_cast<uint64_t*>(b + o_bs), st, 0, s)))
         return rc;
-    if ((rc = launch_wave_decompress(g, layers, payload, rowoff, rowbytes, payload + payload_bytes, lut, dectab,
-                                     out_dev, reinterpret_cast<float*>(b + o_hrow),
+    uint16_t* codes = reinterpret_cast<uint16_t*>(b + o_codes);
+    if ((rc = launch_decode_rows(payload, rowoff, rowbytes, payload + payload_bytes, lut, dectab, codes, cpitch,
+                                 out_dev, rows, d2, st, s)))
+        return rc;
+    if ((rc = launch_wave_decompress(g, layers, codes, cpitch, out_dev, reinterpret_cast<float*>(b + o_hrow),
                                      reinterpret_cast<float*>(b + o_hplane), prog, st, 4000000000ull, s)))
         return rc;
     DevState hs;
