@@ -228,6 +228,21 @@ int dev_errors(const DevState& s) {
 // ---------------------------------------------------------------------------
 // compress
 
+int ensure_pinned(szgb_ctx* c, size_t need);
+
+// a 64-byte aligned host buffer for one field's wavefront arguments (they
+// hold TMA descriptors, which need that alignment)
+struct ArgsBuf {
+    std::vector<unsigned char> buf;
+    void* p;
+    explicit ArgsBuf(size_t n) : buf(n + 64) {
+        p = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(buf.data()) + 63) & ~(uintptr_t)63);
+    }
+};
+
+int launch_wave_one(szgb_ctx* c, const WaveGeom& g, int layers, bool dec, const void* host_args, char* stage,
+                    char* dev_args, uint32_t* dev_order, unsigned* dev_ticket, cudaStream_t s);
+
 int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb_params* p, uint8_t* out,
                   size_t out_cap, int out_on_device, size_t* out_len, szgb_stats* stats, float* rec_dev,
                   uint16_t* codes_dev) {
@@ -272,6 +287,12 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
     A.add(&rowbytes, rows);
     A.add(&rowoff, rows);
     A.add(&blocksums, (rows + 2047) / 2048 + 1);
+    char* wargs;
+    uint32_t* worder;
+    unsigned* wticket;
+    A.add(&wargs, wave_args_bytes());
+    A.add(&worder, 2 * (size_t)g.num_ctas);
+    A.add(&wticket, 1);
     if (!direct_in) A.add(&xs, N);
     else xs = nullptr;
     if (!direct_out) A.add(&ostage, bound);
@@ -303,7 +324,15 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
     }
     {
         PhaseTimer t(c, PH_WAVE_C);
-        if ((rc = launch_wave_compress(g, layers, x, codes, cpitch, rec_dev, halo_row, halo_plane, prog, st,
+        if (!rec_dev) {
+            // the persistent kernel, items in ready-time order
+            ArgsBuf ha(wave_args_bytes());
+            wave_args_compress(ha.p, g, x, codes, cpitch, halo_row, halo_plane, prog, st, c->timeout_ns);
+            if ((rc = ensure_pinned(c, align_up(wave_args_bytes(), 256) + 8 * (size_t)g.num_ctas))) return rc;
+            if ((rc = launch_wave_one(c, g, layers, false, ha.p, static_cast<char*>(c->h_batch), wargs, worder,
+                                      wticket, s)))
+                return rc;
+        } else if ((rc = launch_wave_compress(g, layers, x, codes, cpitch, rec_dev, halo_row, halo_plane, prog, st,
                                        c->timeout_ns, s)))
             return rc;
     }
@@ -475,6 +504,12 @@ int decompress_impl(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_dev
     A.add(&dectab, kDecTabU32);
     A.add(&lenbuf, 65536);
     A.add(&symbuf, 65536);
+    char* wargs;
+    uint32_t* worder;
+    unsigned* wticket;
+    A.add(&wargs, wave_args_bytes());
+    A.add(&worder, 2 * (size_t)g.num_ctas);
+    A.add(&wticket, 1);
     if (!direct_in) A.add(&istage, H.total + 16);
     else istage = nullptr;
     if (!direct_out) A.add(&ostage, N);
@@ -522,8 +557,12 @@ int decompress_impl(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_dev
     }
     {
         PhaseTimer t(c, PH_WAVE_D);
-        if ((rc = launch_wave_decompress(g, H.layers, codes, cpitch, dst, halo_row, halo_plane, prog, st,
-                                         c->timeout_ns, s)))
+        ArgsBuf ha(wave_args_bytes());
+        if ((rc = wave_args_decompress(ha.p, g, codes, cpitch, dst, halo_row, halo_plane, prog, st, c->timeout_ns)))
+            return rc;
+        if ((rc = ensure_pinned(c, align_up(wave_args_bytes(), 256) + 8 * (size_t)g.num_ctas))) return rc;
+        if ((rc = launch_wave_one(c, g, H.layers, true, ha.p, static_cast<char*>(c->h_batch), wargs, worder,
+                                  wticket, s)))
             return rc;
     }
     if (cudaMemcpyAsync(c->h_state, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess)
@@ -650,20 +689,54 @@ struct CompPlan {
     uint32_t* hist;
 };
 
-// the (field, item) order of a batched wavefront: level i lists item i of
-// every field that has one, so each field's items stay in dependency order
-size_t build_order(const std::vector<int>& fields, const std::vector<int>& nitems, uint32_t* dst) {
-    int maxi = 0;
-    for (int f : fields) maxi = std::max(maxi, nitems[f]);
-    size_t t = 0;
-    for (int i = 0; i < maxi; i++)
-        for (int f : fields)
-            if (i < nitems[f]) {
-                dst[2 * t] = (uint32_t)f;
-                dst[2 * t + 1] = (uint32_t)i;
-                t++;
-            }
-    return t;
+// The (field, item) order of a wavefront launch.  Items are taken in the
+// order of the sweep at which their producers let them start: about W + 5
+// sweeps per plane block and 14 per row block in 3D (the skew of the block
+// plus prefetch and publication lag), 9W + 5 per row block in 1D/2D.  Every
+// producer has a smaller key than its consumers, so the order respects the
+// dependencies, and SMs go first to the items that can run first.
+size_t build_order(const std::vector<int>& fields, const std::vector<WaveGeom>& geo, uint32_t* dst) {
+    struct K {
+        uint64_t key;
+        uint32_t f, i;
+    };
+    std::vector<K> v;
+    for (int f : fields) {
+        const WaveGeom& g = geo[f];
+        for (int i = 0; i < g.num_ctas; i++) {
+            uint64_t key;
+            if (g.ndim == 3) key = (uint64_t)(i / g.nb1) * (uint64_t)(g.W + 5) + (uint64_t)(i % g.nb1) * 14u;
+            else key = (uint64_t)i * (uint64_t)(9 * g.W + 5);
+            v.push_back({key, (uint32_t)f, (uint32_t)i});
+        }
+    }
+    std::stable_sort(v.begin(), v.end(), [](const K& a, const K& b) {
+        return a.key != b.key ? a.key < b.key : (a.f != b.f ? a.f < b.f : a.i < b.i);
+    });
+    for (size_t t = 0; t < v.size(); t++) {
+        dst[2 * t] = v[t].f;
+        dst[2 * t + 1] = v[t].i;
+    }
+    return v.size();
+}
+
+// One field's wavefront on the persistent (batch) kernel: its arguments and
+// item order go to the device through the pinned staging area at `stage`.
+int launch_wave_one(szgb_ctx* c, const WaveGeom& g, int layers, bool dec, const void* host_args, char* stage,
+                    char* dev_args, uint32_t* dev_order, unsigned* dev_ticket, cudaStream_t s) {
+    const size_t wsz = wave_args_bytes();
+    memcpy(stage, host_args, wsz);
+    uint32_t* ho = reinterpret_cast<uint32_t*>(stage + align_up(wsz, 256));
+    std::vector<int> one{0};
+    std::vector<WaveGeom> geo{g};
+    const size_t n = build_order(one, geo, ho);
+    if (cudaMemcpyAsync(dev_args, stage, wsz, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(dev_order, ho, 8 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(dev_ticket, 0, sizeof(unsigned), s) != cudaSuccess)
+        return SZGB_ECUDA;
+    const int grid = (int)std::min<size_t>(n, (size_t)c->sm_count);
+    return launch_wave_batch(dev_args, dev_order, (unsigned)n, dev_ticket, layers, dec,
+                             wave_smem_bytes(g, layers, dec), grid, s);
 }
 
 int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const szgb_params* params,
@@ -748,10 +821,12 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
     }
     uint32_t* h_order = reinterpret_cast<uint32_t*>(H + o_ord);
     size_t ord_at[2], ord_n[2];
+    std::vector<WaveGeom> geo(count);
+    for (int f = 0; f < count; f++) geo[f] = P[f].g;
     ord_at[0] = 0;
-    ord_n[0] = build_order(by_layers[0], nitems, h_order);
+    ord_n[0] = build_order(by_layers[0], geo, h_order);
     ord_at[1] = ord_n[0];
-    ord_n[1] = build_order(by_layers[1], nitems, h_order + 2 * ord_n[0]);
+    ord_n[1] = build_order(by_layers[1], geo, h_order + 2 * ord_n[0]);
 
     std::vector<uint64_t> key;
     key.push_back((uint64_t)count);
@@ -953,10 +1028,12 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
     }
     uint32_t* h_order = reinterpret_cast<uint32_t*>(Hb + o_ord);
     size_t ord_at[2], ord_n[2];
+    std::vector<WaveGeom> geo(count);
+    for (int f = 0; f < count; f++) geo[f] = P[f].g;
     ord_at[0] = 0;
-    ord_n[0] = build_order(by_layers[0], nitems, h_order);
+    ord_n[0] = build_order(by_layers[0], geo, h_order);
     ord_at[1] = ord_n[0];
-    ord_n[1] = build_order(by_layers[1], nitems, h_order + 2 * ord_n[0]);
+    ord_n[1] = build_order(by_layers[1], geo, h_order + 2 * ord_n[0]);
     std::vector<uint64_t> key;
     key.push_back((uint64_t)count);
     key.push_back((uint64_t)(uintptr_t)c->scratch);
