@@ -33,6 +33,21 @@
  *      reaches ceil(theta * samples), else 16;
  *   R8 stream layout: little-endian header, codebook, per-row byte lengths,
  *      payload rows of MSB-first bits with inline unpredictable records.
+ *
+ * The lattice variant (szo_compress_lattice) is NOT the paper's method but a
+ * separately labelled, fully parallel form of it: every value is snapped to
+ * the lattice of spacing 2 eb_f first, p = rint(x * (1 / (2 eb_f))) in double
+ * (the reciprocal rounded once), |p| < 2^30; the
+ * integer field p is predicted by the same n-layer coefficients in exact
+ * integer arithmetic from the *lattice* values of the neighbours (zero
+ * outside the domain), and the residual r = p - pred takes the place of the
+ * quantization code (code r + 2^(m-1) when |r| <= 2^(m-1)-1).  A point is an
+ * outlier (code 0) when |r| is larger or its lattice value (float)(p * 2 eb_f)
+ * misses the bound; its record is a flag bit (1: the lattice value is within
+ * the bound), r as 64-bit two's complement and, when the flag is 0, the 32
+ * bits of x.  Since the prediction never uses reconstructed values, every
+ * residual is independent of the others, and the inverse of the predictor
+ * (n prefix sums per axis) recovers p.
  */
 #include "szo.h"
 
@@ -529,6 +544,215 @@ done:
 }
 
 /* ------------------------------------------------------------------ */
+/* the lattice variant                                                  */
+
+typedef struct { int32_t k[3]; int64_t c; } iterm_t;
+
+static iterm_t *make_iterms(int ndim, int layers, int *T_out) {
+    int T = szo_num_terms(ndim, layers);
+    if (T <= 0) return NULL;
+    int32_t *k = (int32_t *)malloc(sizeof(int32_t) * 3 * T);
+    int64_t *c = (int64_t *)malloc(sizeof(int64_t) * T);
+    iterm_t *t = (iterm_t *)malloc(sizeof(iterm_t) * T);
+    if (!k || !c || !t) { free(k); free(c); free(t); return NULL; }
+    szo_terms(ndim, layers, k, c);
+    for (int i = 0; i < T; i++) {
+        t[i].k[0] = k[3 * i]; t[i].k[1] = k[3 * i + 1]; t[i].k[2] = k[3 * i + 2];
+        t[i].c = c[i];
+    }
+    free(k); free(c);
+    *T_out = T;
+    return t;
+}
+
+/* integer prediction from lattice values, neighbours outside = 0 */
+static int64_t ipredict_at(const int64_t *P, const uint64_t d[3], int64_t i, int64_t j, int64_t l,
+                           const iterm_t *t, int T) {
+    int64_t s = 0;
+    for (int q = 0; q < T; q++) {
+        int64_t ii = i - t[q].k[0], jj = j - t[q].k[1], ll = l - t[q].k[2];
+        if (ii >= 0 && jj >= 0 && ll >= 0) s += t[q].c * P[((uint64_t)ii * d[1] + (uint64_t)jj) * d[2] + (uint64_t)ll];
+    }
+    return s;
+}
+
+/* the lattice integer of x and whether its lattice value is within the bound */
+int64_t szo_lattice_point(float x, float eb_f, int *ok) {
+    double twoeb = 2.0 * (double)eb_f;
+    double inv = 1.0 / twoeb;
+    int64_t p = (int64_t)rint((double)x * inv);
+    float v = (float)((double)p * twoeb);
+    if (ok) *ok = fabs((double)x - (double)v) < (double)eb_f;
+    return p;
+}
+
+float szo_lattice_value(int64_t p, float eb_f) { return (float)((double)p * (2.0 * (double)eb_f)); }
+
+int szo_choose_m_lattice(const float *x, int ndim, const uint64_t *shape, int layers, float eb_f,
+                         double theta) {
+    uint64_t d[3];
+    if (norm_shape(ndim, shape, d)) return 16;
+    int T;
+    iterm_t *t = make_iterms(ndim, layers, &T);
+    if (!t) return 16;
+    uint64_t S0 = (d[0] + 7) / 8, S1 = (d[1] + 7) / 8, S2 = (d[2] + 7) / 8, S = S0 * S1 * S2;
+    uint64_t cnt[18] = {0};
+    for (uint64_t a = 0; a < S0; a++)
+        for (uint64_t b = 0; b < S1; b++)
+            for (uint64_t c = 0; c < S2; c++) {
+                int64_t i = (int64_t)(8 * a), j = (int64_t)(8 * b), l = (int64_t)(8 * c);
+                int64_t pred = 0;
+                for (int q = 0; q < T; q++) {
+                    int64_t ii = i - t[q].k[0], jj = j - t[q].k[1], ll = l - t[q].k[2];
+                    if (ii >= 0 && jj >= 0 && ll >= 0)
+                        pred += t[q].c * szo_lattice_point(x[((uint64_t)ii * d[1] + (uint64_t)jj) * d[2] + (uint64_t)ll], eb_f, NULL);
+                }
+                int ok;
+                int64_t p = szo_lattice_point(x[((uint64_t)i * d[1] + (uint64_t)j) * d[2] + (uint64_t)l], eb_f, &ok);
+                int64_t r = p - pred, ar = r < 0 ? -r : r;
+                if (!ok || ar > 32767) continue;
+                int mm = 2;
+                while (ar > ((int64_t)1 << (mm - 1)) - 1) mm++;
+                cnt[mm]++;
+            }
+    free(t);
+    double req = ceil(theta * (double)S);
+    uint64_t cum = 0;
+    for (int mm = 2; mm <= 16; mm++) {
+        cum += cnt[mm];
+        if ((double)cum >= req) return mm;
+    }
+    return 16;
+}
+
+int szo_compress_lattice(const float *x, int ndim, const uint64_t *shape, int mode, double eb_abs,
+                         double eb_rel, int layers, int m, double theta, uint8_t *out, size_t out_cap,
+                         size_t *out_len, float *recorded_out, uint16_t *codes_out) {
+    uint64_t d[3];
+    if (norm_shape(ndim, shape, d) || !x || !out_len) return SZO_EINVAL;
+    if (mode < 0 || mode > 2 || layers < 1 || layers > 4) return SZO_EINVAL;
+    if (m != 0 && (m < 2 || m > 16)) return SZO_EINVAL;
+    if (mode != 1 && !(eb_abs >= 0.0)) return SZO_EINVAL;
+    if (mode != 0 && !(eb_rel >= 0.0)) return SZO_EINVAL;
+    uint64_t N = d[0] * d[1] * d[2];
+    if (N >= ((uint64_t)1 << 32)) return SZO_EINVAL;
+    float xmin = x[0], xmax = x[0];
+    for (uint64_t p = 0; p < N; p++) {
+        if (!isfinite(x[p])) return SZO_ENONFINITE;
+        if (x[p] < xmin) xmin = x[p];
+        if (x[p] > xmax) xmax = x[p];
+    }
+    xmin = xmin + 0.0f;
+    xmax = xmax + 0.0f;
+    float eb_f;
+    szo_effective_eb(mode, eb_abs, eb_rel, xmin, xmax, &eb_f);
+    /* the lattice needs a positive spacing and lattice integers below 2^30 */
+    double amax = fmax(fabs((double)xmin), fabs((double)xmax));
+    if (!(eb_f > 0.0f) || amax * (1.0 / (2.0 * (double)eb_f)) >= 1073741824.0) return SZO_EINVAL;
+    int adaptive = (m == 0);
+    if (adaptive) m = szo_choose_m_lattice(x, ndim, shape, layers, eb_f, theta);
+    int T;
+    iterm_t *t = make_iterms(ndim, layers, &T);
+    int64_t *P = (int64_t *)malloc(sizeof(int64_t) * N);
+    int64_t *R = (int64_t *)malloc(sizeof(int64_t) * N);
+    uint8_t *okv = (uint8_t *)malloc(N);
+    uint16_t *code = (uint16_t *)malloc(sizeof(uint16_t) * N);
+    if (!t || !P || !R || !okv || !code) { free(t); free(P); free(R); free(okv); free(code); return SZO_ENOMEM; }
+    for (uint64_t q = 0; q < N; q++) {
+        int ok;
+        P[q] = szo_lattice_point(x[q], eb_f, &ok);
+        okv[q] = (uint8_t)ok;
+    }
+    const int64_t center = (int64_t)1 << (m - 1), radius = center - 1;
+    uint64_t K = 0;
+    for (uint64_t i = 0; i < d[0]; i++)
+        for (uint64_t j = 0; j < d[1]; j++)
+            for (uint64_t l = 0; l < d[2]; l++) {
+                uint64_t q = (i * d[1] + j) * d[2] + l;
+                R[q] = P[q] - ipredict_at(P, d, (int64_t)i, (int64_t)j, (int64_t)l, t, T);
+                int64_t ar = R[q] < 0 ? -R[q] : R[q];
+                code[q] = (okv[q] && ar <= radius) ? (uint16_t)(R[q] + center) : 0;
+                K += code[q] == 0;
+                if (recorded_out) recorded_out[q] = okv[q] ? szo_lattice_value(P[q], eb_f) : x[q];
+            }
+    /* Huffman coding of the codes, as in the exact path */
+    int nsymtot = 1 << m;
+    uint64_t *freq = (uint64_t *)calloc((size_t)nsymtot, sizeof(uint64_t));
+    uint8_t *len = (uint8_t *)malloc((size_t)nsymtot);
+    uint64_t *cw = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)nsymtot);
+    uint64_t rows = d[0] * d[1], Nr = d[2];
+    uint64_t *rowbytes = (uint64_t *)malloc(sizeof(uint64_t) * rows);
+    int rc = SZO_OK;
+    if (!freq || !len || !cw || !rowbytes) { rc = SZO_ENOMEM; goto done; }
+    for (uint64_t q = 0; q < N; q++) freq[code[q]]++;
+    int maxlen = szo_huffman_lengths(freq, nsymtot, len);
+    szo_canonical_codes(len, nsymtot, cw);
+    uint32_t nsym = 0;
+    for (int s = 0; s < nsymtot; s++) nsym += (len[s] != 0);
+    uint64_t payload = 0, maxrow = 0;
+    for (uint64_t r = 0; r < rows; r++) {
+        uint64_t bits = 0;
+        for (uint64_t l = 0; l < Nr; l++) {
+            uint64_t q = r * Nr + l;
+            bits += len[code[q]];
+            if (code[q] == 0) bits += 1 + 64 + (okv[q] ? 0 : 32);
+        }
+        rowbytes[r] = (bits + 7) / 8;
+        payload += rowbytes[r];
+        if (rowbytes[r] > maxrow) maxrow = rowbytes[r];
+    }
+    int tw = maxrow <= 0xffff ? 2 : 4;
+    uint64_t cb_bytes = pad4(3 * (uint64_t)nsym), tab_bytes = pad4((uint64_t)tw * rows);
+    uint64_t total = HDR_BYTES + cb_bytes + tab_bytes + payload;
+    *out_len = (size_t)total;
+    if (!out || out_cap < total) { rc = SZO_ETRUNC; goto done; }
+    memset(out, 0, (size_t)total);
+    out[0] = 'S'; out[1] = 'Z'; out[2] = 'G'; out[3] = 'B';
+    wr16(out + 4, 1);
+    wr16(out + 6, HDR_BYTES);
+    out[8] = (uint8_t)ndim; out[9] = (uint8_t)layers; out[10] = (uint8_t)m; out[11] = (uint8_t)mode;
+    out[12] = (uint8_t)maxlen; out[13] = (uint8_t)tw;
+    wr64(out + 16, d[0]); wr64(out + 24, d[1]); wr64(out + 32, d[2]);
+    wrf64(out + 40, eb_abs); wrf64(out + 48, eb_rel);
+    wr32(out + 56, f2u(eb_f)); wr32(out + 60, f2u(xmin)); wr32(out + 64, f2u(xmax));
+    wr32(out + 68, nsym); wr64(out + 72, rows); wr64(out + 80, K);
+    wr64(out + 88, payload); wr64(out + 96, total);
+    wrf64(out + 104, theta); out[112] = (uint8_t)adaptive;
+    out[113] = 1; /* the lattice variant */
+    {
+        uint8_t *cb = out + HDR_BYTES;
+        uint32_t e = 0;
+        for (int s = 0; s < nsymtot; s++)
+            if (len[s]) { wr16(cb + 3 * e, (uint16_t)s); cb[3 * e + 2] = len[s]; e++; }
+        uint8_t *tb = out + HDR_BYTES + cb_bytes;
+        for (uint64_t r = 0; r < rows; r++) {
+            if (tw == 2) wr16(tb + 2 * r, (uint16_t)rowbytes[r]);
+            else wr32(tb + 4 * r, (uint32_t)rowbytes[r]);
+        }
+        uint8_t *pl = tb + tab_bytes;
+        uint64_t off = 0;
+        for (uint64_t r = 0; r < rows; r++) {
+            bw_t w = {pl + off, 0};
+            for (uint64_t l = 0; l < Nr; l++) {
+                uint64_t q = r * Nr + l;
+                put_bits(&w, cw[code[q]], len[code[q]]);
+                if (code[q] == 0) {
+                    put_bits(&w, okv[q], 1);
+                    put_bits(&w, (uint64_t)R[q] >> 32, 32);
+                    put_bits(&w, (uint64_t)R[q] & 0xffffffffu, 32);
+                    if (!okv[q]) put_bits(&w, f2u(x[q]), 32);
+                }
+            }
+            off += rowbytes[r];
+        }
+    }
+    if (codes_out) memcpy(codes_out, code, sizeof(uint16_t) * N);
+done:
+    free(t); free(P); free(R); free(okv); free(code); free(freq); free(len); free(cw); free(rowbytes);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ */
 /* decompression (inverse path, same prediction in the same order)      */
 
 int szo_decompress(const uint8_t *in, size_t in_len, float *out, size_t out_cap_elems) {
@@ -583,9 +807,13 @@ int szo_decompress(const uint8_t *in, size_t in_len, float *out, size_t out_cap_
         }
     }
 
+    const int lattice = in[113] == 1;
+    if (in[113] > 1) { free(len); free(cw); free(sorted_sym); return SZO_ECORRUPT; }
     int T;
     term_t *t = make_terms(ndim, layers, &T);
-    if (!t) { free(len); free(cw); free(sorted_sym); return SZO_ENOMEM; }
+    iterm_t *it = lattice ? make_iterms(ndim, layers, &T) : NULL;
+    int64_t *P = lattice ? (int64_t *)malloc(sizeof(int64_t) * N) : NULL;
+    if (!t || (lattice && (!it || !P))) { free(t); free(it); free(P); free(len); free(cw); free(sorted_sym); return SZO_ENOMEM; }
     const uint8_t *tb = in + HDR_BYTES + cb_bytes;
     const uint8_t *pl = tb + tab_bytes;
     float twoeb = 2.0f * eb_f;
@@ -610,6 +838,27 @@ int szo_decompress(const uint8_t *in, size_t in_len, float *out, size_t out_cap_
             }
             if (rc) break;
             uint64_t p = r * Nr + l;
+            if (lattice) {
+                /* p = r + integer prediction from the earlier lattice values */
+                int64_t ipred = ipredict_at(P, d, (int64_t)i, (int64_t)j, (int64_t)l, it, T);
+                if (sym != 0) {
+                    P[p] = ipred + (int64_t)(sym - (1 << (m - 1)));
+                    out[p] = szo_lattice_value(P[p], eb_f);
+                } else {
+                    int64_t ok = get_bits(&br, 1), hi = get_bits(&br, 32), lo = get_bits(&br, 32);
+                    if (ok < 0 || hi < 0 || lo < 0) { rc = SZO_ECORRUPT; break; }
+                    int64_t res = (int64_t)(((uint64_t)hi << 32) | (uint64_t)lo);
+                    P[p] = ipred + res;
+                    if (ok) out[p] = szo_lattice_value(P[p], eb_f);
+                    else {
+                        int64_t u = get_bits(&br, 32);
+                        if (u < 0) { rc = SZO_ECORRUPT; break; }
+                        out[p] = u2f((uint32_t)u);
+                    }
+                    Kseen++;
+                }
+                continue;
+            }
             float pred = predict_at(out, d, (int64_t)i, (int64_t)j, (int64_t)l, t, T);
             if (sym != 0) {
                 float step = (float)(sym - (1 << (m - 1))) * twoeb;
@@ -632,6 +881,6 @@ int szo_decompress(const uint8_t *in, size_t in_len, float *out, size_t out_cap_
         off += nb;
     }
     if (rc == SZO_OK && Kseen != K) rc = SZO_ECORRUPT;
-    free(t); free(len); free(cw); free(sorted_sym);
+    free(t); free(it); free(P); free(len); free(cw); free(sorted_sym);
     return rc;
 }

@@ -56,7 +56,18 @@ int szo_compress(const float *x, int ndim, const uint64_t *shape, int mode,
                  double eb_abs, double eb_rel, int layers, int m, double theta,
                  int order, uint8_t *out, size_t out_cap, size_t *out_len,
                  float *recorded_out, uint16_t *codes_out);
-/* Decompress; out_cap_elems must be >= number of points. */
+/* The lattice variant (not the paper's method; a separately labelled fully
+ * parallel form, header byte 113 = 1): values snapped to the 2 eb_f lattice,
+ * integer n-layer prediction from lattice values, residuals coded like the
+ * quantization codes, outliers stored exactly (see szo.c).  eb must be > 0. */
+int64_t szo_lattice_point(float x, float eb_f, int *ok);
+float szo_lattice_value(int64_t p, float eb_f);
+int szo_choose_m_lattice(const float *x, int ndim, const uint64_t *shape, int layers, float eb_f,
+                         double theta);
+int szo_compress_lattice(const float *x, int ndim, const uint64_t *shape, int mode, double eb_abs,
+                         double eb_rel, int layers, int m, double theta, uint8_t *out, size_t out_cap,
+                         size_t *out_len, float *recorded_out, uint16_t *codes_out);
+/* Decompress (either variant); out_cap_elems must be >= number of points. */
 int szo_decompress(const uint8_t *in, size_t in_len, float *out,
                    size_t out_cap_elems);
 

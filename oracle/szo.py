@@ -54,6 +54,14 @@ def lib():
                                    C.c_int, C.c_int, C.c_double, C.c_int, C.c_void_p, C.c_size_t,
                                    C.POINTER(C.c_size_t), C.c_void_p, C.c_void_p]
         L.szo_decompress.argtypes = [C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t]
+        L.szo_lattice_point.argtypes = [C.c_float, C.c_float, C.POINTER(C.c_int)]
+        L.szo_lattice_point.restype = C.c_int64
+        L.szo_lattice_value.argtypes = [C.c_int64, C.c_float]
+        L.szo_lattice_value.restype = C.c_float
+        L.szo_choose_m_lattice.argtypes = [C.c_void_p, C.c_int, u64p, C.c_int, C.c_float, C.c_double]
+        L.szo_compress_lattice.argtypes = [C.c_void_p, C.c_int, u64p, C.c_int, C.c_double, C.c_double,
+                                           C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_size_t,
+                                           C.POINTER(C.c_size_t), C.c_void_p, C.c_void_p]
         _lib = L
     return _lib
 
@@ -140,6 +148,47 @@ def compress(x, mode=REL, eb_abs=0.0, eb_rel=1e-4, n=1, m=0, theta=0.99, order=0
     return (s, rec, codes) if want_aux else s
 
 
+def lattice_point(x, eb_f):
+    """(p, ok): the lattice integer of x and whether its lattice value is
+    within the bound (the lattice variant)."""
+    ok = C.c_int()
+    p = lib().szo_lattice_point(x, eb_f, C.byref(ok))
+    return p, bool(ok.value)
+
+
+def lattice_value(p, eb_f):
+    return lib().szo_lattice_value(int(p), eb_f)
+
+
+def choose_m_lattice(x, n, eb_f, theta=0.99):
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    return lib().szo_choose_m_lattice(x.ctypes.data, x.ndim, _shape(x), n, eb_f, theta)
+
+
+def compress_lattice(x, mode=REL, eb_abs=0.0, eb_rel=1e-4, n=1, m=0, theta=0.99, want_aux=False,
+                     layers=None):
+    """The lattice variant (not the paper's method; labelled separately).
+    Returns the stream (and, with want_aux, the reconstructed values and the
+    codes)."""
+    if layers is not None:
+        n = layers
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    L = lib()
+    cap = L.szo_stream_bound(x.ndim, _shape(x)) + 11 * x.size + 64
+    out = np.zeros(cap, np.uint8)
+    olen = C.c_size_t()
+    rec = np.empty_like(x) if want_aux else None
+    codes = np.empty(x.shape, np.uint16) if want_aux else None
+    rc = L.szo_compress_lattice(x.ctypes.data, x.ndim, _shape(x), mode, eb_abs, eb_rel, n, m, theta,
+                                out.ctypes.data, cap, C.byref(olen),
+                                rec.ctypes.data if want_aux else None,
+                                codes.ctypes.data if want_aux else None)
+    if rc != 0:
+        raise RuntimeError("szo_compress_lattice failed: %d" % rc)
+    s = out[:olen.value].copy()
+    return (s, rec, codes) if want_aux else s
+
+
 def compress_rc(x, **kw):
     try:
         compress(x, **kw)
@@ -192,4 +241,5 @@ def header(s):
     f["nchunks"], f["K"], f["payload_bytes"], f["total_bytes"] = struct.unpack_from("<4Q", b, 72)
     f["theta"], = struct.unpack_from("<d", b, 104)
     f["adaptive"] = b[112]
+    f["lattice"] = b[113]
     return f
