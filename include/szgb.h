@@ -68,7 +68,24 @@ typedef struct {
                            (Sec. III-B; the paper's default is 1) */
     int m;              /* 2..16: 2^m - 1 intervals; 0 = adaptive (Sec. IV-B) */
     double theta;       /* adaptive-m hit-rate threshold, e.g. 0.99 */
+    int variant;        /* SZGB_VARIANT_EXACT (0): the paper's method;
+                           SZGB_VARIANT_LATTICE (1): the separately labelled
+                           lattice variant (below) */
 } szgb_params;
+
+/* The lattice variant is NOT the paper's method: values are first snapped to
+ * the lattice of spacing 2 eb_f (p = rint(x * (1/(2 eb_f))) in double,
+ * |p| < 2^30, eb_f > 0), the integer field is predicted by the same n-layer
+ * coefficients from the neighbours' lattice values (not from decompressed
+ * values), and the residual is coded like a quantization code; outliers
+ * (residual beyond the radius, or a lattice value that misses the bound)
+ * store the residual in 64 bits and, when needed, x exactly.  Every point
+ * is still within the bound.  Compression and decompression are fully
+ * parallel (no wavefront).  Its streams carry tag 1 in header byte 113 and
+ * are never produced unless requested.  Single-field calls only (batches
+ * and the no-allocation path return SZGB_EUNSUPPORTED). */
+#define SZGB_VARIANT_EXACT 0
+#define SZGB_VARIANT_LATTICE 1
 
 typedef struct {
     uint64_t n_points;      /* points in the field */

@@ -377,10 +377,12 @@ int launch_codebook(const uint32_t* hist, DevState* st, uint8_t* len, uint64_t* 
 // ---------------------------------------------------------------------------
 // per-row bit counts: Huffman code bits plus 9 + t record bits after code 0
 
+// lattice variant when OK != nullptr: an outlier record is 1 + 64 bits, +32
+// when its lattice value misses the bound
 __global__ void __launch_bounds__(256) k_rowbits(const uint16_t* __restrict__ codes, uint64_t pitch,
                                                  const float* __restrict__ x, uint64_t rows,
                                                  uint64_t rowlen, const uint8_t* __restrict__ len,
-                                                 uint32_t* rowbytes, DevState* st) {
+                                                 uint32_t* rowbytes, DevState* st, const uint8_t* __restrict__ OK) {
     const int lane = threadIdx.x & 31;
     const uint64_t wglob = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -395,7 +397,7 @@ __global__ void __launch_bounds__(256) k_rowbits(const uint16_t* __restrict__ co
             uint32_t c = crow[l];
             bits += len[c];
             if (c == 0) {
-                bits += 9 + trunc_bits(__float_as_uint(x[base + l]), e_eb);
+                bits += OK ? (uint64_t)(OK[base + l] ? 65 : 97) : (uint64_t)(9 + trunc_bits(__float_as_uint(x[base + l]), e_eb));
                 kcount++;
             }
         }
@@ -411,12 +413,12 @@ __global__ void __launch_bounds__(256) k_rowbits(const uint16_t* __restrict__ co
 }
 
 int launch_rowbits(const uint16_t* codes, uint64_t pitch, const float* x, uint64_t rows, uint64_t rowlen,
-                   const uint8_t* len, uint32_t* rowbytes, DevState* st, cudaStream_t s) {
+                   const uint8_t* len, uint32_t* rowbytes, DevState* st, cudaStream_t s, const uint8_t* OK) {
     uint64_t warps = rows;
     uint64_t blocks = (warps * 32 + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    k_rowbits<<<(int)blocks, 256, 0, s>>>(codes, pitch, x, rows, rowlen, len, rowbytes, st);
+    k_rowbits<<<(int)blocks, 256, 0, s>>>(codes, pitch, x, rows, rowlen, len, rowbytes, st, OK);
     return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
 }
 
@@ -538,6 +540,7 @@ __global__ void __launch_bounds__(256) k_write_meta(const CallParams cp, uint64_
         wr_u64(h + 96, st->total);
         wr_u64(h + 104, (uint64_t)__double_as_longlong(cp.theta));
         h[112] = (uint8_t)(cp.m_user == 0);
+        h[113] = (uint8_t)cp.variant;
     }
     for (uint64_t i = tid; i < cb; i += nthr) {
         uint64_t e = i / 3;
@@ -576,7 +579,7 @@ __device__ __forceinline__ void put64(uint32_t* buf, uint32_t o, uint64_t v, int
 }
 
 constexpr int kEncWarps = 8;
-constexpr int kEncBufWords = 112;
+constexpr int kEncBufWords = 168;  // 32 points of up to 64 + 97 bits, plus the carry word
 
 // payload: one warp per row; 32 points at a time are placed by a warp scan of
 // their bit lengths into a shared-memory word buffer whose completed words
@@ -593,12 +596,19 @@ __device__ __forceinline__ void store_word_bytes(uint8_t* plb, uint64_t gw, uint
     }
 }
 
+struct LatticeRec {
+    const int32_t* P;   // lattice integers (nullptr: the paper's method)
+    const uint8_t* OK;  // lattice value within the bound
+    int ndim, layers;
+    uint64_t d1;        // rows per plane (the row index of a point is plane * d1 + row)
+};
+
 __global__ void __launch_bounds__(kEncWarps * 32) k_encode(const uint16_t* __restrict__ codes, uint64_t pitch,
                                                           const float* __restrict__ x, uint64_t rows,
                                                           uint64_t rowlen, const uint8_t* __restrict__ len,
                                                           const uint64_t* __restrict__ cw,
                                                           const uint64_t* __restrict__ rowoff,
-                                                          uint8_t* out, DevState* st) {
+                                                          uint8_t* out, DevState* st, const LatticeRec LR) {
     __shared__ uint32_t sbuf[kEncWarps][kEncBufWords];
     if (!st->fits || st->err) return;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -626,12 +636,22 @@ __global__ void __launch_bounds__(kEncWarps * 32) k_encode(const uint16_t* __res
             int nrec = 0;
             uint32_t se = 0, mb = 0;
             int t = 0;
+            uint64_t lres = 0;
+            bool lok = true;
             if (v && c == 0) {
                 uint32_t u = __float_as_uint(x[base + l]);
-                t = trunc_bits(u, e_eb);
-                se = u >> 23;
-                mb = t ? ((u >> (23 - t)) & ((1u << t) - 1u)) : 0u;
-                nrec = 9 + t;
+                if (LR.P) {  // lattice record: flag, r (64 bits), x when the flag is 0
+                    lok = LR.OK[base + l] != 0;
+                    lres = (uint64_t)lattice_resid_rt(LR.P, LR.ndim, LR.layers, LR.d1, rowlen, (int64_t)(r / LR.d1),
+                                                      (int64_t)(r % LR.d1), (int64_t)l);
+                    se = u;
+                    nrec = lok ? 65 : 97;
+                } else {
+                    t = trunc_bits(u, e_eb);
+                    se = u >> 23;
+                    mb = t ? ((u >> (23 - t)) & ((1u << t) - 1u)) : 0u;
+                    nrec = 9 + t;
+                }
             }
             uint32_t nbits = (uint32_t)(L + nrec);
             uint32_t incl = nbits;
@@ -642,7 +662,12 @@ __global__ void __launch_bounds__(kEncWarps * 32) k_encode(const uint16_t* __res
             uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
             uint32_t off = bitpos + incl - nbits;
             if (L) put64(buf, off, code, L);
-            if (nrec) {
+            if (nrec && LR.P) {
+                put32(buf, off + L, lok ? 1u : 0u, 1);
+                put32(buf, off + L + 1, (uint32_t)(lres >> 32), 32);
+                put32(buf, off + L + 33, (uint32_t)lres, 32);
+                if (!lok) put32(buf, off + L + 65, se, 32);
+            } else if (nrec) {
                 put32(buf, off + L, se, 9);
                 if (t) put32(buf, off + L + 9, mb, t);
             }
@@ -679,11 +704,18 @@ int launch_write_meta(const CallParams& cp, uint64_t rows, const uint8_t* len, c
 }
 
 int launch_encode(const uint16_t* codes, uint64_t pitch, const float* x, uint64_t rows, uint64_t rowlen, const uint8_t* len,
-                  const uint64_t* cw, const uint64_t* rowoff, uint8_t* out, DevState* st, cudaStream_t s) {
+                  const uint64_t* cw, const uint64_t* rowoff, uint8_t* out, DevState* st, cudaStream_t s,
+                  const int32_t* P, const uint8_t* OK, int ndim, int layers, uint64_t d1) {
+    LatticeRec LR;
+    LR.P = P;
+    LR.OK = OK;
+    LR.ndim = ndim;
+    LR.layers = layers;
+    LR.d1 = d1;
     uint64_t blocks = (rows + kEncWarps - 1) / kEncWarps;
     if (blocks > 152 * 32) blocks = 152 * 32;
     if (blocks < 1) blocks = 1;
-    k_encode<<<(int)blocks, kEncWarps * 32, 0, s>>>(codes, pitch, x, rows, rowlen, len, cw, rowoff, out, st);
+    k_encode<<<(int)blocks, kEncWarps * 32, 0, s>>>(codes, pitch, x, rows, rowlen, len, cw, rowoff, out, st, LR);
     return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
 }
 

@@ -108,105 +108,6 @@ __device__ __forceinline__ bool wait_progress(const unsigned int* p, unsigned in
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
-// Per-lane bit reader over one row chunk (MSB-first), for decompression.
-
-struct BitReader {
-    const uint8_t* base;
-    uint64_t wpos;       // byte offset of the next word to load (multiple of 4)
-    uint64_t endoff;     // bytes available from base
-    uint64_t win;        // valid bits, MSB aligned
-    int nb;              // valid bits in win
-    uint32_t pf0, pf1;   // the next two words (already requested)
-    uint64_t consumed;   // bits consumed
-
-    __device__ __forceinline__ uint32_t load_word(uint64_t off) const {
-        if (off + 4 <= endoff) return bswap32(__ldg(reinterpret_cast<const uint32_t*>(base + off)));
-        uint32_t v = 0;
-        for (int i = 0; i < 4; i++) v = (v << 8) | (off + i < endoff ? (uint32_t)base[off + i] : 0u);
-        return v;
-    }
-    __device__ __forceinline__ void init(const uint8_t* b, uint64_t start, uint64_t end) {
-        base = b;
-        endoff = end;
-        uint64_t a = start & ~(uint64_t)3;
-        int skip = (int)(start - a) * 8;
-        uint32_t w0 = load_word(a);
-        pf0 = load_word(a + 4);
-        pf1 = load_word(a + 8);
-        wpos = a + 12;
-        win = ((uint64_t)w0 << 32) << skip;
-        nb = 32 - skip;
-        consumed = 0;
-    }
-    __device__ __forceinline__ void refill() {
-        if (nb <= 32) {
-            win |= (uint64_t)pf0 << (32 - nb);
-            nb += 32;
-            pf0 = pf1;
-            pf1 = load_word(wpos);
-            wpos += 4;
-        }
-    }
-    // bit p (0 = next bit) looking past the window into the prefetched words
-    __device__ __forceinline__ uint32_t bit_at(int p) const {
-        if (p < nb) return (uint32_t)(win >> (63 - p)) & 1u;
-        p -= nb;
-        if (p < 32) return (pf0 >> (31 - p)) & 1u;
-        p -= 32;
-        return (pf1 >> (31 - p)) & 1u;
-    }
-    __device__ __forceinline__ void skip(int n) {
-        consumed += (uint64_t)n;
-        while (n > 0) {
-            refill();
-            int s = n < nb ? n : nb;
-            win = (s == 64) ? 0 : (win << s);
-            nb -= s;
-            n -= s;
-        }
-    }
-    __device__ __forceinline__ uint32_t take(int n) {  // n <= 32
-        if (n == 0) return 0;
-        refill();
-        uint32_t v = (uint32_t)(win >> (64 - n));
-        win <<= n;
-        nb -= n;
-        consumed += (uint64_t)n;
-        return v;
-    }
-};
-
-// decode one quantization code; long codes (> lut bits) by canonical search
-__device__ __forceinline__ int decode_symbol(BitReader& br, const uint32_t* s_lut, int T,
-                                             const uint32_t* s_tab, const uint16_t* g_sorted,
-                                             int maxlen, bool& bad) {
-    br.refill();
-    uint32_t e = s_lut[(uint32_t)(br.win >> (64 - T))];
-    int len = (int)(e & 0xffu);
-    if (len != 0) {
-        br.win <<= len;
-        br.nb -= len;
-        br.consumed += (uint64_t)len;
-        return (int)(e >> 8);
-    }
-    // canonical search: the codes of length L are first[L] .. first[L]+count[L]-1
-    uint64_t c = 0;
-    for (int L = 1; L <= maxlen; L++) {
-        c = (c << 1) | br.bit_at(L - 1);
-        if (L <= T) continue;
-        uint64_t first = ((uint64_t)s_tab[65 + L] << 32) | s_tab[L];
-        uint32_t cnt = s_tab[130 + L];
-        if (cnt && c >= first && c - first < cnt) {
-            br.skip(L);
-            return (int)g_sorted[s_tab[195 + L] + (uint32_t)(c - first)];
-        }
-    }
-    bad = true;
-    br.skip(1);
-    return 0;
-}
-
-// ---------------------------------------------------------------------------
 // Huffman decode of every row (a row is one stream chunk), before the
 // reconstruction wavefront: one lane per row, a warp's 32 lanes in lockstep
 // (one symbol per lane per step), codes staged through a shared tile and

@@ -151,6 +151,8 @@ int check_params(const szgb_params* p, CallParams* cp) {
     cp->layers = p->layers;
     cp->m_user = p->m;
     cp->theta = p->theta;
+    if (p->variant != SZGB_VARIANT_EXACT && p->variant != SZGB_VARIANT_LATTICE) return SZGB_EINVAL;
+    cp->variant = p->variant;
     return p->layers > kMaxLayers ? SZGB_EUNSUPPORTED : SZGB_OK;
 }
 
@@ -219,6 +221,7 @@ void halo_sizes(const WaveGeom& g, int layers, size_t* row_floats, size_t* plane
 
 int dev_errors(const DevState& s) {
     if (s.err & kErrNonFinite) return SZGB_ENONFINITE;
+    if (s.err & kErrRange) return SZGB_EINVAL;
     if (s.err & kErrTimeout) return SZGB_ETIMEOUT;
     if (s.err & kErrCorrupt) return SZGB_ECORRUPT;
     if (s.err & kErrOverflow) return SZGB_ETRUNC;
@@ -293,6 +296,12 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
     A.add(&wargs, wave_args_bytes());
     A.add(&worder, 2 * (size_t)g.num_ctas);
     A.add(&wticket, 1);
+    int32_t* latP = nullptr;
+    uint8_t* latOK = nullptr;
+    if (cp.variant == SZGB_VARIANT_LATTICE) {
+        A.add(&latP, N);
+        A.add(&latOK, N);
+    }
     if (!direct_in) A.add(&xs, N);
     else xs = nullptr;
     if (!direct_out) A.add(&ostage, bound);
@@ -318,11 +327,15 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
         PhaseTimer t(c, PH_RANGE);
         if ((rc = launch_range(x, N, st, cp, partials, range_blocks, s))) return rc;
     }
-    if (cp.m_user == 0) {
+    if (cp.variant == SZGB_VARIANT_LATTICE) {
+        // the lattice variant: adaptive m, lattice integers and residual codes, all parallel
+        PhaseTimer t(c, PH_WAVE_C);
+        if ((rc = launch_lattice_compress(x, cp, latP, latOK, codes, cpitch, rec_dev, st, s))) return rc;
+    } else if (cp.m_user == 0) {
         PhaseTimer t(c, PH_ADAPT);
         if ((rc = launch_adapt(x, cp, st, s))) return rc;
     }
-    {
+    if (cp.variant == SZGB_VARIANT_EXACT) {
         PhaseTimer t(c, PH_WAVE_C);
         if (!rec_dev) {
             // the persistent kernel, items in ready-time order
@@ -346,7 +359,7 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
     }
     {
         PhaseTimer t(c, PH_ROWBITS);
-        if ((rc = launch_rowbits(codes, cpitch, x, rows, rowlen, len, rowbytes, st, s))) return rc;
+        if ((rc = launch_rowbits(codes, cpitch, x, rows, rowlen, len, rowbytes, st, s, latOK))) return rc;
     }
     {
         PhaseTimer t(c, PH_SCAN);
@@ -355,7 +368,9 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
     {
         PhaseTimer t(c, PH_WRITE);
         if ((rc = launch_write_meta(cp, rows, len, nodebuf, rowbytes, rowoff, dst, st, s))) return rc;
-        if ((rc = launch_encode(codes, cpitch, x, rows, rowlen, len, cw, rowoff, dst, st, s))) return rc;
+        if ((rc = launch_encode(codes, cpitch, x, rows, rowlen, len, cw, rowoff, dst, st, s, latP, latOK, cp.ndim,
+                                layers, cp.d1)))
+            return rc;
     }
     if (codes_dev && cudaMemcpy2DAsync(codes_dev, rowlen * 2, codes, cpitch * 2, rowlen * 2, rows,
                                        cudaMemcpyDeviceToDevice, s) != cudaSuccess)
@@ -400,6 +415,7 @@ struct Header {
     uint32_t nsym;
     uint64_t nchunks, K, payload, total;
     int adaptive;
+    int variant;
 };
 
 uint64_t rd_le(const uint8_t* p, int n) {
@@ -435,6 +451,8 @@ int parse_header(const uint8_t* h, size_t in_len, Header* o) {
     o->total = rd_le(h + 96, 8);
     u = rd_le(h + 104, 8); memcpy(&o->theta, &u, 8);
     o->adaptive = h[112];
+    o->variant = h[113];
+    if (o->variant > 1) return SZGB_ECORRUPT;
     if (o->ndim < 1 || o->ndim > 3 || o->layers < 1 || o->layers > 4 || o->m < 2 || o->m > 16) return SZGB_ECORRUPT;
     if (o->tw != 2 && o->tw != 4 || o->mode > 2) return SZGB_ECORRUPT;
     if (o->d0 == 0 || o->d1 == 0 || o->d2 == 0 || o->d0 > 0xffffffffull || o->d1 > 0xffffffffull ||
@@ -491,9 +509,18 @@ int decompress_impl(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_dev
     uint8_t *lenbuf, *istage;
     uint16_t* codes;
     const uint64_t cpitch = (H.d2 + 7) & ~(uint64_t)7;
+    const bool lattice = H.variant == SZGB_VARIANT_LATTICE;
+    int32_t* latR = nullptr;
+    uint8_t* latEX = nullptr;
     Arena A;
     A.add(&st, 1);
-    A.add(&codes, rows * cpitch + 8);
+    if (lattice) {
+        A.add(&latR, N);
+        A.add(&latEX, N);
+        codes = nullptr;
+    } else {
+        A.add(&codes, rows * cpitch + 8);
+    }
     A.add(&halo_row, hrow);
     A.add(&halo_plane, hplane);
     A.add(&prog, g.num_ctas);
@@ -549,13 +576,18 @@ int decompress_impl(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_dev
         if ((rc = launch_read_rowbytes(table, H.tw, rows, rowbytes, s))) return rc;
         if ((rc = launch_scan_rows(rowbytes, rows, rowoff, blocksums, st, 0, s))) return rc;
     }
-    {
-        PhaseTimer t(c, PH_DEC_ROWS);
-        if ((rc = launch_decode_rows(payload, rowoff, rowbytes, payload + H.payload, lut, dectab, codes, cpitch, dst,
-                                     rows, H.d2, st, s)))
+    if (lattice) {
+        PhaseTimer t(c, PH_WAVE_D);
+        if ((rc = launch_lattice_decompress(payload, rowoff, rowbytes, payload + H.payload, lut, dectab, H.ndim,
+                                            H.layers, H.d0, H.d1, H.d2, latR, latEX, dst, st, s)))
             return rc;
-    }
-    {
+    } else {
+        {
+            PhaseTimer t(c, PH_DEC_ROWS);
+            if ((rc = launch_decode_rows(payload, rowoff, rowbytes, payload + H.payload, lut, dectab, codes, cpitch,
+                                         dst, rows, H.d2, st, s)))
+                return rc;
+        }
         PhaseTimer t(c, PH_WAVE_D);
         ArgsBuf ha(wave_args_bytes());
         if ((rc = wave_args_decompress(ha.p, g, codes, cpitch, dst, halo_row, halo_plane, prog, st, c->timeout_ns)))
@@ -752,6 +784,7 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
         CompPlan& q = P[f];
         if (!data[f] || !out[f] || ((uintptr_t)data[f] % 16) || ((uintptr_t)out[f] % 4)) return SZGB_EINVAL;
         if ((rc = check_params(&params[f], &q.cp))) return rc;
+        if (q.cp.variant != SZGB_VARIANT_EXACT) return SZGB_EUNSUPPORTED;  // batches run the paper's method
         q.n = q.cp.d0 * q.cp.d1 * q.cp.d2;
         q.rows = q.cp.d0 * q.cp.d1;
         q.rowlen = q.cp.d2;
@@ -946,7 +979,7 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
     for (int f = 0; f < count; f++) {
         DecPlan& q = P[f];
         if ((rc = parse_header(static_cast<uint8_t*>(c->h_batch) + (size_t)f * kHeaderBytes, in_len[f], &q.H))) return rc;
-        if (q.H.layers > kMaxLayers) return SZGB_EUNSUPPORTED;
+        if (q.H.layers > kMaxLayers || q.H.variant != SZGB_VARIANT_EXACT) return SZGB_EUNSUPPORTED;
         q.n = q.H.d0 * q.H.d1 * q.H.d2;
         if (out_cap[f] < q.n) return SZGB_EINVAL;
         q.rows = q.H.nchunks;
@@ -1362,8 +1395,10 @@ size_t szgb_compress_bound(const szgb_params* p) {
     int rc = check_params(p, &cp);
     if (rc != SZGB_OK && rc != SZGB_EUNSUPPORTED) return 0;
     uint64_t N = cp.d0 * cp.d1 * cp.d2, rows = cp.d0 * cp.d1;
-    // header + codebook + table + rows * (N/row points * (64 + 32) bits)
-    return (size_t)(kHeaderBytes + 3 * 65536 + 4 + 4 * rows + 4 + rows + N * 12 + 16);
+    // header + codebook + table + per point at most a 64-bit code and its
+    // record (9 + 23 bits; lattice variant: 1 + 64 + 32 bits)
+    const uint64_t per = cp.variant == SZGB_VARIANT_LATTICE ? 21 : 12;
+    return (size_t)(kHeaderBytes + 3 * 65536 + 4 + 4 * rows + 4 + rows + N * per + 16);
 }
 
 int szgb_compress(szgb_ctx* c, const float* data, int data_on_device, const szgb_params* p, uint8_t* out,
@@ -1400,6 +1435,7 @@ int szgb_stream_info(const uint8_t* in_host, size_t in_len, szgb_params* out, ui
     out->layers = H.layers;
     out->m = H.m;
     out->theta = H.theta;
+    out->variant = H.variant;
     if (n_unpred) *n_unpred = H.K;
     return SZGB_OK;
 }

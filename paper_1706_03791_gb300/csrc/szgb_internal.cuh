@@ -26,6 +26,7 @@ constexpr uint32_t kErrTimeout = 1u;
 constexpr uint32_t kErrCorrupt = 2u;
 constexpr uint32_t kErrNonFinite = 4u;
 constexpr uint32_t kErrOverflow = 8u;   // stream does not fit in the output
+constexpr uint32_t kErrRange = 16u;     // lattice variant: eb_f = 0 or lattice integers >= 2^30
 
 // State of one call, in device memory (zeroed before the call).
 struct DevState {
@@ -64,6 +65,7 @@ struct CallParams {
     int layers;
     int m_user;              // 0 = adaptive
     double theta;
+    int variant;             // 0 = the paper's method, 1 = the lattice variant
 };
 
 // --------------------------------------------------------------------------
@@ -269,6 +271,148 @@ __device__ __forceinline__ void st_shared_f32_if(bool p, uint32_t addr, float v)
 
 __device__ __forceinline__ uint32_t bswap32(uint32_t v) { return __byte_perm(v, 0, 0x0123); }
 
+// ---------------------------------------------------------------------------
+// Per-lane bit reader over one row chunk (MSB-first), for decompression.
+// (used by the row decoders of both variants)
+
+struct BitReader {
+    const uint8_t* base;
+    uint64_t wpos;       // byte offset of the next word to load (multiple of 4)
+    uint64_t endoff;     // bytes available from base
+    uint64_t win;        // valid bits, MSB aligned
+    int nb;              // valid bits in win
+    uint32_t pf0, pf1;   // the next two words (already requested)
+    uint64_t consumed;   // bits consumed
+
+    __device__ __forceinline__ uint32_t load_word(uint64_t off) const {
+        if (off + 4 <= endoff) return bswap32(__ldg(reinterpret_cast<const uint32_t*>(base + off)));
+        uint32_t v = 0;
+        for (int i = 0; i < 4; i++) v = (v << 8) | (off + i < endoff ? (uint32_t)base[off + i] : 0u);
+        return v;
+    }
+    __device__ __forceinline__ void init(const uint8_t* b, uint64_t start, uint64_t end) {
+        base = b;
+        endoff = end;
+        uint64_t a = start & ~(uint64_t)3;
+        int skip = (int)(start - a) * 8;
+        uint32_t w0 = load_word(a);
+        pf0 = load_word(a + 4);
+        pf1 = load_word(a + 8);
+        wpos = a + 12;
+        win = ((uint64_t)w0 << 32) << skip;
+        nb = 32 - skip;
+        consumed = 0;
+    }
+    __device__ __forceinline__ void refill() {
+        if (nb <= 32) {
+            win |= (uint64_t)pf0 << (32 - nb);
+            nb += 32;
+            pf0 = pf1;
+            pf1 = load_word(wpos);
+            wpos += 4;
+        }
+    }
+    // bit p (0 = next bit) looking past the window into the prefetched words
+    __device__ __forceinline__ uint32_t bit_at(int p) const {
+        if (p < nb) return (uint32_t)(win >> (63 - p)) & 1u;
+        p -= nb;
+        if (p < 32) return (pf0 >> (31 - p)) & 1u;
+        p -= 32;
+        return (pf1 >> (31 - p)) & 1u;
+    }
+    __device__ __forceinline__ void skip(int n) {
+        consumed += (uint64_t)n;
+        while (n > 0) {
+            refill();
+            int s = n < nb ? n : nb;
+            win = (s == 64) ? 0 : (win << s);
+            nb -= s;
+            n -= s;
+        }
+    }
+    __device__ __forceinline__ uint32_t take(int n) {  // n <= 32
+        if (n == 0) return 0;
+        refill();
+        uint32_t v = (uint32_t)(win >> (64 - n));
+        win <<= n;
+        nb -= n;
+        consumed += (uint64_t)n;
+        return v;
+    }
+};
+
+// decode one quantization code; long codes (> lut bits) by canonical search
+__device__ __forceinline__ int decode_symbol(BitReader& br, const uint32_t* s_lut, int T,
+                                             const uint32_t* s_tab, const uint16_t* g_sorted,
+                                             int maxlen, bool& bad) {
+    br.refill();
+    uint32_t e = s_lut[(uint32_t)(br.win >> (64 - T))];
+    int len = (int)(e & 0xffu);
+    if (len != 0) {
+        br.win <<= len;
+        br.nb -= len;
+        br.consumed += (uint64_t)len;
+        return (int)(e >> 8);
+    }
+    // canonical search: the codes of length L are first[L] .. first[L]+count[L]-1
+    uint64_t c = 0;
+    for (int L = 1; L <= maxlen; L++) {
+        c = (c << 1) | br.bit_at(L - 1);
+        if (L <= T) continue;
+        uint64_t first = ((uint64_t)s_tab[65 + L] << 32) | s_tab[L];
+        uint32_t cnt = s_tab[130 + L];
+        if (cnt && c >= first && c - first < cnt) {
+            br.skip(L);
+            return (int)g_sorted[s_tab[195 + L] + (uint32_t)(c - first)];
+        }
+    }
+    bad = true;
+    br.skip(1);
+    return 0;
+}
+
+// --------------------------------------------------------------------------
+// the lattice variant (a separately labelled, fully parallel form; see
+// k_lattice.cu): lattice integer of x, p = rint(x * inv) in double with
+// inv = 1 / (2 eb_f), and whether (float)(p * 2 eb_f) is within the bound
+__device__ __forceinline__ int64_t lattice_point(float x, double inv, double twoeb, double ebd, bool& ok) {
+    const int64_t p = (int64_t)rint(__dmul_rn((double)x, inv));
+    const float v = __double2float_rn(__dmul_rn((double)p, twoeb));
+    ok = fabs(__dsub_rn((double)x, (double)v)) < ebd;
+    return p;
+}
+
+// integer residual p - sum_k c_k p(x - k) of the n-layer predictor over the
+// lattice integers P ([d0][d1][d2]), neighbours outside the domain = 0
+template <int ND, int NL>
+__device__ __forceinline__ int64_t lattice_resid(const int32_t* __restrict__ P, uint64_t d1, uint64_t d2, int64_t i,
+                                                 int64_t j, int64_t l) {
+    int64_t pred = 0;
+#pragma unroll
+    for (int k0 = NL; k0 >= 0; k0--) {
+        if (ND < 3 && k0 > 0) continue;
+#pragma unroll
+        for (int k1 = NL; k1 >= 0; k1--) {
+            if (ND < 2 && k1 > 0) continue;
+#pragma unroll
+            for (int k2 = NL; k2 >= 0; k2--) {
+                if (k0 == 0 && k1 == 0 && k2 == 0) continue;
+                const int64_t ii = i - k0, jj = j - k1, ll = l - k2;
+                if (ii < 0 || jj < 0 || ll < 0) continue;
+                pred += (int64_t)term_coef(NL, k0, k1, k2) * (int64_t)P[((uint64_t)ii * d1 + (uint64_t)jj) * d2 + (uint64_t)ll];
+            }
+        }
+    }
+    return (int64_t)P[((uint64_t)i * d1 + (uint64_t)j) * d2 + (uint64_t)l] - pred;
+}
+
+__device__ __forceinline__ int64_t lattice_resid_rt(const int32_t* P, int ndim, int layers, uint64_t d1, uint64_t d2,
+                                                    int64_t i, int64_t j, int64_t l) {
+    if (ndim == 3) return layers == 1 ? lattice_resid<3, 1>(P, d1, d2, i, j, l) : lattice_resid<3, 2>(P, d1, d2, i, j, l);
+    if (ndim == 2) return layers == 1 ? lattice_resid<2, 1>(P, d1, d2, i, j, l) : lattice_resid<2, 2>(P, d1, d2, i, j, l);
+    return layers == 1 ? lattice_resid<1, 1>(P, d1, d2, i, j, l) : lattice_resid<1, 2>(P, d1, d2, i, j, l);
+}
+
 // --------------------------------------------------------------------------
 // geometry of the wavefront launch (host-computed, passed by value)
 struct WaveGeom {
@@ -292,6 +436,13 @@ int launch_wave_compress(const WaveGeom& g, int layers, const float* x, uint16_t
                          DevState* st, uint64_t timeout_ns, cudaStream_t s);
 // decompression: rows decoded first (codes into a row-pitched array, the
 // values of unpredictable points into `out`), then the reconstruction wavefront
+// the lattice variant (k_lattice.cu)
+int launch_lattice_compress(const float* x, const CallParams& cp, int32_t* P, uint8_t* OK, uint16_t* codes,
+                            uint64_t cpitch, float* recorded, DevState* st, cudaStream_t s);
+int launch_lattice_decompress(const uint8_t* payload, const uint64_t* rowoff, const uint32_t* rowbytes,
+                              const uint8_t* stream_end, const uint32_t* lut, const uint32_t* dec_tab, int ndim,
+                              int layers, uint64_t d0, uint64_t d1, uint64_t d2, int32_t* R, uint8_t* EX, float* out,
+                              DevState* st, cudaStream_t s);
 int launch_decode_rows(const uint8_t* payload, const uint64_t* rowoff, const uint32_t* rowbytes,
                        const uint8_t* stream_end, const uint32_t* lut, const uint32_t* dec_tab, uint16_t* codes,
                        uint64_t cpitch, float* out, uint64_t rows, uint64_t N, DevState* st, cudaStream_t s);
@@ -315,14 +466,17 @@ int launch_histogram(const uint16_t* codes, uint64_t rows, uint64_t rowlen, uint
 int launch_codebook(const uint32_t* hist, DevState* st, uint8_t* len, uint64_t* cw, uint64_t* sortbuf,
                     uint32_t* nodebuf, cudaStream_t s);
 int launch_rowbits(const uint16_t* codes, uint64_t pitch, const float* x, uint64_t rows, uint64_t rowlen,
-                   const uint8_t* len, uint32_t* rowbytes, DevState* st, cudaStream_t s);
+                   const uint8_t* len, uint32_t* rowbytes, DevState* st, cudaStream_t s,
+                   const uint8_t* OK = nullptr);
 int launch_scan_rows(const uint32_t* rowbytes, uint64_t rows, uint64_t* rowoff, uint64_t* blocksums,
                      DevState* st, int finalize_compress, cudaStream_t s);
 int launch_write_meta(const CallParams& cp, uint64_t rows, const uint8_t* len, const uint32_t* usedlist,
                       const uint32_t* rowbytes, const uint64_t* rowoff, uint8_t* out, DevState* st,
                       cudaStream_t s);
 int launch_encode(const uint16_t* codes, uint64_t pitch, const float* x, uint64_t rows, uint64_t rowlen, const uint8_t* len,
-                  const uint64_t* cw, const uint64_t* rowoff, uint8_t* out, DevState* st, cudaStream_t s);
+                  const uint64_t* cw, const uint64_t* rowoff, uint8_t* out, DevState* st, cudaStream_t s,
+                  const int32_t* P = nullptr, const uint8_t* OK = nullptr, int ndim = 0, int layers = 0,
+                  uint64_t d1 = 1);
 int launch_decode_tables(const uint8_t* codebook, uint32_t nsym, int m, uint32_t* lut, uint32_t* dec_tab,
                          uint8_t* lenbuf, uint32_t* symbuf, DevState* st, cudaStream_t s);
 int launch_read_rowbytes(const uint8_t* table, int width, uint64_t rows, uint32_t* rowbytes,

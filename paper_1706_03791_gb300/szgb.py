@@ -31,7 +31,7 @@ class SzgbError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("ndim", C.c_int), ("shape", C.c_uint64 * 3), ("mode", C.c_int),
                 ("eb_abs", C.c_double), ("eb_rel", C.c_double), ("layers", C.c_int),
-                ("m", C.c_int), ("theta", C.c_double)]
+                ("m", C.c_int), ("theta", C.c_double), ("variant", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -118,7 +118,10 @@ EXPORTS = ["szgb_create", "szgb_destroy", "szgb_set_stream", "szgb_compress_boun
            "szgb_server_destroy", "szgb_autotune", "szgb_autotune_batch", "szgb_tune_save", "szgb_tune_load"]
 
 
-def make_params(shape, mode=REL, eb_abs=0.0, eb_rel=1e-4, layers=1, m=0, theta=0.99) -> Params:
+VARIANT_EXACT, VARIANT_LATTICE = 0, 1
+
+
+def make_params(shape, mode=REL, eb_abs=0.0, eb_rel=1e-4, layers=1, m=0, theta=0.99, variant=0) -> Params:
     p = Params()
     shape = tuple(int(s) for s in shape)
     p.ndim = len(shape)
@@ -126,6 +129,7 @@ def make_params(shape, mode=REL, eb_abs=0.0, eb_rel=1e-4, layers=1, m=0, theta=0
         p.shape[i] = shape[i] if i < len(shape) else 0
     p.mode, p.eb_abs, p.eb_rel, p.layers, p.m, p.theta = mode, float(eb_abs), float(eb_rel), \
         int(layers), int(m), float(theta)
+    p.variant = int(variant)
     return p
 
 
