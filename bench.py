@@ -423,6 +423,9 @@ def main():
     ap.add_argument("--layers", type=int, default=1)
     ap.add_argument("--ebrel", type=float, default=1e-4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variant", default="exact", choices=["exact", "lattice"],
+                    help="exact: the paper's method (default); lattice: the separately labelled "
+                         "fully parallel lattice variant, reported beside it")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
     ap.add_argument("--duration", type=float, default=30.0, help="serve: seconds of arrivals")
     ap.add_argument("--workload", default="3d", choices=["3d", "climate79", "uneven512", "serve"],
@@ -461,7 +464,7 @@ def main():
     ctx = szgb.Context(local)
     stream = torch.cuda.Stream(device=dev)
     ctx.set_stream(stream.cuda_stream)
-    kw = dict(eb_rel=args.ebrel, layers=args.layers, m=0)
+    kw = dict(eb_rel=args.ebrel, layers=args.layers, m=0, variant=1 if args.variant == "lattice" else 0)
     bound = szgb.compress_bound(x_np.shape, **kw)
     sbuf = torch.empty(bound, dtype=torch.uint8, device=dev)
     y = torch.empty_like(x)
@@ -552,6 +555,9 @@ def main():
     # roofline of the dominant kernel: live CUDA-event phase times
     peak, peak_kind = peaks()
     bits_pp = stream_bytes * 8.0 / N
+    # compress: x read + codes written; decompress: stream read + values written
+    # (the lattice variant's phases carry the same names: its parallel code
+    # and reconstruction passes)
     algo = {"wave_compress": 4.0 + 2.0, "wave_decompress": bits_pp / 8.0 + 4.0}
     dom = max(algo, key=lambda k: phases.get(k, (0, 0))[0])
     ms_dom, calls_dom = phases[dom]
@@ -570,7 +576,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "shape": list(x_np.shape), "eb_rel": args.ebrel,
+        "config": {"workload": WORKLOAD + ("" if args.variant == "exact" else "-LATTICE-VARIANT"),
+                   "variant": args.variant, "shape": list(x_np.shape), "eb_rel": args.ebrel,
                    "layers": args.layers, "m": "adaptive", "m_chosen": int(st0.m),
                    "l2": "flushed (256 MiB write) before every step",
                    "parallelism": "replicas" if ws > 1 else "single"},
@@ -583,7 +590,11 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": nbytes + stream_bytes,
                 "d2h_bytes_per_step": stream_bytes + nbytes},
-        "gpu_launches": 17 * args.steps,
+        # kernels of this library per step: compress 11 (range, adapt, wavefront,
+        # histogram, codebook, row bits, 3 scan, metadata, encode), decompress 7
+        # (tables, row bytes, 3 scan, row decode, wavefront); the lattice variant
+        # compress 12, decompress 7 + 3 axis scans per layer
+        "gpu_launches": (18 if args.variant == "exact" else 19 + 3 * args.layers) * args.steps,
         "clocks": clk,
         "wall_s_timed": t_wall,
     }

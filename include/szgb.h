@@ -74,7 +74,7 @@ typedef struct {
 } szgb_params;
 
 /* The lattice variant is NOT the paper's method: values are first snapped to
- * the lattice of spacing 2 eb_f (p = rint(x * (1/(2 eb_f))) in double,
+ * the lattice of spacing 2 eb_f (p = rint(x * (1/(2 eb_f))) in binary32,
  * |p| < 2^30, eb_f > 0), the integer field is predicted by the same n-layer
  * coefficients from the neighbours' lattice values (not from decompressed
  * values), and the residual is coded like a quantization code; outliers

@@ -36,14 +36,15 @@
  *
  * The lattice variant (szo_compress_lattice) is NOT the paper's method but a
  * separately labelled, fully parallel form of it: every value is snapped to
- * the lattice of spacing 2 eb_f first, p = rint(x * (1 / (2 eb_f))) in double
- * (the reciprocal rounded once), |p| < 2^30; the
+ * the lattice of spacing 2 eb_f first, p = rint(x * inv) in binary32 with
+ * inv = 1 / (2 eb_f) rounded once, |p| < 2^30; the
  * integer field p is predicted by the same n-layer coefficients in exact
  * integer arithmetic from the *lattice* values of the neighbours (zero
  * outside the domain), and the residual r = p - pred takes the place of the
  * quantization code (code r + 2^(m-1) when |r| <= 2^(m-1)-1).  A point is an
- * outlier (code 0) when |r| is larger or its lattice value (float)(p * 2 eb_f)
- * misses the bound; its record is a flag bit (1: the lattice value is within
+ * outlier (code 0) when |r| is larger or its lattice value (float)p * 2 eb_f
+ * (binary32) misses the bound (|x - v| < eb_f or x == v, as the quantizer's
+ * check); its record is a flag bit (1: the lattice value is within
  * the bound), r as 64-bit two's complement and, when the flag is 0, the 32
  * bits of x.  Since the prediction never uses reconstructed values, every
  * residual is independent of the others, and the inverse of the predictor
@@ -576,17 +577,19 @@ static int64_t ipredict_at(const int64_t *P, const uint64_t d[3], int64_t i, int
     return s;
 }
 
-/* the lattice integer of x and whether its lattice value is within the bound */
+/* the lattice integer of x and whether its lattice value is within the
+ * bound; binary32 throughout, each operation rounded to nearest-even */
 int64_t szo_lattice_point(float x, float eb_f, int *ok) {
-    double twoeb = 2.0 * (double)eb_f;
-    double inv = 1.0 / twoeb;
-    int64_t p = (int64_t)rint((double)x * inv);
-    float v = (float)((double)p * twoeb);
-    if (ok) *ok = fabs((double)x - (double)v) < (double)eb_f;
+    float twoeb = 2.0f * eb_f;
+    float inv = 1.0f / twoeb;
+    float y = rintf(x * inv);
+    int64_t p = (int64_t)y;
+    float v = (float)p * twoeb;
+    if (ok) { float e = x - v; *ok = fabsf(e) < eb_f || x == v; }
     return p;
 }
 
-float szo_lattice_value(int64_t p, float eb_f) { return (float)((double)p * (2.0 * (double)eb_f)); }
+float szo_lattice_value(int64_t p, float eb_f) { return (float)p * (2.0f * eb_f); }
 
 int szo_choose_m_lattice(const float *x, int ndim, const uint64_t *shape, int layers, float eb_f,
                          double theta) {
@@ -647,8 +650,8 @@ int szo_compress_lattice(const float *x, int ndim, const uint64_t *shape, int mo
     float eb_f;
     szo_effective_eb(mode, eb_abs, eb_rel, xmin, xmax, &eb_f);
     /* the lattice needs a positive spacing and lattice integers below 2^30 */
-    double amax = fmax(fabs((double)xmin), fabs((double)xmax));
-    if (!(eb_f > 0.0f) || amax * (1.0 / (2.0 * (double)eb_f)) >= 1073741824.0) return SZO_EINVAL;
+    float amax = fmaxf(fabsf(xmin), fabsf(xmax));
+    if (!(eb_f > 0.0f) || !(amax * (1.0f / (2.0f * eb_f)) < 1073741824.0f)) return SZO_EINVAL;
     int adaptive = (m == 0);
     if (adaptive) m = szo_choose_m_lattice(x, ndim, shape, layers, eb_f, theta);
     int T;

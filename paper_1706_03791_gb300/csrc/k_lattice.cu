@@ -3,13 +3,13 @@
 // it; its streams carry their own tag).
 //
 // Every value is snapped to the lattice of spacing 2 eb_f: p = rint(x * inv)
-// with inv = 1 / (2 eb_f) rounded once, in double, |p| < 2^30.  The integer
+// with inv = 1 / (2 eb_f) rounded once, in binary32, |p| < 2^30.  The integer
 // field p is predicted by the n-layer coefficients (Eq. predmodel) from the
 // lattice values of the neighbours -- never from reconstructed values -- so
 // every residual r = p - pred is independent and computed in parallel.  The
 // residual takes the place of the quantization code (r + 2^(m-1) when
 // |r| <= 2^(m-1)-1); a point is an outlier (code 0) when |r| is larger or its
-// lattice value (float)(p * 2 eb_f) misses the bound, and its record stores a
+// lattice value (float)p * 2 eb_f misses the bound, and its record stores a
 // flag (lattice value within the bound), r in 64 bits and, if the flag is 0,
 // the 32 bits of x.  Decompression inverts the predictor with n inclusive
 // prefix sums along every axis (the residual is the n-th mixed difference of
@@ -27,10 +27,10 @@ namespace szgb {
 __global__ void __launch_bounds__(256) k_lattice_p(const float* __restrict__ x, uint64_t n, int32_t* P, uint8_t* OK,
                                                    const DevState* st) {
     if (st->err) return;
-    const double twoeb = 2.0 * (double)st->eb_f, inv = 1.0 / twoeb, ebd = (double)st->eb_f;
+    const float eb = st->eb_f, twoeb = __fmul_rn(2.0f, eb), inv = __fdiv_rn(1.0f, twoeb);
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         bool ok;
-        P[i] = (int32_t)lattice_point(x[i], inv, twoeb, ebd, ok);
+        P[i] = lattice_point(x[i], inv, twoeb, eb, ok);
         OK[i] = ok ? 1 : 0;
     }
 }
@@ -44,15 +44,19 @@ __global__ void __launch_bounds__(256) k_lattice_codes(const int32_t* __restrict
     if (st->err) return;
     const int center = st->center;
     const int64_t radius = center - 1;
-    const double twoeb = 2.0 * (double)st->eb_f;
-    const uint64_t n = d0 * d1 * d2;
-    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < n; q += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t l = q % d2, row = q / d2, j = row % d1, i = row / d1;
-        const int64_t r = lattice_resid<ND, NL>(P, d1, d2, (int64_t)i, (int64_t)j, (int64_t)l);
-        const bool ok = OK[q] != 0;
-        const int64_t ar = r < 0 ? -r : r;
-        codes[row * cpitch + l] = (ok && ar <= radius) ? (uint16_t)(r + center) : (uint16_t)0;
-        if (recorded) recorded[q] = ok ? __double2float_rn(__dmul_rn((double)P[q], twoeb)) : x[q];
+    const float twoeb = __fmul_rn(2.0f, st->eb_f);
+    const uint64_t rows = d0 * d1;
+    // a block walks rows; its threads cover the row's columns (coalesced)
+    for (uint64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        const uint64_t i = row / d1, j = row - i * d1;
+        for (uint64_t l = threadIdx.x; l < d2; l += blockDim.x) {
+            const uint64_t q = row * d2 + l;
+            const int64_t r = lattice_resid<ND, NL>(P, d1, d2, (int64_t)i, (int64_t)j, (int64_t)l);
+            const bool ok = OK[q] != 0;
+            const int64_t ar = r < 0 ? -r : r;
+            codes[row * cpitch + l] = (ok && ar <= radius) ? (uint16_t)(r + center) : (uint16_t)0;
+            if (recorded) recorded[q] = ok ? lattice_value(P[q], twoeb) : x[q];
+        }
     }
 }
 
@@ -66,7 +70,7 @@ __global__ void __launch_bounds__(256) k_adapt_lattice(const float* __restrict__
     if (st->err) return;
     if (threadIdx.x < 18) cnt[threadIdx.x] = 0;
     __syncthreads();
-    const double twoeb = 2.0 * (double)st->eb_f, inv = 1.0 / twoeb, ebd = (double)st->eb_f;
+    const float eb = st->eb_f, twoeb = __fmul_rn(2.0f, eb), inv = __fdiv_rn(1.0f, twoeb);
     const uint64_t S0 = (cp.d0 + 7) / 8, S1 = (cp.d1 + 7) / 8, S2 = (cp.d2 + 7) / 8, S = S0 * S1 * S2;
     for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < S; s += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t a = s / (S1 * S2), b = s % (S1 * S2);
@@ -85,13 +89,13 @@ __global__ void __launch_bounds__(256) k_adapt_lattice(const float* __restrict__
                     if (ii < 0 || jj < 0 || ll < 0) continue;
                     bool okn;
                     const int64_t pn = lattice_point(x[((uint64_t)ii * cp.d1 + (uint64_t)jj) * cp.d2 + (uint64_t)ll],
-                                                     inv, twoeb, ebd, okn);
+                                                     inv, twoeb, eb, okn);
                     pred += (int64_t)term_coef(NL, k0, k1, k2) * pn;
                 }
             }
         }
         bool ok;
-        const int64_t p = lattice_point(x[((uint64_t)i * cp.d1 + (uint64_t)j) * cp.d2 + (uint64_t)l], inv, twoeb, ebd, ok);
+        const int64_t p = lattice_point(x[((uint64_t)i * cp.d1 + (uint64_t)j) * cp.d2 + (uint64_t)l], inv, twoeb, eb, ok);
         const int64_t r = p - pred, ar = r < 0 ? -r : r;
         if (!ok || ar > 32767) continue;
         int mm = 2;
@@ -150,7 +154,8 @@ int launch_lattice_compress(const float* x, const CallParams& cp, int32_t* P, ui
         }
     }
     k_lattice_p<<<grid_for(n, 256), 256, 0, s>>>(x, n, P, OK, st);
-    const int g = grid_for(n, 256);
+    const uint64_t rows = cp.d0 * cp.d1;
+    const int g = (int)std::min<uint64_t>(rows, 152ull * 32);
 #define SZGB_LC(ND, NL) k_lattice_codes<ND, NL><<<g, 256, 0, s>>>(P, OK, x, cp.d0, cp.d1, cp.d2, codes, cpitch, recorded, st)
     if (cp.ndim == 3) {
         if (cp.layers == 1) SZGB_LC(3, 1);
@@ -172,12 +177,15 @@ int launch_lattice_compress(const float* x, const CallParams& cp, int32_t* P, ui
 // row decode: one lane per row; residuals (wrap-around int32) to R, and for
 // outliers whose lattice value misses the bound, the stored x to `out` with
 // EX = 1
-__global__ void __launch_bounds__(256) k_lattice_decode_rows(
+constexpr int kLatDecWarps = 8;
+
+__global__ void __launch_bounds__(kLatDecWarps * 32) k_lattice_decode_rows(
     const uint8_t* __restrict__ payload, const uint64_t* __restrict__ rowoff, const uint32_t* __restrict__ rowbytes,
     const uint8_t* stream_end, const uint32_t* __restrict__ lut, const uint32_t* __restrict__ dectab, int32_t* R,
     uint8_t* EX, float* out, uint64_t rows, uint64_t N, DevState* st) {
     __shared__ uint32_t s_lut[1 << kLutBits];
     __shared__ uint32_t s_tab[260];
+    __shared__ int32_t s_tile[kLatDecWarps][32][33];  // odd word stride: conflict-free
     __shared__ int s_err;
     if (threadIdx.x == 0) s_err = *(volatile const unsigned*)&st->err != 0;
     __syncthreads();
@@ -187,28 +195,41 @@ __global__ void __launch_bounds__(256) k_lattice_decode_rows(
     for (int i = threadIdx.x; i < 260; i += blockDim.x) s_tab[i] = dectab[i];
     __syncthreads();
     const uint16_t* g_sorted = reinterpret_cast<const uint16_t*>(dectab + 260);
-    const uint64_t row = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (row >= rows) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t row0 = ((uint64_t)blockIdx.x * kLatDecWarps + warp) * 32, row = row0 + lane;
+    const bool valid = row < rows;
     BitReader br;
-    br.init(payload, rowoff[row], (uint64_t)(stream_end - payload));
     bool bad = false;
-    int32_t* rr = R + row * N;
-    for (uint64_t l = 0; l < N; l++) {
-        const int code = decode_symbol(br, s_lut, T, s_tab, g_sorted, maxlen, bad);
-        if (code) {
-            rr[l] = code - center;
-        } else {
-            const uint32_t ok = br.take(1);
-            const uint32_t hi = br.take(32), lo = br.take(32);
-            rr[l] = (int32_t)lo;  // r modulo 2^32 (hi only matters modulo 2^32 -- not at all)
-            (void)hi;
-            if (!ok) {
-                out[row * N + l] = __uint_as_float(br.take(32));
-                EX[row * N + l] = 1;
+    if (valid) br.init(payload, rowoff[row], (uint64_t)(stream_end - payload));
+    int32_t(*tile)[33] = s_tile[warp];
+    for (uint64_t l0 = 0; l0 < N; l0 += 32) {
+        const int ncol = (int)min((uint64_t)32, N - l0);
+        for (int j = 0; j < ncol; j++) {
+            int32_t rv = 0;
+            if (valid) {
+                const int code = decode_symbol(br, s_lut, T, s_tab, g_sorted, maxlen, bad);
+                if (code) {
+                    rv = code - center;
+                } else {
+                    const uint32_t ok = br.take(1);
+                    br.take(32);  // the high word: r is needed modulo 2^32 only
+                    rv = (int32_t)br.take(32);
+                    if (!ok) {
+                        out[row * N + l0 + j] = __uint_as_float(br.take(32));
+                        EX[row * N + l0 + j] = 1;
+                    }
+                }
             }
+            tile[lane][j] = rv;
         }
+        __syncwarp();
+        for (int t = 0; t < 32; t++) {
+            const uint64_t r = row0 + t;
+            if (r < rows && lane < ncol) R[r * N + l0 + lane] = tile[t][lane];
+        }
+        __syncwarp();
     }
-    if (bad || br.consumed > (uint64_t)rowbytes[row] * 8) atomicOr(&st->err, kErrCorrupt);
+    if (valid && (bad || br.consumed > (uint64_t)rowbytes[row] * 8)) atomicOr(&st->err, kErrCorrupt);
 }
 
 // inclusive prefix sums (wrap-around int32) along one axis of [d0][d1][d2]
@@ -263,9 +284,9 @@ __global__ void __launch_bounds__(256) k_scan_strided(int32_t* R, uint64_t nline
 __global__ void __launch_bounds__(256) k_lattice_finish(const int32_t* __restrict__ R, const uint8_t* __restrict__ EX,
                                                         float* out, uint64_t n, const DevState* st) {
     if (st->err) return;
-    const double twoeb = 2.0 * (double)st->eb_f;
+    const float twoeb = __fmul_rn(2.0f, st->eb_f);
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
-        if (!EX[i]) out[i] = __double2float_rn(__dmul_rn((double)R[i], twoeb));
+        if (!EX[i]) out[i] = lattice_value(R[i], twoeb);
 }
 
 int launch_lattice_decompress(const uint8_t* payload, const uint64_t* rowoff, const uint32_t* rowbytes,
@@ -274,8 +295,9 @@ int launch_lattice_decompress(const uint8_t* payload, const uint64_t* rowoff, co
                               DevState* st, cudaStream_t s) {
     const uint64_t rows = d0 * d1, n = rows * d2;
     if (cudaMemsetAsync(EX, 0, n, s) != cudaSuccess) return SZGB_ECUDA;
-    k_lattice_decode_rows<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(payload, rowoff, rowbytes, stream_end, lut,
-                                                                         dec_tab, R, EX, out, rows, d2, st);
+    const uint64_t per = 32ull * kLatDecWarps;
+    k_lattice_decode_rows<<<(unsigned)((rows + per - 1) / per), kLatDecWarps * 32, 0, s>>>(
+        payload, rowoff, rowbytes, stream_end, lut, dec_tab, R, EX, out, rows, d2, st);
     for (int rep = 0; rep < layers; rep++) {
         k_scan_axis2<<<grid_for(rows * 32, 256), 256, 0, s>>>(R, rows, d2);
         if (ndim >= 2 && d1 > 1) {

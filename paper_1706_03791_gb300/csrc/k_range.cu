@@ -93,8 +93,9 @@ __global__ void __launch_bounds__(256) k_range(const float* __restrict__ x, uint
     st->inv2eb = ebf > 0.0f ? __fdiv_rn(1.0f, twoeb) : 0.0f;
     st->e_eb = (int)((__float_as_uint(ebf) >> 23) & 0xffu);
     if (cp.variant == 1) {  // the lattice needs a positive spacing and integers below 2^30
-        const double amax = fmax(fabs((double)mn), fabs((double)mx));
-        if (!(ebf > 0.0f) || amax * (1.0 / (2.0 * (double)ebf)) >= 1073741824.0) st->err |= kErrRange;
+        const float amax = fmaxf(fabsf(mn), fabsf(mx));
+        if (!(ebf > 0.0f) || !(__fmul_rn(amax, __fdiv_rn(1.0f, __fmul_rn(2.0f, ebf))) < 1073741824.0f))
+            st->err |= kErrRange;
     }
     st->adaptive = cp.m_user == 0;
     if (cp.m_user) {

@@ -373,14 +373,16 @@ __device__ __forceinline__ int decode_symbol(BitReader& br, const uint32_t* s_lu
 
 // --------------------------------------------------------------------------
 // the lattice variant (a separately labelled, fully parallel form; see
-// k_lattice.cu): lattice integer of x, p = rint(x * inv) in double with
-// inv = 1 / (2 eb_f), and whether (float)(p * 2 eb_f) is within the bound
-__device__ __forceinline__ int64_t lattice_point(float x, double inv, double twoeb, double ebd, bool& ok) {
-    const int64_t p = (int64_t)rint(__dmul_rn((double)x, inv));
-    const float v = __double2float_rn(__dmul_rn((double)p, twoeb));
-    ok = fabs(__dsub_rn((double)x, (double)v)) < ebd;
+// k_lattice.cu): lattice integer of x, p = rint(x * inv) in binary32 with
+// inv = 1 / (2 eb_f), and whether v = (float)p * 2 eb_f is within the bound
+// (|x - v| < eb_f or x == v)
+__device__ __forceinline__ int32_t lattice_point(float x, float inv, float twoeb, float eb, bool& ok) {
+    const int32_t p = (int32_t)rintf(__fmul_rn(x, inv));
+    const float v = __fmul_rn(__int2float_rn(p), twoeb);
+    ok = (fabsf(__fsub_rn(x, v)) < eb) | (x == v);
     return p;
 }
+__device__ __forceinline__ float lattice_value(int32_t p, float twoeb) { return __fmul_rn(__int2float_rn(p), twoeb); }
 
 // integer residual p - sum_k c_k p(x - k) of the n-layer predictor over the
 // lattice integers P ([d0][d1][d2]), neighbours outside the domain = 0

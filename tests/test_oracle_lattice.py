@@ -11,12 +11,14 @@ from synthetic import fields
 
 
 def _lattice_ref(x, eb_f):
-    """(p, ok) from the definition: p = rint(x * (1 / (2 eb_f))) in double; ok
-    when the float lattice value is strictly within eb_f of x."""
-    twoeb = 2.0 * np.float64(eb_f)
-    p = np.rint(x.astype(np.float64) * (1.0 / twoeb)).astype(np.int64)
-    v = (p.astype(np.float64) * twoeb).astype(np.float32)
-    ok = np.abs(x.astype(np.float64) - v.astype(np.float64)) < np.float64(eb_f)
+    """(p, ok) from the definition, in binary32: p = rint(x * inv) with
+    inv = 1 / (2 eb_f); ok when |x - v| < eb_f or x == v for v = p * 2 eb_f."""
+    eb = np.float32(eb_f)
+    twoeb = np.float32(2.0) * eb
+    inv = np.float32(1.0) / twoeb
+    p = np.rint(x.astype(np.float32) * inv).astype(np.int64)
+    v = p.astype(np.float32) * twoeb
+    ok = (np.abs(x - v) < eb) | (x == v)
     return p, v, ok
 
 
