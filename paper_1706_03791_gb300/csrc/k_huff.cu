@@ -15,53 +15,92 @@
 namespace szgb {
 
 // ---------------------------------------------------------------------------
-// histogram of the codes over 2^m bins (warp-aggregated increments)
+// histogram of the codes over 2^m bins
+//
+// The codes are read as 16-byte vectors (8 codes; rows have a pitch of a
+// multiple of 8 entries and the padding is skipped).  The distribution is
+// concentrated around the centre code, so the kHistWin bins around it are
+// counted in per-lane private counters laid out bin-major with the lane
+// innermost (one bank per lane: no atomics, no conflicts); the other bins take
+// shared-memory atomics on a block histogram (2^m <= 8192) or global ones.
 
-// codes are stored row by row with a row pitch of `pitch` entries (>= rowlen)
-__global__ void __launch_bounds__(512) k_hist(const uint16_t* __restrict__ codes, uint64_t rows,
-                                              uint64_t rowlen, uint64_t pitch, uint32_t* hist,
-                                              const DevState* st) {
+constexpr int kHistThreads = 512;
+constexpr int kHistWin = 32;
+constexpr int kHistBlockBins = 8192;
+constexpr size_t kHistSmem = (size_t)(kHistBlockBins + (kHistThreads / 32) * kHistWin * 32) * 4;
+
+__global__ void __launch_bounds__(kHistThreads) k_hist(const uint16_t* __restrict__ codes, uint64_t rows,
+                                                       uint64_t rowlen, uint64_t pitch, uint32_t* hist,
+                                                       const DevState* st) {
     extern __shared__ uint32_t sh[];
     if (st->err) return;
     const int m = st->m;
     const int nb = 1 << m;
-    const bool use_smem = m <= 13;
+    const bool use_smem = nb <= kHistBlockBins;
+    uint32_t* priv = sh + kHistBlockBins;
     if (use_smem)
-        for (int i = threadIdx.x; i < nb; i += blockDim.x) sh[i] = 0;
+        for (int i = threadIdx.x; i < nb; i += kHistThreads) sh[i] = 0;
+    for (int i = threadIdx.x; i < (kHistThreads / 32) * kHistWin * 32; i += kHistThreads) priv[i] = 0;
     __syncthreads();
     uint32_t* H = use_smem ? sh : hist;
-    const int lane = threadIdx.x & 31;
-    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t r = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; r < rows; r += nw) {
-        const uint16_t* row = codes + r * pitch;
-        for (uint64_t l0 = 0; l0 < rowlen; l0 += 32) {
-            const uint64_t l = l0 + lane;
-            const bool v = l < rowlen;
-            const unsigned active = __ballot_sync(0xffffffffu, v);
-            if (!v) continue;
-            uint32_t c = __ldcs(row + l);
-            if (c >= (uint32_t)nb) c = 0;  // codes are < 2^m; never index past the bins
-            const unsigned peers = __match_any_sync(active, c);
-            if (lane == __ffs(peers) - 1) atomicAdd(&H[c], (uint32_t)__popc(peers));
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t* P = priv + wib * kHistWin * 32 + lane;
+    int lo = st->center - kHistWin / 2;
+    lo = lo < 0 ? 0 : lo;
+    const uint64_t vpr = pitch >> 3;  // vectors per row
+    const uint64_t nvec = rows * vpr;
+    for (uint64_t v = blockIdx.x * (uint64_t)kHistThreads + threadIdx.x; v < nvec;
+         v += (uint64_t)gridDim.x * kHistThreads) {
+        const uint64_t r = (nvec >> 32) ? v / vpr : (uint64_t)((uint32_t)v / (uint32_t)vpr);
+        const uint64_t c0 = (v - r * vpr) << 3;
+        const uint4 q = __ldcs(reinterpret_cast<const uint4*>(codes + r * pitch + c0));
+        const uint64_t rem = rowlen - c0;
+        const int nv = rem < 8 ? (int)rem : 8;
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            if (k < nv) {
+                uint32_t c = (w[k >> 1] >> (16 * (k & 1))) & 0xffffu;
+                if (c >= (uint32_t)nb) c = 0;  // codes are < 2^m; never index past the bins
+                const uint32_t d = c - (uint32_t)lo;
+                if (d < (uint32_t)kHistWin) {
+                    P[d * 32] += 1u;
+                } else {
+                    atomicAdd(&H[c], 1u);
+                }
+            }
         }
+    }
+    __syncthreads();
+    // window totals: warp wib sums bins wib, wib + 16, ... over all warps' lanes
+    for (int b = wib; b < kHistWin; b += kHistThreads / 32) {
+        uint32_t t = 0;
+        for (int w2 = 0; w2 < kHistThreads / 32; w2++) t += priv[(w2 * kHistWin + b) * 32 + lane];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0 && t && lo + b < nb) atomicAdd(&H[lo + b], t);
     }
     if (use_smem) {
         __syncthreads();
-        for (int i = threadIdx.x; i < nb; i += blockDim.x)
+        for (int i = threadIdx.x; i < nb; i += kHistThreads)
             if (sh[i]) atomicAdd(&hist[i], sh[i]);
     }
 }
 
 int launch_histogram(const uint16_t* codes, uint64_t rows, uint64_t rowlen, uint64_t pitch, uint32_t* hist,
                      DevState* st, cudaStream_t s) {
-    const uint64_t n = rows * rowlen;
-    int blocks = (int)((n + 4095) / 4096);
-    if (blocks > 4 * 152) blocks = 4 * 152;
+    static std::once_flag once;
+    static bool ok = true;
+    std::call_once(once, [] {
+        ok = cudaFuncSetAttribute(k_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHistSmem) ==
+             cudaSuccess;
+        if (!ok) cudaGetLastError();
+    });
+    if (!ok) return SZGB_ECUDA;
+    const uint64_t nvec = rows * (pitch >> 3);
+    uint64_t blocks = (nvec + kHistThreads * 4 - 1) / (kHistThreads * 4);
+    if (blocks > 2 * 152) blocks = 2 * 152;
     if (blocks < 1) blocks = 1;
-    size_t smem = (size_t)(1 << 13) * 4;
-    if (cudaFuncSetAttribute(k_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return SZGB_ECUDA;
-    k_hist<<<blocks, 512, smem, s>>>(codes, rows, rowlen, pitch, hist, st);
+    k_hist<<<(int)blocks, kHistThreads, kHistSmem, s>>>(codes, rows, rowlen, pitch, hist, st);
     return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
 }
 
@@ -378,7 +417,8 @@ int launch_codebook(const uint32_t* hist, DevState* st, uint8_t* len, uint64_t* 
 // per-row bit counts: Huffman code bits plus 9 + t record bits after code 0
 
 // lattice variant when OK != nullptr: an outlier record is 1 + 64 bits, +32
-// when its lattice value misses the bound
+// when its lattice value misses the bound.  One warp per row; a lane takes 8
+// consecutive codes as one 16-byte vector.
 __global__ void __launch_bounds__(256) k_rowbits(const uint16_t* __restrict__ codes, uint64_t pitch,
                                                  const float* __restrict__ x, uint64_t rows,
                                                  uint64_t rowlen, const uint8_t* __restrict__ len,
@@ -389,25 +429,37 @@ __global__ void __launch_bounds__(256) k_rowbits(const uint16_t* __restrict__ co
     if (st->err) return;
     const int e_eb = st->e_eb;
     unsigned long long kcount = 0;
+    uint32_t maxb = 0;
     for (uint64_t r = wglob; r < rows; r += nw) {
         const uint64_t base = r * rowlen;
         const uint16_t* crow = codes + r * pitch;
         uint64_t bits = 0;
-        for (uint64_t l = lane; l < rowlen; l += 32) {
-            uint32_t c = crow[l];
-            bits += len[c];
-            if (c == 0) {
-                bits += OK ? (uint64_t)(OK[base + l] ? 65 : 97) : (uint64_t)(9 + trunc_bits(__float_as_uint(x[base + l]), e_eb));
-                kcount++;
+        for (uint64_t l = (uint64_t)lane * 8; l < rowlen; l += 256) {
+            const uint4 q = __ldcs(reinterpret_cast<const uint4*>(crow + l));
+            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+            const uint64_t rem = rowlen - l;
+            const int nv = rem < 8 ? (int)rem : 8;
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                if (k < nv) {
+                    const uint32_t c = (w[k >> 1] >> (16 * (k & 1))) & 0xffffu;
+                    bits += __ldg(len + c);
+                    if (c == 0) {
+                        bits += OK ? (uint64_t)(OK[base + l + k] ? 65 : 97)
+                                   : (uint64_t)(9 + trunc_bits(__float_as_uint(x[base + l + k]), e_eb));
+                        kcount++;
+                    }
+                }
             }
         }
         for (int o = 16; o > 0; o >>= 1) bits += __shfl_xor_sync(0xffffffffu, bits, o);
         if (lane == 0) {
-            uint64_t b = (bits + 7) / 8;
-            rowbytes[r] = (uint32_t)b;
-            atomicMax(&st->maxrow, (uint32_t)b);
+            const uint32_t b = (uint32_t)((bits + 7) / 8);
+            rowbytes[r] = b;
+            maxb = b > maxb ? b : maxb;
         }
     }
+    if (lane == 0 && maxb) atomicMax(&st->maxrow, maxb);
     for (int o = 16; o > 0; o >>= 1) kcount += __shfl_xor_sync(0xffffffffu, kcount, o);
     if (lane == 0 && kcount) atomicAdd(&st->K, kcount);
 }
@@ -559,33 +611,21 @@ __global__ void __launch_bounds__(256) k_write_meta(const CallParams cp, uint64_
     }
 }
 
-__device__ __forceinline__ void put32(uint32_t* buf, uint32_t o, uint32_t v, int n) {
-    // n in [1,32], v < 2^n, MSB-first at bit offset o
-    uint32_t i = o >> 5, s = o & 31;
-    if (s + n <= 32) {
-        atomicOr(&buf[i], v << (32 - s - n));
-    } else {
-        atomicOr(&buf[i], v >> (s + n - 32));
-        atomicOr(&buf[i + 1], v << (64 - s - n));
-    }
-}
-__device__ __forceinline__ void put64(uint32_t* buf, uint32_t o, uint64_t v, int n) {
-    if (n > 32) {
-        put32(buf, o, (uint32_t)(v >> 32), n - 32);
-        put32(buf, o + (n - 32), (uint32_t)v, 32);
-    } else if (n > 0) {
-        put32(buf, o, (uint32_t)v, n);
-    }
-}
-
 constexpr int kEncWarps = 8;
-constexpr int kEncBufWords = 168;  // 32 points of up to 64 + 97 bits, plus the carry word
+constexpr int kEncPts = 8;                   // consecutive points per lane (one 16-byte code vector)
+constexpr int kEncChunk = 32 * kEncPts;      // points per warp step
+// a step's bits: 256 points of at most 64 code bits and a 97-bit record, plus
+// the carried partial word
+constexpr int kEncBufWords = (kEncChunk * (64 + 97) + 31) / 32 + 2;
 
-// payload: one warp per row; 32 points at a time are placed by a warp scan of
-// their bit lengths into a shared-memory word buffer whose completed words
-// are stored.  Every payload byte belongs to exactly one row (rows are
-// byte-padded), so a word a row shares with a neighbour is written byte by
-// byte for the row's own bytes only: no atomics, no zeroing pass.
+// payload: one warp per row, 256 points per step.  Each lane sums the bit
+// lengths of its 8 points, a warp scan gives its bit offset, and the lane
+// writes its bits MSB-first into a shared-memory word buffer (words it fills
+// alone are stored, the two it may share with its neighbours are OR-ed).
+// Completed words go to the payload; the buffer is zero outside the carried
+// word between steps.  Every payload byte belongs to exactly one row (rows
+// are byte-padded), so a word a row shares with a neighbour is written byte
+// by byte for the row's own bytes only: no atomics, no zeroing pass.
 __device__ __forceinline__ void store_word_bytes(uint8_t* plb, uint64_t gw, uint32_t val, uint32_t lo,
                                                  uint32_t hi) {
     // val: big-endian word value; write bytes covering bits [lo, hi) of it
@@ -603,92 +643,141 @@ struct LatticeRec {
     uint64_t d1;        // rows per plane (the row index of a point is plane * d1 + row)
 };
 
+// MSB-first bit writer of one lane into the warp's word buffer
+struct LaneBits {
+    uint32_t* buf;
+    uint32_t wi, wfirst, nacc;
+    uint64_t acc;
+    __device__ __forceinline__ LaneBits(uint32_t* b, uint32_t off)
+        : buf(b), wi(off >> 5), wfirst(off >> 5), nacc(off & 31), acc(0) {}
+    // append the n low bits of v, n in [0, 32]
+    __device__ __forceinline__ void put(uint32_t v, uint32_t n) {
+        acc = (acc << n) | v;
+        nacc += n;
+        if (nacc >= 32) {
+            nacc -= 32;
+            const uint32_t w = (uint32_t)(acc >> nacc);
+            if (wi == wfirst) atomicOr(buf + wi, w);
+            else buf[wi] = w;
+            wi++;
+            acc &= (1ull << nacc) - 1ull;
+        }
+    }
+    __device__ __forceinline__ void put64(uint64_t v, uint32_t n) {
+        if (n > 32) {
+            put((uint32_t)(v >> 32), n - 32);
+            put((uint32_t)v, 32);
+        } else {
+            put((uint32_t)v, n);
+        }
+    }
+    __device__ __forceinline__ void finish() {
+        if (nacc) atomicOr(buf + wi, (uint32_t)(acc << (32 - nacc)));
+    }
+};
+
 __global__ void __launch_bounds__(kEncWarps * 32) k_encode(const uint16_t* __restrict__ codes, uint64_t pitch,
                                                           const float* __restrict__ x, uint64_t rows,
                                                           uint64_t rowlen, const uint8_t* __restrict__ len,
                                                           const uint64_t* __restrict__ cw,
                                                           const uint64_t* __restrict__ rowoff,
                                                           uint8_t* out, DevState* st, const LatticeRec LR) {
-    __shared__ uint32_t sbuf[kEncWarps][kEncBufWords];
+    extern __shared__ uint32_t sbuf[];
     if (!st->fits || st->err) return;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    uint32_t* buf = sbuf[wib];
+    uint32_t* buf = sbuf + wib * kEncBufWords;
     uint8_t* plb = out + kHeaderBytes + st->cb_bytes + st->tab_bytes;
     const int e_eb = st->e_eb;
     const uint64_t wglob = blockIdx.x * (uint64_t)kEncWarps + wib;
     const uint64_t nw = (uint64_t)gridDim.x * kEncWarps;
+    for (int i = lane; i < kEncBufWords; i += 32) buf[i] = 0;
+    __syncwarp();
     for (uint64_t r = wglob; r < rows; r += nw) {
         const uint64_t g0 = rowoff[r] * 8;        // first bit of the row in the payload
         const uint64_t w0 = g0 >> 5;              // its word
         const uint32_t lo0 = (uint32_t)(g0 & 31); // bits of w0 owned by earlier rows
         uint64_t curw = w0;                        // global word held in buf[0]
         uint32_t bitpos = lo0;                     // bits already used in buf[0]
-        for (int i = lane; i < kEncBufWords; i += 32) buf[i] = 0;
-        __syncwarp();
         const uint64_t base = r * rowlen;
         const uint16_t* crow = codes + r * pitch;
-        for (uint64_t l0 = 0; l0 < rowlen; l0 += 32) {
-            uint64_t l = l0 + lane;
-            bool v = l < rowlen;
-            uint32_t c = v ? crow[l] : 0u;
-            int L = v ? len[c] : 0;
-            uint64_t code = v ? cw[c] : 0;
-            int nrec = 0;
-            uint32_t se = 0, mb = 0;
-            int t = 0;
-            uint64_t lres = 0;
-            bool lok = true;
-            if (v && c == 0) {
-                uint32_t u = __float_as_uint(x[base + l]);
-                if (LR.P) {  // lattice record: flag, r (64 bits), x when the flag is 0
-                    lok = LR.OK[base + l] != 0;
-                    lres = (uint64_t)lattice_resid_rt(LR.P, LR.ndim, LR.layers, LR.d1, rowlen, (int64_t)(r / LR.d1),
-                                                      (int64_t)(r % LR.d1), (int64_t)l);
-                    se = u;
-                    nrec = lok ? 65 : 97;
-                } else {
-                    t = trunc_bits(u, e_eb);
-                    se = u >> 23;
-                    mb = t ? ((u >> (23 - t)) & ((1u << t) - 1u)) : 0u;
-                    nrec = 9 + t;
+        for (uint64_t l0 = 0; l0 < rowlen; l0 += kEncChunk) {
+            const uint64_t l = l0 + (uint64_t)lane * kEncPts;
+            const int nv = l < rowlen ? (rowlen - l < kEncPts ? (int)(rowlen - l) : kEncPts) : 0;
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+            if (nv) {
+                const uint4 q = __ldcs(reinterpret_cast<const uint4*>(crow + l));
+                w[0] = q.x;
+                w[1] = q.y;
+                w[2] = q.z;
+                w[3] = q.w;
+            }
+            uint32_t nbits = 0;
+            bool any0 = false;
+#pragma unroll
+            for (int k = 0; k < kEncPts; k++) {
+                if (k < nv) {
+                    const uint32_t c = (w[k >> 1] >> (16 * (k & 1))) & 0xffffu;
+                    nbits += __ldg(len + c);
+                    if (c == 0) {
+                        any0 = true;
+                        const uint32_t u = __float_as_uint(x[base + l + k]);
+                        nbits += LR.P ? (LR.OK[base + l + k] ? 65u : 97u) : (uint32_t)(9 + trunc_bits(u, e_eb));
+                    }
                 }
             }
-            uint32_t nbits = (uint32_t)(L + nrec);
             uint32_t incl = nbits;
             for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += y;
             }
-            uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-            uint32_t off = bitpos + incl - nbits;
-            if (L) put64(buf, off, code, L);
-            if (nrec && LR.P) {
-                put32(buf, off + L, lok ? 1u : 0u, 1);
-                put32(buf, off + L + 1, (uint32_t)(lres >> 32), 32);
-                put32(buf, off + L + 33, (uint32_t)lres, 32);
-                if (!lok) put32(buf, off + L + 65, se, 32);
-            } else if (nrec) {
-                put32(buf, off + L, se, 9);
-                if (t) put32(buf, off + L + 9, mb, t);
+            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            LaneBits wr(buf, bitpos + incl - nbits);
+#pragma unroll
+            for (int k = 0; k < kEncPts; k++) {
+                if (k < nv) {
+                    const uint32_t c = (w[k >> 1] >> (16 * (k & 1))) & 0xffffu;
+                    wr.put64(__ldg(cw + c), __ldg(len + c));
+                    if (any0 && c == 0) {
+                        const uint32_t u = __float_as_uint(x[base + l + k]);
+                        if (LR.P) {  // lattice record: flag, r (64 bits), x when the flag is 0
+                            const bool lok = LR.OK[base + l + k] != 0;
+                            const uint64_t lres = (uint64_t)lattice_resid_rt(
+                                LR.P, LR.ndim, LR.layers, LR.d1, rowlen, (int64_t)(r / LR.d1),
+                                (int64_t)(r % LR.d1), (int64_t)(l + k));
+                            wr.put(lok ? 1u : 0u, 1);
+                            wr.put64(lres, 64);
+                            if (!lok) wr.put(u, 32);
+                        } else {
+                            const int t = trunc_bits(u, e_eb);
+                            wr.put(u >> 23, 9);
+                            if (t) wr.put((u >> (23 - t)) & ((1u << t) - 1u), (uint32_t)t);
+                        }
+                    }
+                }
             }
+            wr.finish();
             __syncwarp();
-            uint32_t end = bitpos + total;
-            uint32_t full = end >> 5;
+            const uint32_t end = bitpos + total;
+            const uint32_t full = end >> 5;
             for (uint32_t i = lane; i < full; i += 32) {
-                uint64_t gw = curw + i;
+                const uint64_t gw = curw + i;
                 store_word_bytes(plb, gw, buf[i], gw == w0 ? lo0 : 0u, 32u);
+                buf[i] = 0;
             }
             __syncwarp();
-            uint32_t carry = buf[full];
+            const uint32_t carry = buf[full];
             __syncwarp();
-            for (int i = lane; i < kEncBufWords; i += 32) buf[i] = 0;
-            __syncwarp();
-            if (lane == 0) buf[0] = carry;
+            if (lane == 0 && full) {
+                buf[0] = carry;
+                buf[full] = 0;
+            }
             __syncwarp();
             curw += full;
             bitpos = end & 31;
         }
         if (bitpos && lane == 0) store_word_bytes(plb, curw, buf[0], curw == w0 ? lo0 : 0u, bitpos);
+        __syncwarp();
+        if (lane == 0) buf[0] = 0;
         __syncwarp();
     }
 }
@@ -712,10 +801,18 @@ int launch_encode(const uint16_t* codes, uint64_t pitch, const float* x, uint64_
     LR.ndim = ndim;
     LR.layers = layers;
     LR.d1 = d1;
+    constexpr size_t smem = (size_t)kEncWarps * kEncBufWords * 4;
+    static std::once_flag once;
+    static bool ok = true;
+    std::call_once(once, [] {
+        ok = cudaFuncSetAttribute(k_encode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
+        if (!ok) cudaGetLastError();
+    });
+    if (!ok) return SZGB_ECUDA;
     uint64_t blocks = (rows + kEncWarps - 1) / kEncWarps;
-    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks > 152 * 5) blocks = 152 * 5;
     if (blocks < 1) blocks = 1;
-    k_encode<<<(int)blocks, kEncWarps * 32, 0, s>>>(codes, pitch, x, rows, rowlen, len, cw, rowoff, out, st, LR);
+    k_encode<<<(int)blocks, kEncWarps * 32, smem, s>>>(codes, pitch, x, rows, rowlen, len, cw, rowoff, out, st, LR);
     return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
 }
 

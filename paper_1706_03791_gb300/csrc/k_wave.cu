@@ -24,16 +24,18 @@
 // the critical path; the descending summation order puts them last.
 //
 // Inputs and outputs are staged through shared memory: a warp's 32 rows are
-// cut into 32 x 32 tiles, which the extra warp below loads (x) and stores
+// cut into 32 x 32 tiles, which an extra "staging" warp loads (x) and stores
 // (codes, or decompressed values) with coalesced accesses; a lane reads its x
 // and writes its result at the same tile position, bank-conflict-free.
 //
-// CTA boundaries go through global "halo" buffers written by the lanes that
-// compute the boundary lines; an extra warp per CTA publishes a progress
-// counter every few sweeps (fence + st.release) and prefetches the
-// neighbouring CTAs' halos into the rings with cp.async after bounded
-// acquire-waits.  CTAs take work items from a ticket counter in dependency
-// order, so a CTA only waits for CTAs that are already resident.
+// CTA boundaries go through global "halo" buffers.  An extra warp per CTA
+// copies the boundary lines out of shared memory as 64-bit words that carry
+// the value and a tag (one single-copy-atomic store each, no fence), and
+// loads the neighbouring CTAs' lines into the rings by polling those words
+// until every tag is set (bounded waits): a block is usable the moment it is
+// written, with no progress counter to publish.  The halo buffers are zeroed
+// before every launch.  CTAs take work items from a ticket counter in
+// dependency order, so a CTA only waits for CTAs that are already resident.
 #include <cuda.h>
 
 #include <mutex>
@@ -42,10 +44,10 @@
 
 namespace szgb {
 
-constexpr int kPFH = 2;   // halo blocks are loaded this many sweeps ahead
 constexpr int kPFX = 4;   // x tiles are loaded this many sweeps ahead
-constexpr int kBarReady = 3;  // named barrier: the halo warp has made a sweep's inputs ready
+constexpr int kBarReady = 3;  // named barrier: the helper warps have made a sweep's inputs ready
 constexpr int kBarDone = 4;   // named barrier: the compute warps have finished a sweep
+constexpr int kBarEnd = 5;    // named barrier of the three helper warps at the end of an item
 constexpr int kTW = 32;   // staging tile: 32 rows x kTW columns
 constexpr int kTE = 32 * kTW;  // elements per staging tile
 constexpr int kTS = 3;    // staging ring slots per warp
@@ -55,11 +57,11 @@ constexpr int kRPS = 36;  // plane ring row stride (9 float4: conflict-free)
 constexpr int kRV = 64;   // virtual-row ring: floats per line
 
 struct WaveArgs {
-    // TMA descriptors of the 32 x 32 staging tiles: x (compress) and the
-    // output (codes when compressing, values when decompressing)
+    // TMA descriptor of the 32 x 32 input staging tiles: x (compress) or the
+    // decoded codes (decompress)
     CUtensorMap tm_x;
-    CUtensorMap tm_out;
-    int tma_x, tma_out;
+    int tma_x;
+    int vec_out;      // output rows are 16-byte aligned: tiles leave as 16-byte stores
     uint64_t opitch;  // output row pitch (elements)
     WaveGeom g;
     // compress
@@ -74,7 +76,8 @@ struct WaveArgs {
     const uint32_t* lut;
     const uint32_t* dectab;
     float* out;
-    // common
+    // common: halo lines as 64-bit words (value bits | kHaloTag << 32), zeroed
+    // before the launch; prog: per-item final / aborted state
     float* halo_row;
     float* halo_plane;
     unsigned int* prog;
@@ -87,22 +90,28 @@ __device__ __forceinline__ int posmod(int a, int m) {
     return r < 0 ? r + m : r;
 }
 
-// Bounded wait until *p >= need; `seen` caches the last value observed so
-// that a satisfied requirement costs no memory access.  Returns false on
-// timeout.
-__device__ __forceinline__ bool wait_progress(const unsigned int* p, unsigned int need, unsigned int& seen,
-                                              uint64_t timeout_ns) {
-    if (seen >= need) return true;
-    seen = ld_acquire_u32(p);
-    if (seen >= need) return true;
-    uint64_t t0 = globaltimer();
-    for (unsigned it = 0; it < (1u << 28); it++) {
-        __nanosleep(64);
-        seen = ld_acquire_u32(p);
-        if (seen >= need) return true;
-        if ((it & 63) == 63 && globaltimer() - t0 > timeout_ns) return false;
-    }
-    return false;
+// A halo word: the value's bits in the low half, kHaloTag in the high half.
+// An aligned 64-bit access is single-copy atomic, so a reader that sees the
+// tag sees the value written with it.
+constexpr uint32_t kHaloTag = 0x5a5a0001u;
+__device__ __forceinline__ uint64_t halo_word(float v) {
+    return ((uint64_t)kHaloTag << 32) | __float_as_uint(v);
+}
+// one halo block: 4 words, 32-byte aligned (each 64-bit element of the vector
+// access is single-copy atomic)
+__device__ __forceinline__ void st_relaxed_block(uint64_t* p, uint64_t a, uint64_t b, uint64_t c, uint64_t d) {
+    asm volatile("st.relaxed.gpu.global.v4.u64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(a), "l"(b), "l"(c), "l"(d)
+                 : "memory");
+}
+__device__ __forceinline__ void ld_relaxed_block(const uint64_t* p, uint64_t (&w)[4]) {
+    asm volatile("ld.relaxed.gpu.global.v4.u64 {%0, %1, %2, %3}, [%4];"
+                 : "=l"(w[0]), "=l"(w[1]), "=l"(w[2]), "=l"(w[3])
+                 : "l"(p)
+                 : "memory");
+}
+__device__ __forceinline__ bool halo_tagged(const uint64_t (&w)[4]) {
+    return ((uint32_t)(w[0] >> 32) == kHaloTag) & ((uint32_t)(w[1] >> 32) == kHaloTag) &
+           ((uint32_t)(w[2] >> 32) == kHaloTag) & ((uint32_t)(w[3] >> 32) == kHaloTag);
 }
 
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
@@ -224,9 +233,11 @@ int launch_decode_rows(const uint8_t* payload, const uint64_t* rowoff, const uin
 //       or f32 values (decompress)
 //   MB  [W][kTS] mbarriers of the TMA loads into XR
 //   decoder tables (decompress)
-// Global halos (written by the lanes computing the boundary lines):
-//   3D row halo   [P][nb1][NL][npad]          unshifted columns
-//   3D plane halo [nb0][nb1][NL][32][npad+32] diagonal columns l+t
+// Global halos (64-bit tagged words, copied out of shared memory by the
+// halo warp; a block is 4 consecutive columns):
+//   3D row halo   [P][nb1][NL][npad]                  unshifted columns
+//   3D plane halo [nb0][nb1][NL][(npad+32)/4][32][4]  diagonal columns l+t,
+//                 block-major so that the 32 rows of a block are contiguous
 //   2D row halo   [nb1][NL][npad]
 
 template <int ND, int NL>
@@ -258,7 +269,7 @@ struct WaveCtl {
 };
 
 // One work item (a block of planes x rows, or of rows) of one field.  Every
-// thread of the CTA calls it; threads beyond the item's W + 1 warps return at
+// thread of the CTA calls it; threads beyond the item's W + 3 warps return at
 // once.  The caller separates items with __syncthreads().
 template <int ND, int NL, bool DEC, bool TR>
 __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, unsigned char* smem_raw, WaveCtl& S) {
@@ -268,7 +279,7 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
     const WaveGeom& g = A.g;
     const int W = g.W;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool is_halo = (warp == W);
+    const bool is_helper = (warp >= W);  // warps W, W + 1, W + 2: halo lines in, staging tiles, halo lines out
 
     // shared-memory carve-up from a 128-byte boundary (TMA destinations);
     // the mbarriers sit first, at a place that does not depend on W
@@ -283,7 +294,7 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
     IT* XR = reinterpret_cast<IT*>(HR + (size_t)nhr * NL * kRV);         // W*kTS*kTE inputs
     OT* OR = reinterpret_cast<OT*>(XR + (size_t)W * kTS * kTE);          // W*kTS*kTE outputs
     const bool tma_x = A.tma_x != 0;
-    const bool tma_o = A.tma_out != 0;
+    const bool vec_o = A.vec_out != 0;
 
     if (threadIdx.x == 0) {
         S.abort = 0;
@@ -304,7 +315,7 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
         if (threadIdx.x == 0) st_release_u32(A.prog + item, kProgAbort);
         return;
     }
-    if (warp > W) return;  // a narrower item than the launch
+    if (warp > W + 2) return;  // a narrower item than the launch
 
     const int npad = g.ntiles * kTile;     // row halo line length
     const int nshift = npad + 32;          // plane halo line length (diagonal)
@@ -313,152 +324,287 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
     unsigned int* my_prog = A.prog + item;
     const QParams qp = load_qparams(A.st);
     const int N = (int)g.N;
-    const int nthr_all = (W + 1) * 32;  // threads of the per-sweep barriers
+    const int nthr_all = (W + 3) * 32;  // threads of the per-sweep barriers
 
-    if (is_halo) {
-        // ================= halo warp =================
-        // entry kinds: 0 virtual plane line (PR slot p < NL, row t)
-        //              1 virtual row of a real plane (VR slot w+NL, row q)
-        //              2 virtual row of a virtual plane (VR slot p, row q)
-        //              3 (1D/2D) virtual row of warp 0 (VR group 0, row q)
-        int e_kind[C::MAXE], e_uoff[C::MAXE], e_nblk[C::MAXE];
-        float* e_dst[C::MAXE];  // shared address of block 0 of the line
-        int e_dmask[C::MAXE];   // ring blocks - 1
-        const float* e_src[C::MAXE];
-        const int NE = (ND == 3) ? (NL * 32 + NL * W + NL * NL) : NL;
-#pragma unroll
-        for (int j = 0; j < C::MAXE; j++) {
-            const int e = lane + 32 * j;
-            e_kind[j] = -1;
-            e_uoff[j] = 0;
-            e_nblk[j] = 0;
-            e_dst[j] = nullptr;
-            e_dmask[j] = 0;
-            e_src[j] = nullptr;
-            if (e >= NE) continue;
-            if (ND == 3) {
-                if (e < NL * 32) {
-                    const int p = e / 32, t = e % 32;
-                    e_kind[j] = 0;
-                    e_uoff[j] = 0;
-                    e_nblk[j] = nshift / 4;
-                    e_dst[j] = PR + ((size_t)p * 32 + t) * kRPS;
-                    e_dmask[j] = kRP / 4 - 1;
-                    if (ib > 0)
-                        e_src[j] = A.halo_plane + ((((size_t)(ib - 1) * g.nb1 + jb) * NL + p) * 32 + t) * nshift;
-                } else if (e < NL * 32 + NL * W) {
-                    const int e2 = e - NL * 32, w = e2 / NL, q = e2 % NL;
-                    e_kind[j] = 1;
-                    e_uoff[j] = w;
-                    e_nblk[j] = npad / 4;
-                    e_dst[j] = VR + ((size_t)(w + NL) * NL + q) * kRV;
-                    e_dmask[j] = kRV / 4 - 1;
-                    const uint64_t plane = (uint64_t)ib * W + w;
-                    if (jb > 0 && plane < g.P)
-                        e_src[j] = A.halo_row + (((size_t)plane * g.nb1 + (jb - 1)) * NL + q) * npad;
-                } else {
-                    const int e3 = e - NL * 32 - NL * W, p = e3 / NL, q = e3 % NL;
-                    e_kind[j] = 2;
-                    e_uoff[j] = p - NL;
-                    e_nblk[j] = npad / 4;
-                    e_dst[j] = VR + ((size_t)p * NL + q) * kRV;
-                    e_dmask[j] = kRV / 4 - 1;
-                    if (ib > 0 && jb > 0) {
-                        const uint64_t plane = (uint64_t)(ib - 1) * W + W - NL + p;
-                        e_src[j] = A.halo_row + (((size_t)plane * g.nb1 + (jb - 1)) * NL + q) * npad;
-                    }
-                }
-            } else {
-                e_kind[j] = 3;
+    if (is_helper) {
+        // ================= helper warps: halo lines in (W), staging tiles (W + 1), halo lines out (W + 2)
+        // Iteration r of the helper warps: wait until the compute warps have
+        // finished the sweeps < r (barrier kBarDone), release sweep r
+        // (barrier kBarReady), then work while sweep r runs.
+        //   halo warp (W): decides whether the CTA stops (its arrival on
+        //     kBarReady carries the decision in S.abort), lands the halo
+        //     blocks of sweep r + 1 (requested in iteration r - 2) and
+        //     requests those of r + 3.
+        //   staging warp (W + 1): waits until the x tiles of sweep r are in
+        //     and the output slots reused in sweep r have been read, then
+        //     stores the finished output tiles and loads x tiles ahead.
+        //   copy-out warp (W + 2): copies out the halo blocks completed in
+        //     sweep r - 1 and, at the end, publishes the item's state.
+        // The staging and copy-out warps sync on kBarReady (instead of only
+        // arriving), so they see the decision in the same sweep as the
+        // compute warps.
+        if (warp == W) {
+            // entry kinds: 0 virtual plane line (PR slot p < NL, row t)
+            //              1 virtual row of a real plane (VR slot w+NL, row q)
+            //              2 virtual row of a virtual plane (VR slot p, row q)
+            //              3 (1D/2D) virtual row of warp 0 (VR group 0, row q)
+            const uint64_t* const hrow_g = reinterpret_cast<const uint64_t*>(A.halo_row);
+            const uint64_t* const hplane_g = reinterpret_cast<const uint64_t*>(A.halo_plane);
+            int e_kind[C::MAXE], e_uoff[C::MAXE], e_nblk[C::MAXE];
+            float* e_dst[C::MAXE];  // shared address of block 0 of the line
+            int e_dmask[C::MAXE];   // ring blocks - 1
+            const uint64_t* e_src[C::MAXE];
+            int e_bstr[C::MAXE];              // words between consecutive blocks of the line
+            const unsigned* e_prog[C::MAXE];  // the producer's state word (aborts)
+            const int NE = (ND == 3) ? (NL * 32 + NL * W + NL * NL) : NL;
+    #pragma unroll
+            for (int j = 0; j < C::MAXE; j++) {
+                const int e = lane + 32 * j;
+                e_kind[j] = -1;
                 e_uoff[j] = 0;
-                e_nblk[j] = npad / 4;
-                e_dst[j] = VR + (size_t)e * kRV;
-                e_dmask[j] = kRV / 4 - 1;
-                if (jb > 0) e_src[j] = A.halo_row + ((size_t)(jb - 1) * NL + e) * npad;
-            }
-        }
-        // copy-out entries: the halo lines this CTA produces, moved from shared
-        // memory to the global halo buffers one 4-column block per sweep
-        //   3D row halo: warp w's bottom line q (HR), block b after sweep b+w+8
-        //   3D plane halo: the last NL warps' plane-ring rows (diagonal), block
-        //                  blk after sweep blk+w
-        //   2D row halo: the last warp's bottom lines (VR group W), block b
-        //                after sweep b+9W-1
-        constexpr int MAXC = (ND == 3) ? (NL * kMaxWaveWarps + NL * 32 + 31) / 32 : 1;
-        const float* c_src[MAXC];
-        float* c_dst[MAXC];
-        int c_off[MAXC], c_nblk[MAXC], c_smask[MAXC], c_sstride[MAXC];
-#pragma unroll
-        for (int j = 0; j < MAXC; j++) {
-            const int e = lane + 32 * j;
-            c_src[j] = nullptr;
-            c_dst[j] = nullptr;
-            c_off[j] = 0;
-            c_nblk[j] = 0;
-            c_smask[j] = 0;
-            c_sstride[j] = 0;
-            if (ND == 3) {
-                if (e < NL * W) {
-                    const int w = e / NL, q = e % NL;
-                    const uint64_t plane = (uint64_t)ib * W + w;
-                    if (plane < g.P && jb + 1 < g.nb1) {
-                        c_src[j] = HR + ((size_t)w * NL + q) * kRV;
-                        c_dst[j] = A.halo_row + (((size_t)plane * g.nb1 + jb) * NL + q) * npad;
-                        c_off[j] = w + 9;
-                        c_nblk[j] = npad / 4;
-                        c_smask[j] = kRV / 4 - 1;
+                e_nblk[j] = 0;
+                e_dst[j] = nullptr;
+                e_dmask[j] = 0;
+                e_src[j] = nullptr;
+                e_bstr[j] = 4;
+                e_prog[j] = nullptr;
+                if (e >= NE) continue;
+                if (ND == 3) {
+                    if (e < NL * 32) {
+                        const int p = e / 32, t = e % 32;
+                        e_kind[j] = 0;
+                        e_uoff[j] = 0;
+                        e_nblk[j] = nshift / 4;
+                        e_dst[j] = PR + ((size_t)p * 32 + t) * kRPS;
+                        e_dmask[j] = kRP / 4 - 1;
+                        // rows past the field's end have no producer (their lanes are idle)
+                        if (ib > 0 && (uint64_t)jb * 32 + t < g.M) {
+                            e_src[j] = hplane_g + (((size_t)(ib - 1) * g.nb1 + jb) * NL + p) * 32 * nshift + t * 4;
+                            e_bstr[j] = 32 * 4;
+                            e_prog[j] = A.prog + (ib - 1) * g.nb1 + jb;
+                        }
+                    } else if (e < NL * 32 + NL * W) {
+                        const int e2 = e - NL * 32, w = e2 / NL, q = e2 % NL;
+                        e_kind[j] = 1;
+                        e_uoff[j] = w;
+                        e_nblk[j] = npad / 4;
+                        e_dst[j] = VR + ((size_t)(w + NL) * NL + q) * kRV;
+                        e_dmask[j] = kRV / 4 - 1;
+                        const uint64_t plane = (uint64_t)ib * W + w;
+                        if (jb > 0 && plane < g.P) {
+                            e_src[j] = hrow_g + (((size_t)plane * g.nb1 + (jb - 1)) * NL + q) * npad;
+                            e_prog[j] = A.prog + ib * g.nb1 + jb - 1;
+                        }
+                    } else {
+                        const int e3 = e - NL * 32 - NL * W, p = e3 / NL, q = e3 % NL;
+                        e_kind[j] = 2;
+                        e_uoff[j] = p - NL;
+                        e_nblk[j] = npad / 4;
+                        e_dst[j] = VR + ((size_t)p * NL + q) * kRV;
+                        e_dmask[j] = kRV / 4 - 1;
+                        if (ib > 0 && jb > 0) {
+                            const uint64_t plane = (uint64_t)(ib - 1) * W + W - NL + p;
+                            e_src[j] = hrow_g + (((size_t)plane * g.nb1 + (jb - 1)) * NL + q) * npad;
+                            e_prog[j] = A.prog + (ib - 1) * g.nb1 + jb - 1;
+                        }
                     }
-                } else if (e < NL * W + NL * 32) {
-                    const int e2 = e - NL * W, p2 = e2 / 32, t = e2 % 32, w = W - NL + p2;
-                    const uint64_t plane = (uint64_t)ib * W + w, row = (uint64_t)jb * 32 + t;
-                    if (ib + 1 < g.nb0 && plane < g.P && row < g.M) {
-                        c_src[j] = PR + ((size_t)(w + NL) * 32 + t) * kRPS;
-                        c_dst[j] = A.halo_plane + ((((size_t)ib * g.nb1 + jb) * NL + p2) * 32 + t) * nshift;
-                        c_off[j] = w + 1;
-                        c_nblk[j] = nshift / 4;
-                        c_smask[j] = kRP / 4 - 1;
+                } else {
+                    e_kind[j] = 3;
+                    e_uoff[j] = 0;
+                    e_nblk[j] = npad / 4;
+                    e_dst[j] = VR + (size_t)e * kRV;
+                    e_dmask[j] = kRV / 4 - 1;
+                    if (jb > 0) {
+                        e_src[j] = hrow_g + ((size_t)(jb - 1) * NL + e) * npad;
+                        e_prog[j] = A.prog + jb - 1;
                     }
                 }
-            } else if (e < NL && jb + 1 < g.nb1) {
-                c_src[j] = VR + ((size_t)W * NL + e) * kRV;
-                c_dst[j] = A.halo_row + ((size_t)jb * NL + e) * npad;
-                c_off[j] = 9 * W;
-                c_nblk[j] = npad / 4;
-                c_smask[j] = kRV / 4 - 1;
             }
-        }
-        // in iteration r (sweeps < r complete): the blocks completed in sweep r - 1
-        auto copy_out = [&](int r) {
-#pragma unroll
-            for (int j = 0; j < MAXC; j++) {
-                if (!c_src[j]) continue;
-                const int b = r - c_off[j];
-                if (b < 0 || b >= c_nblk[j]) continue;
-                const float4 v = *reinterpret_cast<const float4*>(c_src[j] + (b & c_smask[j]) * 4);
-                *reinterpret_cast<float4*>(c_dst[j] + (size_t)b * 4) = v;
-            }
-        };
-        const unsigned* prog_row = nullptr;    // CTA above (same planes)
-        const unsigned* prog_plane = nullptr;  // previous plane block
-        const unsigned* prog_diag = nullptr;   // previous plane block, row block above
-        if (ND == 3) {
-            if (jb > 0) prog_row = A.prog + ib * g.nb1 + jb - 1;
-            if (ib > 0) prog_plane = A.prog + (ib - 1) * g.nb1 + jb;
-            if (ib > 0 && jb > 0) prog_diag = A.prog + (ib - 1) * g.nb1 + jb - 1;
-        } else if (jb > 0) {
-            prog_row = A.prog + jb - 1;
-        }
-        // sweeps after which a block needed from sweep u is complete at the producer
-        const int row_lag = (ND == 3) ? 9 : 9 * W;
-        const int plane_lag = W;
-        const int diag_lag = W + 9;
-        bool timed_out = false;
-        // lanes 0, 1, 2 poll the row, plane and diagonal producer in parallel
-        const unsigned* my_src = (lane == 0) ? prog_row : (lane == 1) ? prog_plane : (lane == 2) ? prog_diag : nullptr;
-        const int my_lag = (lane == 0) ? row_lag : (lane == 1) ? plane_lag : diag_lag;
-        unsigned my_seen = 0;
-        const float* dummy = A.halo_row;
+            bool timed_out = false;
 
+            // Halo blocks first needed in sweep u (u may be negative): issue()
+            // requests them (the words land in registers), land() waits until
+            // every requested word carries the tag -- polling again while the
+            // producer has not written it, bounded, and giving up when the
+            // producer reports an abort -- and stores the values into the rings.
+            // Blocks outside a line, or of a CTA boundary without a producer,
+            // are zeros.  Two sets of pending requests alternate between odd and
+            // even sweeps, so requests are in flight for two sweeps before they
+            // are needed and no register copy waits for a load.
+            using PendV = uint64_t[C::MAXE][4];
+            using PendB = int[C::MAXE];
+            uint64_t pvA[C::MAXE][4], pvB[C::MAXE][4];
+            int pbA[C::MAXE], pbB[C::MAXE];
+    #pragma unroll
+            for (int j = 0; j < C::MAXE; j++) pbA[j] = pbB[j] = -1;
+            auto issue = [&](int u, PendV& pv, PendB& pb) {
+    #pragma unroll
+                for (int j = 0; j < C::MAXE; j++) {
+                    pb[j] = -1;
+                    if (e_kind[j] < 0) continue;
+                    const int b = u - e_uoff[j];
+                    if (b < 0) continue;  // columns before the line start are never read
+                    pb[j] = b;
+                    if (e_src[j] && b < e_nblk[j]) ld_relaxed_block(e_src[j] + (size_t)b * e_bstr[j], pv[j]);
+                }
+            };
+            auto land = [&](PendV& pv, PendB& pb) {
+    #pragma unroll
+                for (int j = 0; j < C::MAXE; j++) {
+                    if (pb[j] < 0) continue;
+                    const int b = pb[j];
+                    float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    if (e_src[j] && b < e_nblk[j]) {
+                        if (!timed_out && !halo_tagged(pv[j])) {
+                            const uint64_t t0 = globaltimer();
+                            for (unsigned it = 1;; it++) {
+                                __nanosleep(32);
+                                ld_relaxed_block(e_src[j] + (size_t)b * e_bstr[j], pv[j]);
+                                if (halo_tagged(pv[j])) break;
+                                if ((it & 63) == 0 &&
+                                    (ld_acquire_u32(e_prog[j]) == kProgAbort || globaltimer() - t0 > A.timeout_ns ||
+                                     it >= (1u << 28))) {
+                                    timed_out = true;
+                                    break;
+                                }
+                            }
+                        }
+                        if (!timed_out)
+                            v = make_float4(__uint_as_float((uint32_t)pv[j][0]), __uint_as_float((uint32_t)pv[j][1]),
+                                            __uint_as_float((uint32_t)pv[j][2]), __uint_as_float((uint32_t)pv[j][3]));
+                    }
+                    *reinterpret_cast<float4*>(e_dst[j] + (size_t)((b & e_dmask[j]) * 4)) = v;
+                    pb[j] = -1;
+                }
+                timed_out = __any_sync(0xffffffffu, timed_out);
+            };
+            // prologue: every halo block needed up to sweep 1; requests for 2, 3
+            for (int u = -2 * NL - 1; u < 2; u++) {
+                issue(u, pvA, pbA);
+                land(pvA, pbA);
+            }
+            issue(2, pvA, pbA);
+            issue(3, pvB, pbB);
+            if (lane == 0 && timed_out) S.abort = 1;
+            __syncwarp();
+            named_bar_arrive(kBarReady, nthr_all);  // sweep 0
+            bool stop = timed_out;
+            for (int r = 1; r <= nsweeps && !stop; r++) {
+                named_bar_sync(kBarDone, nthr_all);  // sweeps < r are complete
+                stop = __any_sync(0xffffffffu, timed_out || *(volatile int*)&S.timeout != 0);
+                if (lane == 0 && stop) S.abort = 1;
+                __syncwarp();
+                if (r < nsweeps) named_bar_arrive(kBarReady, nthr_all);  // sweep r
+                if (stop) break;
+                if (r & 1) {
+                    land(pvA, pbA);  // sweep r + 1
+                    issue(r + 3, pvA, pbA);
+                } else {
+                    land(pvB, pbB);
+                    issue(r + 3, pvB, pbB);
+                }
+            }
+            if (lane == 0 && timed_out) S.abort = 1;
+            __syncwarp();
+            named_bar_sync(kBarEnd, 3 * 32);  // the helper warps see the final S.abort
+            return;
+                }
+        if (warp == W + 2) {
+            // copy-out entries: the halo lines this CTA produces, moved from shared
+            // memory to the global halo buffers one 4-column block per sweep
+            //   3D row halo: warp w's bottom line q (HR), block b after sweep b+w+8
+            //   3D plane halo: the last NL warps' plane-ring rows (diagonal), block
+            //                  blk after sweep blk+w
+            //   2D row halo: the last warp's bottom lines (VR group W), block b
+            //                after sweep b+9W-1
+            constexpr int MAXC = (ND == 3) ? (NL * kMaxWaveWarps + NL * 32 + 31) / 32 : 1;
+            uint64_t* const hrow_o = reinterpret_cast<uint64_t*>(A.halo_row);
+            uint64_t* const hplane_o = reinterpret_cast<uint64_t*>(A.halo_plane);
+            const float* c_src[MAXC];
+            uint64_t* c_dst[MAXC];
+            int c_off[MAXC], c_nblk[MAXC], c_smask[MAXC], c_sstride[MAXC], c_bstr[MAXC];
+    #pragma unroll
+            for (int j = 0; j < MAXC; j++) {
+                const int e = lane + 32 * j;
+                c_src[j] = nullptr;
+                c_dst[j] = nullptr;
+                c_off[j] = 0;
+                c_nblk[j] = 0;
+                c_smask[j] = 0;
+                c_sstride[j] = 0;
+                c_bstr[j] = 4;
+                if (ND == 3) {
+                    if (e < NL * W) {
+                        const int w = e / NL, q = e % NL;
+                        const uint64_t plane = (uint64_t)ib * W + w;
+                        if (plane < g.P && jb + 1 < g.nb1) {
+                            c_src[j] = HR + ((size_t)w * NL + q) * kRV;
+                            c_dst[j] = hrow_o + (((size_t)plane * g.nb1 + jb) * NL + q) * npad;
+                            c_off[j] = w + 9;
+                            c_nblk[j] = npad / 4;
+                            c_smask[j] = kRV / 4 - 1;
+                        }
+                    } else if (e < NL * W + NL * 32) {
+                        const int e2 = e - NL * W, p2 = e2 / 32, t = e2 % 32, w = W - NL + p2;
+                        const uint64_t plane = (uint64_t)ib * W + w, row = (uint64_t)jb * 32 + t;
+                        if (ib + 1 < g.nb0 && plane < g.P && row < g.M) {
+                            c_src[j] = PR + ((size_t)(w + NL) * 32 + t) * kRPS;
+                            c_dst[j] = hplane_o + (((size_t)ib * g.nb1 + jb) * NL + p2) * 32 * nshift + t * 4;
+                            c_bstr[j] = 32 * 4;
+                            c_off[j] = w + 1;
+                            c_nblk[j] = nshift / 4;
+                            c_smask[j] = kRP / 4 - 1;
+                        }
+                    }
+                } else if (e < NL && jb + 1 < g.nb1) {
+                    c_src[j] = VR + ((size_t)W * NL + e) * kRV;
+                    c_dst[j] = hrow_o + ((size_t)jb * NL + e) * npad;
+                    c_off[j] = 9 * W;
+                    c_nblk[j] = npad / 4;
+                    c_smask[j] = kRV / 4 - 1;
+                }
+            }
+            // in iteration r (sweeps < r complete): the blocks completed in sweep r - 1
+            auto copy_out = [&](int r) {
+    #pragma unroll
+                for (int j = 0; j < MAXC; j++) {
+                    if (!c_src[j]) continue;
+                    const int b = r - c_off[j];
+                    if (b < 0 || b >= c_nblk[j]) continue;
+                    const float4 v = *reinterpret_cast<const float4*>(c_src[j] + (b & c_smask[j]) * 4);
+                    st_relaxed_block(c_dst[j] + (size_t)b * c_bstr[j], halo_word(v.x), halo_word(v.y), halo_word(v.z),
+                                     halo_word(v.w));
+                }
+            };
+            named_bar_sync(kBarReady, nthr_all);  // sweep 0
+            bool stop = *(volatile int*)&S.abort != 0;
+            for (int r = 1; r <= nsweeps && !stop; r++) {
+                named_bar_sync(kBarDone, nthr_all);  // sweeps < r are complete
+                if (r < nsweeps) {
+                    named_bar_sync(kBarReady, nthr_all);  // sweep r
+                    stop = *(volatile int*)&S.abort != 0;
+                    if (stop) break;
+                }
+                copy_out(r);
+            }
+            __syncwarp();
+            named_bar_sync(kBarEnd, 3 * 32);
+            if (!S.abort) {
+                // the halo blocks completed in the last sweeps
+                for (int r = nsweeps; r <= nsweeps + 9 * W + 9; r++) copy_out(r);
+            }
+            fence_acq_rel_gpu();
+            __syncwarp();
+            if (lane == 0) {
+                if (S.abort) {
+                    atomicOr(&A.st->err, kErrTimeout);
+                    st_release_u32(my_prog, kProgAbort);
+                } else {
+                    st_release_u32(my_prog, final_prog);
+                }
+            }
+            return;
+                }
         // staging tiles of compute warp w: first row, valid rows, skew in
         // sweeps, and TMA coordinates (row, plane)
         auto tile_row0 = [&](int w) -> uint64_t {
@@ -512,15 +658,31 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
                 }
             }
         };
-        // store output tile kt of warp w
+        // store output tile kt of warp w: the staging warp reads the tile
+        // from shared memory and writes it with coalesced stores (16 bytes a
+        // lane when rows are 16-byte aligned: 4 lanes a u16 row, 8 an f32
+        // row).  A chunk that starts inside the row ends inside its pitch
+        // (codes: a pitch of whole 8-code chunks; values: 4 | N when aligned).
         auto store_tile = [&](int w, int kt) {
             const int c0 = kt * kTW;
             const OT* slot = OR + ((size_t)w * kTS + kt % kTS) * kTE;
-            if (tma_o) {
-                if (lane == 0) tma_store_3d(&A.tm_out, c0, tma_row(w), tma_plane(w), slot);
+            const int nv = tile_rows(w);
+            const uint64_t base = tile_row0(w) * A.opitch + (uint64_t)c0;
+            OT* const og = DEC ? reinterpret_cast<OT*>(A.out) : reinterpret_cast<OT*>(A.codes);
+            if (vec_o) {
+                constexpr int EPC = 16 / (int)sizeof(OT);  // elements per 16-byte chunk
+                constexpr int CPR = kTW / EPC;             // chunks per tile row
+                constexpr int RPI = 32 / CPR;              // tile rows per warp instruction
+                const int cr = lane % CPR, rr = lane / CPR;
+                const bool in = c0 + cr * EPC < N;
+#pragma unroll
+                for (int t0 = 0; t0 < 32; t0 += RPI) {
+                    const int t = t0 + rr;
+                    if (!in || t >= nv) continue;
+                    const uint4 v = *reinterpret_cast<const uint4*>(slot + t * kTW + cr * EPC);
+                    *reinterpret_cast<uint4*>(og + base + (uint64_t)t * A.opitch + cr * EPC) = v;
+                }
             } else {
-                const int nv = tile_rows(w);
-                const uint64_t base = tile_row0(w) * A.opitch + (uint64_t)c0;
                 const bool in = c0 + lane < N;
                 for (int t0 = 0; t0 < nv; t0 += 8) {
                     OT v[8];
@@ -529,9 +691,7 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
 #pragma unroll
                     for (int i = 0; i < 8; i++) {
                         if (!in || t0 + i >= nv) continue;
-                        const uint64_t idx = base + (uint64_t)(t0 + i) * A.opitch + lane;
-                        if constexpr (DEC) A.out[idx] = v[i];
-                        else A.codes[idx] = v[i];
+                        og[base + (uint64_t)(t0 + i) * A.opitch + lane] = v[i];
                     }
                 }
             }
@@ -547,7 +707,6 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
                     if (d >= 0 && (d >> 3) < nfull) store_tile(w, d >> 3);
                 }
             }
-            if (lane == 0) bulk_commit();
         };
         // full tiles of warp w stored inside the sweep loop
         auto flushed_in_loop = [&](int w) {
@@ -555,73 +714,39 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
             return lim < 0 ? 0 : min(nfull, lim / 8 + 1);
         };
 
-        // load the blocks first needed in sweep u (u may be negative)
-        auto issue = [&](int u) {
-            if (my_src && !timed_out) {
-                const unsigned need = min((unsigned)max(u + my_lag, 0), final_prog);
-                if (!wait_progress(my_src, need, my_seen, A.timeout_ns)) timed_out = true;
-            }
-            timed_out = __any_sync(0xffffffffu, timed_out);
-#pragma unroll
-            for (int j = 0; j < C::MAXE; j++) {
-                if (e_kind[j] < 0) continue;
-                const int b = u - e_uoff[j];
-                if (b < 0) continue;  // columns before the line start are never read
-                float* dst = e_dst[j] + (size_t)((b & e_dmask[j]) * 4);
-                const bool ok = e_src[j] && !timed_out && b >= 0 && b < e_nblk[j];
-                cp_async16(dst, ok ? (const void*)(e_src[j] + (size_t)b * 4) : (const void*)dummy, ok ? 16 : 0);
-            }
-        };
-        // Iteration r: wait until the compute warps have finished the sweeps
-        // < r (barrier kBarDone), release sweep r (barrier kBarReady, whose
-        // halo blocks were loaded kPFH iterations earlier), then, while sweep
-        // r runs, copy out and publish the halo blocks of sweep r - 1, store
-        // the finished output tiles and load ahead.
-        // prologue: every halo block needed up to sweep kPFH, x tiles up to kPFX
+        // staging warp; prologue: x tiles up to sweep kPFX
         int u_issued = kPFX;  // latest sweep whose x tiles were issued
-        for (int u = -2 * NL - 1; u <= kPFH; u++) issue(u);
         for (int u = 0; u <= kPFX; u++) issue_x(u);
         cp_async_commit();
         cp_async_wait<0>();
-        if (lane == 0 && timed_out) S.abort = 1;
         __syncwarp();
-        named_bar_arrive(kBarReady, nthr_all);  // sweep 0
-        bool stop = timed_out;
+        named_bar_sync(kBarReady, nthr_all);  // sweep 0
+        bool stop = *(volatile int*)&S.abort != 0;
         for (int r = 1; r <= nsweeps && !stop; r++) {
             named_bar_sync(kBarDone, nthr_all);  // sweeps < r are complete
-            cp_async_wait<kPFH - 1>();           // halo blocks of sweep r
-            // output slots rewritten from sweep r on: their stores have read them
-            if (lane == 0) bulk_wait_read<4>();
-            stop = __any_sync(0xffffffffu, timed_out || *(volatile int*)&S.timeout != 0);
-            if (lane == 0 && stop) S.abort = 1;
+            cp_async_wait<kPFX - 1>();           // x tiles of sweep r (when not loaded by TMA)
             __syncwarp();
-            if (r < nsweeps) named_bar_arrive(kBarReady, nthr_all);  // sweep r
-            if (stop) break;
-            copy_out(r);
-            if (r % g.pub == 0) {  // publish: sweeps < r are complete
-                fence_acq_rel_gpu();
-                __syncwarp();
-                if (lane == 0) st_release_u32(my_prog, (unsigned)r);
+            if (r < nsweeps) {
+                named_bar_sync(kBarReady, nthr_all);  // sweep r
+                stop = *(volatile int*)&S.abort != 0;
+                if (stop) break;
             }
             flush(r);
-            issue(r + kPFH);
             issue_x(r + kPFX);
             u_issued = r + kPFX;
             cp_async_commit();
         }
         cp_async_wait<0>();
+        __syncwarp();
+        named_bar_sync(kBarEnd, 3 * 32);
         if (!S.abort) {
-            // the halo blocks completed in the last sweeps
-            for (int r = nsweeps; r <= nsweeps + 9 * W + 9; r++) copy_out(r);
             // the tiles not stored yet (every sweep is complete)
             const int ntl = (N + kTW - 1) / kTW;
             for (int w = 0; w < W; w++) {
                 if (!((wv_mask >> w) & 1u)) continue;
                 for (int kt = flushed_in_loop(w); kt < ntl; kt++) store_tile(w, kt);
             }
-            if (lane == 0) bulk_commit();
         }
-        if (lane == 0) bulk_wait<0>();
         if (tma_x && S.abort && lane == 0) {
             // loads still in flight land in this CTA's shared memory: wait
             // for the latest load of every slot (the last 8 kTS sweeps issued
@@ -635,16 +760,7 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
                 mbar_wait_bounded(MB + w * kTS + kt % kTS, (unsigned)(kt / kTS) & 1u, A.timeout_ns);
             }
         }
-        fence_acq_rel_gpu();
         __syncwarp();
-        if (lane == 0) {
-            if (S.abort) {
-                atomicOr(&A.st->err, kErrTimeout);
-                st_release_u32(my_prog, kProgAbort);
-            } else {
-                st_release_u32(my_prog, final_prog);
-            }
-        }
         return;
     }
 
@@ -671,7 +787,6 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
     const IT* const xw = XR + (size_t)warp * kTS * kTE + lane * kTW;  // this lane's tile rows
     const float* const out_row = DEC ? A.out + rowbase : nullptr;       // unpredictable values (decompress)
     OT* const ow = OR + (size_t)warp * kTS * kTE + lane * kTW;
-    const int qd_last = (N - 1 + 31 + sig) / 4;  // sweep completing the last output tile
     const int col0 = -lane - sig;  // column at step 0
 
     // lanes of the last NL rows keep their values in a shared line: in 3D
@@ -859,16 +974,13 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
                 *reinterpret_cast<float4*>(PR + ((size_t)(warp + NL) * 32 + lane) * kRPS + (blk & (kRP / 4 - 1)) * 4) = v4;
             }
         }
-        // an output tile of this warp is complete after this sweep: make
-        // this thread's writes to it visible to the TMA store
-        if (tma_o && ((q >= 15 + s4 && ((q - 15 - s4) & 7) == 0) || q == qd_last)) fence_proxy_async_smem();
         named_bar_arrive(kBarDone, nthr_all);  // this warp has finished the sweep
     }
 }
 
 // one field, one work item per CTA (items from the field's ticket counter)
 template <int ND, int NL, bool DEC, bool TR>
-__global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __grid_constant__ WaveArgs A) {
+__global__ void __launch_bounds__((kMaxWaveWarps + 3) * 32, 1) k_wave(const __grid_constant__ WaveArgs A) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ WaveCtl S;
     if (threadIdx.x == 0) {
@@ -884,7 +996,7 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1) k_wave(const __gr
 // dependency order (interleaved across fields), so a CTA only waits for
 // items that resident CTAs took earlier.
 template <int NL, bool DEC>
-__global__ void __launch_bounds__((kMaxWaveWarps + 1) * 32, 1)
+__global__ void __launch_bounds__((kMaxWaveWarps + 3) * 32, 1)
     k_wave_batch(const WaveArgs* __restrict__ F, const uint2* __restrict__ order, unsigned total, unsigned* ticket) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ WaveCtl S;
@@ -990,7 +1102,7 @@ static int launch_t(const WaveArgs& a, cudaStream_t s) {
     size_t smem = wave_smem_bytes(a.g, NL, DEC);
     auto fn = k_wave<ND, NL, DEC, TR>;
     if (smem_limit_once<k_wave<ND, NL, DEC, TR>>(smem)) return SZGB_ECUDA;
-    fn<<<a.g.num_ctas, (a.g.W + 1) * 32, smem, s>>>(a);
+    fn<<<a.g.num_ctas, (a.g.W + 3) * 32, smem, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
 }
 
@@ -1021,7 +1133,7 @@ static void fill_compress(WaveArgs& a, const WaveGeom& g, const float* x, uint16
     a.st = st;
     a.timeout_ns = timeout_ns;
     a.tma_x = encode_tiles(&a.tm_x, true, x, g.N, g.M, g.P, g.N) ? 1 : 0;
-    a.tma_out = encode_tiles(&a.tm_out, false, codes, g.N, g.M, g.P, codes_pitch) ? 1 : 0;
+    a.vec_out = ((reinterpret_cast<uintptr_t>(codes) & 15) == 0 && (codes_pitch * 2) % 16 == 0) ? 1 : 0;
 }
 
 static void fill_decompress(WaveArgs& a, const WaveGeom& g, const uint16_t* codes, uint64_t codes_pitch, float* out,
@@ -1038,7 +1150,7 @@ static void fill_decompress(WaveArgs& a, const WaveGeom& g, const uint16_t* code
     a.st = st;
     a.timeout_ns = timeout_ns;
     a.tma_x = encode_tiles(&a.tm_x, false, codes, g.N, g.M, g.P, codes_pitch) ? 1 : 0;
-    a.tma_out = encode_tiles(&a.tm_out, true, out, g.N, g.M, g.P, g.N) ? 1 : 0;
+    a.vec_out = ((reinterpret_cast<uintptr_t>(out) & 15) == 0 && (g.N * 4) % 16 == 0) ? 1 : 0;
 }
 
 int launch_wave_compress(const WaveGeom& g, int layers, const float* x, uint16_t* codes, uint64_t codes_pitch,
@@ -1080,7 +1192,7 @@ int launch_wave_batch(const void* args_dev, const void* order_dev, unsigned tota
                       bool decompress, size_t smem, int grid, cudaStream_t s) {
     const WaveArgs* F = static_cast<const WaveArgs*>(args_dev);
     const uint2* order = static_cast<const uint2*>(order_dev);
-    const int block = (kMaxWaveWarps + 1) * 32;
+    const int block = (kMaxWaveWarps + 3) * 32;
     if (grid < 1) grid = 1;
     cudaError_t e;
     if (!decompress) {

@@ -208,15 +208,21 @@ WaveGeom make_geom(const szgb_ctx* c, const CallParams& cp, int layers) {
     return g;
 }
 
-void halo_sizes(const WaveGeom& g, int layers, size_t* row_floats, size_t* plane_floats) {
+// Halo line sizes in 32-bit units: every value travels as one 64-bit tagged
+// word.  The plane halo follows the row halo in one allocation (one memset
+// per launch); both counts are multiples of 64 (256-byte offsets).
+void halo_sizes(const WaveGeom& g, int layers, size_t* row_words, size_t* plane_words) {
     size_t tpr = (size_t)g.ntiles * kTile;
+    size_t r, p;
     if (g.ndim == 3) {
-        *row_floats = (size_t)g.P * g.nb1 * layers * tpr;
-        *plane_floats = (size_t)g.nb0 * g.nb1 * layers * 32 * (tpr + 32);
+        r = (size_t)g.P * g.nb1 * layers * tpr;
+        p = (size_t)g.nb0 * g.nb1 * layers * 32 * (tpr + 32);
     } else {
-        *row_floats = (size_t)g.nb1 * layers * tpr;
-        *plane_floats = 4;
+        r = (size_t)g.nb1 * layers * tpr;
+        p = 4;
     }
+    *row_words = align_up(2 * r, 64);
+    *plane_words = align_up(2 * p, 64);
 }
 
 int dev_errors(const DevState& s) {
@@ -279,8 +285,7 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
     A.add(&st, 1);
     A.add(&partials, 2 * (size_t)range_blocks);
     A.add(&codes, rows * cpitch + 8);
-    A.add(&halo_row, hrow);
-    A.add(&halo_plane, hplane);
+    A.add(&halo_row, hrow + hplane);
     A.add(&prog, g.num_ctas);
     A.add(&hist, 65536);
     A.add(&len, 65536);
@@ -309,6 +314,7 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
     rc = ensure_scratch(c, A.total);
     if (rc) return rc;
     A.bind(c->scratch);
+    halo_plane = halo_row + hrow;
     const float* x = direct_in ? data : xs;
     uint8_t* dst = direct_out ? out : ostage;
     cudaStream_t s = c->stream;
@@ -322,6 +328,7 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
     }
     if (cudaMemcpyAsync(st, &init, sizeof(DevState), cudaMemcpyHostToDevice, s) != cudaSuccess) return SZGB_ECUDA;
     cudaMemsetAsync(prog, 0, sizeof(unsigned) * g.num_ctas, s);
+    cudaMemsetAsync(halo_row, 0, (hrow + hplane) * 4, s);
     cudaMemsetAsync(hist, 0, 65536 * 4, s);
     {
         PhaseTimer t(c, PH_RANGE);
@@ -521,8 +528,7 @@ int decompress_impl(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_dev
     } else {
         A.add(&codes, rows * cpitch + 8);
     }
-    A.add(&halo_row, hrow);
-    A.add(&halo_plane, hplane);
+    A.add(&halo_row, lattice ? 1 : hrow + hplane);
     A.add(&prog, g.num_ctas);
     A.add(&rowbytes, rows);
     A.add(&rowoff, rows);
@@ -544,6 +550,7 @@ int decompress_impl(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_dev
     rc = ensure_scratch(c, A.total);
     if (rc) return rc;
     A.bind(c->scratch);
+    halo_plane = halo_row + hrow;
     const uint8_t* sb = direct_in ? in : istage;
     float* dst = direct_out ? out : ostage;
     if (!direct_in) {
@@ -562,6 +569,7 @@ int decompress_impl(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_dev
     init.e_eb = (int)((ub >> 23) & 0xffu);
     if (cudaMemcpyAsync(st, &init, sizeof(DevState), cudaMemcpyHostToDevice, s) != cudaSuccess) return SZGB_ECUDA;
     cudaMemsetAsync(prog, 0, sizeof(unsigned) * g.num_ctas, s);
+    if (!lattice) cudaMemsetAsync(halo_row, 0, (hrow + hplane) * 4, s);
     const uint64_t cb = (3ull * H.nsym + 3) & ~3ull;
     const uint64_t tb = ((uint64_t)H.tw * rows + 3) & ~3ull;
     const uint8_t* codebook = sb + kHeaderBytes;
@@ -813,12 +821,14 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
     A.add(&hist_all, (size_t)count * 65536);
     A.add(&wargs, (size_t)count * wsz);
     A.add(&order, 2 * total_items);
+    size_t nhalo = 0;
+    for (int f = 0; f < count; f++) nhalo += P[f].hrow + P[f].hplane;
+    float* halo_all;
+    A.add(&halo_all, nhalo);
     for (int f = 0; f < count; f++) {
         CompPlan& q = P[f];
         A.add(&q.partials, 2 * (size_t)q.range_blocks);
         A.add(&q.codes, q.rows * q.cpitch + 8);
-        A.add(&q.halo_row, q.hrow);
-        A.add(&q.halo_plane, q.hplane);
         A.add(&q.len, 65536);
         A.add(&q.cw, 65536);
         A.add(&q.sortbuf, kSortBufU64);
@@ -830,11 +840,14 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
     if ((rc = ensure_scratch(c, A.total))) return rc;
     A.bind(c->scratch);
     {
-        size_t po = 0;
+        size_t po = 0, ho = 0;
         for (int f = 0; f < count; f++) {
             P[f].prog = prog_all + po;
             P[f].hist = hist_all + (size_t)f * 65536;
+            P[f].halo_row = halo_all + ho;
+            P[f].halo_plane = halo_all + ho + P[f].hrow;
             po += (size_t)nitems[f];
+            ho += P[f].hrow + P[f].hplane;
         }
     }
     // pinned host tables: initial states, wavefront arguments, order; the
@@ -881,6 +894,7 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
             cudaMemcpyAsync(order, h_order, 8 * total_items, cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemsetAsync(tickets, 0, 2 * sizeof(unsigned), s) != cudaSuccess ||
             cudaMemsetAsync(prog_all, 0, nprog * sizeof(unsigned), s) != cudaSuccess ||
+            cudaMemsetAsync(halo_all, 0, nhalo * 4, s) != cudaSuccess ||
             cudaMemsetAsync(hist_all, 0, (size_t)count * 65536 * 4, s) != cudaSuccess)
             return SZGB_ECUDA;
         fork_aux(c);
@@ -1014,11 +1028,13 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
     A.add(&prog_all, nprog);
     A.add(&wargs, (size_t)count * wsz);
     A.add(&order, 2 * total_items);
+    size_t nhalo = 0;
+    for (int f = 0; f < count; f++) nhalo += P[f].hrow + P[f].hplane;
+    float* halo_all;
+    A.add(&halo_all, nhalo);
     for (int f = 0; f < count; f++) {
         DecPlan& q = P[f];
         A.add(&q.codes, q.rows * q.cpitch + 8);
-        A.add(&q.halo_row, q.hrow);
-        A.add(&q.halo_plane, q.hplane);
         A.add(&q.rowbytes, q.rows);
         A.add(&q.rowoff, q.rows);
         A.add(&q.blocksums, (q.rows + 2047) / 2048 + 1);
@@ -1030,9 +1046,12 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
     if ((rc = ensure_scratch(c, A.total))) return rc;
     A.bind(c->scratch);
     {
-        size_t po = 0;
+        size_t po = 0, ho = 0;
         for (int f = 0; f < count; f++) {
             P[f].prog = prog_all + po;
+            P[f].halo_row = halo_all + ho;
+            P[f].halo_plane = halo_all + ho + P[f].hrow;
+            ho += P[f].hrow + P[f].hplane;
             po += (size_t)nitems[f];
         }
     }
@@ -1085,7 +1104,8 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
             cudaMemcpyAsync(wargs, Hb + o_w, (size_t)count * wsz, cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemcpyAsync(order, h_order, 8 * total_items, cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemsetAsync(tickets, 0, 2 * sizeof(unsigned), s) != cudaSuccess ||
-            cudaMemsetAsync(prog_all, 0, nprog * sizeof(unsigned), s) != cudaSuccess)
+            cudaMemsetAsync(prog_all, 0, nprog * sizeof(unsigned), s) != cudaSuccess ||
+            cudaMemsetAsync(halo_all, 0, nhalo * 4, s) != cudaSuccess)
             return SZGB_ECUDA;
         fork_aux(c);
         for (int f = 0; f < count; f++) {

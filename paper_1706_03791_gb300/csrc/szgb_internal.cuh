@@ -281,23 +281,34 @@ struct BitReader {
     uint64_t endoff;     // bytes available from base
     uint64_t win;        // valid bits, MSB aligned
     int nb;              // valid bits in win
-    uint32_t pf0, pf1;   // the next two words (already requested)
+    uint32_t pf0, pf1;   // the next two words, raw (as loaded, little-endian), at wpos - 8 and wpos - 4
     uint64_t consumed;   // bits consumed
 
-    __device__ __forceinline__ uint32_t load_word(uint64_t off) const {
-        if (off + 4 <= endoff) return bswap32(__ldg(reinterpret_cast<const uint32_t*>(base + off)));
+    // A prefetch is a plain predicated load into its register: the byte order
+    // is fixed only when the word enters the window, so the load is waited
+    // for two refills after it was issued, not at once.
+    __device__ __forceinline__ uint32_t load_raw(uint64_t off) const {
+        uint32_t v = 0;
+        if (off + 4 <= endoff) v = __ldg(reinterpret_cast<const uint32_t*>(base + off));
+        return v;
+    }
+    // big-endian value of the word at off from its raw load (the last,
+    // partial word of the stream is read byte by byte)
+    __device__ __forceinline__ uint32_t word(uint64_t off, uint32_t raw) const {
+        if (off + 4 <= endoff) return bswap32(raw);
         uint32_t v = 0;
         for (int i = 0; i < 4; i++) v = (v << 8) | (off + i < endoff ? (uint32_t)base[off + i] : 0u);
         return v;
     }
+    __device__ __forceinline__ uint32_t load_word(uint64_t off) const { return word(off, load_raw(off)); }
     __device__ __forceinline__ void init(const uint8_t* b, uint64_t start, uint64_t end) {
         base = b;
         endoff = end;
         uint64_t a = start & ~(uint64_t)3;
         int skip = (int)(start - a) * 8;
         uint32_t w0 = load_word(a);
-        pf0 = load_word(a + 4);
-        pf1 = load_word(a + 8);
+        pf0 = load_raw(a + 4);
+        pf1 = load_raw(a + 8);
         wpos = a + 12;
         win = ((uint64_t)w0 << 32) << skip;
         nb = 32 - skip;
@@ -305,10 +316,10 @@ struct BitReader {
     }
     __device__ __forceinline__ void refill() {
         if (nb <= 32) {
-            win |= (uint64_t)pf0 << (32 - nb);
+            win |= (uint64_t)word(wpos - 8, pf0) << (32 - nb);
             nb += 32;
             pf0 = pf1;
-            pf1 = load_word(wpos);
+            pf1 = load_raw(wpos);
             wpos += 4;
         }
     }
@@ -316,9 +327,9 @@ struct BitReader {
     __device__ __forceinline__ uint32_t bit_at(int p) const {
         if (p < nb) return (uint32_t)(win >> (63 - p)) & 1u;
         p -= nb;
-        if (p < 32) return (pf0 >> (31 - p)) & 1u;
+        if (p < 32) return (word(wpos - 8, pf0) >> (31 - p)) & 1u;
         p -= 32;
-        return (pf1 >> (31 - p)) & 1u;
+        return (word(wpos - 4, pf1) >> (31 - p)) & 1u;
     }
     __device__ __forceinline__ void skip(int n) {
         consumed += (uint64_t)n;

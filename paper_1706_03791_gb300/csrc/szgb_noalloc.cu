@@ -126,14 +126,15 @@ extern "C" int szgb_decompress_noalloc(const uint8_t* in_dev, size_t in_len, flo
     g.num_ctas = g.nb0 * g.nb1;
     g.pub = 4;
     const size_t tpr = (size_t)g.ntiles * kTile;
-    const size_t hrow = (ndim == 3) ? (size_t)g.P * g.nb1 * layers * tpr : (size_t)g.nb1 * layers * tpr;
-    const size_t hplane = (ndim == 3) ? (size_t)g.nb0 * g.nb1 * layers * 32 * (tpr + 32) : 4;
+    // halo lines in 32-bit units: every value travels as one 64-bit tagged word
+    const size_t hrow = 2 * ((ndim == 3) ? (size_t)g.P * g.nb1 * layers * tpr : (size_t)g.nb1 * layers * tpr);
+    const size_t hplane = 2 * ((ndim == 3) ? (size_t)g.nb0 * g.nb1 * layers * 32 * (tpr + 32) : 4);
 
     // carve the scratch
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = up256(off + (bytes ? bytes : 1)); return o; };
     const size_t o_st = take(sizeof(DevState));
-    const size_t o_hrow = take(hrow * 4), o_hplane = take(hplane * 4);
+    const size_t o_hrow = take((hrow + hplane) * 4), o_hplane = o_hrow + hrow * 4;
     const size_t o_prog = take((size_t)g.num_ctas * 4);
     const size_t o_rb = take(rows * 4), o_ro = take(rows * 8), o_bs = take(((rows + 2047) / 2048 + 1) * 8);
     const size_t o_lut = take(((size_t)1 << kLutBits) * 4), o_tab = take(kDecTabU32 * 4);
@@ -148,7 +149,7 @@ extern "C" int szgb_decompress_noalloc(const uint8_t* in_dev, size_t in_len, flo
     uint32_t* rowbytes = reinterpret_cast<uint32_t*>(b + o_rb);
     uint64_t* rowoff = reinterpret_cast<uint64_t*>(b + o_ro);
 
-    // clear what starts at zero: the call state and the progress counters
+    // clear what starts at zero: the call state, the item states and the halo lines
     DevState init = {};
     init.eb_f = eb_f;
     init.twoeb = 2.0f * eb_f;
@@ -158,6 +159,7 @@ extern "C" int szgb_decompress_noalloc(const uint8_t* in_dev, size_t in_len, flo
     init.e_eb = (int)((ebu >> 23) & 0xffu);
     if (cudaMemcpyAsync(st, &init, sizeof(DevState), cudaMemcpyHostToDevice, s) != cudaSuccess) return SZGB_ECUDA;
     if (cudaMemsetAsync(prog, 0, (size_t)g.num_ctas * 4, s) != cudaSuccess) return SZGB_ECUDA;
+    if (cudaMemsetAsync(b + o_hrow, 0, (hrow + hplane) * 4, s) != cudaSuccess) return SZGB_ECUDA;
 
     const uint8_t* codebook = in_dev + kHeaderBytes;
     const uint8_t* table = codebook + cb;
