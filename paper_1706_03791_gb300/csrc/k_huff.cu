@@ -713,11 +713,17 @@ __global__ void __launch_bounds__(kEncWarps * 32) k_encode(const uint16_t* __res
             }
             uint32_t nbits = 0;
             bool any0 = false;
+            uint32_t L[kEncPts];
+            uint64_t cwk[kEncPts];
 #pragma unroll
             for (int k = 0; k < kEncPts; k++) {
+                L[k] = 0;
+                cwk[k] = 0;
                 if (k < nv) {
                     const uint32_t c = (w[k >> 1] >> (16 * (k & 1))) & 0xffffu;
-                    nbits += __ldg(len + c);
+                    L[k] = __ldg(len + c);
+                    cwk[k] = __ldg(cw + c);
+                    nbits += L[k];
                     if (c == 0) {
                         any0 = true;
                         const uint32_t u = __float_as_uint(x[base + l + k]);
@@ -731,31 +737,47 @@ __global__ void __launch_bounds__(kEncWarps * 32) k_encode(const uint16_t* __res
                 if (lane >= o) incl += y;
             }
             const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-            LaneBits wr(buf, bitpos + incl - nbits);
+            const uint32_t off = bitpos + incl - nbits;
+            if (!any0 && nbits <= 64) {
+                // common case: the lane's codes fit one 64-bit register; they
+                // span at most three buffer words (OR-ed: neighbours may share them)
+                uint64_t bits = 0;
 #pragma unroll
-            for (int k = 0; k < kEncPts; k++) {
-                if (k < nv) {
-                    const uint32_t c = (w[k >> 1] >> (16 * (k & 1))) & 0xffffu;
-                    wr.put64(__ldg(cw + c), __ldg(len + c));
-                    if (any0 && c == 0) {
-                        const uint32_t u = __float_as_uint(x[base + l + k]);
-                        if (LR.P) {  // lattice record: flag, r (64 bits), x when the flag is 0
-                            const bool lok = LR.OK[base + l + k] != 0;
-                            const uint64_t lres = (uint64_t)lattice_resid_rt(
-                                LR.P, LR.ndim, LR.layers, LR.d1, rowlen, (int64_t)(r / LR.d1),
-                                (int64_t)(r % LR.d1), (int64_t)(l + k));
-                            wr.put(lok ? 1u : 0u, 1);
-                            wr.put64(lres, 64);
-                            if (!lok) wr.put(u, 32);
-                        } else {
-                            const int t = trunc_bits(u, e_eb);
-                            wr.put(u >> 23, 9);
-                            if (t) wr.put((u >> (23 - t)) & ((1u << t) - 1u), (uint32_t)t);
+                for (int k = 0; k < kEncPts; k++) bits = (L[k] >= 64) ? cwk[k] : ((bits << L[k]) | cwk[k]);
+                if (nbits) {
+                    const uint64_t a = bits << (64 - nbits);  // MSB-aligned
+                    const uint32_t wi = off >> 5, sh = off & 31;
+                    atomicOr(buf + wi, (uint32_t)(a >> (32 + sh)));
+                    if (sh + nbits > 32) atomicOr(buf + wi + 1, (uint32_t)(a >> sh));
+                    if (sh + nbits > 64) atomicOr(buf + wi + 2, (uint32_t)(a << (32 - sh)));
+                }
+            } else {
+                LaneBits wr(buf, off);
+#pragma unroll
+                for (int k = 0; k < kEncPts; k++) {
+                    if (k < nv) {
+                        const uint32_t c = (w[k >> 1] >> (16 * (k & 1))) & 0xffffu;
+                        wr.put64(cwk[k], L[k]);
+                        if (any0 && c == 0) {
+                            const uint32_t u = __float_as_uint(x[base + l + k]);
+                            if (LR.P) {  // lattice record: flag, r (64 bits), x when the flag is 0
+                                const bool lok = LR.OK[base + l + k] != 0;
+                                const uint64_t lres = (uint64_t)lattice_resid_rt(
+                                    LR.P, LR.ndim, LR.layers, LR.d1, rowlen, (int64_t)(r / LR.d1),
+                                    (int64_t)(r % LR.d1), (int64_t)(l + k));
+                                wr.put(lok ? 1u : 0u, 1);
+                                wr.put64(lres, 64);
+                                if (!lok) wr.put(u, 32);
+                            } else {
+                                const int t = trunc_bits(u, e_eb);
+                                wr.put(u >> 23, 9);
+                                if (t) wr.put((u >> (23 - t)) & ((1u << t) - 1u), (uint32_t)t);
+                            }
                         }
                     }
                 }
+                wr.finish();
             }
-            wr.finish();
             __syncwarp();
             const uint32_t end = bitpos + total;
             const uint32_t full = end >> 5;
@@ -821,7 +843,8 @@ int launch_encode(const uint16_t* codes, uint64_t pitch, const float* x, uint64_
 //   lut[2^T]: (symbol << 8) | length for codes of length <= T (0 = longer)
 //   dectab[0..64] first code low word per length, [65..129] high word,
 //   [130..194] count, [195..259] start index into the sorted list,
-//   then the symbols sorted by (length, symbol) as u16.
+//   then the symbols sorted by (length, symbol) as u16 (65536 entries),
+//   then the multi-symbol table (kMultiBits index bits, see kMultiOff).
 
 __global__ void __launch_bounds__(1024) k_decode_tables(const uint8_t* __restrict__ cb, uint32_t nsym, int m,
                                                         uint32_t* lut, uint32_t* dectab, uint8_t* lenbuf,
@@ -909,6 +932,45 @@ __global__ void __launch_bounds__(1024) k_decode_tables(const uint8_t* __restric
                 if (rank == 0) s_next[L] = f + (uint64_t)__popc(peers);
             }
             __syncwarp();
+        }
+    }
+    __syncthreads();
+    // multi-symbol table: the codes that the next kMultiBits bits hold, taken
+    // greedily -- up to 3 symbols < 256 (one of any size), stopping after an
+    // escape (code 0: raw bits follow it); 0 when the first code is longer
+    {
+        constexpr int TB = kMultiBits;
+        uint32_t* multi = dectab + kMultiOff;
+        // the code at the top of a TB-bit window: symbol and length (0: longer than TB)
+        auto one = [&](uint32_t win, int& L) -> uint32_t {
+            for (int l = 1; l <= TB && l <= maxlen; l++) {
+                const uint64_t c = win >> (TB - l);
+                if (s_cnt[l] && c >= s_first[l] && c - s_first[l] < s_cnt[l]) {
+                    L = l;
+                    return sorted[s_start[l] + (uint32_t)(c - s_first[l])];
+                }
+            }
+            L = 0;
+            return 0;
+        };
+        for (uint32_t i = threadIdx.x; i < (1u << TB); i += blockDim.x) {
+            int L1;
+            const uint32_t s1 = one(i, L1);
+            uint32_t e = 0;
+            if (L1) {
+                uint32_t n = 1, used = (uint32_t)L1;
+                uint32_t sy[3] = {s1, 0, 0};
+                while (n < 3 && sy[n - 1] != 0 && sy[n - 1] < 256) {
+                    int Lk;
+                    const uint32_t sk = one((i << used) & ((1u << TB) - 1u), Lk);
+                    if (!Lk || used + (uint32_t)Lk > (uint32_t)TB || sk >= 256) break;
+                    sy[n++] = sk;
+                    used += (uint32_t)Lk;
+                }
+                if (n == 1) e = 1u | (used << 2) | (s1 << 8);
+                else e = n | (used << 2) | (sy[0] << 8) | (sy[1] << 16) | (sy[2] << 24);
+            }
+            multi[i] = e;
         }
     }
     if (threadIdx.x == 0) {

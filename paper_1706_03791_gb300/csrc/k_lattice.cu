@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kLatDecWarps * 32) k_lattice_decode_rows(
         }
         __syncwarp();
     }
-    if (valid && (bad || br.consumed > (uint64_t)rowbytes[row] * 8)) atomicOr(&st->err, kErrCorrupt);
+    if (valid && (bad || br.consumed() > (uint64_t)rowbytes[row] * 8)) atomicOr(&st->err, kErrCorrupt);
 }
 
 // inclusive prefix sums (wrap-around int32) along one axis of [d0][d1][d2]

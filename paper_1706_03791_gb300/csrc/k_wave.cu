@@ -118,11 +118,15 @@ __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_re
 
 // ---------------------------------------------------------------------------
 // Huffman decode of every row (a row is one stream chunk), before the
-// reconstruction wavefront: one lane per row, a warp's 32 lanes in lockstep
-// (one symbol per lane per step), codes staged through a shared tile and
-// stored coalesced into the row-pitched code array; the value of an
-// unpredictable point (code 0: sign, exponent and top t mantissa bits) goes
-// straight to its place in the output array.
+// reconstruction wavefront: one lane per row.  A step looks up the next
+// kMultiBits bits in the multi-symbol table and takes up to three codes at
+// once (one code, by the single-symbol table or the canonical search, when
+// the first code is longer, or near the end of the ring or of the row).
+// Lanes advance at their own pace through a two-tile ring of 64 columns of
+// their row; a 32-column tile is stored (coalesced, two codes a lane) once
+// every lane of the warp has passed it.  The value of an unpredictable point
+// (code 0: sign, exponent and top t mantissa bits) goes straight to its place
+// in the output array.
 
 struct DecodeArgs {
     const uint8_t* payload;
@@ -139,17 +143,23 @@ struct DecodeArgs {
 };
 
 constexpr int kDecWarps = 8;
-constexpr int kDecTileStride = 34;  // u16 per tile row: an odd word stride, conflict-free
+constexpr int kDecRing = 64;                  // ring columns per lane
+constexpr int kDecRingStride = kDecRing + 2;  // u16 per ring row: an odd word stride
+constexpr size_t kDecSmem = (size_t)(1u << kMultiBits) * 4 + (size_t)(1u << kLutBits) * 4 + 260 * 4 +
+                            (size_t)kDecWarps * 32 * kDecRingStride * 2;
 
 __global__ void __launch_bounds__(kDecWarps * 32) k_decode_rows(const __grid_constant__ DecodeArgs D) {
-    __shared__ uint32_t s_lut[1 << kLutBits];
-    __shared__ uint32_t s_tab[260];
-    __shared__ uint16_t s_tile[kDecWarps][32][kDecTileStride];
+    extern __shared__ __align__(16) uint32_t dsm[];
+    uint32_t* s_multi = dsm;
+    uint32_t* s_lut = s_multi + (1u << kMultiBits);
+    uint32_t* s_tab = s_lut + (1u << kLutBits);
+    uint16_t* s_ring = reinterpret_cast<uint16_t*>(s_tab + 260);
     __shared__ int s_err;
     if (threadIdx.x == 0) s_err = *(volatile const unsigned*)&D.st->err != 0;
     __syncthreads();
     if (s_err) return;
     const int T = (int)D.st->lut_bits, maxlen = (int)D.st->maxlen, e_eb = D.st->e_eb;
+    for (int i = threadIdx.x; i < (1 << kMultiBits); i += blockDim.x) s_multi[i] = D.dectab[kMultiOff + i];
     for (int i = threadIdx.x; i < (1 << T); i += blockDim.x) s_lut[i] = D.lut[i];
     for (int i = threadIdx.x; i < 260; i += blockDim.x) s_tab[i] = D.dectab[i];
     __syncthreads();
@@ -165,31 +175,74 @@ __global__ void __launch_bounds__(kDecWarps * 32) k_decode_rows(const __grid_con
         br.init(D.payload, D.rowoff[row], (uint64_t)(D.stream_end - D.payload));
         avail = (uint64_t)D.rowbytes[row] * 8;
     }
-    uint16_t(*tile)[kDecTileStride] = s_tile[warp];
+    uint16_t* const ring = s_ring + (size_t)warp * 32 * kDecRingStride;
+    uint16_t* const myring = ring + lane * kDecRingStride;
     float* const orow = D.out + row * D.N;
-    for (uint64_t l0 = 0; l0 < D.N; l0 += 32) {
-        const int ncol = (int)min((uint64_t)32, D.N - l0);
-        for (int j = 0; j < ncol; j++) {
-            int code = 0;
-            if (valid) {
-                code = decode_symbol(br, s_lut, T, s_tab, g_sorted, maxlen, bad);
-                if (code == 0) {
+    const uint64_t N = D.N;
+    uint64_t col = valid ? 0 : N;  // next column of this lane's row
+    for (uint64_t tb = 0; tb < N; tb += 32) {
+        const uint64_t tend = min(N, tb + 32), lim = min(N, tb + kDecRing);
+        while (__any_sync(0xffffffffu, col < tend)) {
+            if (col < lim) {
+                bool esc;
+                br.refill();
+                const uint32_t e = s_multi[(uint32_t)(br.win >> (64 - kMultiBits))];
+                const uint32_t n = e & 3u;
+                if (n != 0 && col + n <= lim) {
+                    const uint32_t used = (e >> 2) & 15u;
+                    br.win <<= used;
+                    br.nb -= (int)used;
+                    uint32_t last;
+                    if (n == 1) {
+                        last = e >> 8;
+                        myring[col & (kDecRing - 1)] = (uint16_t)last;
+                    } else {
+                        myring[col & (kDecRing - 1)] = (uint16_t)((e >> 8) & 0xffu);
+                        myring[(col + 1) & (kDecRing - 1)] = (uint16_t)((e >> 16) & 0xffu);
+                        last = (e >> 16) & 0xffu;
+                        if (n == 3) {
+                            last = e >> 24;
+                            myring[(col + 2) & (kDecRing - 1)] = (uint16_t)last;
+                        }
+                    }
+                    col += n;
+                    esc = last == 0;
+                } else {
+                    const int code = decode_symbol(br, s_lut, T, s_tab, g_sorted, maxlen, bad);
+                    myring[col & (kDecRing - 1)] = (uint16_t)code;
+                    col += 1;
+                    esc = code == 0;
+                }
+                if (esc) {
+                    // the value of an unpredictable point: sign, exponent, top t bits
                     const uint32_t se = br.take(9);
                     const int t = trunc_bits(se << 23, e_eb);
                     const uint32_t mb = br.take(t);
-                    orow[l0 + j] = __uint_as_float((se << 23) | (t ? (mb << (23 - t)) : 0u));
+                    orow[col - 1] = __uint_as_float((se << 23) | (t ? (mb << (23 - t)) : 0u));
                 }
             }
-            tile[lane][j] = (uint16_t)code;
         }
         __syncwarp();
-        for (int t = 0; t < 32; t++) {
-            const uint64_t r = row0 + t;
-            if (r < D.rows && lane < ncol) D.codes[r * D.cpitch + l0 + lane] = tile[t][lane];
+        {
+            // tile [tb, tend): two codes a lane, two rows per warp instruction;
+            // a pair that ends past the row's last column lands in the row
+            // pitch's padding
+            const int q = lane & 15;
+            const int c0 = (int)(tb & (kDecRing - 1)) + 2 * q;
+            if (tb + 2 * q < tend) {
+#pragma unroll 4
+                for (int t = lane >> 4; t < 32; t += 2) {
+                    const uint64_t r = row0 + t;
+                    if (r < D.rows) {
+                        const uint32_t v = *reinterpret_cast<const uint32_t*>(ring + t * kDecRingStride + c0);
+                        *reinterpret_cast<uint32_t*>(D.codes + r * D.cpitch + tb + 2 * q) = v;
+                    }
+                }
+            }
         }
         __syncwarp();
     }
-    if (valid && (bad || br.consumed > avail)) atomicOr(&D.st->err, kErrCorrupt);
+    if (valid && (bad || br.consumed() > avail)) atomicOr(&D.st->err, kErrCorrupt);
 }
 
 int launch_decode_rows(const uint8_t* payload, const uint64_t* rowoff, const uint32_t* rowbytes,
@@ -211,7 +264,15 @@ int launch_decode_rows(const uint8_t* payload, const uint64_t* rowoff, const uin
     const uint64_t per = 32ull * kDecWarps;
     const uint64_t blocks = (rows + per - 1) / per;
     if (blocks == 0 || blocks > 0x7fffffffull) return SZGB_EINVAL;
-    k_decode_rows<<<(unsigned)blocks, kDecWarps * 32, 0, s>>>(d);
+    static std::once_flag once;
+    static bool ok = true;
+    std::call_once(once, [] {
+        ok = cudaFuncSetAttribute(k_decode_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDecSmem) ==
+             cudaSuccess;
+        if (!ok) cudaGetLastError();
+    });
+    if (!ok) return SZGB_ECUDA;
+    k_decode_rows<<<(unsigned)blocks, kDecWarps * 32, kDecSmem, s>>>(d);
     return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
 }
 

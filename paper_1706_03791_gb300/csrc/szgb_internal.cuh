@@ -282,7 +282,7 @@ struct BitReader {
     uint64_t win;        // valid bits, MSB aligned
     int nb;              // valid bits in win
     uint32_t pf0, pf1;   // the next two words, raw (as loaded, little-endian), at wpos - 8 and wpos - 4
-    uint64_t consumed;   // bits consumed
+    uint64_t start;      // byte offset of the first bit
 
     // A prefetch is a plain predicated load into its register: the byte order
     // is fixed only when the word enters the window, so the load is waited
@@ -312,8 +312,12 @@ struct BitReader {
         wpos = a + 12;
         win = ((uint64_t)w0 << 32) << skip;
         nb = 32 - skip;
-        consumed = 0;
+        this->start = start;
     }
+    // bits consumed since init: those that entered the window, less the
+    // ones still in it
+    __device__ __forceinline__ uint64_t consumed() const { return 8 * (wpos - 8 - start) - (uint64_t)nb; }
+    // top the window up to more than 32 valid bits
     __device__ __forceinline__ void refill() {
         if (nb <= 32) {
             win |= (uint64_t)word(wpos - 8, pf0) << (32 - nb);
@@ -332,7 +336,6 @@ struct BitReader {
         return (word(wpos - 4, pf1) >> (31 - p)) & 1u;
     }
     __device__ __forceinline__ void skip(int n) {
-        consumed += (uint64_t)n;
         while (n > 0) {
             refill();
             int s = n < nb ? n : nb;
@@ -347,7 +350,6 @@ struct BitReader {
         uint32_t v = (uint32_t)(win >> (64 - n));
         win <<= n;
         nb -= n;
-        consumed += (uint64_t)n;
         return v;
     }
 };
@@ -362,7 +364,6 @@ __device__ __forceinline__ int decode_symbol(BitReader& br, const uint32_t* s_lu
     if (len != 0) {
         br.win <<= len;
         br.nb -= len;
-        br.consumed += (uint64_t)len;
         return (int)(e >> 8);
     }
     // canonical search: the codes of length L are first[L] .. first[L]+count[L]-1
@@ -498,6 +499,10 @@ int launch_read_rowbytes(const uint8_t* table, int width, uint64_t rows, uint32_
 // scratch sizes of the codebook build (elements)
 constexpr size_t kSortBufU64 = 3 * 65536;
 constexpr size_t kNodeBufU32 = 5 * 65536;
-constexpr size_t kDecTabU32 = 260 + 32768;
+// decoder table words: lengths and first codes (260), the sorted symbols
+// (65536 x u16), then the multi-symbol table (2^kMultiBits words)
+constexpr int kMultiBits = 12;
+constexpr size_t kMultiOff = 260 + 32768;
+constexpr size_t kDecTabU32 = kMultiOff + (1u << kMultiBits);
 
 }  // namespace szgb
