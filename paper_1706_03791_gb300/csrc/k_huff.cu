@@ -49,24 +49,38 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(const uint16_t* __restric
     lo = lo < 0 ? 0 : lo;
     const uint64_t vpr = pitch >> 3;  // vectors per row
     const uint64_t nvec = rows * vpr;
-    for (uint64_t v = blockIdx.x * (uint64_t)kHistThreads + threadIdx.x; v < nvec;
-         v += (uint64_t)gridDim.x * kHistThreads) {
-        const uint64_t r = (nvec >> 32) ? v / vpr : (uint64_t)((uint32_t)v / (uint32_t)vpr);
-        const uint64_t c0 = (v - r * vpr) << 3;
-        const uint4 q = __ldcs(reinterpret_cast<const uint4*>(codes + r * pitch + c0));
-        const uint64_t rem = rowlen - c0;
-        const int nv = rem < 8 ? (int)rem : 8;
-        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+    const uint64_t stride = (uint64_t)gridDim.x * kHistThreads;
+    // two vectors in flight per thread
+    for (uint64_t v0 = blockIdx.x * (uint64_t)kHistThreads + threadIdx.x; v0 < nvec; v0 += 2 * stride) {
+        uint4 q[2];
+        int nv[2];
 #pragma unroll
-        for (int k = 0; k < 8; k++) {
-            if (k < nv) {
-                uint32_t c = (w[k >> 1] >> (16 * (k & 1))) & 0xffffu;
-                if (c >= (uint32_t)nb) c = 0;  // codes are < 2^m; never index past the bins
-                const uint32_t d = c - (uint32_t)lo;
-                if (d < (uint32_t)kHistWin) {
-                    P[d * 32] += 1u;
-                } else {
-                    atomicAdd(&H[c], 1u);
+        for (int h = 0; h < 2; h++) {
+            const uint64_t v = v0 + h * stride;
+            nv[h] = 0;
+            q[h] = make_uint4(0u, 0u, 0u, 0u);
+            if (v < nvec) {
+                const uint64_t r = (nvec >> 32) ? v / vpr : (uint64_t)((uint32_t)v / (uint32_t)vpr);
+                const uint64_t c0 = (v - r * vpr) << 3;
+                q[h] = __ldcs(reinterpret_cast<const uint4*>(codes + r * pitch + c0));
+                const uint64_t rem = rowlen - c0;
+                nv[h] = rem < 8 ? (int)rem : 8;
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const uint32_t w[4] = {q[h].x, q[h].y, q[h].z, q[h].w};
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                if (k < nv[h]) {
+                    uint32_t c = (w[k >> 1] >> (16 * (k & 1))) & 0xffffu;
+                    if (c >= (uint32_t)nb) c = 0;  // codes are < 2^m; never index past the bins
+                    const uint32_t d = c - (uint32_t)lo;
+                    if (d < (uint32_t)kHistWin) {
+                        P[d * 32] += 1u;
+                    } else {
+                        atomicAdd(&H[c], 1u);
+                    }
                 }
             }
         }
@@ -434,20 +448,31 @@ __global__ void __launch_bounds__(256) k_rowbits(const uint16_t* __restrict__ co
         const uint64_t base = r * rowlen;
         const uint16_t* crow = codes + r * pitch;
         uint64_t bits = 0;
-        for (uint64_t l = (uint64_t)lane * 8; l < rowlen; l += 256) {
-            const uint4 q = __ldcs(reinterpret_cast<const uint4*>(crow + l));
-            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
-            const uint64_t rem = rowlen - l;
-            const int nv = rem < 8 ? (int)rem : 8;
+        // 512 codes a warp step: two vectors in flight per lane
+        for (uint64_t l0 = (uint64_t)lane * 8; l0 < rowlen; l0 += 512) {
+            uint4 q[2];
 #pragma unroll
-            for (int k = 0; k < 8; k++) {
-                if (k < nv) {
-                    const uint32_t c = (w[k >> 1] >> (16 * (k & 1))) & 0xffffu;
-                    bits += __ldg(len + c);
-                    if (c == 0) {
-                        bits += OK ? (uint64_t)(OK[base + l + k] ? 65 : 97)
-                                   : (uint64_t)(9 + trunc_bits(__float_as_uint(x[base + l + k]), e_eb));
-                        kcount++;
+            for (int h = 0; h < 2; h++) {
+                const uint64_t l = l0 + 256 * h;
+                q[h] = l < rowlen ? __ldcs(reinterpret_cast<const uint4*>(crow + l)) : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const uint64_t l = l0 + 256 * h;
+                if (l >= rowlen) continue;
+                const uint32_t w[4] = {q[h].x, q[h].y, q[h].z, q[h].w};
+                const uint64_t rem = rowlen - l;
+                const int nv = rem < 8 ? (int)rem : 8;
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    if (k < nv) {
+                        const uint32_t c = (w[k >> 1] >> (16 * (k & 1))) & 0xffffu;
+                        bits += __ldg(len + c);
+                        if (c == 0) {
+                            bits += OK ? (uint64_t)(OK[base + l + k] ? 65 : 97)
+                                       : (uint64_t)(9 + trunc_bits(__float_as_uint(x[base + l + k]), e_eb));
+                            kcount++;
+                        }
                     }
                 }
             }
@@ -941,31 +966,34 @@ __global__ void __launch_bounds__(1024) k_decode_tables(const uint8_t* __restric
     {
         constexpr int TB = kMultiBits;
         uint32_t* multi = dectab + kMultiOff;
-        // the code at the top of a TB-bit window: symbol and length (0: longer than TB)
-        auto one = [&](uint32_t win, int& L) -> uint32_t {
+        // first the single code at the top of every TB-bit window:
+        // (symbol << 8) | length, 0 when it is longer than TB
+        __shared__ uint32_t s_one[1u << kMultiBits];
+        for (uint32_t i = threadIdx.x; i < (1u << TB); i += blockDim.x) {
+            uint32_t e = 0;
             for (int l = 1; l <= TB && l <= maxlen; l++) {
-                const uint64_t c = win >> (TB - l);
+                const uint64_t c = i >> (TB - l);
                 if (s_cnt[l] && c >= s_first[l] && c - s_first[l] < s_cnt[l]) {
-                    L = l;
-                    return sorted[s_start[l] + (uint32_t)(c - s_first[l])];
+                    e = ((uint32_t)sorted[s_start[l] + (uint32_t)(c - s_first[l])] << 8) | (uint32_t)l;
+                    break;
                 }
             }
-            L = 0;
-            return 0;
-        };
+            s_one[i] = e;
+        }
+        __syncthreads();
         for (uint32_t i = threadIdx.x; i < (1u << TB); i += blockDim.x) {
-            int L1;
-            const uint32_t s1 = one(i, L1);
+            const uint32_t e1 = s_one[i];
+            const uint32_t s1 = e1 >> 8;
             uint32_t e = 0;
-            if (L1) {
-                uint32_t n = 1, used = (uint32_t)L1;
+            if (e1) {
+                uint32_t n = 1, used = e1 & 0xffu;
                 uint32_t sy[3] = {s1, 0, 0};
                 while (n < 3 && sy[n - 1] != 0 && sy[n - 1] < 256) {
-                    int Lk;
-                    const uint32_t sk = one((i << used) & ((1u << TB) - 1u), Lk);
-                    if (!Lk || used + (uint32_t)Lk > (uint32_t)TB || sk >= 256) break;
+                    const uint32_t ek = s_one[(i << used) & ((1u << TB) - 1u)];
+                    const uint32_t Lk = ek & 0xffu, sk = ek >> 8;
+                    if (!Lk || used + Lk > (uint32_t)TB || sk >= 256) break;
                     sy[n++] = sk;
-                    used += (uint32_t)Lk;
+                    used += Lk;
                 }
                 if (n == 1) e = 1u | (used << 2) | (s1 << 8);
                 else e = n | (used << 2) | (sy[0] << 8) | (sy[1] << 16) | (sy[2] << 24);

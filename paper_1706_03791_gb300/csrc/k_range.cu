@@ -30,7 +30,21 @@ __global__ void __launch_bounds__(256) k_range(const float* __restrict__ x, uint
     if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
         const float4* x4 = reinterpret_cast<const float4*>(x);
         uint64_t n4 = n / 4;
-        for (uint64_t i = tid; i < n4; i += nthr) {
+        // four independent 16-byte loads in flight per thread
+        uint64_t i = tid;
+        for (; i + 3 * nthr < n4; i += 4 * nthr) {
+            float4 v[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) v[k] = __ldcs(x4 + i + k * nthr);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                minmax_acc(v[k].x, mn, mx, bad);
+                minmax_acc(v[k].y, mn, mx, bad);
+                minmax_acc(v[k].z, mn, mx, bad);
+                minmax_acc(v[k].w, mn, mx, bad);
+            }
+        }
+        for (; i < n4; i += nthr) {
             float4 v = __ldcs(x4 + i);
             minmax_acc(v.x, mn, mx, bad);
             minmax_acc(v.y, mn, mx, bad);

@@ -47,7 +47,7 @@ namespace szgb {
 constexpr int kPFX = 4;   // x tiles are loaded this many sweeps ahead
 constexpr int kBarReady = 3;  // named barrier: the helper warps have made a sweep's inputs ready
 constexpr int kBarDone = 4;   // named barrier: the compute warps have finished a sweep
-constexpr int kBarEnd = 5;    // named barrier of the three helper warps at the end of an item
+constexpr int kBarEnd = 5;    // named barrier of the four helper warps at the end of an item
 constexpr int kTW = 32;   // staging tile: 32 rows x kTW columns
 constexpr int kTE = 32 * kTW;  // elements per staging tile
 constexpr int kTS = 3;    // staging ring slots per warp
@@ -330,7 +330,7 @@ struct WaveCtl {
 };
 
 // One work item (a block of planes x rows, or of rows) of one field.  Every
-// thread of the CTA calls it; threads beyond the item's W + 3 warps return at
+// thread of the CTA calls it; threads beyond the item's W + 4 warps return at
 // once.  The caller separates items with __syncthreads().
 template <int ND, int NL, bool DEC, bool TR>
 __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, unsigned char* smem_raw, WaveCtl& S) {
@@ -340,7 +340,7 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
     const WaveGeom& g = A.g;
     const int W = g.W;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool is_helper = (warp >= W);  // warps W, W + 1, W + 2: halo lines in, staging tiles, halo lines out
+    const bool is_helper = (warp >= W);  // warps W and W + 3: halo lines in; W + 1: staging tiles; W + 2: halo lines out
 
     // shared-memory carve-up from a 128-byte boundary (TMA destinations);
     // the mbarriers sit first, at a place that does not depend on W
@@ -376,7 +376,7 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
         if (threadIdx.x == 0) st_release_u32(A.prog + item, kProgAbort);
         return;
     }
-    if (warp > W + 2) return;  // a narrower item than the launch
+    if (warp > W + 3) return;  // a narrower item than the launch
 
     const int npad = g.ntiles * kTile;     // row halo line length
     const int nshift = npad + 32;          // plane halo line length (diagonal)
@@ -385,10 +385,10 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
     unsigned int* my_prog = A.prog + item;
     const QParams qp = load_qparams(A.st);
     const int N = (int)g.N;
-    const int nthr_all = (W + 3) * 32;  // threads of the per-sweep barriers
+    const int nthr_all = (W + 4) * 32;  // threads of the per-sweep barriers
 
     if (is_helper) {
-        // ================= helper warps: halo lines in (W), staging tiles (W + 1), halo lines out (W + 2)
+        // ================= helper warps: halo lines in (W, W + 3), staging tiles (W + 1), halo lines out (W + 2)
         // Iteration r of the helper warps: wait until the compute warps have
         // finished the sweeps < r (barrier kBarDone), release sweep r
         // (barrier kBarReady), then work while sweep r runs.
@@ -404,7 +404,11 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
         // The staging and copy-out warps sync on kBarReady (instead of only
         // arriving), so they see the decision in the same sweep as the
         // compute warps.
-        if (warp == W) {
+        if (warp == W || warp == W + 3) {
+            // two halo-in warps: W takes the even entry slots j (in 3D the
+            // plane lines of the first plane) and decides whether the CTA
+            // stops; W + 3 takes the odd slots (the row lines)
+            const bool decider = warp == W;
             // entry kinds: 0 virtual plane line (PR slot p < NL, row t)
             //              1 virtual row of a real plane (VR slot w+NL, row q)
             //              2 virtual row of a virtual plane (VR slot p, row q)
@@ -429,7 +433,7 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
                 e_src[j] = nullptr;
                 e_bstr[j] = 4;
                 e_prog[j] = nullptr;
-                if (e >= NE) continue;
+                if (e >= NE || (((j & 1) == 0) != decider)) continue;
                 if (ND == 3) {
                     if (e < NL * 32) {
                         const int p = e / 32, t = e % 32;
@@ -546,16 +550,34 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
             }
             issue(2, pvA, pbA);
             issue(3, pvB, pbB);
-            if (lane == 0 && timed_out) S.abort = 1;
-            __syncwarp();
-            named_bar_arrive(kBarReady, nthr_all);  // sweep 0
-            bool stop = timed_out;
+            // the deciding warp arrives on kBarReady with its decision in
+            // S.abort; the other syncs there to see it, and reports its own
+            // timeouts through S.timeout (read by the decider after kBarDone)
+            if (decider) {
+                if (lane == 0 && timed_out) S.abort = 1;
+                __syncwarp();
+                named_bar_arrive(kBarReady, nthr_all);  // sweep 0
+            } else {
+                if (lane == 0 && timed_out) S.timeout = 1;
+                __syncwarp();
+                named_bar_sync(kBarReady, nthr_all);  // sweep 0
+            }
+            bool stop = decider ? timed_out : (*(volatile int*)&S.abort != 0);
             for (int r = 1; r <= nsweeps && !stop; r++) {
                 named_bar_sync(kBarDone, nthr_all);  // sweeps < r are complete
-                stop = __any_sync(0xffffffffu, timed_out || *(volatile int*)&S.timeout != 0);
-                if (lane == 0 && stop) S.abort = 1;
-                __syncwarp();
-                if (r < nsweeps) named_bar_arrive(kBarReady, nthr_all);  // sweep r
+                if (decider) {
+                    stop = __any_sync(0xffffffffu, timed_out || *(volatile int*)&S.timeout != 0);
+                    if (lane == 0 && stop) S.abort = 1;
+                    __syncwarp();
+                    if (r < nsweeps) named_bar_arrive(kBarReady, nthr_all);  // sweep r
+                } else {
+                    if (lane == 0 && timed_out) S.timeout = 1;
+                    __syncwarp();
+                    if (r < nsweeps) {
+                        named_bar_sync(kBarReady, nthr_all);  // sweep r
+                        stop = *(volatile int*)&S.abort != 0;
+                    }
+                }
                 if (stop) break;
                 if (r & 1) {
                     land(pvA, pbA);  // sweep r + 1
@@ -567,9 +589,9 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
             }
             if (lane == 0 && timed_out) S.abort = 1;
             __syncwarp();
-            named_bar_sync(kBarEnd, 3 * 32);  // the helper warps see the final S.abort
+            named_bar_sync(kBarEnd, 4 * 32);  // the helper warps see the final S.abort
             return;
-                }
+        }
         if (warp == W + 2) {
             // copy-out entries: the halo lines this CTA produces, moved from shared
             // memory to the global halo buffers one 4-column block per sweep
@@ -649,7 +671,7 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
                 copy_out(r);
             }
             __syncwarp();
-            named_bar_sync(kBarEnd, 3 * 32);
+            named_bar_sync(kBarEnd, 4 * 32);
             if (!S.abort) {
                 // the halo blocks completed in the last sweeps
                 for (int r = nsweeps; r <= nsweeps + 9 * W + 9; r++) copy_out(r);
@@ -799,7 +821,7 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
         }
         cp_async_wait<0>();
         __syncwarp();
-        named_bar_sync(kBarEnd, 3 * 32);
+        named_bar_sync(kBarEnd, 4 * 32);
         if (!S.abort) {
             // the tiles not stored yet (every sweep is complete)
             const int ntl = (N + kTW - 1) / kTW;
@@ -1041,7 +1063,7 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
 
 // one field, one work item per CTA (items from the field's ticket counter)
 template <int ND, int NL, bool DEC, bool TR>
-__global__ void __launch_bounds__((kMaxWaveWarps + 3) * 32, 1) k_wave(const __grid_constant__ WaveArgs A) {
+__global__ void __launch_bounds__((kMaxWaveWarps + 4) * 32, 1) k_wave(const __grid_constant__ WaveArgs A) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ WaveCtl S;
     if (threadIdx.x == 0) {
@@ -1057,7 +1079,7 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 3) * 32, 1) k_wave(const __gr
 // dependency order (interleaved across fields), so a CTA only waits for
 // items that resident CTAs took earlier.
 template <int NL, bool DEC>
-__global__ void __launch_bounds__((kMaxWaveWarps + 3) * 32, 1)
+__global__ void __launch_bounds__((kMaxWaveWarps + 4) * 32, 1)
     k_wave_batch(const WaveArgs* __restrict__ F, const uint2* __restrict__ order, unsigned total, unsigned* ticket) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ WaveCtl S;
@@ -1163,7 +1185,7 @@ static int launch_t(const WaveArgs& a, cudaStream_t s) {
     size_t smem = wave_smem_bytes(a.g, NL, DEC);
     auto fn = k_wave<ND, NL, DEC, TR>;
     if (smem_limit_once<k_wave<ND, NL, DEC, TR>>(smem)) return SZGB_ECUDA;
-    fn<<<a.g.num_ctas, (a.g.W + 3) * 32, smem, s>>>(a);
+    fn<<<a.g.num_ctas, (a.g.W + 4) * 32, smem, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
 }
 
@@ -1253,7 +1275,7 @@ int launch_wave_batch(const void* args_dev, const void* order_dev, unsigned tota
                       bool decompress, size_t smem, int grid, cudaStream_t s) {
     const WaveArgs* F = static_cast<const WaveArgs*>(args_dev);
     const uint2* order = static_cast<const uint2*>(order_dev);
-    const int block = (kMaxWaveWarps + 3) * 32;
+    const int block = (kMaxWaveWarps + 4) * 32;
     if (grid < 1) grid = 1;
     cudaError_t e;
     if (!decompress) {
