@@ -392,18 +392,127 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
         // Iteration r of the helper warps: wait until the compute warps have
         // finished the sweeps < r (barrier kBarDone), release sweep r
         // (barrier kBarReady), then work while sweep r runs.
-        //   halo warp (W): decides whether the CTA stops (its arrival on
-        //     kBarReady carries the decision in S.abort), lands the halo
-        //     blocks of sweep r + 1 (requested in iteration r - 2) and
-        //     requests those of r + 3.
+        //   halo-in warps (W, W + 3): land the halo blocks of sweep r + 1
+        //     (requested in iteration r - 2) and request those of r + 3; W
+        //     decides whether the CTA stops (its arrival on kBarReady carries
+        //     the decision in S.abort).
         //   staging warp (W + 1): waits until the x tiles of sweep r are in
-        //     and the output slots reused in sweep r have been read, then
-        //     stores the finished output tiles and loads x tiles ahead.
+        //     (when they are not loaded by TMA), then loads x tiles ahead.
         //   copy-out warp (W + 2): copies out the halo blocks completed in
-        //     sweep r - 1 and, at the end, publishes the item's state.
-        // The staging and copy-out warps sync on kBarReady (instead of only
+        //     sweep r - 1, stores the output tile finished in sweep r - 1
+        //     and, at the end, publishes the item's state.
+        // The helper warps other than W sync on kBarReady (instead of only
         // arriving), so they see the decision in the same sweep as the
         // compute warps.
+        // staging tiles of compute warp w: first row, valid rows, skew in
+        // sweeps, and TMA coordinates (row, plane)
+        auto tile_row0 = [&](int w) -> uint64_t {
+            return (ND == 3) ? ((uint64_t)ib * W + w) * g.M + (uint64_t)jb * 32
+                             : (uint64_t)jb * 32 * W + (uint64_t)w * 32;
+        };
+        auto tile_rows = [&](int w) -> int {
+            if (ND == 3) {
+                if ((uint64_t)ib * W + w >= g.P) return 0;
+                return (int)min((uint64_t)32, g.M - (uint64_t)jb * 32);
+            }
+            const uint64_t r0 = (uint64_t)jb * 32 * W + (uint64_t)w * 32;
+            return r0 >= g.M ? 0 : (int)min((uint64_t)32, g.M - r0);
+        };
+        unsigned wv_mask = 0;  // warps with valid rows
+        for (int w = 0; w < W; w++)
+            if (tile_rows(w) > 0) wv_mask |= 1u << w;
+        auto tile_s4 = [&](int w) { return (ND == 3) ? w : 9 * w; };
+        auto tma_row = [&](int w) { return (ND == 3) ? jb * 32 : (jb * W + w) * 32; };
+        auto tma_plane = [&](int w) { return (ND == 3) ? ib * W + w : 0; };
+        // Tile kt of warp w is read from sweep 8 kt + s4(w) on and, when
+        // full, complete after sweep 8 kt + 15 + s4(w).  s4(w) = w (mod 8)
+        // in both topologies, so for a given sweep only warp (sweep mod 8)
+        // can start or finish a tile.
+        // x tile first read in sweep u: issued kPFX + 1 sweeps ahead
+        auto issue_x = [&](int u) {
+            {
+                if (u < 0) return;
+                const int w = u & 7;
+                if (!((wv_mask >> w) & 1u)) return;
+                const int d = u - tile_s4(w);
+                if (d < 0) return;
+                const int kt = d >> 3, c0 = kt * kTW;
+                if (c0 >= N) return;
+                IT* slot = XR + ((size_t)w * kTS + kt % kTS) * kTE;
+                if (tma_x) {
+                    if (lane == 0) {
+                        uint64_t* bar = MB + w * kTS + kt % kTS;
+                        mbar_arrive_expect_tx(bar, kTE * (unsigned)sizeof(IT));
+                        tma_load_3d(slot, &A.tm_x, c0, tma_row(w), tma_plane(w), bar);
+                    }
+                } else if constexpr (!DEC) {  // decompression always has TMA (its code array is ours)
+                    const int nv = tile_rows(w);
+                    const float* xr = A.x + tile_row0(w) * g.N;
+                    const int col = c0 + lane;
+                    for (int t = 0; t < 32; t++) {
+                        const bool ok = t < nv && col < N;
+                        cp_async4(slot + t * kTW + lane,
+                                  ok ? (const void*)(xr + (uint64_t)t * g.N + col) : (const void*)A.x, ok ? 4 : 0);
+                    }
+                }
+            }
+        };
+        // store output tile kt of warp w: the staging warp reads the tile
+        // from shared memory and writes it with coalesced stores (16 bytes a
+        // lane when rows are 16-byte aligned: 4 lanes a u16 row, 8 an f32
+        // row).  A chunk that starts inside the row ends inside its pitch
+        // (codes: a pitch of whole 8-code chunks; values: 4 | N when aligned).
+        auto store_tile = [&](int w, int kt) {
+            const int c0 = kt * kTW;
+            const OT* slot = OR + ((size_t)w * kTS + kt % kTS) * kTE;
+            const int nv = tile_rows(w);
+            const uint64_t base = tile_row0(w) * A.opitch + (uint64_t)c0;
+            OT* const og = DEC ? reinterpret_cast<OT*>(A.out) : reinterpret_cast<OT*>(A.codes);
+            if (vec_o) {
+                constexpr int EPC = 16 / (int)sizeof(OT);  // elements per 16-byte chunk
+                constexpr int CPR = kTW / EPC;             // chunks per tile row
+                constexpr int RPI = 32 / CPR;              // tile rows per warp instruction
+                const int cr = lane % CPR, rr = lane / CPR;
+                const bool in = c0 + cr * EPC < N;
+#pragma unroll
+                for (int t0 = 0; t0 < 32; t0 += RPI) {
+                    const int t = t0 + rr;
+                    if (!in || t >= nv) continue;
+                    const uint4 v = *reinterpret_cast<const uint4*>(slot + t * kTW + cr * EPC);
+                    *reinterpret_cast<uint4*>(og + base + (uint64_t)t * A.opitch + cr * EPC) = v;
+                }
+            } else {
+                const bool in = c0 + lane < N;
+                for (int t0 = 0; t0 < nv; t0 += 8) {
+                    OT v[8];
+#pragma unroll
+                    for (int i = 0; i < 8; i++) v[i] = slot[((t0 + i) & 31) * kTW + lane];
+#pragma unroll
+                    for (int i = 0; i < 8; i++) {
+                        if (!in || t0 + i >= nv) continue;
+                        og[base + (uint64_t)(t0 + i) * A.opitch + lane] = v[i];
+                    }
+                }
+            }
+        };
+        const int nfull = N / kTW;  // full tiles per row
+        // in iteration r (sweeps < r complete): the full tile completed in sweep r - 1
+        auto flush = [&](int r) {
+            const int v = r - 16;
+            if (v >= 0) {
+                const int w = v & 7;
+                if ((wv_mask >> w) & 1u) {
+                    const int d = v - tile_s4(w);
+                    if (d >= 0 && (d >> 3) < nfull) store_tile(w, d >> 3);
+                }
+            }
+        };
+        // full tiles of warp w stored inside the sweep loop
+        auto flushed_in_loop = [&](int w) {
+            const int lim = nsweeps - 17 - tile_s4(w);
+            return lim < 0 ? 0 : min(nfull, lim / 8 + 1);
+        };
+
         if (warp == W || warp == W + 3) {
             // two halo-in warps: W takes the even entry slots j (in 3D the
             // plane lines of the first plane) and decides whether the CTA
@@ -669,12 +778,19 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
                     if (stop) break;
                 }
                 copy_out(r);
+                flush(r);
             }
             __syncwarp();
             named_bar_sync(kBarEnd, 4 * 32);
             if (!S.abort) {
                 // the halo blocks completed in the last sweeps
                 for (int r = nsweeps; r <= nsweeps + 9 * W + 9; r++) copy_out(r);
+                // the tiles not stored yet (every sweep is complete)
+                const int ntl = (N + kTW - 1) / kTW;
+                for (int w = 0; w < W; w++) {
+                    if (!((wv_mask >> w) & 1u)) continue;
+                    for (int kt = flushed_in_loop(w); kt < ntl; kt++) store_tile(w, kt);
+                }
             }
             fence_acq_rel_gpu();
             __syncwarp();
@@ -687,116 +803,7 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
                 }
             }
             return;
-                }
-        // staging tiles of compute warp w: first row, valid rows, skew in
-        // sweeps, and TMA coordinates (row, plane)
-        auto tile_row0 = [&](int w) -> uint64_t {
-            return (ND == 3) ? ((uint64_t)ib * W + w) * g.M + (uint64_t)jb * 32
-                             : (uint64_t)jb * 32 * W + (uint64_t)w * 32;
-        };
-        auto tile_rows = [&](int w) -> int {
-            if (ND == 3) {
-                if ((uint64_t)ib * W + w >= g.P) return 0;
-                return (int)min((uint64_t)32, g.M - (uint64_t)jb * 32);
-            }
-            const uint64_t r0 = (uint64_t)jb * 32 * W + (uint64_t)w * 32;
-            return r0 >= g.M ? 0 : (int)min((uint64_t)32, g.M - r0);
-        };
-        unsigned wv_mask = 0;  // warps with valid rows
-        for (int w = 0; w < W; w++)
-            if (tile_rows(w) > 0) wv_mask |= 1u << w;
-        auto tile_s4 = [&](int w) { return (ND == 3) ? w : 9 * w; };
-        auto tma_row = [&](int w) { return (ND == 3) ? jb * 32 : (jb * W + w) * 32; };
-        auto tma_plane = [&](int w) { return (ND == 3) ? ib * W + w : 0; };
-        // Tile kt of warp w is read from sweep 8 kt + s4(w) on and, when
-        // full, complete after sweep 8 kt + 15 + s4(w).  s4(w) = w (mod 8)
-        // in both topologies, so for a given sweep only warp (sweep mod 8)
-        // can start or finish a tile.
-        // x tile first read in sweep u: issued kPFX + 1 sweeps ahead
-        auto issue_x = [&](int u) {
-            {
-                if (u < 0) return;
-                const int w = u & 7;
-                if (!((wv_mask >> w) & 1u)) return;
-                const int d = u - tile_s4(w);
-                if (d < 0) return;
-                const int kt = d >> 3, c0 = kt * kTW;
-                if (c0 >= N) return;
-                IT* slot = XR + ((size_t)w * kTS + kt % kTS) * kTE;
-                if (tma_x) {
-                    if (lane == 0) {
-                        uint64_t* bar = MB + w * kTS + kt % kTS;
-                        mbar_arrive_expect_tx(bar, kTE * (unsigned)sizeof(IT));
-                        tma_load_3d(slot, &A.tm_x, c0, tma_row(w), tma_plane(w), bar);
-                    }
-                } else if constexpr (!DEC) {  // decompression always has TMA (its code array is ours)
-                    const int nv = tile_rows(w);
-                    const float* xr = A.x + tile_row0(w) * g.N;
-                    const int col = c0 + lane;
-                    for (int t = 0; t < 32; t++) {
-                        const bool ok = t < nv && col < N;
-                        cp_async4(slot + t * kTW + lane,
-                                  ok ? (const void*)(xr + (uint64_t)t * g.N + col) : (const void*)A.x, ok ? 4 : 0);
-                    }
-                }
-            }
-        };
-        // store output tile kt of warp w: the staging warp reads the tile
-        // from shared memory and writes it with coalesced stores (16 bytes a
-        // lane when rows are 16-byte aligned: 4 lanes a u16 row, 8 an f32
-        // row).  A chunk that starts inside the row ends inside its pitch
-        // (codes: a pitch of whole 8-code chunks; values: 4 | N when aligned).
-        auto store_tile = [&](int w, int kt) {
-            const int c0 = kt * kTW;
-            const OT* slot = OR + ((size_t)w * kTS + kt % kTS) * kTE;
-            const int nv = tile_rows(w);
-            const uint64_t base = tile_row0(w) * A.opitch + (uint64_t)c0;
-            OT* const og = DEC ? reinterpret_cast<OT*>(A.out) : reinterpret_cast<OT*>(A.codes);
-            if (vec_o) {
-                constexpr int EPC = 16 / (int)sizeof(OT);  // elements per 16-byte chunk
-                constexpr int CPR = kTW / EPC;             // chunks per tile row
-                constexpr int RPI = 32 / CPR;              // tile rows per warp instruction
-                const int cr = lane % CPR, rr = lane / CPR;
-                const bool in = c0 + cr * EPC < N;
-#pragma unroll
-                for (int t0 = 0; t0 < 32; t0 += RPI) {
-                    const int t = t0 + rr;
-                    if (!in || t >= nv) continue;
-                    const uint4 v = *reinterpret_cast<const uint4*>(slot + t * kTW + cr * EPC);
-                    *reinterpret_cast<uint4*>(og + base + (uint64_t)t * A.opitch + cr * EPC) = v;
-                }
-            } else {
-                const bool in = c0 + lane < N;
-                for (int t0 = 0; t0 < nv; t0 += 8) {
-                    OT v[8];
-#pragma unroll
-                    for (int i = 0; i < 8; i++) v[i] = slot[((t0 + i) & 31) * kTW + lane];
-#pragma unroll
-                    for (int i = 0; i < 8; i++) {
-                        if (!in || t0 + i >= nv) continue;
-                        og[base + (uint64_t)(t0 + i) * A.opitch + lane] = v[i];
-                    }
-                }
-            }
-        };
-        const int nfull = N / kTW;  // full tiles per row
-        // in iteration r (sweeps < r complete): the full tile completed in sweep r - 1
-        auto flush = [&](int r) {
-            const int v = r - 16;
-            if (v >= 0) {
-                const int w = v & 7;
-                if ((wv_mask >> w) & 1u) {
-                    const int d = v - tile_s4(w);
-                    if (d >= 0 && (d >> 3) < nfull) store_tile(w, d >> 3);
-                }
-            }
-        };
-        // full tiles of warp w stored inside the sweep loop
-        auto flushed_in_loop = [&](int w) {
-            const int lim = nsweeps - 17 - tile_s4(w);
-            return lim < 0 ? 0 : min(nfull, lim / 8 + 1);
-        };
-
+        }
         // staging warp; prologue: x tiles up to sweep kPFX
         int u_issued = kPFX;  // latest sweep whose x tiles were issued
         for (int u = 0; u <= kPFX; u++) issue_x(u);
@@ -814,7 +821,6 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
                 stop = *(volatile int*)&S.abort != 0;
                 if (stop) break;
             }
-            flush(r);
             issue_x(r + kPFX);
             u_issued = r + kPFX;
             cp_async_commit();
@@ -822,14 +828,6 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
         cp_async_wait<0>();
         __syncwarp();
         named_bar_sync(kBarEnd, 4 * 32);
-        if (!S.abort) {
-            // the tiles not stored yet (every sweep is complete)
-            const int ntl = (N + kTW - 1) / kTW;
-            for (int w = 0; w < W; w++) {
-                if (!((wv_mask >> w) & 1u)) continue;
-                for (int kt = flushed_in_loop(w); kt < ntl; kt++) store_tile(w, kt);
-            }
-        }
         if (tma_x && S.abort && lane == 0) {
             // loads still in flight land in this CTA's shared memory: wait
             // for the latest load of every slot (the last 8 kTS sweeps issued
