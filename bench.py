@@ -299,7 +299,7 @@ def run_batch_workload(args):
                          "decompress_frac": ((stream_bytes + 4.0 * npts) / (bd / 1e3) / 1e9) / peaks()[0],
                          "note": "algorithmic bytes of the whole pass (compress 6 B/pt + range read; "
                                  "decompress stream + 4 B/pt) over the pass time"},
-            "autotune": {"W": tuned["W"], "pub": tuned["pub"], "seconds": tune_s},
+            "autotune": {"W": tuned["W"], "seconds": tune_s},
             "clocks": clk, "generate_s": gen_s,
             "parallelism": "fields sharded over %d ranks (largest first), no collective" % ws if ws > 1 else "single"}
     print(json.dumps(line), flush=True)

@@ -182,18 +182,19 @@ int szgb_decompress_batch(szgb_ctx *ctx, int count, const uint8_t *const *in_dev
                           const size_t *out_cap_elems, int *opt_status);
 
 /* Autotuner.  Times compression + decompression of the device field
- * `data_dev` (params p) for every candidate wavefront shape (warps per CTA:
- * 2,4,6,8 in 3D, 1,2,4,8 in 1D/2D; progress published every 2, 4 or 8
- * sweeps), best of `reps` runs each, and keeps the fastest for the field's
- * shape class (dimension, layers, bit lengths of planes/rows/columns); later
- * calls on fields of that class use it.  The shape changes the schedule
- * only: streams and reconstructions are identical for every candidate.
- * *W_out, *pub_out, *ms_out (may be NULL) receive the choice and its time. */
+ * `data_dev` (params p) for every candidate wavefront shape (compute warps
+ * per CTA: 2,4,6,8 in 3D, 1,2,4,8 in 1D/2D), best of `reps` runs each, and
+ * keeps the fastest for the field's shape class (dimension, layers, bit
+ * lengths of planes/rows/columns); later calls on fields of that class use
+ * it.  The shape changes the schedule only: streams and reconstructions are
+ * identical for every candidate.  *W_out and *ms_out (may be NULL) receive
+ * the choice and its time; *pub_out is set to 0 (a former progress
+ * publication interval: the wavefront no longer publishes progress). */
 int szgb_autotune(szgb_ctx *ctx, const float *data_dev, const szgb_params *p, int reps,
                   int *W_out, int *pub_out, double *ms_out);
 /* As szgb_autotune for a batch: times szgb_compress_batch +
  * szgb_decompress_batch of the given device fields for every candidate
- * shape (warps per CTA 1,2,4,6,8; publication every 2, 4, 8 sweeps) and
+ * shape (compute warps per CTA 1,2,4,6,8) and
  * keeps the fastest for every shape class in the batch: the shape that is
  * best for one field alone is often not the one that fills the GPU best
  * when many fields share it. */

@@ -24,18 +24,21 @@
 // the critical path; the descending summation order puts them last.
 //
 // Inputs and outputs are staged through shared memory: a warp's 32 rows are
-// cut into 32 x 32 tiles, which an extra "staging" warp loads (x) and stores
-// (codes, or decompressed values) with coalesced accesses; a lane reads its x
-// and writes its result at the same tile position, bank-conflict-free.
+// cut into 32 x 32 tiles; x tiles arrive by TMA, issued by a "staging"
+// helper warp, and finished output tiles (codes, or decompressed values)
+// leave with coalesced 16-byte stores by a "copy-out" helper warp; a lane
+// reads its x and writes its result at the same tile position,
+// bank-conflict-free.
 //
-// CTA boundaries go through global "halo" buffers.  An extra warp per CTA
-// copies the boundary lines out of shared memory as 64-bit words that carry
-// the value and a tag (one single-copy-atomic store each, no fence), and
-// loads the neighbouring CTAs' lines into the rings by polling those words
-// until every tag is set (bounded waits): a block is usable the moment it is
-// written, with no progress counter to publish.  The halo buffers are zeroed
-// before every launch.  CTAs take work items from a ticket counter in
-// dependency order, so a CTA only waits for CTAs that are already resident.
+// CTA boundaries go through global "halo" buffers.  The copy-out warp copies
+// the boundary lines out of shared memory as 64-bit words that carry the
+// value and a tag (single-copy-atomic stores, no fence), and two "halo-in"
+// helper warps load the neighbouring CTAs' lines into the rings by polling
+// those words until every tag is set (bounded waits): a block is usable the
+// moment it is written, with no progress counter to publish.  The halo
+// buffers are zeroed before every launch.  CTAs take work items from a
+// ticket counter in dependency order, so a CTA only waits for CTAs that are
+// already resident.
 #include <cuda.h>
 
 #include <mutex>

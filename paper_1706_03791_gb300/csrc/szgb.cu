@@ -70,7 +70,7 @@ struct szgb_ctx {
     uint64_t ph_calls[PH_N] = {};
     cudaEvent_t ev0[PH_N] = {}, ev1[PH_N] = {};
     int sm_count = 152;
-    int W2 = 8, W3 = 8, pub = 4;
+    int W2 = 8, W3 = 8;
     uint64_t timeout_ns = 4000000000ull;
     // batched paths
     cudaStream_t aux[kAux] = {};
@@ -81,11 +81,11 @@ struct szgb_ctx {
     BatchGraph g_comp, g_dec;
     // autotuned wavefront shapes per shape class (see shape_class)
     struct Tune {
-        int W, pub;
+        int W, pub;  // pub: kept in the table format, always 0
         double ms;
     };
     std::map<uint64_t, Tune> tune;
-    int force_W = 0, force_pub = 0;  // set while the autotuner times a candidate
+    int force_W = 0;  // set while the autotuner times a candidate
 };
 
 namespace {
@@ -167,14 +167,12 @@ uint64_t shape_class(const CallParams& cp, int layers) {
 }
 
 WaveGeom make_geom(const szgb_ctx* c, const CallParams& cp, int layers) {
-    int W2 = c->W2, W3 = c->W3, pub = c->pub;
+    int W2 = c->W2, W3 = c->W3;
     auto it = c->tune.find(shape_class(cp, layers));
     if (it != c->tune.end()) {
         W2 = W3 = it->second.W;
-        pub = it->second.pub;
     }
     if (c->force_W) W2 = W3 = c->force_W;
-    if (c->force_pub) pub = c->force_pub;
     WaveGeom g = {};
     g.N = cp.d2;
     g.ntiles = (int)((cp.d2 + kTile - 1) / kTile);
@@ -204,7 +202,6 @@ WaveGeom make_geom(const szgb_ctx* c, const CallParams& cp, int layers) {
         g.nsweeps = (int)((cp.d2 - 1 + 31 + 36 * (W - 1)) / 4) + 1;  // last step: column N-1 of warp W-1, lane 31
     }
     g.num_ctas = g.nb0 * g.nb1;
-    g.pub = pub;
     return g;
 }
 
@@ -878,7 +875,7 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
     key.push_back((uint64_t)count);
     key.push_back((uint64_t)(uintptr_t)c->scratch);
     key.push_back((uint64_t)(uintptr_t)c->h_batch);
-    key.push_back((uint64_t)c->W2 | ((uint64_t)c->W3 << 16) | ((uint64_t)c->pub << 32));
+    key.push_back((uint64_t)c->W2 | ((uint64_t)c->W3 << 16));
     for (int f = 0; f < count; f++) {
         key.push_back((uint64_t)(uintptr_t)data[f]);
         key.push_back((uint64_t)(uintptr_t)out[f]);
@@ -1090,7 +1087,7 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
     key.push_back((uint64_t)count);
     key.push_back((uint64_t)(uintptr_t)c->scratch);
     key.push_back((uint64_t)(uintptr_t)c->h_batch);
-    key.push_back((uint64_t)c->W2 | ((uint64_t)c->W3 << 16) | ((uint64_t)c->pub << 32));
+    key.push_back((uint64_t)c->W2 | ((uint64_t)c->W3 << 16));
     for (int f = 0; f < count; f++) {
         key.push_back((uint64_t)(uintptr_t)in[f]);
         key.push_back((uint64_t)in_len[f]);
@@ -1176,7 +1173,6 @@ int szgb_create(szgb_ctx** out, int device, size_t device_mem_budget) {
     const char* e;
     if ((e = getenv("SZGB_W2"))) c->W2 = std::max(1, std::min(kMaxWaveWarps, atoi(e)));
     if ((e = getenv("SZGB_W3"))) c->W3 = std::max(1, std::min(kMaxWaveWarps, atoi(e)));
-    if ((e = getenv("SZGB_PUB"))) c->pub = std::max(1, std::min(64, atoi(e)));
     *out = c;
     return SZGB_OK;
 }
@@ -1233,17 +1229,16 @@ int szgb_autotune(szgb_ctx* c, const float* data_dev, const szgb_params* p, int 
     }
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int Ws3[] = {2, 4, 6, 8}, Ws2[] = {1, 2, 4, 8}, pubs[] = {2, 4, 8};
+    const int Ws3[] = {2, 4, 6, 8}, Ws2[] = {1, 2, 4, 8};
     const int* Ws = cp.ndim == 3 ? Ws3 : Ws2;
     double best = 1e30;
-    int bW = c->W3, bP = c->pub;
+    int bW = c->W3;
     const bool prof = c->profiling;
     c->profiling = false;
     for (int wi = 0; wi < 4 && !rc; wi++) {
         if (cp.ndim == 3 && Ws[wi] < 2 * cp.layers) continue;
-        for (int pi = 0; pi < 3 && !rc; pi++) {
+        {
             c->force_W = Ws[wi];
-            c->force_pub = pubs[pi];
             double tmin = 1e30;
             for (int r = 0; r <= reps && !rc; r++) {  // the first run warms up
                 size_t olen = 0;
@@ -1259,22 +1254,21 @@ int szgb_autotune(szgb_ctx* c, const float* data_dev, const szgb_params* p, int 
             if (!rc && tmin < best) {
                 best = tmin;
                 bW = Ws[wi];
-                bP = pubs[pi];
             }
         }
     }
-    c->force_W = c->force_pub = 0;
+    c->force_W = 0;
     c->profiling = prof;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(sbuf);
     cudaFree(ybuf);
     if (rc) return rc;
-    c->tune[shape_class(cp, cp.layers)] = szgb_ctx::Tune{bW, bP, best};
+    c->tune[shape_class(cp, cp.layers)] = szgb_ctx::Tune{bW, 0, best};
     drop_graph(c->g_comp);  // captured batches used the previous shapes
     drop_graph(c->g_dec);
     if (W_out) *W_out = bW;
-    if (pub_out) *pub_out = bP;
+    if (pub_out) *pub_out = 0;
     if (ms_out) *ms_out = best;
     return SZGB_OK;
 }
@@ -1308,14 +1302,13 @@ int szgb_autotune_batch(szgb_ctx* c, int count, const float* const* data_dev, co
     cudaEventCreate(&e1);
     const bool graphs = c->use_graphs;
     c->use_graphs = false;
-    const int Ws[] = {1, 2, 4, 6, 8}, pubs[] = {2, 4, 8};
+    const int Ws[] = {1, 2, 4, 6, 8};
     double best = 1e30;
-    int bW = c->W3, bP = c->pub;
+    int bW = c->W3;
     for (int wi = 0; wi < 5 && !rc; wi++) {
         if (any3 && Ws[wi] < 2 * maxl) continue;
-        for (int pi = 0; pi < 3 && !rc; pi++) {
+        {
             c->force_W = Ws[wi];
-            c->force_pub = pubs[pi];
             double tmin = 1e30;
             for (int r = 0; r <= reps && !rc; r++) {
                 cudaEventRecord(e0, c->stream);
@@ -1331,11 +1324,10 @@ int szgb_autotune_batch(szgb_ctx* c, int count, const float* const* data_dev, co
             if (!rc && tmin < best) {
                 best = tmin;
                 bW = Ws[wi];
-                bP = pubs[pi];
             }
         }
     }
-    c->force_W = c->force_pub = 0;
+    c->force_W = 0;
     c->use_graphs = graphs;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1344,11 +1336,11 @@ int szgb_autotune_batch(szgb_ctx* c, int count, const float* const* data_dev, co
         cudaFree(yb[f]);
     }
     if (rc) return rc;
-    for (int f = 0; f < count; f++) c->tune[shape_class(cps[f], cps[f].layers)] = szgb_ctx::Tune{bW, bP, best};
+    for (int f = 0; f < count; f++) c->tune[shape_class(cps[f], cps[f].layers)] = szgb_ctx::Tune{bW, 0, best};
     drop_graph(c->g_comp);
     drop_graph(c->g_dec);
     if (W_out) *W_out = bW;
-    if (pub_out) *pub_out = bP;
+    if (pub_out) *pub_out = 0;
     if (ms_out) *ms_out = best;
     return SZGB_OK;
 }
@@ -1375,12 +1367,12 @@ int szgb_tune_load(szgb_ctx* c, const char* path) {
         unsigned long long k;
         int W, pub;
         double ms;
-        if (sscanf(line, "%llx %d %d %lf", &k, &W, &pub, &ms) != 4 || W < 1 || W > kMaxWaveWarps || pub < 1 ||
+        if (sscanf(line, "%llx %d %d %lf", &k, &W, &pub, &ms) != 4 || W < 1 || W > kMaxWaveWarps || pub < 0 ||
             pub > 64) {
             rc = SZGB_ECORRUPT;
             break;
         }
-        c->tune[(uint64_t)k] = szgb_ctx::Tune{W, pub, ms};
+        c->tune[(uint64_t)k] = szgb_ctx::Tune{W, 0, ms};
     }
     fclose(f);
     drop_graph(c->g_comp);

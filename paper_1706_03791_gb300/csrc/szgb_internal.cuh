@@ -438,7 +438,6 @@ struct WaveGeom {
     int nsweeps;          // sweeps per CTA including the final flush sweep
     int aligned;          // rows start on 16-byte boundaries (N % 4 == 0)
     int num_ctas;
-    int pub;              // progress is published every `pub` sweeps
 };
 
 // host launchers (each in its own translation unit)

@@ -124,7 +124,6 @@ extern "C" int szgb_decompress_noalloc(const uint8_t* in_dev, size_t in_len, flo
         g.nsweeps = (int)((d2 - 1 + 31 + 36 * (W - 1)) / 4) + 1;  // last step: column N-1 of warp W-1, lane 31
     }
     g.num_ctas = g.nb0 * g.nb1;
-    g.pub = 4;
     const size_t tpr = (size_t)g.ntiles * kTile;
     // halo lines in 32-bit units: every value travels as one 64-bit tagged word
     const size_t hrow = 2 * ((ndim == 3) ? (size_t)g.P * g.nb1 * layers * tpr : (size_t)g.nb1 * layers * tpr);

@@ -24,7 +24,7 @@ def test_autotune_keeps_bits(szo, tmp_path):
             ref = szo.compress(x, **kw)
             xd = torch.from_numpy(x).cuda()
             t = ctx.autotune(xd, reps=1, **kw)
-            assert t["W"] in (1, 2, 4, 6, 8) and t["pub"] in (2, 4, 8) and t["ms"] > 0
+            assert t["W"] in (1, 2, 4, 6, 8) and t["pub"] == 0 and t["ms"] > 0
             s, _ = ctx.compress(xd, **kw)
             assert np.array_equal(s.cpu().numpy(), ref)
             y = ctx.decompress(s)
@@ -60,7 +60,7 @@ def test_autotune_batch_keeps_bits(szo):
     try:
         xd = [torch.from_numpy(x).cuda() for x in xs]
         t = ctx.autotune_batch(xd, kw, reps=1)
-        assert t["W"] in (1, 2, 4, 6, 8) and t["pub"] in (2, 4, 8)
+        assert t["W"] in (1, 2, 4, 6, 8) and t["pub"] == 0
         sb, _ = ctx.compress_batch(xd, kw)
         for x, s in zip(xs, sb):
             assert np.array_equal(s.cpu().numpy(), szo.compress(x, **kw))
