@@ -8,6 +8,7 @@
 // weights); a symbol's code length is its leaf depth (one used symbol gets
 // length 1).  Codes are canonical: ordered by (length, symbol), consecutive
 // within a length.
+#include <cstring>
 #include <mutex>
 
 #include "szgb_internal.cuh"
@@ -202,9 +203,9 @@ constexpr size_t kCbSmem = 65536 + 4 * kCbRing;  // region A (64 KB) + ring (128
 // nodes in a shared-memory ring: the queue never holds more than n/2 nodes)
 // gives every node its parent; depths follow top-down; canonical codes by
 // (length, symbol).
-__global__ void __launch_bounds__(kCbThreads) k_codebook(const uint32_t* __restrict__ hist, DevState* st,
-                                                          uint8_t* len, uint64_t* cw, uint64_t* sortbuf,
-                                                          uint32_t* nodebuf) {
+// the codebook of one field; every thread of the CTA calls it
+__device__ __forceinline__ void codebook_block(const uint32_t* __restrict__ hist, DevState* st, uint8_t* len,
+                                               uint64_t* cw, uint64_t* sortbuf, uint32_t* nodebuf) {
     extern __shared__ __align__(16) unsigned char cb_smem[];
     uint64_t* s_keys = reinterpret_cast<uint64_t*>(cb_smem);          // region A: 8192 keys
     uint32_t* s_a32 = reinterpret_cast<uint32_t*>(cb_smem);           // region A: 16384 words
@@ -411,6 +412,49 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const uint32_t* __restr
     }
     __syncthreads();
     canonical_assign(usedlist, n, len, s_first, cw, nullptr);
+}
+
+__global__ void __launch_bounds__(kCbThreads) k_codebook(const uint32_t* __restrict__ hist, DevState* st,
+                                                          uint8_t* len, uint64_t* cw, uint64_t* sortbuf,
+                                                          uint32_t* nodebuf) {
+    codebook_block(hist, st, len, cw, sortbuf, nodebuf);
+}
+
+struct CodebookArgs {
+    const uint32_t* hist;
+    DevState* st;
+    uint8_t* len;
+    uint64_t* cw;
+    uint64_t* sortbuf;
+    uint32_t* nodebuf;
+};
+
+// every field of a batch in one launch, one CTA per field
+__global__ void __launch_bounds__(kCbThreads) k_codebook_batch(const CodebookArgs* __restrict__ A) {
+    const CodebookArgs a = A[blockIdx.x];
+    codebook_block(a.hist, a.st, a.len, a.cw, a.sortbuf, a.nodebuf);
+}
+
+size_t codebook_args_bytes() { return sizeof(CodebookArgs); }
+
+void codebook_args_fill(void* dst, const uint32_t* hist, DevState* st, uint8_t* len, uint64_t* cw, uint64_t* sortbuf,
+                        uint32_t* nodebuf) {
+    const CodebookArgs a = {hist, st, len, cw, sortbuf, nodebuf};
+    memcpy(dst, &a, sizeof(a));
+}
+
+int launch_codebook_batch(const void* args_dev, int count, cudaStream_t s) {
+    if (count < 1) return SZGB_OK;
+    static std::once_flag once;
+    static bool ok = false;
+    std::call_once(once, [] {
+        ok = cudaFuncSetAttribute(k_codebook_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbSmem) ==
+             cudaSuccess;
+        if (!ok) cudaGetLastError();
+    });
+    if (!ok) return SZGB_ECUDA;
+    k_codebook_batch<<<count, kCbThreads, kCbSmem, s>>>(static_cast<const CodebookArgs*>(args_dev));
+    return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
 }
 
 int launch_codebook(const uint32_t* hist, DevState* st, uint8_t* len, uint64_t* cw, uint64_t* sortbuf,
@@ -871,9 +915,10 @@ int launch_encode(const uint16_t* codes, uint64_t pitch, const float* x, uint64_
 //   then the symbols sorted by (length, symbol) as u16 (65536 entries),
 //   then the multi-symbol table (kMultiBits index bits, see kMultiOff).
 
-__global__ void __launch_bounds__(1024) k_decode_tables(const uint8_t* __restrict__ cb, uint32_t nsym, int m,
-                                                        uint32_t* lut, uint32_t* dectab, uint8_t* lenbuf,
-                                                        uint32_t* symbuf, DevState* st) {
+// the decoder tables of one field; every thread of the CTA calls it
+__device__ __forceinline__ void decode_tables_block(const uint8_t* __restrict__ cb, uint32_t nsym, int m,
+                                                    uint32_t* lut, uint32_t* dectab, uint8_t* lenbuf,
+                                                    uint32_t* symbuf, DevState* st) {
     __shared__ uint32_t s_cnt[66];
     __shared__ uint64_t s_first[66];
     __shared__ uint64_t s_next[66];
@@ -1006,6 +1051,43 @@ __global__ void __launch_bounds__(1024) k_decode_tables(const uint8_t* __restric
         st->lut_bits = (uint32_t)T;
         st->nsym = nsym;
     }
+}
+
+__global__ void __launch_bounds__(1024) k_decode_tables(const uint8_t* __restrict__ cb, uint32_t nsym, int m,
+                                                        uint32_t* lut, uint32_t* dectab, uint8_t* lenbuf,
+                                                        uint32_t* symbuf, DevState* st) {
+    decode_tables_block(cb, nsym, m, lut, dectab, lenbuf, symbuf, st);
+}
+
+struct TablesArgs {
+    const uint8_t* cb;
+    uint32_t* lut;
+    uint32_t* dectab;
+    uint8_t* lenbuf;
+    uint32_t* symbuf;
+    DevState* st;
+    uint32_t nsym;
+    int m;
+};
+
+// every field of a batch in one launch, one CTA per field
+__global__ void __launch_bounds__(1024) k_decode_tables_batch(const TablesArgs* __restrict__ A) {
+    const TablesArgs a = A[blockIdx.x];
+    decode_tables_block(a.cb, a.nsym, a.m, a.lut, a.dectab, a.lenbuf, a.symbuf, a.st);
+}
+
+size_t tables_args_bytes() { return sizeof(TablesArgs); }
+
+void tables_args_fill(void* dst, const uint8_t* codebook, uint32_t nsym, int m, uint32_t* lut, uint32_t* dec_tab,
+                      uint8_t* lenbuf, uint32_t* symbuf, DevState* st) {
+    const TablesArgs a = {codebook, lut, dec_tab, lenbuf, symbuf, st, nsym, m};
+    memcpy(dst, &a, sizeof(a));
+}
+
+int launch_decode_tables_batch(const void* args_dev, int count, cudaStream_t s) {
+    if (count < 1) return SZGB_OK;
+    k_decode_tables_batch<<<count, 1024, 0, s>>>(static_cast<const TablesArgs*>(args_dev));
+    return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
 }
 
 int launch_decode_tables(const uint8_t* codebook, uint32_t nsym, int m, uint32_t* lut, uint32_t* dec_tab,

@@ -41,6 +41,7 @@
 // already resident.
 #include <cuda.h>
 
+#include <cstring>
 #include <mutex>
 
 #include "szgb_internal.cuh"
@@ -148,27 +149,24 @@ struct DecodeArgs {
 constexpr int kDecWarps = 8;
 constexpr int kDecRing = 64;                  // ring columns per lane
 constexpr int kDecRingStride = kDecRing + 2;  // u16 per ring row: an odd word stride
-constexpr size_t kDecSmem = (size_t)(1u << kMultiBits) * 4 + (size_t)(1u << kLutBits) * 4 + 260 * 4 +
-                            (size_t)kDecWarps * 32 * kDecRingStride * 2;
+constexpr size_t kDecSmem = (size_t)(1u << kMultiBits) * 4 + 260 * 4 + (size_t)kDecWarps * 32 * kDecRingStride * 2;
 
-__global__ void __launch_bounds__(kDecWarps * 32) k_decode_rows(const __grid_constant__ DecodeArgs D) {
-    extern __shared__ __align__(16) uint32_t dsm[];
+// rows [blk * 32 kDecWarps, ...) of one field; every thread of the block calls it
+__device__ __forceinline__ void decode_rows_block(const DecodeArgs& D, uint64_t blk, uint32_t* dsm) {
     uint32_t* s_multi = dsm;
-    uint32_t* s_lut = s_multi + (1u << kMultiBits);
-    uint32_t* s_tab = s_lut + (1u << kLutBits);
+    uint32_t* s_tab = s_multi + (1u << kMultiBits);
     uint16_t* s_ring = reinterpret_cast<uint16_t*>(s_tab + 260);
     __shared__ int s_err;
     if (threadIdx.x == 0) s_err = *(volatile const unsigned*)&D.st->err != 0;
     __syncthreads();
     if (s_err) return;
-    const int T = (int)D.st->lut_bits, maxlen = (int)D.st->maxlen, e_eb = D.st->e_eb;
+    const int maxlen = (int)D.st->maxlen, e_eb = D.st->e_eb;
     for (int i = threadIdx.x; i < (1 << kMultiBits); i += blockDim.x) s_multi[i] = D.dectab[kMultiOff + i];
-    for (int i = threadIdx.x; i < (1 << T); i += blockDim.x) s_lut[i] = D.lut[i];
     for (int i = threadIdx.x; i < 260; i += blockDim.x) s_tab[i] = D.dectab[i];
     __syncthreads();
     const uint16_t* g_sorted = reinterpret_cast<const uint16_t*>(D.dectab + 260);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint64_t row0 = ((uint64_t)blockIdx.x * kDecWarps + warp) * 32;
+    const uint64_t row0 = (blk * kDecWarps + warp) * 32;
     const uint64_t row = row0 + lane;
     const bool valid = row < D.rows;
     BitReader br;
@@ -211,7 +209,10 @@ __global__ void __launch_bounds__(kDecWarps * 32) k_decode_rows(const __grid_con
                     col += n;
                     esc = last == 0;
                 } else {
-                    const int code = decode_symbol(br, s_lut, T, s_tab, g_sorted, maxlen, bad);
+                    // one code, by the canonical search: the first code is
+                    // longer than the table, or a multi-code step would pass
+                    // the ring or the row end
+                    const int code = decode_symbol(br, nullptr, 0, s_tab, g_sorted, maxlen, bad);
                     myring[col & (kDecRing - 1)] = (uint16_t)code;
                     col += 1;
                     esc = code == 0;
@@ -246,6 +247,64 @@ __global__ void __launch_bounds__(kDecWarps * 32) k_decode_rows(const __grid_con
         __syncwarp();
     }
     if (valid && (bad || br.consumed() > avail)) atomicOr(&D.st->err, kErrCorrupt);
+}
+
+__global__ void __launch_bounds__(kDecWarps * 32, 4) k_decode_rows(const __grid_constant__ DecodeArgs D) {
+    extern __shared__ __align__(16) uint32_t dsm[];
+    decode_rows_block(D, blockIdx.x, dsm);
+}
+
+// every field of a batch in one launch: field f owns blocks [blk[f], blk[f+1])
+__global__ void __launch_bounds__(kDecWarps * 32, 4)
+    k_decode_rows_batch(const DecodeArgs* __restrict__ F, const uint32_t* __restrict__ blk, int count) {
+    extern __shared__ __align__(16) uint32_t dsm[];
+    int lo = 0, hi = count - 1;  // the last field whose first block is <= blockIdx.x
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (blk[mid] <= blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const DecodeArgs D = F[lo];
+    decode_rows_block(D, blockIdx.x - blk[lo], dsm);
+}
+
+size_t decode_args_bytes() { return sizeof(DecodeArgs); }
+
+uint32_t decode_rows_blocks(uint64_t rows) { return (uint32_t)((rows + 32ull * kDecWarps - 1) / (32ull * kDecWarps)); }
+
+void decode_args_fill(void* dst, const uint8_t* payload, const uint64_t* rowoff, const uint32_t* rowbytes,
+                      const uint8_t* stream_end, const uint32_t* lut, const uint32_t* dec_tab, uint16_t* codes,
+                      uint64_t cpitch, float* out, uint64_t rows, uint64_t N, DevState* st) {
+    DecodeArgs d;
+    d.payload = payload;
+    d.rowoff = rowoff;
+    d.rowbytes = rowbytes;
+    d.stream_end = stream_end;
+    d.lut = lut;
+    d.dectab = dec_tab;
+    d.codes = codes;
+    d.cpitch = cpitch;
+    d.out = out;
+    d.rows = rows;
+    d.N = N;
+    d.st = st;
+    memcpy(dst, &d, sizeof(d));
+}
+
+int launch_decode_rows_batch(const void* args_dev, const uint32_t* blk_dev, int count, uint32_t total_blocks,
+                             cudaStream_t s) {
+    if (count < 1 || total_blocks == 0) return SZGB_OK;
+    static std::once_flag once;
+    static bool ok = true;
+    std::call_once(once, [] {
+        ok = cudaFuncSetAttribute(k_decode_rows_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kDecSmem) == cudaSuccess;
+        if (!ok) cudaGetLastError();
+    });
+    if (!ok) return SZGB_ECUDA;
+    k_decode_rows_batch<<<total_blocks, kDecWarps * 32, kDecSmem, s>>>(static_cast<const DecodeArgs*>(args_dev),
+                                                                       blk_dev, count);
+    return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
 }
 
 int launch_decode_rows(const uint8_t* payload, const uint64_t* rowoff, const uint32_t* rowbytes,

@@ -822,6 +822,9 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
     for (int f = 0; f < count; f++) nhalo += P[f].hrow + P[f].hplane;
     float* halo_all;
     A.add(&halo_all, nhalo);
+    const size_t cbsz = codebook_args_bytes();
+    char* cbargs;
+    A.add(&cbargs, (size_t)count * cbsz);
     for (int f = 0; f < count; f++) {
         CompPlan& q = P[f];
         A.add(&q.partials, 2 * (size_t)q.range_blocks);
@@ -851,7 +854,8 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
     // final states come back to the same place
     const size_t o_st = 0, o_w = align_up((size_t)count * sizeof(DevState), 256);
     const size_t o_ord = align_up(o_w + (size_t)count * wsz, 256);
-    const size_t o_out = align_up(o_ord + 8 * total_items, 256);
+    const size_t o_cb = align_up(o_ord + 8 * total_items, 256);
+    const size_t o_out = align_up(o_cb + (size_t)count * cbsz, 256);
     if ((rc = ensure_pinned(c, o_out + (size_t)count * sizeof(DevState)))) return rc;
     char* H = static_cast<char*>(c->h_batch);
     DevState* h_init = reinterpret_cast<DevState*>(H + o_st);
@@ -861,6 +865,8 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
         h_init[f].cap = out_cap[f];
         wave_args_compress(H + o_w + (size_t)f * wsz, P[f].g, data[f], P[f].codes, P[f].cpitch, P[f].halo_row,
                            P[f].halo_plane, P[f].prog, st + f, c->timeout_ns);
+        codebook_args_fill(H + o_cb + (size_t)f * cbsz, P[f].hist, st + f, P[f].len, P[f].cw, P[f].sortbuf,
+                           P[f].nodebuf);
     }
     uint32_t* h_order = reinterpret_cast<uint32_t*>(H + o_ord);
     size_t ord_at[2], ord_n[2];
@@ -892,7 +898,8 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
             cudaMemsetAsync(tickets, 0, 2 * sizeof(unsigned), s) != cudaSuccess ||
             cudaMemsetAsync(prog_all, 0, nprog * sizeof(unsigned), s) != cudaSuccess ||
             cudaMemsetAsync(halo_all, 0, nhalo * 4, s) != cudaSuccess ||
-            cudaMemsetAsync(hist_all, 0, (size_t)count * 65536 * 4, s) != cudaSuccess)
+            cudaMemsetAsync(hist_all, 0, (size_t)count * 65536 * 4, s) != cudaSuccess ||
+            cudaMemcpyAsync(cbargs, H + o_cb, (size_t)count * cbsz, cudaMemcpyHostToDevice, s) != cudaSuccess)
             return SZGB_ECUDA;
         fork_aux(c);
         for (int f = 0; f < count; f++) {
@@ -912,9 +919,15 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
         fork_aux(c);
         for (int f = 0; f < count; f++) {
             CompPlan& q = P[f];
+            if ((r = launch_histogram(q.codes, q.rows, q.rowlen, q.cpitch, q.hist, st + f, c->aux[f % kAux]))) return r;
+        }
+        join_aux(c);
+        // every field's codebook in one launch (one CTA each)
+        if ((r = launch_codebook_batch(cbargs, count, s))) return r;
+        fork_aux(c);
+        for (int f = 0; f < count; f++) {
+            CompPlan& q = P[f];
             cudaStream_t a = c->aux[f % kAux];
-            if ((r = launch_histogram(q.codes, q.rows, q.rowlen, q.cpitch, q.hist, st + f, a))) return r;
-            if ((r = launch_codebook(q.hist, st + f, q.len, q.cw, q.sortbuf, q.nodebuf, a))) return r;
             if ((r = launch_rowbits(q.codes, q.cpitch, data[f], q.rows, q.rowlen, q.len, q.rowbytes, st + f, a))) return r;
             if ((r = launch_scan_rows(q.rowbytes, q.rows, q.rowoff, q.blocksums, st + f, 1, a))) return r;
             if ((r = launch_write_meta(q.cp, q.rows, q.len, q.nodebuf, q.rowbytes, q.rowoff, out[f], st + f, a))) return r;
@@ -1029,6 +1042,12 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
     for (int f = 0; f < count; f++) nhalo += P[f].hrow + P[f].hplane;
     float* halo_all;
     A.add(&halo_all, nhalo);
+    const size_t dsz = decode_args_bytes(), tsz = tables_args_bytes();
+    char *dargs, *targs;
+    uint32_t* dblk;
+    A.add(&dargs, (size_t)count * dsz);
+    A.add(&targs, (size_t)count * tsz);
+    A.add(&dblk, (size_t)count + 1);
     for (int f = 0; f < count; f++) {
         DecPlan& q = P[f];
         A.add(&q.codes, q.rows * q.cpitch + 8);
@@ -1054,7 +1073,10 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
     }
     const size_t o_st = 0, o_w = align_up((size_t)count * sizeof(DevState), 256);
     const size_t o_ord = align_up(o_w + (size_t)count * wsz, 256);
-    const size_t o_out = align_up(o_ord + 8 * total_items, 256);
+    const size_t o_dec = align_up(o_ord + 8 * total_items, 256);
+    const size_t o_tab = align_up(o_dec + (size_t)count * dsz, 256);
+    const size_t o_blk = align_up(o_tab + (size_t)count * tsz, 256);
+    const size_t o_out = align_up(o_blk + 4 * ((size_t)count + 1), 256);
     if ((rc = ensure_pinned(c, o_out + (size_t)count * sizeof(DevState)))) return rc;
     char* Hb = static_cast<char*>(c->h_batch);
     DevState* h_init = reinterpret_cast<DevState*>(Hb + o_st);
@@ -1074,7 +1096,16 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
         if ((rc = wave_args_decompress(Hb + o_w + (size_t)f * wsz, q.g, q.codes, q.cpitch, out[f], q.halo_row,
                                        q.halo_plane, q.prog, st + f, c->timeout_ns)))
             return rc;
+        decode_args_fill(Hb + o_dec + (size_t)f * dsz, q.payload, q.rowoff, q.rowbytes, q.payload + q.H.payload, q.lut,
+                         q.dectab, q.codes, q.cpitch, out[f], q.rows, q.H.d2, st + f);
+        tables_args_fill(Hb + o_tab + (size_t)f * tsz, q.codebook, q.H.nsym, q.H.m, q.lut, q.dectab, q.lenbuf, q.symbuf,
+                         st + f);
     }
+    // the row decode of every field in one launch
+    uint32_t* h_blk = reinterpret_cast<uint32_t*>(Hb + o_blk);
+    h_blk[0] = 0;
+    for (int f = 0; f < count; f++) h_blk[f + 1] = h_blk[f] + decode_rows_blocks(P[f].rows);
+    const uint32_t dec_blocks = h_blk[count];
     uint32_t* h_order = reinterpret_cast<uint32_t*>(Hb + o_ord);
     size_t ord_at[2], ord_n[2];
     std::vector<WaveGeom> geo(count);
@@ -1102,21 +1133,22 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
             cudaMemcpyAsync(order, h_order, 8 * total_items, cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemsetAsync(tickets, 0, 2 * sizeof(unsigned), s) != cudaSuccess ||
             cudaMemsetAsync(prog_all, 0, nprog * sizeof(unsigned), s) != cudaSuccess ||
-            cudaMemsetAsync(halo_all, 0, nhalo * 4, s) != cudaSuccess)
+            cudaMemsetAsync(halo_all, 0, nhalo * 4, s) != cudaSuccess ||
+            cudaMemcpyAsync(dargs, Hb + o_dec, (size_t)count * dsz, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(dblk, h_blk, 4 * ((size_t)count + 1), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(targs, Hb + o_tab, (size_t)count * tsz, cudaMemcpyHostToDevice, s) != cudaSuccess)
             return SZGB_ECUDA;
+        // every field's decoder tables in one launch (one CTA each)
+        if ((r = launch_decode_tables_batch(targs, count, s))) return r;
         fork_aux(c);
         for (int f = 0; f < count; f++) {
             DecPlan& q = P[f];
             cudaStream_t a = c->aux[f % kAux];
-            if ((r = launch_decode_tables(q.codebook, q.H.nsym, q.H.m, q.lut, q.dectab, q.lenbuf, q.symbuf, st + f, a)))
-                return r;
             if ((r = launch_read_rowbytes(q.table, q.H.tw, q.rows, q.rowbytes, a))) return r;
             if ((r = launch_scan_rows(q.rowbytes, q.rows, q.rowoff, q.blocksums, st + f, 0, a))) return r;
-            if ((r = launch_decode_rows(q.payload, q.rowoff, q.rowbytes, q.payload + q.H.payload, q.lut, q.dectab,
-                                        q.codes, q.cpitch, out[f], q.rows, q.H.d2, st + f, a)))
-                return r;
         }
         join_aux(c);
+        if ((r = launch_decode_rows_batch(dargs, dblk, count, dec_blocks, s))) return r;
         for (int li = 0; li < 2; li++) {
             if (!ord_n[li]) continue;
             const int grid = (int)std::min<size_t>(ord_n[li], (size_t)c->sm_count);

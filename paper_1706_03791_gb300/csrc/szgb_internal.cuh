@@ -355,16 +355,19 @@ struct BitReader {
 };
 
 // decode one quantization code; long codes (> lut bits) by canonical search
+// (T = 0: no lookup table, canonical search only)
 __device__ __forceinline__ int decode_symbol(BitReader& br, const uint32_t* s_lut, int T,
                                              const uint32_t* s_tab, const uint16_t* g_sorted,
                                              int maxlen, bool& bad) {
     br.refill();
-    uint32_t e = s_lut[(uint32_t)(br.win >> (64 - T))];
-    int len = (int)(e & 0xffu);
-    if (len != 0) {
-        br.win <<= len;
-        br.nb -= len;
-        return (int)(e >> 8);
+    if (T > 0) {
+        uint32_t e = s_lut[(uint32_t)(br.win >> (64 - T))];
+        int len = (int)(e & 0xffu);
+        if (len != 0) {
+            br.win <<= len;
+            br.nb -= len;
+            return (int)(e >> 8);
+        }
     }
     // canonical search: the codes of length L are first[L] .. first[L]+count[L]-1
     uint64_t c = 0;
@@ -456,6 +459,26 @@ int launch_lattice_decompress(const uint8_t* payload, const uint64_t* rowoff, co
                               const uint8_t* stream_end, const uint32_t* lut, const uint32_t* dec_tab, int ndim,
                               int layers, uint64_t d0, uint64_t d1, uint64_t d2, int32_t* R, uint8_t* EX, float* out,
                               DevState* st, cudaStream_t s);
+// batched codebook build and decoder tables: one CTA per field, arguments
+// in a device table of *_args_bytes() records filled by *_args_fill
+size_t codebook_args_bytes();
+void codebook_args_fill(void* dst, const uint32_t* hist, DevState* st, uint8_t* len, uint64_t* cw, uint64_t* sortbuf,
+                        uint32_t* nodebuf);
+int launch_codebook_batch(const void* args_dev, int count, cudaStream_t s);
+size_t tables_args_bytes();
+void tables_args_fill(void* dst, const uint8_t* codebook, uint32_t nsym, int m, uint32_t* lut, uint32_t* dec_tab,
+                      uint8_t* lenbuf, uint32_t* symbuf, DevState* st);
+int launch_decode_tables_batch(const void* args_dev, int count, cudaStream_t s);
+// batched row decode: a table of per-field arguments (decode_args_fill, one
+// decode_args_bytes() record per field) and the prefix of per-field block
+// counts (decode_rows_blocks), count + 1 entries, in device memory
+size_t decode_args_bytes();
+uint32_t decode_rows_blocks(uint64_t rows);
+void decode_args_fill(void* dst, const uint8_t* payload, const uint64_t* rowoff, const uint32_t* rowbytes,
+                      const uint8_t* stream_end, const uint32_t* lut, const uint32_t* dec_tab, uint16_t* codes,
+                      uint64_t cpitch, float* out, uint64_t rows, uint64_t N, DevState* st);
+int launch_decode_rows_batch(const void* args_dev, const uint32_t* blk_dev, int count, uint32_t total_blocks,
+                             cudaStream_t s);
 int launch_decode_rows(const uint8_t* payload, const uint64_t* rowoff, const uint32_t* rowbytes,
                        const uint8_t* stream_end, const uint32_t* lut, const uint32_t* dec_tab, uint16_t* codes,
                        uint64_t cpitch, float* out, uint64_t rows, uint64_t N, DevState* st, cudaStream_t s);
