@@ -993,6 +993,23 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
             const unsigned kt0 = lq > 0 ? (unsigned)lq >> 5 : 0u;
             const int sl0 = (int)(kt0 % kTS) * kTE;
             const int sl1 = (sl0 == (kTS - 1) * kTE) ? 0 : sl0 + kTE;
+            // decompression: this sweep's codes and, for code 0, the stored
+            // values, read before the dependent steps so that the loads'
+            // latency overlaps them
+            int dcode[kTile];
+            float duv[kTile];
+            if constexpr (DEC) {
+#pragma unroll
+                for (int k = 0; k < kTile; k++) {
+                    const int l = lq + k;
+                    const bool act = (l >= 0) && (l < N);
+                    const bool cross = lq >= 0 && (lq & (kTW - 1)) + k >= kTW;
+                    const int ti = (cross ? sl1 : sl0) + (l & (kTW - 1));
+                    dcode[k] = act ? (int)xw[ti] : 0;
+                    duv[k] = 0.0f;
+                    if (dcode[k] == 0 && valid && act) duv[k] = out_row[l];
+                }
+            }
 #pragma unroll
             for (int k = 0; k < kTile; k++) {
                 const int l = lq + k;
@@ -1089,12 +1106,10 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
                     const float tr = trunc_value(xv, qp.e_eb);
                     code = quantize_tr(xv, pred, tr, qp, V);
                 } else {
-                    // the decode pass left the code here and, for code 0, the
-                    // unpredictable value in the output array
-                    code = act ? (int)xw[ti] : 0;
-                    float uv = 0.0f;
-                    if (code == 0 && valid && act) uv = out_row[l];
-                    V = code ? dequantize(code, pred, qp) : uv;
+                    // the decode pass left the code in the tile and, for code
+                    // 0, the unpredictable value in the output array
+                    code = dcode[k];
+                    V = code ? dequantize(code, pred, qp) : duv[k];
                 }
                 V = act ? V : 0.0f;
 #pragma unroll
