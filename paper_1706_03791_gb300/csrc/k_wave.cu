@@ -185,11 +185,13 @@ __device__ __forceinline__ void decode_rows_block(const DecodeArgs& D, uint64_t 
         const uint64_t tend = min(N, tb + 32), lim = min(N, tb + kDecRing);
         while (__any_sync(0xffffffffu, col < tend)) {
             if (col < lim) {
-                bool esc;
+                bool esc = false;
                 br.refill();
                 const uint32_t e = s_multi[(uint32_t)(br.win >> (64 - kMultiBits))];
                 const uint32_t n = e & 3u;
-                if (n != 0 && col + n <= lim) {
+                if (n != 0 && col + n > lim && lim < N) {
+                    // ahead of the warp by almost two tiles: wait for the next store
+                } else if (n != 0 && col + n <= lim) {
                     const uint32_t used = (e >> 2) & 15u;
                     br.win <<= used;
                     br.nb -= (int)used;
@@ -211,7 +213,7 @@ __device__ __forceinline__ void decode_rows_block(const DecodeArgs& D, uint64_t 
                 } else {
                     // one code, by the canonical search: the first code is
                     // longer than the table, or a multi-code step would pass
-                    // the ring or the row end
+                    // the row end
                     const int code = decode_symbol(br, nullptr, 0, s_tab, g_sorted, maxlen, bad);
                     myring[col & (kDecRing - 1)] = (uint16_t)code;
                     col += 1;
