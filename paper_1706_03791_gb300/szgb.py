@@ -257,10 +257,8 @@ class Context:
         L = lib()
         if _is_torch(stream):
             import torch
-            hdr = stream[:128].cpu().numpy()
-            info = stream_info_header(hdr)
-            n = int(np.prod(info["shape"]))
-            if out is None:
+            if out is None:  # the shape is in the header (one small device-to-host read)
+                info = stream_info_header(stream[:128].cpu().numpy())
                 out = torch.empty(info["shape"], dtype=torch.float32, device=stream.device)
             rc = L.szgb_decompress(self._h, C.c_void_p(stream.data_ptr()), stream.numel(), 1,
                                    C.c_void_p(out.data_ptr()), out.numel(), 1)

@@ -90,3 +90,26 @@ def test_batch_error_reporting(ctx):
     # the context stays usable
     s, _ = ctx.compress_batch([good], dict(eb_rel=1e-4, m=8))
     assert s[0].numel() > 128
+
+
+def test_single_field_both_paths(ctx, szo):
+    """A single device field runs the direct path (graphs off) or the one-field
+    batched path replayed from a graph (graphs on, the default): both give the
+    oracle's stream and reconstruction, on the first call and on replays."""
+    import torch
+    cases = [MIX[1], MIX[2], MIX[3], MIX[5]]
+    try:
+        for graphs in (False, True):
+            ctx.set_graphs(graphs)
+            for g, kw in cases:
+                x = np.ascontiguousarray(g())
+                sref, rec, _ = szo.compress(x, want_aux=True, **kw)
+                xd = torch.from_numpy(x).cuda()
+                for _ in range(2):
+                    s, st = ctx.compress(xd, **kw)
+                    assert np.array_equal(s.cpu().numpy(), sref)
+                    assert st.stream_bytes == sref.size
+                    y = ctx.decompress(s)
+                    assert np.array_equal(_bits(y.cpu().numpy()), _bits(rec))
+    finally:
+        ctx.set_graphs(True)
