@@ -414,6 +414,55 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_rd(args):
+    """Rate-distortion of the 3D field: bit-rate, compression factor and the
+    quality metrics (Sec. II) for relative bounds 1e-2 .. 1e-6, with the
+    compress and decompress throughput at each bound."""
+    import torch
+    from paper_1706_03791_gb300 import build as B
+    B.build()
+    from paper_1706_03791_gb300 import szgb
+    from synthetic import fields
+    x_np = fields.workload_3d()
+    x = torch.from_numpy(x_np).cuda()
+    nbytes = x_np.nbytes
+    ctx = szgb.Context(0)
+    y = torch.empty_like(x)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    pts = []
+    for eb in (1e-2, 1e-3, 1e-4, 1e-5, 1e-6):
+        kw = dict(eb_rel=eb, layers=args.layers, m=0)
+        sbuf = torch.empty(szgb.compress_bound(x_np.shape, **kw), dtype=torch.uint8, device="cuda")
+        tc, td = [], []
+        for i in range(3 + 5):
+            flush.fill_(1)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            s, st = ctx.compress(x, out=sbuf, **kw)
+            e1.record()
+            ctx.decompress(s, out=y)
+            e2.record()
+            e2.synchronize()
+            if i >= 3:
+                tc.append(e0.elapsed_time(e1))
+                td.append(e1.elapsed_time(e2))
+        q = ctx.quality(x, y)
+        assert q["max_abs_err"] < float(st.eb_f), "error bound violated"
+        n = x_np.size
+        pts.append({"eb_rel": eb, "m": int(st.m), "bit_rate": s.numel() * 8.0 / n,
+                    "compression_factor": nbytes / s.numel(), "psnr_db": q["psnr"], "nrmse": q["nrmse"],
+                    "pearson": q["pearson"], "max_error_over_eb": q["max_abs_err"] / float(st.eb_f),
+                    "unpredictable_fraction": int(st.n_unpred) / n,
+                    "compress_gbs": nbytes / (sorted(tc)[len(tc) // 2] / 1e3) / 1e9,
+                    "decompress_gbs": nbytes / (sorted(td)[len(td) // 2] / 1e3) / 1e9})
+    ref = next(p for p in pts if p["eb_rel"] == 1e-4)
+    print(json.dumps({"metric": "rate-distortion of the 3D 100x500x500 field over rel eb (bits/value at 1e-4)",
+                      "value": ref["bit_rate"], "unit": "bits/value", "higher_is_better": False, "n_gpus": 1,
+                      "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "rd-3d-blobs-100x500x500-fp32-n%d-adaptive-m" % args.layers},
+                      "points": pts}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -428,9 +477,10 @@ def main():
                          "fully parallel lattice variant, reported beside it")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
     ap.add_argument("--duration", type=float, default=30.0, help="serve: seconds of arrivals")
-    ap.add_argument("--workload", default="3d", choices=["3d", "climate79", "uneven512", "serve"],
+    ap.add_argument("--workload", default="3d", choices=["3d", "climate79", "uneven512", "serve", "rd"],
                     help="3d: the single 100x500x500 field (default); climate79 / uneven512: "
-                         "batched many-field workloads, batched+graph vs one field per call")
+                         "batched many-field workloads, batched+graph vs one field per call; "
+                         "rd: rate-distortion sweep of the 3d field over the relative bound")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -438,6 +488,8 @@ def main():
         return run_reference(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "rd":
+        return run_rd(args)
     if args.workload != "3d":
         return run_batch_workload(args)
 
@@ -493,6 +545,7 @@ def main():
     maxerr = float((yv.double() - x.double()).abs().max())
     assert maxerr < st0.eb_f, "error bound violated"
     stream_bytes = int(s0.numel())
+    qual = ctx.quality(x, yv)  # Sec. II, Metrics 1-3, computed on the device
 
     # per-kernel (phase) device times, CUDA events on the library's stream,
     # over a separate profiled pass of the same steps
@@ -585,6 +638,8 @@ def main():
         "decompress_gbs": {"p50": pct(dec_gbs, 50), "p99": pct(dec_gbs, 1)},
         "compression_factor": nbytes / stream_bytes, "bits_per_value": bits_pp,
         "n_unpred": int(st0.n_unpred), "max_error_over_eb": maxerr / float(st0.eb_f),
+        "quality": {"psnr_db": qual["psnr"], "nrmse": qual["nrmse"], "rmse": qual["rmse"],
+                    "pearson": qual["pearson"]},
         "phase_ms": phase_ms,
         "roofline": roof,
         "cpu_baseline": cpu,

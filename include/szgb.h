@@ -208,6 +208,29 @@ int szgb_tune_load(szgb_ctx *ctx, const char *path);
 /* Capture batches in CUDA graphs (1, the default) or launch them directly (0). */
 int szgb_set_graphs(szgb_ctx *ctx, int on);
 
+/* ---- reconstruction quality (Sec. II, Metrics 1-3) ----------------------
+ * One pass over a field x and its reconstruction y (both n float32 values in
+ * device memory, any alignment), on the context's stream, in float64:
+ *   max_abs_err = max |x_i - y_i|              (Metric 1, absolute error)
+ *   max_rel_err = max_abs_err / R_X,  R_X = x_max - x_min (value range of x)
+ *   rmse = sqrt(sum (x_i - y_i)^2 / n), nrmse = rmse / R_X,
+ *   psnr = 20 log10(R_X / rmse)                 (Metric 2)
+ *   pearson = cov(x, y) / (sigma_x sigma_y)     (Metric 3; population moments)
+ * Undefined cases: R_X = 0 gives NaN for nrmse / max_rel_err and for psnr
+ * unless rmse = 0 (psnr = +inf when the reconstruction is exact); a zero
+ * standard deviation gives NaN for pearson.  Inputs are expected finite.
+ * The result is deterministic (a fixed reduction order).  Blocks until done.
+ * Returns SZGB_OK, SZGB_EINVAL (null pointer, n = 0), SZGB_ENOMEM, SZGB_ECUDA. */
+typedef struct szgb_quality {
+    double max_abs_err, max_rel_err;
+    double rmse, nrmse, psnr;
+    double pearson;
+    double x_min, x_max;
+    uint64_t n;
+} szgb_quality;
+int szgb_quality_dev(szgb_ctx *ctx, const float *x_dev, const float *y_dev, size_t n,
+                     szgb_quality *out);
+
 /* ---- serving loop ------------------------------------------------------
  * Requests are taken as they arrive and run by worker threads, each with its
  * own context and stream, so that batches overlap on the device.  A worker

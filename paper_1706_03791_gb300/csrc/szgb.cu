@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <vector>
 
@@ -1450,6 +1451,40 @@ int szgb_set_graphs(szgb_ctx* c, int on) {
         drop_graph(c->g_comp);
         drop_graph(c->g_dec);
     }
+    return SZGB_OK;
+}
+
+int szgb_quality_dev(szgb_ctx* c, const float* x_dev, const float* y_dev, size_t n, szgb_quality* out) {
+    if (!c || !x_dev || !y_dev || !out || n == 0) return SZGB_EINVAL;
+    if (cudaSetDevice(c->device) != cudaSuccess) return SZGB_ECUDA;
+    const int blocks = quality_blocks(n, c->sm_count);
+    const size_t need = quality_scratch_bytes(blocks);
+    int rc;
+    if ((rc = ensure_scratch(c, need))) return rc;
+    if ((rc = ensure_pinned(c, 16 * sizeof(double)))) return rc;
+    cudaStream_t s = c->stream;
+    // the counter word at the end of the scratch starts at 0 (the kernel leaves it at 0)
+    char* scratch = static_cast<char*>(c->scratch);
+    const size_t counter_off = (size_t)(blocks + 1) * 9 * sizeof(double);
+    if (cudaMemsetAsync(scratch + counter_off, 0, sizeof(unsigned), s) != cudaSuccess) return SZGB_ECUDA;
+    double* h = static_cast<double*>(c->h_batch);
+    if ((rc = launch_quality(x_dev, y_dev, n, blocks, scratch, h, s))) return rc;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SZGB_ECUDA;
+    const double se = h[0], sx = h[1], sy = h[2], sxx = h[3], syy = h[4], sxy = h[5];
+    const double nn = (double)n;
+    out->n = n;
+    out->x_min = h[7];
+    out->x_max = h[8];
+    out->max_abs_err = h[6];
+    const double rx = h[8] - h[7];
+    out->rmse = std::sqrt(se / nn);
+    out->max_rel_err = rx > 0 ? out->max_abs_err / rx : std::nan("");
+    out->nrmse = rx > 0 ? out->rmse / rx : std::nan("");
+    out->psnr = out->rmse == 0.0 ? INFINITY : (rx > 0 ? 20.0 * std::log10(rx / out->rmse) : std::nan(""));
+    // moments of x - x_0 and y - x_0 (the shift cancels)
+    const double mx = sx / nn, my = sy / nn;
+    const double vx = sxx / nn - mx * mx, vy = syy / nn - my * my, cv = sxy / nn - mx * my;
+    out->pearson = (vx > 0 && vy > 0) ? cv / std::sqrt(vx * vy) : std::nan("");
     return SZGB_OK;
 }
 

@@ -459,6 +459,11 @@ int launch_lattice_decompress(const uint8_t* payload, const uint64_t* rowoff, co
                               const uint8_t* stream_end, const uint32_t* lut, const uint32_t* dec_tab, int ndim,
                               int layers, uint64_t d0, uint64_t d1, uint64_t d2, int32_t* R, uint8_t* EX, float* out,
                               DevState* st, cudaStream_t s);
+// reconstruction quality: per-block partial sums and their total (k_quality.cu)
+size_t quality_scratch_bytes(int blocks);
+int quality_blocks(uint64_t n, int sm_count);
+int launch_quality(const float* x, const float* y, uint64_t n, int blocks, void* scratch, double* host_out,
+                   cudaStream_t s);
 // batched codebook build and decoder tables: one CTA per field, arguments
 // in a device table of *_args_bytes() records filled by *_args_fill
 size_t codebook_args_bytes();

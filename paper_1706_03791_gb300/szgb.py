@@ -43,6 +43,15 @@ class Stats(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class Quality(C.Structure):
+    _fields_ = [("max_abs_err", C.c_double), ("max_rel_err", C.c_double), ("rmse", C.c_double),
+                ("nrmse", C.c_double), ("psnr", C.c_double), ("pearson", C.c_double), ("x_min", C.c_double),
+                ("x_max", C.c_double), ("n", C.c_uint64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 OP_COMPRESS, OP_DECOMPRESS = 0, 1
 
 
@@ -86,6 +95,7 @@ def lib():
         L.szgb_decompress_batch.argtypes = [vp, C.c_int, C.POINTER(vp), C.POINTER(sz), C.POINTER(vp),
                                             C.POINTER(sz), C.POINTER(C.c_int)]
         L.szgb_set_graphs.argtypes = [vp, C.c_int]
+        L.szgb_quality_dev.argtypes = [vp, vp, vp, sz, C.POINTER(Quality)]
         L.szgb_autotune.argtypes = [vp, vp, C.POINTER(Params), C.c_int, C.POINTER(C.c_int),
                                     C.POINTER(C.c_int), C.POINTER(C.c_double)]
         L.szgb_autotune_batch.argtypes = [vp, C.c_int, C.POINTER(vp), C.POINTER(Params), C.c_int,
@@ -115,7 +125,8 @@ EXPORTS = ["szgb_create", "szgb_destroy", "szgb_set_stream", "szgb_compress_boun
            "szgb_num_phases", "szgb_phase_name", "szgb_phase_times", "szgb_strerror",
            "szgb_decompress_noalloc", "szgb_compress_batch", "szgb_decompress_batch", "szgb_set_graphs",
            "szgb_server_create", "szgb_submit", "szgb_poll", "szgb_wait", "szgb_server_stats",
-           "szgb_server_destroy", "szgb_autotune", "szgb_autotune_batch", "szgb_tune_save", "szgb_tune_load"]
+           "szgb_server_destroy", "szgb_autotune", "szgb_autotune_batch", "szgb_tune_save", "szgb_tune_load",
+           "szgb_quality_dev"]
 
 
 VARIANT_EXACT, VARIANT_LATTICE = 0, 1
@@ -315,6 +326,20 @@ class Context:
     # -- batches -------------------------------------------------------------
     def set_graphs(self, on: bool):
         lib().szgb_set_graphs(self._h, 1 if on else 0)
+
+    def quality(self, x, y) -> dict:
+        """Reconstruction quality of y against x (CUDA float32 tensors of one
+        size): maximum absolute / range-relative error, RMSE, NRMSE, PSNR and
+        Pearson's coefficient (Sec. II, Metrics 1-3), computed on the device."""
+        import torch
+        assert x.is_cuda and y.is_cuda and x.dtype == torch.float32 and y.dtype == torch.float32
+        assert x.is_contiguous() and y.is_contiguous() and x.numel() == y.numel()
+        q = Quality()
+        rc = lib().szgb_quality_dev(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), x.numel(),
+                                    C.byref(q))
+        if rc:
+            raise SzgbError(rc, "szgb_quality_dev")
+        return q.as_dict()
 
     def compress_batch(self, xs, params, outs=None):
         """Compress the CUDA float32 tensors `xs` in one batched call.
