@@ -216,8 +216,12 @@ int launch_adapt(const float* x, const CallParams& cp, DevState* st, cudaStream_
     int blocks = (int)((S + 255) / 256);
     if (blocks > 1024) blocks = 1024;
     if (blocks < 1) blocks = 1;
-    if (cp.layers == 1) k_adapt<1><<<blocks, 256, 0, s>>>(x, cp, st);
-    else k_adapt<2><<<blocks, 256, 0, s>>>(x, cp, st);
+    switch (cp.layers) {
+        case 1: k_adapt<1><<<blocks, 256, 0, s>>>(x, cp, st); break;
+        case 2: k_adapt<2><<<blocks, 256, 0, s>>>(x, cp, st); break;
+        case 3: k_adapt<3><<<blocks, 256, 0, s>>>(x, cp, st); break;
+        default: k_adapt<4><<<blocks, 256, 0, s>>>(x, cp, st); break;
+    }
     return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
 }
 

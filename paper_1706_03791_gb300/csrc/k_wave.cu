@@ -1022,14 +1022,18 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
                 // ---- new neighbour values at column l (shuffles first: they
                 // read the values of the previous step)
                 float nR[NL + 1], nP[NL + 1], nQ[NL + 1][NL + 1];
+                // row t - b at column l is row (t - 1) - (b - 1) of the lane above,
+                // which held column l in the previous step
                 nR[1] = __shfl_up_sync(0xffffffffu, oV[1], 1);
-                if (NL >= 2) nR[2] = __shfl_up_sync(0xffffffffu, Rr[1][0], 1);
+#pragma unroll
+                for (int b = 2; b <= NL; b++) nR[b] = __shfl_up_sync(0xffffffffu, Rr[b - 1][0], 1);
                 if (ND == 3) {
 #pragma unroll
                     for (int a = 1; a <= NL; a++) {
                         nP[a] = (k == 0) ? pr[a].x : (k == 1) ? pr[a].y : (k == 2) ? pr[a].z : pr[a].w;
                         nQ[a][1] = __shfl_up_sync(0xffffffffu, Pp[a][0], 1);
-                        if (NL >= 2) nQ[a][2] = __shfl_up_sync(0xffffffffu, Qq[a][1][0], 1);
+#pragma unroll
+                        for (int b = 2; b <= NL; b++) nQ[a][b] = __shfl_up_sync(0xffffffffu, Qq[a][b - 1][0], 1);
                     }
                 }
                 // lanes next to the top of the block read the rows above
@@ -1169,9 +1173,13 @@ __global__ void __launch_bounds__((kMaxWaveWarps + 4) * 32, 1)
         const uint2 o = order[t];
         const WaveArgs& A = F[o.x];
         const int nd = A.g.ndim;
-        if (nd == 3) wave_item<3, NL, DEC, false>(A, (int)o.y, smem_raw, S);
-        else if (nd == 2) wave_item<2, NL, DEC, false>(A, (int)o.y, smem_raw, S);
-        else wave_item<1, NL, DEC, false>(A, (int)o.y, smem_raw, S);
+        if (nd == 3) {
+            if constexpr (NL <= kMaxLayers3D) wave_item<3, NL, DEC, false>(A, (int)o.y, smem_raw, S);
+        } else if (nd == 2) {
+            wave_item<2, NL, DEC, false>(A, (int)o.y, smem_raw, S);
+        } else {
+            wave_item<1, NL, DEC, false>(A, (int)o.y, smem_raw, S);
+        }
         __syncthreads();
     }
 }
@@ -1269,8 +1277,20 @@ static int launch_t(const WaveArgs& a, cudaStream_t s) {
 template <bool DEC, bool TR>
 static int launch_nd(const WaveArgs& a, int layers, cudaStream_t s) {
     if (a.g.ndim == 3) return layers == 1 ? launch_t<3, 1, DEC, TR>(a, s) : launch_t<3, 2, DEC, TR>(a, s);
-    if (a.g.ndim == 2) return layers == 1 ? launch_t<2, 1, DEC, TR>(a, s) : launch_t<2, 2, DEC, TR>(a, s);
-    return layers == 1 ? launch_t<1, 1, DEC, TR>(a, s) : launch_t<1, 2, DEC, TR>(a, s);
+    if (a.g.ndim == 2) {
+        switch (layers) {
+            case 1: return launch_t<2, 1, DEC, TR>(a, s);
+            case 2: return launch_t<2, 2, DEC, TR>(a, s);
+            case 3: return launch_t<2, 3, DEC, TR>(a, s);
+            default: return launch_t<2, 4, DEC, TR>(a, s);
+        }
+    }
+    switch (layers) {
+        case 1: return launch_t<1, 1, DEC, TR>(a, s);
+        case 2: return launch_t<1, 2, DEC, TR>(a, s);
+        case 3: return launch_t<1, 3, DEC, TR>(a, s);
+        default: return launch_t<1, 4, DEC, TR>(a, s);
+    }
 }
 template <bool DEC>
 static int launch_any(const WaveArgs& a, int layers, cudaStream_t s) {
@@ -1348,32 +1368,31 @@ int wave_args_decompress(void* dst, const WaveGeom& g, const uint16_t* codes, ui
     return a.tma_x ? 0 : SZGB_ECUDA;
 }
 
+template <int NL, bool DEC>
+static int launch_batch_t(const WaveArgs* F, const uint2* order, unsigned total, unsigned* ticket_dev, size_t smem,
+                          int grid, int block, cudaStream_t s) {
+    if (smem_limit_once<k_wave_batch<NL, DEC>>(smem)) return SZGB_ECUDA;
+    k_wave_batch<NL, DEC><<<grid, block, smem, s>>>(F, order, total, ticket_dev);
+    return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
+}
+
 int launch_wave_batch(const void* args_dev, const void* order_dev, unsigned total, unsigned* ticket_dev, int layers,
                       bool decompress, size_t smem, int grid, cudaStream_t s) {
     const WaveArgs* F = static_cast<const WaveArgs*>(args_dev);
     const uint2* order = static_cast<const uint2*>(order_dev);
     const int block = (kMaxWaveWarps + 4) * 32;
     if (grid < 1) grid = 1;
-    cudaError_t e;
-    if (!decompress) {
-        if (layers == 1) {
-            if (smem_limit_once<k_wave_batch<1, false>>(smem)) return SZGB_ECUDA;
-            k_wave_batch<1, false><<<grid, block, smem, s>>>(F, order, total, ticket_dev);
-        } else {
-            if (smem_limit_once<k_wave_batch<2, false>>(smem)) return SZGB_ECUDA;
-            k_wave_batch<2, false><<<grid, block, smem, s>>>(F, order, total, ticket_dev);
-        }
-    } else {
-        if (layers == 1) {
-            if (smem_limit_once<k_wave_batch<1, true>>(smem)) return SZGB_ECUDA;
-            k_wave_batch<1, true><<<grid, block, smem, s>>>(F, order, total, ticket_dev);
-        } else {
-            if (smem_limit_once<k_wave_batch<2, true>>(smem)) return SZGB_ECUDA;
-            k_wave_batch<2, true><<<grid, block, smem, s>>>(F, order, total, ticket_dev);
-        }
+    switch ((decompress ? 4 : 0) + layers - 1) {
+        case 0: return launch_batch_t<1, false>(F, order, total, ticket_dev, smem, grid, block, s);
+        case 1: return launch_batch_t<2, false>(F, order, total, ticket_dev, smem, grid, block, s);
+        case 2: return launch_batch_t<3, false>(F, order, total, ticket_dev, smem, grid, block, s);
+        case 3: return launch_batch_t<4, false>(F, order, total, ticket_dev, smem, grid, block, s);
+        case 4: return launch_batch_t<1, true>(F, order, total, ticket_dev, smem, grid, block, s);
+        case 5: return launch_batch_t<2, true>(F, order, total, ticket_dev, smem, grid, block, s);
+        case 6: return launch_batch_t<3, true>(F, order, total, ticket_dev, smem, grid, block, s);
+        case 7: return launch_batch_t<4, true>(F, order, total, ticket_dev, smem, grid, block, s);
+        default: return SZGB_EUNSUPPORTED;
     }
-    e = cudaGetLastError();
-    return e == cudaSuccess ? 0 : SZGB_ECUDA;
 }
 
 }  // namespace szgb

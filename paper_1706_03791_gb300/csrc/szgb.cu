@@ -156,7 +156,10 @@ int check_params(const szgb_params* p, CallParams* cp) {
     cp->theta = p->theta;
     if (p->variant != SZGB_VARIANT_EXACT && p->variant != SZGB_VARIANT_LATTICE) return SZGB_EINVAL;
     cp->variant = p->variant;
-    return p->layers > kMaxLayers ? SZGB_EUNSUPPORTED : SZGB_OK;
+    // the lattice variant is built for n <= 2
+    if (!layers_supported(p->ndim, p->layers) || (p->variant == SZGB_VARIANT_LATTICE && p->layers > 2))
+        return SZGB_EUNSUPPORTED;
+    return SZGB_OK;
 }
 
 // Shape class of a field for the autotuner: dimension, layers and the bit
@@ -512,7 +515,8 @@ int decompress_impl(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_dev
     Header H;
     int rc = parse_header(hbuf, in_len, &H);
     if (rc) return rc;
-    if (H.layers > kMaxLayers) return SZGB_EUNSUPPORTED;
+    if (!layers_supported(H.ndim, H.layers) || (H.variant == SZGB_VARIANT_LATTICE && H.layers > 2))
+        return SZGB_EUNSUPPORTED;
     const uint64_t N = H.d0 * H.d1 * H.d2;
     if (out_cap_elems < N) return SZGB_EINVAL;
     if (one_field_batched(c) && H.variant == SZGB_VARIANT_EXACT && in_on_device && out_on_device &&
@@ -809,8 +813,8 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
     int rc = ensure_aux(c);
     if (rc) return rc;
     std::vector<CompPlan> P(count);
-    std::vector<int> nitems(count), by_layers[2];
-    size_t smem[2] = {0, 0};
+    std::vector<int> nitems(count), by_layers[kMaxLayers];
+    size_t smem[kMaxLayers] = {};
     for (int f = 0; f < count; f++) {
         CompPlan& q = P[f];
         if (!data[f] || !out[f] || ((uintptr_t)data[f] % 16) || ((uintptr_t)out[f] % 4)) return SZGB_EINVAL;
@@ -839,7 +843,7 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
     char* wargs;
     Arena A;
     A.add(&st, count);
-    A.add(&tickets, 2);
+    A.add(&tickets, kMaxLayers);
     A.add(&prog_all, nprog);
     A.add(&hist_all, (size_t)count * 65536);
     A.add(&wargs, (size_t)count * wsz);
@@ -895,13 +899,14 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
                            P[f].nodebuf);
     }
     uint32_t* h_order = reinterpret_cast<uint32_t*>(H + o_ord);
-    size_t ord_at[2], ord_n[2];
+    size_t ord_at[kMaxLayers], ord_n[kMaxLayers];
     std::vector<WaveGeom> geo(count);
     for (int f = 0; f < count; f++) geo[f] = P[f].g;
-    ord_at[0] = 0;
-    ord_n[0] = build_order(by_layers[0], geo, h_order);
-    ord_at[1] = ord_n[0];
-    ord_n[1] = build_order(by_layers[1], geo, h_order + 2 * ord_n[0]);
+    for (int li = 0, at = 0; li < kMaxLayers; li++) {  // one launch per layer count present
+        ord_at[li] = at;
+        ord_n[li] = build_order(by_layers[li], geo, h_order + 2 * at);
+        at += (int)ord_n[li];
+    }
 
     std::vector<uint64_t> key;
     key.push_back((uint64_t)count);
@@ -921,7 +926,7 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
         if (cudaMemcpyAsync(st, h_init, (size_t)count * sizeof(DevState), cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemcpyAsync(wargs, H + o_w, (size_t)count * wsz, cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemcpyAsync(order, h_order, 8 * total_items, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemsetAsync(tickets, 0, 2 * sizeof(unsigned), s) != cudaSuccess ||
+            cudaMemsetAsync(tickets, 0, kMaxLayers * sizeof(unsigned), s) != cudaSuccess ||
             cudaMemsetAsync(prog_all, 0, nprog * sizeof(unsigned), s) != cudaSuccess ||
             cudaMemsetAsync(halo_all, 0, nhalo * 4, s) != cudaSuccess ||
             cudaMemsetAsync(hist_all, 0, (size_t)count * 65536 * 4, s) != cudaSuccess ||
@@ -935,7 +940,7 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
             if (q.cp.m_user == 0 && (r = launch_adapt(data[f], q.cp, st + f, a))) return r;
         }
         join_aux(c);
-        for (int li = 0; li < 2; li++) {
+        for (int li = 0; li < kMaxLayers; li++) {
             if (!ord_n[li]) continue;
             const int grid = (int)std::min<size_t>(ord_n[li], (size_t)c->sm_count);
             if ((r = launch_wave_batch(wargs, order + 2 * ord_at[li], (unsigned)ord_n[li], tickets + li, li + 1, false,
@@ -1028,12 +1033,12 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
     }
     if (!(host_hdr && count == 1) && cudaStreamSynchronize(s) != cudaSuccess) return SZGB_ECUDA;
     std::vector<DecPlan> P(count);
-    std::vector<int> nitems(count), by_layers[2];
-    size_t smem[2] = {0, 0};
+    std::vector<int> nitems(count), by_layers[kMaxLayers];
+    size_t smem[kMaxLayers] = {};
     for (int f = 0; f < count; f++) {
         DecPlan& q = P[f];
         if ((rc = parse_header(static_cast<uint8_t*>(c->h_batch) + (size_t)f * kHeaderBytes, in_len[f], &q.H))) return rc;
-        if (q.H.layers > kMaxLayers || q.H.variant != SZGB_VARIANT_EXACT) return SZGB_EUNSUPPORTED;
+        if (!layers_supported(q.H.ndim, q.H.layers) || q.H.variant != SZGB_VARIANT_EXACT) return SZGB_EUNSUPPORTED;
         q.n = q.H.d0 * q.H.d1 * q.H.d2;
         if (out_cap[f] < q.n) return SZGB_EINVAL;
         q.rows = q.H.nchunks;
@@ -1064,7 +1069,7 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
     char* wargs;
     Arena A;
     A.add(&st, count);
-    A.add(&tickets, 2);
+    A.add(&tickets, kMaxLayers);
     A.add(&prog_all, nprog);
     A.add(&wargs, (size_t)count * wsz);
     A.add(&order, 2 * total_items);
@@ -1137,13 +1142,14 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
     for (int f = 0; f < count; f++) h_blk[f + 1] = h_blk[f] + decode_rows_blocks(P[f].rows);
     const uint32_t dec_blocks = h_blk[count];
     uint32_t* h_order = reinterpret_cast<uint32_t*>(Hb + o_ord);
-    size_t ord_at[2], ord_n[2];
+    size_t ord_at[kMaxLayers], ord_n[kMaxLayers];
     std::vector<WaveGeom> geo(count);
     for (int f = 0; f < count; f++) geo[f] = P[f].g;
-    ord_at[0] = 0;
-    ord_n[0] = build_order(by_layers[0], geo, h_order);
-    ord_at[1] = ord_n[0];
-    ord_n[1] = build_order(by_layers[1], geo, h_order + 2 * ord_n[0]);
+    for (int li = 0, at = 0; li < kMaxLayers; li++) {  // one launch per layer count present
+        ord_at[li] = at;
+        ord_n[li] = build_order(by_layers[li], geo, h_order + 2 * at);
+        at += (int)ord_n[li];
+    }
     std::vector<uint64_t> key;
     key.push_back((uint64_t)count);
     key.push_back((uint64_t)(uintptr_t)c->scratch);
@@ -1161,7 +1167,7 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
         if (cudaMemcpyAsync(st, h_init, (size_t)count * sizeof(DevState), cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemcpyAsync(wargs, Hb + o_w, (size_t)count * wsz, cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemcpyAsync(order, h_order, 8 * total_items, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemsetAsync(tickets, 0, 2 * sizeof(unsigned), s) != cudaSuccess ||
+            cudaMemsetAsync(tickets, 0, kMaxLayers * sizeof(unsigned), s) != cudaSuccess ||
             cudaMemsetAsync(prog_all, 0, nprog * sizeof(unsigned), s) != cudaSuccess ||
             cudaMemsetAsync(halo_all, 0, nhalo * 4, s) != cudaSuccess ||
             cudaMemcpyAsync(dargs, Hb + o_dec, (size_t)count * dsz, cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -1179,7 +1185,7 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
         }
         join_aux(c);
         if ((r = launch_decode_rows_batch(dargs, dblk, count, dec_blocks, s))) return r;
-        for (int li = 0; li < 2; li++) {
+        for (int li = 0; li < kMaxLayers; li++) {
             if (!ord_n[li]) continue;
             const int grid = (int)std::min<size_t>(ord_n[li], (size_t)c->sm_count);
             if ((r = launch_wave_batch(wargs, order + 2 * ord_at[li], (unsigned)ord_n[li], tickets + li, li + 1, true,

@@ -16,7 +16,11 @@ namespace szgb {
 
 constexpr int kHeaderBytes = 128;
 constexpr int kTile = 4;           // columns per sweep and lane (one float4)
-constexpr int kMaxLayers = 2;      // n supported by the GPU kernels
+constexpr int kMaxLayers = 4;      // n supported by the GPU kernels in 1D and 2D
+constexpr int kMaxLayers3D = 2;    // and in 3D (a 3D lane keeps (n+1)^3 - 1 neighbour values)
+__host__ __device__ inline bool layers_supported(int ndim, int layers) {
+    return layers >= 1 && layers <= (ndim == 3 ? kMaxLayers3D : kMaxLayers);
+}
 constexpr int kLutBits = 11;       // decoder lookup-table index bits
 constexpr int kMaxWaveWarps = 8;   // compute warps per wavefront CTA (plus one halo warp)
 constexpr uint32_t kProgAbort = 0x7fffffffu;

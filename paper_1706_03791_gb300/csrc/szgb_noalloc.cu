@@ -92,7 +92,7 @@ extern "C" int szgb_decompress_noalloc(const uint8_t* in_dev, size_t in_len, flo
     if (nsym < 1 || nsym > (1u << m) || h[12] < 1 || h[12] > 64) return SZGB_ECORRUPT;
     const uint64_t cb = (3ull * nsym + 3) & ~3ull, tb = ((uint64_t)tw * rows + 3) & ~3ull;
     if (total != (uint64_t)kHeaderBytes + cb + tb + payload_bytes || total > in_len) return SZGB_ECORRUPT;
-    if (layers > kMaxLayers || h[113] != 0) return SZGB_EUNSUPPORTED;  // the paper's method only
+    if (!layers_supported(ndim, layers) || h[113] != 0) return SZGB_EUNSUPPORTED;  // the paper's method only
 
     // wavefront geometry (the same schedule as szgb_decompress; any valid
     // schedule gives the same values)

@@ -36,6 +36,8 @@ MIX = [
     (lambda: fields.grf2d(97, 140, seed=66), dict(eb_rel=1e-4, layers=2, m=0)),
     (lambda: fields.blobs3d(21, 45, 36, seed=67, nblobs=6), dict(eb_rel=1e-5, layers=2, m=0)),
     (lambda: fields.grf2d(700, 130, seed=68), dict(eb_rel=1e-3, m=0)),
+    (lambda: fields.grf2d(120, 90, seed=69), dict(eb_rel=1e-4, layers=3, m=0)),
+    (lambda: fields.grf2d(1, 500, seed=71).reshape(500), dict(eb_rel=1e-3, layers=4, m=8)),
 ]
 
 

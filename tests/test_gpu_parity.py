@@ -65,6 +65,12 @@ CASES = [
     ("3d-both", lambda: fields.blobs3d(9, 33, 20, seed=42, nblobs=4), dict(mode=2, eb_abs=1e-3, eb_rel=1e-5, m=12)),
     ("2d-m16", lambda: fields.grf2d(80, 90, seed=43), dict(eb_rel=1e-7, m=16)),
     ("2d-m2", lambda: fields.grf2d(50, 64, seed=44), dict(eb_rel=1e-2, m=2)),
+    # n = 3, 4 (1D and 2D)
+    ("1d-n3", lambda: fields.grf2d(1, 777, seed=47).reshape(777), dict(eb_rel=1e-4, layers=3, m=0)),
+    ("1d-n4", lambda: fields.grf2d(1, 1030, seed=48).reshape(1030), dict(eb_rel=1e-3, layers=4, m=8)),
+    ("2d-n3", lambda: fields.grf2d(97, 140, seed=49), dict(eb_rel=1e-4, layers=3, m=0)),
+    ("2d-n3-multicta", lambda: fields.grf2d(700, 130, seed=50), dict(eb_rel=1e-3, layers=3, m=0)),
+    ("2d-n4-ragged", lambda: fields.grf2d(290, 61, seed=51), dict(eb_rel=1e-4, layers=4, m=10)),
 ]
 
 
@@ -133,8 +139,9 @@ def test_errors(ctx, szo):
     with pytest.raises(szgb.SzgbError) as e:
         ctx.compress(x, out=small, eb_rel=1e-3, m=8)
     assert e.value.code == szgb.ETRUNC
-    with pytest.raises(szgb.SzgbError) as e:
-        ctx.compress(x, eb_rel=1e-3, m=8, layers=3)
+    x3 = fields.blobs3d(6, 20, 24, seed=52, nblobs=3)
+    with pytest.raises(szgb.SzgbError) as e:  # 3D keeps n <= 2 on the GPU
+        ctx.compress(x3, eb_rel=1e-3, m=8, layers=3)
     assert e.value.code == szgb.EUNSUPPORTED
     # the context stays usable after errors
     _check(ctx, szo, x, eb_rel=1e-3, m=8)

@@ -1,6 +1,7 @@
 """Pins of the oracle's n-layer predictor (Sec. III, Eq. predmodel, Table 1,
 Theorem 1) against what the paper prints and what the mathematics fixes."""
 import itertools
+import math
 from math import comb, factorial
 
 import numpy as np
@@ -143,3 +144,22 @@ def test_boundary_zero_padding(szo):
     assert pred[0, 0] == 0.0
     assert np.array_equal(pred[0, 1:], V[0, :-1])
     assert np.array_equal(pred[1:, 0], V[:-1, 0])
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+def test_theorem_polynomial_exactness_1d(szo, n):
+    """In 1D the n-layer prediction is the extrapolation through the n
+    preceding values: exact for every polynomial of degree <= n - 1 (small
+    integer values, so every float operation is exact)."""
+    rng = np.random.default_rng(30 + n)
+    coef = rng.integers(-3, 4, size=n)
+    t = np.arange(24, dtype=np.int64)
+    f = sum(int(c) * t ** k for k, c in enumerate(coef))
+    assert np.abs(f).max() < 2 ** 20
+    V = f.astype(np.float32)
+    pred = szo.predict_field(V, n)
+    assert np.array_equal(pred[n:], V[n:])
+    # degree n is not reproduced: the residual is the n-th difference, n! c_n
+    g = (t ** n).astype(np.float32)
+    res = g - szo.predict_field(g, n)
+    assert np.all(res[n:] == math.factorial(n))
