@@ -116,7 +116,8 @@ size_t szgb_compress_bound(const szgb_params *p);
  * device, out_cap bytes).  *out_len receives the stream size, also when
  * SZGB_ETRUNC reports that out_cap is too small.  opt_stats may be NULL.
  * Fails with SZGB_ENONFINITE on NaN/Inf input, SZGB_EINVAL on bad
- * parameters, SZGB_EUNSUPPORTED for layers > 2. */
+ * parameters, SZGB_EUNSUPPORTED for a layer count the wavefront does not
+ * carry (1D and 2D fields take layers 1..4, 3D fields 1..2). */
 int szgb_compress(szgb_ctx *ctx, const float *data, int data_on_device,
                   const szgb_params *p, uint8_t *out, size_t out_cap,
                   int out_on_device, size_t *out_len, szgb_stats *opt_stats);
@@ -230,6 +231,25 @@ typedef struct szgb_quality {
 } szgb_quality;
 int szgb_quality_dev(szgb_ctx *ctx, const float *x_dev, const float *y_dev, size_t n,
                      szgb_quality *out);
+
+/* ---- prediction hitting rate (Sec. III, Table 2) -------------------------
+ * Counts the points i of the field x whose n-layer prediction f_i (Sec. III,
+ * the unified predictor), formed from the values v at i's preceding
+ * neighbours, lies within eb of x_i: |x_i - f_i| <= eb (inclusive).  f_i is
+ * the float32 value the compressor forms (terms in descending lexicographic
+ * order, products and sums rounded one at a time, values outside the field
+ * 0); the difference and the comparison are float64.  v = x gives the count
+ * behind R_PH^orig; v = the values the compressor recorded (the recorded_dev
+ * output of szgb_compress_trace, equal to the decompressed field) gives the
+ * count behind R_PH^decomp; divide by the number of points for the rate.
+ *  - x_dev, v_dev: device, float32, raster order (last axis fastest), shape
+ *    shape[0..ndim-1] (slowest first), ndim 1..3, extents 1..2^32-1 and fewer
+ *    than 2^40 points; layers 1..4 in every dimension; eb >= 0.
+ *  - runs on the context's stream and blocks until done; *n_hit is set on
+ *    success.  Returns SZGB_OK, SZGB_EINVAL (null pointer, bad shape, layers
+ *    or eb), SZGB_ENOMEM, SZGB_EBUDGET, SZGB_ECUDA. */
+int szgb_hit_count_dev(szgb_ctx *ctx, const float *x_dev, const float *v_dev, int ndim,
+                       const uint64_t *shape, int layers, double eb, uint64_t *n_hit);
 
 /* ---- serving loop ------------------------------------------------------
  * Requests are taken as they arrive and run by worker threads, each with its

@@ -225,4 +225,46 @@ int launch_adapt(const float* x, const CallParams& cp, DevState* st, cudaStream_
     return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
 }
 
+// ---------------------------------------------------------------------------
+// Prediction hitting rate (Sec. III): count the points whose n-layer
+// prediction from the values V at the preceding neighbours lies within eb of
+// x, |x - f(V)| <= eb (inclusive), the prediction formed in float32 exactly as
+// above and the difference compared in float64.  V = x gives the rate on
+// original values, V = the recorded (decompressed) values the rate the
+// compressor sees.  Grid-stride over all points; per-warp sums, one atomic
+// add per warp (an integer sum: the count does not depend on the schedule).
+
+template <int NL>
+__global__ void __launch_bounds__(256) k_hits(const float* __restrict__ x, const float* __restrict__ V,
+                                              uint64_t d0, uint64_t d1, uint64_t d2, int ndim, double eb,
+                                              unsigned long long* count) {
+    const uint64_t plane = d1 * d2, N = d0 * plane;
+    unsigned long long c = 0;
+    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < N;
+         s += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i = s / plane, r = s - i * plane, j = r / d2, l = r - j * d2;
+        const float pred = predict_original<NL>(V, d1, d2, (int64_t)i, (int64_t)j, (int64_t)l, ndim);
+        c += fabs((double)__ldg(x + s) - (double)pred) <= eb ? 1ull : 0ull;
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+// d0..d2: extents, slowest first, 1 for absent axes (a 2D field is 1 x d1 x d2)
+int launch_hits(const float* x, const float* V, uint64_t d0, uint64_t d1, uint64_t d2, int ndim, int layers,
+                double eb, unsigned long long* count, int sm_count, cudaStream_t s) {
+    const uint64_t N = d0 * d1 * d2;
+    uint64_t b = (N + 255) / 256;
+    const uint64_t cap = 8ull * (uint64_t)(sm_count > 0 ? sm_count : 1);
+    b = b < 1 ? 1 : (b > cap ? cap : b);
+    const int blocks = (int)b;
+    switch (layers) {
+        case 1: k_hits<1><<<blocks, 256, 0, s>>>(x, V, d0, d1, d2, ndim, eb, count); break;
+        case 2: k_hits<2><<<blocks, 256, 0, s>>>(x, V, d0, d1, d2, ndim, eb, count); break;
+        case 3: k_hits<3><<<blocks, 256, 0, s>>>(x, V, d0, d1, d2, ndim, eb, count); break;
+        default: k_hits<4><<<blocks, 256, 0, s>>>(x, V, d0, d1, d2, ndim, eb, count); break;
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
+}
+
 }  // namespace szgb

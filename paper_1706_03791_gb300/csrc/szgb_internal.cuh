@@ -451,6 +451,9 @@ struct WaveGeom {
 int launch_range(const float* x, uint64_t n, DevState* st, const CallParams& cp, float* partials,
                  int nblocks, cudaStream_t s);
 int launch_adapt(const float* x, const CallParams& cp, DevState* st, cudaStream_t s);
+// prediction hits |x - f(V)| <= eb over a d0 x d1 x d2 field, added to *count
+int launch_hits(const float* x, const float* V, uint64_t d0, uint64_t d1, uint64_t d2, int ndim, int layers,
+                double eb, unsigned long long* count, int sm_count, cudaStream_t s);
 int launch_wave_compress(const WaveGeom& g, int layers, const float* x, uint16_t* codes,
                          uint64_t codes_pitch, float* recorded, float* halo_row, float* halo_plane, unsigned int* prog,
                          DevState* st, uint64_t timeout_ns, cudaStream_t s);

@@ -96,6 +96,8 @@ def lib():
                                             C.POINTER(sz), C.POINTER(C.c_int)]
         L.szgb_set_graphs.argtypes = [vp, C.c_int]
         L.szgb_quality_dev.argtypes = [vp, vp, vp, sz, C.POINTER(Quality)]
+        L.szgb_hit_count_dev.argtypes = [vp, vp, vp, C.c_int, C.POINTER(C.c_uint64), C.c_int, C.c_double,
+                                         C.POINTER(C.c_uint64)]
         L.szgb_autotune.argtypes = [vp, vp, C.POINTER(Params), C.c_int, C.POINTER(C.c_int),
                                     C.POINTER(C.c_int), C.POINTER(C.c_double)]
         L.szgb_autotune_batch.argtypes = [vp, C.c_int, C.POINTER(vp), C.POINTER(Params), C.c_int,
@@ -126,7 +128,7 @@ EXPORTS = ["szgb_create", "szgb_destroy", "szgb_set_stream", "szgb_compress_boun
            "szgb_decompress_noalloc", "szgb_compress_batch", "szgb_decompress_batch", "szgb_set_graphs",
            "szgb_server_create", "szgb_submit", "szgb_poll", "szgb_wait", "szgb_server_stats",
            "szgb_server_destroy", "szgb_autotune", "szgb_autotune_batch", "szgb_tune_save", "szgb_tune_load",
-           "szgb_quality_dev"]
+           "szgb_quality_dev", "szgb_hit_count_dev"]
 
 
 VARIANT_EXACT, VARIANT_LATTICE = 0, 1
@@ -340,6 +342,35 @@ class Context:
         if rc:
             raise SzgbError(rc, "szgb_quality_dev")
         return q.as_dict()
+
+    def hit_count(self, x, v, layers: int, eb: float) -> int:
+        """Points of x whose n-layer prediction from the values v at the
+        preceding neighbours lies within eb of x (Sec. III): v = x counts the
+        hits behind R_PH^orig, v = the compressor's recorded values (see
+        compress_trace) those behind R_PH^decomp.  CUDA float32 tensors of
+        one shape, computed on the device."""
+        import torch
+        assert x.is_cuda and v.is_cuda and x.dtype == torch.float32 and v.dtype == torch.float32
+        assert x.is_contiguous() and v.is_contiguous() and tuple(x.shape) == tuple(v.shape)
+        shp = (C.c_uint64 * max(1, x.dim()))(*[int(a) for a in x.shape])
+        n = C.c_uint64()
+        rc = lib().szgb_hit_count_dev(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(v.data_ptr()), x.dim(), shp,
+                                      int(layers), float(eb), C.byref(n))
+        if rc:
+            raise SzgbError(rc, "szgb_hit_count_dev")
+        return int(n.value)
+
+    def hit_rates(self, x, layers: int, **kw) -> dict:
+        """R_PH^orig and R_PH^decomp of the CUDA float32 field x for the
+        n-layer predictor under the bound in kw (Sec. III, Table 2): the
+        second is taken from this compressor's own recorded values, with the
+        effective float32 bound eb_f of the compression."""
+        _, rec, _, st = self.compress_trace(x, layers=layers, **kw)
+        N = x.numel()
+        h_o = self.hit_count(x, x, layers, st.eb_f)
+        h_d = self.hit_count(x, rec, layers, st.eb_f)
+        return {"n": layers, "N": N, "eb_f": st.eb_f, "m": st.m, "hits_orig": h_o, "hits_decomp": h_d,
+                "R_orig": h_o / N, "R_decomp": h_d / N}
 
     def compress_batch(self, xs, params, outs=None):
         """Compress the CUDA float32 tensors `xs` in one batched call.
