@@ -463,6 +463,44 @@ def run_rd(args):
                       "points": pts}))
 
 
+def run_layers(args):
+    """Best-layer report (Sec. III, Table 2) on the device: R_PH^orig and
+    R_PH^decomp for n = 1..4 on the 3D field, a 2D climate-like field and a
+    smooth 2D field.  R_PH^decomp needs the compressor's recorded values, so
+    it is reported for the layer counts the wavefront carries (3D: n <= 2)."""
+    import torch
+    from paper_1706_03791_gb300 import build as B
+    B.build()
+    from paper_1706_03791_gb300 import szgb
+    from synthetic import fields
+    ctx = szgb.Context(0)
+    cases = [("3d-blobs-100x500x500", fields.workload_3d()),
+             ("2d-climate-1800x3600", fields.climate2d(7)),
+             ("2d-k6-smooth-1024x1024", fields.grf2d(1024, 1024, seed=3, slope=6.0, noise=0.0))]
+    rows = []
+    for name, x_np in cases:
+        x = torch.from_numpy(x_np).cuda()
+        for eb in (1e-3, 1e-4):
+            for n in (1, 2, 3, 4):
+                row = {"field": name, "eb_rel": eb, "n": n}
+                if x.dim() < 3 or n <= 2:
+                    r = ctx.hit_rates(x, n, eb_rel=eb)
+                    row.update(R_orig=r["R_orig"], R_decomp=r["R_decomp"], m=r["m"])
+                    ebf = r["eb_f"]  # the bound depends on the field and eb only, not on n
+                else:
+                    row.update(R_orig=ctx.hit_count(x, x, n, ebf) / x.numel(), R_decomp=None, m=None)
+                rows.append(row)
+        for r in rows:
+            if r["field"] == name:
+                print("%-24s eb %-6g n=%d  R_orig %7.3f%%  R_decomp %s  m %s" % (
+                    name, r["eb_rel"], r["n"], 100 * r["R_orig"],
+                    "%7.3f%%" % (100 * r["R_decomp"]) if r["R_decomp"] is not None else "   n/a  ",
+                    r["m"]), file=sys.stderr)
+    print(json.dumps({"metric": "prediction hitting rate by layer count (Sec. III, Table 2)", "value": None,
+                      "unit": "fraction", "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "best-layer hit rates, rel eb 1e-3 and 1e-4"}, "rows": rows}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -477,10 +515,11 @@ def main():
                          "fully parallel lattice variant, reported beside it")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
     ap.add_argument("--duration", type=float, default=30.0, help="serve: seconds of arrivals")
-    ap.add_argument("--workload", default="3d", choices=["3d", "climate79", "uneven512", "serve", "rd"],
+    ap.add_argument("--workload", default="3d", choices=["3d", "climate79", "uneven512", "serve", "rd", "layers"],
                     help="3d: the single 100x500x500 field (default); climate79 / uneven512: "
                          "batched many-field workloads, batched+graph vs one field per call; "
-                         "rd: rate-distortion sweep of the 3d field over the relative bound")
+                         "rd: rate-distortion sweep of the 3d field over the relative bound; "
+                         "layers: prediction hitting rate by layer count (Table 2)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -490,6 +529,8 @@ def main():
         return run_serve(args)
     if args.workload == "rd":
         return run_rd(args)
+    if args.workload == "layers":
+        return run_layers(args)
     if args.workload != "3d":
         return run_batch_workload(args)
 
