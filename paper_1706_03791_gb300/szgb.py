@@ -167,6 +167,29 @@ def _is_torch(a):
     return type(a).__module__.startswith("torch")
 
 
+def _require_cuda(t, dtype, name, device=None):
+    """Raise unless `t` is a contiguous CUDA tensor of `dtype` (on `device`
+    when given): the library reads and writes through its raw pointer."""
+    if not _is_torch(t) or not getattr(t, "is_cuda", False):
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, not %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if device is not None and t.device.index != device:
+        raise ValueError("%s is on cuda:%s, the context on cuda:%d" % (name, t.device.index, device))
+
+
+def _require_host(a, dtype, name):
+    """Raise unless `a` is a C-contiguous NumPy array of `dtype`."""
+    if not isinstance(a, np.ndarray):
+        raise TypeError("%s must be a NumPy array" % name)
+    if a.dtype != dtype:
+        raise TypeError("%s must be %s, not %s" % (name, np.dtype(dtype), a.dtype))
+    if not a.flags.c_contiguous:
+        raise ValueError("%s must be C-contiguous" % name)
+
+
 class Context:
     """A library context (device scratch and a stream) on one CUDA device."""
 
@@ -215,9 +238,10 @@ class Context:
         olen = C.c_size_t()
         if _is_torch(x):
             import torch
-            assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()
+            _require_cuda(x, torch.float32, "x", self.device)
             if out is None:
                 out = torch.empty(bound, dtype=torch.uint8, device=x.device)
+            _require_cuda(out, torch.uint8, "out", self.device)
             rc = L.szgb_compress(self._h, C.c_void_p(x.data_ptr()), 1, C.byref(p),
                                  C.c_void_p(out.data_ptr()), out.numel(), 1, C.byref(olen), C.byref(st))
             if rc:
@@ -226,6 +250,7 @@ class Context:
         xa = np.ascontiguousarray(x, dtype=np.float32)
         if out is None:
             out = np.empty(bound, np.uint8)
+        _require_host(out, np.uint8, "out")
         rc = L.szgb_compress(self._h, C.c_void_p(xa.ctypes.data), 0, C.byref(p),
                              C.c_void_p(out.ctypes.data), out.size, 0, C.byref(olen), C.byref(st))
         if rc:
@@ -247,6 +272,7 @@ class Context:
         """Device-only compression that also returns the recorded (exact
         decompressed) values and the quantization codes, for testing."""
         import torch
+        _require_cuda(x, torch.float32, "x", self.device)
         p = make_params(tuple(x.shape), **kw)
         L = lib()
         bound = int(L.szgb_compress_bound(C.byref(p)))
@@ -270,9 +296,11 @@ class Context:
         L = lib()
         if _is_torch(stream):
             import torch
+            _require_cuda(stream, torch.uint8, "stream", self.device)
             if out is None:  # the shape is in the header (one small device-to-host read)
                 info = stream_info_header(stream[:128].cpu().numpy())
                 out = torch.empty(info["shape"], dtype=torch.float32, device=stream.device)
+            _require_cuda(out, torch.float32, "out", self.device)
             rc = L.szgb_decompress(self._h, C.c_void_p(stream.data_ptr()), stream.numel(), 1,
                                    C.c_void_p(out.data_ptr()), out.numel(), 1)
             if rc:
@@ -282,6 +310,7 @@ class Context:
         info = stream_info_header(s[:128])
         if out is None:
             out = np.empty(info["shape"], np.float32)
+        _require_host(out, np.float32, "out")
         rc = L.szgb_decompress(self._h, C.c_void_p(s.ctypes.data), s.size, 0,
                                C.c_void_p(out.ctypes.data), out.size, 0)
         if rc:
@@ -291,6 +320,8 @@ class Context:
     # -- autotuner -----------------------------------------------------------
     def autotune(self, x, reps: int = 2, **kw) -> dict:
         """Pick the wavefront shape for the shape class of the CUDA tensor `x`."""
+        import torch
+        _require_cuda(x, torch.float32, "x", self.device)
         p = make_params(tuple(x.shape), **kw)
         W, pub, ms = C.c_int(), C.c_int(), C.c_double()
         rc = lib().szgb_autotune(self._h, C.c_void_p(x.data_ptr()), C.byref(p), int(reps), C.byref(W),
@@ -302,11 +333,13 @@ class Context:
     def autotune_batch(self, xs, params, reps: int = 1) -> dict:
         """Pick one wavefront shape for the batch of CUDA tensors `xs`
         (timed as batched passes) and keep it for every shape class in it."""
+        import torch
         n = len(xs)
         if isinstance(params, dict):
             params = [params] * n
         P = (Params * n)()
         for i, (x, kw) in enumerate(zip(xs, params)):
+            _require_cuda(x, torch.float32, "xs[%d]" % i, self.device)
             P[i] = make_params(tuple(x.shape), **kw)
         dp = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
         W, pub, ms = C.c_int(), C.c_int(), C.c_double()
@@ -334,8 +367,10 @@ class Context:
         size): maximum absolute / range-relative error, RMSE, NRMSE, PSNR and
         Pearson's coefficient (Sec. II, Metrics 1-3), computed on the device."""
         import torch
-        assert x.is_cuda and y.is_cuda and x.dtype == torch.float32 and y.dtype == torch.float32
-        assert x.is_contiguous() and y.is_contiguous() and x.numel() == y.numel()
+        _require_cuda(x, torch.float32, "x", self.device)
+        _require_cuda(y, torch.float32, "y", self.device)
+        if x.numel() != y.numel():
+            raise ValueError("x and y need the same number of values")
         q = Quality()
         rc = lib().szgb_quality_dev(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), x.numel(),
                                     C.byref(q))
@@ -350,8 +385,10 @@ class Context:
         compress_trace) those behind R_PH^decomp.  CUDA float32 tensors of
         one shape, computed on the device."""
         import torch
-        assert x.is_cuda and v.is_cuda and x.dtype == torch.float32 and v.dtype == torch.float32
-        assert x.is_contiguous() and v.is_contiguous() and tuple(x.shape) == tuple(v.shape)
+        _require_cuda(x, torch.float32, "x", self.device)
+        _require_cuda(v, torch.float32, "v", self.device)
+        if tuple(x.shape) != tuple(v.shape) or not 1 <= x.dim() <= 3:
+            raise ValueError("x and v need one 1D, 2D or 3D shape")
         shp = (C.c_uint64 * max(1, x.dim()))(*[int(a) for a in x.shape])
         n = C.c_uint64()
         rc = lib().szgb_hit_count_dev(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(v.data_ptr()), x.dim(), shp,
@@ -384,12 +421,16 @@ class Context:
             params = [params] * n
         P = (Params * n)()
         for i, (x, kw) in enumerate(zip(xs, params)):
-            assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()
+            _require_cuda(x, torch.float32, "xs[%d]" % i, self.device)
             P[i] = make_params(tuple(x.shape), **kw)
         L = lib()
         if outs is None:
             outs = [torch.empty(int(L.szgb_compress_bound(C.byref(P[i]))), dtype=torch.uint8, device=xs[i].device)
                     for i in range(n)]
+        if len(outs) != n:
+            raise ValueError("one output per field")
+        for i, o in enumerate(outs):
+            _require_cuda(o, torch.uint8, "outs[%d]" % i, self.device)
         dp = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
         op = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
         cap = (C.c_size_t * n)(*[o.numel() for o in outs])
@@ -405,11 +446,17 @@ class Context:
         float32 CUDA tensors (allocated from the headers when `outs` is None)."""
         import torch
         n = len(streams)
+        for i, s in enumerate(streams):
+            _require_cuda(s, torch.uint8, "streams[%d]" % i, self.device)
         if outs is None:
             outs = []
             for s in streams:
                 info = stream_info_header(s[:128].cpu().numpy())
                 outs.append(torch.empty(info["shape"], dtype=torch.float32, device=s.device))
+        if len(outs) != n:
+            raise ValueError("one output per stream")
+        for i, o in enumerate(outs):
+            _require_cuda(o, torch.float32, "outs[%d]" % i, self.device)
         ip = (C.c_void_p * n)(*[s.data_ptr() for s in streams])
         il = (C.c_size_t * n)(*[s.numel() for s in streams])
         op = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
@@ -438,6 +485,9 @@ def decompress_noalloc(stream, out, cuda_stream: int = 0) -> int:
     """szgb_decompress_noalloc on a uint8 CUDA tensor `stream` into the
     float32 CUDA tensor `out`; returns the C status code.  No memory is
     allocated by the library (the caller provides `out`)."""
+    import torch
+    _require_cuda(stream, torch.uint8, "stream")
+    _require_cuda(out, torch.float32, "out")
     return lib().szgb_decompress_noalloc(C.c_void_p(stream.data_ptr()), stream.numel(),
                                          C.c_void_p(out.data_ptr()), out.numel(),
                                          C.c_void_p(cuda_stream or 0))
@@ -477,7 +527,8 @@ class Server:
     def submit_compress(self, x: np.ndarray, out: np.ndarray, **kw) -> int:
         """Queue compression of the host float32 array `x` into the host uint8
         array `out`; returns the ticket."""
-        assert x.dtype == np.float32 and x.flags.c_contiguous and out.dtype == np.uint8
+        _require_host(x, np.float32, "x")
+        _require_host(out, np.uint8, "out")
         r = Request()
         r.op = OP_COMPRESS
         r.in_ = x.ctypes.data
@@ -489,7 +540,8 @@ class Server:
 
     def submit_decompress(self, stream: np.ndarray, out: np.ndarray) -> int:
         """Queue decompression of the host stream into the host float32 array `out`."""
-        assert stream.dtype == np.uint8 and out.dtype == np.float32 and out.flags.c_contiguous
+        _require_host(stream, np.uint8, "stream")
+        _require_host(out, np.float32, "out")
         r = Request()
         r.op = OP_DECOMPRESS
         r.in_ = stream.ctypes.data
