@@ -78,6 +78,8 @@ static int64_t binom(int n, int k) {
     return r;
 }
 
+/* 1D..3D shape as three extents, slowest first, leading 1s (the lattice
+ * variant) */
 static int norm_shape(int ndim, const uint64_t *shape, uint64_t d[3]) {
     if (ndim < 1 || ndim > 3 || !shape) return SZO_EINVAL;
     d[0] = d[1] = 1;
@@ -86,50 +88,79 @@ static int norm_shape(int ndim, const uint64_t *shape, uint64_t d[3]) {
     return SZO_OK;
 }
 
+/* 1D..4D shape as four extents, slowest first, leading 1s (the paper's
+ * method: its predictor is defined for any number of dimensions) */
+static int norm_shape4(int ndim, const uint64_t *shape, uint64_t d[4]) {
+    if (ndim < 1 || ndim > 4 || !shape) return SZO_EINVAL;
+    d[0] = d[1] = d[2] = 1;
+    for (int a = 0; a < ndim; a++) d[4 - ndim + a] = shape[a];
+    for (int a = 0; a < 4; a++) if (d[a] == 0) return SZO_EINVAL;
+    return SZO_OK;
+}
+
 /* ------------------------------------------------------------------ */
 /* n-layer predictor (Sec. III, Eq. predmodel)                          */
 
 int szo_num_terms(int ndim, int layers) {
-    if (ndim < 1 || ndim > 3 || layers < 1) return SZO_EINVAL;
+    if (ndim < 1 || ndim > 4 || layers < 1) return SZO_EINVAL;
     int t = 1;
     for (int a = 0; a < ndim; a++) t *= (layers + 1);
     return t - 1;
 }
 
 /* Enumerates k in [0,n]^d \ {0} in descending lexicographic order (slowest
- * axis most significant) with coefficient -prod_j (-1)^k_j C(n, k_j). */
-int szo_terms(int ndim, int layers, int32_t *k_out, int64_t *coef_out) {
+ * axis most significant) with coefficient -prod_j (-1)^k_j C(n, k_j); k is
+ * written as 4 ints per term, leading zeros for d < 4. */
+static int enum_terms(int ndim, int layers, int32_t *k4, int64_t *coef_out) {
     int T = szo_num_terms(ndim, layers);
     if (T < 0) return T;
     int n = layers, idx = 0;
     int total = T + 1;
     for (int code = total - 1; code >= 1; code--) {
-        int k[3] = {0, 0, 0}, c = code;
-        for (int a = ndim - 1; a >= 0; a--) { k[3 - ndim + a] = c % (n + 1); c /= (n + 1); }
+        int k[4] = {0, 0, 0, 0}, c = code;
+        for (int a = ndim - 1; a >= 0; a--) { k[4 - ndim + a] = c % (n + 1); c /= (n + 1); }
         int64_t prod = 1;
-        for (int a = 0; a < 3; a++) {
+        for (int a = 0; a < 4; a++) {
             int64_t s = (k[a] & 1) ? -1 : 1;
             prod *= s * binom(n, k[a]);
         }
-        if (k_out) { k_out[3 * idx] = k[0]; k_out[3 * idx + 1] = k[1]; k_out[3 * idx + 2] = k[2]; }
+        if (k4) for (int a = 0; a < 4; a++) k4[4 * idx + a] = k[a];
         if (coef_out) coef_out[idx] = -prod;
         idx++;
     }
     return T;
 }
 
-typedef struct { int32_t k[3]; float c; } term_t;
+int szo_terms(int ndim, int layers, int32_t *k_out, int64_t *coef_out) {
+    if (ndim > 3) return SZO_EINVAL;
+    int T = szo_num_terms(ndim, layers);
+    if (T < 0) return T;
+    int32_t *k4 = (int32_t *)malloc(sizeof(int32_t) * 4 * (size_t)T);
+    if (!k4) return SZO_ENOMEM;
+    enum_terms(ndim, layers, k4, coef_out);
+    if (k_out)
+        for (int i = 0; i < T; i++)
+            for (int a = 0; a < 3; a++) k_out[3 * i + a] = k4[4 * i + 1 + a];
+    free(k4);
+    return T;
+}
+
+int szo_terms4(int ndim, int layers, int32_t *k_out, int64_t *coef_out) {
+    return enum_terms(ndim, layers, k_out, coef_out);
+}
+
+typedef struct { int32_t k[4]; float c; } term_t;
 
 static term_t *make_terms(int ndim, int layers, int *T_out) {
     int T = szo_num_terms(ndim, layers);
     if (T <= 0) return NULL;
-    int32_t *k = (int32_t *)malloc(sizeof(int32_t) * 3 * T);
+    int32_t *k = (int32_t *)malloc(sizeof(int32_t) * 4 * T);
     int64_t *c = (int64_t *)malloc(sizeof(int64_t) * T);
     term_t *t = (term_t *)malloc(sizeof(term_t) * T);
     if (!k || !c || !t) { free(k); free(c); free(t); return NULL; }
-    szo_terms(ndim, layers, k, c);
+    enum_terms(ndim, layers, k, c);
     for (int i = 0; i < T; i++) {
-        t[i].k[0] = k[3 * i]; t[i].k[1] = k[3 * i + 1]; t[i].k[2] = k[3 * i + 2];
+        for (int a = 0; a < 4; a++) t[i].k[a] = k[4 * i + a];
         t[i].c = (float)c[i];
     }
     free(k); free(c);
@@ -137,16 +168,23 @@ static term_t *make_terms(int ndim, int layers, int *T_out) {
     return t;
 }
 
+/* raster index of the point with coordinates x[0..3] */
+static uint64_t lin4(const uint64_t d[4], const int64_t x[4]) {
+    return (((uint64_t)x[0] * d[1] + (uint64_t)x[1]) * d[2] + (uint64_t)x[2]) * d[3] + (uint64_t)x[3];
+}
+
 /* f(x) = sum_k c_k V(x - k); V outside the domain = 0 (R1); summed in the
  * term order, first product initialising the sum (R2). */
-static float predict_at(const float *V, const uint64_t d[3], int64_t i, int64_t j,
-                        int64_t l, const term_t *t, int T) {
+static float predict_at(const float *V, const uint64_t d[4], const int64_t x[4], const term_t *t, int T) {
     float pred = 0.0f;
     for (int s = 0; s < T; s++) {
-        int64_t ii = i - t[s].k[0], jj = j - t[s].k[1], ll = l - t[s].k[2];
-        float v = 0.0f;
-        if (ii >= 0 && jj >= 0 && ll >= 0)
-            v = V[((uint64_t)ii * d[1] + (uint64_t)jj) * d[2] + (uint64_t)ll];
+        int64_t y[4];
+        int inside = 1;
+        for (int a = 0; a < 4; a++) {
+            y[a] = x[a] - t[s].k[a];
+            if (y[a] < 0) inside = 0;
+        }
+        float v = inside ? V[lin4(d, y)] : 0.0f;
         float prod = t[s].c * v;
         pred = (s == 0) ? prod : pred + prod;
     }
@@ -155,15 +193,17 @@ static float predict_at(const float *V, const uint64_t d[3], int64_t i, int64_t 
 
 int szo_predict_field(const float *V, int ndim, const uint64_t *shape, int layers,
                       float *pred_out) {
-    uint64_t d[3];
-    if (norm_shape(ndim, shape, d) || !V || !pred_out) return SZO_EINVAL;
+    uint64_t d[4];
+    if (norm_shape4(ndim, shape, d) || !V || !pred_out) return SZO_EINVAL;
     int T;
     term_t *t = make_terms(ndim, layers, &T);
     if (!t) return SZO_EINVAL;
-    for (uint64_t i = 0; i < d[0]; i++)
-        for (uint64_t j = 0; j < d[1]; j++)
-            for (uint64_t l = 0; l < d[2]; l++)
-                pred_out[(i * d[1] + j) * d[2] + l] = predict_at(V, d, i, j, l, t, T);
+    int64_t x[4];
+    for (x[0] = 0; x[0] < (int64_t)d[0]; x[0]++)
+        for (x[1] = 0; x[1] < (int64_t)d[1]; x[1]++)
+            for (x[2] = 0; x[2] < (int64_t)d[2]; x[2]++)
+                for (x[3] = 0; x[3] < (int64_t)d[3]; x[3]++)
+                    pred_out[lin4(d, x)] = predict_at(V, d, x, t, T);
     free(t);
     return SZO_OK;
 }
@@ -235,8 +275,8 @@ int szo_quantize(float x, float pred, float eb_f, int m, float *recorded) {
 
 int szo_choose_m(const float *x, int ndim, const uint64_t *shape, int layers,
                  float eb_f, double theta) {
-    uint64_t d[3];
-    if (norm_shape(ndim, shape, d) || !x) return SZO_EINVAL;
+    uint64_t d[4];
+    if (norm_shape4(ndim, shape, d) || !x) return SZO_EINVAL;
     int T;
     term_t *t = make_terms(ndim, layers, &T);
     if (!t) return SZO_EINVAL;
@@ -244,22 +284,24 @@ int szo_choose_m(const float *x, int ndim, const uint64_t *shape, int layers,
     uint64_t S = 0;
     float twoeb = 2.0f * eb_f;
     float inv = (eb_f > 0.0f) ? 1.0f / twoeb : 0.0f;
-    for (uint64_t i = 0; i < d[0]; i += 8)
-        for (uint64_t j = 0; j < d[1]; j += 8)
-            for (uint64_t l = 0; l < d[2]; l += 8) {
-                S++;
-                float xv = x[(i * d[1] + j) * d[2] + l];
-                float pred = predict_at(x, d, i, j, l, t, T); /* original values */
-                float diff = xv - pred;
-                float q = rintf(diff * inv);
-                if (!(fabsf(q) <= 32767.0f)) continue;
-                float dq = pred + (float)(int)q * twoeb;
-                if (!(fabsf(xv - dq) < eb_f || xv == dq)) continue;
-                float aq = fabsf(q);
-                int mm = 2;
-                while (aq > (float)((1 << (mm - 1)) - 1)) mm++;
-                need[mm]++;
-            }
+    int64_t c[4];
+    for (c[0] = 0; c[0] < (int64_t)d[0]; c[0] += 8)
+        for (c[1] = 0; c[1] < (int64_t)d[1]; c[1] += 8)
+            for (c[2] = 0; c[2] < (int64_t)d[2]; c[2] += 8)
+                for (c[3] = 0; c[3] < (int64_t)d[3]; c[3] += 8) {
+                    S++;
+                    float xv = x[lin4(d, c)];
+                    float pred = predict_at(x, d, c, t, T); /* original values */
+                    float diff = xv - pred;
+                    float q = rintf(diff * inv);
+                    if (!(fabsf(q) <= 32767.0f)) continue;
+                    float dq = pred + (float)(int)q * twoeb;
+                    if (!(fabsf(xv - dq) < eb_f || xv == dq)) continue;
+                    float aq = fabsf(q);
+                    int mm = 2;
+                    while (aq > (float)((1 << (mm - 1)) - 1)) mm++;
+                    need[mm]++;
+                }
     free(t);
     double req = ceil(theta * (double)S);
     uint64_t cum = 0;
@@ -384,9 +426,9 @@ static void wrf64(uint8_t *p, double d) { uint64_t u; memcpy(&u, &d, 8); wr64(p,
 static uint64_t pad4(uint64_t v) { return (v + 3) & ~(uint64_t)3; }
 
 size_t szo_stream_bound(int ndim, const uint64_t *shape) {
-    uint64_t d[3];
-    if (norm_shape(ndim, shape, d)) return 0;
-    uint64_t N = d[0] * d[1] * d[2], rows = d[0] * d[1];
+    uint64_t d[4];
+    if (norm_shape4(ndim, shape, d)) return 0;
+    uint64_t N = d[0] * d[1] * d[2] * d[3], rows = d[0] * d[1] * d[2];
     return (size_t)(HDR_BYTES + pad4(3 * 65536) + pad4(4 * rows) + rows + (N * 78 + 7) / 8 + 16);
 }
 
@@ -397,14 +439,18 @@ int szo_compress(const float *x, int ndim, const uint64_t *shape, int mode,
                  double eb_abs, double eb_rel, int layers, int m, double theta,
                  int order, uint8_t *out, size_t out_cap, size_t *out_len,
                  float *recorded_out, uint16_t *codes_out) {
-    uint64_t d[3];
-    if (norm_shape(ndim, shape, d) || !x || !out_len) return SZO_EINVAL;
+    uint64_t d[4];
+    if (norm_shape4(ndim, shape, d) || !x || !out_len) return SZO_EINVAL;
     if (mode < 0 || mode > 2 || layers < 1 || layers > 4) return SZO_EINVAL;
     if (m != 0 && (m < 2 || m > 16)) return SZO_EINVAL;
     if (mode != 1 && !(eb_abs >= 0.0)) return SZO_EINVAL;
     if (mode != 0 && !(eb_rel >= 0.0)) return SZO_EINVAL;
-    uint64_t N = d[0] * d[1] * d[2];
-    if (N >= ((uint64_t)1 << 32)) return SZO_EINVAL;
+    uint64_t N = 1;
+    for (int a = 0; a < 4; a++) {
+        if (d[a] >= ((uint64_t)1 << 32)) return SZO_EINVAL;
+        N *= d[a]; /* each factor < 2^32 and the product so far < 2^32 */
+        if (N >= ((uint64_t)1 << 32)) return SZO_EINVAL;
+    }
 
     /* range and finite check */
     float xmin = x[0], xmax = x[0];
@@ -429,26 +475,30 @@ int szo_compress(const float *x, int ndim, const uint64_t *shape, int mode,
 
     /* the hot loop: predict, quantize, fall back, record */
     uint64_t K = 0;
+    int64_t c[4];
     if (order == 0) {
-        for (uint64_t i = 0; i < d[0]; i++)
-            for (uint64_t j = 0; j < d[1]; j++)
-                for (uint64_t l = 0; l < d[2]; l++) {
-                    uint64_t p = (i * d[1] + j) * d[2] + l;
-                    float pred = predict_at(V, d, i, j, l, t, T);
-                    code[p] = (uint16_t)szo_quantize(x[p], pred, eb_f, m, &V[p]);
-                }
+        for (c[0] = 0; c[0] < (int64_t)d[0]; c[0]++)
+            for (c[1] = 0; c[1] < (int64_t)d[1]; c[1]++)
+                for (c[2] = 0; c[2] < (int64_t)d[2]; c[2]++)
+                    for (c[3] = 0; c[3] < (int64_t)d[3]; c[3]++) {
+                        uint64_t p = lin4(d, c);
+                        float pred = predict_at(V, d, c, t, T);
+                        code[p] = (uint16_t)szo_quantize(x[p], pred, eb_f, m, &V[p]);
+                    }
     } else {
-        /* hyperplane order: every point of i+j+l = h before any of h+1 */
-        uint64_t H = (d[0] - 1) + (d[1] - 1) + (d[2] - 1);
-        for (uint64_t h = 0; h <= H; h++)
-            for (uint64_t i = 0; i < d[0] && i <= h; i++)
-                for (uint64_t j = 0; j < d[1] && i + j <= h; j++) {
-                    uint64_t l = h - i - j;
-                    if (l >= d[2]) continue;
-                    uint64_t p = (i * d[1] + j) * d[2] + l;
-                    float pred = predict_at(V, d, i, j, l, t, T);
-                    code[p] = (uint16_t)szo_quantize(x[p], pred, eb_f, m, &V[p]);
-                }
+        /* hyperplane order: every point whose coordinates sum to h before
+         * any point of h+1 */
+        int64_t H = (int64_t)((d[0] - 1) + (d[1] - 1) + (d[2] - 1) + (d[3] - 1));
+        for (int64_t h = 0; h <= H; h++)
+            for (c[0] = 0; c[0] < (int64_t)d[0] && c[0] <= h; c[0]++)
+                for (c[1] = 0; c[1] < (int64_t)d[1] && c[0] + c[1] <= h; c[1]++)
+                    for (c[2] = 0; c[2] < (int64_t)d[2] && c[0] + c[1] + c[2] <= h; c[2]++) {
+                        c[3] = h - c[0] - c[1] - c[2];
+                        if (c[3] >= (int64_t)d[3]) continue;
+                        uint64_t p = lin4(d, c);
+                        float pred = predict_at(V, d, c, t, T);
+                        code[p] = (uint16_t)szo_quantize(x[p], pred, eb_f, m, &V[p]);
+                    }
     }
     for (uint64_t p = 0; p < N; p++) K += (code[p] == 0);
 
@@ -465,7 +515,7 @@ int szo_compress(const float *x, int ndim, const uint64_t *shape, int mode,
     for (int s = 0; s < nsymtot; s++) nsym += (len[s] != 0);
 
     /* per-row bit counts: code bits, plus 9 + t record bits for code 0 */
-    uint64_t rows = d[0] * d[1], Nr = d[2];
+    uint64_t rows = d[0] * d[1] * d[2], Nr = d[3];
     uint64_t *rowbytes = (uint64_t *)malloc(sizeof(uint64_t) * rows);
     if (!rowbytes) { free(t); free(V); free(code); free(freq); free(len); free(cw); return SZO_ENOMEM; }
     uint64_t payload = 0, maxrow = 0;
@@ -495,7 +545,9 @@ int szo_compress(const float *x, int ndim, const uint64_t *shape, int mode,
     wr16(out + 6, HDR_BYTES);
     out[8] = (uint8_t)ndim; out[9] = (uint8_t)layers; out[10] = (uint8_t)m; out[11] = (uint8_t)mode;
     out[12] = (uint8_t)maxlen; out[13] = (uint8_t)tw;
-    wr64(out + 16, d[0]); wr64(out + 24, d[1]); wr64(out + 32, d[2]);
+    /* the three fastest extents; a 4D field's slowest extent at byte 120 */
+    wr64(out + 16, d[1]); wr64(out + 24, d[2]); wr64(out + 32, d[3]);
+    if (ndim == 4) wr64(out + 120, d[0]);
     wrf64(out + 40, eb_abs); wrf64(out + 48, eb_rel);
     wr32(out + 56, f2u(eb_f)); wr32(out + 60, f2u(xmin)); wr32(out + 64, f2u(xmax));
     wr32(out + 68, nsym); wr64(out + 72, rows); wr64(out + 80, K);
@@ -763,17 +815,21 @@ int szo_decompress(const uint8_t *in, size_t in_len, float *out, size_t out_cap_
     if (!(in[0] == 'S' && in[1] == 'Z' && in[2] == 'G' && in[3] == 'B')) return SZO_ECORRUPT;
     if (rd16(in + 4) != 1 || rd16(in + 6) != HDR_BYTES) return SZO_ECORRUPT;
     int ndim = in[8], layers = in[9], m = in[10], tw = in[13];
-    if (ndim < 1 || ndim > 3 || layers < 1 || layers > 4 || m < 2 || m > 16) return SZO_ECORRUPT;
+    if (ndim < 1 || ndim > 4 || layers < 1 || layers > 4 || m < 2 || m > 16) return SZO_ECORRUPT;
     if (tw != 2 && tw != 4) return SZO_ECORRUPT;
-    uint64_t d[3] = {rd64(in + 16), rd64(in + 24), rd64(in + 32)};
-    for (int a = 0; a < 3; a++) if (d[a] == 0 || d[a] > ((uint64_t)1 << 32)) return SZO_ECORRUPT;
-    uint64_t N = d[0] * d[1] * d[2];
-    if (N >= ((uint64_t)1 << 32)) return SZO_ECORRUPT;
+    /* extents slowest first; a 4D field's slowest extent is at byte 120 */
+    uint64_t d[4] = {ndim == 4 ? rd64(in + 120) : 1, rd64(in + 16), rd64(in + 24), rd64(in + 32)};
+    uint64_t N = 1;
+    for (int a = 0; a < 4; a++) {
+        if (d[a] == 0 || d[a] >= ((uint64_t)1 << 32)) return SZO_ECORRUPT;
+        N *= d[a];
+        if (N >= ((uint64_t)1 << 32)) return SZO_ECORRUPT;
+    }
     if (out_cap_elems < N) return SZO_EINVAL;
     float eb_f = u2f(rd32(in + 56));
     uint32_t nsym = rd32(in + 68);
     uint64_t rows = rd64(in + 72), K = rd64(in + 80), payload = rd64(in + 88), total = rd64(in + 96);
-    if (rows != d[0] * d[1] || nsym < 1 || nsym > (1u << m)) return SZO_ECORRUPT;
+    if (rows != d[0] * d[1] * d[2] || nsym < 1 || nsym > (1u << m)) return SZO_ECORRUPT;
     uint64_t cb_bytes = pad4(3 * (uint64_t)nsym), tab_bytes = pad4((uint64_t)tw * rows);
     if (total != HDR_BYTES + cb_bytes + tab_bytes + payload || total > in_len) return SZO_ECORRUPT;
 
@@ -811,7 +867,8 @@ int szo_decompress(const uint8_t *in, size_t in_len, float *out, size_t out_cap_
     }
 
     const int lattice = in[113] == 1;
-    if (in[113] > 1) { free(len); free(cw); free(sorted_sym); return SZO_ECORRUPT; }
+    if (in[113] > 1 || (lattice && ndim > 3)) { free(len); free(cw); free(sorted_sym); return SZO_ECORRUPT; }
+    const uint64_t d3[3] = {d[1], d[2], d[3]}; /* the lattice variant's 3-axis view (d[0] = 1) */
     int T;
     term_t *t = make_terms(ndim, layers, &T);
     iterm_t *it = lattice ? make_iterms(ndim, layers, &T) : NULL;
@@ -821,13 +878,15 @@ int szo_decompress(const uint8_t *in, size_t in_len, float *out, size_t out_cap_
     const uint8_t *pl = tb + tab_bytes;
     float twoeb = 2.0f * eb_f;
     int rc = SZO_OK;
-    uint64_t off = 0, Kseen = 0, Nr = d[2];
+    uint64_t off = 0, Kseen = 0, Nr = d[3];
     for (uint64_t r = 0; r < rows && rc == SZO_OK; r++) {
         uint64_t nb = (tw == 2) ? rd16(tb + 2 * r) : rd32(tb + 4 * r);
         if (off + nb > payload) { rc = SZO_ECORRUPT; break; }
         br_t br = {pl + off, 0, nb * 8};
-        uint64_t i = r / d[1], j = r % d[1];
+        /* row r holds the points (r / (d1 d2), (r / d2) mod d1, r mod d2, 0..d3-1) */
+        int64_t pt[4] = {(int64_t)(r / (d[1] * d[2])), (int64_t)((r / d[2]) % d[1]), (int64_t)(r % d[2]), 0};
         for (uint64_t l = 0; l < Nr; l++) {
+            pt[3] = (int64_t)l;
             /* bit-by-bit canonical decode */
             uint64_t c = 0;
             int L = 0, sym = -1;
@@ -843,7 +902,7 @@ int szo_decompress(const uint8_t *in, size_t in_len, float *out, size_t out_cap_
             uint64_t p = r * Nr + l;
             if (lattice) {
                 /* p = r + integer prediction from the earlier lattice values */
-                int64_t ipred = ipredict_at(P, d, (int64_t)i, (int64_t)j, (int64_t)l, it, T);
+                int64_t ipred = ipredict_at(P, d3, pt[1], pt[2], pt[3], it, T);
                 if (sym != 0) {
                     P[p] = ipred + (int64_t)(sym - (1 << (m - 1)));
                     out[p] = szo_lattice_value(P[p], eb_f);
@@ -862,7 +921,7 @@ int szo_decompress(const uint8_t *in, size_t in_len, float *out, size_t out_cap_
                 }
                 continue;
             }
-            float pred = predict_at(out, d, (int64_t)i, (int64_t)j, (int64_t)l, t, T);
+            float pred = predict_at(out, d, pt, t, T);
             if (sym != 0) {
                 float step = (float)(sym - (1 << (m - 1))) * twoeb;
                 out[p] = pred + step;

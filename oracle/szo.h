@@ -8,8 +8,9 @@
  * CPU-baseline leg of the benchmark.  It shares no code, header or constant
  * table with the GPU library.
  *
- * Array convention: shape[] is slowest -> fastest (C order); a d-dimensional
- * field is handled as (shape0, shape1, shape2) with leading extents 1.
+ * Array convention: shape[] is slowest -> fastest (C order).  The paper's
+ * method takes 1D..4D fields, handled as four extents with leading 1s (its
+ * predictor is defined for any dimension); the lattice variant takes 1D..3D.
  * Error codes: 0 ok, -1 invalid argument, -2 non-finite input, -3 output
  * buffer too small (needed size in *out_len), -4 corrupt stream, -5 no memory.
  */
@@ -21,12 +22,16 @@
 extern "C" {
 #endif
 
-/* Number of prediction terms, (n+1)^d - 1 (Algorithm 1, coefficient step). */
+/* Number of prediction terms, (n+1)^d - 1 (Algorithm 1, coefficient step),
+ * d = 1..4. */
 int szo_num_terms(int ndim, int layers);
-/* Offsets k (3 ints each, leading zeros for d < 3) and integer coefficients
- * -prod_j (-1)^k_j C(n,k_j) of the n-layer predictor (Eq. predmodel), in the
- * summation order the oracle uses (descending lexicographic k). */
+/* Offsets k (3 ints each, leading zeros for d < 3; d <= 3) and integer
+ * coefficients -prod_j (-1)^k_j C(n,k_j) of the n-layer predictor
+ * (Eq. predmodel), in the summation order the oracle uses (descending
+ * lexicographic k). */
 int szo_terms(int ndim, int layers, int32_t *k_out, int64_t *coef_out);
+/* The same with 4 ints per offset (leading zeros for d < 4), d = 1..4. */
+int szo_terms4(int ndim, int layers, int32_t *k_out, int64_t *coef_out);
 /* Prediction of every point from the values in V (Eq. predmodel), with
  * neighbours outside the domain taken as 0. */
 int szo_predict_field(const float *V, int ndim, const uint64_t *shape,
@@ -49,7 +54,9 @@ int szo_choose_m(const float *x, int ndim, const uint64_t *shape, int layers,
                  float eb_f, double theta);
 /* Worst-case stream size. */
 size_t szo_stream_bound(int ndim, const uint64_t *shape);
-/* Compress.  order 0 = raster order, 1 = hyperplane (i+j+k) order.  Optional
+/* Compress (1D..4D).  order 0 = raster order, 1 = hyperplane order (by
+ * the sum of the coordinates).  A 4D stream keeps its slowest extent at
+ * header byte 120.  Optional
  * outputs: recorded values (the decompressed values the compressor predicts
  * from) and the quantization codes, both in raster order. */
 int szo_compress(const float *x, int ndim, const uint64_t *shape, int mode,

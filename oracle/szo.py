@@ -39,6 +39,7 @@ def lib():
         u64p = C.POINTER(C.c_uint64)
         L.szo_num_terms.argtypes = [C.c_int, C.c_int]
         L.szo_terms.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_void_p]
+        L.szo_terms4.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_void_p]
         L.szo_predict_field.argtypes = [C.c_void_p, C.c_int, u64p, C.c_int, C.c_void_p]
         L.szo_effective_eb.argtypes = [C.c_int, C.c_double, C.c_double, C.c_float, C.c_float,
                                        C.POINTER(C.c_float)]
@@ -67,15 +68,22 @@ def lib():
 
 
 def _shape(a):
-    return (C.c_uint64 * 3)(*[int(s) for s in a.shape] + [1] * (3 - a.ndim))
+    if not 1 <= a.ndim <= 4:
+        raise ValueError("1D..4D fields only")
+    return (C.c_uint64 * 4)(*[int(s) for s in a.shape] + [1] * (4 - a.ndim))
 
 
 def terms(ndim: int, n: int):
-    """(k offsets [T,3], integer coefficients [T]) in summation order."""
+    """(k offsets [T, max(3, ndim)], integer coefficients [T]) in summation
+    order; offsets have leading zeros for the absent axes."""
     T = lib().szo_num_terms(ndim, n)
-    k = np.zeros((T, 3), np.int32)
     c = np.zeros(T, np.int64)
-    lib().szo_terms(ndim, n, k.ctypes.data, c.ctypes.data)
+    if ndim <= 3:
+        k = np.zeros((T, 3), np.int32)
+        lib().szo_terms(ndim, n, k.ctypes.data, c.ctypes.data)
+    else:
+        k = np.zeros((T, 4), np.int32)
+        lib().szo_terms4(ndim, n, k.ctypes.data, c.ctypes.data)
     return k, c
 
 
@@ -200,14 +208,13 @@ def compress_rc(x, **kw):
 def decompress(stream, shape=None):
     s = np.ascontiguousarray(stream, dtype=np.uint8)
     hdr = header(s)
-    d = hdr["shape"]
-    N = int(d[0] * d[1] * d[2])
+    dims = hdr["dims"]
+    N = int(np.prod(dims, dtype=np.uint64))
     out = np.empty(N, np.float32)
     rc = lib().szo_decompress(s.ctypes.data, s.size, out.ctypes.data, N)
     if rc != 0:
         raise RuntimeError("szo_decompress failed: %d" % rc)
-    nd = hdr["ndim"]
-    return out.reshape(tuple(int(v) for v in d[3 - nd:]))
+    return out.reshape(dims)
 
 
 def decompress_rc(stream):
@@ -215,8 +222,7 @@ def decompress_rc(stream):
     out = np.empty(max(1, 1 << 20), np.float32)
     try:
         hdr = header(s)
-        d = hdr["shape"]
-        N = int(d[0] * d[1] * d[2])
+        N = int(np.prod(hdr["dims"], dtype=np.uint64))
         if N > out.size:
             out = np.empty(N, np.float32)
     except Exception:
@@ -242,4 +248,9 @@ def header(s):
     f["theta"], = struct.unpack_from("<d", b, 104)
     f["adaptive"] = b[112]
     f["lattice"] = b[113]
+    # all four extents (a 4D field keeps its slowest one at byte 120) and the
+    # field's own shape
+    d0, = struct.unpack_from("<Q", b, 120)
+    f["shape4"] = ((d0 if f["ndim"] == 4 else 1),) + tuple(f["shape"])
+    f["dims"] = tuple(int(v) for v in f["shape4"][4 - f["ndim"]:]) if 1 <= f["ndim"] <= 4 else ()
     return f

@@ -482,6 +482,9 @@ int parse_header(const uint8_t* h, size_t in_len, Header* o) {
     o->adaptive = h[112];
     o->variant = h[113];
     if (o->variant > 1) return SZGB_ECORRUPT;
+    // a 4D field (the predictor of Sec. III in four dimensions; slowest extent
+    // at byte 120) is a valid stream this library does not decode
+    if (o->ndim == 4 && o->variant == 0 && rd_le(h + 120, 8) != 0) return SZGB_EUNSUPPORTED;
     if (o->ndim < 1 || o->ndim > 3 || o->layers < 1 || o->layers > 4 || o->m < 2 || o->m > 16) return SZGB_ECORRUPT;
     if (o->tw != 2 && o->tw != 4 || o->mode > 2) return SZGB_ECORRUPT;
     if (o->d0 == 0 || o->d1 == 0 || o->d2 == 0 || o->d0 > 0xffffffffull || o->d1 > 0xffffffffull ||

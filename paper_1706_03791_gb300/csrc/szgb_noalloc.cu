@@ -84,6 +84,7 @@ extern "C" int szgb_decompress_noalloc(const uint8_t* in_dev, size_t in_len, flo
     memcpy(&eb_f, &ebu, 4);
     const uint32_t nsym = (uint32_t)le(h + 68, 4);
     const uint64_t rows = le(h + 72, 8), payload_bytes = le(h + 88, 8), total = le(h + 96, 8);
+    if (ndim == 4 && h[113] == 0 && le(h + 120, 8) != 0) return SZGB_EUNSUPPORTED;  // a 4D field: not decoded here
     if (ndim < 1 || ndim > 3 || layers < 1 || m < 2 || m > 16 || (tw != 2 && tw != 4)) return SZGB_ECORRUPT;
     if (d0 == 0 || d1 == 0 || d2 == 0 || d0 > 0xffffffffull || d1 > 0xffffffffull || d2 > 0xffffffffull)
         return SZGB_ECORRUPT;

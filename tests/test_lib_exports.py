@@ -55,3 +55,13 @@ def test_stream_info_parses_oracle_header(szgb, szo):
         szgb.stream_info(bad)
     with pytest.raises(szgb.SzgbError):
         szgb.stream_info(s[:-1])
+
+
+def test_4d_stream_reported_unsupported(szgb, szo):
+    # the oracle writes 4D streams (the predictor of Sec. III in four
+    # dimensions); the GPU library recognises and declines them
+    x = np.random.default_rng(4).normal(size=(3, 4, 5, 6)).astype(np.float32)
+    s = szo.compress(x, eb_rel=1e-3, m=8)
+    with pytest.raises(szgb.SzgbError) as e:
+        szgb.stream_info(s)
+    assert e.value.code == szgb.EUNSUPPORTED

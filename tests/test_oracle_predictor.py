@@ -30,7 +30,7 @@ def test_table1_coefficients(szo, n):
     assert got == _table1()[n]
 
 
-@pytest.mark.parametrize("d", [1, 2, 3])
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
 @pytest.mark.parametrize("n", [1, 2, 3, 4])
 def test_term_count_and_sum(szo, d, n):
     """(n+1)^d - 1 coefficients (Algorithm 1, coefficient step); in 2D the
@@ -42,13 +42,15 @@ def test_term_count_and_sum(szo, d, n):
         assert len(c) == n * (n + 2)
     assert int(c.sum()) == 1
     # every offset is in [0,n]^d, none is the point itself, all distinct
-    offs = {tuple(a[3 - d:]) for a in k}
+    w = k.shape[1]  # 3 columns up to 3D, 4 in 4D; absent axes are 0
+    assert all(not a[:w - d].any() for a in k)
+    offs = {tuple(a[w - d:]) for a in k}
     assert len(offs) == len(c)
     assert all(max(o) <= n and min(o) >= 0 and any(o) for o in offs)
     # closed form of each coefficient: -prod_j (-1)^k_j C(n, k_j)
     for a, v in zip(k, c):
         prod = 1
-        for kj in a[3 - d:]:
+        for kj in a[w - d:]:
             prod *= (-1) ** int(kj) * comb(n, int(kj))
         assert v == -prod
 
@@ -123,6 +125,29 @@ def test_product_structure_exactness(szo, d, n):
     g = _poly_field(shape, [(1, tuple([n] * d))]).astype(np.float32)
     pg = szo.predict_field(g, n)
     assert not np.array_equal(pg[sl], g[sl])
+
+
+@pytest.mark.parametrize("n", [1, 2])
+def test_product_structure_exactness_4d(szo, n):
+    """The factorisation holds in 4D (the predictor is defined for any d):
+    V - f = prod over the 4 axes of the n-th backward difference, so
+    monomials with an exponent below n are reproduced away from the first n
+    layers and x^n y^n z^n w^n is not.  Values stay below 2^16, so every
+    partial sum (at most (2^(4n) - 1) * 2^16 < 2^24) is exact."""
+    shape = (4, 4, 4, 5)
+    rng = np.random.default_rng(40 + n)
+    cand = [e for e in itertools.product(range(n + 2), repeat=4) if min(e) < n and sum(e) <= 6]
+    pick = rng.choice(len(cand), size=8, replace=False)
+    mons = [(int(rng.integers(1, 3)), cand[i]) for i in pick]
+    f = _poly_field(shape, mons)
+    assert np.abs(f).max() < 2 ** 16
+    V = f.astype(np.float32)
+    pred = szo.predict_field(V, n)
+    sl = tuple(slice(n, None) for _ in range(4))
+    assert np.array_equal(pred[sl], V[sl])
+    g = _poly_field(shape, [(1, (n, n, n, n))]).astype(np.float32)
+    res = (g - szo.predict_field(g, n))[sl]
+    assert np.all(res == float(factorial(n) ** 4))  # the mixed n-th difference of prod x_a^n
 
 
 def test_additive_field_exact_n1(szo):
