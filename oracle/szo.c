@@ -618,15 +618,18 @@ static iterm_t *make_iterms(int ndim, int layers, int *T_out) {
     return t;
 }
 
-/* integer prediction from lattice values, neighbours outside = 0 */
+/* integer prediction from lattice values, neighbours outside = 0.  Summed
+ * modulo 2^64: exact for every stream the compressor writes (|p| < 2^30,
+ * small coefficients), and free of signed overflow on corrupt input. */
 static int64_t ipredict_at(const int64_t *P, const uint64_t d[3], int64_t i, int64_t j, int64_t l,
                            const iterm_t *t, int T) {
-    int64_t s = 0;
+    uint64_t s = 0;
     for (int q = 0; q < T; q++) {
         int64_t ii = i - t[q].k[0], jj = j - t[q].k[1], ll = l - t[q].k[2];
-        if (ii >= 0 && jj >= 0 && ll >= 0) s += t[q].c * P[((uint64_t)ii * d[1] + (uint64_t)jj) * d[2] + (uint64_t)ll];
+        if (ii >= 0 && jj >= 0 && ll >= 0)
+            s += (uint64_t)t[q].c * (uint64_t)P[((uint64_t)ii * d[1] + (uint64_t)jj) * d[2] + (uint64_t)ll];
     }
-    return s;
+    return (int64_t)s;
 }
 
 /* the lattice integer of x and whether its lattice value is within the
@@ -904,13 +907,13 @@ int szo_decompress(const uint8_t *in, size_t in_len, float *out, size_t out_cap_
                 /* p = r + integer prediction from the earlier lattice values */
                 int64_t ipred = ipredict_at(P, d3, pt[1], pt[2], pt[3], it, T);
                 if (sym != 0) {
-                    P[p] = ipred + (int64_t)(sym - (1 << (m - 1)));
+                    P[p] = (int64_t)((uint64_t)ipred + (uint64_t)(int64_t)(sym - (1 << (m - 1))));
                     out[p] = szo_lattice_value(P[p], eb_f);
                 } else {
                     int64_t ok = get_bits(&br, 1), hi = get_bits(&br, 32), lo = get_bits(&br, 32);
                     if (ok < 0 || hi < 0 || lo < 0) { rc = SZO_ECORRUPT; break; }
                     int64_t res = (int64_t)(((uint64_t)hi << 32) | (uint64_t)lo);
-                    P[p] = ipred + res;
+                    P[p] = (int64_t)((uint64_t)ipred + (uint64_t)res); /* modulo 2^64, as above */
                     if (ok) out[p] = szo_lattice_value(P[p], eb_f);
                     else {
                         int64_t u = get_bits(&br, 32);
