@@ -9,7 +9,9 @@ the import fails: there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes as C
+import json
 import os
+import time
 
 import numpy as np
 
@@ -495,20 +497,35 @@ def decompress_noalloc(stream, out, cuda_stream: int = 0) -> int:
 
 class Server:
     """The serving loop (szgb_server_*): host buffers in, host buffers out.
-    The buffers of a request are kept referenced here until it is done."""
+    The buffers of a request are kept referenced here until it is done.
 
-    def __init__(self, device: int = 0, budget: int = 100 << 30, workers: int = 2, max_batch: int = 64):
+    With `log_path`, one JSON line per completed request is appended there:
+    ticket, op, shape, input and output bytes, status, latency from submit
+    to the completion seen by poll/wait, and for a compressed stream its
+    compression factor, bit-rate (Sec. II, Metric 4), m and unpredictable
+    count from the stream header."""
+
+    def __init__(self, device: int = 0, budget: int = 100 << 30, workers: int = 2, max_batch: int = 64,
+                 log_path: str | None = None):
         self._h = C.c_void_p()
+        self._keep = {}
+        self._meta = {}
+        self._log = None
         rc = lib().szgb_server_create(C.byref(self._h), int(device), int(budget), int(workers), int(max_batch))
         if rc:
             raise SzgbError(rc, "szgb_server_create")
-        self._keep = {}
+        if log_path:
+            self._log = open(log_path, "a")
 
     def close(self):
         if self._h:
             lib().szgb_server_destroy(self._h)
             self._h = C.c_void_p()
             self._keep.clear()
+            self._meta.clear()
+        if self._log is not None:
+            self._log.close()
+            self._log = None
 
     def __del__(self):
         try:
@@ -516,13 +533,32 @@ class Server:
         except Exception:
             pass
 
-    def _submit(self, req, keep):
+    def _submit(self, req, keep, meta):
         t = C.c_uint64()
+        t0 = time.perf_counter()
         rc = lib().szgb_submit(self._h, C.byref(req), C.byref(t))
         if rc:
             raise SzgbError(rc, "szgb_submit")
         self._keep[t.value] = keep
+        meta["t0"] = t0
+        self._meta[t.value] = meta
         return t.value
+
+    def _finish(self, ticket: int, status: int, out_len: int):
+        keep = self._keep.pop(ticket, None)
+        meta = self._meta.pop(ticket, None)
+        if self._log is None or meta is None:
+            return
+        rec = {"ticket": ticket, "op": meta["op"], "shape": meta["shape"], "in_bytes": meta["in_bytes"],
+               "out_bytes": int(out_len), "status": int(status),
+               "latency_s": time.perf_counter() - meta["t0"]}
+        if status == OK and meta["op"] == "compress" and out_len >= 128:
+            n = int(np.prod(meta["shape"], dtype=np.int64))
+            hdr = stream_info_header(keep[1][:128])
+            rec.update(compression_factor=meta["in_bytes"] / out_len, bit_rate=8.0 * out_len / n,
+                       m=int(hdr["m"]), n_unpred=int(np.frombuffer(bytes(keep[1][80:88]), "<u8")[0]))
+        self._log.write(json.dumps(rec) + "\n")
+        self._log.flush()
 
     def submit_compress(self, x: np.ndarray, out: np.ndarray, **kw) -> int:
         """Queue compression of the host float32 array `x` into the host uint8
@@ -536,7 +572,7 @@ class Server:
         r.params = make_params(x.shape, **kw)
         r.out = out.ctypes.data
         r.out_cap = out.nbytes
-        return self._submit(r, (x, out))
+        return self._submit(r, (x, out), {"op": "compress", "shape": list(x.shape), "in_bytes": x.nbytes})
 
     def submit_decompress(self, stream: np.ndarray, out: np.ndarray) -> int:
         """Queue decompression of the host stream into the host float32 array `out`."""
@@ -548,7 +584,8 @@ class Server:
         r.in_bytes = stream.nbytes
         r.out = out.ctypes.data
         r.out_cap = out.nbytes
-        return self._submit(r, (stream, out))
+        return self._submit(r, (stream, out), {"op": "decompress", "shape": list(out.shape),
+                                                "in_bytes": stream.nbytes})
 
     def poll(self, ticket: int):
         """(done, status, out_len); status and out_len are None until done."""
@@ -557,7 +594,7 @@ class Server:
         if rc:
             raise SzgbError(rc, "szgb_poll")
         if d.value:
-            self._keep.pop(ticket, None)
+            self._finish(ticket, st.value, n.value)
             return True, st.value, n.value
         return False, None, None
 
@@ -567,7 +604,7 @@ class Server:
         rc = lib().szgb_wait(self._h, C.c_uint64(ticket), C.byref(st), C.byref(n))
         if rc:
             raise SzgbError(rc, "szgb_wait")
-        self._keep.pop(ticket, None)
+        self._finish(ticket, st.value, n.value)
         return st.value, n.value
 
     def stats(self) -> dict:

@@ -62,3 +62,28 @@ def test_server_completes_every_request_without_gpu(szgb):
             srv.poll(tickets[0])  # released after completion
     finally:
         srv.close()
+
+
+def test_server_request_log(szgb, tmp_path):
+    import json
+    log = tmp_path / "requests.jsonl"
+    srv = szgb.Server(0, budget=64 << 20, workers=1, max_batch=2, log_path=str(log))
+    try:
+        xs = [np.random.default_rng(i).standard_normal((30, 20)).astype(np.float32) for i in range(3)]
+        outs = [np.empty(1 << 16, np.uint8) for _ in xs]
+        tickets = [srv.submit_compress(x, o, eb_rel=1e-3) for x, o in zip(xs, outs)]
+        done = [srv.wait(t) for t in tickets[:2]]
+        while not srv.poll(tickets[2])[0]:
+            pass
+    finally:
+        srv.close()
+    recs = [json.loads(line) for line in log.read_text().splitlines()]
+    assert sorted(r["ticket"] for r in recs) == sorted(tickets)
+    for r in recs:
+        assert r["op"] == "compress" and r["shape"] == [30, 20] and r["in_bytes"] == 30 * 20 * 4
+        assert r["latency_s"] >= 0.0
+        if r["status"] == szgb.OK:  # with a GPU: the stream's own figures
+            assert r["compression_factor"] == pytest.approx(r["in_bytes"] / r["out_bytes"])
+        else:
+            assert r["status"] == szgb.ECUDA and "compression_factor" not in r
+    assert all(st in (szgb.OK, szgb.ECUDA) for st, _ in done)
