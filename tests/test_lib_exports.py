@@ -65,3 +65,27 @@ def test_4d_stream_reported_unsupported(szgb, szo):
     with pytest.raises(szgb.SzgbError) as e:
         szgb.stream_info(s)
     assert e.value.code == szgb.EUNSUPPORTED
+
+
+def test_header_parser_survives_corruption(szgb, szo):
+    # the library's host-side header check (szgb_stream_info) on mutated and
+    # truncated headers: a parsed result or an error code, never a crash, and
+    # a parsed shape always has ndim extents within the declared bounds
+    x = np.random.default_rng(9).normal(size=(5, 7, 9)).astype(np.float32)
+    s = szo.compress(x, eb_rel=1e-3, m=8)
+    rng = np.random.default_rng(10)
+    ok = 0
+    for t in range(3000):
+        m = s.copy()
+        for _ in range(int(rng.integers(1, 4))):
+            m[int(rng.integers(0, 128))] = int(rng.integers(0, 256))
+        cut = int(rng.integers(0, len(m) + 1)) if t % 7 == 0 else len(m)
+        try:
+            info = szgb.stream_info(m[:cut])
+        except szgb.SzgbError as e:
+            assert e.code in (szgb.ECORRUPT, szgb.EUNSUPPORTED)
+            continue
+        ok += 1
+        assert 1 <= info["ndim"] <= 3 and all(1 <= d < 2 ** 32 for d in info["shape"])
+        assert 1 <= info["layers"] <= 4 and 2 <= info["m"] <= 16
+    assert ok > 0
