@@ -27,6 +27,9 @@
  * row holding, for every point, its canonical Huffman code (MSB first) and,
  * after a code 0, the unpredictable value's sign, exponent and top t mantissa
  * bits.  The same bytes are produced by the CPU oracle of the test-suite.
+ * The format also carries 4D fields (the predictor of Sec. III in four
+ * dimensions; the slowest extent at header byte 120); this library does not
+ * decode them and returns SZGB_EUNSUPPORTED for such a stream.
  */
 #ifndef SZGB_H
 #define SZGB_H
