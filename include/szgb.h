@@ -299,6 +299,15 @@ int szgb_server_stats(szgb_server *srv, uint64_t *batches, uint64_t *completed,
 /* Finishes the pending requests, stops the workers and frees the server. */
 void szgb_server_destroy(szgb_server *srv);
 
+/* Algorithm 1, last step (Sec. IV-B): after a compression, the share of
+ * points that fell into one of the 2^m - 1 quantization intervals,
+ * R = (n_points - n_unpred) / n_points, is compared with the threshold
+ * theta; below it a larger m is suggested.  Returns m + 1 (at most 16) when
+ * R < theta, else m, and stores R in *hit_rate_out when it is not NULL.
+ * Host only, no device work.  SZGB_EINVAL for a null st, n_points = 0,
+ * n_unpred > n_points, m outside 2..16 or a NaN theta. */
+int szgb_suggest_m(const szgb_stats *st, double theta, double *hit_rate_out);
+
 /* Reads the header of a stream held in host memory: parameters (with the
  * m actually used) and the number of unpredictable points. */
 int szgb_stream_info(const uint8_t *in_host, size_t in_len, szgb_params *out,

@@ -59,6 +59,22 @@ def hit_rates(x, n: int, mode=szo.REL, eb_abs=0.0, eb_rel=1e-4, m=0, theta=0.99)
             "R_orig": h_orig / N, "R_decomp": h_dec / N, "rec": rec, "codes": codes}
 
 
+def interval_hit_rate(codes) -> float:
+    """Algorithm 1, counting step after the coding (Sec. IV-B): the share of
+    points that fell into one of the 2^m - 1 quantization intervals, i.e.
+    whose code is not the unpredictable code 0."""
+    codes = np.asarray(codes)
+    return float(np.count_nonzero(codes != 0)) / codes.size
+
+
+def suggest_m(codes, m: int, theta: float) -> int:
+    """Algorithm 1, last step (Sec. IV-B): when the interval hit rate stays
+    below theta a larger m is suggested (m + 1, at most 16); otherwise m."""
+    if interval_hit_rate(codes) < theta:
+        return min(m + 1, 16)
+    return m
+
+
 def best_layer_table(x, layers=(1, 2, 3, 4), **kw) -> list:
     """One row per layer count, as in Table 2: (n, R_PH^orig, R_PH^decomp, m)."""
     rows = []

@@ -1566,6 +1566,15 @@ int szgb_decompress(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_dev
     return decompress_impl(c, in, in_len, in_on_device, out, out_cap_elems, out_on_device);
 }
 
+int szgb_suggest_m(const szgb_stats* st, double theta, double* hit_rate_out) {
+    if (!st || st->n_points == 0 || st->n_unpred > st->n_points || st->m < 2 || st->m > 16 || !(theta == theta))
+        return SZGB_EINVAL;
+    // predictable points: those that fell into one of the 2^m - 1 intervals
+    const double rate = (double)(st->n_points - st->n_unpred) / (double)st->n_points;
+    if (hit_rate_out) *hit_rate_out = rate;
+    return (rate < theta && st->m < 16) ? st->m + 1 : st->m;
+}
+
 int szgb_stream_info(const uint8_t* in_host, size_t in_len, szgb_params* out, uint64_t* n_unpred) {
     if (!in_host || !out) return SZGB_EINVAL;
     Header H;

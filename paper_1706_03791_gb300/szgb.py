@@ -98,6 +98,7 @@ def lib():
                                             C.POINTER(sz), C.POINTER(C.c_int)]
         L.szgb_set_graphs.argtypes = [vp, C.c_int]
         L.szgb_quality_dev.argtypes = [vp, vp, vp, sz, C.POINTER(Quality)]
+        L.szgb_suggest_m.argtypes = [C.POINTER(Stats), C.c_double, C.POINTER(C.c_double)]
         L.szgb_hit_count_dev.argtypes = [vp, vp, vp, C.c_int, C.POINTER(C.c_uint64), C.c_int, C.c_double,
                                          C.POINTER(C.c_uint64)]
         L.szgb_autotune.argtypes = [vp, vp, C.POINTER(Params), C.c_int, C.POINTER(C.c_int),
@@ -130,7 +131,7 @@ EXPORTS = ["szgb_create", "szgb_destroy", "szgb_set_stream", "szgb_compress_boun
            "szgb_decompress_noalloc", "szgb_compress_batch", "szgb_decompress_batch", "szgb_set_graphs",
            "szgb_server_create", "szgb_submit", "szgb_poll", "szgb_wait", "szgb_server_stats",
            "szgb_server_destroy", "szgb_autotune", "szgb_autotune_batch", "szgb_tune_save", "szgb_tune_load",
-           "szgb_quality_dev", "szgb_hit_count_dev"]
+           "szgb_quality_dev", "szgb_hit_count_dev", "szgb_suggest_m"]
 
 
 VARIANT_EXACT, VARIANT_LATTICE = 0, 1
@@ -151,6 +152,17 @@ def make_params(shape, mode=REL, eb_abs=0.0, eb_rel=1e-4, layers=1, m=0, theta=0
 def compress_bound(shape, **kw) -> int:
     p = make_params(shape, **kw)
     return int(lib().szgb_compress_bound(C.byref(p)))
+
+
+def suggest_m(stats, theta: float = 0.99):
+    """Algorithm 1, last step: (suggested m, interval hit rate) from the
+    Stats of a compression -- m + 1 (at most 16) when fewer than theta of
+    the points fell into one of the 2^m - 1 intervals, else m."""
+    r = C.c_double()
+    m = lib().szgb_suggest_m(C.byref(stats), float(theta), C.byref(r))
+    if m < 0:
+        raise SzgbError(m, "szgb_suggest_m")
+    return m, r.value
 
 
 def stream_info(stream) -> dict:

@@ -89,3 +89,24 @@ def test_header_parser_survives_corruption(szgb, szo):
         assert 1 <= info["ndim"] <= 3 and all(1 <= d < 2 ** 32 for d in info["shape"])
         assert 1 <= info["layers"] <= 4 and 2 <= info["m"] <= 16
     assert ok > 0
+
+
+def test_suggest_m_matches_oracle(szgb, szo):
+    # Algorithm 1's last step on the host: the library's suggestion from a
+    # compression's counts equals the oracle's from its codes
+    from oracle.hitrate import interval_hit_rate, suggest_m
+    from synthetic import fields
+    x = fields.grf2d(48, 40, seed=12)
+    for m in (2, 3, 6, 10):
+        for theta in (0.5, 0.9, 0.99, 1.0):
+            s, _, codes = szo.compress(x, eb_rel=1e-4, m=m, want_aux=True)
+            h = szo.header(s)
+            st = szgb.Stats()
+            st.n_points, st.n_unpred, st.m = x.size, h["K"], h["m"]
+            got_m, got_r = szgb.suggest_m(st, theta)
+            assert got_r == interval_hit_rate(codes)
+            assert got_m == suggest_m(codes, m, theta)
+    bad = szgb.Stats()
+    bad.n_points, bad.n_unpred, bad.m = 10, 11, 8
+    with pytest.raises(szgb.SzgbError):
+        szgb.suggest_m(bad, 0.9)

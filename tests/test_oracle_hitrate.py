@@ -87,3 +87,21 @@ def test_table2_shape_on_smooth_field():
     r1, r2 = hit_rates(x, 1, eb_rel=1e-4), hit_rates(x, 2, eb_rel=1e-4)
     assert r2["R_orig"] > r1["R_orig"]
     assert r1["R_decomp"] > r2["R_decomp"]
+
+
+def test_interval_hit_rate_and_suggestion():
+    # a field whose prediction errors need more than m = 2's single pair of
+    # side intervals: the rate falls with smaller m and the suggestion asks
+    # for one more bit exactly when the rate is below theta
+    from oracle.hitrate import interval_hit_rate, suggest_m
+    x = fields.grf2d(64, 64, seed=8)
+    rates = {}
+    for m in (2, 4, 8, 12):
+        _, _, codes = szo.compress(x, eb_rel=1e-4, m=m, want_aux=True)
+        r = interval_hit_rate(codes)
+        assert r == 1.0 - np.count_nonzero(codes == 0) / codes.size
+        rates[m] = r
+        assert suggest_m(codes, m, 0.99) == (min(m + 1, 16) if r < 0.99 else m)
+    assert rates[2] < rates[4] < rates[8] <= rates[12]
+    assert suggest_m(np.zeros(10, np.uint16), 16, 0.5) == 16  # no m above 16
+    assert suggest_m(np.ones(10, np.uint16), 3, 1.0) == 3      # every point in an interval
