@@ -180,6 +180,46 @@ def cpu_baseline_sample():
             "sample": "10x500x500 slab of the field, compress+decompress, %d reps, single thread" % reps}
 
 
+def _oracle_round_trip(item):
+    """One field through the oracle, compress then decompress; its bytes."""
+    x, eb = item
+    from oracle import szo
+    s = szo.compress(x, eb_rel=eb, n=1, m=0)
+    szo.decompress(s)
+    return x.nbytes
+
+
+def _noop(_):
+    return 0
+
+
+def cpu_baseline_fields(items, budget_s=8.0, workers=None):
+    """The oracle, as it stands, on independent fields (the paper's parallel
+    mode: processes without communication): single thread over the fields in
+    order until about budget_s, then the same fields spread over a spawned
+    process pool on every host core (workers started before timing).  Both
+    figures count input bytes twice (compress + decompress), as the GPU line
+    does."""
+    import multiprocessing as mp
+    t0 = time.perf_counter()
+    k, nb = 0, 0
+    while k < len(items) and (k == 0 or time.perf_counter() - t0 < budget_s):
+        nb += _oracle_round_trip(items[k])
+        k += 1
+    single = 2 * nb / (time.perf_counter() - t0) / 1e9
+    workers = workers or os.cpu_count() or 1
+    sample = items[:max(k, min(len(items), workers))]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        pool.map(_noop, range(workers), chunksize=1)  # start the workers and import numpy there
+        t1 = time.perf_counter()
+        nb_all = sum(pool.map(_oracle_round_trip, sample, chunksize=1))
+        dt = time.perf_counter() - t1
+    return {"value": single, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": "first %d fields of the batch, compress+decompress, single thread" % k,
+            "all_cores": {"value": 2 * nb_all / dt / 1e9, "unit": "GB/s", "cores": workers,
+                          "sample": "first %d fields, one field per task, spawned process pool" % len(sample)}}
+
+
 def run_batch_workload(args):
     """Many independent fields: the batched path (one persistent wavefront
     launch per pass, captured in a CUDA graph) against one compress and one
@@ -212,6 +252,12 @@ def run_batch_workload(args):
     kws = [dict(eb_rel=eb, layers=args.layers, m=0) for _, eb in items]
     nbytes = sum(x.numel() * 4 for x in xs)
     npts = sum(x.numel() for x in xs)
+    cpu_items = []
+    if not args.no_cpu_baseline and rank == 0:  # a bounded sample, at most ~1.5 GB of fields
+        for it in items:
+            if cpu_items and sum(x.nbytes for x, _ in cpu_items) + it[0].nbytes > 1.5e9:
+                break
+            cpu_items.append(it)
     del items
     ctx = szgb.Context(local)
     stream = torch.cuda.Stream(device=dev)
@@ -283,6 +329,7 @@ def run_batch_workload(args):
             dist.barrier()
             return
     val = 2 * nbytes / ((bc + bd) / 1e3) / 1e9
+    cpu = cpu_baseline_fields(cpu_items) if cpu_items else None  # after the GPU timing
     line = {"metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": bc + bd, "higher_is_better": True,
             "scaling": "strong" if ws > 1 else "weak",
@@ -300,6 +347,7 @@ def run_batch_workload(args):
                          "note": "algorithmic bytes of the whole pass (compress 6 B/pt + range read; "
                                  "decompress stream + 4 B/pt) over the pass time"},
             "autotune": {"W": tuned["W"], "seconds": tune_s},
+            "cpu_baseline": cpu,
             "clocks": clk, "generate_s": gen_s,
             "parallelism": "fields sharded over %d ranks (largest first), no collective" % ws if ws > 1 else "single"}
     print(json.dumps(line), flush=True)
