@@ -67,8 +67,9 @@ typedef struct {
     int mode;           /* SZGB_ABS / SZGB_REL / SZGB_ABS_AND_REL */
     double eb_abs;      /* absolute bound (>= 0), modes ABS, ABS_AND_REL */
     double eb_rel;      /* relative bound (>= 0) times (max - min) */
-    int layers;         /* n of the n-layer predictor; 1 or 2 on the GPU
-                           (Sec. III-B; the paper's default is 1) */
+    int layers;         /* n of the n-layer predictor (Sec. III-B; the
+                           paper's default is 1): 1..4 for 1D and 2D
+                           fields, 1..2 for 3D fields */
     int m;              /* 2..16: 2^m - 1 intervals; 0 = adaptive (Sec. IV-B) */
     double theta;       /* adaptive-m hit-rate threshold, e.g. 0.99 */
     int variant;        /* SZGB_VARIANT_EXACT (0): the paper's method;
@@ -291,7 +292,9 @@ int szgb_submit(szgb_server *srv, const szgb_request *req, uint64_t *ticket);
  * SZGB_E* code) and *out_len (stream bytes, or 4 x points) are set and the
  * ticket is released. */
 int szgb_poll(szgb_server *srv, uint64_t ticket, int *done, int *status, size_t *out_len);
-/* Blocks until the request finished; then as szgb_poll with *done = 1. */
+/* Blocks until the request finished; then as szgb_poll with *done = 1.
+ * When another thread takes the result of the same ticket first (by poll
+ * or wait), returns SZGB_EINVAL. */
 int szgb_wait(szgb_server *srv, uint64_t ticket, int *status, size_t *out_len);
 /* Batches run, requests completed, and the peak admitted footprint. */
 int szgb_server_stats(szgb_server *srv, uint64_t *batches, uint64_t *completed,

@@ -307,10 +307,16 @@ int szgb_poll(szgb_server* S, uint64_t ticket, int* done, int* status, size_t* o
 int szgb_wait(szgb_server* S, uint64_t ticket, int* status, size_t* out_len) {
     if (!S) return SZGB_EINVAL;
     std::unique_lock<std::mutex> lk(S->mu);
+    if (S->reqs.find(ticket) == S->reqs.end()) return SZGB_EINVAL;
+    // look the ticket up again on every wake-up: another caller may have
+    // taken the result (and freed the request) meanwhile
+    S->cv_done.wait(lk, [&] {
+        auto jt = S->reqs.find(ticket);
+        return jt == S->reqs.end() || jt->second->done;
+    });
     auto it = S->reqs.find(ticket);
     if (it == S->reqs.end()) return SZGB_EINVAL;
     Req* q = it->second;
-    S->cv_done.wait(lk, [&] { return q->done; });
     if (status) *status = q->status;
     if (out_len) *out_len = q->out_len;
     S->reqs.erase(it);

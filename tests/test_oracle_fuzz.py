@@ -2,7 +2,7 @@
 UndefinedBehaviorSanitizer: corrupted and truncated streams of the exact
 method (1D..4D) and of the lattice variant either decode within the declared
 shape or return an error code, with no invalid access and no undefined
-behaviour (the driver is tests/fuzz/oracle_fuzz.c)."""
+behaviour (the driver is tests/native/oracle_fuzz.c)."""
 import os
 import shutil
 import subprocess
@@ -21,7 +21,7 @@ def fuzz_bin(tmp_path_factory):
     out = str(tmp_path_factory.mktemp("fuzz") / "oracle_fuzz")
     cmd = [gcc, "-std=c11", "-O1", "-g", "-ffp-contract=off", "-fno-fast-math",
            "-fsanitize=address,undefined", "-fno-sanitize-recover=all",
-           "-o", out, os.path.join(ROOT, "oracle", "szo.c"), os.path.join(HERE, "fuzz", "oracle_fuzz.c"), "-lm"]
+           "-o", out, os.path.join(ROOT, "oracle", "szo.c"), os.path.join(HERE, "native", "oracle_fuzz.c"), "-lm"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         if "sanitize" in (r.stderr or "") or "asan" in (r.stderr or ""):
