@@ -68,8 +68,9 @@ typedef struct {
     double eb_abs;      /* absolute bound (>= 0), modes ABS, ABS_AND_REL */
     double eb_rel;      /* relative bound (>= 0) times (max - min) */
     int layers;         /* n of the n-layer predictor (Sec. III-B; the
-                           paper's default is 1): 1..4 for 1D and 2D
-                           fields, 1..2 for 3D fields */
+                           paper's default is 1): 1..4; batches, the
+                           autotuner and szgb_decompress_noalloc take 3D
+                           fields up to n = 2 */
     int m;              /* 2..16: 2^m - 1 intervals; 0 = adaptive (Sec. IV-B) */
     double theta;       /* adaptive-m hit-rate threshold, e.g. 0.99 */
     int variant;        /* SZGB_VARIANT_EXACT (0): the paper's method;
@@ -120,8 +121,9 @@ size_t szgb_compress_bound(const szgb_params *p);
  * device, out_cap bytes).  *out_len receives the stream size, also when
  * SZGB_ETRUNC reports that out_cap is too small.  opt_stats may be NULL.
  * Fails with SZGB_ENONFINITE on NaN/Inf input, SZGB_EINVAL on bad
- * parameters, SZGB_EUNSUPPORTED for a layer count the wavefront does not
- * carry (1D and 2D fields take layers 1..4, 3D fields 1..2). */
+ * parameters.  Layers 1..4 in every dimension: 3D fields with n = 3, 4 run
+ * on hyperplane kernels (one launch per hyperplane), everything else on the
+ * wavefront. */
 int szgb_compress(szgb_ctx *ctx, const float *data, int data_on_device,
                   const szgb_params *p, uint8_t *out, size_t out_cap,
                   int out_on_device, size_t *out_len, szgb_stats *opt_stats);
@@ -173,15 +175,17 @@ int szgb_decompress_noalloc(const uint8_t *in_dev, size_t in_len, float *out_dev
  * capacities, parameters) repeat (szgb_set_graphs(ctx, 0) launches directly
  * instead).  out_len[i] receives each stream size, also on SZGB_ETRUNC;
  * opt_stats is NULL or holds count entries.  Returns 0 or the error of the
- * first field that failed. */
+ * first field that failed; SZGB_EUNSUPPORTED for the lattice variant and for
+ * 3D fields with n > 2 (single-field calls take those). */
 int szgb_compress_batch(szgb_ctx *ctx, int count, const float *const *data_dev,
                         const szgb_params *params, uint8_t *const *out_dev,
                         const size_t *out_cap, size_t *out_len, szgb_stats *opt_stats);
 
 /* Batched decompression: stream i (in_dev[i], in_len[i] bytes, 4-byte
  * aligned) into out_dev[i] (out_cap_elems[i] floats, 16-byte aligned), all
- * device memory; one persistent wavefront launch as above.  opt_status is
- * NULL or receives count per-field codes. */
+ * device memory; one persistent wavefront launch as above (the same
+ * SZGB_EUNSUPPORTED cases).  opt_status is NULL or receives count per-field
+ * codes. */
 int szgb_decompress_batch(szgb_ctx *ctx, int count, const uint8_t *const *in_dev,
                           const size_t *in_len, float *const *out_dev,
                           const size_t *out_cap_elems, int *opt_status);
@@ -194,7 +198,9 @@ int szgb_decompress_batch(szgb_ctx *ctx, int count, const uint8_t *const *in_dev
  * it.  The shape changes the schedule only: streams and reconstructions are
  * identical for every candidate.  *W_out and *ms_out (may be NULL) receive
  * the choice and its time; *pub_out is set to 0 (a former progress
- * publication interval: the wavefront no longer publishes progress). */
+ * publication interval: the wavefront no longer publishes progress).
+ * SZGB_EUNSUPPORTED for 3D fields with n > 2, which do not run on the
+ * wavefront. */
 int szgb_autotune(szgb_ctx *ctx, const float *data_dev, const szgb_params *p, int reps,
                   int *W_out, int *pub_out, double *ms_out);
 /* As szgb_autotune for a batch: times szgb_compress_batch +
@@ -286,7 +292,8 @@ int szgb_server_create(szgb_server **out, int device, size_t device_mem_budget,
                        int workers, int max_batch);
 /* Queues a request; the caller keeps `in` and `out` valid and untouched
  * until the request is done.  *ticket identifies it.  SZGB_EBUDGET when the
- * request alone exceeds the budget. */
+ * request alone exceeds the budget; SZGB_EUNSUPPORTED for what the batched
+ * path does not carry (the lattice variant, 3D fields with n > 2). */
 int szgb_submit(szgb_server *srv, const szgb_request *req, uint64_t *ticket);
 /* Non-blocking: *done = 1 once the request finished; then *status (its
  * SZGB_E* code) and *out_len (stream bytes, or 4 x points) are set and the

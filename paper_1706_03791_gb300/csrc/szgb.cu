@@ -156,8 +156,9 @@ int check_params(const szgb_params* p, CallParams* cp) {
     cp->theta = p->theta;
     if (p->variant != SZGB_VARIANT_EXACT && p->variant != SZGB_VARIANT_LATTICE) return SZGB_EINVAL;
     cp->variant = p->variant;
-    // the lattice variant is built for n <= 2
-    if (!layers_supported(p->ndim, p->layers) || (p->variant == SZGB_VARIANT_LATTICE && p->layers > 2))
+    // the lattice variant is built for n <= 2; batched, autotuned and
+    // no-allocation calls check the wavefront's set (layers_supported) too
+    if (!layers_single(p->ndim, p->layers) || (p->variant == SZGB_VARIANT_LATTICE && p->layers > 2))
         return SZGB_EUNSUPPORTED;
     return SZGB_OK;
 }
@@ -274,8 +275,10 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
     CallParams cp;
     int rc = check_params(p, &cp);
     if (rc) return rc;
-    if (one_field_batched(c) && !rec_dev && !codes_dev && cp.variant == SZGB_VARIANT_EXACT && data_on_device &&
-        out_on_device && ((uintptr_t)data % 16) == 0 && ((uintptr_t)out % 4) == 0) {
+    // 3D fields with n = 3, 4: the hyperplane kernels instead of the wavefront
+    const bool hyper = cp.variant == SZGB_VARIANT_EXACT && !layers_supported(cp.ndim, cp.layers);
+    if (one_field_batched(c) && !hyper && !rec_dev && !codes_dev && cp.variant == SZGB_VARIANT_EXACT &&
+        data_on_device && out_on_device && ((uintptr_t)data % 16) == 0 && ((uintptr_t)out % 4) == 0) {
         const float* d1[1] = {data};
         uint8_t* o1[1] = {out};
         const size_t cap1[1] = {out_cap};
@@ -290,6 +293,7 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
     WaveGeom g = make_geom(c, cp, layers);
     size_t hrow, hplane;
     halo_sizes(g, layers, &hrow, &hplane);
+    if (hyper) hrow = hplane = 0;  // no halo exchange: neighbours come from the recorded values
     const size_t bound = szgb_compress_bound(p);
     const bool direct_out = out_on_device && ((uintptr_t)out % 4 == 0) && out_cap >= bound;
     const bool direct_in = data_on_device && ((uintptr_t)data % 16 == 0);
@@ -332,6 +336,8 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
     else xs = nullptr;
     if (!direct_out) A.add(&ostage, bound);
     else ostage = nullptr;
+    float* hvals = rec_dev;  // the hyperplane path's recorded values
+    if (hyper && !rec_dev) A.add(&hvals, N);
     rc = ensure_scratch(c, A.total);
     if (rc) return rc;
     A.bind(c->scratch);
@@ -366,7 +372,9 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
     }
     if (cp.variant == SZGB_VARIANT_EXACT) {
         PhaseTimer t(c, PH_WAVE_C);
-        if (!rec_dev) {
+        if (hyper) {
+            if ((rc = launch_hyper_compress(layers, x, hvals, codes, cpitch, cp.d0, cp.d1, cp.d2, st, s))) return rc;
+        } else if (!rec_dev) {
             // the persistent kernel, items in ready-time order
             ArgsBuf ha(wave_args_bytes());
             wave_args_compress(ha.p, g, x, codes, cpitch, halo_row, halo_plane, prog, st, c->timeout_ns);
@@ -518,11 +526,13 @@ int decompress_impl(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_dev
     Header H;
     int rc = parse_header(hbuf, in_len, &H);
     if (rc) return rc;
-    if (!layers_supported(H.ndim, H.layers) || (H.variant == SZGB_VARIANT_LATTICE && H.layers > 2))
+    if (!layers_single(H.ndim, H.layers) || (H.variant == SZGB_VARIANT_LATTICE && H.layers > 2))
         return SZGB_EUNSUPPORTED;
+    // 3D fields with n = 3, 4: the hyperplane kernels instead of the wavefront
+    const bool hyper = H.variant == SZGB_VARIANT_EXACT && !layers_supported(H.ndim, H.layers);
     const uint64_t N = H.d0 * H.d1 * H.d2;
     if (out_cap_elems < N) return SZGB_EINVAL;
-    if (one_field_batched(c) && H.variant == SZGB_VARIANT_EXACT && in_on_device && out_on_device &&
+    if (one_field_batched(c) && !hyper && H.variant == SZGB_VARIANT_EXACT && in_on_device && out_on_device &&
         ((uintptr_t)in % 4) == 0 && ((uintptr_t)out % 16) == 0)
         return decompress_batch_impl(c, 1, &in, &in_len, &out, &out_cap_elems, nullptr, hbuf);
     const uint64_t rows = H.nchunks;
@@ -535,6 +545,7 @@ int decompress_impl(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_dev
     WaveGeom g = make_geom(c, cp, H.layers);
     size_t hrow, hplane;
     halo_sizes(g, H.layers, &hrow, &hplane);
+    if (hyper) hrow = hplane = 0;  // no halo exchange: neighbours come from the output
     const bool direct_in = in_on_device && ((uintptr_t)in % 4 == 0);
     const bool direct_out = out_on_device && ((uintptr_t)out % 16 == 0);
     DevState* st;
@@ -627,13 +638,18 @@ int decompress_impl(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_dev
                 return rc;
         }
         PhaseTimer t(c, PH_WAVE_D);
-        ArgsBuf ha(wave_args_bytes());
-        if ((rc = wave_args_decompress(ha.p, g, codes, cpitch, dst, halo_row, halo_plane, prog, st, c->timeout_ns)))
-            return rc;
-        if ((rc = ensure_pinned(c, align_up(wave_args_bytes(), 256) + 8 * (size_t)g.num_ctas))) return rc;
-        if ((rc = launch_wave_one(c, g, H.layers, true, ha.p, static_cast<char*>(c->h_batch), wargs, worder,
-                                  wticket, s)))
-            return rc;
+        if (hyper) {
+            if ((rc = launch_hyper_decompress(H.layers, codes, cpitch, dst, H.d0, H.d1, H.d2, st, s))) return rc;
+        } else {
+            ArgsBuf ha(wave_args_bytes());
+            if ((rc = wave_args_decompress(ha.p, g, codes, cpitch, dst, halo_row, halo_plane, prog, st,
+                                           c->timeout_ns)))
+                return rc;
+            if ((rc = ensure_pinned(c, align_up(wave_args_bytes(), 256) + 8 * (size_t)g.num_ctas))) return rc;
+            if ((rc = launch_wave_one(c, g, H.layers, true, ha.p, static_cast<char*>(c->h_batch), wargs, worder,
+                                      wticket, s)))
+                return rc;
+        }
     }
     if (cudaMemcpyAsync(c->h_state, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return SZGB_ECUDA;
@@ -823,6 +839,7 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
         if (!data[f] || !out[f] || ((uintptr_t)data[f] % 16) || ((uintptr_t)out[f] % 4)) return SZGB_EINVAL;
         if ((rc = check_params(&params[f], &q.cp))) return rc;
         if (q.cp.variant != SZGB_VARIANT_EXACT) return SZGB_EUNSUPPORTED;  // batches run the paper's method
+        if (!layers_supported(q.cp.ndim, q.cp.layers)) return SZGB_EUNSUPPORTED;  // ... on the wavefront
         q.n = q.cp.d0 * q.cp.d1 * q.cp.d2;
         q.rows = q.cp.d0 * q.cp.d1;
         q.rowlen = q.cp.d2;
@@ -1288,6 +1305,7 @@ int szgb_autotune(szgb_ctx* c, const float* data_dev, const szgb_params* p, int 
     if (!c || !data_dev || !p) return SZGB_EINVAL;
     int rc = check_params(p, &cp);
     if (rc) return rc;
+    if (!layers_supported(cp.ndim, cp.layers)) return SZGB_EUNSUPPORTED;  // it tunes the wavefront
     if (cudaSetDevice(c->device) != cudaSuccess) return SZGB_ECUDA;
     if (reps < 1) reps = 1;
     const uint64_t N = cp.d0 * cp.d1 * cp.d2;
@@ -1360,6 +1378,7 @@ int szgb_autotune_batch(szgb_ctx* c, int count, const float* const* data_dev, co
     int maxl = 1;
     for (int f = 0; f < count && !rc; f++) {
         rc = check_params(&params[f], &cps[f]);
+        if (rc == SZGB_OK && !layers_supported(cps[f].ndim, cps[f].layers)) rc = SZGB_EUNSUPPORTED;
         if (rc) break;
         any3 |= cps[f].ndim == 3;
         maxl = std::max(maxl, cps[f].layers);

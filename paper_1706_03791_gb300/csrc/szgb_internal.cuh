@@ -16,10 +16,16 @@ namespace szgb {
 
 constexpr int kHeaderBytes = 128;
 constexpr int kTile = 4;           // columns per sweep and lane (one float4)
-constexpr int kMaxLayers = 4;      // n supported by the GPU kernels in 1D and 2D
-constexpr int kMaxLayers3D = 2;    // and in 3D (a 3D lane keeps (n+1)^3 - 1 neighbour values)
+constexpr int kMaxLayers = 4;      // n supported by the GPU kernels in 1D, 2D and 3D
+constexpr int kMaxLayers3D = 2;    // n the 3D wavefront carries (a lane keeps (n+1)^3 - 1 values)
+// layer counts the wavefront kernels (single, batched, no-allocation) carry
 __host__ __device__ inline bool layers_supported(int ndim, int layers) {
     return layers >= 1 && layers <= (ndim == 3 ? kMaxLayers3D : kMaxLayers);
+}
+// layer counts the single-field calls carry: the wavefront's, plus 3D fields
+// with n = 3, 4 through the hyperplane kernels (k_hyper.cu)
+__host__ __device__ inline bool layers_single(int ndim, int layers) {
+    return layers >= 1 && layers <= kMaxLayers && ndim >= 1 && ndim <= 3;
 }
 constexpr int kLutBits = 11;       // decoder lookup-table index bits
 constexpr int kMaxWaveWarps = 8;   // compute warps per wavefront CTA (plus one halo warp)
@@ -451,6 +457,11 @@ struct WaveGeom {
 int launch_range(const float* x, uint64_t n, DevState* st, const CallParams& cp, float* partials,
                  int nblocks, cudaStream_t s);
 int launch_adapt(const float* x, const CallParams& cp, DevState* st, cudaStream_t s);
+// 3D fields with n = 3, 4 layers, one launch per hyperplane (k_hyper.cu)
+int launch_hyper_compress(int layers, const float* x, float* V, uint16_t* codes, uint64_t cpitch, uint64_t P,
+                          uint64_t M, uint64_t N, const DevState* st, cudaStream_t s);
+int launch_hyper_decompress(int layers, uint16_t* codes, uint64_t cpitch, float* out, uint64_t P, uint64_t M,
+                            uint64_t N, const DevState* st, cudaStream_t s);
 // prediction hits |x - f(V)| <= eb over a d0 x d1 x d2 field, added to *count
 int launch_hits(const float* x, const float* V, uint64_t d0, uint64_t d1, uint64_t d2, int ndim, int layers,
                 double eb, unsigned long long* count, int sm_count, cudaStream_t s);

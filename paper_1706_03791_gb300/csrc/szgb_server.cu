@@ -61,6 +61,13 @@ struct szgb_server {
 
 namespace {
 
+// requests run as batches, which carry the paper's method on the wavefront:
+// 3D fields up to n = 2 layers, 1D and 2D fields up to n = 4; anything else
+// is refused at submission rather than failing the batch it would join
+bool batch_carries(const szgb_params& p) {
+    return p.variant == SZGB_VARIANT_EXACT && p.layers >= 1 && p.layers <= (p.ndim == 3 ? 2 : 4);
+}
+
 // device scratch the library needs for one field, beyond its I/O buffers
 // (codes 2 B/pt, halos, per-row tables; Huffman tables 3.6 MB per field)
 size_t scratch_estimate(int op, uint64_t n_points) {
@@ -239,6 +246,10 @@ int szgb_submit(szgb_server* S, const szgb_request* r, uint64_t* ticket) {
             delete q;
             return SZGB_EINVAL;
         }
+        if (!batch_carries(p)) {
+            delete q;
+            return SZGB_EUNSUPPORTED;
+        }
         uint64_t n = 1;
         for (int a = 0; a < p.ndim; a++) n *= p.shape[a];
         const size_t bound = szgb_compress_bound(&p);
@@ -255,6 +266,7 @@ int szgb_submit(szgb_server* S, const szgb_request* r, uint64_t* ticket) {
         szgb_params p;
         uint64_t k = 0;
         int rc = szgb_stream_info(static_cast<const uint8_t*>(r->in), r->in_bytes, &p, &k);
+        if (rc == SZGB_OK && !batch_carries(p)) rc = SZGB_EUNSUPPORTED;
         if (rc) {
             delete q;
             return rc;

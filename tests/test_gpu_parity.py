@@ -139,9 +139,9 @@ def test_errors(ctx, szo):
     with pytest.raises(szgb.SzgbError) as e:
         ctx.compress(x, out=small, eb_rel=1e-3, m=8)
     assert e.value.code == szgb.ETRUNC
-    x3 = fields.blobs3d(6, 20, 24, seed=52, nblobs=3)
-    with pytest.raises(szgb.SzgbError) as e:  # 3D keeps n <= 2 on the GPU
-        ctx.compress(x3, eb_rel=1e-3, m=8, layers=3)
+    x3 = torch.from_numpy(fields.blobs3d(6, 20, 24, seed=52, nblobs=3)).cuda()
+    with pytest.raises(szgb.SzgbError) as e:  # batches keep 3D at n <= 2 (refused before any launch)
+        ctx.compress_batch([x3], dict(eb_rel=1e-3, m=8, layers=3))
     assert e.value.code == szgb.EUNSUPPORTED
     # the context stays usable after errors
     _check(ctx, szo, x, eb_rel=1e-3, m=8)

@@ -87,3 +87,17 @@ def test_server_request_log(szgb, tmp_path):
         else:
             assert r["status"] == szgb.ECUDA and "compression_factor" not in r
     assert all(st in (szgb.OK, szgb.ECUDA) for st, _ in done)
+
+
+def test_server_refuses_what_batches_do_not_carry(szgb):
+    # 3D fields with n > 2 and the lattice variant run as single-field calls
+    # only; the server refuses them at submission instead of failing a batch
+    srv = szgb.Server(0, budget=64 << 20, workers=1, max_batch=2)
+    try:
+        x3 = np.zeros((6, 8, 10), np.float32)
+        for kw in (dict(layers=3), dict(layers=4), dict(layers=1, variant=szgb.VARIANT_LATTICE)):
+            with pytest.raises(szgb.SzgbError) as e:
+                srv.submit_compress(x3, np.empty(1 << 16, np.uint8), eb_rel=1e-3, **kw)
+            assert e.value.code == szgb.EUNSUPPORTED
+    finally:
+        srv.close()
