@@ -65,8 +65,9 @@ __global__ void __launch_bounds__(kHyperThreads) k_hyper(const float* __restrict
         const int code = codes[row * cpitch + (uint64_t)l];
         if (code) V[p] = dequantize(code, pred, qp);
     } else {
+        const float xv = x[p];
         float rec;
-        const int code = quantize(x[p], pred, qp, rec);
+        const int code = quantize_tr(xv, pred, trunc_value(xv, qp.e_eb), qp, rec);  // as the wavefront
         V[p] = rec;
         codes[row * cpitch + (uint64_t)l] = (uint16_t)code;
     }
