@@ -48,10 +48,12 @@ class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
     def __init__(self, index):
+        import tempfile
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else "/tmp/szgb_clocks.csv"
+        # the raw samples go to $SZGB_CLOCKS_CSV when set (to keep them), else a temporary file
+        self.path = os.environ.get("SZGB_CLOCKS_CSV") or os.path.join(
+            tempfile.gettempdir(), "szgb_clocks_%d_%d.csv" % (os.getpid(), index))
 
     def start(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
