@@ -28,8 +28,8 @@
  * after a code 0, the unpredictable value's sign, exponent and top t mantissa
  * bits.  The same bytes are produced by the CPU oracle of the test-suite.
  * The format also carries 4D fields (the predictor of Sec. III in four
- * dimensions; the slowest extent at header byte 120); this library does not
- * decode them and returns SZGB_EUNSUPPORTED for such a stream.
+ * dimensions; the slowest extent at header byte 120): szgb_compress_4d
+ * writes them and szgb_decompress reads them.
  */
 #ifndef SZGB_H
 #define SZGB_H
@@ -136,6 +136,23 @@ int szgb_compress_trace(szgb_ctx *ctx, const float *data_dev, const szgb_params 
                         uint8_t *out_dev, size_t out_cap, size_t *out_len,
                         szgb_stats *opt_stats, float *recorded_dev,
                         uint16_t *codes_dev);
+
+/* 4D fields (Sec. III: the n-layer predictor of Eq. predmodel with d = 4;
+ * quantization and coding as for 1D-3D).  Compresses the device array
+ * data_dev of shape[0..3] (slowest first; each extent 1..2^32-1, shape[0] x
+ * shape[1] and the point count below 2^32; 16-byte aligned) with the bound,
+ * layers (1..4), m and theta of p (p->ndim, p->shape ignored; the exact
+ * variant only).  out_dev (device, 4-byte aligned) takes out_cap bytes; the
+ * stream never exceeds szgb_compress_bound of the 3D view
+ * (shape[0] shape[1], shape[2], shape[3]).  recorded_dev and codes_dev are
+ * NULL or device arrays of one entry per point as in szgb_compress_trace.
+ * The stream's header says ndim = 4 and keeps shape[0] at byte 120;
+ * szgb_decompress decodes it (szgb_stream_info, the batched and the
+ * no-allocation calls return SZGB_EUNSUPPORTED for it).  Runs on hyperplane
+ * kernels, one launch per i0 + i + j + l = h.  Errors as szgb_compress. */
+int szgb_compress_4d(szgb_ctx *ctx, const float *data_dev, const uint64_t *shape,
+                     const szgb_params *p, uint8_t *out_dev, size_t out_cap, size_t *out_len,
+                     szgb_stats *opt_stats, float *recorded_dev, uint16_t *codes_dev);
 
 /* Decompresses `in` (host or device, in_len bytes) into `out` (host or
  * device; out_cap_elems floats, at least the number of points).

@@ -37,4 +37,30 @@ SZGB_HD HyperBox hyper_box(int64_t h, int64_t P, int64_t M, int64_t N) {
     return b;
 }
 
+// The box of hyperplane h = i0 + i + j + l of a D x P x M x N field, as
+// (i0, i, j) triples with l = h - i0 - i - j; an entry is a point iff
+// 0 <= l < N.  0 <= h <= (D-1) + (P-1) + (M-1) + (N-1); all extents >= 1.
+struct HyperBox4 {
+    int64_t alo, ilo, jlo;  // first i0, i, j of the box
+    uint64_t na, ni, nj;    // extents; t -> (alo + t / (ni nj), ilo + (t / nj) % ni, jlo + t % nj)
+};
+
+SZGB_HD HyperBox4 hyper_box4(int64_t h, int64_t D, int64_t P, int64_t M, int64_t N) {
+    HyperBox4 b;
+    const int64_t rest3 = (P - 1) + (M - 1) + (N - 1), rest2 = (M - 1) + (N - 1);
+    const int64_t alo = h - rest3 > 0 ? h - rest3 : 0;
+    const int64_t ahi = h < D - 1 ? h : D - 1;
+    const int64_t ilo = h - ahi - rest2 > 0 ? h - ahi - rest2 : 0;
+    const int64_t ihi = h - alo < P - 1 ? h - alo : P - 1;
+    const int64_t jlo = h - ahi - ihi - (N - 1) > 0 ? h - ahi - ihi - (N - 1) : 0;
+    const int64_t jhi = h - alo - ilo < M - 1 ? h - alo - ilo : M - 1;
+    b.alo = alo;
+    b.ilo = ilo;
+    b.jlo = jlo;
+    b.na = ahi >= alo ? (uint64_t)(ahi - alo + 1) : 0;
+    b.ni = ihi >= ilo ? (uint64_t)(ihi - ilo + 1) : 0;
+    b.nj = jhi >= jlo ? (uint64_t)(jhi - jlo + 1) : 0;
+    return b;
+}
+
 #endif

@@ -267,16 +267,18 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
 // direct path.
 bool one_field_batched(const szgb_ctx* c) { return c->use_graphs && !c->profiling && !c->force_W; }
 
+// D4 != 0: a 4D field D4 x P x M x N given as its (D4 P) x M x N view in p
 int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb_params* p, uint8_t* out,
                   size_t out_cap, int out_on_device, size_t* out_len, szgb_stats* stats, float* rec_dev,
-                  uint16_t* codes_dev) {
+                  uint16_t* codes_dev, uint64_t D4 = 0) {
     if (!c || !data || !out_len) return SZGB_EINVAL;
     if (((uintptr_t)rec_dev % 16) != 0 || ((uintptr_t)codes_dev % 8) != 0) return SZGB_EINVAL;
     CallParams cp;
     int rc = check_params(p, &cp);
     if (rc) return rc;
-    // 3D fields with n = 3, 4: the hyperplane kernels instead of the wavefront
-    const bool hyper = cp.variant == SZGB_VARIANT_EXACT && !layers_supported(cp.ndim, cp.layers);
+    // 3D fields with n = 3, 4, and 4D fields: the hyperplane kernels instead of the wavefront
+    if (D4 && (cp.ndim != 3 || cp.variant != SZGB_VARIANT_EXACT || cp.d0 % D4 != 0)) return SZGB_EINVAL;
+    const bool hyper = D4 || (cp.variant == SZGB_VARIANT_EXACT && !layers_supported(cp.ndim, cp.layers));
     if (one_field_batched(c) && !hyper && !rec_dev && !codes_dev && cp.variant == SZGB_VARIANT_EXACT &&
         data_on_device && out_on_device && ((uintptr_t)data % 16) == 0 && ((uintptr_t)out % 4) == 0) {
         const float* d1[1] = {data};
@@ -368,11 +370,18 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
         if ((rc = launch_lattice_compress(x, cp, latP, latOK, codes, cpitch, rec_dev, st, s))) return rc;
     } else if (cp.m_user == 0) {
         PhaseTimer t(c, PH_ADAPT);
-        if ((rc = launch_adapt(x, cp, st, s))) return rc;
+        if (D4) {
+            if ((rc = launch_adapt4(x, D4, cp.d0 / D4, cp.d1, cp.d2, layers, cp.theta, st, s))) return rc;
+        } else if ((rc = launch_adapt(x, cp, st, s))) {
+            return rc;
+        }
     }
     if (cp.variant == SZGB_VARIANT_EXACT) {
         PhaseTimer t(c, PH_WAVE_C);
-        if (hyper) {
+        if (D4) {
+            if ((rc = launch_hyper4(false, layers, x, hvals, codes, cpitch, D4, cp.d0 / D4, cp.d1, cp.d2, st, s)))
+                return rc;
+        } else if (hyper) {
             if ((rc = launch_hyper_compress(layers, x, hvals, codes, cpitch, cp.d0, cp.d1, cp.d2, st, s))) return rc;
         } else if (!rec_dev) {
             // the persistent kernel, items in ready-time order
@@ -408,6 +417,7 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
         if ((rc = launch_encode(codes, cpitch, x, rows, rowlen, len, cw, rowoff, dst, st, s, latP, latOK, cp.ndim,
                                 layers, cp.d1)))
             return rc;
+        if (D4 && (rc = launch_patch_header4(dst, D4, cp.d0 / D4, st, s))) return rc;
     }
     if (codes_dev && cudaMemcpy2DAsync(codes_dev, rowlen * 2, codes, cpitch * 2, rowlen * 2, rows,
                                        cudaMemcpyDeviceToDevice, s) != cudaSuccess)
@@ -523,13 +533,31 @@ int decompress_impl(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_dev
     } else {
         memcpy(hbuf, in, kHeaderBytes);
     }
+    // a 4D stream (D x P x M x N; D at byte 120) is checked and decoded as its
+    // (D P) x M x N view, then reconstructed over the 4D hyperplanes
+    uint8_t h3[kHeaderBytes];
+    const uint8_t* hp = hbuf;
+    uint64_t D4 = 0;
+    if (hbuf[8] == 4 && hbuf[113] == 0) {
+        D4 = rd_le(hbuf + 120, 8);
+        const uint64_t P4 = rd_le(hbuf + 16, 8);
+        if (D4 == 0 || P4 == 0 || D4 > 0xffffffffull || P4 > 0xffffffffull || D4 * P4 > 0xffffffffull)
+            return SZGB_ECORRUPT;
+        memcpy(h3, hbuf, kHeaderBytes);
+        h3[8] = 3;
+        for (int k = 0; k < 8; k++) {
+            h3[16 + k] = (uint8_t)((D4 * P4) >> (8 * k));
+            h3[120 + k] = 0;
+        }
+        hp = h3;
+    }
     Header H;
-    int rc = parse_header(hbuf, in_len, &H);
+    int rc = parse_header(hp, in_len, &H);
     if (rc) return rc;
     if (!layers_single(H.ndim, H.layers) || (H.variant == SZGB_VARIANT_LATTICE && H.layers > 2))
         return SZGB_EUNSUPPORTED;
-    // 3D fields with n = 3, 4: the hyperplane kernels instead of the wavefront
-    const bool hyper = H.variant == SZGB_VARIANT_EXACT && !layers_supported(H.ndim, H.layers);
+    // 3D fields with n = 3, 4, and 4D fields: the hyperplane kernels instead of the wavefront
+    const bool hyper = D4 || (H.variant == SZGB_VARIANT_EXACT && !layers_supported(H.ndim, H.layers));
     const uint64_t N = H.d0 * H.d1 * H.d2;
     if (out_cap_elems < N) return SZGB_EINVAL;
     if (one_field_batched(c) && !hyper && H.variant == SZGB_VARIANT_EXACT && in_on_device && out_on_device &&
@@ -638,7 +666,10 @@ int decompress_impl(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_dev
                 return rc;
         }
         PhaseTimer t(c, PH_WAVE_D);
-        if (hyper) {
+        if (D4) {
+            if ((rc = launch_hyper4(true, H.layers, nullptr, dst, codes, cpitch, D4, H.d0 / D4, H.d1, H.d2, st, s)))
+                return rc;
+        } else if (hyper) {
             if ((rc = launch_hyper_decompress(H.layers, codes, cpitch, dst, H.d0, H.d1, H.d2, st, s))) return rc;
         } else {
             ArgsBuf ha(wave_args_bytes());
@@ -1578,6 +1609,24 @@ int szgb_compress_trace(szgb_ctx* c, const float* data_dev, const szgb_params* p
                         uint16_t* codes_dev) {
     if (!out_dev) return SZGB_EINVAL;
     return compress_impl(c, data_dev, 1, p, out_dev, out_cap, 1, out_len, opt_stats, recorded_dev, codes_dev);
+}
+
+int szgb_compress_4d(szgb_ctx* c, const float* data_dev, const uint64_t* shape, const szgb_params* p,
+                     uint8_t* out_dev, size_t out_cap, size_t* out_len, szgb_stats* opt_stats, float* recorded_dev,
+                     uint16_t* codes_dev) {
+    if (!c || !data_dev || !shape || !p || !out_dev || !out_len) return SZGB_EINVAL;
+    for (int a = 0; a < 4; a++)
+        if (shape[a] == 0 || shape[a] > 0xffffffffull) return SZGB_EINVAL;
+    if (shape[0] * shape[1] > 0xffffffffull) return SZGB_EINVAL;
+    if (p->variant != SZGB_VARIANT_EXACT) return SZGB_EUNSUPPORTED;
+    // the (D P) x M x N view carries the bound, m and the stream layout (rows of N points)
+    szgb_params q = *p;
+    q.ndim = 3;
+    q.shape[0] = shape[0] * shape[1];
+    q.shape[1] = shape[2];
+    q.shape[2] = shape[3];
+    return compress_impl(c, data_dev, 1, &q, out_dev, out_cap, 1, out_len, opt_stats, recorded_dev, codes_dev,
+                         shape[0]);
 }
 
 int szgb_decompress(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_device, float* out,

@@ -83,6 +83,8 @@ def lib():
                                     C.POINTER(sz), C.POINTER(Stats)]
         L.szgb_compress_trace.argtypes = [vp, vp, C.POINTER(Params), vp, sz, C.POINTER(sz),
                                           C.POINTER(Stats), vp, vp]
+        L.szgb_compress_4d.argtypes = [vp, vp, C.POINTER(C.c_uint64), C.POINTER(Params), vp, sz, C.POINTER(sz),
+                                       C.POINTER(Stats), vp, vp]
         L.szgb_decompress.argtypes = [vp, vp, sz, C.c_int, vp, sz, C.c_int]
         L.szgb_stream_info.argtypes = [vp, sz, C.POINTER(Params), C.POINTER(C.c_uint64)]
         L.szgb_set_profiling.argtypes = [vp, C.c_int]
@@ -131,7 +133,7 @@ EXPORTS = ["szgb_create", "szgb_destroy", "szgb_set_stream", "szgb_compress_boun
            "szgb_decompress_noalloc", "szgb_compress_batch", "szgb_decompress_batch", "szgb_set_graphs",
            "szgb_server_create", "szgb_submit", "szgb_poll", "szgb_wait", "szgb_server_stats",
            "szgb_server_destroy", "szgb_autotune", "szgb_autotune_batch", "szgb_tune_save", "szgb_tune_load",
-           "szgb_quality_dev", "szgb_hit_count_dev", "szgb_suggest_m"]
+           "szgb_quality_dev", "szgb_hit_count_dev", "szgb_suggest_m", "szgb_compress_4d"]
 
 
 VARIANT_EXACT, VARIANT_LATTICE = 0, 1
@@ -140,6 +142,8 @@ VARIANT_EXACT, VARIANT_LATTICE = 0, 1
 def make_params(shape, mode=REL, eb_abs=0.0, eb_rel=1e-4, layers=1, m=0, theta=0.99, variant=0) -> Params:
     p = Params()
     shape = tuple(int(s) for s in shape)
+    if len(shape) == 4:  # a 4D field is described by its (D P) x M x N view (szgb_compress_4d)
+        shape = (shape[0] * shape[1], shape[2], shape[3])
     p.ndim = len(shape)
     for i in range(3):
         p.shape[i] = shape[i] if i < len(shape) else 0
@@ -256,12 +260,16 @@ class Context:
             if out is None:
                 out = torch.empty(bound, dtype=torch.uint8, device=x.device)
             _require_cuda(out, torch.uint8, "out", self.device)
+            if x.dim() == 4:
+                return self._compress_4d(x, p, out, None, None)
             rc = L.szgb_compress(self._h, C.c_void_p(x.data_ptr()), 1, C.byref(p),
                                  C.c_void_p(out.data_ptr()), out.numel(), 1, C.byref(olen), C.byref(st))
             if rc:
                 raise SzgbError(rc, "szgb_compress")
             return out[:olen.value], st
         xa = np.ascontiguousarray(x, dtype=np.float32)
+        if xa.ndim == 4:
+            raise ValueError("4D fields are compressed from device memory (a CUDA tensor)")
         if out is None:
             out = np.empty(bound, np.uint8)
         _require_host(out, np.uint8, "out")
@@ -293,6 +301,9 @@ class Context:
         out = torch.empty(bound, dtype=torch.uint8, device=x.device)
         rec = torch.empty_like(x)
         codes = torch.empty(x.shape, dtype=torch.int16, device=x.device)
+        if x.dim() == 4:
+            s_, st = self._compress_4d(x, p, out, rec, codes)
+            return s_, rec, codes, st
         st = Stats()
         olen = C.c_size_t()
         rc = L.szgb_compress_trace(self._h, C.c_void_p(x.data_ptr()), C.byref(p),
@@ -302,6 +313,19 @@ class Context:
         if rc:
             raise SzgbError(rc, "szgb_compress_trace")
         return out[:olen.value], rec, codes, st
+
+    def _compress_4d(self, x, p, out, rec, codes):
+        """szgb_compress_4d on the CUDA tensor x (4 dimensions)."""
+        shp = (C.c_uint64 * 4)(*[int(a) for a in x.shape])
+        st = Stats()
+        olen = C.c_size_t()
+        rc = lib().szgb_compress_4d(self._h, C.c_void_p(x.data_ptr()), shp, C.byref(p), C.c_void_p(out.data_ptr()),
+                                    out.numel(), C.byref(olen), C.byref(st),
+                                    C.c_void_p(rec.data_ptr()) if rec is not None else None,
+                                    C.c_void_p(codes.data_ptr()) if codes is not None else None)
+        if rc:
+            raise SzgbError(rc, "szgb_compress_4d")
+        return out[:olen.value], st
 
     # -- decompression -------------------------------------------------------
     def decompress(self, stream, out=None, shape=None):
@@ -492,7 +516,11 @@ def stream_info_header(hdr) -> dict:
     b = bytes(np.asarray(hdr[:128], dtype=np.uint8))
     ndim = b[8]
     d = struct.unpack_from("<3Q", b, 16)
-    return {"ndim": ndim, "shape": tuple(int(v) for v in d[3 - ndim:]), "m": b[10], "layers": b[9]}
+    if ndim == 4:  # a 4D field keeps its slowest extent at byte 120
+        shape = (int(struct.unpack_from("<Q", b, 120)[0]),) + tuple(int(v) for v in d)
+    else:
+        shape = tuple(int(v) for v in d[3 - ndim:])
+    return {"ndim": ndim, "shape": shape, "m": b[10], "layers": b[9]}
 
 
 def decompress_noalloc(stream, out, cuda_stream: int = 0) -> int:

@@ -41,6 +41,23 @@ def test_device_calls_reject_host_tensors(ctx):
         szgb.decompress_noalloc(torch.zeros(200, dtype=torch.uint8), x)
 
 
+def test_4d_fields_need_device_memory(ctx):
+    with pytest.raises(ValueError):
+        ctx.compress(np.zeros((2, 3, 4, 5), np.float32), eb_rel=1e-3)
+    with pytest.raises(TypeError):
+        ctx.compress(torch.zeros(2, 3, 4, 5), eb_rel=1e-3)
+    # the 4D bound is the bound of the (D P) x M x N view
+    assert szgb.compress_bound((2, 3, 4, 5), eb_rel=1e-3) == szgb.compress_bound((6, 4, 5), eb_rel=1e-3) > 0
+
+
+def test_4d_header_shape():
+    from oracle import szo
+    x = np.random.default_rng(3).normal(size=(2, 3, 4, 5)).astype(np.float32)
+    s = szo.compress(x, eb_rel=1e-3, m=8)
+    info = szgb.stream_info_header(s[:128])
+    assert info["ndim"] == 4 and info["shape"] == x.shape
+
+
 def test_host_outputs_checked(ctx):
     x = np.zeros((8, 8), np.float32)
     with pytest.raises(TypeError):

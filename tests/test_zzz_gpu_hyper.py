@@ -1,8 +1,9 @@
-"""3D fields with n = 3 and 4 layers (Sec. III, Eq. predmodel) on the GPU's
-hyperplane kernels against the oracle: byte-identical streams, bit-identical
-recorded values, codes and reconstructions, on fields that span many
-hyperplanes with ragged extents, plus unit extents, an absolute bound, a
-tight bound and host buffers.  The batched path keeps 3D at n <= 2 and
+"""The GPU's hyperplane kernels against the oracle: 3D fields with n = 3 and 4
+layers, and 4D fields with n = 1..4 (Sec. III, Eq. predmodel in four
+dimensions).  Byte-identical streams, bit-identical recorded values, codes
+and reconstructions, on fields that span many hyperplanes with ragged
+extents, plus unit extents, an absolute bound, a tight bound, fixed and
+adaptive m and host buffers.  The batched path keeps 3D at n <= 2 and
 refuses these fields before any launch.  This file runs after the other GPU
 tests."""
 import numpy as np
@@ -74,3 +75,41 @@ def test_batched_path_refuses(ctx):
     with pytest.raises(szgb.SzgbError) as e:
         ctx.compress_batch([x], dict(eb_rel=1e-3, layers=4))
     assert e.value.code == szgb.EUNSUPPORTED
+
+
+def _field4(shape, seed):
+    rng = np.random.default_rng(seed)
+    g = np.meshgrid(*[np.linspace(0, 1, n) for n in shape], indexing="ij")
+    f = np.sin(3 * g[0] + 2 * g[1]) * np.cos(2 * g[2] - g[3]) + 0.5 * g[3] ** 2
+    f += rng.normal(scale=1e-3, size=shape)
+    return f.astype(np.float32)
+
+
+CASES4 = [
+    ("4d-n1", (5, 6, 7, 9), dict(eb_rel=1e-3, layers=1, m=0)),
+    ("4d-n2", (4, 7, 6, 11), dict(eb_rel=1e-4, layers=2, m=0)),
+    ("4d-n3-m8", (6, 5, 5, 8), dict(eb_rel=1e-3, layers=3, m=8)),
+    ("4d-n4-abs", (5, 5, 6, 6), dict(mode=0, eb_abs=1e-3, layers=4, m=0)),
+    ("4d-unit", (1, 1, 3, 40), dict(eb_rel=1e-4, layers=2, m=0)),
+    ("4d-samples", (9, 10, 9, 17), dict(eb_rel=1e-4, layers=1, m=0)),  # several adaptive-m samples per axis
+]
+
+
+@pytest.mark.parametrize("name,shape,kw", CASES4, ids=[c[0] for c in CASES4])
+def test_parity_4d(ctx, name, shape, kw):
+    import torch
+    from oracle import szo
+    x = _field4(shape, seed=sum(shape))
+    xd = torch.from_numpy(x).cuda()
+    s_gpu, rec, codes, st = ctx.compress_trace(xd, **kw)
+    s_ref, rec_ref, codes_ref = szo.compress(x, want_aux=True, **kw)
+    assert np.array_equal(codes.cpu().numpy().view(np.uint16), codes_ref), "codes differ"
+    assert np.array_equal(rec.cpu().numpy().view(np.uint32), rec_ref.view(np.uint32)), "recorded values differ"
+    assert np.array_equal(s_gpu.cpu().numpy(), s_ref), "stream bytes differ"
+    y = ctx.decompress(s_gpu)
+    assert tuple(y.shape) == shape
+    assert np.array_equal(y.cpu().numpy().view(np.uint32), rec_ref.view(np.uint32)), "reconstruction differs"
+    y2 = ctx.decompress(np.asarray(s_ref))  # the oracle's stream through the host path
+    assert np.array_equal(y2.view(np.uint32), rec_ref.view(np.uint32))
+    s_plain, _ = ctx.compress(xd, **kw)
+    assert np.array_equal(s_plain.cpu().numpy(), s_ref)
