@@ -516,8 +516,7 @@ def run_rd(args):
 def run_layers(args):
     """Best-layer report (Sec. III, Table 2) on the device: R_PH^orig and
     R_PH^decomp for n = 1..4 on the 3D field, a 2D climate-like field and a
-    smooth 2D field.  R_PH^decomp needs the compressor's recorded values, so
-    it is reported for the layer counts the wavefront carries (3D: n <= 2)."""
+    smooth 2D field, R_PH^decomp from the compressor's recorded values."""
     import torch
     from paper_1706_03791_gb300 import build as B
     B.build()
@@ -533,18 +532,14 @@ def run_layers(args):
         for eb in (1e-3, 1e-4):
             for n in (1, 2, 3, 4):
                 row = {"field": name, "eb_rel": eb, "n": n}
-                if x.dim() < 3 or n <= 2:
-                    r = ctx.hit_rates(x, n, eb_rel=eb)
-                    row.update(R_orig=r["R_orig"], R_decomp=r["R_decomp"], m=r["m"])
-                    ebf = r["eb_f"]  # the bound depends on the field and eb only, not on n
-                else:
-                    row.update(R_orig=ctx.hit_count(x, x, n, ebf) / x.numel(), R_decomp=None, m=None)
+                r = ctx.hit_rates(x, n, eb_rel=eb)  # 3D n = 3, 4 compress on the hyperplane kernels
+                row.update(R_orig=r["R_orig"], R_decomp=r["R_decomp"], m=r["m"])
                 rows.append(row)
         for r in rows:
             if r["field"] == name:
                 print("%-24s eb %-6g n=%d  R_orig %7.3f%%  R_decomp %s  m %s" % (
                     name, r["eb_rel"], r["n"], 100 * r["R_orig"],
-                    "%7.3f%%" % (100 * r["R_decomp"]) if r["R_decomp"] is not None else "   n/a  ",
+                    "%7.3f%%" % (100 * r["R_decomp"]),
                     r["m"]), file=sys.stderr)
     print(json.dumps({"metric": "prediction hitting rate by layer count (Sec. III, Table 2)", "value": None,
                       "unit": "fraction", "n_gpus": 1, "dtype": "f32", "data": "synthetic",
