@@ -546,6 +546,55 @@ def run_layers(args):
                       "config": {"workload": "best-layer hit rates, rel eb 1e-3 and 1e-4"}, "rows": rows}))
 
 
+def run_hyper(args):
+    """The hyperplane paths: the 3D field at n = 3, 4 and a 4D field at
+    n = 1, 2, compress + decompress timed with CUDA events (L2 flushed before
+    each step), every point checked against its bound."""
+    import numpy as np
+    import torch
+    from paper_1706_03791_gb300 import build as B
+    B.build()
+    from paper_1706_03791_gb300 import szgb
+    from synthetic import fields
+    ctx = szgb.Context(0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    g = np.meshgrid(*[np.linspace(0, 1, n) for n in (16, 64, 64, 64)], indexing="ij")
+    x4 = (np.sin(3 * g[0] + 2 * g[1]) * np.cos(2 * g[2] - g[3]) + 0.5 * g[3] ** 2).astype(np.float32)
+    cases = [("3d-blobs-100x500x500", fields.workload_3d(), (3, 4)), ("4d-smooth-16x64x64x64", x4, (1, 2))]
+    rows = []
+    for name, x_np, layer_set in cases:
+        x = torch.from_numpy(x_np).cuda()
+        nbytes = x_np.nbytes
+        for n in layer_set:
+            kw = dict(eb_rel=1e-4, layers=n, m=0)
+            sbuf = torch.empty(szgb.compress_bound(x_np.shape, **kw), dtype=torch.uint8, device="cuda")
+            y = torch.empty_like(x)
+            tc, td = [], []
+            for i in range(args.warmup + args.steps):
+                flush.fill_(1)
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                e0.record()
+                s_, st = ctx.compress(x, out=sbuf, **kw)
+                e1.record()
+                ctx.decompress(s_, out=y)
+                e2.record()
+                e2.synchronize()
+                if i >= args.warmup:
+                    tc.append(e0.elapsed_time(e1))
+                    td.append(e1.elapsed_time(e2))
+            q = ctx.quality(x.reshape(-1), y.reshape(-1))
+            assert q["max_abs_err"] < float(st.eb_f), "error bound violated"
+            c_ms, d_ms = statistics.median(tc), statistics.median(td)
+            rows.append({"field": name, "layers": n, "m": int(st.m), "bit_rate": s_.numel() * 8.0 / x_np.size,
+                         "compress_gbs": nbytes / (c_ms / 1e3) / 1e9, "decompress_gbs": nbytes / (d_ms / 1e3) / 1e9,
+                         "psnr_db": q["psnr"]})
+            print(rows[-1], file=sys.stderr)
+    print(json.dumps({"metric": "hyperplane paths: compress and decompress GB/s of FP32 input", "value": None,
+                      "unit": "GB/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "f32",
+                      "data": "synthetic", "config": {"workload": "3D n = 3, 4 and 4D n = 1, 2, rel eb 1e-4"},
+                      "rows": rows}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -560,11 +609,12 @@ def main():
                          "fully parallel lattice variant, reported beside it")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
     ap.add_argument("--duration", type=float, default=30.0, help="serve: seconds of arrivals")
-    ap.add_argument("--workload", default="3d", choices=["3d", "climate79", "uneven512", "serve", "rd", "layers"],
+    ap.add_argument("--workload", default="3d", choices=["3d", "climate79", "uneven512", "serve", "rd", "layers", "hyper"],
                     help="3d: the single 100x500x500 field (default); climate79 / uneven512: "
                          "batched many-field workloads, batched+graph vs one field per call; "
                          "rd: rate-distortion sweep of the 3d field over the relative bound; "
-                         "layers: prediction hitting rate by layer count (Table 2)")
+                         "layers: prediction hitting rate by layer count (Table 2); "
+                         "hyper: the hyperplane paths (3D n = 3, 4; 4D)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -576,6 +626,8 @@ def main():
         return run_rd(args)
     if args.workload == "layers":
         return run_layers(args)
+    if args.workload == "hyper":
+        return run_hyper(args)
     if args.workload != "3d":
         return run_batch_workload(args)
 
