@@ -266,6 +266,8 @@ int main() {
     check(run_case<4>({6, 8, 10}, 1, 0.0, 1e-4, 0), "3d n4 rel adaptive");
     check(run_case<4>({1, 1, 40}, 1, 0.0, 1e-3, 10), "3d n4 unit extents");
     check(run_case<3>({9, 2, 17}, 2, 1e-3, 1e-4, 0), "3d n3 both");
+    check(run_case<3>({20, 30, 7}, 1, 0.0, 1e-4, 0), "3d n3 boxes of several blocks");
+    check(run_case<4>({18, 17, 5}, 1, 0.0, 1e-6, 16), "3d n4 m16 several blocks");
     // 4D, n = 1..4, adaptive m checked against the oracle's choice
     check(run_case<1>({5, 6, 7, 9}, 1, 0.0, 1e-3, 0), "4d n1");
     check(run_case<2>({4, 7, 6, 11}, 1, 0.0, 1e-4, 0), "4d n2");
@@ -273,6 +275,7 @@ int main() {
     check(run_case<4>({5, 5, 6, 6}, 0, 1e-3, 0.0, 0), "4d n4 abs");
     check(run_case<2>({1, 1, 3, 40}, 1, 0.0, 1e-4, 0), "4d unit");
     check(run_case<1>({9, 10, 9, 17}, 1, 0.0, 1e-4, 0), "4d samples");
+    check(run_case<3>({8, 9, 8, 9}, 2, 1e-3, 1e-5, 0), "4d n3 both, several blocks");
     std::printf("cases %d failures %d\n", cases, bad);
     return bad ? 1 : 0;
 }
