@@ -270,7 +270,7 @@ int szgb_quality_dev(szgb_ctx *ctx, const float *x_dev, const float *y_dev, size
  * output of szgb_compress_trace, equal to the decompressed field) gives the
  * count behind R_PH^decomp; divide by the number of points for the rate.
  *  - x_dev, v_dev: device, float32, raster order (last axis fastest), shape
- *    shape[0..ndim-1] (slowest first), ndim 1..3, extents 1..2^32-1 and fewer
+ *    shape[0..ndim-1] (slowest first), ndim 1..4, extents 1..2^32-1 and fewer
  *    than 2^40 points; layers 1..4 in every dimension; eb >= 0.
  *  - runs on the context's stream and blocks until done; *n_hit is set on
  *    success.  Returns SZGB_OK, SZGB_EINVAL (null pointer, bad shape, layers

@@ -168,6 +168,17 @@ __device__ __forceinline__ int adapt4_bucket(const float* __restrict__ x, const 
     return mm;
 }
 
+// Prediction hit of point s (raster index) of a 4D field (Sec. III): the
+// n-layer prediction from the values V at its preceding neighbours lies
+// within eb of x, compared in float64 (V = x: original values).
+template <int NL>
+__device__ __forceinline__ bool hit4_point(const float* __restrict__ x, const float* __restrict__ V, const Dims4& d,
+                                           uint64_t s, double eb) {
+    const uint64_t l = s % d.N, r1 = s / d.N, j = r1 % d.M, r2 = r1 / d.M, i = r2 % d.P, a = r2 / d.P;
+    const float pred = predict4<NL, true>(V, d, (int64_t)a, (int64_t)i, (int64_t)j, (int64_t)l);
+    return fabs((double)__ldg(x + s) - (double)pred) <= eb;
+}
+
 }  // namespace szgb
 
 #endif

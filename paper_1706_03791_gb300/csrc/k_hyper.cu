@@ -161,4 +161,34 @@ int launch_patch_header4(uint8_t* header, uint64_t D, uint64_t P, const DevState
     return cudaGetLastError() == cudaSuccess ? SZGB_OK : SZGB_ECUDA;
 }
 
+// Prediction hits of a 4D field, |x - f(V)| <= eb, added to *count: a
+// grid-stride loop, per-warp sums, one atomic add per warp (an integer sum).
+template <int NL>
+__global__ void __launch_bounds__(256) k_hits4(const float* __restrict__ x, const float* __restrict__ V, Dims4 d,
+                                               double eb, unsigned long long* count) {
+    const uint64_t n = d.D * d.P * d.M * d.N;
+    unsigned long long c = 0;
+    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n; s += (uint64_t)gridDim.x * blockDim.x)
+        c += hit4_point<NL>(x, V, d, s, eb) ? 1ull : 0ull;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+int launch_hits4(const float* x, const float* V, uint64_t D, uint64_t P, uint64_t M, uint64_t N, int layers,
+                 double eb, unsigned long long* count, int sm_count, cudaStream_t s) {
+    const Dims4 d = {D, P, M, N};
+    const uint64_t n = D * P * M * N;
+    uint64_t b = (n + 255) / 256;
+    const uint64_t cap = 8ull * (uint64_t)(sm_count > 0 ? sm_count : 1);
+    b = b < 1 ? 1 : (b > cap ? cap : b);
+    switch (layers) {
+        case 1: k_hits4<1><<<(unsigned)b, 256, 0, s>>>(x, V, d, eb, count); break;
+        case 2: k_hits4<2><<<(unsigned)b, 256, 0, s>>>(x, V, d, eb, count); break;
+        case 3: k_hits4<3><<<(unsigned)b, 256, 0, s>>>(x, V, d, eb, count); break;
+        case 4: k_hits4<4><<<(unsigned)b, 256, 0, s>>>(x, V, d, eb, count); break;
+        default: return SZGB_EINVAL;
+    }
+    return cudaGetLastError() == cudaSuccess ? SZGB_OK : SZGB_ECUDA;
+}
+
 }  // namespace szgb

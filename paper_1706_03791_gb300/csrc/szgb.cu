@@ -1549,15 +1549,15 @@ int szgb_quality_dev(szgb_ctx* c, const float* x_dev, const float* y_dev, size_t
 
 int szgb_hit_count_dev(szgb_ctx* c, const float* x_dev, const float* v_dev, int ndim, const uint64_t* shape,
                        int layers, double eb, uint64_t* n_hit) {
-    if (!c || !x_dev || !v_dev || !shape || !n_hit || ndim < 1 || ndim > 3 || layers < 1 || layers > kMaxLayers ||
+    if (!c || !x_dev || !v_dev || !shape || !n_hit || ndim < 1 || ndim > 4 || layers < 1 || layers > kMaxLayers ||
         !(eb >= 0.0))
         return SZGB_EINVAL;
-    uint64_t d[3] = {1, 1, 1};
+    uint64_t d[4] = {1, 1, 1, 1};  // slowest first; 1D-3D fields use d[1..3]
     for (int a = 0; a < ndim; a++) {
         if (shape[a] == 0 || shape[a] > 0xffffffffull) return SZGB_EINVAL;
-        d[3 - ndim + a] = shape[a];
+        d[4 - ndim + a] = shape[a];
     }
-    if ((unsigned __int128)d[0] * d[1] * d[2] >= ((unsigned __int128)1 << 40)) return SZGB_EINVAL;
+    if ((unsigned __int128)d[0] * d[1] * d[2] * d[3] >= ((unsigned __int128)1 << 40)) return SZGB_EINVAL;
     if (cudaSetDevice(c->device) != cudaSuccess) return SZGB_ECUDA;
     int rc;
     if ((rc = ensure_scratch(c, 64))) return rc;
@@ -1565,7 +1565,9 @@ int szgb_hit_count_dev(szgb_ctx* c, const float* x_dev, const float* v_dev, int 
     cudaStream_t s = c->stream;
     unsigned long long* count = static_cast<unsigned long long*>(c->scratch);
     if (cudaMemsetAsync(count, 0, sizeof(unsigned long long), s) != cudaSuccess) return SZGB_ECUDA;
-    if ((rc = launch_hits(x_dev, v_dev, d[0], d[1], d[2], ndim, layers, eb, count, c->sm_count, s))) return rc;
+    if (ndim == 4) rc = launch_hits4(x_dev, v_dev, d[0], d[1], d[2], d[3], layers, eb, count, c->sm_count, s);
+    else rc = launch_hits(x_dev, v_dev, d[1], d[2], d[3], ndim, layers, eb, count, c->sm_count, s);
+    if (rc) return rc;
     unsigned long long* h = static_cast<unsigned long long*>(c->h_batch);
     if (cudaMemcpyAsync(h, count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return SZGB_ECUDA;

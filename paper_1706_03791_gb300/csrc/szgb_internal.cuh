@@ -469,6 +469,8 @@ int launch_hyper4(bool dec, int layers, const float* x, float* V, uint16_t* code
 int launch_adapt4(const float* x, uint64_t D, uint64_t P, uint64_t M, uint64_t N, int layers, double theta,
                   DevState* st, cudaStream_t s);
 int launch_patch_header4(uint8_t* header, uint64_t D, uint64_t P, const DevState* st, cudaStream_t s);
+int launch_hits4(const float* x, const float* V, uint64_t D, uint64_t P, uint64_t M, uint64_t N, int layers,
+                 double eb, unsigned long long* count, int sm_count, cudaStream_t s);
 // prediction hits |x - f(V)| <= eb over a d0 x d1 x d2 field, added to *count
 int launch_hits(const float* x, const float* V, uint64_t d0, uint64_t d1, uint64_t d2, int ndim, int layers,
                 double eb, unsigned long long* count, int sm_count, cudaStream_t s);

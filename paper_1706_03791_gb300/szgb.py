@@ -425,8 +425,8 @@ class Context:
         import torch
         _require_cuda(x, torch.float32, "x", self.device)
         _require_cuda(v, torch.float32, "v", self.device)
-        if tuple(x.shape) != tuple(v.shape) or not 1 <= x.dim() <= 3:
-            raise ValueError("x and v need one 1D, 2D or 3D shape")
+        if tuple(x.shape) != tuple(v.shape) or not 1 <= x.dim() <= 4:
+            raise ValueError("x and v need one 1D..4D shape")
         shp = (C.c_uint64 * max(1, x.dim()))(*[int(a) for a in x.shape])
         n = C.c_uint64()
         rc = lib().szgb_hit_count_dev(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(v.data_ptr()), x.dim(), shp,

@@ -2,8 +2,8 @@
 // (paper_1706_03791_gb300/csrc/hyper_kernels.cuh), run on the host thread by
 // thread, hyperplane by hyperplane, against the oracle: codes and recorded
 // values of 3D fields with n = 3, 4 and of 4D fields with n = 1..4, their
-// reconstruction from the codes and the unpredictable values, and the 4D
-// adaptive-m choice.  The CUDA intrinsics the kernels use are given their
+// reconstruction from the codes and the unpredictable values, the 4D
+// adaptive-m choice and the 4D prediction hit counts.  The CUDA intrinsics the kernels use are given their
 // IEEE meaning (every product and sum rounded once, no contraction: build
 // with -ffp-contract=off); the quantizer helpers are host transcriptions of
 // the library's device helpers.
@@ -246,6 +246,20 @@ int run_case(const std::vector<uint64_t>& shape, int mode, double eb_abs, double
     else emulate3<NL, true>(nullptr, Y.data(), codes.data(), cpitch, shape[0], shape[1], shape[2], &st);
     for (uint64_t p = 0; p < n; p++)
         if (__float_as_uint(Y[p]) != __float_as_uint(rec[p])) return 15;
+    if (nd == 4) {
+        // prediction hits (Sec. III) from original and from recorded values
+        std::vector<float> pred(n);
+        for (int which = 0; which < 2; which++) {
+            const float* V0 = which ? rec.data() : x.data();
+            if (szo_predict_field(V0, 4, shape.data(), NL, pred.data()) != 0) return 16;
+            uint64_t ref = 0, got = 0;
+            for (uint64_t p = 0; p < n; p++) {
+                ref += std::fabs((double)x[p] - (double)pred[p]) <= (double)ebf;
+                got += hit4_point<NL>(x.data(), V0, d, p, (double)ebf);
+            }
+            if (got != ref) return 17;
+        }
+    }
     return 0;
 }
 

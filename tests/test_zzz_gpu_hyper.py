@@ -113,3 +113,18 @@ def test_parity_4d(ctx, name, shape, kw):
     assert np.array_equal(y2.view(np.uint32), rec_ref.view(np.uint32))
     s_plain, _ = ctx.compress(xd, **kw)
     assert np.array_equal(s_plain.cpu().numpy(), s_ref)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+def test_hit_counts_4d(ctx, n):
+    # szgb_hit_count_dev on 4D fields against the oracle's count (Sec. III)
+    import torch
+    from oracle import hitrate
+    x = _field4((5, 6, 7, 9), seed=70 + n)
+    xd = torch.from_numpy(x).cuda()
+    span = float(x.max() - x.min())
+    for eb in (0.0, 1e-3 * span, 1e-2 * span):
+        assert ctx.hit_count(xd, xd, n, eb) == hitrate.hit_count(x, x, n, eb), eb
+    r = ctx.hit_rates(xd, n, eb_rel=1e-3)
+    ref = hitrate.hit_rates(x, n, eb_rel=1e-3)
+    assert r["hits_orig"] == ref["hits_orig"] and r["hits_decomp"] == ref["hits_decomp"]
