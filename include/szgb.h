@@ -1,6 +1,6 @@
 /*
  * szgb.h -- C ABI of the GB300 (sm_103a) error-bounded lossy compressor for
- * FP32 1D/2D/3D arrays: multilayer prediction from preceding decompressed
+ * FP32 1D/2D/3D/4D arrays: multilayer prediction from preceding decompressed
  * values (arXiv:1706.03791 Sec. III, Eq. predmodel), error-controlled
  * linear-scaling quantization into 2^m - 1 intervals with a truncated binary
  * representation for unpredictable values (Sec. IV-A, Sec. IV-B, Algorithm
@@ -267,7 +267,8 @@ int szgb_quality_dev(szgb_ctx *ctx, const float *x_dev, const float *y_dev, size
  * order, products and sums rounded one at a time, values outside the field
  * 0); the difference and the comparison are float64.  v = x gives the count
  * behind R_PH^orig; v = the values the compressor recorded (the recorded_dev
- * output of szgb_compress_trace, equal to the decompressed field) gives the
+ * output of szgb_compress_trace or szgb_compress_4d, equal to the
+ * decompressed field) gives the
  * count behind R_PH^decomp; divide by the number of points for the rate.
  *  - x_dev, v_dev: device, float32, raster order (last axis fastest), shape
  *    shape[0..ndim-1] (slowest first), ndim 1..4, extents 1..2^32-1 and fewer
