@@ -246,9 +246,10 @@ class Context:
     # -- compression ---------------------------------------------------------
     def compress(self, x, out=None, **kw):
         """Compress `x` (a CUDA float32 tensor, or a NumPy float32 array on the
-        host).  Returns (stream, stats): with a CUDA input, `stream` is a view
-        of the uint8 CUDA tensor `out` (allocated when None); with a NumPy
-        input, a NumPy uint8 array."""
+        host; 1D-3D, or 4D as a CUDA tensor through szgb_compress_4d).
+        Returns (stream, stats): with a CUDA input, `stream` is a view of the
+        uint8 CUDA tensor `out` (allocated when None); with a NumPy input, a
+        NumPy uint8 array."""
         p = make_params(tuple(x.shape), **kw)
         L = lib()
         bound = int(L.szgb_compress_bound(C.byref(p)))
