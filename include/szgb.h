@@ -162,22 +162,31 @@ int szgb_decompress(szgb_ctx *ctx, const uint8_t *in, size_t in_len,
                     int out_on_device);
 
 /* Decompression that allocates no memory, for callers that cannot call
- * cudaMalloc (for example code that issues work while a stream capture is
- * open, services with a fixed device-memory plan, or allocator callbacks).
- * The paper has no counterpart: this is an operational variant of
- * szgb_decompress with identical output.
+ * cudaMalloc: a service that keeps a fixed device-memory plan for its whole
+ * life (an allocation that could fail, or fragment a planned pool, at an
+ * arbitrary moment is not allowed there), or code running inside an
+ * allocator or framework callback, where allocating would re-enter the
+ * allocator.  The paper has no counterpart: this is an operational variant
+ * of szgb_decompress with identical output.
  *  - in_dev (in_len bytes, 4-byte aligned) and out_dev (out_cap_elems floats,
- *    16-byte aligned) are device buffers owned by the caller; work is issued
- *    on `cuda_stream` (a cudaStream_t, NULL = legacy default stream) and the
- *    call returns after that stream has finished it.
+ *    16-byte aligned) are device buffers owned by the caller, on the current
+ *    device; work is issued on `cuda_stream` (a cudaStream_t of the current
+ *    device, NULL = legacy default stream).  The call copies the 128-byte
+ *    header to the host and waits for the stream twice (before the kernels,
+ *    to read the header, and at the end); it returns after the stream has
+ *    finished its work.
  *  - Scratch is a fixed 128 MiB static device array held by every GPU that
  *    loads the library until the process exits; a stream whose decompression
  *    needs more returns SZGB_ESCRATCH before any work is issued.
- *  - The first call on a device looks up that array's device address; make
- *    that first call before any stream capture is opened.
+ *  - The first call on a device looks up that array's device address
+ *    (cudaGetSymbolAddress, once per device).
  *  - Every call on a device shares the array; calls whose work overlaps on
  *    the GPU race.  It never calls cudaMalloc/cudaFree or an allocating
- *    library routine. */
+ *    library routine.
+ *  - Errors: SZGB_EINVAL (null or misaligned buffer, out too small),
+ *    SZGB_ECORRUPT (inconsistent stream), SZGB_EUNSUPPORTED (4D streams,
+ *    lattice-variant streams, 3D streams with n > 2), SZGB_ESCRATCH,
+ *    SZGB_ETIMEOUT, SZGB_ECUDA, as szgb_decompress. */
 int szgb_decompress_noalloc(const uint8_t *in_dev, size_t in_len, float *out_dev,
                             size_t out_cap_elems, void *cuda_stream);
 

@@ -180,6 +180,12 @@ WaveGeom make_geom(const szgb_ctx* c, const CallParams& cp, int layers) {
         W2 = W3 = it->second.W;
     }
     if (c->force_W) W2 = W3 = c->force_W;
+    return make_geom_w(cp, layers, W2, W3);
+}
+
+}  // namespace
+
+WaveGeom szgb::make_geom_w(const CallParams& cp, int layers, int W2, int W3) {
     WaveGeom g = {};
     g.N = cp.d2;
     g.ntiles = (int)((cp.d2 + kTile - 1) / kTile);
@@ -212,10 +218,14 @@ WaveGeom make_geom(const szgb_ctx* c, const CallParams& cp, int layers) {
     return g;
 }
 
+namespace {
+
 // Halo line sizes in 32-bit units: every value travels as one 64-bit tagged
 // word.  The plane halo follows the row halo in one allocation (one memset
 // per launch); both counts are multiples of 64 (256-byte offsets).
-void halo_sizes(const WaveGeom& g, int layers, size_t* row_words, size_t* plane_words) {
+}  // namespace
+
+void szgb::halo_sizes(const WaveGeom& g, int layers, size_t* row_words, size_t* plane_words) {
     size_t tpr = (size_t)g.ntiles * kTile;
     size_t r, p;
     if (g.ndim == 3) {
@@ -229,7 +239,11 @@ void halo_sizes(const WaveGeom& g, int layers, size_t* row_words, size_t* plane_
     *plane_words = align_up(2 * p, 64);
 }
 
-int dev_errors(const DevState& s) {
+namespace {
+
+}  // namespace
+
+int szgb::dev_errors(const DevState& s) {
     if (s.err & kErrNonFinite) return SZGB_ENONFINITE;
     if (s.err & kErrRange) return SZGB_EINVAL;
     if (s.err & kErrTimeout) return SZGB_ETIMEOUT;
@@ -237,6 +251,8 @@ int dev_errors(const DevState& s) {
     if (s.err & kErrOverflow) return SZGB_ETRUNC;
     return SZGB_OK;
 }
+
+namespace {
 
 // ---------------------------------------------------------------------------
 // compress
@@ -454,16 +470,6 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
 // ---------------------------------------------------------------------------
 // stream header (host side)
 
-struct Header {
-    int ndim, layers, m, mode, maxlen, tw;
-    uint64_t d0, d1, d2;
-    double eb_abs, eb_rel, theta;
-    float eb_f, xmin, xmax;
-    uint32_t nsym;
-    uint64_t nchunks, K, payload, total;
-    int adaptive;
-    int variant;
-};
 
 uint64_t rd_le(const uint8_t* p, int n) {
     uint64_t v = 0;
@@ -471,7 +477,9 @@ uint64_t rd_le(const uint8_t* p, int n) {
     return v;
 }
 
-int parse_header(const uint8_t* h, size_t in_len, Header* o) {
+}  // namespace
+
+int szgb::parse_header(const uint8_t* h, size_t in_len, Header* o) {
     if (in_len < (size_t)kHeaderBytes) return SZGB_ECORRUPT;
     if (!(h[0] == 'S' && h[1] == 'Z' && h[2] == 'G' && h[3] == 'B')) return SZGB_ECORRUPT;
     if (rd_le(h + 4, 2) != 1 || rd_le(h + 6, 2) != (uint64_t)kHeaderBytes) return SZGB_ECORRUPT;
@@ -519,6 +527,8 @@ int parse_header(const uint8_t* h, size_t in_len, Header* o) {
     if (o->total != (uint64_t)kHeaderBytes + cb + tb + o->payload || o->total > in_len) return SZGB_ECORRUPT;
     return SZGB_OK;
 }
+
+namespace {
 
 int decompress_impl(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_device, float* out,
                     size_t out_cap_elems, int out_on_device) {

@@ -453,6 +453,32 @@ struct WaveGeom {
     int num_ctas;
 };
 
+// Wavefront geometry of a field for a given number of compute warps per CTA
+// in 1D/2D (W2) and 3D (W3); any valid geometry gives the same values.
+WaveGeom make_geom_w(const CallParams& cp, int layers, int W2, int W3);
+// Halo line sizes of a wavefront launch in 32-bit units (every value travels
+// as one 64-bit tagged word; the plane halo follows the row halo).
+void halo_sizes(const WaveGeom& g, int layers, size_t* row_words, size_t* plane_words);
+
+// Stream header fields (little-endian, 128 bytes; the layout is listed with
+// the stream format in the library's header file).
+struct Header {
+    int ndim, layers, m, mode, maxlen, tw;
+    uint64_t d0, d1, d2;
+    double eb_abs, eb_rel, theta;
+    float eb_f, xmin, xmax;
+    uint32_t nsym;
+    uint64_t nchunks, K, payload, total;
+    int adaptive;
+    int variant;
+};
+// Parses and checks a 1D-3D header held in host memory; SZGB_ECORRUPT for an
+// inconsistent one, SZGB_EUNSUPPORTED for a 4D one (callers that decode 4D
+// streams rewrite the header to its 3D view first).
+int parse_header(const uint8_t* h, size_t in_len, Header* o);
+// The SZGB_E* code of the error flags a call left in its device state.
+int dev_errors(const DevState& s);
+
 // host launchers (each in its own translation unit)
 int launch_range(const float* x, uint64_t n, DevState* st, const CallParams& cp, float* partials,
                  int nblocks, cudaStream_t s);

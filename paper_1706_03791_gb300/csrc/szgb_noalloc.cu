@@ -1,15 +1,15 @@
 // szgb_noalloc.cu -- decompression that allocates no memory.
 //
-// Some callers cannot call cudaMalloc: a thread that issues work while a
-// stream capture is open (allocation is not a capturable operation), a
-// service that must keep a fixed device-memory plan for its whole life, or
-// code that runs inside an allocator or framework callback where allocating
-// would re-enter the allocator.  szgb_decompress_noalloc serves them.  It
-// runs the same kernels as szgb_decompress, but every scratch buffer those
-// kernels use (halo rows/planes, progress counters, per-row byte lengths and
-// offsets, decoder tables, call state) is carved out of the fixed array
-// below, which every GPU that loads this library holds until the process
-// exits.  Inputs and outputs are the caller's device buffers.
+// Some callers cannot call cudaMalloc: a service that must keep a fixed
+// device-memory plan for its whole life (an allocation that fails at an
+// arbitrary moment, or that fragments a pre-planned pool, is not allowed
+// there), or code that runs inside an allocator or framework callback, where
+// allocating would re-enter the allocator.  szgb_decompress_noalloc serves
+// them.  It runs the same kernels as szgb_decompress, but every scratch
+// buffer those kernels use (halo rows/planes, progress counters, per-row byte
+// lengths and offsets, decoder tables, call state) is carved out of the fixed
+// array below, which every GPU that loads this library holds until the
+// process exits.  Inputs and outputs are the caller's device buffers.
 //
 // The array is shared by every call on a device and keeps the last call's
 // contents; what must start at zero is cleared on the stream at the start of
@@ -52,12 +52,6 @@ int scratch_address(void** out) {
     return SZGB_OK;
 }
 
-uint64_t le(const uint8_t* p, int n) {
-    uint64_t v = 0;
-    for (int i = n - 1; i >= 0; i--) v = (v << 8) | p[i];
-    return v;
-}
-
 size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 }  // namespace
@@ -75,60 +69,26 @@ extern "C" int szgb_decompress_noalloc(const uint8_t* in_dev, size_t in_len, flo
     uint8_t h[kHeaderBytes];
     if (cudaMemcpyAsync(h, in_dev, kHeaderBytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return SZGB_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return SZGB_ECUDA;
-    if (!(h[0] == 'S' && h[1] == 'Z' && h[2] == 'G' && h[3] == 'B')) return SZGB_ECORRUPT;
-    if (le(h + 4, 2) != 1 || le(h + 6, 2) != (uint64_t)kHeaderBytes) return SZGB_ECORRUPT;
-    const int ndim = h[8], layers = h[9], m = h[10], tw = h[13];
-    const uint64_t d0 = le(h + 16, 8), d1 = le(h + 24, 8), d2 = le(h + 32, 8);
-    float eb_f;
-    uint32_t ebu = (uint32_t)le(h + 56, 4);
-    memcpy(&eb_f, &ebu, 4);
-    const uint32_t nsym = (uint32_t)le(h + 68, 4);
-    const uint64_t rows = le(h + 72, 8), payload_bytes = le(h + 88, 8), total = le(h + 96, 8);
-    if (ndim == 4 && h[113] == 0 && le(h + 120, 8) != 0) return SZGB_EUNSUPPORTED;  // a 4D field: not decoded here
-    if (ndim < 1 || ndim > 3 || layers < 1 || m < 2 || m > 16 || (tw != 2 && tw != 4)) return SZGB_ECORRUPT;
-    if (d0 == 0 || d1 == 0 || d2 == 0 || d0 > 0xffffffffull || d1 > 0xffffffffull || d2 > 0xffffffffull)
-        return SZGB_ECORRUPT;
-    if ((unsigned __int128)d0 * d1 * d2 >= ((unsigned __int128)1 << 32)) return SZGB_ECORRUPT;
-    if ((ndim < 3 && d0 != 1) || (ndim < 2 && d1 != 1) || rows != d0 * d1) return SZGB_ECORRUPT;
-    if (nsym < 1 || nsym > (1u << m) || h[12] < 1 || h[12] > 64) return SZGB_ECORRUPT;
+    Header H;
+    if ((rc = parse_header(h, in_len, &H))) return rc;  // SZGB_EUNSUPPORTED for a 4D stream
+    if (!layers_supported(H.ndim, H.layers) || H.variant != SZGB_VARIANT_EXACT) return SZGB_EUNSUPPORTED;
+    const int ndim = H.ndim, layers = H.layers, m = H.m, tw = H.tw;
+    const uint64_t d2 = H.d2;
+    const uint32_t nsym = H.nsym;
+    const uint64_t rows = H.nchunks, payload_bytes = H.payload;
     const uint64_t cb = (3ull * nsym + 3) & ~3ull, tb = ((uint64_t)tw * rows + 3) & ~3ull;
-    if (total != (uint64_t)kHeaderBytes + cb + tb + payload_bytes || total > in_len) return SZGB_ECORRUPT;
-    if (!layers_supported(ndim, layers) || h[113] != 0) return SZGB_EUNSUPPORTED;  // the paper's method only
 
-    // wavefront geometry (the same schedule as szgb_decompress; any valid
-    // schedule gives the same values)
-    WaveGeom g = {};
-    g.N = d2;
-    g.ntiles = (int)((d2 + kTile - 1) / kTile);
-    g.aligned = (d2 % 4) == 0;
-    if (ndim == 3) {
-        g.ndim = 3;
-        g.P = d0;
-        g.M = d1;
-        int W = 8;
-        if ((uint64_t)W > d0) W = (int)d0;
-        if (W < 2 * layers) W = 2 * layers;
-        g.W = W;
-        g.nb0 = (int)((d0 + W - 1) / W);
-        g.nb1 = (int)((d1 + 31) / 32);
-        g.nsweeps = (int)((d2 - 1 + 31 + 4 * (W - 1)) / 4) + 1;  // last step: column N-1 of warp W-1, lane 31
-    } else {
-        g.ndim = ndim;
-        g.P = 1;
-        g.M = d0 * d1;
-        int W = 8, need = (int)((g.M + 31) / 32);
-        if (W > need) W = need;
-        if (W < 1) W = 1;
-        g.W = W;
-        g.nb0 = 1;
-        g.nb1 = (int)((g.M + 32ull * W - 1) / (32ull * W));
-        g.nsweeps = (int)((d2 - 1 + 31 + 36 * (W - 1)) / 4) + 1;  // last step: column N-1 of warp W-1, lane 31
-    }
-    g.num_ctas = g.nb0 * g.nb1;
-    const size_t tpr = (size_t)g.ntiles * kTile;
-    // halo lines in 32-bit units: every value travels as one 64-bit tagged word
-    const size_t hrow = 2 * ((ndim == 3) ? (size_t)g.P * g.nb1 * layers * tpr : (size_t)g.nb1 * layers * tpr);
-    const size_t hplane = 2 * ((ndim == 3) ? (size_t)g.nb0 * g.nb1 * layers * 32 * (tpr + 32) : 4);
+    // wavefront geometry: the same schedule as szgb_decompress with its
+    // default shape (any valid schedule gives the same values)
+    CallParams cp = {};
+    cp.ndim = ndim;
+    cp.d0 = H.d0;
+    cp.d1 = H.d1;
+    cp.d2 = H.d2;
+    cp.layers = layers;
+    const WaveGeom g = make_geom_w(cp, layers, kMaxWaveWarps, kMaxWaveWarps);
+    size_t hrow, hplane;  // halo lines in 32-bit units
+    halo_sizes(g, layers, &hrow, &hplane);
 
     // carve the scratch
     size_t off = 0;
@@ -142,7 +102,7 @@ extern "C" int szgb_decompress_noalloc(const uint8_t* in_dev, size_t in_len, flo
     const uint64_t cpitch = (d2 + 7) & ~7ull;
     const size_t o_codes = take((rows * cpitch + 8) * 2);
     if (off > kNoAllocScratchBytes) return SZGB_ESCRATCH;
-    if (out_cap_elems < d0 * d1 * d2) return SZGB_EINVAL;
+    if (out_cap_elems < H.d0 * H.d1 * H.d2) return SZGB_EINVAL;
     char* b = static_cast<char*>(base);
     DevState* st = reinterpret_cast<DevState*>(b + o_st);
     unsigned int* prog = reinterpret_cast<unsigned int*>(b + o_prog);
@@ -150,9 +110,11 @@ extern "C" int szgb_decompress_noalloc(const uint8_t* in_dev, size_t in_len, flo
     uint64_t* rowoff = reinterpret_cast<uint64_t*>(b + o_ro);
 
     // clear what starts at zero: the call state, the item states and the halo lines
+    uint32_t ebu;
+    memcpy(&ebu, &H.eb_f, 4);
     DevState init = {};
-    init.eb_f = eb_f;
-    init.twoeb = 2.0f * eb_f;
+    init.eb_f = H.eb_f;
+    init.twoeb = 2.0f * H.eb_f;
     init.m = m;
     init.center = 1 << (m - 1);
     init.radius = (float)((1 << (m - 1)) - 1);
@@ -182,8 +144,7 @@ extern "C" int szgb_decompress_noalloc(const uint8_t* in_dev, size_t in_len, flo
     DevState hs;
     if (cudaMemcpyAsync(&hs, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SZGB_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return SZGB_ECUDA;
-    if (hs.err & kErrTimeout) return SZGB_ETIMEOUT;
-    if (hs.err & kErrCorrupt) return SZGB_ECORRUPT;
+    if ((rc = dev_errors(hs))) return rc;
     if (hs.payload != payload_bytes) return SZGB_ECORRUPT;
     return SZGB_OK;
 }

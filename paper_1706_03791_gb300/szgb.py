@@ -527,13 +527,19 @@ def stream_info_header(hdr) -> dict:
 def decompress_noalloc(stream, out, cuda_stream: int = 0) -> int:
     """szgb_decompress_noalloc on a uint8 CUDA tensor `stream` into the
     float32 CUDA tensor `out`; returns the C status code.  No memory is
-    allocated by the library (the caller provides `out`)."""
+    allocated by the library (the caller provides `out`).  `stream` and `out`
+    must be on the same device; the call runs with that device current, and
+    `cuda_stream` (a cudaStream_t handle, 0 = the legacy default stream) must
+    belong to it."""
     import torch
     _require_cuda(stream, torch.uint8, "stream")
     _require_cuda(out, torch.float32, "out")
-    return lib().szgb_decompress_noalloc(C.c_void_p(stream.data_ptr()), stream.numel(),
-                                         C.c_void_p(out.data_ptr()), out.numel(),
-                                         C.c_void_p(cuda_stream or 0))
+    if stream.device != out.device:
+        raise ValueError("stream is on %s but out is on %s" % (stream.device, out.device))
+    with torch.cuda.device(stream.device):
+        return lib().szgb_decompress_noalloc(C.c_void_p(stream.data_ptr()), stream.numel(),
+                                             C.c_void_p(out.data_ptr()), out.numel(),
+                                             C.c_void_p(cuda_stream or 0))
 
 
 class Server:

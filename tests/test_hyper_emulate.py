@@ -1,7 +1,7 @@
 """The hyperplane kernels' device code (3D n = 3, 4 and 4D n = 1..4), run
 thread by thread on the host by tests/native/hyper_emulate.cpp, against the
 oracle: codes, recorded values, reconstruction and the 4D adaptive m, bit for
-bit.  No GPU needed; the GPU parity cases are in test_zzz_gpu_hyper.py."""
+bit.  No GPU needed; the GPU parity cases are in test_zy_gpu_hyper.py."""
 import os
 import shutil
 import subprocess

@@ -30,22 +30,49 @@ def _same(a, b):
     return np.array_equal(a.cpu().numpy().view(np.uint32), b.cpu().numpy().view(np.uint32))
 
 
-def test_noalloc_matches_decompress_twice(env):
+CASES = [
+    ("3d-n1", lambda: fields.blobs3d(24, 70, 44, seed=61, nblobs=6), dict(eb_rel=1e-4, m=0)),
+    ("2d-n2", lambda: fields.grf2d(300, 130, seed=62), dict(eb_rel=1e-4, m=0, layers=2)),
+    ("1d-n1", lambda: fields.grf2d(1, 3001, seed=63).reshape(3001), dict(eb_rel=1e-4, m=0)),
+    ("2d-n4", lambda: fields.grf2d(97, 211, seed=64), dict(eb_rel=1e-4, m=0, layers=4)),
+]
+
+
+@pytest.mark.parametrize("name,gen,kw", CASES, ids=[c[0] for c in CASES])
+def test_noalloc_matches_decompress_twice(env, szo, name, gen, kw):
     torch, szgb, ctx = env
-    cases = [(fields.blobs3d(24, 70, 44, seed=61, nblobs=6), dict(eb_rel=1e-4, m=0)),
-             (fields.grf2d(300, 130, seed=62), dict(eb_rel=1e-4, m=0, layers=2))]
-    for x, kw in cases:
-        xd = torch.from_numpy(x).cuda()
-        s, _ = ctx.compress(xd, **kw)
-        s = s.clone()
-        ref = ctx.decompress(s)
+    x = np.ascontiguousarray(gen())
+    xd = torch.from_numpy(x).cuda()
+    s, _ = ctx.compress(xd, **kw)
+    s = s.clone()
+    ref = ctx.decompress(s)
+    torch.cuda.synchronize()
+    # the oracle's reconstruction of the same stream, independent of the GPU path
+    rec = szo.decompress(s.cpu().numpy())
+    assert np.array_equal(ref.cpu().numpy().reshape(-1).view(np.uint32),
+                          np.ascontiguousarray(rec).reshape(-1).view(np.uint32))
+    for _ in range(2):
+        out = torch.full_like(ref, float("nan"))
+        rc = szgb.decompress_noalloc(s, out, torch.cuda.current_stream().cuda_stream)
         torch.cuda.synchronize()
-        for _ in range(2):
-            out = torch.full_like(ref, float("nan"))
-            rc = szgb.decompress_noalloc(s, out, torch.cuda.current_stream().cuda_stream)
-            torch.cuda.synchronize()
-            assert rc == szgb.OK, szgb.strerror(rc)
-            assert _same(out, ref)
+        assert rc == szgb.OK, szgb.strerror(rc)
+        assert _same(out, ref)
+
+
+def test_noalloc_refuses_unsupported(env, szo):
+    """Streams this entry point does not decode are refused before any work:
+    3D with n = 3 (hyperplane path), 4D, and the lattice variant."""
+    torch, szgb, ctx = env
+    cases = [
+        szo.compress(fields.blobs3d(6, 20, 24, seed=71, nblobs=3), eb_rel=1e-4, n=3, m=8),
+        szo.compress(fields.blobs3d(8, 10, 12, seed=72, nblobs=3).reshape(2, 4, 10, 12), eb_rel=1e-4, n=1, m=8),
+        szo.compress_lattice(fields.grf2d(40, 56, seed=73), eb_rel=1e-4, n=1, m=8),
+    ]
+    for sref in cases:
+        s = torch.from_numpy(np.ascontiguousarray(sref)).cuda()
+        out = torch.empty(8192, dtype=torch.float32, device="cuda")
+        rc = szgb.decompress_noalloc(s, out, 0)
+        assert rc == szgb.EUNSUPPORTED, szgb.strerror(rc)
 
 
 def test_noalloc_refuses_oversize(env):
