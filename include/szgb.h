@@ -245,6 +245,22 @@ int szgb_tune_load(szgb_ctx *ctx, const char *path);
 /* Capture batches in CUDA graphs (1, the default) or launch them directly (0). */
 int szgb_set_graphs(szgb_ctx *ctx, int on);
 
+/* ---- test hooks for the bounded device-side waits -------------------------
+ * Not part of the method (the paper has no counterpart): they let a test make
+ * the wavefront's bounded waits run out without faulting or hanging the GPU.
+ * szgb_debug_set_wait_limit sets the limit of every device-side wait of later
+ * calls on this context (`ns` nanoseconds; 0 restores the default of 4 s).
+ * szgb_debug_skip_item makes the wavefront CTA that takes work item `item`
+ * (0-based, in every field of a call) return without running it or
+ * publishing its state (-1 turns the hook off).  Its consumers then poll
+ * halo words that are never written until the limit, set the device error
+ * flag, publish an aborted state (which stops their own consumers) and
+ * return; the call returns SZGB_ETIMEOUT and the context stays usable.
+ * While an item is skipped, calls launch directly (no CUDA graphs).
+ * SZGB_EINVAL for a null context or item < -1. */
+int szgb_debug_set_wait_limit(szgb_ctx *ctx, uint64_t ns);
+int szgb_debug_skip_item(szgb_ctx *ctx, int item);
+
 /* ---- reconstruction quality (Sec. II, Metrics 1-3) ----------------------
  * One pass over a field x and its reconstruction y (both n float32 values in
  * device memory, any alignment), on the context's stream, in float64:

@@ -402,6 +402,9 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
     using IT = typename Elems<DEC>::In;
     using OT = typename Elems<DEC>::Out;
     const WaveGeom& g = A.g;
+    // test hook: this item is never run and never publishes its state, so
+    // its consumers' bounded waits run out (uniform over the CTA)
+    if (g.debug_skip == item + 1) return;
     const int W = g.W;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool is_helper = (warp >= W);  // warps W and W + 3: halo lines in; W + 1: staging tiles; W + 2: halo lines out

@@ -89,6 +89,7 @@ struct szgb_ctx {
     };
     std::map<uint64_t, Tune> tune;
     int force_W = 0;  // set while the autotuner times a candidate
+    int debug_skip = 0;  // test hook: 1 + the wavefront work item never run; 0 = none
 };
 
 namespace {
@@ -180,7 +181,9 @@ WaveGeom make_geom(const szgb_ctx* c, const CallParams& cp, int layers) {
         W2 = W3 = it->second.W;
     }
     if (c->force_W) W2 = W3 = c->force_W;
-    return make_geom_w(cp, layers, W2, W3);
+    WaveGeom g = make_geom_w(cp, layers, W2, W3);
+    g.debug_skip = c->debug_skip;
+    return g;
 }
 
 }  // namespace
@@ -281,7 +284,9 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
 // replayed, which removes most of the per-call launch gaps.  Profiled runs
 // (per-kernel phase events), test hooks and autotuning candidates keep the
 // direct path.
-bool one_field_batched(const szgb_ctx* c) { return c->use_graphs && !c->profiling && !c->force_W; }
+bool one_field_batched(const szgb_ctx* c) {
+    return c->use_graphs && !c->profiling && !c->force_W && !c->debug_skip;
+}
 
 // D4 != 0: a 4D field D4 x P x M x N given as its (D4 P) x M x N view in p
 int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb_params* p, uint8_t* out,
@@ -776,7 +781,7 @@ void drop_graph(BatchGraph& G) {
 template <typename F>
 int run_batch(szgb_ctx* c, BatchGraph& G, const std::vector<uint64_t>& key, F enqueue) {
     cudaStream_t s = c->stream;
-    if (!c->use_graphs) return enqueue();
+    if (!c->use_graphs || c->debug_skip) return enqueue();
     if (!(G.exec && G.key == key)) {
         drop_graph(G);
         if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) return SZGB_ECUDA;
@@ -1520,6 +1525,18 @@ int szgb_set_graphs(szgb_ctx* c, int on) {
         drop_graph(c->g_comp);
         drop_graph(c->g_dec);
     }
+    return SZGB_OK;
+}
+
+int szgb_debug_set_wait_limit(szgb_ctx* c, uint64_t ns) {
+    if (!c) return SZGB_EINVAL;
+    c->timeout_ns = ns ? ns : 4000000000ull;
+    return SZGB_OK;
+}
+
+int szgb_debug_skip_item(szgb_ctx* c, int item) {
+    if (!c || item < -1) return SZGB_EINVAL;
+    c->debug_skip = item + 1;
     return SZGB_OK;
 }
 

@@ -451,6 +451,8 @@ struct WaveGeom {
     int nsweeps;          // sweeps per CTA including the final flush sweep
     int aligned;          // rows start on 16-byte boundaries (N % 4 == 0)
     int num_ctas;
+    int debug_skip;       // test hook: 1 + the work item that is never run
+                          // (its consumers' bounded waits run out); 0 = none
 };
 
 // Wavefront geometry of a field for a given number of compute warps per CTA

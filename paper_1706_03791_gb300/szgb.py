@@ -99,6 +99,8 @@ def lib():
         L.szgb_decompress_batch.argtypes = [vp, C.c_int, C.POINTER(vp), C.POINTER(sz), C.POINTER(vp),
                                             C.POINTER(sz), C.POINTER(C.c_int)]
         L.szgb_set_graphs.argtypes = [vp, C.c_int]
+        L.szgb_debug_set_wait_limit.argtypes = [vp, C.c_uint64]
+        L.szgb_debug_skip_item.argtypes = [vp, C.c_int]
         L.szgb_quality_dev.argtypes = [vp, vp, vp, sz, C.POINTER(Quality)]
         L.szgb_suggest_m.argtypes = [C.POINTER(Stats), C.c_double, C.POINTER(C.c_double)]
         L.szgb_hit_count_dev.argtypes = [vp, vp, vp, C.c_int, C.POINTER(C.c_uint64), C.c_int, C.c_double,
@@ -133,7 +135,8 @@ EXPORTS = ["szgb_create", "szgb_destroy", "szgb_set_stream", "szgb_compress_boun
            "szgb_decompress_noalloc", "szgb_compress_batch", "szgb_decompress_batch", "szgb_set_graphs",
            "szgb_server_create", "szgb_submit", "szgb_poll", "szgb_wait", "szgb_server_stats",
            "szgb_server_destroy", "szgb_autotune", "szgb_autotune_batch", "szgb_tune_save", "szgb_tune_load",
-           "szgb_quality_dev", "szgb_hit_count_dev", "szgb_suggest_m", "szgb_compress_4d"]
+           "szgb_quality_dev", "szgb_hit_count_dev", "szgb_suggest_m", "szgb_compress_4d",
+           "szgb_debug_set_wait_limit", "szgb_debug_skip_item"]
 
 
 VARIANT_EXACT, VARIANT_LATTICE = 0, 1
@@ -400,6 +403,20 @@ class Context:
     # -- batches -------------------------------------------------------------
     def set_graphs(self, on: bool):
         lib().szgb_set_graphs(self._h, 1 if on else 0)
+
+    def debug_set_wait_limit(self, ns: int):
+        """Test hook: limit of the device-side waits of later calls (0 = the
+        default, 4 s)."""
+        rc = lib().szgb_debug_set_wait_limit(self._h, int(ns))
+        if rc:
+            raise SzgbError(rc, "szgb_debug_set_wait_limit")
+
+    def debug_skip_item(self, item: int):
+        """Test hook: the wavefront work item `item` is never run (-1 = off),
+        so the waits of its consumers run out and calls return ETIMEOUT."""
+        rc = lib().szgb_debug_skip_item(self._h, int(item))
+        if rc:
+            raise SzgbError(rc, "szgb_debug_skip_item")
 
     def quality(self, x, y) -> dict:
         """Reconstruction quality of y against x (CUDA float32 tensors of one
