@@ -49,9 +49,18 @@
 namespace szgb {
 
 constexpr int kPFX = 4;   // x tiles are loaded this many sweeps ahead
-constexpr int kBarReady = 3;  // named barrier: the helper warps have made a sweep's inputs ready
-constexpr int kBarDone = 4;   // named barrier: the compute warps have finished a sweep
 constexpr int kBarEnd = 5;    // named barrier of the four helper warps at the end of an item
+// Per-sweep named barriers, two of each so that consecutive sweeps use
+// different ones: "ready u" (barrier 6 + u % 2: sweep u's inputs are ready)
+// and "done u" (barrier 8 + u % 2: the compute warps have finished sweep u).
+// Every warp of the item takes part in both.
+constexpr int kBarReady0 = 6;
+constexpr int kBarDone0 = 8;
+__device__ __forceinline__ void bar_ready_arrive(int u, int n) { named_bar_arrive(kBarReady0 + (u & 1), n); }
+__device__ __forceinline__ void bar_ready_sync(int u, int n) { named_bar_sync(kBarReady0 + (u & 1), n); }
+__device__ __forceinline__ void bar_done_arrive(int u, int n) { named_bar_arrive(kBarDone0 + (u & 1), n); }
+__device__ __forceinline__ void bar_done_sync(int u, int n) { named_bar_sync(kBarDone0 + (u & 1), n); }
+constexpr int kNoStop = 0x7fffffff;  // WaveCtl::stop_at when the item runs to the end
 constexpr int kTW = 32;   // staging tile: 32 rows x kTW columns
 constexpr int kTE = 32 * kTW;  // elements per staging tile
 constexpr int kTS = 3;    // staging ring slots per warp
@@ -387,7 +396,8 @@ struct Elems<true> {
 // Per-CTA control words of one work item.
 struct WaveCtl {
     unsigned int ticket;
-    int abort;     // written by the halo warp only; read after kBarReady
+    int stop_at;   // first sweep not to run (kNoStop: none); written by the
+                   // deciding halo warp before it arrives on that sweep's ready barrier
     int timeout;   // a compute warp's bounded wait ran out
     int err;       // an earlier stage failed (read once, by thread 0)
     int mbar_live; // the mbarriers hold a previous item's state
@@ -401,7 +411,15 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
     using C = Cfg<ND, NL>;
     using IT = typename Elems<DEC>::In;
     using OT = typename Elems<DEC>::Out;
-    const WaveGeom& g = A.g;
+    // value copies: in the batched kernel the arguments live in global
+    // memory, and every named barrier (a memory clobber) would force the
+    // per-sweep code to load them again
+    const WaveGeom g = A.g;
+    const uint64_t a_opitch = A.opitch;
+    const uint64_t a_timeout = A.timeout_ns;
+    const float* const a_x = A.x;
+    float* const a_out = A.out;
+    uint16_t* const a_codes = A.codes;
     // test hook: this item is never run and never publishes its state, so
     // its consumers' bounded waits run out (uniform over the CTA)
     if (g.debug_skip == item + 1) return;
@@ -425,7 +443,7 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
     const bool vec_o = A.vec_out != 0;
 
     if (threadIdx.x == 0) {
-        S.abort = 0;
+        S.stop_at = kNoStop;
         S.timeout = 0;
         S.err = *(volatile const unsigned*)&A.st->err != 0;
         if (tma_x) {
@@ -456,21 +474,27 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
 
     if (is_helper) {
         // ================= helper warps: halo lines in (W, W + 3), staging tiles (W + 1), halo lines out (W + 2)
-        // Iteration r of the helper warps: wait until the compute warps have
-        // finished the sweeps < r (barrier kBarDone), release sweep r
-        // (barrier kBarReady), then work while sweep r runs.
+        // Iteration r of the helper warps (pipelined barriers): arrive on
+        // "ready r" first (sweep r's inputs were prepared in iteration r - 1),
+        // then wait on "done r - 1" (the compute warps have finished the
+        // sweeps < r), then work while sweep r runs:
         //   halo-in warps (W, W + 3): land the halo blocks of sweep r + 1
         //     (requested in iteration r - 2) and request those of r + 3; W
-        //     decides whether the CTA stops (its arrival on kBarReady carries
-        //     the decision in S.abort).
+        //     decides whether the CTA stops and writes the decision
+        //     (S.stop_at = r) before its arrival on "ready r".
         //   staging warp (W + 1): waits until the x tiles of sweep r are in
-        //     (when they are not loaded by TMA), then loads x tiles ahead.
+        //     (when they are not loaded by TMA) before arriving, then loads x
+        //     tiles ahead and stores the first half of the output tile
+        //     finished in sweep r - 1.
         //   copy-out warp (W + 2): copies out the halo blocks completed in
-        //     sweep r - 1, stores the output tile finished in sweep r - 1
-        //     and, at the end, publishes the item's state.
-        // The helper warps other than W sync on kBarReady (instead of only
-        // arriving), so they see the decision in the same sweep as the
-        // compute warps.
+        //     sweep r - 1, stores the second half of that output tile and, at
+        //     the end, publishes the item's state.
+        // The helper warps other than W read the decision after "done r - 1"
+        // (the decider wrote it before taking part in that barrier; a later
+        // decision names a later sweep, so reading it early changes nothing),
+        // and sweep 0's after "ready 0".  Since helpers arrive on "ready r"
+        // before the compute warps finish sweep r - 1, the compute warps pass
+        // from one sweep to the next with a single barrier completion.
         // staging tiles of compute warp w: first row, valid rows, skew in
         // sweeps, and TMA coordinates (row, plane)
         auto tile_row0 = [&](int w) -> uint64_t {
@@ -514,63 +538,65 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
                     }
                 } else if constexpr (!DEC) {  // decompression always has TMA (its code array is ours)
                     const int nv = tile_rows(w);
-                    const float* xr = A.x + tile_row0(w) * g.N;
+                    const float* xr = a_x + tile_row0(w) * g.N;
                     const int col = c0 + lane;
                     for (int t = 0; t < 32; t++) {
                         const bool ok = t < nv && col < N;
                         cp_async4(slot + t * kTW + lane,
-                                  ok ? (const void*)(xr + (uint64_t)t * g.N + col) : (const void*)A.x, ok ? 4 : 0);
+                                  ok ? (const void*)(xr + (uint64_t)t * g.N + col) : (const void*)a_x, ok ? 4 : 0);
                     }
                 }
             }
         };
-        // store output tile kt of warp w: the staging warp reads the tile
-        // from shared memory and writes it with coalesced stores (16 bytes a
-        // lane when rows are 16-byte aligned: 4 lanes a u16 row, 8 an f32
-        // row).  A chunk that starts inside the row ends inside its pitch
-        // (codes: a pitch of whole 8-code chunks; values: 4 | N when aligned).
-        auto store_tile = [&](int w, int kt) {
+        // store rows [t_lo, t_hi) of output tile kt of warp w: read from
+        // shared memory, written with coalesced stores (16 bytes a lane when
+        // rows are 16-byte aligned: 4 lanes a u16 row, 8 an f32 row).  A
+        // chunk that starts inside the row ends inside its pitch (codes: a
+        // pitch of whole 8-code chunks; values: 4 | N when aligned).
+        auto store_tile = [&](int w, int kt, int t_lo, int t_hi) {
             const int c0 = kt * kTW;
             const OT* slot = OR + ((size_t)w * kTS + kt % kTS) * kTE;
             const int nv = tile_rows(w);
-            const uint64_t base = tile_row0(w) * A.opitch + (uint64_t)c0;
-            OT* const og = DEC ? reinterpret_cast<OT*>(A.out) : reinterpret_cast<OT*>(A.codes);
+            const uint64_t base = tile_row0(w) * a_opitch + (uint64_t)c0;
+            OT* const og = DEC ? reinterpret_cast<OT*>(a_out) : reinterpret_cast<OT*>(a_codes);
             if (vec_o) {
                 constexpr int EPC = 16 / (int)sizeof(OT);  // elements per 16-byte chunk
                 constexpr int CPR = kTW / EPC;             // chunks per tile row
                 constexpr int RPI = 32 / CPR;              // tile rows per warp instruction
                 const int cr = lane % CPR, rr = lane / CPR;
                 const bool in = c0 + cr * EPC < N;
-#pragma unroll
-                for (int t0 = 0; t0 < 32; t0 += RPI) {
+#pragma unroll 4
+                for (int t0 = t_lo; t0 < t_hi; t0 += RPI) {
                     const int t = t0 + rr;
                     if (!in || t >= nv) continue;
                     const uint4 v = *reinterpret_cast<const uint4*>(slot + t * kTW + cr * EPC);
-                    *reinterpret_cast<uint4*>(og + base + (uint64_t)t * A.opitch + cr * EPC) = v;
+                    *reinterpret_cast<uint4*>(og + base + (uint64_t)t * a_opitch + cr * EPC) = v;
                 }
             } else {
                 const bool in = c0 + lane < N;
-                for (int t0 = 0; t0 < nv; t0 += 8) {
+                for (int t0 = t_lo; t0 < min(nv, t_hi); t0 += 8) {
                     OT v[8];
 #pragma unroll
                     for (int i = 0; i < 8; i++) v[i] = slot[((t0 + i) & 31) * kTW + lane];
 #pragma unroll
                     for (int i = 0; i < 8; i++) {
                         if (!in || t0 + i >= nv) continue;
-                        og[base + (uint64_t)(t0 + i) * A.opitch + lane] = v[i];
+                        og[base + (uint64_t)(t0 + i) * a_opitch + lane] = v[i];
                     }
                 }
             }
         };
         const int nfull = N / kTW;  // full tiles per row
-        // in iteration r (sweeps < r complete): the full tile completed in sweep r - 1
-        auto flush = [&](int r) {
+        // in iteration r (sweeps < r complete): rows [t_lo, t_hi) of the full
+        // tile completed in sweep r - 1 (the staging and copy-out warps take
+        // half a tile each)
+        auto flush = [&](int r, int t_lo, int t_hi) {
             const int v = r - 16;
             if (v >= 0) {
                 const int w = v & 7;
                 if ((wv_mask >> w) & 1u) {
                     const int d = v - tile_s4(w);
-                    if (d >= 0 && (d >> 3) < nfull) store_tile(w, d >> 3);
+                    if (d >= 0 && (d >> 3) < nfull) store_tile(w, d >> 3, t_lo, t_hi);
                 }
             }
         };
@@ -598,7 +624,7 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
             int e_bstr[C::MAXE];              // words between consecutive blocks of the line
             const unsigned* e_prog[C::MAXE];  // the producer's state word (aborts)
             const int NE = (ND == 3) ? (NL * 32 + NL * W + NL * NL) : NL;
-    #pragma unroll
+#pragma unroll
             for (int j = 0; j < C::MAXE; j++) {
                 const int e = lane + 32 * j;
                 e_kind[j] = -1;
@@ -676,10 +702,10 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
             using PendB = int[C::MAXE];
             uint64_t pvA[C::MAXE][4], pvB[C::MAXE][4];
             int pbA[C::MAXE], pbB[C::MAXE];
-    #pragma unroll
+#pragma unroll
             for (int j = 0; j < C::MAXE; j++) pbA[j] = pbB[j] = -1;
             auto issue = [&](int u, PendV& pv, PendB& pb) {
-    #pragma unroll
+#pragma unroll
                 for (int j = 0; j < C::MAXE; j++) {
                     pb[j] = -1;
                     if (e_kind[j] < 0) continue;
@@ -690,7 +716,7 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
                 }
             };
             auto land = [&](PendV& pv, PendB& pb) {
-    #pragma unroll
+#pragma unroll
                 for (int j = 0; j < C::MAXE; j++) {
                     if (pb[j] < 0) continue;
                     const int b = pb[j];
@@ -703,7 +729,7 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
                                 ld_relaxed_block(e_src[j] + (size_t)b * e_bstr[j], pv[j]);
                                 if (halo_tagged(pv[j])) break;
                                 if ((it & 63) == 0 &&
-                                    (ld_acquire_u32(e_prog[j]) == kProgAbort || globaltimer() - t0 > A.timeout_ns ||
+                                    (ld_acquire_u32(e_prog[j]) == kProgAbort || globaltimer() - t0 > a_timeout ||
                                      it >= (1u << 28))) {
                                     timed_out = true;
                                     break;
@@ -726,33 +752,34 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
             }
             issue(2, pvA, pbA);
             issue(3, pvB, pbB);
-            // the deciding warp arrives on kBarReady with its decision in
-            // S.abort; the other syncs there to see it, and reports its own
-            // timeouts through S.timeout (read by the decider after kBarDone)
+            // sweep 0: the decider arrives with its decision, the other halo-in
+            // warp waits to read it and reports its own timeouts through
+            // S.timeout (read by the decider after a later done barrier)
             if (decider) {
-                if (lane == 0 && timed_out) S.abort = 1;
+                if (lane == 0 && timed_out) S.stop_at = 0;
                 __syncwarp();
-                named_bar_arrive(kBarReady, nthr_all);  // sweep 0
+                bar_ready_arrive(0, nthr_all);
             } else {
                 if (lane == 0 && timed_out) S.timeout = 1;
                 __syncwarp();
-                named_bar_sync(kBarReady, nthr_all);  // sweep 0
+                bar_ready_sync(0, nthr_all);
             }
-            bool stop = decider ? timed_out : (*(volatile int*)&S.abort != 0);
+            bool stop = decider ? timed_out : (*(volatile int*)&S.stop_at <= 0);
             for (int r = 1; r <= nsweeps && !stop; r++) {
-                named_bar_sync(kBarDone, nthr_all);  // sweeps < r are complete
                 if (decider) {
-                    stop = __any_sync(0xffffffffu, timed_out || *(volatile int*)&S.timeout != 0);
-                    if (lane == 0 && stop) S.abort = 1;
-                    __syncwarp();
-                    if (r < nsweeps) named_bar_arrive(kBarReady, nthr_all);  // sweep r
+                    if (r < nsweeps) {
+                        stop = __any_sync(0xffffffffu, timed_out || *(volatile int*)&S.timeout != 0);
+                        if (lane == 0 && stop) S.stop_at = r;
+                        __syncwarp();
+                        bar_ready_arrive(r, nthr_all);  // sweep r
+                    }
+                    bar_done_sync(r - 1, nthr_all);  // sweeps < r are complete
                 } else {
                     if (lane == 0 && timed_out) S.timeout = 1;
                     __syncwarp();
-                    if (r < nsweeps) {
-                        named_bar_sync(kBarReady, nthr_all);  // sweep r
-                        stop = *(volatile int*)&S.abort != 0;
-                    }
+                    if (r < nsweeps) bar_ready_arrive(r, nthr_all);  // sweep r
+                    bar_done_sync(r - 1, nthr_all);                  // sweeps < r are complete
+                    stop = *(volatile int*)&S.stop_at <= r;
                 }
                 if (stop) break;
                 if (r & 1) {
@@ -763,9 +790,10 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
                     issue(r + 3, pvB, pbB);
                 }
             }
-            if (lane == 0 && timed_out) S.abort = 1;
+            // a timeout in the last landing marks the item aborted
+            if (lane == 0 && timed_out) atomicMin(&S.stop_at, nsweeps);
             __syncwarp();
-            named_bar_sync(kBarEnd, 4 * 32);  // the helper warps see the final S.abort
+            named_bar_sync(kBarEnd, 4 * 32);  // the helper warps see the final S.stop_at
             return;
         }
         if (warp == W + 2) {
@@ -782,7 +810,7 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
             const float* c_src[MAXC];
             uint64_t* c_dst[MAXC];
             int c_off[MAXC], c_nblk[MAXC], c_smask[MAXC], c_sstride[MAXC], c_bstr[MAXC];
-    #pragma unroll
+#pragma unroll
             for (int j = 0; j < MAXC; j++) {
                 const int e = lane + 32 * j;
                 c_src[j] = nullptr;
@@ -825,7 +853,7 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
             }
             // in iteration r (sweeps < r complete): the blocks completed in sweep r - 1
             auto copy_out = [&](int r) {
-    #pragma unroll
+#pragma unroll
                 for (int j = 0; j < MAXC; j++) {
                     if (!c_src[j]) continue;
                     const int b = r - c_off[j];
@@ -835,34 +863,33 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
                                      halo_word(v.w));
                 }
             };
-            named_bar_sync(kBarReady, nthr_all);  // sweep 0
-            bool stop = *(volatile int*)&S.abort != 0;
+            bar_ready_sync(0, nthr_all);
+            bool stop = *(volatile int*)&S.stop_at <= 0;
             for (int r = 1; r <= nsweeps && !stop; r++) {
-                named_bar_sync(kBarDone, nthr_all);  // sweeps < r are complete
-                if (r < nsweeps) {
-                    named_bar_sync(kBarReady, nthr_all);  // sweep r
-                    stop = *(volatile int*)&S.abort != 0;
-                    if (stop) break;
-                }
+                if (r < nsweeps) bar_ready_arrive(r, nthr_all);  // sweep r
+                bar_done_sync(r - 1, nthr_all);                  // sweeps < r are complete
+                stop = *(volatile int*)&S.stop_at <= r;
+                if (stop) break;
                 copy_out(r);
-                flush(r);
+                flush(r, 16, 32);
             }
             __syncwarp();
             named_bar_sync(kBarEnd, 4 * 32);
-            if (!S.abort) {
+            const bool aborted = S.stop_at != kNoStop;
+            if (!aborted) {
                 // the halo blocks completed in the last sweeps
                 for (int r = nsweeps; r <= nsweeps + 9 * W + 9; r++) copy_out(r);
                 // the tiles not stored yet (every sweep is complete)
                 const int ntl = (N + kTW - 1) / kTW;
                 for (int w = 0; w < W; w++) {
                     if (!((wv_mask >> w) & 1u)) continue;
-                    for (int kt = flushed_in_loop(w); kt < ntl; kt++) store_tile(w, kt);
+                    for (int kt = flushed_in_loop(w); kt < ntl; kt++) store_tile(w, kt, 0, 32);
                 }
             }
             fence_acq_rel_gpu();
             __syncwarp();
             if (lane == 0) {
-                if (S.abort) {
+                if (aborted) {
                     atomicOr(&A.st->err, kErrTimeout);
                     st_release_u32(my_prog, kProgAbort);
                 } else {
@@ -877,25 +904,24 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
         cp_async_commit();
         cp_async_wait<0>();
         __syncwarp();
-        named_bar_sync(kBarReady, nthr_all);  // sweep 0
-        bool stop = *(volatile int*)&S.abort != 0;
+        bar_ready_sync(0, nthr_all);
+        bool stop = *(volatile int*)&S.stop_at <= 0;
         for (int r = 1; r <= nsweeps && !stop; r++) {
-            named_bar_sync(kBarDone, nthr_all);  // sweeps < r are complete
-            cp_async_wait<kPFX - 1>();           // x tiles of sweep r (when not loaded by TMA)
+            cp_async_wait<kPFX - 1>();  // x tiles of sweep r (when not loaded by TMA)
             __syncwarp();
-            if (r < nsweeps) {
-                named_bar_sync(kBarReady, nthr_all);  // sweep r
-                stop = *(volatile int*)&S.abort != 0;
-                if (stop) break;
-            }
+            if (r < nsweeps) bar_ready_arrive(r, nthr_all);  // sweep r
+            bar_done_sync(r - 1, nthr_all);                  // sweeps < r are complete
+            stop = *(volatile int*)&S.stop_at <= r;
+            if (stop) break;
             issue_x(r + kPFX);
             u_issued = r + kPFX;
             cp_async_commit();
+            flush(r, 0, 16);
         }
         cp_async_wait<0>();
         __syncwarp();
         named_bar_sync(kBarEnd, 4 * 32);
-        if (tma_x && S.abort && lane == 0) {
+        if (tma_x && S.stop_at != kNoStop && lane == 0) {
             // loads still in flight land in this CTA's shared memory: wait
             // for the latest load of every slot (the last 8 kTS sweeps issued
             // hold it) before leaving
@@ -905,7 +931,7 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
                 const int d = u - tile_s4(w);
                 if (d < 0 || (d >> 3) * kTW >= N) continue;
                 const int kt = d >> 3;
-                mbar_wait_bounded(MB + w * kTS + kt % kTS, (unsigned)(kt / kTS) & 1u, A.timeout_ns);
+                mbar_wait_bounded(MB + w * kTS + kt % kTS, (unsigned)(kt / kTS) & 1u, a_timeout);
             }
         }
         __syncwarp();
@@ -933,7 +959,7 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
     const uint64_t rowbase = rowid * g.N;
     float* const rec_row = TR ? A.recorded + rowbase : nullptr;
     const IT* const xw = XR + (size_t)warp * kTS * kTE + lane * kTW;  // this lane's tile rows
-    const float* const out_row = DEC ? A.out + rowbase : nullptr;       // unpredictable values (decompress)
+    const float* const out_row = DEC ? a_out + rowbase : nullptr;       // unpredictable values (decompress)
     OT* const ow = OR + (size_t)warp * kTS * kTE + lane * kTW;
     const int col0 = -lane - sig;  // column at step 0
 
@@ -967,14 +993,14 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
 
 
     for (int q = 0; q < nsweeps; q++) {
-        named_bar_sync(kBarReady, nthr_all);  // this sweep's inputs are ready
-        if (*(volatile int*)&S.abort) break;
+        bar_ready_sync(q, nthr_all);  // this sweep's inputs are ready
+        if (*(volatile int*)&S.stop_at <= q) break;
         // this warp's next x tile is first read in this sweep: wait for its load
         if (tma_x && wvalid) {
             const int d = q - s4;
             if (d >= 0 && (d & 7) == 0 && (d >> 3) * kTW < N) {
                 const int kt = d >> 3;
-                if (!mbar_wait_bounded(MB + warp * kTS + kt % kTS, (unsigned)(kt / kTS) & 1u, A.timeout_ns)) {
+                if (!mbar_wait_bounded(MB + warp * kTS + kt % kTS, (unsigned)(kt / kTS) & 1u, a_timeout)) {
                     if (lane == 0) {
                         atomicOr(&A.st->err, kErrTimeout);
                         S.timeout = 1;  // the halo warp stops the CTA after this sweep
@@ -986,162 +1012,238 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
         const int wl0 = 4 * q - sig;  // lane 0's column at step 0 (warp-uniform)
         // a warp is idle in sweeps where none of its lanes has a column
         if (wl0 + 3 >= 0 && wl0 - 31 < N) {
-            float4 pr[NL + 1];
-            if (ND == 3) {
-                const int blk = (q - warp) & (kRP / 4 - 1);
+            // 3D, one layer, a sweep whose 4 columns lie inside the row for
+            // every lane: the same terms, order and arithmetic as the general
+            // step below, without its boundary cases (the rows above lane 0
+            // come as one float4 per sweep)
+            bool interior = false;
+            if constexpr (ND == 3 && NL == 1) {
+                if (wl0 >= 31 && wl0 + 3 < N) {
+                    interior = true;
+                    const int blk = (q - warp) & (kRP / 4 - 1);
+                    const float4 p4 = *reinterpret_cast<const float4*>(PR + ((size_t)warp * 32 + lane) * kRPS + blk * 4);
+                    const int cl0 = wl0 & (kRV - 1);
+                    const float4 r4 = *reinterpret_cast<const float4*>(vr_own + cl0);
+                    const float4 q4 = *reinterpret_cast<const float4*>(VR + (size_t)warp * kRV + cl0);
+                    const int c0 = lq & (kTW - 1);
+                    const int sl0 = (int)(((unsigned)lq >> 5) % kTS) * kTE;
+                    const int sl1 = (sl0 == (kTS - 1) * kTE) ? 0 : sl0 + kTE;
+                    int tix[kTile];
 #pragma unroll
-                for (int a = 1; a <= NL; a++)
-                    pr[a] = *reinterpret_cast<const float4*>(PR + ((size_t)(warp + NL - a) * 32 + lane) * kRPS + blk * 4);
+                    for (int k = 0; k < kTile; k++) tix[k] = (c0 + k >= kTW) ? sl1 + c0 + k - kTW : sl0 + c0 + k;
+                    int dc[kTile];
+                    float du[kTile];
+                    if constexpr (DEC) {
+#pragma unroll
+                        for (int k = 0; k < kTile; k++) {
+                            dc[k] = (int)xw[tix[k]];
+                            du[k] = 0.0f;
+                            if (dc[k] == 0 && valid) du[k] = out_row[lq + k];
+                        }
+                    }
+                    float vo[kTile];
+#pragma unroll
+                    for (int k = 0; k < kTile; k++) {
+                        const float pk = (k == 0) ? p4.x : (k == 1) ? p4.y : (k == 2) ? p4.z : p4.w;
+                        const float rk = (k == 0) ? r4.x : (k == 1) ? r4.y : (k == 2) ? r4.z : r4.w;
+                        const float qk = (k == 0) ? q4.x : (k == 1) ? q4.y : (k == 2) ? q4.z : q4.w;
+                        float nr = __shfl_up_sync(0xffffffffu, oV[1], 1);
+                        float nq = __shfl_up_sync(0xffffffffu, Pp[1][0], 1);
+                        nr = (lane == 0) ? rk : nr;
+                        nq = (lane == 0) ? qk : nq;
+                        Rr[1][1] = Rr[1][0];
+                        Rr[1][0] = nr;
+                        Pp[1][1] = Pp[1][0];
+                        Pp[1][0] = pk;
+                        Qq[1][1][1] = Qq[1][1][0];
+                        Qq[1][1][0] = nq;
+                        // descending (a, b, e): +(1,1,1) -(1,1,0) -(1,0,1) +(1,0,0) -(0,1,1) +(0,1,0) +(0,0,1)
+                        float pred = Qq[1][1][1];
+                        pred = __fsub_rn(pred, Qq[1][1][0]);
+                        pred = __fsub_rn(pred, Pp[1][1]);
+                        pred = __fadd_rn(pred, Pp[1][0]);
+                        pred = __fsub_rn(pred, Rr[1][1]);
+                        pred = __fadd_rn(pred, Rr[1][0]);
+                        pred = __fadd_rn(pred, oV[1]);
+                        float V;
+                        if constexpr (!DEC) {
+                            const float xv = xw[tix[k]];
+                            const float tr = trunc_value(xv, qp.e_eb);
+                            const int code = quantize_tr(xv, pred, tr, qp, V);
+                            ow[tix[k]] = (uint16_t)code;
+                        } else {
+                            V = dc[k] ? dequantize(dc[k], pred, qp) : du[k];
+                            ow[tix[k]] = V;
+                        }
+                        oV[1] = V;
+                        vo[k] = V;
+                        st_shared_f32_if(has_hr, hr_addr + 4u * (uint32_t)((lq + k) & (kRV - 1)), V);
+                        if constexpr (TR) {
+                            if (valid) rec_row[lq + k] = V;
+                        }
+                    }
+                    *reinterpret_cast<float4*>(PR + ((size_t)(warp + NL) * 32 + lane) * kRPS + blk * 4) =
+                        make_float4(vo[0], vo[1], vo[2], vo[3]);
+                }
             }
-            float vout[kTile];
-            // staging slots of this sweep's columns (a sweep spans at most two tiles)
-            const unsigned kt0 = lq > 0 ? (unsigned)lq >> 5 : 0u;
-            const int sl0 = (int)(kt0 % kTS) * kTE;
-            const int sl1 = (sl0 == (kTS - 1) * kTE) ? 0 : sl0 + kTE;
-            // decompression: this sweep's codes and, for code 0, the stored
-            // values, read before the dependent steps so that the loads'
-            // latency overlaps them
-            int dcode[kTile];
-            float duv[kTile];
-            if constexpr (DEC) {
+            if (!interior) {
+                float4 pr[NL + 1];
+                if (ND == 3) {
+                    const int blk = (q - warp) & (kRP / 4 - 1);
+#pragma unroll
+                    for (int a = 1; a <= NL; a++)
+                        pr[a] = *reinterpret_cast<const float4*>(PR + ((size_t)(warp + NL - a) * 32 + lane) * kRPS + blk * 4);
+                }
+                float vout[kTile];
+                // staging slots of this sweep's columns (a sweep spans at most two tiles)
+                const unsigned kt0 = lq > 0 ? (unsigned)lq >> 5 : 0u;
+                const int sl0 = (int)(kt0 % kTS) * kTE;
+                const int sl1 = (sl0 == (kTS - 1) * kTE) ? 0 : sl0 + kTE;
+                // decompression: this sweep's codes and, for code 0, the stored
+                // values, read before the dependent steps so that the loads'
+                // latency overlaps them
+                int dcode[kTile];
+                float duv[kTile];
+                if constexpr (DEC) {
+#pragma unroll
+                    for (int k = 0; k < kTile; k++) {
+                        const int l = lq + k;
+                        const bool act = (l >= 0) && (l < N);
+                        const bool cross = lq >= 0 && (lq & (kTW - 1)) + k >= kTW;
+                        const int ti = (cross ? sl1 : sl0) + (l & (kTW - 1));
+                        dcode[k] = act ? (int)xw[ti] : 0;
+                        duv[k] = 0.0f;
+                        if (dcode[k] == 0 && valid && act) duv[k] = out_row[l];
+                    }
+                }
 #pragma unroll
                 for (int k = 0; k < kTile; k++) {
                     const int l = lq + k;
                     const bool act = (l >= 0) && (l < N);
+                    // position of column l in this lane's staging rows
                     const bool cross = lq >= 0 && (lq & (kTW - 1)) + k >= kTW;
                     const int ti = (cross ? sl1 : sl0) + (l & (kTW - 1));
-                    dcode[k] = act ? (int)xw[ti] : 0;
-                    duv[k] = 0.0f;
-                    if (dcode[k] == 0 && valid && act) duv[k] = out_row[l];
-                }
-            }
+                    // ---- new neighbour values at column l (shuffles first: they
+                    // read the values of the previous step)
+                    float nR[NL + 1], nP[NL + 1], nQ[NL + 1][NL + 1];
+                    // row t - b at column l is row (t - 1) - (b - 1) of the lane above,
+                    // which held column l in the previous step
+                    nR[1] = __shfl_up_sync(0xffffffffu, oV[1], 1);
 #pragma unroll
-            for (int k = 0; k < kTile; k++) {
-                const int l = lq + k;
-                const bool act = (l >= 0) && (l < N);
-                // position of column l in this lane's staging rows
-                const bool cross = lq >= 0 && (lq & (kTW - 1)) + k >= kTW;
-                const int ti = (cross ? sl1 : sl0) + (l & (kTW - 1));
-                // ---- new neighbour values at column l (shuffles first: they
-                // read the values of the previous step)
-                float nR[NL + 1], nP[NL + 1], nQ[NL + 1][NL + 1];
-                // row t - b at column l is row (t - 1) - (b - 1) of the lane above,
-                // which held column l in the previous step
-                nR[1] = __shfl_up_sync(0xffffffffu, oV[1], 1);
+                    for (int b = 2; b <= NL; b++) nR[b] = __shfl_up_sync(0xffffffffu, Rr[b - 1][0], 1);
+                    if (ND == 3) {
 #pragma unroll
-                for (int b = 2; b <= NL; b++) nR[b] = __shfl_up_sync(0xffffffffu, Rr[b - 1][0], 1);
-                if (ND == 3) {
+                        for (int a = 1; a <= NL; a++) {
+                            nP[a] = (k == 0) ? pr[a].x : (k == 1) ? pr[a].y : (k == 2) ? pr[a].z : pr[a].w;
+                            nQ[a][1] = __shfl_up_sync(0xffffffffu, Pp[a][0], 1);
 #pragma unroll
-                    for (int a = 1; a <= NL; a++) {
-                        nP[a] = (k == 0) ? pr[a].x : (k == 1) ? pr[a].y : (k == 2) ? pr[a].z : pr[a].w;
-                        nQ[a][1] = __shfl_up_sync(0xffffffffu, Pp[a][0], 1);
-#pragma unroll
-                        for (int b = 2; b <= NL; b++) nQ[a][b] = __shfl_up_sync(0xffffffffu, Qq[a][b - 1][0], 1);
-                    }
-                }
-                // lanes next to the top of the block read the rows above
-                // (every lane loads, from a clamped line; lanes >= b discard)
-                if (ND >= 2) {
-                    const int cl = l & (kRV - 1);
-#pragma unroll
-                    for (int b = 1; b <= NL; b++) {
-                        const int vr = min(NL + lane - b, NL - 1);
-                        const bool top = lane < b;
-                        const float r_v = vr_own[vr * kRV + cl];
-                        nR[b] = top ? r_v : nR[b];
-                        if (ND == 3) {
-#pragma unroll
-                            for (int a = 1; a <= NL; a++) {
-                                const float q_v = VR[((size_t)(warp + NL - a) * NL + vr) * kRV + cl];
-                                nQ[a][b] = top ? q_v : nQ[a][b];
-                            }
+                            for (int b = 2; b <= NL; b++) nQ[a][b] = __shfl_up_sync(0xffffffffu, Qq[a][b - 1][0], 1);
                         }
                     }
-                }
-                // shift histories, insert (zeros outside the row)
-#pragma unroll
-                for (int b = 1; b <= NL; b++) {
-#pragma unroll
-                    for (int e = NL; e >= 1; e--) Rr[b][e] = Rr[b][e - 1];
-                    Rr[b][0] = act ? nR[b] : 0.0f;
-                }
-                if (ND == 3) {
-#pragma unroll
-                    for (int a = 1; a <= NL; a++) {
-#pragma unroll
-                        for (int e = NL; e >= 1; e--) Pp[a][e] = Pp[a][e - 1];
-                        Pp[a][0] = act ? nP[a] : 0.0f;
+                    // lanes next to the top of the block read the rows above
+                    // (every lane loads, from a clamped line; lanes >= b discard)
+                    if (ND >= 2) {
+                        const int cl = l & (kRV - 1);
 #pragma unroll
                         for (int b = 1; b <= NL; b++) {
+                            const int vr = min(NL + lane - b, NL - 1);
+                            const bool top = lane < b;
+                            const float r_v = vr_own[vr * kRV + cl];
+                            nR[b] = top ? r_v : nR[b];
+                            if (ND == 3) {
 #pragma unroll
-                            for (int e = NL; e >= 1; e--) Qq[a][b][e] = Qq[a][b][e - 1];
-                            Qq[a][b][0] = act ? nQ[a][b] : 0.0f;
-                        }
-                    }
-                }
-                // ---- prediction: terms in descending lexicographic (a, b, e)
-                float pred = 0.0f;
-                bool first = true;
-                constexpr int AA = (ND == 3) ? NL : 0;
-                constexpr int BB = (ND >= 2) ? NL : 0;
-#pragma unroll
-                for (int a = AA; a >= 0; a--) {
-#pragma unroll
-                    for (int b = BB; b >= 0; b--) {
-#pragma unroll
-                        for (int e = NL; e >= 0; e--) {
-                            if (a == 0 && b == 0 && e == 0) continue;
-                            const float v = (a > 0 && b > 0) ? Qq[a][b][e]
-                                          : (a > 0)          ? Pp[a][e]
-                                          : (b > 0)          ? Rr[b][e]
-                                                             : oV[e];
-                            const int c = term_coef(NL, a, b, e);
-                            if (NL == 1) {
-                                if (first) pred = (c > 0) ? v : -v;
-                                else pred = (c > 0) ? __fadd_rn(pred, v) : __fsub_rn(pred, v);
-                            } else {
-                                const float prod = __fmul_rn((float)c, v);
-                                pred = first ? prod : __fadd_rn(pred, prod);
+                                for (int a = 1; a <= NL; a++) {
+                                    const float q_v = VR[((size_t)(warp + NL - a) * NL + vr) * kRV + cl];
+                                    nQ[a][b] = top ? q_v : nQ[a][b];
+                                }
                             }
-                            first = false;
                         }
                     }
-                }
-                // ---- quantize (compress) / decode + dequantize (decompress)
-                float V;
-                int code = 0;
-                if constexpr (!DEC) {
-                    const float xv = act ? xw[ti] : 0.0f;
-                    const float tr = trunc_value(xv, qp.e_eb);
-                    code = quantize_tr(xv, pred, tr, qp, V);
-                } else {
-                    // the decode pass left the code in the tile and, for code
-                    // 0, the unpredictable value in the output array
-                    code = dcode[k];
-                    V = code ? dequantize(code, pred, qp) : duv[k];
-                }
-                V = act ? V : 0.0f;
+                    // shift histories, insert (zeros outside the row)
 #pragma unroll
-                for (int e = NL; e >= 2; e--) oV[e] = oV[e - 1];
-                oV[1] = V;
-                vout[k] = V;
-                if (act) {
-                    if constexpr (DEC) ow[ti] = V;
-                    else ow[ti] = (uint16_t)code;
+                    for (int b = 1; b <= NL; b++) {
+#pragma unroll
+                        for (int e = NL; e >= 1; e--) Rr[b][e] = Rr[b][e - 1];
+                        Rr[b][0] = act ? nR[b] : 0.0f;
+                    }
+                    if (ND == 3) {
+#pragma unroll
+                        for (int a = 1; a <= NL; a++) {
+#pragma unroll
+                            for (int e = NL; e >= 1; e--) Pp[a][e] = Pp[a][e - 1];
+                            Pp[a][0] = act ? nP[a] : 0.0f;
+#pragma unroll
+                            for (int b = 1; b <= NL; b++) {
+#pragma unroll
+                                for (int e = NL; e >= 1; e--) Qq[a][b][e] = Qq[a][b][e - 1];
+                                Qq[a][b][0] = act ? nQ[a][b] : 0.0f;
+                            }
+                        }
+                    }
+                    // ---- prediction: terms in descending lexicographic (a, b, e)
+                    float pred = 0.0f;
+                    bool first = true;
+                    constexpr int AA = (ND == 3) ? NL : 0;
+                    constexpr int BB = (ND >= 2) ? NL : 0;
+#pragma unroll
+                    for (int a = AA; a >= 0; a--) {
+#pragma unroll
+                        for (int b = BB; b >= 0; b--) {
+#pragma unroll
+                            for (int e = NL; e >= 0; e--) {
+                                if (a == 0 && b == 0 && e == 0) continue;
+                                const float v = (a > 0 && b > 0) ? Qq[a][b][e]
+                                              : (a > 0)          ? Pp[a][e]
+                                              : (b > 0)          ? Rr[b][e]
+                                                                 : oV[e];
+                                const int c = term_coef(NL, a, b, e);
+                                if (NL == 1) {
+                                    if (first) pred = (c > 0) ? v : -v;
+                                    else pred = (c > 0) ? __fadd_rn(pred, v) : __fsub_rn(pred, v);
+                                } else {
+                                    const float prod = __fmul_rn((float)c, v);
+                                    pred = first ? prod : __fadd_rn(pred, prod);
+                                }
+                                first = false;
+                            }
+                        }
+                    }
+                    // ---- quantize (compress) / decode + dequantize (decompress)
+                    float V;
+                    int code = 0;
+                    if constexpr (!DEC) {
+                        const float xv = act ? xw[ti] : 0.0f;
+                        const float tr = trunc_value(xv, qp.e_eb);
+                        code = quantize_tr(xv, pred, tr, qp, V);
+                    } else {
+                        // the decode pass left the code in the tile and, for code
+                        // 0, the unpredictable value in the output array
+                        code = dcode[k];
+                        V = code ? dequantize(code, pred, qp) : duv[k];
+                    }
+                    V = act ? V : 0.0f;
+#pragma unroll
+                    for (int e = NL; e >= 2; e--) oV[e] = oV[e - 1];
+                    oV[1] = V;
+                    vout[k] = V;
+                    if (act) {
+                        if constexpr (DEC) ow[ti] = V;
+                        else ow[ti] = (uint16_t)code;
+                    }
+                    st_shared_f32_if(has_hr && act, hr_addr + 4u * (uint32_t)(l & (kRV - 1)), V);
+                    if constexpr (TR) {
+                        if (valid && act) rec_row[l] = V;
+                    }
                 }
-                st_shared_f32_if(has_hr && act, hr_addr + 4u * (uint32_t)(l & (kRV - 1)), V);
-                if constexpr (TR) {
-                    if (valid && act) rec_row[l] = V;
+                // this sweep's 4 values, diagonal block q - warp: plane ring and plane halo
+                if (ND == 3) {
+                    const int blk = q - warp;
+                    const float4 v4 = make_float4(vout[0], vout[1], vout[2], vout[3]);
+                    *reinterpret_cast<float4*>(PR + ((size_t)(warp + NL) * 32 + lane) * kRPS + (blk & (kRP / 4 - 1)) * 4) = v4;
                 }
-            }
-            // this sweep's 4 values, diagonal block q - warp: plane ring and plane halo
-            if (ND == 3) {
-                const int blk = q - warp;
-                const float4 v4 = make_float4(vout[0], vout[1], vout[2], vout[3]);
-                *reinterpret_cast<float4*>(PR + ((size_t)(warp + NL) * 32 + lane) * kRPS + (blk & (kRP / 4 - 1)) * 4) = v4;
             }
         }
-        named_bar_arrive(kBarDone, nthr_all);  // this warp has finished the sweep
+        bar_done_arrive(q, nthr_all);  // this warp has finished the sweep
     }
 }
 
