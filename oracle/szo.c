@@ -429,7 +429,8 @@ size_t szo_stream_bound(int ndim, const uint64_t *shape) {
     uint64_t d[4];
     if (norm_shape4(ndim, shape, d)) return 0;
     uint64_t N = d[0] * d[1] * d[2] * d[3], rows = d[0] * d[1] * d[2];
-    return (size_t)(HDR_BYTES + pad4(3 * 65536) + pad4(4 * rows) + rows + (N * 78 + 7) / 8 + 16);
+    uint64_t nch = rows * ((d[3] + 31) / 32); /* the most chunks: 32 points each */
+    return (size_t)(HDR_BYTES + pad4(3 * 65536) + pad4(4 * nch) + nch + (N * 78 + 7) / 8 + 16);
 }
 
 /* ------------------------------------------------------------------ */
@@ -439,7 +440,24 @@ int szo_compress(const float *x, int ndim, const uint64_t *shape, int mode,
                  double eb_abs, double eb_rel, int layers, int m, double theta,
                  int order, uint8_t *out, size_t out_cap, size_t *out_len,
                  float *recorded_out, uint16_t *codes_out) {
+    return szo_compress_chunked(x, ndim, shape, mode, eb_abs, eb_rel, layers, m, theta, order, 0, out, out_cap,
+                                out_len, recorded_out, codes_out);
+}
+
+/* chunk length along a row: chunk_points when it splits the row, else the
+ * whole row (0: whole rows) */
+static uint64_t chunk_len(uint32_t chunk_points, uint64_t row_len) {
+    return (chunk_points == 0 || chunk_points >= row_len) ? row_len : chunk_points;
+}
+
+static int chunk_points_valid(uint32_t c) { return c == 0 || (c >= 32 && (c & (c - 1)) == 0); }
+
+int szo_compress_chunked(const float *x, int ndim, const uint64_t *shape, int mode,
+                         double eb_abs, double eb_rel, int layers, int m, double theta,
+                         int order, uint32_t chunk_points, uint8_t *out, size_t out_cap, size_t *out_len,
+                         float *recorded_out, uint16_t *codes_out) {
     uint64_t d[4];
+    if (!chunk_points_valid(chunk_points)) return SZO_EINVAL;
     if (norm_shape4(ndim, shape, d) || !x || !out_len) return SZO_EINVAL;
     if (mode < 0 || mode > 2 || layers < 1 || layers > 4) return SZO_EINVAL;
     if (m != 0 && (m < 2 || m > 16)) return SZO_EINVAL;
@@ -514,25 +532,29 @@ int szo_compress(const float *x, int ndim, const uint64_t *shape, int mode,
     uint32_t nsym = 0;
     for (int s = 0; s < nsymtot; s++) nsym += (len[s] != 0);
 
-    /* per-row bit counts: code bits, plus 9 + t record bits for code 0 */
+    /* chunks: each row is cut into pieces of Ce points (the last one
+     * shorter), taken row by row; per-chunk bit counts are the code bits plus
+     * 9 + t record bits after every code 0, rounded up to whole bytes */
     uint64_t rows = d[0] * d[1] * d[2], Nr = d[3];
-    uint64_t *rowbytes = (uint64_t *)malloc(sizeof(uint64_t) * rows);
+    uint64_t Ce = chunk_len(chunk_points, Nr), nseg = (Nr + Ce - 1) / Ce, nch = rows * nseg;
+    uint64_t *rowbytes = (uint64_t *)malloc(sizeof(uint64_t) * nch);
     if (!rowbytes) { free(t); free(V); free(code); free(freq); free(len); free(cw); return SZO_ENOMEM; }
     uint64_t payload = 0, maxrow = 0;
-    for (uint64_t r = 0; r < rows; r++) {
+    for (uint64_t ch = 0; ch < nch; ch++) {
+        uint64_t r = ch / nseg, l0 = (ch % nseg) * Ce, l1 = l0 + Ce < Nr ? l0 + Ce : Nr;
         uint64_t bits = 0;
-        for (uint64_t l = 0; l < Nr; l++) {
+        for (uint64_t l = l0; l < l1; l++) {
             uint64_t p = r * Nr + l;
             bits += len[code[p]];
             if (code[p] == 0) bits += 9 + (uint64_t)szo_truncate(x[p], eb_f, NULL);
         }
-        rowbytes[r] = (bits + 7) / 8;
-        payload += rowbytes[r];
-        if (rowbytes[r] > maxrow) maxrow = rowbytes[r];
+        rowbytes[ch] = (bits + 7) / 8;
+        payload += rowbytes[ch];
+        if (rowbytes[ch] > maxrow) maxrow = rowbytes[ch];
     }
     int tw = maxrow <= 0xffff ? 2 : 4;
     uint64_t cb_bytes = pad4(3 * (uint64_t)nsym);
-    uint64_t tab_bytes = pad4((uint64_t)tw * rows);
+    uint64_t tab_bytes = pad4((uint64_t)tw * nch);
     uint64_t total = HDR_BYTES + cb_bytes + tab_bytes + payload;
     *out_len = (size_t)total;
     int rc = SZO_OK;
@@ -550,9 +572,10 @@ int szo_compress(const float *x, int ndim, const uint64_t *shape, int mode,
     if (ndim == 4) wr64(out + 120, d[0]);
     wrf64(out + 40, eb_abs); wrf64(out + 48, eb_rel);
     wr32(out + 56, f2u(eb_f)); wr32(out + 60, f2u(xmin)); wr32(out + 64, f2u(xmax));
-    wr32(out + 68, nsym); wr64(out + 72, rows); wr64(out + 80, K);
+    wr32(out + 68, nsym); wr64(out + 72, nch); wr64(out + 80, K);
     wr64(out + 88, payload); wr64(out + 96, total);
     wrf64(out + 104, theta); out[112] = (uint8_t)adaptive;
+    wr32(out + 116, Ce < Nr ? (uint32_t)Ce : 0u); /* chunk length; 0: whole rows */
 
     /* codebook: (symbol, length) for the used symbols, ascending symbol */
     {
@@ -564,18 +587,19 @@ int szo_compress(const float *x, int ndim, const uint64_t *shape, int mode,
     /* chunk table */
     {
         uint8_t *tb = out + HDR_BYTES + cb_bytes;
-        for (uint64_t r = 0; r < rows; r++) {
-            if (tw == 2) wr16(tb + 2 * r, (uint16_t)rowbytes[r]);
-            else wr32(tb + 4 * r, (uint32_t)rowbytes[r]);
+        for (uint64_t ch = 0; ch < nch; ch++) {
+            if (tw == 2) wr16(tb + 2 * ch, (uint16_t)rowbytes[ch]);
+            else wr32(tb + 4 * ch, (uint32_t)rowbytes[ch]);
         }
     }
-    /* payload */
+    /* payload: every chunk starts on a byte */
     {
         uint8_t *pl = out + HDR_BYTES + cb_bytes + tab_bytes;
         uint64_t off = 0;
-        for (uint64_t r = 0; r < rows; r++) {
+        for (uint64_t ch = 0; ch < nch; ch++) {
+            uint64_t r = ch / nseg, l0 = (ch % nseg) * Ce, l1 = l0 + Ce < Nr ? l0 + Ce : Nr;
             bw_t w = {pl + off, 0};
-            for (uint64_t l = 0; l < Nr; l++) {
+            for (uint64_t l = l0; l < l1; l++) {
                 uint64_t p = r * Nr + l;
                 put_bits(&w, cw[code[p]], len[code[p]]);
                 if (code[p] == 0) {
@@ -586,7 +610,7 @@ int szo_compress(const float *x, int ndim, const uint64_t *shape, int mode,
                     if (tt) put_bits(&w, (u >> (23 - tt)) & ((1u << tt) - 1u), tt);
                 }
             }
-            off += rowbytes[r];
+            off += rowbytes[ch];
         }
     }
     if (recorded_out) memcpy(recorded_out, V, sizeof(float) * N);
@@ -831,9 +855,13 @@ int szo_decompress(const uint8_t *in, size_t in_len, float *out, size_t out_cap_
     if (out_cap_elems < N) return SZO_EINVAL;
     float eb_f = u2f(rd32(in + 56));
     uint32_t nsym = rd32(in + 68);
-    uint64_t rows = rd64(in + 72), K = rd64(in + 80), payload = rd64(in + 88), total = rd64(in + 96);
-    if (rows != d[0] * d[1] * d[2] || nsym < 1 || nsym > (1u << m)) return SZO_ECORRUPT;
-    uint64_t cb_bytes = pad4(3 * (uint64_t)nsym), tab_bytes = pad4((uint64_t)tw * rows);
+    uint64_t nch = rd64(in + 72), K = rd64(in + 80), payload = rd64(in + 88), total = rd64(in + 96);
+    uint64_t rows = d[0] * d[1] * d[2], Nr = d[3];
+    uint32_t cpts = rd32(in + 116); /* chunk length; 0: whole rows */
+    if (cpts && (!chunk_points_valid(cpts) || cpts >= Nr)) return SZO_ECORRUPT;
+    uint64_t Ce = chunk_len(cpts, Nr), nseg = (Nr + Ce - 1) / Ce;
+    if (nch != rows * nseg || nsym < 1 || nsym > (1u << m)) return SZO_ECORRUPT;
+    uint64_t cb_bytes = pad4(3 * (uint64_t)nsym), tab_bytes = pad4((uint64_t)tw * nch);
     if (total != HDR_BYTES + cb_bytes + tab_bytes + payload || total > in_len) return SZO_ECORRUPT;
 
     int nsymtot = 1 << m;
@@ -870,7 +898,7 @@ int szo_decompress(const uint8_t *in, size_t in_len, float *out, size_t out_cap_
     }
 
     const int lattice = in[113] == 1;
-    if (in[113] > 1 || (lattice && ndim > 3)) { free(len); free(cw); free(sorted_sym); return SZO_ECORRUPT; }
+    if (in[113] > 1 || (lattice && (ndim > 3 || cpts))) { free(len); free(cw); free(sorted_sym); return SZO_ECORRUPT; }
     const uint64_t d3[3] = {d[1], d[2], d[3]}; /* the lattice variant's 3-axis view (d[0] = 1) */
     int T;
     term_t *t = make_terms(ndim, layers, &T);
@@ -881,14 +909,16 @@ int szo_decompress(const uint8_t *in, size_t in_len, float *out, size_t out_cap_
     const uint8_t *pl = tb + tab_bytes;
     float twoeb = 2.0f * eb_f;
     int rc = SZO_OK;
-    uint64_t off = 0, Kseen = 0, Nr = d[3];
-    for (uint64_t r = 0; r < rows && rc == SZO_OK; r++) {
-        uint64_t nb = (tw == 2) ? rd16(tb + 2 * r) : rd32(tb + 4 * r);
+    uint64_t off = 0, Kseen = 0;
+    for (uint64_t ch = 0; ch < nch && rc == SZO_OK; ch++) {
+        uint64_t nb = (tw == 2) ? rd16(tb + 2 * ch) : rd32(tb + 4 * ch);
         if (off + nb > payload) { rc = SZO_ECORRUPT; break; }
         br_t br = {pl + off, 0, nb * 8};
-        /* row r holds the points (r / (d1 d2), (r / d2) mod d1, r mod d2, 0..d3-1) */
+        /* chunk ch holds points l0 .. l1-1 of row r = ch / nseg, and row r the
+         * points (r / (d1 d2), (r / d2) mod d1, r mod d2, 0..d3-1) */
+        uint64_t r = ch / nseg, l0 = (ch % nseg) * Ce, l1 = l0 + Ce < Nr ? l0 + Ce : Nr;
         int64_t pt[4] = {(int64_t)(r / (d[1] * d[2])), (int64_t)((r / d[2]) % d[1]), (int64_t)(r % d[2]), 0};
-        for (uint64_t l = 0; l < Nr; l++) {
+        for (uint64_t l = l0; l < l1; l++) {
             pt[3] = (int64_t)l;
             /* bit-by-bit canonical decode */
             uint64_t c = 0;

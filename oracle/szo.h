@@ -63,6 +63,17 @@ int szo_compress(const float *x, int ndim, const uint64_t *shape, int mode,
                  double eb_abs, double eb_rel, int layers, int m, double theta,
                  int order, uint8_t *out, size_t out_cap, size_t *out_len,
                  float *recorded_out, uint16_t *codes_out);
+/* As szo_compress, with the Huffman payload cut into chunks of chunk_points
+ * points along each row (a power of two >= 32; 0, or a value >= the row
+ * length: one chunk per row).  Chunk s of row r holds the points
+ * [s C, min(N, (s + 1) C)) of that row; chunks follow row by row, each in its
+ * own byte-padded bit string with its byte length in the chunk table, and C
+ * is stored at header byte 116 (0 for whole rows).  SZO_EINVAL for any other
+ * chunk_points. */
+int szo_compress_chunked(const float *x, int ndim, const uint64_t *shape, int mode,
+                         double eb_abs, double eb_rel, int layers, int m, double theta,
+                         int order, uint32_t chunk_points, uint8_t *out, size_t out_cap, size_t *out_len,
+                         float *recorded_out, uint16_t *codes_out);
 /* The lattice variant (not the paper's method; a separately labelled fully
  * parallel form, header byte 113 = 1): values snapped to the 2 eb_f lattice,
  * integer n-layer prediction from lattice values, residuals coded like the

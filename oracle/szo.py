@@ -54,6 +54,9 @@ def lib():
         L.szo_compress.argtypes = [C.c_void_p, C.c_int, u64p, C.c_int, C.c_double, C.c_double,
                                    C.c_int, C.c_int, C.c_double, C.c_int, C.c_void_p, C.c_size_t,
                                    C.POINTER(C.c_size_t), C.c_void_p, C.c_void_p]
+        L.szo_compress_chunked.argtypes = [C.c_void_p, C.c_int, u64p, C.c_int, C.c_double, C.c_double,
+                                           C.c_int, C.c_int, C.c_double, C.c_int, C.c_uint32, C.c_void_p,
+                                           C.c_size_t, C.POINTER(C.c_size_t), C.c_void_p, C.c_void_p]
         L.szo_decompress.argtypes = [C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t]
         L.szo_lattice_point.argtypes = [C.c_float, C.c_float, C.POINTER(C.c_int)]
         L.szo_lattice_point.restype = C.c_int64
@@ -134,9 +137,11 @@ def choose_m(x, n, eb_f, theta=0.99):
 
 
 def compress(x, mode=REL, eb_abs=0.0, eb_rel=1e-4, n=1, m=0, theta=0.99, order=0,
-             want_aux=False, layers=None):
+             want_aux=False, layers=None, chunk_points=0):
     """Returns the stream bytes (and, with want_aux, the recorded values and
-    the quantization codes).  `layers` is an alias of n."""
+    the quantization codes).  `layers` is an alias of n.  `chunk_points`
+    cuts every row's Huffman payload into chunks of that many points (a
+    power of two >= 32; 0: one chunk per row)."""
     if layers is not None:
         n = layers
     x = np.ascontiguousarray(x, dtype=np.float32)
@@ -146,10 +151,10 @@ def compress(x, mode=REL, eb_abs=0.0, eb_rel=1e-4, n=1, m=0, theta=0.99, order=0
     olen = C.c_size_t()
     rec = np.empty_like(x) if want_aux else None
     codes = np.empty(x.shape, np.uint16) if want_aux else None
-    rc = L.szo_compress(x.ctypes.data, x.ndim, _shape(x), mode, eb_abs, eb_rel, n, m, theta,
-                        order, out.ctypes.data, cap, C.byref(olen),
-                        rec.ctypes.data if want_aux else None,
-                        codes.ctypes.data if want_aux else None)
+    rc = L.szo_compress_chunked(x.ctypes.data, x.ndim, _shape(x), mode, eb_abs, eb_rel, n, m, theta,
+                                order, int(chunk_points), out.ctypes.data, cap, C.byref(olen),
+                                rec.ctypes.data if want_aux else None,
+                                codes.ctypes.data if want_aux else None)
     if rc != 0:
         raise RuntimeError("szo_compress failed: %d" % rc)
     s = out[:olen.value].copy()
@@ -248,6 +253,7 @@ def header(s):
     f["theta"], = struct.unpack_from("<d", b, 104)
     f["adaptive"] = b[112]
     f["lattice"] = b[113]
+    f["chunk_points"], = struct.unpack_from("<I", b, 116)  # 0: one chunk per row
     # all four extents (a 4D field keeps its slowest one at byte 120) and the
     # field's own shape
     d0, = struct.unpack_from("<Q", b, 120)
