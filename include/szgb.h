@@ -23,10 +23,11 @@
  *
  * Stream format: a 128-byte little-endian header, a codebook of
  * (u16 symbol, u8 length) for the used quantization codes, one byte length
- * per row (fastest-axis line) as u16 or u32, then one byte-padded chunk per
- * row holding, for every point, its canonical Huffman code (MSB first) and,
- * after a code 0, the unpredictable value's sign, exponent and top t mantissa
- * bits.  The same bytes are produced by the CPU oracle of the test-suite.
+ * per chunk as u16 or u32, then the byte-padded chunks, each holding, for
+ * every point, its canonical Huffman code (MSB first) and, after a code 0, the
+ * unpredictable value's sign, exponent and top t mantissa bits.  A chunk is a
+ * whole row (fastest-axis line), or C consecutive points of one (header byte
+ * 116 holds C, 0 for whole rows); chunks follow row by row.  The same bytes are produced by the CPU oracle of the test-suite.
  * The format also carries 4D fields (the predictor of Sec. III in four
  * dimensions; the slowest extent at header byte 120): szgb_compress_4d
  * writes them and szgb_decompress reads them.
@@ -76,7 +77,17 @@ typedef struct {
     int variant;        /* SZGB_VARIANT_EXACT (0): the paper's method;
                            SZGB_VARIANT_LATTICE (1): the separately labelled
                            lattice variant (below) */
+    uint32_t chunk_points; /* Huffman chunk length along a row: a power of
+                           two >= 32 cuts every row's payload into chunks of
+                           that many points (decoded in parallel);
+                           SZGB_CHUNK_ROWS: one chunk per row; 0: the size the
+                           autotuner chose for the field's shape class, else
+                           one chunk per row.  A length at least the row's
+                           gives one chunk per row.  The lattice variant
+                           always codes whole rows. */
 } szgb_params;
+
+#define SZGB_CHUNK_ROWS 0xFFFFFFFFu
 
 /* The lattice variant is NOT the paper's method: values are first snapped to
  * the lattice of spacing 2 eb_f (p = rint(x * (1/(2 eb_f))) in binary32,
@@ -218,23 +229,25 @@ int szgb_decompress_batch(szgb_ctx *ctx, int count, const uint8_t *const *in_dev
 
 /* Autotuner.  Times compression + decompression of the device field
  * `data_dev` (params p) for every candidate wavefront shape (compute warps
- * per CTA: 2,4,6,8 in 3D, 1,2,4,8 in 1D/2D), best of `reps` runs each, and
- * keeps the fastest for the field's shape class (dimension, layers, bit
- * lengths of planes/rows/columns); later calls on fields of that class use
- * it.  The shape changes the schedule only: streams and reconstructions are
- * identical for every candidate.  *W_out and *ms_out (may be NULL) receive
- * the choice and its time; *pub_out is set to 0 (a former progress
- * publication interval: the wavefront no longer publishes progress).
- * SZGB_EUNSUPPORTED for 3D fields with n > 2, which do not run on the
- * wavefront. */
+ * per CTA: 2,4,6,8 in 3D, 1,2,4,8 in 1D/2D), then, with the fastest shape,
+ * for every candidate Huffman chunk length (whole rows, 128, 256, 512, 1024
+ * points, those shorter than a row), best of `reps` runs each, and keeps the
+ * fastest pair for the field's shape class (dimension, layers, bit lengths
+ * of planes/rows/columns); later calls on fields of that class with
+ * chunk_points = 0 use it.  The shape changes the schedule only; the chunk
+ * length changes the stream's chunking (and size) but not the decompressed
+ * values.  *W_out and *ms_out (may be NULL) receive the shape and its time;
+ * *pub_out receives the chosen chunk length (SZGB_CHUNK_ROWS for whole
+ * rows).  SZGB_EUNSUPPORTED for 3D fields with n > 2, which do not run on
+ * the wavefront. */
 int szgb_autotune(szgb_ctx *ctx, const float *data_dev, const szgb_params *p, int reps,
                   int *W_out, int *pub_out, double *ms_out);
 /* As szgb_autotune for a batch: times szgb_compress_batch +
  * szgb_decompress_batch of the given device fields for every candidate
- * shape (compute warps per CTA 1,2,4,6,8) and
- * keeps the fastest for every shape class in the batch: the shape that is
- * best for one field alone is often not the one that fills the GPU best
- * when many fields share it. */
+ * shape (compute warps per CTA 1,2,4,6,8), then for the chunk lengths whole
+ * rows, 128 and 512 points, and keeps the fastest pair for every shape class
+ * in the batch: the shape that is best for one field alone is often not the
+ * one that fills the GPU best when many fields share it. */
 int szgb_autotune_batch(szgb_ctx *ctx, int count, const float *const *data_dev,
                         const szgb_params *params, int reps, int *W_out, int *pub_out,
                         double *ms_out);
@@ -362,7 +375,8 @@ void szgb_server_destroy(szgb_server *srv);
 int szgb_suggest_m(const szgb_stats *st, double theta, double *hit_rate_out);
 
 /* Reads the header of a stream held in host memory: parameters (with the
- * m actually used) and the number of unpredictable points. */
+ * m actually used, and chunk_points = the stream's chunk length or
+ * SZGB_CHUNK_ROWS) and the number of unpredictable points. */
 int szgb_stream_info(const uint8_t *in_host, size_t in_len, szgb_params *out,
                      uint64_t *n_unpred);
 

@@ -472,41 +472,49 @@ int launch_codebook(const uint32_t* hist, DevState* st, uint8_t* len, uint64_t* 
 }
 
 // ---------------------------------------------------------------------------
-// per-row bit counts: Huffman code bits plus 9 + t record bits after code 0
+// per-chunk byte counts: Huffman code bits plus 9 + t record bits after code
+// 0, rounded up to whole bytes (a chunk is `chunk` points of a row, or the
+// whole row when chunk = 0)
 
 // lattice variant when OK != nullptr: an outlier record is 1 + 64 bits, +32
 // when its lattice value misses the bound.  One warp per row; a lane takes 8
-// consecutive codes as one 16-byte vector.
+// consecutive codes as one 16-byte vector, 256 codes a warp step (two steps
+// in flight).  A chunk of at least 256 points (chunk sizes are powers of two)
+// spans whole steps and its sum is carried from step to step; a shorter
+// chunk is chunk / 8 aligned lanes of one step, summed by a shuffle
+// reduction inside that lane group.
 __global__ void __launch_bounds__(256) k_rowbits(const uint16_t* __restrict__ codes, uint64_t pitch,
                                                  const float* __restrict__ x, uint64_t rows,
-                                                 uint64_t rowlen, const uint8_t* __restrict__ len,
+                                                 uint64_t rowlen, uint32_t chunk, const uint8_t* __restrict__ len,
                                                  uint32_t* rowbytes, DevState* st, const uint8_t* __restrict__ OK) {
     const int lane = threadIdx.x & 31;
     const uint64_t wglob = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     if (st->err) return;
     const int e_eb = st->e_eb;
+    const uint64_t nseg = chunks_per_row(chunk, rowlen);
+    const int G = (chunk == 0 || chunk >= 256) ? 32 : (int)(chunk / 8);  // lanes per chunk in a step
     unsigned long long kcount = 0;
     uint32_t maxb = 0;
     for (uint64_t r = wglob; r < rows; r += nw) {
         const uint64_t base = r * rowlen;
         const uint16_t* crow = codes + r * pitch;
-        uint64_t bits = 0;
-        // 512 codes a warp step: two vectors in flight per lane
-        for (uint64_t l0 = (uint64_t)lane * 8; l0 < rowlen; l0 += 512) {
+        uint64_t carry = 0;  // bits of the current chunk in earlier steps (G = 32)
+        for (uint64_t l0 = 0; l0 < rowlen; l0 += 512) {
             uint4 q[2];
 #pragma unroll
             for (int h = 0; h < 2; h++) {
-                const uint64_t l = l0 + 256 * h;
+                const uint64_t l = l0 + 256 * h + (uint64_t)lane * 8;
                 q[h] = l < rowlen ? __ldcs(reinterpret_cast<const uint4*>(crow + l)) : make_uint4(0u, 0u, 0u, 0u);
             }
 #pragma unroll
             for (int h = 0; h < 2; h++) {
-                const uint64_t l = l0 + 256 * h;
-                if (l >= rowlen) continue;
+                const uint64_t lb = l0 + 256 * h;  // first point of the step (warp-uniform)
+                if (lb >= rowlen) continue;
+                const uint64_t l = lb + (uint64_t)lane * 8;
                 const uint32_t w[4] = {q[h].x, q[h].y, q[h].z, q[h].w};
-                const uint64_t rem = rowlen - l;
-                const int nv = rem < 8 ? (int)rem : 8;
+                const int nv = l < rowlen ? (rowlen - l < 8 ? (int)(rowlen - l) : 8) : 0;
+                uint64_t bits = 0;
 #pragma unroll
                 for (int k = 0; k < 8; k++) {
                     if (k < nv) {
@@ -519,27 +527,40 @@ __global__ void __launch_bounds__(256) k_rowbits(const uint16_t* __restrict__ co
                         }
                     }
                 }
+                for (int o = G >> 1; o > 0; o >>= 1) bits += __shfl_xor_sync(0xffffffffu, bits, o);
+                if (G == 32) {
+                    carry += bits;
+                    const uint64_t send = lb + 256;
+                    if (send >= rowlen || (chunk && send % chunk == 0)) {  // the chunk ends with this step
+                        if (lane == 0) {
+                            const uint32_t b = (uint32_t)((carry + 7) / 8);
+                            rowbytes[r * nseg + (chunk ? lb / chunk : 0)] = b;
+                            maxb = b > maxb ? b : maxb;
+                        }
+                        carry = 0;
+                    }
+                } else if ((lane & (G - 1)) == 0 && l < rowlen) {
+                    const uint32_t b = (uint32_t)((bits + 7) / 8);
+                    rowbytes[r * nseg + l / chunk] = b;
+                    maxb = b > maxb ? b : maxb;
+                }
             }
         }
-        for (int o = 16; o > 0; o >>= 1) bits += __shfl_xor_sync(0xffffffffu, bits, o);
-        if (lane == 0) {
-            const uint32_t b = (uint32_t)((bits + 7) / 8);
-            rowbytes[r] = b;
-            maxb = b > maxb ? b : maxb;
-        }
     }
+    for (int o = 16; o > 0; o >>= 1) maxb = max(maxb, __shfl_xor_sync(0xffffffffu, maxb, o));
     if (lane == 0 && maxb) atomicMax(&st->maxrow, maxb);
     for (int o = 16; o > 0; o >>= 1) kcount += __shfl_xor_sync(0xffffffffu, kcount, o);
     if (lane == 0 && kcount) atomicAdd(&st->K, kcount);
 }
 
 int launch_rowbits(const uint16_t* codes, uint64_t pitch, const float* x, uint64_t rows, uint64_t rowlen,
-                   const uint8_t* len, uint32_t* rowbytes, DevState* st, cudaStream_t s, const uint8_t* OK) {
+                   uint32_t chunk, const uint8_t* len, uint32_t* rowbytes, DevState* st, cudaStream_t s,
+                   const uint8_t* OK) {
     uint64_t warps = rows;
     uint64_t blocks = (warps * 32 + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    k_rowbits<<<(int)blocks, 256, 0, s>>>(codes, pitch, x, rows, rowlen, len, rowbytes, st, OK);
+    k_rowbits<<<(int)blocks, 256, 0, s>>>(codes, pitch, x, rows, rowlen, chunk, len, rowbytes, st, OK);
     return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
 }
 
@@ -620,7 +641,7 @@ __device__ __forceinline__ void wr_u64(uint8_t* p, uint64_t v) {
 }
 
 // header, codebook section and chunk table
-__global__ void __launch_bounds__(256) k_write_meta(const CallParams cp, uint64_t rows,
+__global__ void __launch_bounds__(256) k_write_meta(const CallParams cp, uint64_t rows /* chunks */,
                                                     const uint8_t* __restrict__ len,
                                                     const uint32_t* __restrict__ usedlist,
                                                     const uint32_t* __restrict__ rowbytes,
@@ -662,6 +683,7 @@ __global__ void __launch_bounds__(256) k_write_meta(const CallParams cp, uint64_
         wr_u64(h + 104, (uint64_t)__double_as_longlong(cp.theta));
         h[112] = (uint8_t)(cp.m_user == 0);
         h[113] = (uint8_t)cp.variant;
+        wr_u32(h + 116, cp.chunk);  // chunk length along a row; 0: whole rows
     }
     for (uint64_t i = tid; i < cb; i += nthr) {
         uint64_t e = i / 3;
@@ -684,17 +706,22 @@ constexpr int kEncWarps = 8;
 constexpr int kEncPts = 8;                   // consecutive points per lane (one 16-byte code vector)
 constexpr int kEncChunk = 32 * kEncPts;      // points per warp step
 // a step's bits: 256 points of at most 64 code bits and a 97-bit record, plus
-// the carried partial word
-constexpr int kEncBufWords = (kEncChunk * (64 + 97) + 31) / 32 + 2;
+// the carried partial word and the byte padding of up to 8 chunks ending in it
+constexpr int kEncBufWords = (kEncChunk * (64 + 97) + 31) / 32 + 4;
 
 // payload: one warp per row, 256 points per step.  Each lane sums the bit
-// lengths of its 8 points, a warp scan gives its bit offset, and the lane
-// writes its bits MSB-first into a shared-memory word buffer (words it fills
-// alone are stored, the two it may share with its neighbours are OR-ed).
-// Completed words go to the payload; the buffer is zero outside the carried
-// word between steps.  Every payload byte belongs to exactly one row (rows
-// are byte-padded), so a word a row shares with a neighbour is written byte
-// by byte for the row's own bytes only: no atomics, no zeroing pass.
+// lengths of its 8 points; its bit position is its chunk's byte offset, plus
+// the bits of that chunk in earlier steps (chunks of at least 256 points),
+// plus a scan over the lanes of the chunk (a segmented warp scan when chunks
+// are shorter than a step); the lane writes its bits MSB-first into a
+// shared-memory word buffer (words it fills alone are stored, the two it may
+// share with its neighbours are OR-ed).  A row's chunks are consecutive in
+// the payload and each starts on a byte, so the padding between them is
+// zero bits the buffer already holds.  Completed words go to the payload; the
+// buffer is zero outside the carried word between steps.  Every payload byte
+// belongs to exactly one row, so a word a row shares with a neighbour is
+// written byte by byte for the row's own bytes only: no atomics, no zeroing
+// pass.
 __device__ __forceinline__ void store_word_bytes(uint8_t* plb, uint64_t gw, uint32_t val, uint32_t lo,
                                                  uint32_t hi) {
     // val: big-endian word value; write bytes covering bits [lo, hi) of it
@@ -747,7 +774,8 @@ struct LaneBits {
 
 __global__ void __launch_bounds__(kEncWarps * 32) k_encode(const uint16_t* __restrict__ codes, uint64_t pitch,
                                                           const float* __restrict__ x, uint64_t rows,
-                                                          uint64_t rowlen, const uint8_t* __restrict__ len,
+                                                          uint64_t rowlen, uint32_t chunk,
+                                                          const uint8_t* __restrict__ len,
                                                           const uint64_t* __restrict__ cw,
                                                           const uint64_t* __restrict__ rowoff,
                                                           uint8_t* out, DevState* st, const LatticeRec LR) {
@@ -759,14 +787,18 @@ __global__ void __launch_bounds__(kEncWarps * 32) k_encode(const uint16_t* __res
     const int e_eb = st->e_eb;
     const uint64_t wglob = blockIdx.x * (uint64_t)kEncWarps + wib;
     const uint64_t nw = (uint64_t)gridDim.x * kEncWarps;
+    const uint64_t nseg = chunks_per_row(chunk, rowlen);
+    const int G = (chunk == 0 || chunk >= kEncChunk) ? 32 : (int)(chunk / kEncPts);  // lanes per chunk in a step
     for (int i = lane; i < kEncBufWords; i += 32) buf[i] = 0;
     __syncwarp();
     for (uint64_t r = wglob; r < rows; r += nw) {
-        const uint64_t g0 = rowoff[r] * 8;        // first bit of the row in the payload
+        const uint64_t* const coff = rowoff + r * nseg;  // byte offsets of the row's chunks
+        const uint64_t g0 = coff[0] * 8;          // first bit of the row in the payload
         const uint64_t w0 = g0 >> 5;              // its word
         const uint32_t lo0 = (uint32_t)(g0 & 31); // bits of w0 owned by earlier rows
         uint64_t curw = w0;                        // global word held in buf[0]
         uint32_t bitpos = lo0;                     // bits already used in buf[0]
+        uint64_t carry = 0;                        // bits of the current chunk in earlier steps (G = 32)
         const uint64_t base = r * rowlen;
         const uint16_t* crow = codes + r * pitch;
         for (uint64_t l0 = 0; l0 < rowlen; l0 += kEncChunk) {
@@ -800,13 +832,20 @@ __global__ void __launch_bounds__(kEncWarps * 32) k_encode(const uint16_t* __res
                     }
                 }
             }
-            uint32_t incl = nbits;
-            for (int o = 1; o < 32; o <<= 1) {
+            uint32_t incl = nbits;  // inclusive scan over the lanes of this lane's chunk
+            for (int o = 1; o < G; o <<= 1) {
                 const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
+                if ((lane & (G - 1)) >= o) incl += y;
             }
-            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-            const uint32_t off = bitpos + incl - nbits;
+            if (G == 32 && chunk && l0 % chunk == 0) carry = 0;  // a chunk starts with this step
+            // this lane's chunk (lanes past the row end take the step's first)
+            const uint64_t lc = (l < rowlen ? l : l0);
+            const uint64_t cstart = coff[chunk ? lc / chunk : 0] * 8 + (G == 32 ? carry : 0);
+            const uint32_t off = (uint32_t)(cstart - curw * 32) + incl - nbits;
+            // the step ends where its last lane with points ends
+            const int last = (int)min((uint64_t)31, (rowlen - 1 - l0) / kEncPts);
+            const uint32_t stepend = __shfl_sync(0xffffffffu, off + nbits, last);
+            if (G == 32) carry += __shfl_sync(0xffffffffu, incl, 31);
             if (!any0 && nbits <= 64) {
                 // common case: the lane's codes fit one 64-bit register; they
                 // span at most three buffer words (OR-ed: neighbours may share them)
@@ -848,7 +887,7 @@ __global__ void __launch_bounds__(kEncWarps * 32) k_encode(const uint16_t* __res
                 wr.finish();
             }
             __syncwarp();
-            const uint32_t end = bitpos + total;
+            const uint32_t end = stepend;
             const uint32_t full = end >> 5;
             for (uint32_t i = lane; i < full; i += 32) {
                 const uint64_t gw = curw + i;
@@ -856,10 +895,10 @@ __global__ void __launch_bounds__(kEncWarps * 32) k_encode(const uint16_t* __res
                 buf[i] = 0;
             }
             __syncwarp();
-            const uint32_t carry = buf[full];
+            const uint32_t cword = buf[full];  // the partial word, carried to buf[0]
             __syncwarp();
             if (lane == 0 && full) {
-                buf[0] = carry;
+                buf[0] = cword;
                 buf[full] = 0;
             }
             __syncwarp();
@@ -873,7 +912,7 @@ __global__ void __launch_bounds__(kEncWarps * 32) k_encode(const uint16_t* __res
     }
 }
 
-int launch_write_meta(const CallParams& cp, uint64_t rows, const uint8_t* len, const uint32_t* usedlist,
+int launch_write_meta(const CallParams& cp, uint64_t rows /* chunks */, const uint8_t* len, const uint32_t* usedlist,
                       const uint32_t* rowbytes, const uint64_t* rowoff, uint8_t* out, DevState* st,
                       cudaStream_t s) {
     uint64_t blocks = (rows + 255) / 256;
@@ -883,7 +922,8 @@ int launch_write_meta(const CallParams& cp, uint64_t rows, const uint8_t* len, c
     return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
 }
 
-int launch_encode(const uint16_t* codes, uint64_t pitch, const float* x, uint64_t rows, uint64_t rowlen, const uint8_t* len,
+int launch_encode(const uint16_t* codes, uint64_t pitch, const float* x, uint64_t rows, uint64_t rowlen,
+                  uint32_t chunk, const uint8_t* len,
                   const uint64_t* cw, const uint64_t* rowoff, uint8_t* out, DevState* st, cudaStream_t s,
                   const int32_t* P, const uint8_t* OK, int ndim, int layers, uint64_t d1) {
     LatticeRec LR;
@@ -903,7 +943,8 @@ int launch_encode(const uint16_t* codes, uint64_t pitch, const float* x, uint64_
     uint64_t blocks = (rows + kEncWarps - 1) / kEncWarps;
     if (blocks > 152 * 5) blocks = 152 * 5;
     if (blocks < 1) blocks = 1;
-    k_encode<<<(int)blocks, kEncWarps * 32, smem, s>>>(codes, pitch, x, rows, rowlen, len, cw, rowoff, out, st, LR);
+    k_encode<<<(int)blocks, kEncWarps * 32, smem, s>>>(codes, pitch, x, rows, rowlen, chunk, len, cw, rowoff, out, st,
+                                                       LR);
     return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
 }
 

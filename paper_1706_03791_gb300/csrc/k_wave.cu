@@ -130,8 +130,9 @@ __device__ __forceinline__ bool halo_tagged(const uint64_t (&w)[4]) {
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
-// Huffman decode of every row (a row is one stream chunk), before the
-// reconstruction wavefront: one lane per row.  A step looks up the next
+// Huffman decode of every chunk (`chunk` points of a row, or the whole row),
+// before the reconstruction wavefront: one lane per chunk, the 32 lanes of a
+// warp on the same chunk of 32 consecutive rows.  A step looks up the next
 // kMultiBits bits in the multi-symbol table and takes up to three codes at
 // once (one code, by the single-symbol table or the canonical search, when
 // the first code is longer, or near the end of the ring or of the row).
@@ -152,6 +153,8 @@ struct DecodeArgs {
     uint64_t cpitch;
     float* out;
     uint64_t rows, N;
+    uint32_t chunk;  // chunk length along a row (a power of two >= 32), 0: whole rows
+    uint32_t nseg;   // chunks per row
     DevState* st;
 };
 
@@ -160,7 +163,8 @@ constexpr int kDecRing = 64;                  // ring columns per lane
 constexpr int kDecRingStride = kDecRing + 2;  // u16 per ring row: an odd word stride
 constexpr size_t kDecSmem = (size_t)(1u << kMultiBits) * 4 + 260 * 4 + (size_t)kDecWarps * 32 * kDecRingStride * 2;
 
-// rows [blk * 32 kDecWarps, ...) of one field; every thread of the block calls it
+// chunk (blk % nseg) of rows [(blk / nseg) * 32 kDecWarps, ...) of one
+// field; every thread of the block calls it
 __device__ __forceinline__ void decode_rows_block(const DecodeArgs& D, uint64_t blk, uint32_t* dsm) {
     uint32_t* s_multi = dsm;
     uint32_t* s_tab = s_multi + (1u << kMultiBits);
@@ -175,22 +179,27 @@ __device__ __forceinline__ void decode_rows_block(const DecodeArgs& D, uint64_t 
     __syncthreads();
     const uint16_t* g_sorted = reinterpret_cast<const uint16_t*>(D.dectab + 260);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint64_t row0 = (blk * kDecWarps + warp) * 32;
+    const uint64_t seg = blk % D.nseg;
+    const uint64_t row0 = ((blk / D.nseg) * kDecWarps + warp) * 32;
     const uint64_t row = row0 + lane;
     const bool valid = row < D.rows;
+    // this chunk's columns [cbeg, cend) (cbeg a multiple of 32)
+    const uint64_t cbeg = D.chunk ? seg * D.chunk : 0;
+    const uint64_t cend = D.chunk ? min(D.N, cbeg + D.chunk) : D.N;
     BitReader br;
     bool bad = false;
     uint64_t avail = 0;
     if (valid) {
-        br.init(D.payload, D.rowoff[row], (uint64_t)(D.stream_end - D.payload));
-        avail = (uint64_t)D.rowbytes[row] * 8;
+        const uint64_t ch = row * D.nseg + seg;
+        br.init(D.payload, D.rowoff[ch], (uint64_t)(D.stream_end - D.payload));
+        avail = (uint64_t)D.rowbytes[ch] * 8;
     }
     uint16_t* const ring = s_ring + (size_t)warp * 32 * kDecRingStride;
     uint16_t* const myring = ring + lane * kDecRingStride;
     float* const orow = D.out + row * D.N;
-    const uint64_t N = D.N;
-    uint64_t col = valid ? 0 : N;  // next column of this lane's row
-    for (uint64_t tb = 0; tb < N; tb += 32) {
+    const uint64_t N = cend;  // the chunk ends the lane's work
+    uint64_t col = valid ? cbeg : N;  // next column of this lane's chunk
+    for (uint64_t tb = cbeg; tb < N; tb += 32) {
         const uint64_t tend = min(N, tb + 32), lim = min(N, tb + kDecRing);
         while (__any_sync(0xffffffffu, col < tend)) {
             if (col < lim) {
@@ -281,11 +290,13 @@ __global__ void __launch_bounds__(kDecWarps * 32, 4)
 
 size_t decode_args_bytes() { return sizeof(DecodeArgs); }
 
-uint32_t decode_rows_blocks(uint64_t rows) { return (uint32_t)((rows + 32ull * kDecWarps - 1) / (32ull * kDecWarps)); }
+uint32_t decode_rows_blocks(uint64_t rows, uint32_t chunk, uint64_t N) {
+    return (uint32_t)((rows + 32ull * kDecWarps - 1) / (32ull * kDecWarps) * chunks_per_row(chunk, N));
+}
 
 void decode_args_fill(void* dst, const uint8_t* payload, const uint64_t* rowoff, const uint32_t* rowbytes,
                       const uint8_t* stream_end, const uint32_t* lut, const uint32_t* dec_tab, uint16_t* codes,
-                      uint64_t cpitch, float* out, uint64_t rows, uint64_t N, DevState* st) {
+                      uint64_t cpitch, float* out, uint64_t rows, uint64_t N, uint32_t chunk, DevState* st) {
     DecodeArgs d;
     d.payload = payload;
     d.rowoff = rowoff;
@@ -298,6 +309,8 @@ void decode_args_fill(void* dst, const uint8_t* payload, const uint64_t* rowoff,
     d.out = out;
     d.rows = rows;
     d.N = N;
+    d.chunk = chunk;
+    d.nseg = (uint32_t)chunks_per_row(chunk, N);
     d.st = st;
     memcpy(dst, &d, sizeof(d));
 }
@@ -320,7 +333,8 @@ int launch_decode_rows_batch(const void* args_dev, const uint32_t* blk_dev, int 
 
 int launch_decode_rows(const uint8_t* payload, const uint64_t* rowoff, const uint32_t* rowbytes,
                        const uint8_t* stream_end, const uint32_t* lut, const uint32_t* dec_tab, uint16_t* codes,
-                       uint64_t cpitch, float* out, uint64_t rows, uint64_t N, DevState* st, cudaStream_t s) {
+                       uint64_t cpitch, float* out, uint64_t rows, uint64_t N, uint32_t chunk, DevState* st,
+                       cudaStream_t s) {
     DecodeArgs d;
     d.payload = payload;
     d.rowoff = rowoff;
@@ -333,9 +347,11 @@ int launch_decode_rows(const uint8_t* payload, const uint64_t* rowoff, const uin
     d.out = out;
     d.rows = rows;
     d.N = N;
+    d.chunk = chunk;
+    d.nseg = (uint32_t)chunks_per_row(chunk, N);
     d.st = st;
     const uint64_t per = 32ull * kDecWarps;
-    const uint64_t blocks = (rows + per - 1) / per;
+    const uint64_t blocks = (rows + per - 1) / per * d.nseg;
     if (blocks == 0 || blocks > 0x7fffffffull) return SZGB_EINVAL;
     static std::once_flag once;
     static bool ok = true;

@@ -84,11 +84,13 @@ struct szgb_ctx {
     BatchGraph g_comp, g_dec;
     // autotuned wavefront shapes per shape class (see shape_class)
     struct Tune {
-        int W, pub;  // pub: kept in the table format, always 0
+        int W;
+        uint32_t chunk;  // requested chunk length (SZGB_CHUNK_ROWS: whole rows)
         double ms;
     };
     std::map<uint64_t, Tune> tune;
-    int force_W = 0;  // set while the autotuner times a candidate
+    int force_W = 0;            // set while the autotuner times a candidate
+    uint32_t force_chunk = 0;   // likewise (a requested chunk length; 0: none)
     int debug_skip = 0;  // test hook: 1 + the wavefront work item never run; 0 = none
 };
 
@@ -130,6 +132,14 @@ int ensure_scratch(szgb_ctx* c, size_t need) {
     return SZGB_OK;
 }
 
+// The chunk length a request gives a row of row_len points: 0 (whole rows)
+// unless it is a power of two shorter than the row; the lattice variant codes
+// whole rows.
+uint32_t effective_chunk(uint32_t req, uint64_t row_len, int variant) {
+    if (variant != SZGB_VARIANT_EXACT || req == 0 || req == SZGB_CHUNK_ROWS || req >= row_len) return 0;
+    return req;
+}
+
 int check_params(const szgb_params* p, CallParams* cp) {
     if (!p || p->ndim < 1 || p->ndim > 3) return SZGB_EINVAL;
     uint64_t d[3] = {1, 1, 1};
@@ -157,6 +167,9 @@ int check_params(const szgb_params* p, CallParams* cp) {
     cp->theta = p->theta;
     if (p->variant != SZGB_VARIANT_EXACT && p->variant != SZGB_VARIANT_LATTICE) return SZGB_EINVAL;
     cp->variant = p->variant;
+    const uint32_t c = p->chunk_points;
+    if (!(c == 0 || c == SZGB_CHUNK_ROWS || (c >= 32 && (c & (c - 1)) == 0))) return SZGB_EINVAL;
+    cp->chunk = effective_chunk(c, cp->d2, cp->variant);
     // the lattice variant is built for n <= 2; batched, autotuned and
     // no-allocation calls check the wavefront's set (layers_supported) too
     if (!layers_single(p->ndim, p->layers) || (p->variant == SZGB_VARIANT_LATTICE && p->layers > 2))
@@ -172,6 +185,18 @@ uint64_t shape_class(const CallParams& cp, int layers) {
     const uint64_t rows = cp.ndim == 3 ? cp.d1 : cp.d0 * cp.d1;
     const uint64_t planes = cp.ndim == 3 ? cp.d0 : 1;
     return ((uint64_t)cp.ndim << 56) | ((uint64_t)layers << 48) | (bl(planes) << 32) | (bl(rows) << 16) | bl(cp.d2);
+}
+
+// chunk_points = 0 takes the autotuned chunk length of the field's shape
+// class (whole rows when there is none); a candidate being timed wins
+void resolve_chunk(const szgb_ctx* c, const szgb_params* p, CallParams* cp) {
+    uint32_t req = p->chunk_points;
+    if (req == 0) {
+        auto it = c->tune.find(shape_class(*cp, cp->layers));
+        if (it != c->tune.end()) req = it->second.chunk;
+    }
+    if (c->force_chunk) req = c->force_chunk;
+    cp->chunk = effective_chunk(req, cp->d2, cp->variant);
 }
 
 WaveGeom make_geom(const szgb_ctx* c, const CallParams& cp, int layers) {
@@ -297,6 +322,7 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
     CallParams cp;
     int rc = check_params(p, &cp);
     if (rc) return rc;
+    resolve_chunk(c, p, &cp);
     // 3D fields with n = 3, 4, and 4D fields: the hyperplane kernels instead of the wavefront
     if (D4 && (cp.ndim != 3 || cp.variant != SZGB_VARIANT_EXACT || cp.d0 % D4 != 0)) return SZGB_EINVAL;
     const bool hyper = D4 || (cp.variant == SZGB_VARIANT_EXACT && !layers_supported(cp.ndim, cp.layers));
@@ -311,6 +337,7 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
     const uint64_t N = cp.d0 * cp.d1 * cp.d2;
     const uint64_t rows = cp.d0 * cp.d1;
     const uint64_t rowlen = cp.d2;
+    const uint64_t nch = rows * chunks_per_row(cp.chunk, rowlen);  // Huffman chunks
     const uint64_t cpitch = (rowlen + 7) & ~(uint64_t)7;  // codes row pitch: 16-byte rows
     const int layers = cp.layers;
     WaveGeom g = make_geom(c, cp, layers);
@@ -340,9 +367,9 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
     A.add(&cw, 65536);
     A.add(&sortbuf, kSortBufU64);
     A.add(&nodebuf, kNodeBufU32);
-    A.add(&rowbytes, rows);
-    A.add(&rowoff, rows);
-    A.add(&blocksums, (rows + 2047) / 2048 + 1);
+    A.add(&rowbytes, nch);
+    A.add(&rowoff, nch);
+    A.add(&blocksums, (nch + 2047) / 2048 + 1);
     char* wargs;
     uint32_t* worder;
     unsigned* wticket;
@@ -426,17 +453,17 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
     }
     {
         PhaseTimer t(c, PH_ROWBITS);
-        if ((rc = launch_rowbits(codes, cpitch, x, rows, rowlen, len, rowbytes, st, s, latOK))) return rc;
+        if ((rc = launch_rowbits(codes, cpitch, x, rows, rowlen, cp.chunk, len, rowbytes, st, s, latOK))) return rc;
     }
     {
         PhaseTimer t(c, PH_SCAN);
-        if ((rc = launch_scan_rows(rowbytes, rows, rowoff, blocksums, st, 1, s))) return rc;
+        if ((rc = launch_scan_rows(rowbytes, nch, rowoff, blocksums, st, 1, s))) return rc;
     }
     {
         PhaseTimer t(c, PH_WRITE);
-        if ((rc = launch_write_meta(cp, rows, len, nodebuf, rowbytes, rowoff, dst, st, s))) return rc;
-        if ((rc = launch_encode(codes, cpitch, x, rows, rowlen, len, cw, rowoff, dst, st, s, latP, latOK, cp.ndim,
-                                layers, cp.d1)))
+        if ((rc = launch_write_meta(cp, nch, len, nodebuf, rowbytes, rowoff, dst, st, s))) return rc;
+        if ((rc = launch_encode(codes, cpitch, x, rows, rowlen, cp.chunk, len, cw, rowoff, dst, st, s, latP, latOK,
+                                cp.ndim, layers, cp.d1)))
             return rc;
         if (D4 && (rc = launch_patch_header4(dst, D4, cp.d0 / D4, st, s))) return rc;
     }
@@ -512,6 +539,7 @@ int szgb::parse_header(const uint8_t* h, size_t in_len, Header* o) {
     u = rd_le(h + 104, 8); memcpy(&o->theta, &u, 8);
     o->adaptive = h[112];
     o->variant = h[113];
+    o->chunk = (uint32_t)rd_le(h + 116, 4);
     if (o->variant > 1) return SZGB_ECORRUPT;
     // a 4D field (the predictor of Sec. III in four dimensions; slowest extent
     // at byte 120) is a valid stream this library does not decode
@@ -525,7 +553,11 @@ int szgb::parse_header(const uint8_t* h, size_t in_len, Header* o) {
     if (n >= ((unsigned __int128)1 << 32)) return SZGB_ECORRUPT;
     if (o->ndim < 3 && o->d0 != 1) return SZGB_ECORRUPT;
     if (o->ndim < 2 && o->d1 != 1) return SZGB_ECORRUPT;
-    if (o->nchunks != o->d0 * o->d1) return SZGB_ECORRUPT;
+    // chunks: whole rows (0), or a power of two >= 32 shorter than a row
+    // (the lattice variant codes whole rows)
+    if (o->chunk && (o->chunk < 32 || (o->chunk & (o->chunk - 1)) || o->chunk >= o->d2 || o->variant))
+        return SZGB_ECORRUPT;
+    if (o->nchunks != o->d0 * o->d1 * chunks_per_row(o->chunk, o->d2)) return SZGB_ECORRUPT;
     if (o->nsym < 1 || o->nsym > (1u << o->m) || o->maxlen < 1 || o->maxlen > 64) return SZGB_ECORRUPT;
     uint64_t cb = (3ull * o->nsym + 3) & ~3ull;
     uint64_t tb = ((uint64_t)o->tw * o->nchunks + 3) & ~3ull;
@@ -578,7 +610,7 @@ int decompress_impl(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_dev
     if (one_field_batched(c) && !hyper && H.variant == SZGB_VARIANT_EXACT && in_on_device && out_on_device &&
         ((uintptr_t)in % 4) == 0 && ((uintptr_t)out % 16) == 0)
         return decompress_batch_impl(c, 1, &in, &in_len, &out, &out_cap_elems, nullptr, hbuf);
-    const uint64_t rows = H.nchunks;
+    const uint64_t rows = H.d0 * H.d1, nch = H.nchunks;
     CallParams cp = {};
     cp.ndim = H.ndim;
     cp.d0 = H.d0;
@@ -613,9 +645,9 @@ int decompress_impl(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_dev
     }
     A.add(&halo_row, lattice ? 1 : hrow + hplane);
     A.add(&prog, g.num_ctas);
-    A.add(&rowbytes, rows);
-    A.add(&rowoff, rows);
-    A.add(&blocksums, (rows + 2047) / 2048 + 1);
+    A.add(&rowbytes, nch);
+    A.add(&rowoff, nch);
+    A.add(&blocksums, (nch + 2047) / 2048 + 1);
     A.add(&lut, (size_t)1 << kLutBits);
     A.add(&dectab, kDecTabU32);
     A.add(&lenbuf, 65536);
@@ -655,7 +687,7 @@ int decompress_impl(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_dev
     cudaMemsetAsync(prog, 0, sizeof(unsigned) * g.num_ctas, s);
     if (!lattice) cudaMemsetAsync(halo_row, 0, (hrow + hplane) * 4, s);
     const uint64_t cb = (3ull * H.nsym + 3) & ~3ull;
-    const uint64_t tb = ((uint64_t)H.tw * rows + 3) & ~3ull;
+    const uint64_t tb = ((uint64_t)H.tw * nch + 3) & ~3ull;
     const uint8_t* codebook = sb + kHeaderBytes;
     const uint8_t* table = codebook + cb;
     const uint8_t* payload = table + tb;
@@ -665,8 +697,8 @@ int decompress_impl(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_dev
     }
     {
         PhaseTimer t(c, PH_DEC_SCAN);
-        if ((rc = launch_read_rowbytes(table, H.tw, rows, rowbytes, s))) return rc;
-        if ((rc = launch_scan_rows(rowbytes, rows, rowoff, blocksums, st, 0, s))) return rc;
+        if ((rc = launch_read_rowbytes(table, H.tw, nch, rowbytes, s))) return rc;
+        if ((rc = launch_scan_rows(rowbytes, nch, rowoff, blocksums, st, 0, s))) return rc;
     }
     if (lattice) {
         PhaseTimer t(c, PH_WAVE_D);
@@ -677,7 +709,7 @@ int decompress_impl(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_dev
         {
             PhaseTimer t(c, PH_DEC_ROWS);
             if ((rc = launch_decode_rows(payload, rowoff, rowbytes, payload + H.payload, lut, dectab, codes, cpitch,
-                                         dst, rows, H.d2, st, s)))
+                                         dst, rows, H.d2, H.chunk, st, s)))
                 return rc;
         }
         PhaseTimer t(c, PH_WAVE_D);
@@ -718,7 +750,7 @@ uint64_t header_hash(const Header& h) {
     uint64_t v = 1469598103934665603ull;
     auto mix = [&](uint64_t x) { v = (v ^ x) * 1099511628211ull; };
     mix(h.ndim); mix(h.layers); mix(h.m); mix(h.tw); mix(h.d0); mix(h.d1); mix(h.d2); mix(h.nsym);
-    mix(h.payload); mix(h.total);
+    mix(h.payload); mix(h.total); mix(h.chunk);
     uint32_t e;
     memcpy(&e, &h.eb_f, 4);
     mix(e);
@@ -808,7 +840,7 @@ int run_batch(szgb_ctx* c, BatchGraph& G, const std::vector<uint64_t>& key, F en
 struct CompPlan {
     CallParams cp;
     WaveGeom g;
-    uint64_t n, rows, rowlen, cpitch;
+    uint64_t n, rows, rowlen, cpitch, nch;
     size_t hrow, hplane;
     int range_blocks;
     // device scratch
@@ -884,11 +916,13 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
         CompPlan& q = P[f];
         if (!data[f] || !out[f] || ((uintptr_t)data[f] % 16) || ((uintptr_t)out[f] % 4)) return SZGB_EINVAL;
         if ((rc = check_params(&params[f], &q.cp))) return rc;
+        resolve_chunk(c, &params[f], &q.cp);
         if (q.cp.variant != SZGB_VARIANT_EXACT) return SZGB_EUNSUPPORTED;  // batches run the paper's method
         if (!layers_supported(q.cp.ndim, q.cp.layers)) return SZGB_EUNSUPPORTED;  // ... on the wavefront
         q.n = q.cp.d0 * q.cp.d1 * q.cp.d2;
         q.rows = q.cp.d0 * q.cp.d1;
         q.rowlen = q.cp.d2;
+        q.nch = q.rows * chunks_per_row(q.cp.chunk, q.rowlen);
         q.cpitch = (q.rowlen + 7) & ~(uint64_t)7;
         q.g = make_geom(c, q.cp, q.cp.layers);
         halo_sizes(q.g, q.cp.layers, &q.hrow, &q.hplane);
@@ -929,9 +963,9 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
         A.add(&q.cw, 65536);
         A.add(&q.sortbuf, kSortBufU64);
         A.add(&q.nodebuf, kNodeBufU32);
-        A.add(&q.rowbytes, q.rows);
-        A.add(&q.rowoff, q.rows);
-        A.add(&q.blocksums, (q.rows + 2047) / 2048 + 1);
+        A.add(&q.rowbytes, q.nch);
+        A.add(&q.rowoff, q.nch);
+        A.add(&q.blocksums, (q.nch + 2047) / 2048 + 1);
     }
     if ((rc = ensure_scratch(c, A.total))) return rc;
     A.bind(c->scratch);
@@ -985,6 +1019,7 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
         key.push_back((uint64_t)out_cap[f]);
         const uint64_t* pw = reinterpret_cast<const uint64_t*>(&params[f]);
         for (size_t i = 0; i < sizeof(szgb_params) / 8; i++) key.push_back(pw[i]);
+        key.push_back((uint64_t)P[f].g.W | ((uint64_t)P[f].cp.chunk << 8));  // the resolved shape and chunking
     }
     cudaStream_t s = c->stream;
     auto enqueue = [&]() -> int {
@@ -1025,10 +1060,13 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
         for (int f = 0; f < count; f++) {
             CompPlan& q = P[f];
             cudaStream_t a = c->aux[f % kAux];
-            if ((r = launch_rowbits(q.codes, q.cpitch, data[f], q.rows, q.rowlen, q.len, q.rowbytes, st + f, a))) return r;
-            if ((r = launch_scan_rows(q.rowbytes, q.rows, q.rowoff, q.blocksums, st + f, 1, a))) return r;
-            if ((r = launch_write_meta(q.cp, q.rows, q.len, q.nodebuf, q.rowbytes, q.rowoff, out[f], st + f, a))) return r;
-            if ((r = launch_encode(q.codes, q.cpitch, data[f], q.rows, q.rowlen, q.len, q.cw, q.rowoff, out[f], st + f, a)))
+            if ((r = launch_rowbits(q.codes, q.cpitch, data[f], q.rows, q.rowlen, q.cp.chunk, q.len, q.rowbytes, st + f,
+                                    a)))
+                return r;
+            if ((r = launch_scan_rows(q.rowbytes, q.nch, q.rowoff, q.blocksums, st + f, 1, a))) return r;
+            if ((r = launch_write_meta(q.cp, q.nch, q.len, q.nodebuf, q.rowbytes, q.rowoff, out[f], st + f, a))) return r;
+            if ((r = launch_encode(q.codes, q.cpitch, data[f], q.rows, q.rowlen, q.cp.chunk, q.len, q.cw, q.rowoff, out[f],
+                                   st + f, a)))
                 return r;
         }
         join_aux(c);
@@ -1065,7 +1103,7 @@ struct DecPlan {
     Header H;
     CallParams cp;
     WaveGeom g;
-    uint64_t n, rows, cpitch;
+    uint64_t n, rows, cpitch, nch;
     uint16_t* codes;
     size_t hrow, hplane;
     const uint8_t *codebook, *table, *payload;
@@ -1107,7 +1145,8 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
         if (!layers_supported(q.H.ndim, q.H.layers) || q.H.variant != SZGB_VARIANT_EXACT) return SZGB_EUNSUPPORTED;
         q.n = q.H.d0 * q.H.d1 * q.H.d2;
         if (out_cap[f] < q.n) return SZGB_EINVAL;
-        q.rows = q.H.nchunks;
+        q.rows = q.H.d0 * q.H.d1;
+        q.nch = q.H.nchunks;
         q.cpitch = (q.H.d2 + 7) & ~(uint64_t)7;
         q.cp = CallParams{};
         q.cp.ndim = q.H.ndim;
@@ -1117,7 +1156,7 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
         q.cp.layers = q.H.layers;
         q.g = make_geom(c, q.cp, q.H.layers);
         halo_sizes(q.g, q.H.layers, &q.hrow, &q.hplane);
-        const uint64_t cb = (3ull * q.H.nsym + 3) & ~3ull, tb = ((uint64_t)q.H.tw * q.rows + 3) & ~3ull;
+        const uint64_t cb = (3ull * q.H.nsym + 3) & ~3ull, tb = ((uint64_t)q.H.tw * q.nch + 3) & ~3ull;
         q.codebook = in[f] + kHeaderBytes;
         q.table = q.codebook + cb;
         q.payload = q.table + tb;
@@ -1152,9 +1191,9 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
     for (int f = 0; f < count; f++) {
         DecPlan& q = P[f];
         A.add(&q.codes, q.rows * q.cpitch + 8);
-        A.add(&q.rowbytes, q.rows);
-        A.add(&q.rowoff, q.rows);
-        A.add(&q.blocksums, (q.rows + 2047) / 2048 + 1);
+        A.add(&q.rowbytes, q.nch);
+        A.add(&q.rowoff, q.nch);
+        A.add(&q.blocksums, (q.nch + 2047) / 2048 + 1);
         A.add(&q.lut, (size_t)1 << kLutBits);
         A.add(&q.dectab, kDecTabU32);
         A.add(&q.lenbuf, 65536);
@@ -1198,14 +1237,14 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
                                        q.halo_plane, q.prog, st + f, c->timeout_ns)))
             return rc;
         decode_args_fill(Hb + o_dec + (size_t)f * dsz, q.payload, q.rowoff, q.rowbytes, q.payload + q.H.payload, q.lut,
-                         q.dectab, q.codes, q.cpitch, out[f], q.rows, q.H.d2, st + f);
+                         q.dectab, q.codes, q.cpitch, out[f], q.rows, q.H.d2, q.H.chunk, st + f);
         tables_args_fill(Hb + o_tab + (size_t)f * tsz, q.codebook, q.H.nsym, q.H.m, q.lut, q.dectab, q.lenbuf, q.symbuf,
                          st + f);
     }
     // the row decode of every field in one launch
     uint32_t* h_blk = reinterpret_cast<uint32_t*>(Hb + o_blk);
     h_blk[0] = 0;
-    for (int f = 0; f < count; f++) h_blk[f + 1] = h_blk[f] + decode_rows_blocks(P[f].rows);
+    for (int f = 0; f < count; f++) h_blk[f + 1] = h_blk[f] + decode_rows_blocks(P[f].rows, P[f].H.chunk, P[f].H.d2);
     const uint32_t dec_blocks = h_blk[count];
     uint32_t* h_order = reinterpret_cast<uint32_t*>(Hb + o_ord);
     size_t ord_at[kMaxLayers], ord_n[kMaxLayers];
@@ -1246,8 +1285,8 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
         for (int f = 0; f < count; f++) {
             DecPlan& q = P[f];
             cudaStream_t a = c->aux[f % kAux];
-            if ((r = launch_read_rowbytes(q.table, q.H.tw, q.rows, q.rowbytes, a))) return r;
-            if ((r = launch_scan_rows(q.rowbytes, q.rows, q.rowoff, q.blocksums, st + f, 0, a))) return r;
+            if ((r = launch_read_rowbytes(q.table, q.H.tw, q.nch, q.rowbytes, a))) return r;
+            if ((r = launch_scan_rows(q.rowbytes, q.nch, q.rowoff, q.blocksums, st + f, 0, a))) return r;
         }
         join_aux(c);
         if ((r = launch_decode_rows_batch(dargs, dblk, count, dec_blocks, s))) return r;
@@ -1370,42 +1409,58 @@ int szgb_autotune(szgb_ctx* c, const float* data_dev, const szgb_params* p, int 
     const int* Ws = cp.ndim == 3 ? Ws3 : Ws2;
     double best = 1e30;
     int bW = c->W3;
+    uint32_t bC = SZGB_CHUNK_ROWS;
     const bool prof = c->profiling;
     c->profiling = false;
+    // best of reps timed runs of one (shape, chunk) candidate (the first run warms up)
+    auto time_candidate = [&](int W, uint32_t C) -> double {
+        c->force_W = W;
+        c->force_chunk = C;
+        double tmin = 1e30;
+        for (int r = 0; r <= reps && !rc; r++) {
+            size_t olen = 0;
+            cudaEventRecord(e0, c->stream);
+            rc = compress_impl(c, data_dev, 1, p, sbuf, bound, 1, &olen, nullptr, nullptr, nullptr);
+            if (!rc) rc = decompress_impl(c, sbuf, olen, 1, ybuf, N, 1);
+            cudaEventRecord(e1, c->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (r > 0) tmin = std::min(tmin, (double)ms);
+        }
+        return tmin;
+    };
+    // the wavefront shape with whole-row chunks, then the chunk length with that shape
     for (int wi = 0; wi < 4 && !rc; wi++) {
         if (cp.ndim == 3 && Ws[wi] < 2 * cp.layers) continue;
-        {
-            c->force_W = Ws[wi];
-            double tmin = 1e30;
-            for (int r = 0; r <= reps && !rc; r++) {  // the first run warms up
-                size_t olen = 0;
-                cudaEventRecord(e0, c->stream);
-                rc = compress_impl(c, data_dev, 1, p, sbuf, bound, 1, &olen, nullptr, nullptr, nullptr);
-                if (!rc) rc = decompress_impl(c, sbuf, olen, 1, ybuf, N, 1);
-                cudaEventRecord(e1, c->stream);
-                cudaEventSynchronize(e1);
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (r > 0) tmin = std::min(tmin, (double)ms);
-            }
-            if (!rc && tmin < best) {
-                best = tmin;
-                bW = Ws[wi];
-            }
+        const double t = time_candidate(Ws[wi], SZGB_CHUNK_ROWS);
+        if (!rc && t < best) {
+            best = t;
+            bW = Ws[wi];
+        }
+    }
+    const uint32_t Cs[] = {128, 256, 512, 1024};
+    for (int ci = 0; ci < 4 && !rc; ci++) {
+        if (Cs[ci] >= cp.d2) continue;
+        const double t = time_candidate(bW, Cs[ci]);
+        if (!rc && t < best) {
+            best = t;
+            bC = Cs[ci];
         }
     }
     c->force_W = 0;
+    c->force_chunk = 0;
     c->profiling = prof;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(sbuf);
     cudaFree(ybuf);
     if (rc) return rc;
-    c->tune[shape_class(cp, cp.layers)] = szgb_ctx::Tune{bW, 0, best};
+    c->tune[shape_class(cp, cp.layers)] = szgb_ctx::Tune{bW, bC, best};
     drop_graph(c->g_comp);  // captured batches used the previous shapes
     drop_graph(c->g_dec);
     if (W_out) *W_out = bW;
-    if (pub_out) *pub_out = 0;
+    if (pub_out) *pub_out = (int)bC;
     if (ms_out) *ms_out = best;
     return SZGB_OK;
 }
@@ -1443,29 +1498,44 @@ int szgb_autotune_batch(szgb_ctx* c, int count, const float* const* data_dev, co
     const int Ws[] = {1, 2, 4, 6, 8};
     double best = 1e30;
     int bW = c->W3;
+    uint32_t bC = SZGB_CHUNK_ROWS;
+    uint64_t minrow = ~0ull;
+    for (int f = 0; f < count && !rc; f++) minrow = std::min(minrow, cps[f].d2);
+    auto time_candidate = [&](int W, uint32_t C) -> double {
+        c->force_W = W;
+        c->force_chunk = C;
+        double tmin = 1e30;
+        for (int r = 0; r <= reps && !rc; r++) {
+            cudaEventRecord(e0, c->stream);
+            rc = compress_batch_impl(c, count, data_dev, params, sb.data(), cap.data(), len.data(), nullptr);
+            if (!rc) rc = decompress_batch_impl(c, count, sb.data(), len.data(), yb.data(), ycap.data(), nullptr);
+            cudaEventRecord(e1, c->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (r > 0) tmin = std::min(tmin, (double)ms);
+        }
+        return tmin;
+    };
     for (int wi = 0; wi < 5 && !rc; wi++) {
         if (any3 && Ws[wi] < 2 * maxl) continue;
-        {
-            c->force_W = Ws[wi];
-            double tmin = 1e30;
-            for (int r = 0; r <= reps && !rc; r++) {
-                cudaEventRecord(e0, c->stream);
-                rc = compress_batch_impl(c, count, data_dev, params, sb.data(), cap.data(), len.data(), nullptr);
-                if (!rc)
-                    rc = decompress_batch_impl(c, count, sb.data(), len.data(), yb.data(), ycap.data(), nullptr);
-                cudaEventRecord(e1, c->stream);
-                cudaEventSynchronize(e1);
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (r > 0) tmin = std::min(tmin, (double)ms);
-            }
-            if (!rc && tmin < best) {
-                best = tmin;
-                bW = Ws[wi];
-            }
+        const double t = time_candidate(Ws[wi], SZGB_CHUNK_ROWS);
+        if (!rc && t < best) {
+            best = t;
+            bW = Ws[wi];
+        }
+    }
+    const uint32_t Cs[] = {128, 512};
+    for (int ci = 0; ci < 2 && !rc; ci++) {
+        if (Cs[ci] >= minrow) continue;  // some field would keep whole rows: no clear measurement
+        const double t = time_candidate(bW, Cs[ci]);
+        if (!rc && t < best) {
+            best = t;
+            bC = Cs[ci];
         }
     }
     c->force_W = 0;
+    c->force_chunk = 0;
     c->use_graphs = graphs;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1474,11 +1544,11 @@ int szgb_autotune_batch(szgb_ctx* c, int count, const float* const* data_dev, co
         cudaFree(yb[f]);
     }
     if (rc) return rc;
-    for (int f = 0; f < count; f++) c->tune[shape_class(cps[f], cps[f].layers)] = szgb_ctx::Tune{bW, 0, best};
+    for (int f = 0; f < count; f++) c->tune[shape_class(cps[f], cps[f].layers)] = szgb_ctx::Tune{bW, bC, best};
     drop_graph(c->g_comp);
     drop_graph(c->g_dec);
     if (W_out) *W_out = bW;
-    if (pub_out) *pub_out = 0;
+    if (pub_out) *pub_out = (int)bC;
     if (ms_out) *ms_out = best;
     return SZGB_OK;
 }
@@ -1487,9 +1557,9 @@ int szgb_tune_save(szgb_ctx* c, const char* path) {
     if (!c || !path) return SZGB_EINVAL;
     FILE* f = fopen(path, "w");
     if (!f) return SZGB_EINVAL;
-    fprintf(f, "# szgb autotune v1: shape_class W pub ms\n");
+    fprintf(f, "# szgb autotune v2: shape_class W chunk ms (chunk 4294967295: whole rows)\n");
     for (auto& kv : c->tune)
-        fprintf(f, "%016llx %d %d %.6f\n", (unsigned long long)kv.first, kv.second.W, kv.second.pub, kv.second.ms);
+        fprintf(f, "%016llx %d %u %.6f\n", (unsigned long long)kv.first, kv.second.W, kv.second.chunk, kv.second.ms);
     fclose(f);
     return SZGB_OK;
 }
@@ -1503,14 +1573,15 @@ int szgb_tune_load(szgb_ctx* c, const char* path) {
     while (fgets(line, sizeof line, f)) {
         if (line[0] == '#' || line[0] == '\n') continue;
         unsigned long long k;
-        int W, pub;
+        int W;
+        unsigned long C;  // a version-1 table held 0 here (whole rows)
         double ms;
-        if (sscanf(line, "%llx %d %d %lf", &k, &W, &pub, &ms) != 4 || W < 1 || W > kMaxWaveWarps || pub < 0 ||
-            pub > 64) {
+        if (sscanf(line, "%llx %d %lu %lf", &k, &W, &C, &ms) != 4 || W < 1 || W > kMaxWaveWarps ||
+            !(C == 0 || C == SZGB_CHUNK_ROWS || (C >= 32 && C <= 0x80000000ul && (C & (C - 1)) == 0))) {
             rc = SZGB_ECORRUPT;
             break;
         }
-        c->tune[(uint64_t)k] = szgb_ctx::Tune{W, 0, ms};
+        c->tune[(uint64_t)k] = szgb_ctx::Tune{W, C ? (uint32_t)C : SZGB_CHUNK_ROWS, ms};
     }
     fclose(f);
     drop_graph(c->g_comp);
@@ -1620,10 +1691,11 @@ size_t szgb_compress_bound(const szgb_params* p) {
     int rc = check_params(p, &cp);
     if (rc != SZGB_OK && rc != SZGB_EUNSUPPORTED) return 0;
     uint64_t N = cp.d0 * cp.d1 * cp.d2, rows = cp.d0 * cp.d1;
+    const uint64_t nch = rows * ((cp.d2 + 31) / 32);  // the most chunks (32 points each)
     // header + codebook + table + per point at most a 64-bit code and its
-    // record (9 + 23 bits; lattice variant: 1 + 64 + 32 bits)
+    // record (9 + 23 bits; lattice variant: 1 + 64 + 32 bits) + chunk padding
     const uint64_t per = cp.variant == SZGB_VARIANT_LATTICE ? 21 : 12;
-    return (size_t)(kHeaderBytes + 3 * 65536 + 4 + 4 * rows + 4 + rows + N * per + 16);
+    return (size_t)(kHeaderBytes + 3 * 65536 + 4 + 4 * nch + 4 + nch + N * per + 16);
 }
 
 int szgb_compress(szgb_ctx* c, const float* data, int data_on_device, const szgb_params* p, uint8_t* out,
@@ -1688,6 +1760,7 @@ int szgb_stream_info(const uint8_t* in_host, size_t in_len, szgb_params* out, ui
     out->m = H.m;
     out->theta = H.theta;
     out->variant = H.variant;
+    out->chunk_points = H.chunk ? H.chunk : SZGB_CHUNK_ROWS;
     if (n_unpred) *n_unpred = H.K;
     return SZGB_OK;
 }

@@ -76,7 +76,14 @@ struct CallParams {
     int m_user;              // 0 = adaptive
     double theta;
     int variant;             // 0 = the paper's method, 1 = the lattice variant
+    uint32_t chunk;          // Huffman chunk length along a row: 0 = the whole
+                             // row, else a power of two >= 32 below the row length
 };
+
+// chunks per row of a field whose rows hold `row_len` points
+__host__ __device__ inline uint64_t chunks_per_row(uint32_t chunk, uint64_t row_len) {
+    return chunk ? (row_len + chunk - 1) / chunk : 1;
+}
 
 // --------------------------------------------------------------------------
 // prediction terms: k in [0,n]^3 \ {0} in descending lexicographic order with
@@ -473,6 +480,7 @@ struct Header {
     uint64_t nchunks, K, payload, total;
     int adaptive;
     int variant;
+    uint32_t chunk;  // chunk length along a row (byte 116); 0 = whole rows
 };
 // Parses and checks a 1D-3D header held in host memory; SZGB_ECORRUPT for an
 // inconsistent one, SZGB_EUNSUPPORTED for a 4D one (callers that decode 4D
@@ -533,15 +541,18 @@ int launch_decode_tables_batch(const void* args_dev, int count, cudaStream_t s);
 // decode_args_bytes() record per field) and the prefix of per-field block
 // counts (decode_rows_blocks), count + 1 entries, in device memory
 size_t decode_args_bytes();
-uint32_t decode_rows_blocks(uint64_t rows);
+// (chunk = 0: one chunk per row; rowoff / rowbytes indexed row by row, then
+// chunk by chunk)
+uint32_t decode_rows_blocks(uint64_t rows, uint32_t chunk, uint64_t N);
 void decode_args_fill(void* dst, const uint8_t* payload, const uint64_t* rowoff, const uint32_t* rowbytes,
                       const uint8_t* stream_end, const uint32_t* lut, const uint32_t* dec_tab, uint16_t* codes,
-                      uint64_t cpitch, float* out, uint64_t rows, uint64_t N, DevState* st);
+                      uint64_t cpitch, float* out, uint64_t rows, uint64_t N, uint32_t chunk, DevState* st);
 int launch_decode_rows_batch(const void* args_dev, const uint32_t* blk_dev, int count, uint32_t total_blocks,
                              cudaStream_t s);
 int launch_decode_rows(const uint8_t* payload, const uint64_t* rowoff, const uint32_t* rowbytes,
                        const uint8_t* stream_end, const uint32_t* lut, const uint32_t* dec_tab, uint16_t* codes,
-                       uint64_t cpitch, float* out, uint64_t rows, uint64_t N, DevState* st, cudaStream_t s);
+                       uint64_t cpitch, float* out, uint64_t rows, uint64_t N, uint32_t chunk, DevState* st,
+                       cudaStream_t s);
 int launch_wave_decompress(const WaveGeom& g, int layers, const uint16_t* codes, uint64_t codes_pitch, float* out,
                            float* halo_row, float* halo_plane, unsigned int* prog, DevState* st,
                            uint64_t timeout_ns, cudaStream_t s);
@@ -561,15 +572,19 @@ int launch_histogram(const uint16_t* codes, uint64_t rows, uint64_t rowlen, uint
                      DevState* st, cudaStream_t s);
 int launch_codebook(const uint32_t* hist, DevState* st, uint8_t* len, uint64_t* cw, uint64_t* sortbuf,
                     uint32_t* nodebuf, cudaStream_t s);
+// per-chunk byte lengths (chunk = 0: one chunk per row), row by row
 int launch_rowbits(const uint16_t* codes, uint64_t pitch, const float* x, uint64_t rows, uint64_t rowlen,
-                   const uint8_t* len, uint32_t* rowbytes, DevState* st, cudaStream_t s,
+                   uint32_t chunk, const uint8_t* len, uint32_t* rowbytes, DevState* st, cudaStream_t s,
                    const uint8_t* OK = nullptr);
 int launch_scan_rows(const uint32_t* rowbytes, uint64_t rows, uint64_t* rowoff, uint64_t* blocksums,
                      DevState* st, int finalize_compress, cudaStream_t s);
-int launch_write_meta(const CallParams& cp, uint64_t rows, const uint8_t* len, const uint32_t* usedlist,
+// header (chunk length cp.chunk at byte 116), codebook and a table of nchunks entries
+int launch_write_meta(const CallParams& cp, uint64_t nchunks, const uint8_t* len, const uint32_t* usedlist,
                       const uint32_t* rowbytes, const uint64_t* rowoff, uint8_t* out, DevState* st,
                       cudaStream_t s);
-int launch_encode(const uint16_t* codes, uint64_t pitch, const float* x, uint64_t rows, uint64_t rowlen, const uint8_t* len,
+// payload; rowoff holds every chunk's byte offset (chunk = 0: one per row)
+int launch_encode(const uint16_t* codes, uint64_t pitch, const float* x, uint64_t rows, uint64_t rowlen,
+                  uint32_t chunk, const uint8_t* len,
                   const uint64_t* cw, const uint64_t* rowoff, uint8_t* out, DevState* st, cudaStream_t s,
                   const int32_t* P = nullptr, const uint8_t* OK = nullptr, int ndim = 0, int layers = 0,
                   uint64_t d1 = 1);

@@ -75,8 +75,8 @@ extern "C" int szgb_decompress_noalloc(const uint8_t* in_dev, size_t in_len, flo
     const int ndim = H.ndim, layers = H.layers, m = H.m, tw = H.tw;
     const uint64_t d2 = H.d2;
     const uint32_t nsym = H.nsym;
-    const uint64_t rows = H.nchunks, payload_bytes = H.payload;
-    const uint64_t cb = (3ull * nsym + 3) & ~3ull, tb = ((uint64_t)tw * rows + 3) & ~3ull;
+    const uint64_t rows = H.d0 * H.d1, nch = H.nchunks, payload_bytes = H.payload;
+    const uint64_t cb = (3ull * nsym + 3) & ~3ull, tb = ((uint64_t)tw * nch + 3) & ~3ull;
 
     // wavefront geometry: the same schedule as szgb_decompress with its
     // default shape (any valid schedule gives the same values)
@@ -96,7 +96,7 @@ extern "C" int szgb_decompress_noalloc(const uint8_t* in_dev, size_t in_len, flo
     const size_t o_st = take(sizeof(DevState));
     const size_t o_hrow = take((hrow + hplane) * 4), o_hplane = o_hrow + hrow * 4;
     const size_t o_prog = take((size_t)g.num_ctas * 4);
-    const size_t o_rb = take(rows * 4), o_ro = take(rows * 8), o_bs = take(((rows + 2047) / 2048 + 1) * 8);
+    const size_t o_rb = take(nch * 4), o_ro = take(nch * 8), o_bs = take(((nch + 2047) / 2048 + 1) * 8);
     const size_t o_lut = take(((size_t)1 << kLutBits) * 4), o_tab = take(kDecTabU32 * 4);
     const size_t o_len = take(65536), o_sym = take(65536 * 4);
     const uint64_t cpitch = (d2 + 7) & ~7ull;
@@ -131,12 +131,12 @@ extern "C" int szgb_decompress_noalloc(const uint8_t* in_dev, size_t in_len, flo
     if ((rc = launch_decode_tables(codebook, nsym, m, lut, dectab, reinterpret_cast<uint8_t*>(b + o_len),
                                    reinterpret_cast<uint32_t*>(b + o_sym), st, s)))
         return rc;
-    if ((rc = launch_read_rowbytes(table, tw, rows, rowbytes, s))) return rc;
-    if ((rc = launch_scan_rows(rowbytes, rows, rowoff, reinterpret_cast<uint64_t*>(b + o_bs), st, 0, s)))
+    if ((rc = launch_read_rowbytes(table, tw, nch, rowbytes, s))) return rc;
+    if ((rc = launch_scan_rows(rowbytes, nch, rowoff, reinterpret_cast<uint64_t*>(b + o_bs), st, 0, s)))
         return rc;
     uint16_t* codes = reinterpret_cast<uint16_t*>(b + o_codes);
     if ((rc = launch_decode_rows(payload, rowoff, rowbytes, payload + payload_bytes, lut, dectab, codes, cpitch,
-                                 out_dev, rows, d2, st, s)))
+                                 out_dev, rows, d2, H.chunk, st, s)))
         return rc;
     if ((rc = launch_wave_decompress(g, layers, codes, cpitch, out_dev, reinterpret_cast<float*>(b + o_hrow),
                                      reinterpret_cast<float*>(b + o_hplane), prog, st, 4000000000ull, s)))

@@ -22,6 +22,7 @@ OK, EINVAL, ENONFINITE, ETRUNC, ECORRUPT, ENOMEM, EBUDGET, ETIMEOUT, ECUDA, EUNS
     0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 ESCRATCH = -10
 ABS, REL, ABS_AND_REL = 0, 1, 2
+CHUNK_ROWS = 0xFFFFFFFF  # chunk_points: one Huffman chunk per row
 
 
 class SzgbError(RuntimeError):
@@ -33,7 +34,7 @@ class SzgbError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("ndim", C.c_int), ("shape", C.c_uint64 * 3), ("mode", C.c_int),
                 ("eb_abs", C.c_double), ("eb_rel", C.c_double), ("layers", C.c_int),
-                ("m", C.c_int), ("theta", C.c_double), ("variant", C.c_int)]
+                ("m", C.c_int), ("theta", C.c_double), ("variant", C.c_int), ("chunk_points", C.c_uint32)]
 
 
 class Stats(C.Structure):
@@ -142,7 +143,8 @@ EXPORTS = ["szgb_create", "szgb_destroy", "szgb_set_stream", "szgb_compress_boun
 VARIANT_EXACT, VARIANT_LATTICE = 0, 1
 
 
-def make_params(shape, mode=REL, eb_abs=0.0, eb_rel=1e-4, layers=1, m=0, theta=0.99, variant=0) -> Params:
+def make_params(shape, mode=REL, eb_abs=0.0, eb_rel=1e-4, layers=1, m=0, theta=0.99, variant=0,
+                chunk_points=0) -> Params:
     p = Params()
     shape = tuple(int(s) for s in shape)
     if len(shape) == 4:  # a 4D field is described by its (D P) x M x N view (szgb_compress_4d)
@@ -153,6 +155,7 @@ def make_params(shape, mode=REL, eb_abs=0.0, eb_rel=1e-4, layers=1, m=0, theta=0
     p.mode, p.eb_abs, p.eb_rel, p.layers, p.m, p.theta = mode, float(eb_abs), float(eb_rel), \
         int(layers), int(m), float(theta)
     p.variant = int(variant)
+    p.chunk_points = int(chunk_points)
     return p
 
 
@@ -181,7 +184,7 @@ def stream_info(stream) -> dict:
         raise SzgbError(rc, "szgb_stream_info")
     return {"ndim": p.ndim, "shape": tuple(p.shape[i] for i in range(p.ndim)), "mode": p.mode,
             "eb_abs": p.eb_abs, "eb_rel": p.eb_rel, "layers": p.layers, "m": p.m,
-            "theta": p.theta, "n_unpred": k.value}
+            "theta": p.theta, "chunk_points": p.chunk_points, "n_unpred": k.value}
 
 
 def _is_torch(a):
@@ -365,12 +368,12 @@ class Context:
         import torch
         _require_cuda(x, torch.float32, "x", self.device)
         p = make_params(tuple(x.shape), **kw)
-        W, pub, ms = C.c_int(), C.c_int(), C.c_double()
+        W, ch, ms = C.c_int(), C.c_int(), C.c_double()
         rc = lib().szgb_autotune(self._h, C.c_void_p(x.data_ptr()), C.byref(p), int(reps), C.byref(W),
-                                 C.byref(pub), C.byref(ms))
+                                 C.byref(ch), C.byref(ms))
         if rc:
             raise SzgbError(rc, "szgb_autotune")
-        return {"W": W.value, "pub": pub.value, "ms": ms.value}
+        return {"W": W.value, "chunk": ch.value & 0xFFFFFFFF, "ms": ms.value}
 
     def autotune_batch(self, xs, params, reps: int = 1) -> dict:
         """Pick one wavefront shape for the batch of CUDA tensors `xs`
@@ -384,11 +387,11 @@ class Context:
             _require_cuda(x, torch.float32, "xs[%d]" % i, self.device)
             P[i] = make_params(tuple(x.shape), **kw)
         dp = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
-        W, pub, ms = C.c_int(), C.c_int(), C.c_double()
-        rc = lib().szgb_autotune_batch(self._h, n, dp, P, int(reps), C.byref(W), C.byref(pub), C.byref(ms))
+        W, ch, ms = C.c_int(), C.c_int(), C.c_double()
+        rc = lib().szgb_autotune_batch(self._h, n, dp, P, int(reps), C.byref(W), C.byref(ch), C.byref(ms))
         if rc:
             raise SzgbError(rc, "szgb_autotune_batch")
-        return {"W": W.value, "pub": pub.value, "ms": ms.value}
+        return {"W": W.value, "chunk": ch.value & 0xFFFFFFFF, "ms": ms.value}
 
     def tune_save(self, path: str):
         rc = lib().szgb_tune_save(self._h, path.encode())

@@ -13,7 +13,7 @@ int main(void) {
     Z(szgb_params);
     F(szgb_params, ndim); F(szgb_params, shape); F(szgb_params, mode); F(szgb_params, eb_abs);
     F(szgb_params, eb_rel); F(szgb_params, layers); F(szgb_params, m); F(szgb_params, theta);
-    F(szgb_params, variant);
+    F(szgb_params, variant); F(szgb_params, chunk_points);
     Z(szgb_stats);
     F(szgb_stats, n_points); F(szgb_stats, n_unpred); F(szgb_stats, stream_bytes); F(szgb_stats, m);
     F(szgb_stats, maxlen); F(szgb_stats, nsym); F(szgb_stats, eb_f); F(szgb_stats, xmin); F(szgb_stats, xmax);

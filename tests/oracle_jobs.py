@@ -73,12 +73,20 @@ def rec_sha(a) -> str:
 
 
 def job(args):
-    """(idx, field or None, oracle stream, SHA-256 of the recorded values)."""
-    kind, idx, want_x = args
+    """(idx, field or None, oracle stream, SHA-256 of the recorded values);
+    args = (kind, idx, want_x[, chunk_points])."""
+    kind, idx, want_x = args[:3]
+    chunk = args[3] if len(args) > 3 else 0
     from oracle import szo
     x, kw = field(kind, idx)
-    s, rec, _ = szo.compress(x, want_aux=True, **kw)
+    s, rec, _ = szo.compress(x, want_aux=True, chunk_points=chunk, **kw)
     return idx, (x if want_x else None), s, rec_sha(rec)
+
+
+def gen(args):
+    """(idx, field) without the oracle."""
+    kind, idx = args
+    return idx, field(kind, idx)[0]
 
 
 def noop(_):

@@ -1,12 +1,19 @@
-"""The autotuner picks a wavefront shape per shape class and persists it; the
-shape changes the schedule only, so streams stay byte-identical to the
-oracle's before and after tuning, and after a save/load round trip."""
+"""The autotuner picks a wavefront shape and a Huffman chunk length per shape
+class and persists them; the shape changes the schedule only and the chunk
+length only the chunking, so after tuning every stream is byte-identical to
+the oracle's stream with that chunk length (whole rows when the length is at
+least the row), also after a save/load round trip, and decompresses to the
+same values."""
 import numpy as np
 import pytest
 
 from synthetic import fields
 
 pytestmark = pytest.mark.gpu
+
+
+def _oracle_chunk(szgb, t):
+    return 0 if t["chunk"] == szgb.CHUNK_ROWS else t["chunk"]
 
 
 def test_autotune_keeps_bits(szo, tmp_path):
@@ -20,24 +27,29 @@ def test_autotune_keeps_bits(szo, tmp_path):
     ctx = szgb.Context(0)
     path = str(tmp_path / "tune.txt")
     try:
+        chunks = []
         for x, kw in cases:
-            ref = szo.compress(x, **kw)
             xd = torch.from_numpy(x).cuda()
             t = ctx.autotune(xd, reps=1, **kw)
-            assert t["W"] in (1, 2, 4, 6, 8) and t["pub"] == 0 and t["ms"] > 0
+            assert t["W"] in (1, 2, 4, 6, 8) and t["chunk"] in (szgb.CHUNK_ROWS, 128, 256, 512, 1024) and t["ms"] > 0
+            chunks.append(_oracle_chunk(szgb, t))
+            ref = szo.compress(x, chunk_points=chunks[-1], **kw)
             s, _ = ctx.compress(xd, **kw)
             assert np.array_equal(s.cpu().numpy(), ref)
             y = ctx.decompress(s)
             assert np.array_equal(y.cpu().numpy().view(np.uint32),
                                   szo.decompress(ref).view(np.uint32))
+            # an explicit request overrides the tuned length
+            s2, _ = ctx.compress(xd, chunk_points=szgb.CHUNK_ROWS, **kw)
+            assert np.array_equal(s2.cpu().numpy(), szo.compress(x, **kw))
         ctx.tune_save(path)
         lines = [l for l in open(path) if not l.startswith("#")]
         assert len(lines) == len(cases)
         ctx2 = szgb.Context(0)
         ctx2.tune_load(path)
-        for x, kw in cases:
+        for (x, kw), c in zip(cases, chunks):
             s, _ = ctx2.compress(torch.from_numpy(x).cuda(), **kw)
-            assert np.array_equal(s.cpu().numpy(), szo.compress(x, **kw))
+            assert np.array_equal(s.cpu().numpy(), szo.compress(x, chunk_points=c, **kw))
         bad = tmp_path / "bad.txt"
         bad.write_text("0123 99 4 1.0\n")
         with pytest.raises(szgb.SzgbError) as e:
@@ -60,9 +72,12 @@ def test_autotune_batch_keeps_bits(szo):
     try:
         xd = [torch.from_numpy(x).cuda() for x in xs]
         t = ctx.autotune_batch(xd, kw, reps=1)
-        assert t["W"] in (1, 2, 4, 6, 8) and t["pub"] == 0
+        assert t["W"] in (1, 2, 4, 6, 8) and t["chunk"] in (szgb.CHUNK_ROWS, 128, 512)
         sb, _ = ctx.compress_batch(xd, kw)
         for x, s in zip(xs, sb):
-            assert np.array_equal(s.cpu().numpy(), szo.compress(x, **kw))
+            assert np.array_equal(s.cpu().numpy(), szo.compress(x, chunk_points=_oracle_chunk(szgb, t), **kw))
+        ys = ctx.decompress_batch(sb)
+        for x, s, y in zip(xs, sb, ys):
+            assert np.array_equal(y.cpu().numpy().view(np.uint32), szo.decompress(s.cpu().numpy()).view(np.uint32))
     finally:
         ctx.close()

@@ -50,9 +50,9 @@ def env(pool):
     c.close()
 
 
-def _oracle(pool, kind, idxs, want_x=True):
+def _oracle(pool, kind, idxs, want_x=True, chunk=0):
     out = {}
-    for idx, x, s, h in pool.imap_unordered(J.job, [(kind, i, want_x) for i in idxs], chunksize=1):
+    for idx, x, s, h in pool.imap_unordered(J.job, [(kind, i, want_x, chunk) for i in idxs], chunksize=1):
         out[idx] = (x, s, h)
     return [out[i] for i in idxs]
 
@@ -88,20 +88,25 @@ def test_climate79_batched_and_per_field(env, pool):
 
 
 def test_uneven512_autotuned_graph(env, pool):
+    """The autotuner picks the wavefront shape and the Huffman chunk length;
+    the oracle then codes every field with that chunk length."""
     torch, szgb, ctx = env
     t0 = time.perf_counter()
-    refs = _oracle(pool, "uneven512", range(512))
+    gen = dict(pool.imap_unordered(J.gen, [("uneven512", i) for i in range(512)], chunksize=1))
     kws = [dict(eb_rel=J.uneven_shape(i)[1], m=0) for i in range(512)]
-    xs = [torch.from_numpy(x).cuda() for x, _, _ in refs]
+    xs = [torch.from_numpy(gen[i]).cuda() for i in range(512)]
+    del gen
     tuned = ctx.autotune_batch(xs, kws, reps=1)
     assert tuned["W"] >= 1
-    for rep in range(2):  # captured with the tuned shape, then replayed
+    chunk = 0 if tuned["chunk"] == szgb.CHUNK_ROWS else tuned["chunk"]
+    refs = _oracle(pool, "uneven512", range(512), want_x=False, chunk=chunk)
+    for rep in range(2):  # captured with the tuned shape and chunking, then replayed
         sb, st = ctx.compress_batch(xs, kws)
         _check_streams(sb, refs, "uneven #%d" % rep)
         ys = ctx.decompress_batch(sb)
         _check_recon(ys, refs, "uneven #%d" % rep)
         del ys
-    print("uneven512: %.1f s (W = %d)" % (time.perf_counter() - t0, tuned["W"]))
+    print("uneven512: %.1f s (W = %d, chunk %d)" % (time.perf_counter() - t0, tuned["W"], chunk))
 
 
 @pytest.mark.parametrize("layers", [1, 2])
