@@ -157,10 +157,27 @@ def run_reference(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": "planes 0-19 of the 100x500x500 field",
                        "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": val, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": "20x500x500 slab, compress+decompress, single thread"},
+            "cpu_baseline": dict({"value": val, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                                  "sample": "20x500x500 slab, compress+decompress, single thread"}, **host_cpu()),
             "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def host_cpu():
+    """Core count and CPU model of the host the oracle runs on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"host_cores": os.cpu_count(), "host_cpu": model}
 
 
 def cpu_baseline_sample():
@@ -178,8 +195,10 @@ def cpu_baseline_sample():
         if time.perf_counter() - t0 > 12.0:
             break
     dt = time.perf_counter() - t0
-    return {"value": 2 * slab.nbytes * reps / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": "10x500x500 slab of the field, compress+decompress, %d reps, single thread" % reps}
+    d = {"value": 2 * slab.nbytes * reps / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+         "sample": "10x500x500 slab of the field, compress+decompress, %d reps, single thread" % reps}
+    d.update(host_cpu())
+    return d
 
 
 def _oracle_round_trip(item):
@@ -216,10 +235,88 @@ def cpu_baseline_fields(items, budget_s=8.0, workers=None):
         t1 = time.perf_counter()
         nb_all = sum(pool.map(_oracle_round_trip, sample, chunksize=1))
         dt = time.perf_counter() - t1
-    return {"value": single, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": "first %d fields of the batch, compress+decompress, single thread" % k,
-            "all_cores": {"value": 2 * nb_all / dt / 1e9, "unit": "GB/s", "cores": workers,
-                          "sample": "first %d fields, one field per task, spawned process pool" % len(sample)}}
+    d = {"value": single, "unit": "GB/s", "cores": 1, "kind": "oracle",
+         "sample": "first %d fields of the batch, compress+decompress, single thread" % k,
+         "all_cores": {"value": 2 * nb_all / dt / 1e9, "unit": "GB/s", "cores": workers,
+                       "sample": "first %d fields, one field per task, spawned process pool" % len(sample)}}
+    d.update(host_cpu())
+    return d
+
+
+def batched_subset(szgb, torch, dev, stream, nfields=16, steps=5, cpu=True):
+    """The batched form against the plain one-field-per-call form on the same
+    GPU: climate fields 0..nfields-1 of the 79-field batch (1800 x 3600, rel
+    eb 1e-4, n = 1, adaptive m), device-resident (inputs larger than L2), one
+    batched pass (persistent wavefront launch, CUDA graph) against one
+    compress and one decompress call per field, both timed with CUDA events
+    on the library's stream (median of `steps` passes after a warm-up), every
+    point checked against its bound."""
+    from synthetic import fields
+    peak = peaks()[0]
+    xs_np = [fields.climate_batch_field(i) for i in range(nfields)]
+    xs = [torch.from_numpy(x).to(dev) for x in xs_np]
+    npts = sum(x.numel() for x in xs)
+    nbytes = 4 * npts
+    kw = dict(eb_rel=1e-4, layers=1, m=0)
+    bctx = szgb.Context(dev.index or 0)
+    bctx.set_stream(stream.cuda_stream)
+    outs = [torch.empty(szgb.compress_bound(tuple(x.shape), **kw), dtype=torch.uint8, device=dev) for x in xs]
+    ys = [torch.empty_like(x) for x in xs]
+    tuned = bctx.autotune_batch(xs, kw, reps=1)
+
+    def timed(fn):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        r = fn(e1)
+        e2.record(stream)
+        e2.synchronize()
+        return e0.elapsed_time(e1), e1.elapsed_time(e2), r
+
+    def batched(e1):
+        sb, st = bctx.compress_batch(xs, kw, outs)
+        e1.record(stream)
+        bctx.decompress_batch(sb, ys)
+        return sb, st
+
+    def per_field(e1):
+        ss = [bctx.compress(x, out=o, **kw)[0] for x, o in zip(xs, outs)]
+        e1.record(stream)
+        for s_, y in zip(ss, ys):
+            bctx.decompress(s_, out=y)
+        return ss
+
+    for _ in range(2):
+        timed(batched)
+    tb = [timed(batched) for _ in range(steps)]
+    sb, st = tb[-1][2]
+    worst = max(float((y.double() - x.double()).abs().max()) / float(t.eb_f) for x, y, t in zip(xs, ys, st))
+    assert worst < 1.0, "error bound violated"
+    timed(per_field)
+    tp = [timed(per_field) for _ in range(max(2, steps // 2))]
+    bc, bd = statistics.median(t[0] for t in tb), statistics.median(t[1] for t in tb)
+    pc, pd = statistics.median(t[0] for t in tp), statistics.median(t[1] for t in tp)
+    stream_bytes = sum(int(s_.numel()) for s_ in sb)
+    b8 = stream_bytes / npts  # stream bytes per point
+    bctx.close()
+    out = {"workload": "climate fields 0-%d of the 79-field batch, 1800x3600 fp32, rel eb 1e-4, n1, adaptive m"
+                       % (nfields - 1),
+           "fields": nfields, "input_gb": nbytes / 1e9, "l2": "inputs larger than L2",
+           "value": 2 * nbytes / ((bc + bd) / 1e3) / 1e9, "unit": "GB/s",
+           "per_field_calls_value": 2 * nbytes / ((pc + pd) / 1e3) / 1e9,
+           "batched_over_per_field": (pc + pd) / (bc + bd),
+           "compress_gbs": {"batched": nbytes / (bc / 1e3) / 1e9, "per_field_calls": nbytes / (pc / 1e3) / 1e9},
+           "decompress_gbs": {"batched": nbytes / (bd / 1e3) / 1e9, "per_field_calls": nbytes / (pd / 1e3) / 1e9},
+           "compression_factor": nbytes / stream_bytes, "max_error_over_eb": worst,
+           "autotuned": {"W": tuned["W"], "chunk_points": ("whole rows" if tuned["chunk"] == szgb.CHUNK_ROWS
+                                                            else tuned["chunk"])},
+           "roofline": {"bound": "hbm", "peak": peak, "unit": "GB/s",
+                        "compress_frac": ((8.0 + b8) * npts / (bc / 1e3) / 1e9) / peak,
+                        "decompress_frac": ((4.0 + b8) * npts / (bd / 1e3) / 1e9) / peak,
+                        "note": "algorithmic bytes of the whole batched pass: compress 8 B/pt (range and "
+                                "predict reads) + stream, decompress stream + 4 B/pt"}}
+    if cpu:
+        out["cpu_baseline"] = cpu_baseline_fields([(x, 1e-4) for x in xs_np], budget_s=5.0)
+    return out
 
 
 def run_batch_workload(args):
@@ -604,6 +701,8 @@ def main():
     ap.add_argument("--layers", type=int, default=1)
     ap.add_argument("--ebrel", type=float, default=1e-4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default shape, whole-row chunks)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched sub-measurement of the default run")
     ap.add_argument("--variant", default="exact", choices=["exact", "lattice"],
                     help="exact: the paper's method (default); lattice: the separately labelled "
                          "fully parallel lattice variant, reported beside it")
@@ -655,6 +754,9 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     ctx.set_stream(stream.cuda_stream)
     kw = dict(eb_rel=args.ebrel, layers=args.layers, m=0, variant=1 if args.variant == "lattice" else 0)
+    # the wavefront shape and the Huffman chunk length are picked by the
+    # autotuner before the timed region (chunk_points = 0 takes its choice)
+    tuned = ctx.autotune(x, reps=2, **kw) if args.variant == "exact" and not args.no_tune else None
     bound = szgb.compress_bound(x_np.shape, **kw)
     sbuf = torch.empty(bound, dtype=torch.uint8, device=dev)
     y = torch.empty_like(x)
@@ -763,6 +865,9 @@ def main():
             dist.barrier()
         return
     cpu = None if args.no_cpu_baseline else cpu_baseline_sample()
+    batched = None
+    if not args.no_batched and args.variant == "exact" and ws == 1:
+        batched = batched_subset(szgb, torch, dev, stream, cpu=not args.no_cpu_baseline)
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -770,6 +875,8 @@ def main():
         "config": {"workload": WORKLOAD + ("" if args.variant == "exact" else "-LATTICE-VARIANT"),
                    "variant": args.variant, "shape": list(x_np.shape), "eb_rel": args.ebrel,
                    "layers": args.layers, "m": "adaptive", "m_chosen": int(st0.m),
+                   "autotuned": ({"W": tuned["W"], "chunk_points": ("whole rows" if tuned["chunk"] == szgb.CHUNK_ROWS
+                                                                    else tuned["chunk"])} if tuned else None),
                    "l2": "flushed (256 MiB write) before every step",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "compress_gbs": {"p50": pct(comp_gbs, 50), "p99": pct(comp_gbs, 1)},
@@ -781,6 +888,7 @@ def main():
         "phase_ms": phase_ms,
         "roofline": roof,
         "cpu_baseline": cpu,
+        "batched": batched,
         "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": nbytes + stream_bytes,
                 "d2h_bytes_per_step": stream_bytes + nbytes},
         # kernels of this library per step: compress 11 (range, adapt, wavefront,

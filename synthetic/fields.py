@@ -119,19 +119,22 @@ def climate2d(seed: int, n0: int = 1800, n1: int = 3600, mask: bool = False,
     return f.astype(np.float32)
 
 
-def climate_batch(nfields: int = 79, n0: int = 1800, n1: int = 3600,
-                  seed0: int = 300) -> list:
-    """The 79-field climate batch: fields seed0..seed0+78; 15% (12) carry a
-    masked constant region and 5% (4) a step front."""
+def climate_batch_field(i: int, nfields: int = 79, n0: int = 1800, n1: int = 3600,
+                        seed0: int = 300) -> np.ndarray:
+    """Field i of the climate batch: seed seed0 + i; 15% of the fields
+    (12 of 79) carry a masked constant region and 5% (4 of 79) a step
+    front, spread evenly over the batch."""
     nmask = round(0.15 * nfields)
     nfront = round(0.05 * nfields)
     masked = {(k * nfields) // max(nmask, 1) + 1 for k in range(nmask)}
     fronts = {(k * nfields) // max(nfront, 1) + 3 for k in range(nfront)}
-    out = []
-    for i in range(nfields):
-        out.append(climate2d(seed0 + i, n0, n1, mask=i in masked,
-                             front=i in fronts))
-    return out
+    return climate2d(seed0 + i, n0, n1, mask=i in masked, front=i in fronts)
+
+
+def climate_batch(nfields: int = 79, n0: int = 1800, n1: int = 3600,
+                  seed0: int = 300) -> list:
+    """The 79-field climate batch (climate_batch_field for i = 0..78)."""
+    return [climate_batch_field(i, nfields, n0, n1, seed0) for i in range(nfields)]
 
 
 def uneven_batch(nfields: int = 512, seed: int = 4, seed0: int = 4000,

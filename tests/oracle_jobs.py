@@ -20,12 +20,7 @@ def field(kind: str, idx: int):
     from synthetic import fields
     if kind == "climate79":
         # fields.climate_batch() field by field: seeds 300..378, 12 masked, 4 fronts
-        nf = 79
-        nmask, nfront = round(0.15 * nf), round(0.05 * nf)
-        masked = {(k * nf) // nmask + 1 for k in range(nmask)}
-        fronts = {(k * nf) // nfront + 3 for k in range(nfront)}
-        x = fields.climate2d(300 + idx, 1800, 3600, mask=idx in masked, front=idx in fronts)
-        return x, dict(eb_rel=1e-4, m=0)
+        return fields.climate_batch_field(idx), dict(eb_rel=1e-4, m=0)
     if kind == "uneven512":
         shape, eb = uneven_shape(idx)
         g = fields._spectral_noise(np.random.default_rng(4000 + idx), shape, 3.0)
