@@ -569,11 +569,29 @@ int launch_rowbits(const uint16_t* codes, uint64_t pitch, const float* x, uint64
 
 constexpr int kScanTile = 2048;
 
+// in: the counts (tab == nullptr), or the stream's chunk table of `width`-byte
+// little-endian entries, whose values are also written to counts_out
 __global__ void __launch_bounds__(1024) k_scan_local(const uint32_t* __restrict__ in, uint64_t n,
-                                                     uint64_t* out, uint64_t* blocksums) {
+                                                     uint64_t* out, uint64_t* blocksums,
+                                                     const uint8_t* __restrict__ tab, int width,
+                                                     uint32_t* __restrict__ counts_out) {
     __shared__ uint64_t s[kScanTile];
     const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
-    for (int i = threadIdx.x; i < kScanTile; i += blockDim.x) s[i] = (base + i < n) ? in[base + i] : 0;
+    for (int i = threadIdx.x; i < kScanTile; i += blockDim.x) {
+        uint64_t v = 0;
+        if (base + i < n) {
+            if (tab) {
+                const uint8_t* p = tab + (base + i) * width;
+                uint32_t u = p[0] | ((uint32_t)p[1] << 8);
+                if (width == 4) u |= ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+                counts_out[base + i] = u;
+                v = u;
+            } else {
+                v = in[base + i];
+            }
+        }
+        s[i] = v;
+    }
     __syncthreads();
     // Hillis-Steele inclusive scan over 2048 elements (2 per thread)
     for (int off = 1; off < kScanTile; off <<= 1) {
@@ -593,11 +611,23 @@ __global__ void __launch_bounds__(1024) k_scan_local(const uint32_t* __restrict_
     if (threadIdx.x == 0) blocksums[blockIdx.x] = s[kScanTile - 1];
 }
 
-__global__ void __launch_bounds__(1024) k_scan_blocks(uint64_t* blocksums, int nblocks, DevState* st,
-                                                      uint64_t rows, int finalize) {
-    if (threadIdx.x == 0) {
-        uint64_t acc = 0;
-        for (int b = 0; b < nblocks; b++) { uint64_t t = blocksums[b]; blocksums[b] = acc; acc += t; }
+// one warp: exclusive scan of the block sums, 32 at a time
+__global__ void __launch_bounds__(32) k_scan_blocks(uint64_t* blocksums, int nblocks, DevState* st,
+                                                    uint64_t rows, int finalize) {
+    const int lane = threadIdx.x;
+    uint64_t acc = 0;
+    for (int b0 = 0; b0 < nblocks; b0 += 32) {
+        const int b = b0 + lane;
+        const uint64_t t = b < nblocks ? blocksums[b] : 0;
+        uint64_t incl = t;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (b < nblocks) blocksums[b] = acc + incl - t;
+        acc += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) {
         if (finalize) {
             st->payload = acc;
             unsigned tw = st->maxrow <= 0xffffu ? 2u : 4u;
@@ -621,9 +651,10 @@ __global__ void __launch_bounds__(1024) k_scan_add(uint64_t* out, uint64_t n, co
 }
 
 int launch_scan_rows(const uint32_t* rowbytes, uint64_t rows, uint64_t* rowoff, uint64_t* blocksums,
-                     DevState* st, int finalize_compress, cudaStream_t s) {
+                     DevState* st, int finalize_compress, cudaStream_t s, const uint8_t* table, int width) {
     int nb = (int)((rows + kScanTile - 1) / kScanTile);
-    k_scan_local<<<nb, 1024, 0, s>>>(rowbytes, rows, rowoff, blocksums);
+    k_scan_local<<<nb, 1024, 0, s>>>(table ? nullptr : rowbytes, rows, rowoff, blocksums, table, width,
+                                     const_cast<uint32_t*>(rowbytes));
     k_scan_blocks<<<1, 32, 0, s>>>(blocksums, nb, st, rows, finalize_compress);
     k_scan_add<<<nb, 1024, 0, s>>>(rowoff, rows, blocksums);
     return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
@@ -1137,22 +1168,5 @@ int launch_decode_tables(const uint8_t* codebook, uint32_t nsym, int m, uint32_t
     return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
 }
 
-__global__ void k_read_rowbytes(const uint8_t* __restrict__ tab, int width, uint64_t rows, uint32_t* rb) {
-    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < rows;
-         r += (uint64_t)gridDim.x * blockDim.x) {
-        const uint8_t* p = tab + r * width;
-        uint32_t v = p[0] | ((uint32_t)p[1] << 8);
-        if (width == 4) v |= ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
-        rb[r] = v;
-    }
-}
-
-int launch_read_rowbytes(const uint8_t* table, int width, uint64_t rows, uint32_t* rowbytes, cudaStream_t s) {
-    uint64_t blocks = (rows + 255) / 256;
-    if (blocks > 4096) blocks = 4096;
-    if (blocks < 1) blocks = 1;
-    k_read_rowbytes<<<(int)blocks, 256, 0, s>>>(table, width, rows, rowbytes);
-    return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
-}
 
 }  // namespace szgb

@@ -80,14 +80,28 @@ __global__ void __launch_bounds__(256) k_range(const float* __restrict__ x, uint
         last = (t == gridDim.x - 1);
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
+    if (!last) return;
+    // the last block: every thread folds a strided share of the partials,
+    // then the block reduces them (min and max are exact in any order)
     __threadfence();
     const volatile float* vp = partials;
-    mn = vp[0];
-    mx = vp[1];
-    for (unsigned b = 1; b < gridDim.x; b++) {
+    mn = FLT_MAX;
+    mx = -FLT_MAX;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
         mn = fminf(mn, vp[2 * b]);
         mx = fmaxf(mx, vp[2 * b + 1]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    __syncthreads();  // smn / smx are reused
+    if (l == 0) { smn[w] = mn; smx[w] = mx; }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int i = 1; i < (int)(blockDim.x >> 5); i++) {
+        mn = fminf(mn, smn[i]);
+        mx = fmaxf(mx, smx[i]);
     }
     // the stored range is the value range: a signed zero is stored as +0
     mn = __fadd_rn(mn, 0.0f);

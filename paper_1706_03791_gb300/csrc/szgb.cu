@@ -697,8 +697,7 @@ int decompress_impl(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_dev
     }
     {
         PhaseTimer t(c, PH_DEC_SCAN);
-        if ((rc = launch_read_rowbytes(table, H.tw, nch, rowbytes, s))) return rc;
-        if ((rc = launch_scan_rows(rowbytes, nch, rowoff, blocksums, st, 0, s))) return rc;
+        if ((rc = launch_scan_rows(rowbytes, nch, rowoff, blocksums, st, 0, s, table, H.tw))) return rc;
     }
     if (lattice) {
         PhaseTimer t(c, PH_WAVE_D);
@@ -1279,15 +1278,16 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
             cudaMemcpyAsync(dblk, h_blk, 4 * ((size_t)count + 1), cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemcpyAsync(targs, Hb + o_tab, (size_t)count * tsz, cudaMemcpyHostToDevice, s) != cudaSuccess)
             return SZGB_ECUDA;
-        // every field's decoder tables in one launch (one CTA each)
-        if ((r = launch_decode_tables_batch(targs, count, s))) return r;
+        // every field's chunk offsets (auxiliary streams) while the decoder
+        // tables of every field are built in one launch (one CTA each)
         fork_aux(c);
         for (int f = 0; f < count; f++) {
             DecPlan& q = P[f];
             cudaStream_t a = c->aux[f % kAux];
-            if ((r = launch_read_rowbytes(q.table, q.H.tw, q.nch, q.rowbytes, a))) return r;
-            if ((r = launch_scan_rows(q.rowbytes, q.nch, q.rowoff, q.blocksums, st + f, 0, a))) return r;
+            if ((r = launch_scan_rows(q.rowbytes, q.nch, q.rowoff, q.blocksums, st + f, 0, a, q.table, q.H.tw)))
+                return r;
         }
+        if ((r = launch_decode_tables_batch(targs, count, s))) return r;
         join_aux(c);
         if ((r = launch_decode_rows_batch(dargs, dblk, count, dec_blocks, s))) return r;
         for (int li = 0; li < kMaxLayers; li++) {

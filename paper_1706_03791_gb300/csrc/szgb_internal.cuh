@@ -576,8 +576,12 @@ int launch_codebook(const uint32_t* hist, DevState* st, uint8_t* len, uint64_t* 
 int launch_rowbits(const uint16_t* codes, uint64_t pitch, const float* x, uint64_t rows, uint64_t rowlen,
                    uint32_t chunk, const uint8_t* len, uint32_t* rowbytes, DevState* st, cudaStream_t s,
                    const uint8_t* OK = nullptr);
+// exclusive scan of the chunk byte counts into offsets; with `table` (the
+// stream's chunk table, entries of `width` bytes) the counts are read from it
+// and stored in rowbytes (which is then written, not read)
 int launch_scan_rows(const uint32_t* rowbytes, uint64_t rows, uint64_t* rowoff, uint64_t* blocksums,
-                     DevState* st, int finalize_compress, cudaStream_t s);
+                     DevState* st, int finalize_compress, cudaStream_t s, const uint8_t* table = nullptr,
+                     int width = 0);
 // header (chunk length cp.chunk at byte 116), codebook and a table of nchunks entries
 int launch_write_meta(const CallParams& cp, uint64_t nchunks, const uint8_t* len, const uint32_t* usedlist,
                       const uint32_t* rowbytes, const uint64_t* rowoff, uint8_t* out, DevState* st,
@@ -590,8 +594,6 @@ int launch_encode(const uint16_t* codes, uint64_t pitch, const float* x, uint64_
                   uint64_t d1 = 1);
 int launch_decode_tables(const uint8_t* codebook, uint32_t nsym, int m, uint32_t* lut, uint32_t* dec_tab,
                          uint8_t* lenbuf, uint32_t* symbuf, DevState* st, cudaStream_t s);
-int launch_read_rowbytes(const uint8_t* table, int width, uint64_t rows, uint32_t* rowbytes,
-                         cudaStream_t s);
 
 // scratch sizes of the codebook build (elements)
 constexpr size_t kSortBufU64 = 3 * 65536;

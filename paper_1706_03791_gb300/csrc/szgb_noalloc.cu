@@ -131,8 +131,7 @@ extern "C" int szgb_decompress_noalloc(const uint8_t* in_dev, size_t in_len, flo
     if ((rc = launch_decode_tables(codebook, nsym, m, lut, dectab, reinterpret_cast<uint8_t*>(b + o_len),
                                    reinterpret_cast<uint32_t*>(b + o_sym), st, s)))
         return rc;
-    if ((rc = launch_read_rowbytes(table, tw, nch, rowbytes, s))) return rc;
-    if ((rc = launch_scan_rows(rowbytes, nch, rowoff, reinterpret_cast<uint64_t*>(b + o_bs), st, 0, s)))
+    if ((rc = launch_scan_rows(rowbytes, nch, rowoff, reinterpret_cast<uint64_t*>(b + o_bs), st, 0, s, table, tw)))
         return rc;
     uint16_t* codes = reinterpret_cast<uint16_t*>(b + o_codes);
     if ((rc = launch_decode_rows(payload, rowoff, rowbytes, payload + payload_bytes, lut, dectab, codes, cpitch,
