@@ -459,7 +459,9 @@ def run_serve(args):
     each) of 2D fields (side log-uniform in [256, 4096]) and 3D fields (side
     log-uniform in [64, 512]), k^-3 random fields, rel eb 1e-4, admitted under
     a 100 GB device-memory budget; host buffers in and out.  Requests draw
-    their field from a seeded pool of fields generated with that recipe.
+    their field from a seeded pool of `--pool` fields generated with that
+    recipe (64 by default: every request's field cannot be generated anew at
+    200 requests/s).
     Reports p50/p99 latency (arrival to completion) and sustained GB/s."""
     import numpy as np
     import torch
@@ -468,7 +470,7 @@ def run_serve(args):
     from paper_1706_03791_gb300 import szgb
     from synthetic import fields
     rng = np.random.default_rng(5)
-    npool = 24
+    npool = args.pool
     t0 = time.perf_counter()
     pool = []
     for i in range(npool):
@@ -495,7 +497,7 @@ def run_serve(args):
     cbufs = [[torch.empty(x.numel() * 4 + (1 << 16), dtype=torch.uint8).pin_memory() for _ in range(nbuf)] for x in pool]
     dbufs = [[torch.empty(x.numel(), dtype=torch.float32).pin_memory() for _ in range(nbuf)] for x in pool]
     free = {(op, i): list(range(nbuf)) for op in "cd" for i in range(npool)}
-    srv = szgb.Server(0, budget=100 << 30, workers=3, max_batch=32)
+    srv = szgb.Server(0, budget=100 << 30, workers=args.workers, max_batch=32, log_path=args.serve_log)
     # warm-up: one request of each pool entry and operation
     for i in range(npool):
         t = srv.submit_compress(pool[i].numpy(), cbufs[i][0].numpy(), **kw)
@@ -553,7 +555,7 @@ def run_serve(args):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "serve-poisson%.0f-%.0fs-2d256-4096-3d64-512-fp32-releb1e-4" % (args.rate, args.duration),
                        "requests": nreq, "pool_fields": npool, "mean_request_mb": mean_mb,
-                       "offered_gbs": args.rate * mean_mb / 1e3, "budget_gb": 100, "workers": 3,
+                       "offered_gbs": args.rate * mean_mb / 1e3, "budget_gb": 100, "workers": args.workers,
                        "max_batch": 32, "io": "pinned host buffers in and out"},
             "latency_ms": {"p50": pct(lat_ms, 50), "p99": pct(lat_ms, 99), "max": lat_ms[-1]},
             "batches": stats["batches"], "peak_reserved_gb": stats["peak_reserved"] / 1e9,
@@ -708,6 +710,9 @@ def main():
                          "fully parallel lattice variant, reported beside it")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
     ap.add_argument("--duration", type=float, default=30.0, help="serve: seconds of arrivals")
+    ap.add_argument("--pool", type=int, default=64, help="serve: fields drawn from the recipe that requests pick from")
+    ap.add_argument("--workers", type=int, default=3, help="serve: server worker threads")
+    ap.add_argument("--serve-log", default=None, help="serve: append one JSON line per completed request here")
     ap.add_argument("--workload", default="3d", choices=["3d", "climate79", "uneven512", "serve", "rd", "layers", "hyper"],
                     help="3d: the single 100x500x500 field (default); climate79 / uneven512: "
                          "batched many-field workloads, batched+graph vs one field per call; "

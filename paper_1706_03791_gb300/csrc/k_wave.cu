@@ -1102,6 +1102,57 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
                         make_float4(vo[0], vo[1], vo[2], vo[3]);
                 }
             }
+            // 2D, one layer, the same for rows: in descending (b, e) order
+            // -(1,1) +(1,0) +(0,1)
+            if constexpr (ND == 2 && NL == 1) {
+                if (wl0 >= 31 && wl0 + 3 < N) {
+                    interior = true;
+                    const int cl0 = wl0 & (kRV - 1);
+                    const float4 r4 = *reinterpret_cast<const float4*>(vr_own + cl0);
+                    const int c0 = lq & (kTW - 1);
+                    const int sl0 = (int)(((unsigned)lq >> 5) % kTS) * kTE;
+                    const int sl1 = (sl0 == (kTS - 1) * kTE) ? 0 : sl0 + kTE;
+                    int tix[kTile];
+#pragma unroll
+                    for (int k = 0; k < kTile; k++) tix[k] = (c0 + k >= kTW) ? sl1 + c0 + k - kTW : sl0 + c0 + k;
+                    int dc[kTile];
+                    float du[kTile];
+                    if constexpr (DEC) {
+#pragma unroll
+                        for (int k = 0; k < kTile; k++) {
+                            dc[k] = (int)xw[tix[k]];
+                            du[k] = 0.0f;
+                            if (dc[k] == 0 && valid) du[k] = out_row[lq + k];
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < kTile; k++) {
+                        const float rk = (k == 0) ? r4.x : (k == 1) ? r4.y : (k == 2) ? r4.z : r4.w;
+                        float nr = __shfl_up_sync(0xffffffffu, oV[1], 1);
+                        nr = (lane == 0) ? rk : nr;
+                        Rr[1][1] = Rr[1][0];
+                        Rr[1][0] = nr;
+                        float pred = -Rr[1][1];
+                        pred = __fadd_rn(pred, Rr[1][0]);
+                        pred = __fadd_rn(pred, oV[1]);
+                        float V;
+                        if constexpr (!DEC) {
+                            const float xv = xw[tix[k]];
+                            const float tr = trunc_value(xv, qp.e_eb);
+                            const int code = quantize_tr(xv, pred, tr, qp, V);
+                            ow[tix[k]] = (uint16_t)code;
+                        } else {
+                            V = dc[k] ? dequantize(dc[k], pred, qp) : du[k];
+                            ow[tix[k]] = V;
+                        }
+                        oV[1] = V;
+                        st_shared_f32_if(has_hr, hr_addr + 4u * (uint32_t)((lq + k) & (kRV - 1)), V);
+                        if constexpr (TR) {
+                            if (valid) rec_row[lq + k] = V;
+                        }
+                    }
+                }
+            }
             if (!interior) {
                 float4 pr[NL + 1];
                 if (ND == 3) {

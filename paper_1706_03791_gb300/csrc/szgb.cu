@@ -116,14 +116,17 @@ struct PhaseTimer {
 int ensure_scratch(szgb_ctx* c, size_t need) {
     if (need <= c->scratch_cap) return SZGB_OK;
     if (c->budget && need > c->budget) return SZGB_EBUDGET;
+    const size_t old_cap = c->scratch_cap;
     if (c->scratch) {
         cudaStreamSynchronize(c->stream);
         cudaFree(c->scratch);
         c->scratch = nullptr;
         c->scratch_cap = 0;
     }
-    size_t cap = align_up(need + need / 8, 1 << 20);
-    if (c->budget && cap > c->budget) cap = need;
+    // grow at least twofold: a regrowth frees the old block, and cudaFree
+    // waits for all work on the device
+    size_t cap = align_up(std::max(need + need / 8, 2 * old_cap), 1 << 20);
+    if (c->budget && cap > c->budget) cap = c->budget;  // need <= budget
     if (cudaMalloc(&c->scratch, cap) != cudaSuccess) {
         cudaGetLastError();
         return SZGB_ENOMEM;
@@ -774,13 +777,15 @@ int ensure_aux(szgb_ctx* c) {
 
 int ensure_pinned(szgb_ctx* c, size_t need) {
     if (need <= c->h_batch_cap) return SZGB_OK;
+    const size_t old_cap = c->h_batch_cap;
     if (c->h_batch) {
         cudaStreamSynchronize(c->stream);
         cudaFreeHost(c->h_batch);
         c->h_batch = nullptr;
         c->h_batch_cap = 0;
     }
-    size_t cap = align_up(need + need / 4, 1 << 16);
+    // grow at least twofold from 1 MiB: cudaFreeHost waits for the device
+    size_t cap = align_up(std::max(std::max(need + need / 4, (size_t)1 << 20), 2 * old_cap), 1 << 16);
     if (cudaMallocHost(&c->h_batch, cap) != cudaSuccess) {
         cudaGetLastError();
         return SZGB_ENOMEM;

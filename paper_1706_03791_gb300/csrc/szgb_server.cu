@@ -4,17 +4,27 @@
 //
 // Every worker thread owns a library context (its own stream, device scratch
 // and codebook tables, all kept resident between batches) and a resident
-// device I/O arena.  A worker takes the oldest pending requests that fit in
-// the budget (at most max_batch), copies their host inputs to the device,
-// runs one batched compression and one batched decompression, copies the
-// results back and completes the requests.  Requests that arrive while a
+// device I/O arena.  A worker takes pending requests in arrival order that
+// fit in the budget (at most max_batch), copies their host inputs to the
+// device, runs one batched compression and one batched decompression, copies
+// the results back and completes the requests.  Requests that arrive while a
 // batch is on the GPU wait for the next free worker; with several workers,
-// the copies and kernels of different batches overlap.  A request's result
+// the copies and kernels of different batches overlap.
+//
+// Batches are formed by size, so that small requests do not wait behind
+// large ones: a large request (I/O of kLargeBytes or more) runs alone, a
+// batch of small requests gathers at most kBatchBytes of I/O, and with two
+// or more workers worker 0 takes small requests only, so that one worker is
+// always free of large ones.  The other workers take the oldest pending
+// request's kind first.  A request's result
 // is exactly the result of the single-field calls: batches change the
 // schedule, never the bits.
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <condition_variable>
 #include <deque>
 #include <mutex>
@@ -30,6 +40,21 @@ namespace {
 
 size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
 constexpr int kNoStatus = -1000;  // a batch call returned before reaching the field
+constexpr size_t kLargeBytes = 128ull << 20;  // a request of this much I/O or more runs alone
+constexpr size_t kBatchBytes = 64ull << 20;   // I/O bytes a batch of small requests gathers at most
+constexpr size_t kCopyPiece = 16ull << 20;    // host<->device copies go in pieces of this size
+
+// A host<->device copy in pieces, so that the copies of other workers'
+// streams can be scheduled between them.
+cudaError_t copy_pieces(void* dst, const void* src, size_t n, cudaMemcpyKind kind, cudaStream_t st) {
+    for (size_t o = 0; o < n; o += kCopyPiece) {
+        const size_t len = std::min(kCopyPiece, n - o);
+        const cudaError_t e =
+            cudaMemcpyAsync(static_cast<char*>(dst) + o, static_cast<const char*>(src) + o, len, kind, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
 
 struct Req {
     szgb_request r;
@@ -75,8 +100,30 @@ size_t scratch_estimate(int op, uint64_t n_points) {
     return (size_t)(0.3 * (double)n_points) + (1u << 20);
 }
 
+// Debug trace: with SZGB_SERVER_TRACE=<file>, one line per batch (worker,
+// requests, I/O bytes, and the seconds at which the batch was taken, its
+// inputs were queued, its kernels returned and its outputs arrived).
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+struct Trace {
+    FILE* f = nullptr;
+    std::mutex mu;
+    Trace() {
+        const char* p = getenv("SZGB_SERVER_TRACE");
+        if (p && *p) f = fopen(p, "a");
+    }
+    ~Trace() {
+        if (f) fclose(f);
+    }
+};
+Trace& trace() {
+    static Trace t;
+    return t;
+}
+
 void run_batch(szgb_server* S, szgb_ctx* ctx, cudaStream_t st, void*& dbuf, size_t& dcap,
-               std::vector<Req*>& batch) {
+               std::vector<Req*>& batch, double* t_in, double* t_run) {
     // device I/O layout of the batch
     std::vector<size_t> off_in(batch.size()), off_out(batch.size());
     size_t total = 0;
@@ -90,7 +137,9 @@ void run_batch(szgb_server* S, szgb_ctx* ctx, cudaStream_t st, void*& dbuf, size
         if (dbuf) cudaFree(dbuf);
         dbuf = nullptr;
         dcap = 0;
-        size_t cap = up256(total + total / 4);
+        // grow at least twofold: every regrowth frees the old arena, and
+        // cudaFree waits for the whole device (every worker's work)
+        size_t cap = up256(std::max(total + total / 4, 2 * dcap));
         if (cudaMalloc(&dbuf, cap) != cudaSuccess) {
             cudaGetLastError();
             for (Req* q : batch) q->status = SZGB_ENOMEM;
@@ -100,12 +149,13 @@ void run_batch(szgb_server* S, szgb_ctx* ctx, cudaStream_t st, void*& dbuf, size
     }
     char* D = static_cast<char*>(dbuf);
     for (size_t i = 0; i < batch.size(); i++) {
-        if (cudaMemcpyAsync(D + off_in[i], batch[i]->r.in, batch[i]->r.in_bytes, cudaMemcpyHostToDevice, st) !=
+        if (copy_pieces(D + off_in[i], batch[i]->r.in, batch[i]->r.in_bytes, cudaMemcpyHostToDevice, st) !=
             cudaSuccess) {
             for (Req* q : batch) q->status = SZGB_ECUDA;
             return;
         }
     }
+    *t_in = now_s();
     // one batched call per operation
     std::vector<size_t> ci, di;
     for (size_t i = 0; i < batch.size(); i++) (batch[i]->r.op == SZGB_OP_COMPRESS ? ci : di).push_back(i);
@@ -132,10 +182,11 @@ void run_batch(szgb_server* S, szgb_ctx* ctx, cudaStream_t st, void*& dbuf, size
             q->out_len = len[k];
             if (q->status == SZGB_OK && len[k] > q->r.out_cap) q->status = SZGB_ETRUNC;
             if (q->status == SZGB_OK &&
-                cudaMemcpyAsync(q->r.out, D + off_out[ci[k]], len[k], cudaMemcpyDeviceToHost, st) != cudaSuccess)
+                copy_pieces(q->r.out, D + off_out[ci[k]], len[k], cudaMemcpyDeviceToHost, st) != cudaSuccess)
                 q->status = SZGB_ECUDA;
         }
     }
+    *t_run = now_s();
     if (!di.empty()) {
         const int n = (int)di.size();
         std::vector<const uint8_t*> in(n);
@@ -155,7 +206,7 @@ void run_batch(szgb_server* S, szgb_ctx* ctx, cudaStream_t st, void*& dbuf, size
             q->status = sts[k] != kNoStatus ? sts[k] : (rc ? rc : SZGB_ECUDA);
             q->out_len = q->n_points * 4;
             if (q->status == SZGB_OK &&
-                cudaMemcpyAsync(q->r.out, D + off_out[di[k]], q->out_len, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+                copy_pieces(q->r.out, D + off_out[di[k]], q->out_len, cudaMemcpyDeviceToHost, st) != cudaSuccess)
                 q->status = SZGB_ECUDA;
         }
     }
@@ -163,17 +214,55 @@ void run_batch(szgb_server* S, szgb_ctx* ctx, cudaStream_t st, void*& dbuf, size
         for (Req* q : batch) q->status = SZGB_ECUDA;
 }
 
-void worker_main(szgb_server* S) {
+bool is_large(const Req* q) { return q->dev_in + q->dev_out >= kLargeBytes; }
+
+// The next batch of worker `wid` from the pending queue (caller holds the
+// lock): see the file comment.  Requests are taken in arrival order within
+// their kind; a request that does not fit the budget stops the scan (no
+// overtaking past the budget).
+void take_batch(szgb_server* S, int wid, std::vector<Req*>& batch) {
+    const bool small_only = wid == 0 && S->workers.size() >= 2;
+    auto take = [&](std::deque<Req*>::iterator it) {
+        Req* q = *it;
+        S->reserved += q->need;
+        S->peak_reserved = std::max(S->peak_reserved, S->reserved);
+        batch.push_back(q);
+        return S->pending.erase(it);
+    };
+    if (!small_only && !S->pending.empty() && is_large(S->pending.front())) {  // alone
+        if (S->reserved + S->pending.front()->need <= S->budget) take(S->pending.begin());
+        return;
+    }
+    size_t bytes = 0;
+    for (auto it = S->pending.begin(); it != S->pending.end() && (int)batch.size() < S->max_batch;) {
+        Req* q = *it;
+        if (is_large(q)) {
+            ++it;
+            continue;
+        }
+        if (S->reserved + q->need > S->budget) break;
+        if (!batch.empty() && bytes + q->dev_in + q->dev_out > kBatchBytes) break;
+        bytes += q->dev_in + q->dev_out;
+        it = take(it);
+    }
+}
+
+void worker_main(szgb_server* S, int wid) {
     cudaSetDevice(S->device);
     szgb_ctx* ctx = nullptr;
-    cudaStream_t st = nullptr;
+    // batches of small requests run on a high-priority stream, a large
+    // request on a low-priority one: when both have work ready, the small
+    // batch's thread blocks are scheduled first
+    cudaStream_t st_small = nullptr, st_large = nullptr;
     int init_rc = szgb_create(&ctx, S->device, 0);
-    if (init_rc == SZGB_OK && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+    int prio_low = 0, prio_high = 0;
+    if (init_rc == SZGB_OK && cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess)
         init_rc = SZGB_ECUDA;
-    if (init_rc == SZGB_OK) {
-        szgb_set_stream(ctx, st);
-        szgb_set_graphs(ctx, 0);  // every batch differs: launch directly
-    }
+    if (init_rc == SZGB_OK &&
+        (cudaStreamCreateWithPriority(&st_small, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
+         cudaStreamCreateWithPriority(&st_large, cudaStreamNonBlocking, prio_low) != cudaSuccess))
+        init_rc = SZGB_ECUDA;
+    if (init_rc == SZGB_OK) szgb_set_graphs(ctx, 0);  // every batch differs: launch directly
     void* dbuf = nullptr;
     size_t dcap = 0;
     for (;;) {
@@ -182,24 +271,30 @@ void worker_main(szgb_server* S) {
             std::unique_lock<std::mutex> lk(S->mu);
             for (;;) {
                 if (S->stop && S->pending.empty()) break;
-                // the oldest requests that fit in the budget, in arrival order
-                while (!S->pending.empty() && (int)batch.size() < S->max_batch) {
-                    Req* q = S->pending.front();
-                    if (S->reserved + q->need > S->budget) break;
-                    S->reserved += q->need;
-                    S->peak_reserved = std::max(S->peak_reserved, S->reserved);
-                    batch.push_back(q);
-                    S->pending.pop_front();
-                }
+                take_batch(S, wid, batch);
                 if (!batch.empty()) break;
+                // stopping with only requests this worker does not take: leave
+                // them to the workers that do
+                if (S->stop && wid == 0 && S->workers.size() >= 2) break;
                 S->cv_work.wait(lk);
             }
             if (batch.empty()) break;  // stopping, nothing pending
         }
+        const double t_take = now_s();
+        double t_in = t_take, t_run = t_take;
         if (init_rc != SZGB_OK) {
             for (Req* q : batch) q->status = init_rc;
         } else {
-            run_batch(S, ctx, st, dbuf, dcap, batch);
+            cudaStream_t st = (batch.size() == 1 && is_large(batch[0])) ? st_large : st_small;
+            szgb_set_stream(ctx, st);
+            run_batch(S, ctx, st, dbuf, dcap, batch, &t_in, &t_run);
+        }
+        if (trace().f) {
+            size_t io = 0;
+            for (Req* q : batch) io += q->dev_in + q->dev_out;
+            std::lock_guard<std::mutex> tl(trace().mu);
+            fprintf(trace().f, "%d %zu %zu %.6f %.6f %.6f %.6f\n", wid, batch.size(), io, t_take, t_in, t_run,
+                    now_s());
         }
         {
             std::lock_guard<std::mutex> lk(S->mu);
@@ -215,7 +310,8 @@ void worker_main(szgb_server* S) {
     }
     if (dbuf) cudaFree(dbuf);
     if (ctx) szgb_destroy(ctx);
-    if (st) cudaStreamDestroy(st);
+    if (st_small) cudaStreamDestroy(st_small);
+    if (st_large) cudaStreamDestroy(st_large);
 }
 
 }  // namespace
@@ -230,7 +326,11 @@ int szgb_server_create(szgb_server** out, int device, size_t device_mem_budget, 
     S->device = device;
     S->budget = device_mem_budget;
     S->max_batch = max_batch;
-    for (int i = 0; i < workers; i++) S->workers.emplace_back(worker_main, S);
+    {
+        // the workers read S->workers.size() under the lock
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (int i = 0; i < workers; i++) S->workers.emplace_back(worker_main, S, i);
+    }
     *out = S;
     return SZGB_OK;
 }
@@ -296,7 +396,7 @@ int szgb_submit(szgb_server* S, const szgb_request* r, uint64_t* ticket) {
         S->pending.push_back(q);
         *ticket = q->ticket;
     }
-    S->cv_work.notify_one();
+    S->cv_work.notify_all();  // the worker that takes it may not be the first to wake
     return SZGB_OK;
 }
 

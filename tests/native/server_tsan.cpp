@@ -2,7 +2,9 @@
 // ThreadSanitizer: several threads submit compress and decompress requests,
 // take results by wait and by poll (two takers race for some tickets), and
 // one thread reads the statistics throughout; then the server is destroyed
-// with requests still queued.  Built by the test that runs it, with the
+// with requests still queued.  A second server mixes large requests (run
+// alone, never by worker 0) with small ones and is destroyed with a large
+// request queued.  Built by the test that runs it, with the
 // server source instrumented.  On a machine without a GPU every admitted
 // request completes with SZGB_ECUDA, which exercises the same queue,
 // admission and completion paths.
@@ -143,7 +145,67 @@ int main() {
         if (szgb_submit(S, &r, &tk) != SZGB_OK) failures++;
     }
     szgb_server_destroy(S);
-    std::printf("requests %d completed %llu batches %llu races %d failures %d\n", total,
-                (unsigned long long)c, (unsigned long long)b, lost_races.load(), failures.load());
+
+    // size classes: requests of 128 MiB of I/O or more run alone, never on
+    // worker 0; they must complete beside small ones, and a large request
+    // still queued at destruction is finished too
+    szgb_server* L = nullptr;
+    if (szgb_server_create(&L, 0, 2ull << 30, 3, 8) != SZGB_OK) {
+        std::fprintf(stderr, "server_create (large) failed\n");
+        return 1;
+    }
+    const size_t big_rows = 4096, big_cols = 4200;  // 68.8 MB in, 64 MiB out: large
+    std::vector<float> big(big_rows * big_cols, 0.5f);
+    std::vector<unsigned char> big_out(64u << 20);
+    szgb_params bp = field_params();
+    bp.shape[0] = big_rows;
+    bp.shape[1] = big_cols;
+    std::vector<uint64_t> lt;
+    for (int k = 0; k < 6; k++) {
+        szgb_request r;
+        std::memset(&r, 0, sizeof(r));
+        r.op = SZGB_OP_COMPRESS;
+        if (k % 3 == 1) {  // a large request between small ones
+            r.in = big.data();
+            r.in_bytes = big.size() * sizeof(float);
+            r.params = bp;
+            r.out = big_out.data();
+            r.out_cap = big_out.size();
+        } else {
+            r.in = xs[k].data();
+            r.in_bytes = xs[k].size() * sizeof(float);
+            r.params = field_params();
+            r.out = outs[k].data();
+            r.out_cap = outs[k].size();
+        }
+        uint64_t tk = 0;
+        if (szgb_submit(L, &r, &tk) != SZGB_OK) failures++;
+        lt.push_back(tk);
+    }
+    for (uint64_t tk : lt) {
+        int st = 0;
+        size_t len = 0;
+        if (szgb_wait(L, tk, &st, &len) != SZGB_OK || !expected(st)) failures++;
+    }
+    uint64_t lb = 0, lc = 0;
+    szgb_server_stats(L, &lb, &lc, nullptr);
+    if (lc != lt.size()) failures++;
+    {
+        szgb_request r;
+        std::memset(&r, 0, sizeof(r));
+        r.op = SZGB_OP_COMPRESS;
+        r.in = big.data();
+        r.in_bytes = big.size() * sizeof(float);
+        r.params = bp;
+        r.out = big_out.data();
+        r.out_cap = big_out.size();
+        uint64_t tk = 0;
+        if (szgb_submit(L, &r, &tk) != SZGB_OK) failures++;
+    }
+    szgb_server_destroy(L);  // returns only after the queued large request ran
+
+    std::printf("requests %d completed %llu batches %llu races %d large-phase %llu failures %d\n", total,
+                (unsigned long long)c, (unsigned long long)b, lost_races.load(), (unsigned long long)lc,
+                failures.load());
     return failures.load() == 0 ? 0 : 1;
 }
