@@ -145,7 +145,9 @@ __device__ void bitonic_sort(uint64_t* a, int n_pow2) {
 
 // canonical code assignment over symbols listed in ascending order: the code
 // of a symbol of length L is first[L] + (number of earlier symbols of length
-// L).  Done by warp 0, 32 symbols at a time.
+// L).  Done by warp 0, 32 symbols at a time.  cw_out[s] holds the encoder's
+// table entry: the length in the top byte, the code below it (lengths are at
+// most 46, so a code fits in 56 bits).
 __device__ void canonical_assign(const uint32_t* syms, int n, const uint8_t* len, uint64_t* first_io,
                                  uint64_t* cw_out, uint32_t* rank_out) {
     if (threadIdx.x >= 32) return;
@@ -160,7 +162,7 @@ __device__ void canonical_assign(const uint32_t* syms, int n, const uint8_t* len
             unsigned peers = __match_any_sync(act, L);
             int rank = __popc(peers & ((1u << lane) - 1u));
             uint64_t f = first_io[L];
-            if (cw_out) cw_out[s] = f + (uint64_t)rank;
+            if (cw_out) cw_out[s] = ((uint64_t)L << 56) | (f + (uint64_t)rank);
             if (rank_out) rank_out[i] = (uint32_t)(f + rank);
             __syncwarp(act);
             if (rank == 0) first_io[L] = f + (uint64_t)__popc(peers);
@@ -262,7 +264,7 @@ __device__ __forceinline__ void codebook_block(const uint32_t* __restrict__ hist
         if (tid == 0) {
             uint32_t s = usedlist[0];
             len[s] = 1;
-            cw[s] = 0;
+            cw[s] = 1ull << 56;  // length 1, code 0
             st->nsym = 1;
             st->maxlen = 1;
         }
@@ -853,8 +855,9 @@ __global__ void __launch_bounds__(kEncWarps * 32) k_encode(const uint16_t* __res
                 cwk[k] = 0;
                 if (k < nv) {
                     const uint32_t c = (w[k >> 1] >> (16 * (k & 1))) & 0xffffu;
-                    L[k] = __ldg(len + c);
-                    cwk[k] = __ldg(cw + c);
+                    const uint64_t e = __ldg(cw + c);  // length << 56 | code
+                    L[k] = (uint32_t)(e >> 56);
+                    cwk[k] = e & ((1ull << 56) - 1ull);
                     nbits += L[k];
                     if (c == 0) {
                         any0 = true;
@@ -882,7 +885,7 @@ __global__ void __launch_bounds__(kEncWarps * 32) k_encode(const uint16_t* __res
                 // span at most three buffer words (OR-ed: neighbours may share them)
                 uint64_t bits = 0;
 #pragma unroll
-                for (int k = 0; k < kEncPts; k++) bits = (L[k] >= 64) ? cwk[k] : ((bits << L[k]) | cwk[k]);
+                for (int k = 0; k < kEncPts; k++) bits = (bits << L[k]) | cwk[k];  // L <= 46
                 if (nbits) {
                     const uint64_t a = bits << (64 - nbits);  // MSB-aligned
                     const uint32_t wi = off >> 5, sh = off & 31;

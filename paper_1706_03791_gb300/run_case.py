@@ -1,7 +1,7 @@
 """Run one compress + decompress of a synthetic field on cuda:0 (a small,
 self-contained case for profilers such as ncu).
 
-    python -m paper_1706_03791_gb300.run_case --kind blobs3d --shape 100 500 500 --reps 2
+    python -m paper_1706_03791_gb300.run_case --kind blobs3d --shape 100 500 500 --reps 2 --chunk 256
 """
 from __future__ import annotations
 
@@ -21,6 +21,7 @@ def main():
     ap.add_argument("--ebrel", type=float, default=1e-4)
     ap.add_argument("--layers", type=int, default=1)
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--chunk", type=int, default=0, help="Huffman chunk length (0: the context's autotuned length, else whole rows)")
     args = ap.parse_args()
     import torch
     from paper_1706_03791_gb300 import build, szgb
@@ -33,7 +34,7 @@ def main():
     xd = torch.from_numpy(x).cuda()
     ctx = szgb.Context(0)
     for _ in range(args.reps):
-        s, st = ctx.compress(xd, eb_rel=args.ebrel, layers=args.layers, m=0)
+        s, st = ctx.compress(xd, eb_rel=args.ebrel, layers=args.layers, m=0, chunk_points=args.chunk)
         y = ctx.decompress(s)
     torch.cuda.synchronize()
     err = float((y.double() - xd.double()).abs().max())
