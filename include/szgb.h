@@ -29,8 +29,8 @@
  * whole row (fastest-axis line), or C consecutive points of one (header byte
  * 116 holds C, 0 for whole rows); chunks follow row by row.  The same bytes are produced by the CPU oracle of the test-suite.
  * The format also carries 4D fields (the predictor of Sec. III in four
- * dimensions; the slowest extent at header byte 120): szgb_compress_4d
- * writes them and szgb_decompress reads them.
+ * dimensions; ndim 4 at header byte 8, the slowest extent at byte 120, the
+ * other three at bytes 16-40).  Every call takes them.
  */
 #ifndef SZGB_H
 #define SZGB_H
@@ -63,15 +63,17 @@ extern "C" {
 typedef struct szgb_ctx szgb_ctx;
 
 typedef struct {
-    int ndim;           /* 1, 2 or 3 */
-    uint64_t shape[3];  /* extents, slowest -> fastest */
+    int ndim;           /* 1, 2, 3 or 4 */
+    uint64_t shape[4];  /* extents, slowest -> fastest; entries past ndim
+                           are ignored.  4D: shape[0] x shape[1] and the
+                           point count below 2^32, the exact variant only */
     int mode;           /* SZGB_ABS / SZGB_REL / SZGB_ABS_AND_REL */
     double eb_abs;      /* absolute bound (>= 0), modes ABS, ABS_AND_REL */
     double eb_rel;      /* relative bound (>= 0) times (max - min) */
     int layers;         /* n of the n-layer predictor (Sec. III-B; the
-                           paper's default is 1): 1..4; batches, the
-                           autotuner and szgb_decompress_noalloc take 3D
-                           fields up to n = 2 */
+                           paper's default is 1): 1..4 in every dimension
+                           (the autotuner tunes the wavefront: 1D-3D with
+                           n <= 2 in 3D) */
     int m;              /* 2..16: 2^m - 1 intervals; 0 = adaptive (Sec. IV-B) */
     double theta;       /* adaptive-m hit-rate threshold, e.g. 0.99 */
     int variant;        /* SZGB_VARIANT_EXACT (0): the paper's method;
@@ -98,8 +100,9 @@ typedef struct {
  * store the residual in 64 bits and, when needed, x exactly.  Every point
  * is still within the bound.  Compression and decompression are fully
  * parallel (no wavefront).  Its streams carry tag 1 in header byte 113 and
- * are never produced unless requested.  Single-field calls only (batches
- * and the no-allocation path return SZGB_EUNSUPPORTED). */
+ * are never produced unless requested.  1D-3D with n <= 2; batches run such
+ * fields one by one on their own kernels; the no-allocation path returns
+ * SZGB_EUNSUPPORTED for its streams. */
 #define SZGB_VARIANT_EXACT 0
 #define SZGB_VARIANT_LATTICE 1
 
@@ -132,9 +135,12 @@ size_t szgb_compress_bound(const szgb_params *p);
  * device, out_cap bytes).  *out_len receives the stream size, also when
  * SZGB_ETRUNC reports that out_cap is too small.  opt_stats may be NULL.
  * Fails with SZGB_ENONFINITE on NaN/Inf input, SZGB_EINVAL on bad
- * parameters.  Layers 1..4 in every dimension: 3D fields with n = 3, 4 run
- * on hyperplane kernels (one launch per hyperplane), everything else on the
- * wavefront. */
+ * parameters.  Layers 1..4 in every dimension: 3D fields with n = 3, 4 and
+ * 4D fields run on the hyperplane kernels, 1D-3D fields otherwise on the
+ * wavefront.  A 4D field's stream
+ * says ndim = 4 and keeps shape[0] at header byte 120; its rows of shape[3]
+ * points are coded as those of the (shape[0] shape[1]) x shape[2] x shape[3]
+ * view, whose szgb_compress_bound it never exceeds. */
 int szgb_compress(szgb_ctx *ctx, const float *data, int data_on_device,
                   const szgb_params *p, uint8_t *out, size_t out_cap,
                   int out_on_device, size_t *out_len, szgb_stats *opt_stats);
@@ -149,18 +155,11 @@ int szgb_compress_trace(szgb_ctx *ctx, const float *data_dev, const szgb_params 
                         uint16_t *codes_dev);
 
 /* 4D fields (Sec. III: the n-layer predictor of Eq. predmodel with d = 4;
- * quantization and coding as for 1D-3D).  Compresses the device array
- * data_dev of shape[0..3] (slowest first; each extent 1..2^32-1, shape[0] x
- * shape[1] and the point count below 2^32; 16-byte aligned) with the bound,
- * layers (1..4), m and theta of p (p->ndim, p->shape ignored; the exact
- * variant only).  out_dev (device, 4-byte aligned) takes out_cap bytes; the
- * stream never exceeds szgb_compress_bound of the 3D view
- * (shape[0] shape[1], shape[2], shape[3]).  recorded_dev and codes_dev are
- * NULL or device arrays of one entry per point as in szgb_compress_trace.
- * The stream's header says ndim = 4 and keeps shape[0] at byte 120;
- * szgb_decompress decodes it (szgb_stream_info, the batched and the
- * no-allocation calls return SZGB_EUNSUPPORTED for it).  Runs on hyperplane
- * kernels, one launch per i0 + i + j + l = h.  Errors as szgb_compress. */
+ * quantization and coding as for 1D-3D) with trace outputs: as
+ * szgb_compress_trace of the device array data_dev with p->ndim = 4 and
+ * p->shape = shape[0..3] (p->ndim and p->shape are ignored; the exact
+ * variant only).  recorded_dev and codes_dev are NULL or device arrays of
+ * one entry per point.  Errors as szgb_compress. */
 int szgb_compress_4d(szgb_ctx *ctx, const float *data_dev, const uint64_t *shape,
                      const szgb_params *p, uint8_t *out_dev, size_t out_cap, size_t *out_len,
                      szgb_stats *opt_stats, float *recorded_dev, uint16_t *codes_dev);
@@ -195,8 +194,8 @@ int szgb_decompress(szgb_ctx *ctx, const uint8_t *in, size_t in_len,
  *    the GPU race.  It never calls cudaMalloc/cudaFree or an allocating
  *    library routine.
  *  - Errors: SZGB_EINVAL (null or misaligned buffer, out too small),
- *    SZGB_ECORRUPT (inconsistent stream), SZGB_EUNSUPPORTED (4D streams,
- *    lattice-variant streams, 3D streams with n > 2), SZGB_ESCRATCH,
+ *    SZGB_ECORRUPT (inconsistent stream), SZGB_EUNSUPPORTED (streams of
+ *    the lattice variant), SZGB_ESCRATCH,
  *    SZGB_ETIMEOUT, SZGB_ECUDA, as szgb_decompress. */
 int szgb_decompress_noalloc(const uint8_t *in_dev, size_t in_len, float *out_dev,
                             size_t out_cap_elems, void *cuda_stream);
@@ -212,17 +211,19 @@ int szgb_decompress_noalloc(const uint8_t *in_dev, size_t in_len, float *out_dev
  * capacities, parameters) repeat (szgb_set_graphs(ctx, 0) launches directly
  * instead).  out_len[i] receives each stream size, also on SZGB_ETRUNC;
  * opt_stats is NULL or holds count entries.  Returns 0 or the error of the
- * first field that failed; SZGB_EUNSUPPORTED for the lattice variant and for
- * 3D fields with n > 2 (single-field calls take those). */
+ * first field (in batch order) that failed.  Fields the wavefront does not
+ * carry (3D n = 3, 4; 4D; the lattice variant) run after the batch's
+ * wavefront fields, one at a time on their own kernels, outside the graph.
+ * A bad parameter of any field fails the call before any work. */
 int szgb_compress_batch(szgb_ctx *ctx, int count, const float *const *data_dev,
                         const szgb_params *params, uint8_t *const *out_dev,
                         const size_t *out_cap, size_t *out_len, szgb_stats *opt_stats);
 
 /* Batched decompression: stream i (in_dev[i], in_len[i] bytes, 4-byte
  * aligned) into out_dev[i] (out_cap_elems[i] floats, 16-byte aligned), all
- * device memory; one persistent wavefront launch as above (the same
- * SZGB_EUNSUPPORTED cases).  opt_status is NULL or receives count per-field
- * codes. */
+ * device memory; one persistent wavefront launch as above (streams of
+ * fields the wavefront does not carry run one at a time after it).
+ * opt_status is NULL or receives count per-field codes. */
 int szgb_decompress_batch(szgb_ctx *ctx, int count, const uint8_t *const *in_dev,
                           const size_t *in_len, float *const *out_dev,
                           const size_t *out_cap_elems, int *opt_status);
@@ -238,8 +239,8 @@ int szgb_decompress_batch(szgb_ctx *ctx, int count, const uint8_t *const *in_dev
  * length changes the stream's chunking (and size) but not the decompressed
  * values.  *W_out and *ms_out (may be NULL) receive the shape and its time;
  * *pub_out receives the chosen chunk length (SZGB_CHUNK_ROWS for whole
- * rows).  SZGB_EUNSUPPORTED for 3D fields with n > 2, which do not run on
- * the wavefront. */
+ * rows).  SZGB_EUNSUPPORTED for 3D fields with n > 2 and 4D fields, which
+ * do not run on the wavefront. */
 int szgb_autotune(szgb_ctx *ctx, const float *data_dev, const szgb_params *p, int reps,
                   int *W_out, int *pub_out, double *ms_out);
 /* As szgb_autotune for a batch: times szgb_compress_batch +
@@ -348,8 +349,9 @@ int szgb_server_create(szgb_server **out, int device, size_t device_mem_budget,
                        int workers, int max_batch);
 /* Queues a request; the caller keeps `in` and `out` valid and untouched
  * until the request is done.  *ticket identifies it.  SZGB_EBUDGET when the
- * request alone exceeds the budget; SZGB_EUNSUPPORTED for what the batched
- * path does not carry (the lattice variant, 3D fields with n > 2). */
+ * request alone exceeds the budget.  Requests the batched wavefront does not
+ * carry (3D n = 3, 4; 4D; the lattice variant) run alone, on their own
+ * kernels. */
 int szgb_submit(szgb_server *srv, const szgb_request *req, uint64_t *ticket);
 /* Non-blocking: *done = 1 once the request finished; then *status (its
  * SZGB_E* code) and *out_len (stream bytes, or 4 x points) are set and the
@@ -375,8 +377,9 @@ void szgb_server_destroy(szgb_server *srv);
 int szgb_suggest_m(const szgb_stats *st, double theta, double *hit_rate_out);
 
 /* Reads the header of a stream held in host memory: parameters (with the
- * m actually used, and chunk_points = the stream's chunk length or
- * SZGB_CHUNK_ROWS) and the number of unpredictable points. */
+ * m actually used, chunk_points = the stream's chunk length or
+ * SZGB_CHUNK_ROWS, ndim 1..4 with the field's own extents) and the number
+ * of unpredictable points.  SZGB_ECORRUPT for an inconsistent header. */
 int szgb_stream_info(const uint8_t *in_host, size_t in_len, szgb_params *out,
                      uint64_t *n_unpred);
 

@@ -143,12 +143,22 @@ uint32_t effective_chunk(uint32_t req, uint64_t row_len, int variant) {
     return req;
 }
 
+// A 4D field D x P x M x N becomes its (D P) x M x N view with cp->D4 = D:
+// its rows of N points are coded as the view's (Sec. III with d = 4).
 int check_params(const szgb_params* p, CallParams* cp) {
-    if (!p || p->ndim < 1 || p->ndim > 3) return SZGB_EINVAL;
-    uint64_t d[3] = {1, 1, 1};
-    for (int a = 0; a < p->ndim; a++) {
+    if (!p || p->ndim < 1 || p->ndim > 4) return SZGB_EINVAL;
+    for (int a = 0; a < p->ndim; a++)
         if (p->shape[a] == 0 || p->shape[a] > 0xffffffffull) return SZGB_EINVAL;
-        d[3 - p->ndim + a] = p->shape[a];
+    uint64_t d[3] = {1, 1, 1};
+    cp->D4 = 0;
+    if (p->ndim == 4) {
+        if (p->shape[0] * p->shape[1] > 0xffffffffull) return SZGB_EINVAL;
+        d[0] = p->shape[0] * p->shape[1];
+        d[1] = p->shape[2];
+        d[2] = p->shape[3];
+        cp->D4 = p->shape[0];
+    } else {
+        for (int a = 0; a < p->ndim; a++) d[3 - p->ndim + a] = p->shape[a];
     }
     unsigned __int128 n = (unsigned __int128)d[0] * d[1] * d[2];
     if (n >= ((unsigned __int128)1 << 32)) return SZGB_EINVAL;
@@ -158,7 +168,7 @@ int check_params(const szgb_params* p, CallParams* cp) {
     if (p->m != 0 && (p->m < 2 || p->m > 16)) return SZGB_EINVAL;
     if (p->layers < 1 || p->layers > 4) return SZGB_EINVAL;
     if (p->m == 0 && !(p->theta == p->theta)) return SZGB_EINVAL;
-    cp->ndim = p->ndim;
+    cp->ndim = p->ndim == 4 ? 3 : p->ndim;
     cp->d0 = d[0];
     cp->d1 = d[1];
     cp->d2 = d[2];
@@ -173,10 +183,9 @@ int check_params(const szgb_params* p, CallParams* cp) {
     const uint32_t c = p->chunk_points;
     if (!(c == 0 || c == SZGB_CHUNK_ROWS || (c >= 32 && (c & (c - 1)) == 0))) return SZGB_EINVAL;
     cp->chunk = effective_chunk(c, cp->d2, cp->variant);
-    // the lattice variant is built for n <= 2; batched, autotuned and
-    // no-allocation calls check the wavefront's set (layers_supported) too
-    if (!layers_single(p->ndim, p->layers) || (p->variant == SZGB_VARIANT_LATTICE && p->layers > 2))
-        return SZGB_EUNSUPPORTED;
+    // the lattice variant is built for 1D-3D with n <= 2; the autotuner
+    // checks the wavefront's set (wave_carries) too
+    if (p->variant == SZGB_VARIANT_LATTICE && (p->layers > 2 || p->ndim == 4)) return SZGB_EUNSUPPORTED;
     return SZGB_OK;
 }
 
@@ -316,10 +325,10 @@ bool one_field_batched(const szgb_ctx* c) {
     return c->use_graphs && !c->profiling && !c->force_W && !c->debug_skip;
 }
 
-// D4 != 0: a 4D field D4 x P x M x N given as its (D4 P) x M x N view in p
+// a 4D field runs on its (D4 P) x M x N view (cp.D4 = D4)
 int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb_params* p, uint8_t* out,
                   size_t out_cap, int out_on_device, size_t* out_len, szgb_stats* stats, float* rec_dev,
-                  uint16_t* codes_dev, uint64_t D4 = 0) {
+                  uint16_t* codes_dev) {
     if (!c || !data || !out_len) return SZGB_EINVAL;
     if (((uintptr_t)rec_dev % 16) != 0 || ((uintptr_t)codes_dev % 8) != 0) return SZGB_EINVAL;
     CallParams cp;
@@ -327,8 +336,8 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
     if (rc) return rc;
     resolve_chunk(c, p, &cp);
     // 3D fields with n = 3, 4, and 4D fields: the hyperplane kernels instead of the wavefront
-    if (D4 && (cp.ndim != 3 || cp.variant != SZGB_VARIANT_EXACT || cp.d0 % D4 != 0)) return SZGB_EINVAL;
-    const bool hyper = D4 || (cp.variant == SZGB_VARIANT_EXACT && !layers_supported(cp.ndim, cp.layers));
+    const uint64_t D4 = cp.D4;
+    const bool hyper = cp.variant == SZGB_VARIANT_EXACT && !wave_carries(cp);
     if (one_field_batched(c) && !hyper && !rec_dev && !codes_dev && cp.variant == SZGB_VARIANT_EXACT &&
         data_on_device && out_on_device && ((uintptr_t)data % 16) == 0 && ((uintptr_t)out % 4) == 0) {
         const float* d1[1] = {data};
@@ -544,9 +553,17 @@ int szgb::parse_header(const uint8_t* h, size_t in_len, Header* o) {
     o->variant = h[113];
     o->chunk = (uint32_t)rd_le(h + 116, 4);
     if (o->variant > 1) return SZGB_ECORRUPT;
-    // a 4D field (the predictor of Sec. III in four dimensions; slowest extent
-    // at byte 120) is a valid stream this library does not decode
-    if (o->ndim == 4 && o->variant == 0 && rd_le(h + 120, 8) != 0) return SZGB_EUNSUPPORTED;
+    // a 4D field D x P x M x N (the predictor of Sec. III in four dimensions;
+    // D at byte 120, P at byte 16) is checked as its (D P) x M x N view
+    o->D4 = 0;
+    if (o->ndim == 4 && o->variant == 0) {
+        const uint64_t D = rd_le(h + 120, 8), P = o->d0;
+        if (D == 0 || P == 0 || D > 0xffffffffull || P > 0xffffffffull || D * P > 0xffffffffull)
+            return SZGB_ECORRUPT;
+        o->ndim = 3;
+        o->d0 = D * P;
+        o->D4 = D;
+    }
     if (o->ndim < 1 || o->ndim > 3 || o->layers < 1 || o->layers > 4 || o->m < 2 || o->m > 16) return SZGB_ECORRUPT;
     if (o->tw != 2 && o->tw != 4 || o->mode > 2) return SZGB_ECORRUPT;
     if (o->d0 == 0 || o->d1 == 0 || o->d2 == 0 || o->d0 > 0xffffffffull || o->d1 > 0xffffffffull ||
@@ -583,31 +600,15 @@ int decompress_impl(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_dev
     } else {
         memcpy(hbuf, in, kHeaderBytes);
     }
-    // a 4D stream (D x P x M x N; D at byte 120) is checked and decoded as its
-    // (D P) x M x N view, then reconstructed over the 4D hyperplanes
-    uint8_t h3[kHeaderBytes];
-    const uint8_t* hp = hbuf;
-    uint64_t D4 = 0;
-    if (hbuf[8] == 4 && hbuf[113] == 0) {
-        D4 = rd_le(hbuf + 120, 8);
-        const uint64_t P4 = rd_le(hbuf + 16, 8);
-        if (D4 == 0 || P4 == 0 || D4 > 0xffffffffull || P4 > 0xffffffffull || D4 * P4 > 0xffffffffull)
-            return SZGB_ECORRUPT;
-        memcpy(h3, hbuf, kHeaderBytes);
-        h3[8] = 3;
-        for (int k = 0; k < 8; k++) {
-            h3[16 + k] = (uint8_t)((D4 * P4) >> (8 * k));
-            h3[120 + k] = 0;
-        }
-        hp = h3;
-    }
+    // a 4D stream (D x P x M x N) is decoded as its (D P) x M x N view, then
+    // reconstructed over the 4D hyperplanes
     Header H;
-    int rc = parse_header(hp, in_len, &H);
+    int rc = parse_header(hbuf, in_len, &H);
     if (rc) return rc;
-    if (!layers_single(H.ndim, H.layers) || (H.variant == SZGB_VARIANT_LATTICE && H.layers > 2))
-        return SZGB_EUNSUPPORTED;
+    if (H.variant == SZGB_VARIANT_LATTICE && H.layers > 2) return SZGB_EUNSUPPORTED;
+    const uint64_t D4 = H.D4;
     // 3D fields with n = 3, 4, and 4D fields: the hyperplane kernels instead of the wavefront
-    const bool hyper = D4 || (H.variant == SZGB_VARIANT_EXACT && !layers_supported(H.ndim, H.layers));
+    const bool hyper = H.variant == SZGB_VARIANT_EXACT && !wave_carries(H);
     const uint64_t N = H.d0 * H.d1 * H.d2;
     if (out_cap_elems < N) return SZGB_EINVAL;
     if (one_field_batched(c) && !hyper && H.variant == SZGB_VARIANT_EXACT && in_on_device && out_on_device &&
@@ -752,7 +753,7 @@ uint64_t header_hash(const Header& h) {
     uint64_t v = 1469598103934665603ull;
     auto mix = [&](uint64_t x) { v = (v ^ x) * 1099511628211ull; };
     mix(h.ndim); mix(h.layers); mix(h.m); mix(h.tw); mix(h.d0); mix(h.d1); mix(h.d2); mix(h.nsym);
-    mix(h.payload); mix(h.total); mix(h.chunk);
+    mix(h.payload); mix(h.total); mix(h.chunk); mix(h.D4);
     uint32_t e;
     memcpy(&e, &h.eb_f, 4);
     mix(e);
@@ -921,8 +922,7 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
         if (!data[f] || !out[f] || ((uintptr_t)data[f] % 16) || ((uintptr_t)out[f] % 4)) return SZGB_EINVAL;
         if ((rc = check_params(&params[f], &q.cp))) return rc;
         resolve_chunk(c, &params[f], &q.cp);
-        if (q.cp.variant != SZGB_VARIANT_EXACT) return SZGB_EUNSUPPORTED;  // batches run the paper's method
-        if (!layers_supported(q.cp.ndim, q.cp.layers)) return SZGB_EUNSUPPORTED;  // ... on the wavefront
+        if (!wave_carries(q.cp)) return SZGB_EUNSUPPORTED;  // the public call routes these to compress_impl
         q.n = q.cp.d0 * q.cp.d1 * q.cp.d2;
         q.rows = q.cp.d0 * q.cp.d1;
         q.rowlen = q.cp.d2;
@@ -1118,6 +1118,7 @@ struct DecPlan {
     uint8_t* lenbuf;
 };
 
+// host_hdr: NULL, or the count headers (kHeaderBytes each) already on the host
 int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, const size_t* in_len,
                           float* const* out, const size_t* out_cap, int* status, const uint8_t* host_hdr) {
     if (!c || count < 1 || !in || !in_len || !out || !out_cap) return SZGB_EINVAL;
@@ -1132,21 +1133,22 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
     for (int f = 0; f < count; f++) {
         if (!in[f] || !out[f] || ((uintptr_t)in[f] % 4) || ((uintptr_t)out[f] % 16) || in_len[f] < (size_t)kHeaderBytes)
             return SZGB_EINVAL;
-        if (host_hdr && count == 1) {
-            memcpy(c->h_batch, host_hdr, kHeaderBytes);
+        if (host_hdr) {
+            memcpy(static_cast<char*>(c->h_batch) + (size_t)f * kHeaderBytes, host_hdr + (size_t)f * kHeaderBytes,
+                   kHeaderBytes);
         } else if (cudaMemcpyAsync(static_cast<char*>(c->h_batch) + (size_t)f * kHeaderBytes, in[f], kHeaderBytes,
                                    cudaMemcpyDeviceToHost, s) != cudaSuccess) {
             return SZGB_ECUDA;
         }
     }
-    if (!(host_hdr && count == 1) && cudaStreamSynchronize(s) != cudaSuccess) return SZGB_ECUDA;
+    if (!host_hdr && cudaStreamSynchronize(s) != cudaSuccess) return SZGB_ECUDA;
     std::vector<DecPlan> P(count);
     std::vector<int> nitems(count), by_layers[kMaxLayers];
     size_t smem[kMaxLayers] = {};
     for (int f = 0; f < count; f++) {
         DecPlan& q = P[f];
         if ((rc = parse_header(static_cast<uint8_t*>(c->h_batch) + (size_t)f * kHeaderBytes, in_len[f], &q.H))) return rc;
-        if (!layers_supported(q.H.ndim, q.H.layers) || q.H.variant != SZGB_VARIANT_EXACT) return SZGB_EUNSUPPORTED;
+        if (!wave_carries(q.H)) return SZGB_EUNSUPPORTED;  // the public call routes these to decompress_impl
         q.n = q.H.d0 * q.H.d1 * q.H.d2;
         if (out_cap[f] < q.n) return SZGB_EINVAL;
         q.rows = q.H.d0 * q.H.d1;
@@ -1379,14 +1381,123 @@ void szgb_destroy(szgb_ctx* c) {
     delete c;
 }
 
+// Batches: the fields the wavefront carries run as one batch (one persistent
+// launch per pass); the others (3D n = 3, 4; 4D; the lattice variant) follow
+// one by one on their own kernels through the single-field path.  Every
+// field's result is that of the single-field call; the return value is the
+// error of the first field (in batch order) that failed.
 int szgb_compress_batch(szgb_ctx* c, int count, const float* const* data_dev, const szgb_params* params,
                         uint8_t* const* out_dev, const size_t* out_cap, size_t* out_len, szgb_stats* opt_stats) {
-    return compress_batch_impl(c, count, data_dev, params, out_dev, out_cap, out_len, opt_stats);
+    if (!c || count < 1 || !data_dev || !params || !out_dev || !out_cap || !out_len) return SZGB_EINVAL;
+    std::vector<int> wave, side;
+    for (int f = 0; f < count; f++) {
+        CallParams cp;
+        int rc = check_params(&params[f], &cp);
+        if (rc) return rc;
+        if (!data_dev[f] || !out_dev[f] || ((uintptr_t)data_dev[f] % 16) || ((uintptr_t)out_dev[f] % 4))
+            return SZGB_EINVAL;
+        (wave_carries(cp) ? wave : side).push_back(f);
+    }
+    if (side.empty()) return compress_batch_impl(c, count, data_dev, params, out_dev, out_cap, out_len, opt_stats);
+    std::vector<szgb_stats> st(count);
+    std::vector<int> status(count, SZGB_OK);
+    if (!wave.empty()) {
+        const size_t k = wave.size();
+        std::vector<const float*> d(k);
+        std::vector<szgb_params> p(k);
+        std::vector<uint8_t*> o(k);
+        std::vector<size_t> cap(k), len(k);
+        std::vector<szgb_stats> ws(k);
+        for (size_t i = 0; i < k; i++) {
+            d[i] = data_dev[wave[i]];
+            p[i] = params[wave[i]];
+            o[i] = out_dev[wave[i]];
+            cap[i] = out_cap[wave[i]];
+        }
+        const int rc = compress_batch_impl(c, (int)k, d.data(), p.data(), o.data(), cap.data(), len.data(), ws.data());
+        if (rc != SZGB_OK) {
+            bool per_field = false;  // a field's own error, or one of the whole call
+            for (size_t i = 0; i < k; i++) per_field |= ws[i].status == rc;
+            if (!per_field) return rc;
+        }
+        for (size_t i = 0; i < k; i++) {
+            out_len[wave[i]] = len[i];
+            st[wave[i]] = ws[i];
+            status[wave[i]] = ws[i].status;
+        }
+    }
+    for (int f : side) {
+        szgb_stats one = {};
+        status[f] = compress_impl(c, data_dev[f], 1, &params[f], out_dev[f], out_cap[f], 1, &out_len[f], &one,
+                                  nullptr, nullptr);
+        if (status[f] == SZGB_ECUDA) return status[f];
+        one.status = status[f];
+        st[f] = one;
+    }
+    int first = SZGB_OK;
+    for (int f = 0; f < count && !first; f++) first = status[f];
+    if (opt_stats)
+        for (int f = 0; f < count; f++) opt_stats[f] = st[f];
+    return first;
 }
 
 int szgb_decompress_batch(szgb_ctx* c, int count, const uint8_t* const* in_dev, const size_t* in_len,
                           float* const* out_dev, const size_t* out_cap_elems, int* opt_status) {
-    return decompress_batch_impl(c, count, in_dev, in_len, out_dev, out_cap_elems, opt_status);
+    if (!c || count < 1 || !in_dev || !in_len || !out_dev || !out_cap_elems) return SZGB_EINVAL;
+    if (cudaSetDevice(c->device) != cudaSuccess) return SZGB_ECUDA;
+    // every header to the host (one small copy per field, one synchronisation)
+    int rc = ensure_pinned(c, (size_t)count * kHeaderBytes);
+    if (rc) return rc;
+    for (int f = 0; f < count; f++) {
+        if (!in_dev[f] || !out_dev[f] || ((uintptr_t)in_dev[f] % 4) || ((uintptr_t)out_dev[f] % 16) ||
+            in_len[f] < (size_t)kHeaderBytes)
+            return SZGB_EINVAL;
+        if (cudaMemcpyAsync(static_cast<char*>(c->h_batch) + (size_t)f * kHeaderBytes, in_dev[f], kHeaderBytes,
+                            cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+            return SZGB_ECUDA;
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SZGB_ECUDA;
+    std::vector<uint8_t> hdr(static_cast<uint8_t*>(c->h_batch), static_cast<uint8_t*>(c->h_batch) + (size_t)count * kHeaderBytes);
+    std::vector<int> wave, side;
+    for (int f = 0; f < count; f++) {
+        Header H;
+        if ((rc = parse_header(hdr.data() + (size_t)f * kHeaderBytes, in_len[f], &H))) return rc;
+        (wave_carries(H) ? wave : side).push_back(f);
+    }
+    if (side.empty())
+        return decompress_batch_impl(c, count, in_dev, in_len, out_dev, out_cap_elems, opt_status, hdr.data());
+    std::vector<int> status(count, SZGB_OK);
+    if (!wave.empty()) {
+        const size_t k = wave.size();
+        std::vector<const uint8_t*> in(k);
+        std::vector<size_t> len(k), cap(k);
+        std::vector<float*> o(k);
+        std::vector<uint8_t> h(k * kHeaderBytes);
+        std::vector<int> ws(k, SZGB_OK);
+        for (size_t i = 0; i < k; i++) {
+            in[i] = in_dev[wave[i]];
+            len[i] = in_len[wave[i]];
+            o[i] = out_dev[wave[i]];
+            cap[i] = out_cap_elems[wave[i]];
+            memcpy(h.data() + i * kHeaderBytes, hdr.data() + (size_t)wave[i] * kHeaderBytes, kHeaderBytes);
+        }
+        rc = decompress_batch_impl(c, (int)k, in.data(), len.data(), o.data(), cap.data(), ws.data(), h.data());
+        if (rc != SZGB_OK) {
+            bool per_field = false;  // a field's own error, or one of the whole call
+            for (size_t i = 0; i < k; i++) per_field |= ws[i] == rc;
+            if (!per_field) return rc;
+        }
+        for (size_t i = 0; i < k; i++) status[wave[i]] = ws[i];
+    }
+    for (int f : side) {
+        status[f] = decompress_impl(c, in_dev[f], in_len[f], 1, out_dev[f], out_cap_elems[f], 1);
+        if (status[f] == SZGB_ECUDA) return status[f];
+    }
+    int first = SZGB_OK;
+    for (int f = 0; f < count && !first; f++) first = status[f];
+    if (opt_status)
+        for (int f = 0; f < count; f++) opt_status[f] = status[f];
+    return first;
 }
 
 int szgb_autotune(szgb_ctx* c, const float* data_dev, const szgb_params* p, int reps, int* W_out, int* pub_out,
@@ -1395,7 +1506,7 @@ int szgb_autotune(szgb_ctx* c, const float* data_dev, const szgb_params* p, int 
     if (!c || !data_dev || !p) return SZGB_EINVAL;
     int rc = check_params(p, &cp);
     if (rc) return rc;
-    if (!layers_supported(cp.ndim, cp.layers)) return SZGB_EUNSUPPORTED;  // it tunes the wavefront
+    if (cp.D4 || !layers_supported(cp.ndim, cp.layers)) return SZGB_EUNSUPPORTED;  // it tunes the wavefront
     if (cudaSetDevice(c->device) != cudaSuccess) return SZGB_ECUDA;
     if (reps < 1) reps = 1;
     const uint64_t N = cp.d0 * cp.d1 * cp.d2;
@@ -1484,7 +1595,7 @@ int szgb_autotune_batch(szgb_ctx* c, int count, const float* const* data_dev, co
     int maxl = 1;
     for (int f = 0; f < count && !rc; f++) {
         rc = check_params(&params[f], &cps[f]);
-        if (rc == SZGB_OK && !layers_supported(cps[f].ndim, cps[f].layers)) rc = SZGB_EUNSUPPORTED;
+        if (rc == SZGB_OK && (cps[f].D4 || !layers_supported(cps[f].ndim, cps[f].layers))) rc = SZGB_EUNSUPPORTED;
         if (rc) break;
         any3 |= cps[f].ndim == 3;
         maxl = std::max(maxl, cps[f].layers);
@@ -1721,18 +1832,11 @@ int szgb_compress_4d(szgb_ctx* c, const float* data_dev, const uint64_t* shape, 
                      uint8_t* out_dev, size_t out_cap, size_t* out_len, szgb_stats* opt_stats, float* recorded_dev,
                      uint16_t* codes_dev) {
     if (!c || !data_dev || !shape || !p || !out_dev || !out_len) return SZGB_EINVAL;
-    for (int a = 0; a < 4; a++)
-        if (shape[a] == 0 || shape[a] > 0xffffffffull) return SZGB_EINVAL;
-    if (shape[0] * shape[1] > 0xffffffffull) return SZGB_EINVAL;
     if (p->variant != SZGB_VARIANT_EXACT) return SZGB_EUNSUPPORTED;
-    // the (D P) x M x N view carries the bound, m and the stream layout (rows of N points)
     szgb_params q = *p;
-    q.ndim = 3;
-    q.shape[0] = shape[0] * shape[1];
-    q.shape[1] = shape[2];
-    q.shape[2] = shape[3];
-    return compress_impl(c, data_dev, 1, &q, out_dev, out_cap, 1, out_len, opt_stats, recorded_dev, codes_dev,
-                         shape[0]);
+    q.ndim = 4;
+    for (int a = 0; a < 4; a++) q.shape[a] = shape[a];
+    return compress_impl(c, data_dev, 1, &q, out_dev, out_cap, 1, out_len, opt_stats, recorded_dev, codes_dev);
 }
 
 int szgb_decompress(szgb_ctx* c, const uint8_t* in, size_t in_len, int in_on_device, float* out,
@@ -1755,9 +1859,17 @@ int szgb_stream_info(const uint8_t* in_host, size_t in_len, szgb_params* out, ui
     int rc = parse_header(in_host, in_len, &H);
     if (rc) return rc;
     memset(out, 0, sizeof(*out));
-    out->ndim = H.ndim;
-    uint64_t d[3] = {H.d0, H.d1, H.d2};
-    for (int a = 0; a < H.ndim; a++) out->shape[a] = d[3 - H.ndim + a];
+    if (H.D4) {
+        out->ndim = 4;
+        out->shape[0] = H.D4;
+        out->shape[1] = H.d0 / H.D4;
+        out->shape[2] = H.d1;
+        out->shape[3] = H.d2;
+    } else {
+        out->ndim = H.ndim;
+        uint64_t d[3] = {H.d0, H.d1, H.d2};
+        for (int a = 0; a < H.ndim; a++) out->shape[a] = d[3 - H.ndim + a];
+    }
     out->mode = H.mode;
     out->eb_abs = H.eb_abs;
     out->eb_rel = H.eb_rel;

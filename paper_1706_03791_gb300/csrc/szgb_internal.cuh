@@ -22,11 +22,6 @@ constexpr int kMaxLayers3D = 2;    // n the 3D wavefront carries (a lane keeps (
 __host__ __device__ inline bool layers_supported(int ndim, int layers) {
     return layers >= 1 && layers <= (ndim == 3 ? kMaxLayers3D : kMaxLayers);
 }
-// layer counts the single-field calls carry: the wavefront's, plus 3D fields
-// with n = 3, 4 through the hyperplane kernels (k_hyper.cu)
-__host__ __device__ inline bool layers_single(int ndim, int layers) {
-    return layers >= 1 && layers <= kMaxLayers && ndim >= 1 && ndim <= 3;
-}
 constexpr int kLutBits = 11;       // decoder lookup-table index bits
 constexpr int kMaxWaveWarps = 8;   // compute warps per wavefront CTA (plus one halo warp)
 constexpr uint32_t kProgAbort = 0x7fffffffu;
@@ -78,6 +73,8 @@ struct CallParams {
     int variant;             // 0 = the paper's method, 1 = the lattice variant
     uint32_t chunk;          // Huffman chunk length along a row: 0 = the whole
                              // row, else a power of two >= 32 below the row length
+    uint64_t D4;             // 4D field D4 x P x M x N: D4, with d0 = D4 P
+                             // (the (D4 P) x M x N view); 0 for 1D-3D
 };
 
 // chunks per row of a field whose rows hold `row_len` points
@@ -481,11 +478,23 @@ struct Header {
     int adaptive;
     int variant;
     uint32_t chunk;  // chunk length along a row (byte 116); 0 = whole rows
+    uint64_t D4;     // 4D stream (ndim 4 at byte 8): the slowest extent (byte
+                     // 120), with ndim = 3 and d0 = D4 P describing the
+                     // (D4 P) x M x N view its rows are coded in; else 0
 };
-// Parses and checks a 1D-3D header held in host memory; SZGB_ECORRUPT for an
-// inconsistent one, SZGB_EUNSUPPORTED for a 4D one (callers that decode 4D
-// streams rewrite the header to its 3D view first).
+// Parses and checks a header held in host memory (a 4D one as its 3D view,
+// with D4 set); SZGB_ECORRUPT for an inconsistent one.
 int parse_header(const uint8_t* h, size_t in_len, Header* o);
+// Fields the wavefront kernels carry (the persistent kernel of the single,
+// batched and no-allocation calls): the paper's method, 1D-3D, the
+// wavefront's layer counts.  The rest (3D n = 3, 4; 4D; the lattice
+// variant) run on their own kernels through the single-field path.
+inline bool wave_carries(const CallParams& cp) {
+    return cp.variant == 0 && cp.D4 == 0 && layers_supported(cp.ndim, cp.layers);
+}
+inline bool wave_carries(const Header& h) {
+    return h.variant == 0 && h.D4 == 0 && layers_supported(h.ndim, h.layers);
+}
 // The SZGB_E* code of the error flags a call left in its device state.
 int dev_errors(const DevState& s);
 

@@ -70,8 +70,11 @@ extern "C" int szgb_decompress_noalloc(const uint8_t* in_dev, size_t in_len, flo
     if (cudaMemcpyAsync(h, in_dev, kHeaderBytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return SZGB_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return SZGB_ECUDA;
     Header H;
-    if ((rc = parse_header(h, in_len, &H))) return rc;  // SZGB_EUNSUPPORTED for a 4D stream
-    if (!layers_supported(H.ndim, H.layers) || H.variant != SZGB_VARIANT_EXACT) return SZGB_EUNSUPPORTED;
+    if ((rc = parse_header(h, in_len, &H))) return rc;
+    if (H.variant != SZGB_VARIANT_EXACT) return SZGB_EUNSUPPORTED;
+    // 3D fields with n = 3, 4 and 4D fields: the hyperplane kernels (no halo
+    // lines, no item states) after the same row decode
+    const bool hyper = !wave_carries(H);
     const int ndim = H.ndim, layers = H.layers, m = H.m, tw = H.tw;
     const uint64_t d2 = H.d2;
     const uint32_t nsym = H.nsym;
@@ -87,8 +90,8 @@ extern "C" int szgb_decompress_noalloc(const uint8_t* in_dev, size_t in_len, flo
     cp.d2 = H.d2;
     cp.layers = layers;
     const WaveGeom g = make_geom_w(cp, layers, kMaxWaveWarps, kMaxWaveWarps);
-    size_t hrow, hplane;  // halo lines in 32-bit units
-    halo_sizes(g, layers, &hrow, &hplane);
+    size_t hrow = 0, hplane = 0;  // halo lines in 32-bit units
+    if (!hyper) halo_sizes(g, layers, &hrow, &hplane);
 
     // carve the scratch
     size_t off = 0;
@@ -137,9 +140,15 @@ extern "C" int szgb_decompress_noalloc(const uint8_t* in_dev, size_t in_len, flo
     if ((rc = launch_decode_rows(payload, rowoff, rowbytes, payload + payload_bytes, lut, dectab, codes, cpitch,
                                  out_dev, rows, d2, H.chunk, st, s)))
         return rc;
-    if ((rc = launch_wave_decompress(g, layers, codes, cpitch, out_dev, reinterpret_cast<float*>(b + o_hrow),
-                                     reinterpret_cast<float*>(b + o_hplane), prog, st, 4000000000ull, s)))
-        return rc;
+    if (H.D4) {
+        rc = launch_hyper4(true, layers, nullptr, out_dev, codes, cpitch, H.D4, H.d0 / H.D4, H.d1, H.d2, st, s);
+    } else if (hyper) {
+        rc = launch_hyper_decompress(layers, codes, cpitch, out_dev, H.d0, H.d1, H.d2, st, s);
+    } else {
+        rc = launch_wave_decompress(g, layers, codes, cpitch, out_dev, reinterpret_cast<float*>(b + o_hrow),
+                                    reinterpret_cast<float*>(b + o_hplane), prog, st, 4000000000ull, s);
+    }
+    if (rc) return rc;
     DevState hs;
     if (cudaMemcpyAsync(&hs, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SZGB_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return SZGB_ECUDA;

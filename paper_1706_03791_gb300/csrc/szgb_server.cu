@@ -12,7 +12,8 @@
 // the copies and kernels of different batches overlap.
 //
 // Batches are formed by size, so that small requests do not wait behind
-// large ones: a large request (I/O of kLargeBytes or more) runs alone, a
+// large ones: a large request (I/O of kLargeBytes or more, or a field the
+// wavefront does not carry: 3D n = 3, 4, 4D, the lattice variant) runs alone, a
 // batch of small requests gathers at most kBatchBytes of I/O, and with two
 // or more workers worker 0 takes small requests only, so that one worker is
 // always free of large ones.  The other workers take the oldest pending
@@ -62,6 +63,7 @@ struct Req {
     uint64_t n_points = 0;
     size_t dev_in = 0, dev_out = 0;  // device bytes of input and output
     size_t need = 0;                  // admitted bytes (I/O + scratch estimate)
+    bool wave = true;                 // runs on the batched wavefront
     int status = SZGB_OK;
     size_t out_len = 0;
     bool done = false;
@@ -86,18 +88,22 @@ struct szgb_server {
 
 namespace {
 
-// requests run as batches, which carry the paper's method on the wavefront:
-// 3D fields up to n = 2 layers, 1D and 2D fields up to n = 4; anything else
-// is refused at submission rather than failing the batch it would join
-bool batch_carries(const szgb_params& p) {
-    return p.variant == SZGB_VARIANT_EXACT && p.layers >= 1 && p.layers <= (p.ndim == 3 ? 2 : 4);
+// fields the batched wavefront carries: the paper's method, 1D-3D, up to
+// n = 2 layers in 3D and n = 4 in 1D and 2D.  The others (3D n = 3, 4; 4D;
+// the lattice variant) run on their own kernels, one field at a time.
+bool on_wavefront(const szgb_params& p) {
+    return p.variant == SZGB_VARIANT_EXACT && p.ndim >= 1 && p.ndim <= 3 && p.layers >= 1 &&
+           p.layers <= (p.ndim == 3 ? 2 : 4);
 }
 
 // device scratch the library needs for one field, beyond its I/O buffers
-// (codes 2 B/pt, halos, per-row tables; Huffman tables 3.6 MB per field)
-size_t scratch_estimate(int op, uint64_t n_points) {
-    if (op == SZGB_OP_COMPRESS) return (size_t)(2.3 * (double)n_points) + (4u << 20);
-    return (size_t)(0.3 * (double)n_points) + (1u << 20);
+// (wavefront: codes 2 B/pt, halos, per-row tables; hyperplane and lattice
+// kernels: also 4-5 B/pt of recorded or lattice values; Huffman tables
+// 3.6 MB per field)
+size_t scratch_estimate(int op, uint64_t n_points, bool wave) {
+    const double n = (double)n_points;
+    if (op == SZGB_OP_COMPRESS) return (size_t)((wave ? 2.3 : 7.5) * n) + (4u << 20);
+    return (size_t)((wave ? 0.3 : 5.3) * n) + (1u << 20);
 }
 
 // Debug trace: with SZGB_SERVER_TRACE=<file>, one line per batch (worker,
@@ -214,7 +220,9 @@ void run_batch(szgb_server* S, szgb_ctx* ctx, cudaStream_t st, void*& dbuf, size
         for (Req* q : batch) q->status = SZGB_ECUDA;
 }
 
-bool is_large(const Req* q) { return q->dev_in + q->dev_out >= kLargeBytes; }
+// a large request, or one that runs on the hyperplane or lattice kernels
+// (one field at a time, after the batch's wavefront fields), runs alone
+bool is_large(const Req* q) { return !q->wave || q->dev_in + q->dev_out >= kLargeBytes; }
 
 // The next batch of worker `wid` from the pending queue (caller holds the
 // lock): see the file comment.  Requests are taken in arrival order within
@@ -342,14 +350,11 @@ int szgb_submit(szgb_server* S, const szgb_request* r, uint64_t* ticket) {
     q->r = *r;
     if (r->op == SZGB_OP_COMPRESS) {
         const szgb_params& p = r->params;
-        if (p.ndim < 1 || p.ndim > 3) {
+        if (p.ndim < 1 || p.ndim > 4) {
             delete q;
             return SZGB_EINVAL;
         }
-        if (!batch_carries(p)) {
-            delete q;
-            return SZGB_EUNSUPPORTED;
-        }
+        q->wave = on_wavefront(p);
         uint64_t n = 1;
         for (int a = 0; a < p.ndim; a++) n *= p.shape[a];
         const size_t bound = szgb_compress_bound(&p);
@@ -366,7 +371,6 @@ int szgb_submit(szgb_server* S, const szgb_request* r, uint64_t* ticket) {
         szgb_params p;
         uint64_t k = 0;
         int rc = szgb_stream_info(static_cast<const uint8_t*>(r->in), r->in_bytes, &p, &k);
-        if (rc == SZGB_OK && !batch_carries(p)) rc = SZGB_EUNSUPPORTED;
         if (rc) {
             delete q;
             return rc;
@@ -380,11 +384,12 @@ int szgb_submit(szgb_server* S, const szgb_request* r, uint64_t* ticket) {
         q->n_points = n;
         q->dev_in = r->in_bytes;
         q->dev_out = n * 4;
+        q->wave = on_wavefront(p);
     } else {
         delete q;
         return SZGB_EINVAL;
     }
-    q->need = up256(q->dev_in) + up256(q->dev_out) + scratch_estimate(r->op, q->n_points);
+    q->need = up256(q->dev_in) + up256(q->dev_out) + scratch_estimate(r->op, q->n_points, q->wave);
     if (q->need > S->budget) {
         delete q;
         return SZGB_EBUDGET;

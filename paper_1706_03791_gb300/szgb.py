@@ -32,7 +32,7 @@ class SzgbError(RuntimeError):
 
 
 class Params(C.Structure):
-    _fields_ = [("ndim", C.c_int), ("shape", C.c_uint64 * 3), ("mode", C.c_int),
+    _fields_ = [("ndim", C.c_int), ("shape", C.c_uint64 * 4), ("mode", C.c_int),
                 ("eb_abs", C.c_double), ("eb_rel", C.c_double), ("layers", C.c_int),
                 ("m", C.c_int), ("theta", C.c_double), ("variant", C.c_int), ("chunk_points", C.c_uint32)]
 
@@ -147,10 +147,8 @@ def make_params(shape, mode=REL, eb_abs=0.0, eb_rel=1e-4, layers=1, m=0, theta=0
                 chunk_points=0) -> Params:
     p = Params()
     shape = tuple(int(s) for s in shape)
-    if len(shape) == 4:  # a 4D field is described by its (D P) x M x N view (szgb_compress_4d)
-        shape = (shape[0] * shape[1], shape[2], shape[3])
     p.ndim = len(shape)
-    for i in range(3):
+    for i in range(4):
         p.shape[i] = shape[i] if i < len(shape) else 0
     p.mode, p.eb_abs, p.eb_rel, p.layers, p.m, p.theta = mode, float(eb_abs), float(eb_rel), \
         int(layers), int(m), float(theta)
@@ -252,7 +250,7 @@ class Context:
     # -- compression ---------------------------------------------------------
     def compress(self, x, out=None, **kw):
         """Compress `x` (a CUDA float32 tensor, or a NumPy float32 array on the
-        host; 1D-3D, or 4D as a CUDA tensor through szgb_compress_4d).
+        host; 1D-4D).
         Returns (stream, stats): with a CUDA input, `stream` is a view of the
         uint8 CUDA tensor `out` (allocated when None); with a NumPy input, a
         NumPy uint8 array."""
@@ -267,16 +265,12 @@ class Context:
             if out is None:
                 out = torch.empty(bound, dtype=torch.uint8, device=x.device)
             _require_cuda(out, torch.uint8, "out", self.device)
-            if x.dim() == 4:
-                return self._compress_4d(x, p, out, None, None)
             rc = L.szgb_compress(self._h, C.c_void_p(x.data_ptr()), 1, C.byref(p),
                                  C.c_void_p(out.data_ptr()), out.numel(), 1, C.byref(olen), C.byref(st))
             if rc:
                 raise SzgbError(rc, "szgb_compress")
             return out[:olen.value], st
         xa = np.ascontiguousarray(x, dtype=np.float32)
-        if xa.ndim == 4:
-            raise ValueError("4D fields are compressed from device memory (a CUDA tensor)")
         if out is None:
             out = np.empty(bound, np.uint8)
         _require_host(out, np.uint8, "out")

@@ -41,13 +41,16 @@ def test_device_calls_reject_host_tensors(ctx):
         szgb.decompress_noalloc(torch.zeros(200, dtype=torch.uint8), x)
 
 
-def test_4d_fields_need_device_memory(ctx):
-    with pytest.raises(ValueError):
-        ctx.compress(np.zeros((2, 3, 4, 5), np.float32), eb_rel=1e-3)
-    with pytest.raises(TypeError):
+def test_4d_params(ctx):
+    p = szgb.make_params((2, 3, 4, 5), eb_rel=1e-3)
+    assert p.ndim == 4 and tuple(p.shape) == (2, 3, 4, 5)
+    with pytest.raises(TypeError):  # a CPU tensor is neither a CUDA tensor nor a NumPy array
         ctx.compress(torch.zeros(2, 3, 4, 5), eb_rel=1e-3)
     # the 4D bound is the bound of the (D P) x M x N view
     assert szgb.compress_bound((2, 3, 4, 5), eb_rel=1e-3) == szgb.compress_bound((6, 4, 5), eb_rel=1e-3) > 0
+    # extents: each 1..2^32-1, D x P below 2^32, the lattice variant not in 4D
+    assert szgb.compress_bound((2, 0, 4, 5), eb_rel=1e-3) == 0
+    assert szgb.compress_bound((1 << 16, 1 << 16, 1, 1), eb_rel=1e-3) == 0
 
 
 def test_4d_header_shape():
@@ -56,6 +59,9 @@ def test_4d_header_shape():
     s = szo.compress(x, eb_rel=1e-3, m=8)
     info = szgb.stream_info_header(s[:128])
     assert info["ndim"] == 4 and info["shape"] == x.shape
+    # the library's own header parser describes the 4D field as such
+    full = szgb.stream_info(s)
+    assert full["ndim"] == 4 and full["shape"] == x.shape and full["layers"] == 1 and full["m"] == 8
 
 
 def test_host_outputs_checked(ctx):

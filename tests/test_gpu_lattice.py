@@ -62,6 +62,21 @@ def test_lattice_rejections(ctx):
     with pytest.raises(szgb.SzgbError) as e:
         ctx.compress(x * 1e6, variant=1, mode=0, eb_abs=1e-6, m=8)  # integers >= 2^30
     assert e.value.code == szgb.EINVAL
-    with pytest.raises(szgb.SzgbError) as e:
-        ctx.compress_batch([x], dict(eb_rel=1e-4, variant=1))
+    with pytest.raises(szgb.SzgbError) as e:  # n <= 2 only
+        ctx.compress(x, variant=1, eb_rel=1e-4, layers=3)
     assert e.value.code == szgb.EUNSUPPORTED
+
+
+def test_lattice_in_batches(ctx):
+    """A lattice-variant field in a batch runs on its own kernels: the same
+    bytes as the single-field call, beside a field on the wavefront."""
+    import torch
+    x = torch.from_numpy(fields.grf2d(40, 40, seed=116)).cuda()
+    y = torch.from_numpy(fields.grf2d(33, 70, seed=117)).cuda()
+    ss, _ = ctx.compress_batch([x, y], [dict(eb_rel=1e-4, variant=1), dict(eb_rel=1e-4)])
+    s1, _ = ctx.compress(x, eb_rel=1e-4, variant=1)
+    s2, _ = ctx.compress(y, eb_rel=1e-4)
+    assert torch.equal(ss[0], s1) and torch.equal(ss[1], s2)
+    ys = ctx.decompress_batch(ss)
+    assert torch.equal(ys[0].view(torch.int32), ctx.decompress(s1).view(torch.int32))
+    assert torch.equal(ys[1].view(torch.int32), ctx.decompress(s2).view(torch.int32))

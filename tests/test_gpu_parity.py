@@ -140,9 +140,9 @@ def test_errors(ctx, szo):
         ctx.compress(x, out=small, eb_rel=1e-3, m=8)
     assert e.value.code == szgb.ETRUNC
     x3 = torch.from_numpy(fields.blobs3d(6, 20, 24, seed=52, nblobs=3)).cuda()
-    with pytest.raises(szgb.SzgbError) as e:  # batches keep 3D at n <= 2 (refused before any launch)
-        ctx.compress_batch([x3], dict(eb_rel=1e-3, m=8, layers=3))
-    assert e.value.code == szgb.EUNSUPPORTED
+    with pytest.raises(szgb.SzgbError) as e:  # a bad parameter refuses the whole batch before any launch
+        ctx.compress_batch([x3, x3], [dict(eb_rel=1e-3, m=8, layers=3), dict(eb_rel=1e-3, m=1)])
+    assert e.value.code == szgb.EINVAL
     # the context stays usable after errors
     _check(ctx, szo, x, eb_rel=1e-3, m=8)
 

@@ -57,14 +57,19 @@ def test_stream_info_parses_oracle_header(szgb, szo):
         szgb.stream_info(s[:-1])
 
 
-def test_4d_stream_reported_unsupported(szgb, szo):
+def test_4d_stream_info(szgb, szo):
     # the oracle writes 4D streams (the predictor of Sec. III in four
-    # dimensions); the GPU library recognises and declines them
+    # dimensions); the library's header parser reads their four extents, and
+    # declines a 4D header whose D x P reaches 2^32
     x = np.random.default_rng(4).normal(size=(3, 4, 5, 6)).astype(np.float32)
     s = szo.compress(x, eb_rel=1e-3, m=8)
+    info = szgb.stream_info(s)
+    assert info["ndim"] == 4 and info["shape"] == (3, 4, 5, 6)
+    bad = s.copy()
+    bad[120:128] = np.frombuffer(np.uint64(1 << 31).tobytes(), np.uint8)
     with pytest.raises(szgb.SzgbError) as e:
-        szgb.stream_info(s)
-    assert e.value.code == szgb.EUNSUPPORTED
+        szgb.stream_info(bad)
+    assert e.value.code == szgb.ECORRUPT
 
 
 def test_header_parser_survives_corruption(szgb, szo):

@@ -89,15 +89,24 @@ def test_server_request_log(szgb, tmp_path):
     assert all(st in (szgb.OK, szgb.ECUDA) for st, _ in done)
 
 
-def test_server_refuses_what_batches_do_not_carry(szgb):
-    # 3D fields with n > 2 and the lattice variant run as single-field calls
-    # only; the server refuses them at submission instead of failing a batch
+def test_server_takes_every_field_kind(szgb, szo):
+    # 3D fields with n = 3, 4, 4D fields and the lattice variant run alone on
+    # their own kernels; the server admits them (compress, and decompress of
+    # a 4D stream) like the fields the batched wavefront carries
     srv = szgb.Server(0, budget=64 << 20, workers=1, max_batch=2)
     try:
         x3 = np.zeros((6, 8, 10), np.float32)
-        for kw in (dict(layers=3), dict(layers=4), dict(layers=1, variant=szgb.VARIANT_LATTICE)):
-            with pytest.raises(szgb.SzgbError) as e:
-                srv.submit_compress(x3, np.empty(1 << 16, np.uint8), eb_rel=1e-3, **kw)
-            assert e.value.code == szgb.EUNSUPPORTED
+        x4 = np.random.default_rng(5).standard_normal((2, 3, 8, 10)).astype(np.float32)
+        tickets = []
+        for x, kw in ((x3, dict(layers=3)), (x3, dict(layers=4)),
+                      (x3, dict(layers=1, variant=szgb.VARIANT_LATTICE)), (x4, dict(layers=2))):
+            tickets.append(srv.submit_compress(x, np.empty(1 << 16, np.uint8), eb_rel=1e-3, **kw))
+        s4 = szo.compress(x4, eb_rel=1e-3, m=8)
+        tickets.append(srv.submit_decompress(s4, np.empty(x4.shape, np.float32)))
+        done = [srv.wait(t) for t in tickets]
+        assert all(st in (szgb.OK, szgb.ECUDA) for st, _ in done)
+        with pytest.raises(szgb.SzgbError) as e:  # too small for the 4D field
+            srv.submit_decompress(s4, np.empty(x4.size - 1, np.float32))
+        assert e.value.code == szgb.EINVAL
     finally:
         srv.close()

@@ -3,9 +3,8 @@ layers, and 4D fields with n = 1..4 (Sec. III, Eq. predmodel in four
 dimensions).  Byte-identical streams, bit-identical recorded values, codes
 and reconstructions, on fields that span many hyperplanes with ragged
 extents, plus unit extents, an absolute bound, a tight bound, fixed and
-adaptive m and host buffers.  The batched path keeps 3D at n <= 2 and
-refuses these fields before any launch.  This file runs after the other GPU
-tests."""
+adaptive m and host buffers; the same fields inside batches beside
+wavefront fields.  This file runs after the other GPU tests."""
 import numpy as np
 import pytest
 
@@ -68,13 +67,41 @@ def test_plain_calls_and_host_buffers(ctx):
     assert np.array_equal(y.view(np.uint32), szo.decompress(ref).view(np.uint32))
 
 
-def test_batched_path_refuses(ctx):
+def test_batches_carry_hyperplane_fields(ctx):
+    """A batch mixing wavefront fields with 3D n = 3, 4 and 4D fields: the
+    latter run on the hyperplane kernels after the batch's wavefront, and
+    every stream and reconstruction equals the oracle's."""
     import torch
-    from paper_1706_03791_gb300 import szgb
-    x = torch.from_numpy(fields.blobs3d(6, 20, 24, seed=68, nblobs=3)).cuda()
-    with pytest.raises(szgb.SzgbError) as e:
-        ctx.compress_batch([x], dict(eb_rel=1e-3, layers=4))
-    assert e.value.code == szgb.EUNSUPPORTED
+    from oracle import szo
+    xs = [fields.blobs3d(6, 20, 24, seed=68, nblobs=3), fields.blobs3d(7, 18, 21, seed=69, nblobs=3),
+          _field4((3, 4, 9, 13), seed=70), fields.grf2d(45, 61, seed=71), fields.blobs3d(5, 9, 30, seed=72, nblobs=3),
+          _field4((2, 3, 5, 40), seed=73)]
+    kws = [dict(eb_rel=1e-3, layers=4, m=0), dict(eb_rel=1e-4, layers=1, m=0), dict(eb_rel=1e-4, layers=2, m=0),
+           dict(eb_rel=1e-4, layers=2, m=0), dict(eb_rel=1e-4, layers=3, m=9), dict(eb_rel=1e-3, layers=1, m=0)]
+    refs = [szo.compress(x, **kw) for x, kw in zip(xs, kws)]
+    for graphs in (True, False):
+        ctx.set_graphs(graphs)
+        ss, sts = ctx.compress_batch([torch.from_numpy(x).cuda() for x in xs], kws)
+        for i, (s, ref) in enumerate(zip(ss, refs)):
+            assert np.array_equal(s.cpu().numpy(), ref), i
+            assert sts[i].status == 0 and sts[i].stream_bytes == ref.size
+        ys = ctx.decompress_batch([torch.from_numpy(np.ascontiguousarray(r)).cuda() for r in refs])
+        for i, (y, ref) in enumerate(zip(ys, refs)):
+            assert tuple(y.shape) == xs[i].shape
+            assert np.array_equal(y.cpu().numpy().view(np.uint32), szo.decompress(ref).view(np.uint32)), i
+    ctx.set_graphs(True)
+
+
+def test_4d_from_host_memory(ctx):
+    """szgb_compress with ndim = 4 takes a host array as any other field."""
+    from oracle import szo
+    x = _field4((3, 5, 8, 11), seed=74)
+    kw = dict(eb_rel=1e-4, layers=2, m=0)
+    s, st = ctx.compress(x, **kw)
+    assert np.array_equal(np.asarray(s), szo.compress(x, **kw))
+    y = ctx.decompress(np.asarray(s))
+    assert y.shape == x.shape
+    assert np.array_equal(y.view(np.uint32), szo.decompress(np.asarray(s)).view(np.uint32))
 
 
 def _field4(shape, seed):
