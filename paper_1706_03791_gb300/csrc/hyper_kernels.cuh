@@ -1,6 +1,7 @@
-// hyper_kernels.cuh -- the hyperplane kernels' device code: 3D fields with
-// n = 3, 4 layers and 4D fields (Sec. III, Eq. predmodel), compression and
-// reconstruction one hyperplane per launch, and the 4D adaptive-m sample.
+// hyper_kernels.cuh -- device code shared by the hyperplane kernels of 3D
+// fields with n = 3, 4 layers and 4D fields (Sec. III, Eq. predmodel): the
+// 4D term coefficients and prediction, the 4D adaptive-m sample and the 4D
+// prediction hit (the tiled schedule itself is in hyper_tile.cuh).
 //
 // Included by k_hyper.cu after szgb_internal.cuh (which supplies DevState,
 // QParams, load_qparams, quantize_tr, dequantize, trunc_value, sgn_binom and
@@ -11,64 +12,6 @@
 #define SZGB_HYPER_KERNELS_CUH
 
 namespace szgb {
-
-constexpr int kHyperThreads = 256;
-
-// n-layer prediction of point (i, j, l) from V, terms in descending
-// lexicographic order of k, values outside the field 0.  V is written by
-// earlier launches, so it is read through L2 (no read-only cache).
-template <int NL>
-__device__ __forceinline__ float predict_hyper(const float* V, uint64_t M, uint64_t N, int64_t i, int64_t j,
-                                               int64_t l) {
-    float pred = 0.0f;
-    bool first = true;
-#pragma unroll
-    for (int k0 = NL; k0 >= 0; k0--) {
-#pragma unroll
-        for (int k1 = NL; k1 >= 0; k1--) {
-#pragma unroll
-            for (int k2 = NL; k2 >= 0; k2--) {
-                if (k0 == 0 && k1 == 0 && k2 == 0) continue;
-                const int64_t ii = i - k0, jj = j - k1, ll = l - k2;
-                float v = 0.0f;
-                if (ii >= 0 && jj >= 0 && ll >= 0) v = __ldcg(V + ((uint64_t)ii * M + (uint64_t)jj) * N + (uint64_t)ll);
-                const float prod = __fmul_rn((float)term_coef(NL, k0, k1, k2), v);
-                pred = first ? prod : __fadd_rn(pred, prod);
-                first = false;
-            }
-        }
-    }
-    return pred;
-}
-
-// One hyperplane.  DEC = false: x -> codes and recorded values V.
-// DEC = true: codes (and, at code 0, the unpredictable value already in V,
-// as the row decoder leaves it) -> reconstructed V.
-template <int NL, bool DEC>
-__global__ void __launch_bounds__(kHyperThreads) k_hyper(const float* __restrict__ x, float* V, uint16_t* codes,
-                                                         uint64_t cpitch, uint64_t M, uint64_t N, int64_t h,
-                                                         HyperBox b, const DevState* st) {
-    if (st->err) return;
-    const uint64_t t = blockIdx.x * (uint64_t)kHyperThreads + threadIdx.x;
-    if (t >= b.ni * b.nj) return;
-    const int64_t i = b.ilo + (int64_t)(t / b.nj), j = b.jlo + (int64_t)(t % b.nj), l = h - i - j;
-    if (l < 0 || (uint64_t)l >= N) return;
-    const QParams qp = load_qparams(st);
-    const uint64_t row = (uint64_t)i * M + (uint64_t)j;
-    const uint64_t p = row * N + (uint64_t)l;
-    const float pred = predict_hyper<NL>(V, M, N, i, j, l);
-    if (DEC) {
-        const int code = codes[row * cpitch + (uint64_t)l];
-        if (code) V[p] = dequantize(code, pred, qp);
-    } else {
-        const float xv = x[p];
-        float rec;
-        const int code = quantize_tr(xv, pred, trunc_value(xv, qp.e_eb), qp, rec);  // as the wavefront
-        V[p] = rec;
-        codes[row * cpitch + (uint64_t)l] = (uint16_t)code;
-    }
-}
-
 
 // ---------------------------------------------------------------------------
 // 4D fields D x P x M x N (the predictor of Eq. predmodel with d = 4): the same
@@ -116,34 +59,6 @@ __device__ __forceinline__ float predict4(const float* V, const Dims4& d, int64_
     }
     return pred;
 }
-
-template <int NL, bool DEC>
-__global__ void __launch_bounds__(kHyperThreads) k_hyper4(const float* __restrict__ x, float* V, uint16_t* codes,
-                                                          uint64_t cpitch, Dims4 d, int64_t h, HyperBox4 b,
-                                                          const DevState* st) {
-    if (st->err) return;
-    const uint64_t t = blockIdx.x * (uint64_t)kHyperThreads + threadIdx.x;
-    const uint64_t plane = b.ni * b.nj;
-    if (t >= b.na * plane) return;
-    const int64_t a = b.alo + (int64_t)(t / plane), i = b.ilo + (int64_t)((t / b.nj) % b.ni),
-                  j = b.jlo + (int64_t)(t % b.nj), l = h - a - i - j;
-    if (l < 0 || (uint64_t)l >= d.N) return;
-    const QParams qp = load_qparams(st);
-    const uint64_t row = ((uint64_t)a * d.P + (uint64_t)i) * d.M + (uint64_t)j;
-    const uint64_t p = row * d.N + (uint64_t)l;
-    const float pred = predict4<NL, false>(V, d, a, i, j, l);
-    if (DEC) {
-        const int code = codes[row * cpitch + (uint64_t)l];
-        if (code) V[p] = dequantize(code, pred, qp);
-    } else {
-        const float xv = x[p];
-        float rec;
-        const int code = quantize_tr(xv, pred, trunc_value(xv, qp.e_eb), qp, rec);
-        V[p] = rec;
-        codes[row * cpitch + (uint64_t)l] = (uint16_t)code;
-    }
-}
-
 
 // One adaptive-m sample of a 4D field (sample index s over the points whose
 // coordinates are all multiples of 8): the smallest m whose radius holds its

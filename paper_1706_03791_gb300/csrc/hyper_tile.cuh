@@ -1,0 +1,224 @@
+// hyper_tile.cuh -- the hyperplane schedule for the predictors the wavefront
+// does not carry (3D fields with n = 3, 4 layers; 4D fields with n = 1..4;
+// Sec. III, Eq. predmodel), done tile by tile in shared memory.
+//
+// Every prediction term reaches back by a k != 0 with k >= 0 componentwise,
+// so a point depends only on points whose coordinate sum is smaller.  The
+// field is cut into tiles of TA x TI x TJ x TL points (3D: TI x TJ x TL);
+// tile (A, I, J, L) depends only on tiles whose index sum is smaller, so all
+// tiles with A + I + J + L = H run in one launch, in increasing H.  A tile's
+// CTA
+//   1. loads the box [lo - n, lo + T) of recorded values (zero outside the
+//      field; the part below lo was written by earlier launches) and its own
+//      input (compression: x; reconstruction: the codes and, at code 0, the
+//      unpredictable values the row decoder left in the output),
+//   2. walks its own hyperplanes a + i + j + l = s (tile-local coordinates),
+//      one thread per tile row (a, i, j), one __syncthreads per step: the
+//      prediction reads only shared memory,
+//   3. stores its points' recorded values (and codes) with coalesced rows.
+// The arithmetic is the wavefront's and the oracle's: the same term order
+// (descending lexicographic k), every product and sum rounded once, the
+// same quantizer and truncation; values outside the field are 0.
+//
+// The three phases are separate functions so that the host-side emulation
+// test can run them thread by thread (within a step no thread reads a point
+// another thread writes in that step: such points have equal coordinate
+// sums, never a neighbour's).
+#ifndef SZGB_HYPER_TILE_CUH
+#define SZGB_HYPER_TILE_CUH
+
+namespace szgb {
+
+template <int DIM, int NL>
+struct TileGeom {
+    // tile extents: 3D 8 x 16 x 32; 4D 4 x 4 x 8 x 32 (2 x 4 x 8 x 32 for n >= 3,
+    // whose halo is wider)
+    static constexpr int TA = DIM == 4 ? (NL <= 2 ? 4 : 2) : 1;
+    static constexpr int TI = DIM == 4 ? 4 : 8;
+    static constexpr int TJ = DIM == 4 ? 8 : 16;
+    static constexpr int TL = 32;
+    static constexpr int HA = DIM == 4 ? NL : 0;  // halo planes along the 4th axis (3D: none)
+    static constexpr int BA = TA + HA, BI = TI + NL, BJ = TJ + NL;
+    // even row length: lanes on consecutive rows, whose columns differ by
+    // one, land BL - 1 words apart, an odd stride (distinct banks)
+    static constexpr int BL = (TL + NL + 1) & ~1;
+    static constexpr int VBOX = BA * BI * BJ * BL;  // recorded values (floats)
+    static constexpr int XBOX = TA * TI * TJ * TL;  // own points: x (floats) and codes (u16)
+    static constexpr int THREADS = TA * TI * TJ;    // one thread per tile row
+    static constexpr int STEPS = TA + TI + TJ + TL - 3;
+    static constexpr size_t smem_bytes(bool dec) {
+        return (size_t)VBOX * 4 + (dec ? 0 : (size_t)XBOX * 4) + (size_t)XBOX * 2;
+    }
+};
+
+// one tile of one launch: its extents, arrays and first point
+struct TileCtx {
+    const float* x;
+    float* V;
+    uint16_t* codes;
+    uint64_t cpitch;
+    Dims4 d;                 // field extents D x P x M x N (3D: D = 1)
+    int64_t a0, i0, j0, l0;  // the tile's first point
+};
+
+// Tile of block `blk` on tile diagonal H: box b over the tile grid (its
+// (A, I, J) triples), nL tiles along the rows.  False when the block's L is
+// outside the grid (the box is a superset).
+template <int DIM, int NL>
+__host__ __device__ __forceinline__ bool tile_at(const HyperBox4& b, int64_t H, int64_t nL, uint64_t blk,
+                                                 TileCtx* t) {
+    using G = TileGeom<DIM, NL>;
+    const uint64_t plane = b.ni * b.nj;
+    const int64_t A = b.alo + (int64_t)(blk / plane), I = b.ilo + (int64_t)((blk / b.nj) % b.ni),
+                  J = b.jlo + (int64_t)(blk % b.nj), L = H - A - I - J;
+    if (L < 0 || L >= nL) return false;
+    t->a0 = A * G::TA;
+    t->i0 = I * G::TI;
+    t->j0 = J * G::TJ;
+    t->l0 = L * G::TL;
+    return true;
+}
+
+__host__ __device__ __forceinline__ uint64_t field_index(const Dims4& d, int64_t a, int64_t i, int64_t j, int64_t l) {
+    return (((uint64_t)a * d.P + (uint64_t)i) * d.M + (uint64_t)j) * d.N + (uint64_t)l;
+}
+
+__host__ __device__ __forceinline__ uint64_t code_index(const Dims4& d, uint64_t cpitch, int64_t a, int64_t i,
+                                                        int64_t j, int64_t l) {
+    return (((uint64_t)a * d.P + (uint64_t)i) * d.M + (uint64_t)j) * cpitch + (uint64_t)l;
+}
+
+// Phase 1 for thread tid: the box of recorded values (compression skips the
+// tile's own points, which it computes; reconstruction keeps them, since the
+// unpredictable values are already there), and the tile's x or codes.
+template <int DIM, int NL, bool DEC>
+__device__ __forceinline__ void tile_load(const TileCtx& t, float* Vs, float* Xs, uint16_t* Cs, int tid) {
+    using G = TileGeom<DIM, NL>;
+    for (int e = tid; e < G::VBOX; e += G::THREADS) {
+        int r = e;
+        const int bl = r % G::BL;
+        r /= G::BL;
+        const int bj = r % G::BJ;
+        r /= G::BJ;
+        const int bi = r % G::BI;
+        const int ba = r / G::BI;
+        const int64_t a = t.a0 + ba - G::HA, i = t.i0 + bi - NL, j = t.j0 + bj - NL, l = t.l0 + bl - NL;
+        float v = 0.0f;
+        const bool inside = bl < G::TL + NL && a >= 0 && i >= 0 && j >= 0 && l >= 0 && (uint64_t)a < t.d.D &&
+                            (uint64_t)i < t.d.P && (uint64_t)j < t.d.M && (uint64_t)l < t.d.N;
+        const bool own = a >= t.a0 && i >= t.i0 && j >= t.j0 && l >= t.l0;
+        if (inside && (DEC || !own)) v = __ldcg(t.V + field_index(t.d, a, i, j, l));
+        Vs[e] = v;
+    }
+    for (int e = tid; e < G::XBOX; e += G::THREADS) {
+        int r = e;
+        const int tl = r % G::TL;
+        r /= G::TL;
+        const int tj = r % G::TJ;
+        r /= G::TJ;
+        const int ti = r % G::TI;
+        const int ta = r / G::TI;
+        const int64_t a = t.a0 + ta, i = t.i0 + ti, j = t.j0 + tj, l = t.l0 + tl;
+        const bool inside = (uint64_t)a < t.d.D && (uint64_t)i < t.d.P && (uint64_t)j < t.d.M && (uint64_t)l < t.d.N;
+        if (DEC) {
+            Cs[e] = inside ? t.codes[code_index(t.d, t.cpitch, a, i, j, l)] : (uint16_t)0;
+        } else {
+            Xs[e] = inside ? __ldg(t.x + field_index(t.d, a, i, j, l)) : 0.0f;
+        }
+    }
+}
+
+// n-layer prediction of the point at box index ve from the box of recorded
+// values: terms in descending lexicographic order of k.
+template <int DIM, int NL>
+__device__ __forceinline__ float predict_tile(const float* Vs, int ve) {
+    using G = TileGeom<DIM, NL>;
+    float pred = 0.0f;
+    bool first = true;
+    if constexpr (DIM == 3) {
+#pragma unroll
+        for (int k0 = NL; k0 >= 0; k0--) {
+#pragma unroll
+            for (int k1 = NL; k1 >= 0; k1--) {
+#pragma unroll
+                for (int k2 = NL; k2 >= 0; k2--) {
+                    if (k0 == 0 && k1 == 0 && k2 == 0) continue;
+                    const float v = Vs[ve - (k0 * G::BJ + k1) * G::BL - k2];
+                    const float prod = __fmul_rn((float)term_coef(NL, k0, k1, k2), v);
+                    pred = first ? prod : __fadd_rn(pred, prod);
+                    first = false;
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k0 = NL; k0 >= 0; k0--) {
+#pragma unroll
+            for (int k1 = NL; k1 >= 0; k1--) {
+#pragma unroll
+                for (int k2 = NL; k2 >= 0; k2--) {
+#pragma unroll
+                    for (int k3 = NL; k3 >= 0; k3--) {
+                        if (k0 == 0 && k1 == 0 && k2 == 0 && k3 == 0) continue;
+                        const float v = Vs[ve - ((k0 * G::BI + k1) * G::BJ + k2) * G::BL - k3];
+                        const float prod = __fmul_rn((float)term_coef4(NL, k0, k1, k2, k3), v);
+                        pred = first ? prod : __fadd_rn(pred, prod);
+                        first = false;
+                    }
+                }
+            }
+        }
+    }
+    return pred;
+}
+
+// Phase 2, step s, thread tid: the point of its row on tile hyperplane s.
+template <int DIM, int NL, bool DEC>
+__device__ __forceinline__ void tile_step(const TileCtx& t, float* Vs, const float* Xs, uint16_t* Cs, int tid, int s,
+                                          const QParams& qp) {
+    using G = TileGeom<DIM, NL>;
+    const int tj = tid % G::TJ, ti = (tid / G::TJ) % G::TI, ta = tid / (G::TJ * G::TI);
+    const int tl = s - ta - ti - tj;
+    if (tid >= G::THREADS || tl < 0 || tl >= G::TL) return;
+    if ((uint64_t)(t.a0 + ta) >= t.d.D || (uint64_t)(t.i0 + ti) >= t.d.P || (uint64_t)(t.j0 + tj) >= t.d.M ||
+        (uint64_t)(t.l0 + tl) >= t.d.N)
+        return;
+    const int ve = (((ta + G::HA) * G::BI + ti + NL) * G::BJ + tj + NL) * G::BL + tl + NL;
+    const int xe = ((ta * G::TI + ti) * G::TJ + tj) * G::TL + tl;
+    const float pred = predict_tile<DIM, NL>(Vs, ve);
+    if (DEC) {
+        const int code = Cs[xe];
+        if (code) Vs[ve] = dequantize(code, pred, qp);
+    } else {
+        const float xv = Xs[xe];
+        float rec;
+        const int code = quantize_tr(xv, pred, trunc_value(xv, qp.e_eb), qp, rec);
+        Vs[ve] = rec;
+        Cs[xe] = (uint16_t)code;
+    }
+}
+
+// Phase 3 for thread tid: the tile's recorded values (and codes) to global
+// memory, rows of TL points.
+template <int DIM, int NL, bool DEC>
+__device__ __forceinline__ void tile_store(const TileCtx& t, const float* Vs, const uint16_t* Cs, int tid) {
+    using G = TileGeom<DIM, NL>;
+    for (int e = tid; e < G::XBOX; e += G::THREADS) {
+        int r = e;
+        const int tl = r % G::TL;
+        r /= G::TL;
+        const int tj = r % G::TJ;
+        r /= G::TJ;
+        const int ti = r % G::TI;
+        const int ta = r / G::TI;
+        const int64_t a = t.a0 + ta, i = t.i0 + ti, j = t.j0 + tj, l = t.l0 + tl;
+        if ((uint64_t)a >= t.d.D || (uint64_t)i >= t.d.P || (uint64_t)j >= t.d.M || (uint64_t)l >= t.d.N) continue;
+        const int ve = (((ta + G::HA) * G::BI + ti + NL) * G::BJ + tj + NL) * G::BL + tl + NL;
+        t.V[field_index(t.d, a, i, j, l)] = Vs[ve];
+        if (!DEC) t.codes[code_index(t.d, t.cpitch, a, i, j, l)] = Cs[e];
+    }
+}
+
+}  // namespace szgb
+
+#endif

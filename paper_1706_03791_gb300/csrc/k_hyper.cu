@@ -1,33 +1,62 @@
 // k_hyper.cu -- 3D fields with n = 3 or 4 layers, and 4D fields (Sec. III,
 // Eq. predmodel): the prediction, quantization, fallback and record of
-// Algorithm 1, and the matching reconstruction, one hyperplane per launch.
-// The kernels' device code is in hyper_kernels.cuh; this file launches them.
+// Algorithm 1, and the matching reconstruction, on the tiled hyperplane
+// schedule of hyper_tile.cuh (one launch per diagonal of tiles).
 //
 // A 3D wavefront lane would keep (n+1)^3 - 1 neighbour values in registers
 // (63 at n = 3, 124 at n = 4), which does not fit beside the wavefront's
-// helper warps.  Here every neighbour comes from the recorded values in
-// global memory (L2-resident for the planes in flight) instead.  A point's
-// neighbours all lie on earlier hyperplanes, so one launch per hyperplane on
-// one stream is the whole schedule: a launch boundary orders the hyperplanes,
-// and there is no device-side wait of any kind.  The arithmetic is the
-// wavefront's: the same term order, products and sums rounded one at a time,
-// the same quantizer and truncation.
+// helper warps.  Here a tile's CTA stages the tile with its halo of recorded
+// values in shared memory and walks the tile's own hyperplanes there; a
+// launch boundary orders the diagonals of tiles, and there is no device-side
+// wait of any kind.  The arithmetic is the wavefront's: the same term order,
+// products and sums rounded one at a time, the same quantizer and
+// truncation.
 #include "szgb_internal.cuh"
 #include "hyper_box.h"
 #include "hyper_kernels.cuh"
+#include "hyper_tile.cuh"
 
 namespace szgb {
 
-template <int NL, bool DEC>
-static int run_hyper(const float* x, float* V, uint16_t* codes, uint64_t cpitch, uint64_t P, uint64_t M, uint64_t N,
-                     const DevState* st, cudaStream_t s) {
-    const int64_t H = (int64_t)(P - 1) + (int64_t)(M - 1) + (int64_t)(N - 1);
-    for (int64_t h = 0; h <= H; h++) {
-        const HyperBox b = hyper_box(h, (int64_t)P, (int64_t)M, (int64_t)N);
-        const uint64_t n = b.ni * b.nj;
+template <int DIM, int NL, bool DEC>
+__global__ void __launch_bounds__(TileGeom<DIM, NL>::THREADS)
+    k_hyper_tile(const float* __restrict__ x, float* V, uint16_t* codes, uint64_t cpitch, Dims4 d, int64_t H,
+                 HyperBox4 b, int64_t nL, const DevState* st) {
+    using G = TileGeom<DIM, NL>;
+    if (st->err) return;
+    extern __shared__ __align__(16) unsigned char tile_smem[];
+    float* Vs = reinterpret_cast<float*>(tile_smem);
+    float* Xs = Vs + G::VBOX;
+    uint16_t* Cs = reinterpret_cast<uint16_t*>(DEC ? Xs : Xs + G::XBOX);
+    TileCtx t = {x, V, codes, cpitch, d, 0, 0, 0, 0};
+    if (!tile_at<DIM, NL>(b, H, nL, blockIdx.x, &t)) return;  // the whole block
+    const int tid = threadIdx.x;
+    tile_load<DIM, NL, DEC>(t, Vs, Xs, Cs, tid);
+    const QParams qp = load_qparams(st);
+    __syncthreads();
+    for (int s = 0; s < G::STEPS; s++) {
+        tile_step<DIM, NL, DEC>(t, Vs, Xs, Cs, tid, s, qp);
+        __syncthreads();
+    }
+    tile_store<DIM, NL, DEC>(t, Vs, Cs, tid);
+}
+
+// every diagonal of tiles of a D x P x M x N field (3D: D = 1), in order
+template <int DIM, int NL, bool DEC>
+static int run_tiles(const float* x, float* V, uint16_t* codes, uint64_t cpitch, const Dims4& d, const DevState* st,
+                     cudaStream_t s) {
+    using G = TileGeom<DIM, NL>;
+    const size_t smem = G::smem_bytes(DEC);
+    if (cudaFuncSetAttribute(k_hyper_tile<DIM, NL, DEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return SZGB_ECUDA;
+    const int64_t nA = (int64_t)((d.D + G::TA - 1) / G::TA), nI = (int64_t)((d.P + G::TI - 1) / G::TI),
+                  nJ = (int64_t)((d.M + G::TJ - 1) / G::TJ), nL = (int64_t)((d.N + G::TL - 1) / G::TL);
+    for (int64_t H = 0; H <= (nA - 1) + (nI - 1) + (nJ - 1) + (nL - 1); H++) {
+        const HyperBox4 b = hyper_box4(H, nA, nI, nJ, nL);
+        const uint64_t n = b.na * b.ni * b.nj;
         if (n == 0) continue;
-        const unsigned blocks = (unsigned)((n + kHyperThreads - 1) / kHyperThreads);
-        k_hyper<NL, DEC><<<blocks, kHyperThreads, 0, s>>>(x, V, codes, cpitch, M, N, h, b, st);
+        k_hyper_tile<DIM, NL, DEC><<<(unsigned)n, G::THREADS, smem, s>>>(x, V, codes, cpitch, d, H, b, nL, st);
         if (cudaGetLastError() != cudaSuccess) return SZGB_ECUDA;
     }
     return SZGB_OK;
@@ -38,8 +67,9 @@ static int run_hyper(const float* x, float* V, uint16_t* codes, uint64_t cpitch,
 // holds the bound and m (range and adaptive-m kernels run before).
 int launch_hyper_compress(int layers, const float* x, float* V, uint16_t* codes, uint64_t cpitch, uint64_t P,
                           uint64_t M, uint64_t N, const DevState* st, cudaStream_t s) {
-    if (layers == 3) return run_hyper<3, false>(x, V, codes, cpitch, P, M, N, st, s);
-    if (layers == 4) return run_hyper<4, false>(x, V, codes, cpitch, P, M, N, st, s);
+    const Dims4 d = {1, P, M, N};
+    if (layers == 3) return run_tiles<3, 3, false>(x, V, codes, cpitch, d, st, s);
+    if (layers == 4) return run_tiles<3, 4, false>(x, V, codes, cpitch, d, st, s);
     return SZGB_EUNSUPPORTED;
 }
 
@@ -47,38 +77,24 @@ int launch_hyper_compress(int layers, const float* x, float* V, uint16_t* codes,
 // out at their points; out is completed in place.
 int launch_hyper_decompress(int layers, uint16_t* codes, uint64_t cpitch, float* out, uint64_t P, uint64_t M,
                             uint64_t N, const DevState* st, cudaStream_t s) {
-    if (layers == 3) return run_hyper<3, true>(nullptr, out, codes, cpitch, P, M, N, st, s);
-    if (layers == 4) return run_hyper<4, true>(nullptr, out, codes, cpitch, P, M, N, st, s);
+    const Dims4 d = {1, P, M, N};
+    if (layers == 3) return run_tiles<3, 3, true>(nullptr, out, codes, cpitch, d, st, s);
+    if (layers == 4) return run_tiles<3, 4, true>(nullptr, out, codes, cpitch, d, st, s);
     return SZGB_EUNSUPPORTED;
-}
-
-template <int NL, bool DEC>
-static int run_hyper4(const float* x, float* V, uint16_t* codes, uint64_t cpitch, const Dims4& d,
-                      const DevState* st, cudaStream_t s) {
-    const int64_t H = (int64_t)(d.D - 1) + (int64_t)(d.P - 1) + (int64_t)(d.M - 1) + (int64_t)(d.N - 1);
-    for (int64_t h = 0; h <= H; h++) {
-        const HyperBox4 b = hyper_box4(h, (int64_t)d.D, (int64_t)d.P, (int64_t)d.M, (int64_t)d.N);
-        const uint64_t n = b.na * b.ni * b.nj;
-        if (n == 0) continue;
-        const unsigned blocks = (unsigned)((n + kHyperThreads - 1) / kHyperThreads);
-        k_hyper4<NL, DEC><<<blocks, kHyperThreads, 0, s>>>(x, V, codes, cpitch, d, h, b, st);
-        if (cudaGetLastError() != cudaSuccess) return SZGB_ECUDA;
-    }
-    return SZGB_OK;
 }
 
 int launch_hyper4(bool dec, int layers, const float* x, float* V, uint16_t* codes, uint64_t cpitch, uint64_t D,
                   uint64_t P, uint64_t M, uint64_t N, const DevState* st, cudaStream_t s) {
     const Dims4 d = {D, P, M, N};
     switch (layers * 2 + (dec ? 1 : 0)) {
-        case 2: return run_hyper4<1, false>(x, V, codes, cpitch, d, st, s);
-        case 3: return run_hyper4<1, true>(x, V, codes, cpitch, d, st, s);
-        case 4: return run_hyper4<2, false>(x, V, codes, cpitch, d, st, s);
-        case 5: return run_hyper4<2, true>(x, V, codes, cpitch, d, st, s);
-        case 6: return run_hyper4<3, false>(x, V, codes, cpitch, d, st, s);
-        case 7: return run_hyper4<3, true>(x, V, codes, cpitch, d, st, s);
-        case 8: return run_hyper4<4, false>(x, V, codes, cpitch, d, st, s);
-        case 9: return run_hyper4<4, true>(x, V, codes, cpitch, d, st, s);
+        case 2: return run_tiles<4, 1, false>(x, V, codes, cpitch, d, st, s);
+        case 3: return run_tiles<4, 1, true>(x, V, codes, cpitch, d, st, s);
+        case 4: return run_tiles<4, 2, false>(x, V, codes, cpitch, d, st, s);
+        case 5: return run_tiles<4, 2, true>(x, V, codes, cpitch, d, st, s);
+        case 6: return run_tiles<4, 3, false>(x, V, codes, cpitch, d, st, s);
+        case 7: return run_tiles<4, 3, true>(x, V, codes, cpitch, d, st, s);
+        case 8: return run_tiles<4, 4, false>(x, V, codes, cpitch, d, st, s);
+        case 9: return run_tiles<4, 4, true>(x, V, codes, cpitch, d, st, s);
         default: return SZGB_EUNSUPPORTED;
     }
 }

@@ -1,6 +1,6 @@
 // hyper_emulate.cpp -- the hyperplane kernels' own device code
-// (paper_1706_03791_gb300/csrc/hyper_kernels.cuh), run on the host thread by
-// thread, hyperplane by hyperplane, against the oracle: codes and recorded
+// (paper_1706_03791_gb300/csrc/hyper_tile.cuh and hyper_kernels.cuh), run on
+// the host tile by tile, step by step, thread by thread, against the oracle: codes and recorded
 // values of 3D fields with n = 3, 4 and of 4D fields with n = 1..4, their
 // reconstruction from the codes and the unpredictable values, the 4D
 // adaptive-m choice and the 4D prediction hit counts.  The CUDA intrinsics the kernels use are given their
@@ -9,6 +9,7 @@
 // the library's device helpers.
 //
 // Usage: hyper_emulate  -> "cases N failures F", exit status 0 iff F == 0.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -96,6 +97,7 @@ inline float dequantize(int code, float pred, const QParams& qp) {
 
 #include "../../paper_1706_03791_gb300/csrc/hyper_box.h"
 #include "../../paper_1706_03791_gb300/csrc/hyper_kernels.cuh"
+#include "../../paper_1706_03791_gb300/csrc/hyper_tile.cuh"
 
 extern "C" {
 #include "../../oracle/szo.h"
@@ -150,31 +152,28 @@ DevState state_for(const std::vector<float>& x, int mode, double eb_abs, double 
     return st;
 }
 
-template <int NL, bool DEC>
-void emulate3(const float* x, float* V, uint16_t* codes, uint64_t cpitch, uint64_t P, uint64_t M, uint64_t N,
-              const DevState* st) {
-    const int64_t H = (int64_t)(P - 1) + (int64_t)(M - 1) + (int64_t)(N - 1);
-    for (int64_t h = 0; h <= H; h++) {
-        const HyperBox b = hyper_box(h, (int64_t)P, (int64_t)M, (int64_t)N);
-        const uint64_t n = b.ni * b.nj, blocks = (n + kHyperThreads - 1) / kHyperThreads;
-        for (uint64_t t = 0; t < blocks * kHyperThreads; t++) {
-            blockIdx.x = (unsigned)(t / kHyperThreads);
-            threadIdx.x = (unsigned)(t % kHyperThreads);
-            k_hyper<NL, DEC>(x, V, codes, cpitch, M, N, h, b, st);
-        }
-    }
-}
-
-template <int NL, bool DEC>
-void emulate4(const float* x, float* V, uint16_t* codes, uint64_t cpitch, const Dims4& d, const DevState* st) {
-    const int64_t H = (int64_t)(d.D - 1) + (int64_t)(d.P - 1) + (int64_t)(d.M - 1) + (int64_t)(d.N - 1);
-    for (int64_t h = 0; h <= H; h++) {
-        const HyperBox4 b = hyper_box4(h, (int64_t)d.D, (int64_t)d.P, (int64_t)d.M, (int64_t)d.N);
-        const uint64_t n = b.na * b.ni * b.nj, blocks = (n + kHyperThreads - 1) / kHyperThreads;
-        for (uint64_t t = 0; t < blocks * kHyperThreads; t++) {
-            blockIdx.x = (unsigned)(t / kHyperThreads);
-            threadIdx.x = (unsigned)(t % kHyperThreads);
-            k_hyper4<NL, DEC>(x, V, codes, cpitch, d, h, b, st);
+// the tiled schedule, tile by tile and thread by thread: every thread's load,
+// then every step of every thread, then every thread's store (no thread reads
+// a point another thread writes in the same step)
+template <int DIM, int NL, bool DEC>
+void emulate_tiles(const float* x, float* V, uint16_t* codes, uint64_t cpitch, const Dims4& d, const DevState* st) {
+    using G = TileGeom<DIM, NL>;
+    const int64_t nA = (int64_t)((d.D + G::TA - 1) / G::TA), nI = (int64_t)((d.P + G::TI - 1) / G::TI),
+                  nJ = (int64_t)((d.M + G::TJ - 1) / G::TJ), nL = (int64_t)((d.N + G::TL - 1) / G::TL);
+    std::vector<float> Vs(G::VBOX), Xs(G::XBOX);
+    std::vector<uint16_t> Cs(G::XBOX);
+    const QParams qp = load_qparams(st);
+    for (int64_t H = 0; H <= (nA - 1) + (nI - 1) + (nJ - 1) + (nL - 1); H++) {
+        const HyperBox4 b = hyper_box4(H, nA, nI, nJ, nL);
+        for (uint64_t blk = 0; blk < b.na * b.ni * b.nj; blk++) {
+            TileCtx t = {x, V, codes, cpitch, d, 0, 0, 0, 0};
+            if (!tile_at<DIM, NL>(b, H, nL, blk, &t)) continue;
+            std::fill(Vs.begin(), Vs.end(), std::nanf(""));
+            for (int tid = 0; tid < G::THREADS; tid++) tile_load<DIM, NL, DEC>(t, Vs.data(), Xs.data(), Cs.data(), tid);
+            for (int s = 0; s < G::STEPS; s++)
+                for (int tid = 0; tid < G::THREADS; tid++)
+                    tile_step<DIM, NL, DEC>(t, Vs.data(), Xs.data(), Cs.data(), tid, s, qp);
+            for (int tid = 0; tid < G::THREADS; tid++) tile_store<DIM, NL, DEC>(t, Vs.data(), Cs.data(), tid);
         }
     }
 }
@@ -230,9 +229,9 @@ int run_case(const std::vector<uint64_t>& shape, int mode, double eb_abs, double
     if (nd == 4) d = {shape[0], shape[1], shape[2], shape[3]};
     if (nd == 4) {
         if (m_user == 0 && adapt4_m<NL>(x.data(), d, st, 0.99) != m) return 12;
-        emulate4<NL, false>(x.data(), V.data(), codes.data(), cpitch, d, &st);
+        emulate_tiles<4, NL, false>(x.data(), V.data(), codes.data(), cpitch, d, &st);
     } else {
-        emulate3<NL, false>(x.data(), V.data(), codes.data(), cpitch, shape[0], shape[1], shape[2], &st);
+        emulate_tiles<3, NL, false>(x.data(), V.data(), codes.data(), cpitch, {1, shape[0], shape[1], shape[2]}, &st);
     }
     for (uint64_t p = 0; p < n; p++) {
         if (codes[(p / N) * cpitch + p % N] != code_ref[p]) return 13;
@@ -242,8 +241,8 @@ int run_case(const std::vector<uint64_t>& shape, int mode, double eb_abs, double
     std::vector<float> Y(n, std::nanf(""));
     for (uint64_t p = 0; p < n; p++)
         if (code_ref[p] == 0) Y[p] = rec[p];
-    if (nd == 4) emulate4<NL, true>(nullptr, Y.data(), codes.data(), cpitch, d, &st);
-    else emulate3<NL, true>(nullptr, Y.data(), codes.data(), cpitch, shape[0], shape[1], shape[2], &st);
+    if (nd == 4) emulate_tiles<4, NL, true>(nullptr, Y.data(), codes.data(), cpitch, d, &st);
+    else emulate_tiles<3, NL, true>(nullptr, Y.data(), codes.data(), cpitch, {1, shape[0], shape[1], shape[2]}, &st);
     for (uint64_t p = 0; p < n; p++)
         if (__float_as_uint(Y[p]) != __float_as_uint(rec[p])) return 15;
     if (nd == 4) {
@@ -290,6 +289,12 @@ int main() {
     check(run_case<2>({1, 1, 3, 40}, 1, 0.0, 1e-4, 0), "4d unit");
     check(run_case<1>({9, 10, 9, 17}, 1, 0.0, 1e-4, 0), "4d samples");
     check(run_case<3>({8, 9, 8, 9}, 2, 1e-3, 1e-5, 0), "4d n3 both, several blocks");
+    // several tiles along every axis, each with a ragged last tile
+    check(run_case<3>({19, 37, 70}, 1, 0.0, 1e-4, 0), "3d n3 3x3x3 tiles");
+    check(run_case<4>({17, 33, 65}, 1, 0.0, 1e-5, 0), "3d n4 3x3x3 tiles");
+    check(run_case<1>({9, 10, 17, 40}, 1, 0.0, 1e-4, 0), "4d n1 3x3x3x2 tiles");
+    check(run_case<2>({9, 6, 9, 33}, 0, 1e-3, 0.0, 0), "4d n2 3x2x2x2 tiles");
+    check(run_case<4>({5, 9, 17, 33}, 1, 0.0, 1e-4, 0), "4d n4 3x3x3x2 tiles");
     std::printf("cases %d failures %d\n", cases, bad);
     return bad ? 1 : 0;
 }
