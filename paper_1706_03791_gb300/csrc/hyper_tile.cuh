@@ -43,11 +43,12 @@ struct TileGeom {
     // one, land BL - 1 words apart, an odd stride (distinct banks)
     static constexpr int BL = (TL + NL + 1) & ~1;
     static constexpr int VBOX = BA * BI * BJ * BL;  // recorded values (floats)
+    static constexpr int VPAD = (VBOX + 3) & ~3;    // floats before x / codes (16-byte offset)
     static constexpr int XBOX = TA * TI * TJ * TL;  // own points: x (floats) and codes (u16)
     static constexpr int THREADS = TA * TI * TJ;    // one thread per tile row
     static constexpr int STEPS = TA + TI + TJ + TL - 3;
     static constexpr size_t smem_bytes(bool dec) {
-        return (size_t)VBOX * 4 + (dec ? 0 : (size_t)XBOX * 4) + (size_t)XBOX * 2;
+        return (size_t)VPAD * 4 + (dec ? 0 : (size_t)XBOX * 4) + (size_t)XBOX * 2;
     }
 };
 
@@ -90,7 +91,12 @@ __host__ __device__ __forceinline__ uint64_t code_index(const Dims4& d, uint64_t
 
 // Phase 1 for thread tid: the box of recorded values (compression skips the
 // tile's own points, which it computes; reconstruction keeps them, since the
-// unpredictable values are already there), and the tile's x or codes.
+// unpredictable values are already there), and the tile's x or codes, as
+// asynchronous copies that zero-fill what lies outside the field; the thread
+// waits for its own copies (the caller's barrier then publishes them).
+// Codes move 8 at a time: a tile row starts on a multiple of 8 codes and a
+// code row's pitch is a multiple of 8, so a group that starts inside the row
+// ends inside its pitch.
 template <int DIM, int NL, bool DEC>
 __device__ __forceinline__ void tile_load(const TileCtx& t, float* Vs, float* Xs, uint16_t* Cs, int tid) {
     using G = TileGeom<DIM, NL>;
@@ -103,29 +109,43 @@ __device__ __forceinline__ void tile_load(const TileCtx& t, float* Vs, float* Xs
         const int bi = r % G::BI;
         const int ba = r / G::BI;
         const int64_t a = t.a0 + ba - G::HA, i = t.i0 + bi - NL, j = t.j0 + bj - NL, l = t.l0 + bl - NL;
-        float v = 0.0f;
         const bool inside = bl < G::TL + NL && a >= 0 && i >= 0 && j >= 0 && l >= 0 && (uint64_t)a < t.d.D &&
                             (uint64_t)i < t.d.P && (uint64_t)j < t.d.M && (uint64_t)l < t.d.N;
         const bool own = a >= t.a0 && i >= t.i0 && j >= t.j0 && l >= t.l0;
-        if (inside && (DEC || !own)) v = __ldcg(t.V + field_index(t.d, a, i, j, l));
-        Vs[e] = v;
+        const bool take = inside && (DEC || !own);
+        cp_async4(Vs + e, take ? t.V + field_index(t.d, a, i, j, l) : t.V, take ? 4 : 0);
     }
-    for (int e = tid; e < G::XBOX; e += G::THREADS) {
-        int r = e;
-        const int tl = r % G::TL;
-        r /= G::TL;
-        const int tj = r % G::TJ;
-        r /= G::TJ;
-        const int ti = r % G::TI;
-        const int ta = r / G::TI;
-        const int64_t a = t.a0 + ta, i = t.i0 + ti, j = t.j0 + tj, l = t.l0 + tl;
-        const bool inside = (uint64_t)a < t.d.D && (uint64_t)i < t.d.P && (uint64_t)j < t.d.M && (uint64_t)l < t.d.N;
-        if (DEC) {
-            Cs[e] = inside ? t.codes[code_index(t.d, t.cpitch, a, i, j, l)] : (uint16_t)0;
-        } else {
-            Xs[e] = inside ? __ldg(t.x + field_index(t.d, a, i, j, l)) : 0.0f;
+    if (DEC) {
+        for (int e = tid; e < G::XBOX / 8; e += G::THREADS) {
+            int r = e;
+            const int tl = (r % (G::TL / 8)) * 8;
+            r /= G::TL / 8;
+            const int tj = r % G::TJ;
+            r /= G::TJ;
+            const int ti = r % G::TI;
+            const int ta = r / G::TI;
+            const int64_t a = t.a0 + ta, i = t.i0 + ti, j = t.j0 + tj, l = t.l0 + tl;
+            const bool inside =
+                (uint64_t)a < t.d.D && (uint64_t)i < t.d.P && (uint64_t)j < t.d.M && (uint64_t)l < t.d.N;
+            cp_async16(Cs + 8 * e, inside ? t.codes + code_index(t.d, t.cpitch, a, i, j, l) : t.codes, inside ? 16 : 0);
+        }
+    } else {
+        for (int e = tid; e < G::XBOX; e += G::THREADS) {
+            int r = e;
+            const int tl = r % G::TL;
+            r /= G::TL;
+            const int tj = r % G::TJ;
+            r /= G::TJ;
+            const int ti = r % G::TI;
+            const int ta = r / G::TI;
+            const int64_t a = t.a0 + ta, i = t.i0 + ti, j = t.j0 + tj, l = t.l0 + tl;
+            const bool inside =
+                (uint64_t)a < t.d.D && (uint64_t)i < t.d.P && (uint64_t)j < t.d.M && (uint64_t)l < t.d.N;
+            cp_async4(Xs + e, inside ? t.x + field_index(t.d, a, i, j, l) : t.x, inside ? 4 : 0);
         }
     }
+    cp_async_commit();
+    cp_async_wait<0>();
 }
 
 // n-layer prediction of the point at box index ve from the box of recorded

@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(TileGeom<DIM, NL>::THREADS)
     if (st->err) return;
     extern __shared__ __align__(16) unsigned char tile_smem[];
     float* Vs = reinterpret_cast<float*>(tile_smem);
-    float* Xs = Vs + G::VBOX;
+    float* Xs = Vs + G::VPAD;
     uint16_t* Cs = reinterpret_cast<uint16_t*>(DEC ? Xs : Xs + G::XBOX);
     TileCtx t = {x, V, codes, cpitch, d, 0, 0, 0, 0};
     if (!tile_at<DIM, NL>(b, H, nL, blockIdx.x, &t)) return;  // the whole block

@@ -88,6 +88,19 @@ inline int quantize_tr(float x, float pred, float tr, const QParams& qp, float& 
     V = ok ? dq : tr;
     return ok ? ((int)qn + qp.center) : 0;
 }
+// asynchronous global->shared copies: on the host, an immediate copy of
+// src_bytes and zeros for the rest
+inline void cp_async4(void* dst, const void* src, int src_bytes) {
+    std::memset(dst, 0, 4);
+    if (src_bytes) std::memcpy(dst, src, (size_t)src_bytes);
+}
+inline void cp_async16(void* dst, const void* src, int src_bytes) {
+    std::memset(dst, 0, 16);
+    if (src_bytes) std::memcpy(dst, src, (size_t)src_bytes);
+}
+inline void cp_async_commit() {}
+template <int N>
+inline void cp_async_wait() {}
 inline float dequantize(int code, float pred, const QParams& qp) {
     const float qf = (float)(code - qp.center);
     return __fadd_rn(pred, __fmul_rn(qf, qp.twoeb));
