@@ -259,6 +259,15 @@ int szgb_tune_load(szgb_ctx *ctx, const char *path);
 /* Capture batches in CUDA graphs (1, the default) or launch them directly (0). */
 int szgb_set_graphs(szgb_ctx *ctx, int on);
 
+/* Caps the grid of this context's persistent wavefront launches at
+ * max_ctas CTAs (one CTA per SM; 0 = one per SM of the device, the
+ * default).  A persistent launch holds its SMs until its last work item is
+ * done, so kernels issued meanwhile on other streams (even higher-priority
+ * ones) wait for SMs; a cap leaves the other SMs free for them (the serving
+ * loop caps its large requests this way).  Changes the schedule only, never
+ * the results.  SZGB_EINVAL for a negative cap. */
+int szgb_set_wave_ctas(szgb_ctx *ctx, int max_ctas);
+
 /* ---- test hooks for the bounded device-side waits -------------------------
  * Not part of the method (the paper has no counterpart): they let a test make
  * the wavefront's bounded waits run out without faulting or hanging the GPU.

@@ -148,44 +148,52 @@ __device__ __forceinline__ void tile_load(const TileCtx& t, float* Vs, float* Xs
     cp_async_wait<0>();
 }
 
+// Term t of the n-layer predictor (t = 0, 1, ... in descending
+// lexicographic order of k, the all-zero k excluded): digit `axis` of k.
+// Term t is the number (n+1)^DIM - 1 - t written in base n + 1.
+template <int DIM, int NL>
+__host__ __device__ __forceinline__ constexpr int term_digit(int t, int axis) {
+    int u = 1;
+    for (int a = 0; a < DIM; a++) u *= NL + 1;
+    u = u - 1 - t;
+    for (int a = DIM - 1; a > axis; a--) u /= NL + 1;
+    return u % (NL + 1);
+}
+
 // n-layer prediction of the point at box index ve from the box of recorded
-// values: terms in descending lexicographic order of k.
+// values: terms in descending lexicographic order of k, each product and sum
+// rounded once.  The values of 32 terms at a time are read first (so that
+// their shared-memory loads overlap), then summed in that order.
 template <int DIM, int NL>
 __device__ __forceinline__ float predict_tile(const float* Vs, int ve) {
     using G = TileGeom<DIM, NL>;
+    constexpr int T = DIM == 3 ? (NL + 1) * (NL + 1) * (NL + 1) - 1 : (NL + 1) * (NL + 1) * (NL + 1) * (NL + 1) - 1;
+    constexpr int GRP = 32;
     float pred = 0.0f;
-    bool first = true;
-    if constexpr (DIM == 3) {
 #pragma unroll
-        for (int k0 = NL; k0 >= 0; k0--) {
+    for (int g0 = 0; g0 < T; g0 += GRP) {
+        float v[GRP];
 #pragma unroll
-            for (int k1 = NL; k1 >= 0; k1--) {
-#pragma unroll
-                for (int k2 = NL; k2 >= 0; k2--) {
-                    if (k0 == 0 && k1 == 0 && k2 == 0) continue;
-                    const float v = Vs[ve - (k0 * G::BJ + k1) * G::BL - k2];
-                    const float prod = __fmul_rn((float)term_coef(NL, k0, k1, k2), v);
-                    pred = first ? prod : __fadd_rn(pred, prod);
-                    first = false;
-                }
+        for (int q = 0; q < GRP; q++) {
+            const int t = g0 + q;
+            if (t < T) {
+                const int off = DIM == 3 ? (term_digit<DIM, NL>(t, 0) * G::BJ + term_digit<DIM, NL>(t, 1)) * G::BL +
+                                               term_digit<DIM, NL>(t, 2)
+                                         : ((term_digit<DIM, NL>(t, 0) * G::BI + term_digit<DIM, NL>(t, 1)) * G::BJ +
+                                            term_digit<DIM, NL>(t, 2)) * G::BL + term_digit<DIM, NL>(t, 3);
+                v[q] = Vs[ve - off];
             }
         }
-    } else {
 #pragma unroll
-        for (int k0 = NL; k0 >= 0; k0--) {
-#pragma unroll
-            for (int k1 = NL; k1 >= 0; k1--) {
-#pragma unroll
-                for (int k2 = NL; k2 >= 0; k2--) {
-#pragma unroll
-                    for (int k3 = NL; k3 >= 0; k3--) {
-                        if (k0 == 0 && k1 == 0 && k2 == 0 && k3 == 0) continue;
-                        const float v = Vs[ve - ((k0 * G::BI + k1) * G::BJ + k2) * G::BL - k3];
-                        const float prod = __fmul_rn((float)term_coef4(NL, k0, k1, k2, k3), v);
-                        pred = first ? prod : __fadd_rn(pred, prod);
-                        first = false;
-                    }
-                }
+        for (int q = 0; q < GRP; q++) {
+            const int t = g0 + q;
+            if (t < T) {
+                const int c = DIM == 3 ? term_coef(NL, term_digit<DIM, NL>(t, 0), term_digit<DIM, NL>(t, 1),
+                                                   term_digit<DIM, NL>(t, 2))
+                                       : term_coef4(NL, term_digit<DIM, NL>(t, 0), term_digit<DIM, NL>(t, 1),
+                                                    term_digit<DIM, NL>(t, 2), term_digit<DIM, NL>(t, 3));
+                const float prod = __fmul_rn((float)c, v[q]);
+                pred = t == 0 ? prod : __fadd_rn(pred, prod);
             }
         }
     }

@@ -92,6 +92,7 @@ struct szgb_ctx {
     int force_W = 0;            // set while the autotuner times a candidate
     uint32_t force_chunk = 0;   // likewise (a requested chunk length; 0: none)
     int debug_skip = 0;  // test hook: 1 + the wavefront work item never run; 0 = none
+    int wave_ctas = 0;   // most CTAs of a persistent wavefront launch (0: one per SM)
 };
 
 namespace {
@@ -315,6 +316,14 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
                         uint8_t* const* out, const size_t* out_cap, size_t* out_len, szgb_stats* stats);
 int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, const size_t* in_len,
                           float* const* out, const size_t* out_cap, int* status, const uint8_t* host_hdr = nullptr);
+
+// grid of a persistent wavefront launch over n work items: one CTA per SM,
+// at most the context's cap
+int wave_grid(const szgb_ctx* c, size_t n) {
+    size_t cap = (size_t)c->sm_count;
+    if (c->wave_ctas > 0 && (size_t)c->wave_ctas < cap) cap = (size_t)c->wave_ctas;
+    return (int)std::min(n, cap);
+}
 
 // A single device-resident field of the paper's method takes the batched
 // path (one field): its whole pass is captured once in a CUDA graph and
@@ -903,7 +912,7 @@ int launch_wave_one(szgb_ctx* c, const WaveGeom& g, int layers, bool dec, const 
         cudaMemcpyAsync(dev_order, ho, 8 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(dev_ticket, 0, sizeof(unsigned), s) != cudaSuccess)
         return SZGB_ECUDA;
-    const int grid = (int)std::min<size_t>(n, (size_t)c->sm_count);
+    const int grid = wave_grid(c, n);
     return launch_wave_batch(dev_args, dev_order, (unsigned)n, dev_ticket, layers, dec,
                              wave_smem_bytes(g, layers, dec), grid, s);
 }
@@ -1016,7 +1025,7 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
     key.push_back((uint64_t)count);
     key.push_back((uint64_t)(uintptr_t)c->scratch);
     key.push_back((uint64_t)(uintptr_t)c->h_batch);
-    key.push_back((uint64_t)c->W2 | ((uint64_t)c->W3 << 16));
+    key.push_back((uint64_t)c->W2 | ((uint64_t)c->W3 << 16) | ((uint64_t)(uint32_t)c->wave_ctas << 32));
     for (int f = 0; f < count; f++) {
         key.push_back((uint64_t)(uintptr_t)data[f]);
         key.push_back((uint64_t)(uintptr_t)out[f]);
@@ -1047,7 +1056,7 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
         join_aux(c);
         for (int li = 0; li < kMaxLayers; li++) {
             if (!ord_n[li]) continue;
-            const int grid = (int)std::min<size_t>(ord_n[li], (size_t)c->sm_count);
+            const int grid = wave_grid(c, ord_n[li]);
             if ((r = launch_wave_batch(wargs, order + 2 * ord_at[li], (unsigned)ord_n[li], tickets + li, li + 1, false,
                                        smem[li], grid, s)))
                 return r;
@@ -1265,7 +1274,7 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
     key.push_back((uint64_t)count);
     key.push_back((uint64_t)(uintptr_t)c->scratch);
     key.push_back((uint64_t)(uintptr_t)c->h_batch);
-    key.push_back((uint64_t)c->W2 | ((uint64_t)c->W3 << 16));
+    key.push_back((uint64_t)c->W2 | ((uint64_t)c->W3 << 16) | ((uint64_t)(uint32_t)c->wave_ctas << 32));
     for (int f = 0; f < count; f++) {
         key.push_back((uint64_t)(uintptr_t)in[f]);
         key.push_back((uint64_t)in_len[f]);
@@ -1299,7 +1308,7 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
         if ((r = launch_decode_rows_batch(dargs, dblk, count, dec_blocks, s))) return r;
         for (int li = 0; li < kMaxLayers; li++) {
             if (!ord_n[li]) continue;
-            const int grid = (int)std::min<size_t>(ord_n[li], (size_t)c->sm_count);
+            const int grid = wave_grid(c, ord_n[li]);
             if ((r = launch_wave_batch(wargs, order + 2 * ord_at[li], (unsigned)ord_n[li], tickets + li, li + 1, true,
                                        smem[li], grid, s)))
                 return r;
@@ -1712,6 +1721,12 @@ int szgb_set_graphs(szgb_ctx* c, int on) {
         drop_graph(c->g_comp);
         drop_graph(c->g_dec);
     }
+    return SZGB_OK;
+}
+
+int szgb_set_wave_ctas(szgb_ctx* c, int max_ctas) {
+    if (!c || max_ctas < 0) return SZGB_EINVAL;
+    c->wave_ctas = max_ctas;
     return SZGB_OK;
 }
 

@@ -16,8 +16,10 @@
 // wavefront does not carry: 3D n = 3, 4, 4D, the lattice variant) runs alone, a
 // batch of small requests gathers at most kBatchBytes of I/O, and with two
 // or more workers worker 0 takes small requests only, so that one worker is
-// always free of large ones.  The other workers take the oldest pending
-// request's kind first.  A request's result
+// always free of large ones; the other workers take the oldest pending
+// request's kind first.  A persistent wavefront launch holds its SMs until
+// it ends, so a large request's wavefront runs on three quarters of the SMs
+// (szgb_set_wave_ctas) and small batches keep the rest.  A request's result
 // is exactly the result of the single-field calls: batches change the
 // schedule, never the bits.
 #include <stdio.h>
@@ -271,6 +273,9 @@ void worker_main(szgb_server* S, int wid) {
          cudaStreamCreateWithPriority(&st_large, cudaStreamNonBlocking, prio_low) != cudaSuccess))
         init_rc = SZGB_ECUDA;
     if (init_rc == SZGB_OK) szgb_set_graphs(ctx, 0);  // every batch differs: launch directly
+    int sms = 0;
+    if (init_rc == SZGB_OK && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, S->device) != cudaSuccess)
+        init_rc = SZGB_ECUDA;
     void* dbuf = nullptr;
     size_t dcap = 0;
     for (;;) {
@@ -293,8 +298,13 @@ void worker_main(szgb_server* S, int wid) {
         if (init_rc != SZGB_OK) {
             for (Req* q : batch) q->status = init_rc;
         } else {
-            cudaStream_t st = (batch.size() == 1 && is_large(batch[0])) ? st_large : st_small;
+            const bool large = batch.size() == 1 && is_large(batch[0]);
+            cudaStream_t st = large ? st_large : st_small;
             szgb_set_stream(ctx, st);
+            // a large request's persistent wavefront leaves a quarter of the
+            // SMs free: the small batches' kernels find SMs there instead of
+            // waiting for the whole launch
+            szgb_set_wave_ctas(ctx, large ? sms - sms / 4 : 0);
             run_batch(S, ctx, st, dbuf, dcap, batch, &t_in, &t_run);
         }
         if (trace().f) {

@@ -100,6 +100,7 @@ def lib():
         L.szgb_decompress_batch.argtypes = [vp, C.c_int, C.POINTER(vp), C.POINTER(sz), C.POINTER(vp),
                                             C.POINTER(sz), C.POINTER(C.c_int)]
         L.szgb_set_graphs.argtypes = [vp, C.c_int]
+        L.szgb_set_wave_ctas.argtypes = [vp, C.c_int]
         L.szgb_debug_set_wait_limit.argtypes = [vp, C.c_uint64]
         L.szgb_debug_skip_item.argtypes = [vp, C.c_int]
         L.szgb_quality_dev.argtypes = [vp, vp, vp, sz, C.POINTER(Quality)]
@@ -133,7 +134,7 @@ def strerror(code: int) -> str:
 EXPORTS = ["szgb_create", "szgb_destroy", "szgb_set_stream", "szgb_compress_bound", "szgb_compress",
            "szgb_compress_trace", "szgb_decompress", "szgb_stream_info", "szgb_set_profiling",
            "szgb_num_phases", "szgb_phase_name", "szgb_phase_times", "szgb_strerror",
-           "szgb_decompress_noalloc", "szgb_compress_batch", "szgb_decompress_batch", "szgb_set_graphs",
+           "szgb_decompress_noalloc", "szgb_compress_batch", "szgb_decompress_batch", "szgb_set_graphs", "szgb_set_wave_ctas",
            "szgb_server_create", "szgb_submit", "szgb_poll", "szgb_wait", "szgb_server_stats",
            "szgb_server_destroy", "szgb_autotune", "szgb_autotune_batch", "szgb_tune_save", "szgb_tune_load",
            "szgb_quality_dev", "szgb_hit_count_dev", "szgb_suggest_m", "szgb_compress_4d",
@@ -400,6 +401,13 @@ class Context:
     # -- batches -------------------------------------------------------------
     def set_graphs(self, on: bool):
         lib().szgb_set_graphs(self._h, 1 if on else 0)
+
+    def set_wave_ctas(self, max_ctas: int):
+        """Cap the persistent wavefront launches of this context at max_ctas
+        CTAs (0 = one per SM), leaving the other SMs to other streams."""
+        rc = lib().szgb_set_wave_ctas(self._h, int(max_ctas))
+        if rc:
+            raise SzgbError(rc, "szgb_set_wave_ctas")
 
     def debug_set_wait_limit(self, ns: int):
         """Test hook: limit of the device-side waits of later calls (0 = the

@@ -115,3 +115,31 @@ def test_single_field_both_paths(ctx, szo):
                     assert np.array_equal(_bits(y.cpu().numpy()), _bits(rec))
     finally:
         ctx.set_graphs(True)
+
+
+def test_capped_wavefront_grid(ctx, szo):
+    """A cap on the persistent wavefront's CTAs (szgb_set_wave_ctas) changes
+    the schedule only: with 1, 7 and 40 CTAs, graphs on and off, the batch's
+    streams and reconstructions are the oracle's."""
+    import torch
+    from paper_1706_03791_gb300 import szgb
+    xs = [np.ascontiguousarray(g()) for g, _ in MIX]
+    kws = [kw for _, kw in MIX]
+    refs = [szo.compress(x, want_aux=True, **kw) for x, kw in zip(xs, kws)]
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    try:
+        for cap in (1, 7, 40):
+            ctx.set_wave_ctas(cap)
+            for graphs in (True, False):
+                ctx.set_graphs(graphs)
+                ss, _ = ctx.compress_batch(xd, kws)
+                for i, (s, (sref, rec, _)) in enumerate(zip(ss, refs)):
+                    assert np.array_equal(s.cpu().numpy(), sref), (cap, graphs, i)
+                ys = ctx.decompress_batch(ss)
+                for i, (y, (_, rec, _)) in enumerate(zip(ys, refs)):
+                    assert np.array_equal(_bits(y.cpu().numpy()), _bits(rec)), (cap, graphs, i)
+        with pytest.raises(szgb.SzgbError):
+            ctx.set_wave_ctas(-1)
+    finally:
+        ctx.set_wave_ctas(0)
+        ctx.set_graphs(True)
