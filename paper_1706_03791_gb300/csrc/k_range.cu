@@ -140,6 +140,33 @@ int launch_range(const float* x, uint64_t n, DevState* st, const CallParams& cp,
 }
 
 // ---------------------------------------------------------------------------
+// The field's rows at a 16-byte row pitch, for the wavefront's TMA tiles when
+// the row length N is not a multiple of 4 (a TMA tile needs 16-byte row
+// strides): row r of x goes to xp + r P, P = N rounded up to 4.  A warp
+// copies one row at a time (coalesced loads and stores), grid-stride over
+// the rows.
+
+__global__ void __launch_bounds__(256) k_pitch_rows(const float* __restrict__ x, uint64_t rows, uint64_t N,
+                                                    float* __restrict__ xp, uint64_t P) {
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    for (uint64_t r = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += nw) {
+        const float* src = x + r * N;
+        float* dst = xp + r * P;
+#pragma unroll 4
+        for (uint64_t c = (uint64_t)lane; c < N; c += 32) dst[c] = __ldg(src + c);
+    }
+}
+
+int launch_pitch_rows(const float* x, uint64_t rows, uint64_t N, float* xp, uint64_t P, int sm_count, cudaStream_t s) {
+    uint64_t blocks = (rows + 7) / 8;  // 8 warps a block
+    const uint64_t cap = 8ull * (uint64_t)(sm_count > 0 ? sm_count : 1);
+    blocks = blocks < 1 ? 1 : (blocks > cap ? cap : blocks);
+    k_pitch_rows<<<(unsigned)blocks, 256, 0, s>>>(x, rows, N, xp, P);
+    return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
 // K8: adaptive m.  Samples are the points whose coordinates are all multiples
 // of 8; each is predicted from the ORIGINAL neighbour values with the n-layer
 // stencil (terms in descending lexicographic order, products and sums rounded

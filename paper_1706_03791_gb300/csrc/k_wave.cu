@@ -5,8 +5,8 @@
 // values of its (n+1)^d - 1 preceding neighbours, quantized into 2^m - 1
 // intervals of width 2 eb (Sec. IV-A) or stored as a truncated binary
 // representation, and its recorded value is kept for later predictions.
-// Decompression runs the same prediction in the same dependency order, with
-// the Huffman decode of each row fused in (a row is one stream chunk).
+// Decompression runs the same prediction in the same dependency order over
+// the codes that k_decode_rows (below) decoded from the stream's chunks.
 //
 // Parallel schedule.  A point depends only on neighbours with smaller
 // (plane, row, column) coordinates, so any order that respects that DAG gives
@@ -76,6 +76,7 @@ struct WaveArgs {
     int tma_x;
     int vec_out;      // output rows are 16-byte aligned: tiles leave as 16-byte stores
     uint64_t opitch;  // output row pitch (elements)
+    uint64_t xpitch;  // input row pitch (elements; compress)
     WaveGeom g;
     // compress
     const float* x;
@@ -554,12 +555,12 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
                     }
                 } else if constexpr (!DEC) {  // decompression always has TMA (its code array is ours)
                     const int nv = tile_rows(w);
-                    const float* xr = a_x + tile_row0(w) * g.N;
+                    const float* xr = a_x + tile_row0(w) * A.xpitch;
                     const int col = c0 + lane;
                     for (int t = 0; t < 32; t++) {
                         const bool ok = t < nv && col < N;
                         cp_async4(slot + t * kTW + lane,
-                                  ok ? (const void*)(xr + (uint64_t)t * g.N + col) : (const void*)a_x, ok ? 4 : 0);
+                                  ok ? (const void*)(xr + (uint64_t)t * A.xpitch + col) : (const void*)a_x, ok ? 4 : 0);
                     }
                 }
             }
@@ -1470,12 +1471,13 @@ static int launch_any(const WaveArgs& a, int layers, cudaStream_t s) {
     return launch_nd<DEC, false>(a, layers, s);
 }
 
-static void fill_compress(WaveArgs& a, const WaveGeom& g, const float* x, uint16_t* codes, uint64_t codes_pitch,
-                          float* recorded, float* halo_row, float* halo_plane, unsigned int* prog, DevState* st,
-                          uint64_t timeout_ns) {
+static void fill_compress(WaveArgs& a, const WaveGeom& g, const float* x, uint64_t x_pitch, uint16_t* codes,
+                          uint64_t codes_pitch, float* recorded, float* halo_row, float* halo_plane,
+                          unsigned int* prog, DevState* st, uint64_t timeout_ns) {
     memset(&a, 0, sizeof(a));
     a.g = g;
     a.x = x;
+    a.xpitch = x_pitch;
     a.codes = codes;
     a.opitch = codes_pitch;
     a.recorded = recorded;
@@ -1484,7 +1486,7 @@ static void fill_compress(WaveArgs& a, const WaveGeom& g, const float* x, uint16
     a.prog = prog;
     a.st = st;
     a.timeout_ns = timeout_ns;
-    a.tma_x = encode_tiles(&a.tm_x, true, x, g.N, g.M, g.P, g.N) ? 1 : 0;
+    a.tma_x = encode_tiles(&a.tm_x, true, x, g.N, g.M, g.P, x_pitch) ? 1 : 0;
     a.vec_out = ((reinterpret_cast<uintptr_t>(codes) & 15) == 0 && (codes_pitch * 2) % 16 == 0) ? 1 : 0;
 }
 
@@ -1505,11 +1507,11 @@ static void fill_decompress(WaveArgs& a, const WaveGeom& g, const uint16_t* code
     a.vec_out = ((reinterpret_cast<uintptr_t>(out) & 15) == 0 && (g.N * 4) % 16 == 0) ? 1 : 0;
 }
 
-int launch_wave_compress(const WaveGeom& g, int layers, const float* x, uint16_t* codes, uint64_t codes_pitch,
-                         float* recorded, float* halo_row, float* halo_plane, unsigned int* prog,
-                         DevState* st, uint64_t timeout_ns, cudaStream_t s) {
+int launch_wave_compress(const WaveGeom& g, int layers, const float* x, uint64_t x_pitch, uint16_t* codes,
+                         uint64_t codes_pitch, float* recorded, float* halo_row, float* halo_plane,
+                         unsigned int* prog, DevState* st, uint64_t timeout_ns, cudaStream_t s) {
     WaveArgs a;
-    fill_compress(a, g, x, codes, codes_pitch, recorded, halo_row, halo_plane, prog, st, timeout_ns);
+    fill_compress(a, g, x, x_pitch, codes, codes_pitch, recorded, halo_row, halo_plane, prog, st, timeout_ns);
     return launch_any<false>(a, layers, s);
 }
 
@@ -1527,10 +1529,11 @@ int launch_wave_decompress(const WaveGeom& g, int layers, const uint16_t* codes,
 
 size_t wave_args_bytes() { return sizeof(WaveArgs); }
 
-void wave_args_compress(void* dst, const WaveGeom& g, const float* x, uint16_t* codes, uint64_t codes_pitch,
-                        float* halo_row, float* halo_plane, unsigned int* prog, DevState* st, uint64_t timeout_ns) {
-    fill_compress(*static_cast<WaveArgs*>(dst), g, x, codes, codes_pitch, nullptr, halo_row, halo_plane, prog, st,
-                  timeout_ns);
+void wave_args_compress(void* dst, const WaveGeom& g, const float* x, uint64_t x_pitch, uint16_t* codes,
+                        uint64_t codes_pitch, float* halo_row, float* halo_plane, unsigned int* prog, DevState* st,
+                        uint64_t timeout_ns) {
+    fill_compress(*static_cast<WaveArgs*>(dst), g, x, x_pitch, codes, codes_pitch, nullptr, halo_row, halo_plane,
+                  prog, st, timeout_ns);
 }
 
 int wave_args_decompress(void* dst, const WaveGeom& g, const uint16_t* codes, uint64_t codes_pitch, float* out,

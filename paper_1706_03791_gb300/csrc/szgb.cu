@@ -409,6 +409,13 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
     else ostage = nullptr;
     float* hvals = rec_dev;  // the hyperplane path's recorded values
     if (hyper && !rec_dev) A.add(&hvals, N);
+    // the wavefront reads x through TMA tiles, which need 16-byte row
+    // strides: rows of a length that is not a multiple of 4 are staged at
+    // a pitch rounded up to 4
+    const bool wave = cp.variant == SZGB_VARIANT_EXACT && !hyper;
+    const uint64_t xpitch = (wave && rowlen % 4) ? (rowlen + 3) & ~(uint64_t)3 : rowlen;
+    float* xpad = nullptr;
+    if (xpitch != rowlen) A.add(&xpad, rows * xpitch);
     rc = ensure_scratch(c, A.total);
     if (rc) return rc;
     A.bind(c->scratch);
@@ -452,17 +459,23 @@ int compress_impl(szgb_ctx* c, const float* data, int data_on_device, const szgb
                 return rc;
         } else if (hyper) {
             if ((rc = launch_hyper_compress(layers, x, hvals, codes, cpitch, cp.d0, cp.d1, cp.d2, st, s))) return rc;
-        } else if (!rec_dev) {
-            // the persistent kernel, items in ready-time order
-            ArgsBuf ha(wave_args_bytes());
-            wave_args_compress(ha.p, g, x, codes, cpitch, halo_row, halo_plane, prog, st, c->timeout_ns);
-            if ((rc = ensure_pinned(c, align_up(wave_args_bytes(), 256) + 8 * (size_t)g.num_ctas))) return rc;
-            if ((rc = launch_wave_one(c, g, layers, false, ha.p, static_cast<char*>(c->h_batch), wargs, worder,
-                                      wticket, s)))
+        } else {
+            if (xpad && (rc = launch_pitch_rows(x, rows, rowlen, xpad, xpitch, c->sm_count, s))) return rc;
+            const float* xw = xpad ? xpad : x;
+            if (!rec_dev) {
+                // the persistent kernel, items in ready-time order
+                ArgsBuf ha(wave_args_bytes());
+                wave_args_compress(ha.p, g, xw, xpitch, codes, cpitch, halo_row, halo_plane, prog, st,
+                                   c->timeout_ns);
+                if ((rc = ensure_pinned(c, align_up(wave_args_bytes(), 256) + 8 * (size_t)g.num_ctas))) return rc;
+                if ((rc = launch_wave_one(c, g, layers, false, ha.p, static_cast<char*>(c->h_batch), wargs, worder,
+                                          wticket, s)))
+                    return rc;
+            } else if ((rc = launch_wave_compress(g, layers, xw, xpitch, codes, cpitch, rec_dev, halo_row, halo_plane,
+                                                  prog, st, c->timeout_ns, s))) {
                 return rc;
-        } else if ((rc = launch_wave_compress(g, layers, x, codes, cpitch, rec_dev, halo_row, halo_plane, prog, st,
-                                       c->timeout_ns, s)))
-            return rc;
+            }
+        }
     }
     {
         PhaseTimer t(c, PH_HIST);
@@ -865,6 +878,8 @@ struct CompPlan {
     uint64_t *cw, *sortbuf, *rowoff, *blocksums;
     unsigned* prog;
     uint32_t* hist;
+    float* xpad;      // rows staged at a 16-byte pitch for the wavefront (or null)
+    uint64_t xpitch;  // row pitch of the wavefront's input
 };
 
 // The (field, item) order of a wavefront launch.  Items are taken in the
@@ -979,6 +994,10 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
         A.add(&q.rowbytes, q.nch);
         A.add(&q.rowoff, q.nch);
         A.add(&q.blocksums, (q.nch + 2047) / 2048 + 1);
+        q.xpitch = (q.rowlen + 3) & ~(uint64_t)3;  // TMA tiles need 16-byte row strides
+        q.xpad = nullptr;
+        if (q.xpitch != q.rowlen) A.add(&q.xpad, q.rows * q.xpitch);
+        else q.xpitch = q.rowlen;
     }
     if ((rc = ensure_scratch(c, A.total))) return rc;
     A.bind(c->scratch);
@@ -1006,8 +1025,9 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
     for (int f = 0; f < count; f++) {
         h_init[f] = DevState{};
         h_init[f].cap = out_cap[f];
-        wave_args_compress(H + o_w + (size_t)f * wsz, P[f].g, data[f], P[f].codes, P[f].cpitch, P[f].halo_row,
-                           P[f].halo_plane, P[f].prog, st + f, c->timeout_ns);
+        wave_args_compress(H + o_w + (size_t)f * wsz, P[f].g, P[f].xpad ? P[f].xpad : data[f], P[f].xpitch,
+                           P[f].codes, P[f].cpitch, P[f].halo_row, P[f].halo_plane, P[f].prog, st + f,
+                           c->timeout_ns);
         codebook_args_fill(H + o_cb + (size_t)f * cbsz, P[f].hist, st + f, P[f].len, P[f].cw, P[f].sortbuf,
                            P[f].nodebuf);
     }
@@ -1052,6 +1072,8 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
             cudaStream_t a = c->aux[f % kAux];
             if ((r = launch_range(data[f], q.n, st + f, q.cp, q.partials, q.range_blocks, a))) return r;
             if (q.cp.m_user == 0 && (r = launch_adapt(data[f], q.cp, st + f, a))) return r;
+            if (q.xpad && (r = launch_pitch_rows(data[f], q.rows, q.rowlen, q.xpad, q.xpitch, c->sm_count, a)))
+                return r;
         }
         join_aux(c);
         for (int li = 0; li < kMaxLayers; li++) {

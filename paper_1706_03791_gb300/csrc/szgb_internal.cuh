@@ -519,7 +519,11 @@ int launch_hits4(const float* x, const float* V, uint64_t D, uint64_t P, uint64_
 // prediction hits |x - f(V)| <= eb over a d0 x d1 x d2 field, added to *count
 int launch_hits(const float* x, const float* V, uint64_t d0, uint64_t d1, uint64_t d2, int ndim, int layers,
                 double eb, unsigned long long* count, int sm_count, cudaStream_t s);
-int launch_wave_compress(const WaveGeom& g, int layers, const float* x, uint16_t* codes,
+// rows of x (N floats each) copied to xp at row pitch P (k_range.cu)
+int launch_pitch_rows(const float* x, uint64_t rows, uint64_t N, float* xp, uint64_t P, int sm_count, cudaStream_t s);
+// x: the input with row pitch x_pitch (N, or N rounded up to 4 when the rows
+// were staged by launch_pitch_rows)
+int launch_wave_compress(const WaveGeom& g, int layers, const float* x, uint64_t x_pitch, uint16_t* codes,
                          uint64_t codes_pitch, float* recorded, float* halo_row, float* halo_plane, unsigned int* prog,
                          DevState* st, uint64_t timeout_ns, cudaStream_t s);
 // decompression: rows decoded first (codes into a row-pitched array, the
@@ -569,8 +573,9 @@ size_t wave_smem_bytes(const WaveGeom& g, int layers, bool decompress);
 // batched wavefront: a device table of per-field arguments (filled on the
 // host, wave_args_bytes() each, 64-byte aligned) and a (field, item) order
 size_t wave_args_bytes();
-void wave_args_compress(void* dst, const WaveGeom& g, const float* x, uint16_t* codes, uint64_t codes_pitch,
-                        float* halo_row, float* halo_plane, unsigned int* prog, DevState* st, uint64_t timeout_ns);
+void wave_args_compress(void* dst, const WaveGeom& g, const float* x, uint64_t x_pitch, uint16_t* codes,
+                        uint64_t codes_pitch, float* halo_row, float* halo_plane, unsigned int* prog, DevState* st,
+                        uint64_t timeout_ns);
 int wave_args_decompress(void* dst, const WaveGeom& g, const uint16_t* codes, uint64_t codes_pitch, float* out,
                          float* halo_row, float* halo_plane, unsigned int* prog, DevState* st, uint64_t timeout_ns);
 int launch_wave_batch(const void* args_dev, const void* order_dev, unsigned total, unsigned* ticket_dev, int layers,
