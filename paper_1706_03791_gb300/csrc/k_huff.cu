@@ -337,53 +337,92 @@ __device__ __forceinline__ void codebook_block(const uint32_t* __restrict__ hist
     }
     __syncthreads();
     // 3. two-queue merge (thread 0): leaves 0..n-1, internal nodes n..2n-2;
-    //    a leaf is taken first on equal weight
+    //    a leaf is taken first on equal weight.  The fronts of both queues and
+    //    the element behind each are kept in registers, so that a pick never
+    //    waits for a shared-memory load: the load for the element behind is
+    //    issued when the front moves up.
     if (tid == 0) {
         const uint32_t* LW = leaves_smem ? s_a32 : leafw_g;
         int q1 = 0, q2 = n, nxt = n;
-        uint32_t wl = LW[0], wq = 0;
+        uint32_t wl = LW[0], wl1 = n > 1 ? LW[1] : 0u;  // leaf queue: front, behind it
+        uint32_t wq = 0, wq1 = 0;                       // internal queue: front, behind it (if present)
         for (int step = 0; step < n - 1; step++) {
-            int pk0, pk1;
-            uint32_t w0, w1;
-            {
+            int pk[2];
+            uint32_t w[2];
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
                 const bool leaf = q1 < n && (q2 >= nxt || wl <= wq);
                 if (leaf) {
-                    pk0 = q1; w0 = wl; q1++; wl = q1 < n ? LW[q1] : 0u;
+                    pk[k] = q1;
+                    w[k] = wl;
+                    q1++;
+                    wl = wl1;
+                    wl1 = q1 + 1 < n ? LW[q1 + 1] : 0u;
                 } else {
-                    pk0 = q2; w0 = wq; q2++; wq = q2 < nxt ? s_ring[q2 & (kCbRing - 1)] : 0u;
+                    pk[k] = q2;
+                    w[k] = wq;
+                    q2++;
+                    wq = wq1;
+                    wq1 = q2 + 1 < nxt ? s_ring[(q2 + 1) & (kCbRing - 1)] : 0u;
                 }
             }
-            {
-                const bool leaf = q1 < n && (q2 >= nxt || wl <= wq);
-                if (leaf) {
-                    pk1 = q1; w1 = wl; q1++; wl = q1 < n ? LW[q1] : 0u;
-                } else {
-                    pk1 = q2; w1 = wq; q2++; wq = q2 < nxt ? s_ring[q2 & (kCbRing - 1)] : 0u;
-                }
-            }
-            const uint32_t sum = w0 + w1;
+            const uint32_t sum = w[0] + w[1];
             s_ring[nxt & (kCbRing - 1)] = sum;
-            if (q2 == nxt) wq = sum;  // the queue was empty: the new node is its head
-            par[pk0] = (uint32_t)nxt;
-            par[pk1] = (uint32_t)nxt;
+            if (q2 == nxt) wq = sum;            // the queue was empty: the new node is its front
+            else if (q2 + 1 == nxt) wq1 = sum;  // ... or the element behind the front
+            par[pk[0]] = (uint32_t)nxt;
+            par[pk[1]] = (uint32_t)nxt;
             nxt++;
         }
     }
     __syncthreads();
-    // 4. depths: internal nodes top-down (parents have larger ids), then leaves
+    // 4. depths of the internal nodes (node n + i is internal node i; the root
+    //    is nint - 1; every parent has a larger index).  Up to 16384 internal
+    //    nodes: pointer jumping -- every node holds an ancestor and its
+    //    distance to it, and each round replaces the ancestor by the
+    //    ancestor's ancestor (adding the distances) until every node reaches
+    //    the root; two buffers, one barrier a round.  Beyond that: one pass
+    //    top-down on one thread.
     const int nint = n - 1;
-    const bool par_smem = nint <= 16384;
-    if (par_smem)
-        for (int i = tid; i < nint; i += kCbThreads) s_a32[i] = par[n + i];
-    __syncthreads();
-    if (tid == 0) {
-        s_dint[nint - 1] = 0;  // the root, node 2n-2
-        for (int v = nint - 2; v >= 0; v--) {
-            const uint32_t p = par_smem ? s_a32[v] : par[n + v];
-            s_dint[v] = (uint8_t)(s_dint[p - (uint32_t)n] + 1);
+    if (nint <= 16384) {
+        uint16_t* ancA = reinterpret_cast<uint16_t*>(cb_smem + 65536);  // ring region: 4 x 32 KB
+        uint16_t* ancB = ancA + 16384;
+        uint8_t* dA = cb_smem + 65536 + 65536;
+        uint8_t* dB = dA + 16384;
+        for (int i = tid; i < nint; i += kCbThreads) {
+            const bool root = i == nint - 1;
+            ancA[i] = (uint16_t)(root ? i : (int)(par[n + i] - (uint32_t)n));
+            dA[i] = root ? 0 : 1;
         }
+        __syncthreads();
+        for (;;) {
+            int moved = 0;
+            for (int i = tid; i < nint; i += kCbThreads) {
+                const int a = ancA[i];
+                const int aa = ancA[a];
+                ancB[i] = (uint16_t)aa;
+                dB[i] = (uint8_t)(dA[i] + (a == aa ? 0 : dA[a]));
+                moved |= a != aa;
+            }
+            const int any = __syncthreads_or(moved);
+            uint16_t* ta = ancA;
+            ancA = ancB;
+            ancB = ta;
+            uint8_t* td = dA;
+            dA = dB;
+            dB = td;
+            if (!any) break;
+        }
+        // dA holds every internal node's depth (distance to the root)
+        for (int i = tid; i < nint; i += kCbThreads) s_dint[i] = dA[i];  // s_dint lies before dA (ring region)
+        __syncthreads();
+    } else {
+        if (tid == 0) {
+            s_dint[nint - 1] = 0;  // the root, node 2n-2
+            for (int v = nint - 2; v >= 0; v--) s_dint[v] = (uint8_t)(s_dint[par[n + v] - (uint32_t)n] + 1);
+        }
+        __syncthreads();
     }
-    __syncthreads();
     for (int i = tid; i < n; i += kCbThreads) {
         const uint32_t d = (uint32_t)s_dint[par[i] - (uint32_t)n] + 1u;
         len[sortedsym[i]] = (uint8_t)d;
