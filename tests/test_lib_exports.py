@@ -115,3 +115,31 @@ def test_suggest_m_matches_oracle(szgb, szo):
     bad.n_points, bad.n_unpred, bad.m = 10, 11, 8
     with pytest.raises(szgb.SzgbError):
         szgb.suggest_m(bad, 0.9)
+
+
+@pytest.mark.gpu
+def test_batch_parameters_checked_before_any_work(szgb):
+    # every field's parameters and buffers are checked before the batch touches
+    # any buffer: a bad field fails the whole call with SZGB_EINVAL (the
+    # pointers here are not device memory; no kernel may run on them)
+    L = szgb.lib()
+    h = C.c_void_p()
+    assert L.szgb_create(C.byref(h), 0, 0) == szgb.OK
+    try:
+        n = 2
+        P = (szgb.Params * n)()
+        P[0] = szgb.make_params((8, 8), eb_rel=1e-3)
+        P[1] = szgb.make_params((2, 3, 4, 5), eb_rel=1e-3, m=1)  # m = 1: invalid
+        dp = (C.c_void_p * n)(4096, 8192)
+        op = (C.c_void_p * n)(4096 * 3, 4096 * 4)
+        cap = (C.c_size_t * n)(1 << 16, 1 << 16)
+        olen = (C.c_size_t * n)()
+        assert L.szgb_compress_batch(h, n, dp, P, op, cap, olen, None) == szgb.EINVAL
+        P[1] = szgb.make_params((2, 3, 4, 5), eb_rel=1e-3)
+        dp[1] = 8200  # not 16-byte aligned
+        assert L.szgb_compress_batch(h, n, dp, P, op, cap, olen, None) == szgb.EINVAL
+        assert L.szgb_compress_batch(h, 0, dp, P, op, cap, olen, None) == szgb.EINVAL
+        assert L.szgb_set_wave_ctas(h, -1) == szgb.EINVAL
+        assert L.szgb_set_wave_ctas(h, 7) == szgb.OK
+    finally:
+        L.szgb_destroy(h)
