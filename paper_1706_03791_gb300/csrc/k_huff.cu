@@ -555,15 +555,15 @@ __global__ void __launch_bounds__(256) k_rowbits(const uint16_t* __restrict__ co
                 const uint64_t l = lb + (uint64_t)lane * 8;
                 const uint32_t w[4] = {q[h].x, q[h].y, q[h].z, q[h].w};
                 const int nv = l < rowlen ? (rowlen - l < 8 ? (int)(rowlen - l) : 8) : 0;
-                uint64_t bits = 0;
+                uint32_t bits = 0;  // at most 8 x (64 + 97) per lane, 32 lanes: fits 32 bits
 #pragma unroll
                 for (int k = 0; k < 8; k++) {
                     if (k < nv) {
                         const uint32_t c = (w[k >> 1] >> (16 * (k & 1))) & 0xffffu;
                         bits += __ldg(len + c);
                         if (c == 0) {
-                            bits += OK ? (uint64_t)(OK[base + l + k] ? 65 : 97)
-                                       : (uint64_t)(9 + trunc_bits(__float_as_uint(x[base + l + k]), e_eb));
+                            bits += OK ? (OK[base + l + k] ? 65u : 97u)
+                                       : (uint32_t)(9 + trunc_bits(__float_as_uint(x[base + l + k]), e_eb));
                             kcount++;
                         }
                     }
@@ -611,45 +611,60 @@ int launch_rowbits(const uint16_t* codes, uint64_t pitch, const float* x, uint64
 constexpr int kScanTile = 2048;
 
 // in: the counts (tab == nullptr), or the stream's chunk table of `width`-byte
-// little-endian entries, whose values are also written to counts_out
+// little-endian entries (4-byte aligned), whose values are also written to
+// counts_out.  A thread takes two consecutive entries; a warp-shuffle scan of
+// the thread sums, then of the warp sums, gives every entry its exclusive
+// prefix within the tile (two barriers).
 __global__ void __launch_bounds__(1024) k_scan_local(const uint32_t* __restrict__ in, uint64_t n,
                                                      uint64_t* out, uint64_t* blocksums,
                                                      const uint8_t* __restrict__ tab, int width,
                                                      uint32_t* __restrict__ counts_out) {
-    __shared__ uint64_t s[kScanTile];
+    __shared__ uint64_t s_w[32];
     const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
-    for (int i = threadIdx.x; i < kScanTile; i += blockDim.x) {
-        uint64_t v = 0;
-        if (base + i < n) {
-            if (tab) {
-                const uint8_t* p = tab + (base + i) * width;
-                uint32_t u = p[0] | ((uint32_t)p[1] << 8);
-                if (width == 4) u |= ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
-                counts_out[base + i] = u;
-                v = u;
-            } else {
-                v = in[base + i];
+    const uint64_t i0 = base + 2 * (uint64_t)threadIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t v0 = 0, v1 = 0;
+    if (tab) {
+        if (width == 2) {
+            if (i0 + 1 < n) {
+                const uint32_t u = *reinterpret_cast<const uint32_t*>(tab + 2 * i0);  // two entries
+                v0 = u & 0xffffu;
+                v1 = u >> 16;
+            } else if (i0 < n) {
+                v0 = *reinterpret_cast<const uint16_t*>(tab + 2 * i0);
             }
+        } else {
+            if (i0 < n) v0 = reinterpret_cast<const uint32_t*>(tab)[i0];
+            if (i0 + 1 < n) v1 = reinterpret_cast<const uint32_t*>(tab)[i0 + 1];
         }
-        s[i] = v;
+        if (i0 < n) counts_out[i0] = v0;
+        if (i0 + 1 < n) counts_out[i0 + 1] = v1;
+    } else {
+        if (i0 < n) v0 = in[i0];
+        if (i0 + 1 < n) v1 = in[i0 + 1];
+    }
+    const uint64_t t = (uint64_t)v0 + v1;
+    uint64_t incl = t;  // inclusive scan of the thread sums within the warp
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_w[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {  // exclusive scan of the warp sums
+        const uint64_t w = s_w[lane];
+        uint64_t wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        s_w[lane] = wi - w;
+        if (lane == 31) blocksums[blockIdx.x] = wi;
     }
     __syncthreads();
-    // Hillis-Steele inclusive scan over 2048 elements (2 per thread)
-    for (int off = 1; off < kScanTile; off <<= 1) {
-        uint64_t a0 = 0, a1 = 0;
-        int i0 = threadIdx.x, i1 = threadIdx.x + 1024;
-        if (i0 >= off) a0 = s[i0 - off];
-        if (i1 >= off) a1 = s[i1 - off];
-        __syncthreads();
-        s[i0] += a0;
-        s[i1] += a1;
-        __syncthreads();
-    }
-    for (int i = threadIdx.x; i < kScanTile; i += blockDim.x) {
-        uint64_t excl = i ? s[i - 1] : 0;
-        if (base + i < n) out[base + i] = excl;
-    }
-    if (threadIdx.x == 0) blocksums[blockIdx.x] = s[kScanTile - 1];
+    const uint64_t excl = s_w[wid] + incl - t;
+    if (i0 < n) out[i0] = excl;
+    if (i0 + 1 < n) out[i0 + 1] = excl + v0;
 }
 
 // one warp: exclusive scan of the block sums, 32 at a time

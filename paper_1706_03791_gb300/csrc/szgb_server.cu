@@ -18,7 +18,7 @@
 // or more workers worker 0 takes small requests only, so that one worker is
 // always free of large ones; the other workers take the oldest pending
 // request's kind first.  A persistent wavefront launch holds its SMs until
-// it ends, so a large request's wavefront runs on three quarters of the SMs
+// it ends, so a large request's wavefront runs on half of the SMs
 // (szgb_set_wave_ctas) and small batches keep the rest.  A request's result
 // is exactly the result of the single-field calls: batches change the
 // schedule, never the bits.
@@ -301,10 +301,11 @@ void worker_main(szgb_server* S, int wid) {
             const bool large = batch.size() == 1 && is_large(batch[0]);
             cudaStream_t st = large ? st_large : st_small;
             szgb_set_stream(ctx, st);
-            // a large request's persistent wavefront leaves a quarter of the
-            // SMs free: the small batches' kernels find SMs there instead of
-            // waiting for the whole launch
-            szgb_set_wave_ctas(ctx, large ? sms - sms / 4 : 0);
+            // a large request's persistent wavefront takes half of the SMs:
+            // two large requests run side by side, and the small batches'
+            // kernels find SMs between their launches instead of waiting for
+            // whole persistent launches
+            szgb_set_wave_ctas(ctx, large ? sms / 2 : 0);
             run_batch(S, ctx, st, dbuf, dcap, batch, &t_in, &t_run);
         }
         if (trace().f) {
