@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libszgb.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["szgb.cu", "k_range.cu", "k_wave.cu", "k_huff.cu", "szgb_noalloc.cu", "szgb_server.cu", "k_lattice.cu",
+SOURCES = ["szgb.cu", "k_range.cu", "k_wave.cu", "k_decode.cu", "k_huff.cu", "szgb_noalloc.cu", "szgb_server.cu", "k_lattice.cu",
            "k_quality.cu", "k_hyper.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-prec-div=true", "-prec-sqrt=true",
