@@ -535,6 +535,8 @@ __global__ void __launch_bounds__(256) k_rowbits(const uint16_t* __restrict__ co
     const int e_eb = st->e_eb;
     const uint64_t nseg = chunks_per_row(chunk, rowlen);
     const int G = (chunk == 0 || chunk >= 256) ? 32 : (int)(chunk / 8);  // lanes per chunk in a step
+    const int cshift = chunk ? __ffs((int)chunk) - 1 : 0;                // chunk is a power of two
+    const uint64_t cmask = chunk ? (uint64_t)chunk - 1 : 0;
     unsigned long long kcount = 0;
     uint32_t maxb = 0;
     for (uint64_t r = wglob; r < rows; r += nw) {
@@ -572,17 +574,17 @@ __global__ void __launch_bounds__(256) k_rowbits(const uint16_t* __restrict__ co
                 if (G == 32) {
                     carry += bits;
                     const uint64_t send = lb + 256;
-                    if (send >= rowlen || (chunk && send % chunk == 0)) {  // the chunk ends with this step
+                    if (send >= rowlen || (chunk && (send & cmask) == 0)) {  // the chunk ends with this step
                         if (lane == 0) {
                             const uint32_t b = (uint32_t)((carry + 7) / 8);
-                            rowbytes[r * nseg + (chunk ? lb / chunk : 0)] = b;
+                            rowbytes[r * nseg + (chunk ? lb >> cshift : 0)] = b;
                             maxb = b > maxb ? b : maxb;
                         }
                         carry = 0;
                     }
                 } else if ((lane & (G - 1)) == 0 && l < rowlen) {
                     const uint32_t b = (uint32_t)((bits + 7) / 8);
-                    rowbytes[r * nseg + l / chunk] = b;
+                    rowbytes[r * nseg + (l >> cshift)] = b;
                     maxb = b > maxb ? b : maxb;
                 }
             }
@@ -594,12 +596,27 @@ __global__ void __launch_bounds__(256) k_rowbits(const uint16_t* __restrict__ co
     if (lane == 0 && kcount) atomicAdd(&st->K, kcount);
 }
 
+// Blocks of `fn` that are resident at once on the current device (its SMs times
+// the blocks an SM holds at this block size and shared memory): a grid-stride
+// kernel launched with exactly that many runs in one wave, with no partial
+// second wave at the end.
+static uint64_t resident_blocks(const void* fn, int block, size_t smem) {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, block, smem) != cudaSuccess || per < 1 || sms < 1) {
+        cudaGetLastError();
+        return 152;
+    }
+    return (uint64_t)sms * (uint64_t)per;
+}
+
 int launch_rowbits(const uint16_t* codes, uint64_t pitch, const float* x, uint64_t rows, uint64_t rowlen,
                    uint32_t chunk, const uint8_t* len, uint32_t* rowbytes, DevState* st, cudaStream_t s,
                    const uint8_t* OK) {
+    static const uint64_t resident = resident_blocks(reinterpret_cast<const void*>(k_rowbits), 256, 0);
     uint64_t warps = rows;
     uint64_t blocks = (warps * 32 + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > resident) blocks = resident;
     if (blocks < 1) blocks = 1;
     k_rowbits<<<(int)blocks, 256, 0, s>>>(codes, pitch, x, rows, rowlen, chunk, len, rowbytes, st, OK);
     return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
@@ -876,6 +893,8 @@ __global__ void __launch_bounds__(kEncWarps * 32) k_encode(const uint16_t* __res
     const uint64_t nw = (uint64_t)gridDim.x * kEncWarps;
     const uint64_t nseg = chunks_per_row(chunk, rowlen);
     const int G = (chunk == 0 || chunk >= kEncChunk) ? 32 : (int)(chunk / kEncPts);  // lanes per chunk in a step
+    const int cshift = chunk ? __ffs((int)chunk) - 1 : 0;  // chunk is a power of two (0: whole rows)
+    const uint64_t cmask = chunk ? (uint64_t)chunk - 1 : 0;
     for (int i = lane; i < kEncBufWords; i += 32) buf[i] = 0;
     __syncwarp();
     for (uint64_t r = wglob; r < rows; r += nw) {
@@ -925,10 +944,10 @@ __global__ void __launch_bounds__(kEncWarps * 32) k_encode(const uint16_t* __res
                 const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
                 if ((lane & (G - 1)) >= o) incl += y;
             }
-            if (G == 32 && chunk && l0 % chunk == 0) carry = 0;  // a chunk starts with this step
+            if (G == 32 && chunk && (l0 & cmask) == 0) carry = 0;  // a chunk starts with this step
             // this lane's chunk (lanes past the row end take the step's first)
             const uint64_t lc = (l < rowlen ? l : l0);
-            const uint64_t cstart = coff[chunk ? lc / chunk : 0] * 8 + (G == 32 ? carry : 0);
+            const uint64_t cstart = coff[chunk ? lc >> cshift : 0] * 8 + (G == 32 ? carry : 0);
             const uint32_t off = (uint32_t)(cstart - curw * 32) + incl - nbits;
             // the step ends where its last lane with points ends
             const int last = (int)min((uint64_t)31, (rowlen - 1 - l0) / kEncPts);
@@ -1028,8 +1047,9 @@ int launch_encode(const uint16_t* codes, uint64_t pitch, const float* x, uint64_
         if (!ok) cudaGetLastError();
     });
     if (!ok) return SZGB_ECUDA;
+    static const uint64_t resident = resident_blocks(reinterpret_cast<const void*>(k_encode), kEncWarps * 32, smem);
     uint64_t blocks = (rows + kEncWarps - 1) / kEncWarps;
-    if (blocks > 152 * 5) blocks = 152 * 5;
+    if (blocks > resident) blocks = resident;
     if (blocks < 1) blocks = 1;
     k_encode<<<(int)blocks, kEncWarps * 32, smem, s>>>(codes, pitch, x, rows, rowlen, chunk, len, cw, rowoff, out, st,
                                                        LR);
