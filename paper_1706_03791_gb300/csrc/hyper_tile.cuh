@@ -31,11 +31,11 @@ namespace szgb {
 
 template <int DIM, int NL>
 struct TileGeom {
-    // tile extents: 3D 8 x 16 x 32; 4D 4 x 4 x 8 x 32 (2 x 4 x 8 x 32 for n >= 3,
+    // tile extents: 3D 8 x 32 x 32; 4D 4 x 4 x 8 x 32 (2 x 4 x 8 x 32 for n >= 3,
     // whose halo is wider)
     static constexpr int TA = DIM == 4 ? (NL <= 2 ? 4 : 2) : 1;
     static constexpr int TI = DIM == 4 ? 4 : 8;
-    static constexpr int TJ = DIM == 4 ? 8 : 16;
+    static constexpr int TJ = DIM == 4 ? 8 : 32;
     static constexpr int TL = 32;
     static constexpr int HA = DIM == 4 ? NL : 0;  // halo planes along the 4th axis (3D: none)
     static constexpr int BA = TA + HA, BI = TI + NL, BJ = TJ + NL;
