@@ -51,8 +51,21 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(const uint16_t* __restric
     const uint64_t vpr = pitch >> 3;  // vectors per row
     const uint64_t nvec = rows * vpr;
     const uint64_t stride = (uint64_t)gridDim.x * kHistThreads;
+    // the (row, vector) of the thread's vector, advanced by the grid stride
+    // with a carry instead of a division per vector
+    const uint64_t v_first = blockIdx.x * (uint64_t)kHistThreads + threadIdx.x;
+    const uint64_t sr = stride / vpr, sc = stride - sr * vpr;
+    uint64_t vr = v_first / vpr, vc = v_first - vr * vpr;
+    auto advance = [&](uint64_t& r, uint64_t& c) {
+        r += sr;
+        c += sc;
+        if (c >= vpr) {
+            c -= vpr;
+            r++;
+        }
+    };
     // two vectors in flight per thread
-    for (uint64_t v0 = blockIdx.x * (uint64_t)kHistThreads + threadIdx.x; v0 < nvec; v0 += 2 * stride) {
+    for (uint64_t v0 = v_first; v0 < nvec; v0 += 2 * stride) {
         uint4 q[2];
         int nv[2];
 #pragma unroll
@@ -61,12 +74,12 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(const uint16_t* __restric
             nv[h] = 0;
             q[h] = make_uint4(0u, 0u, 0u, 0u);
             if (v < nvec) {
-                const uint64_t r = (nvec >> 32) ? v / vpr : (uint64_t)((uint32_t)v / (uint32_t)vpr);
-                const uint64_t c0 = (v - r * vpr) << 3;
-                q[h] = __ldcs(reinterpret_cast<const uint4*>(codes + r * pitch + c0));
+                const uint64_t c0 = vc << 3;
+                q[h] = __ldcs(reinterpret_cast<const uint4*>(codes + vr * pitch + c0));
                 const uint64_t rem = rowlen - c0;
                 nv[h] = rem < 8 ? (int)rem : 8;
             }
+            advance(vr, vc);
         }
 #pragma unroll
         for (int h = 0; h < 2; h++) {
