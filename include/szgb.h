@@ -30,7 +30,7 @@
  * 116 holds C, 0 for whole rows); chunks follow row by row.  The same bytes are produced by the CPU oracle of the test-suite.
  * The format also carries 4D fields (the predictor of Sec. III in four
  * dimensions; ndim 4 at header byte 8, the slowest extent at byte 120, the
- * other three at bytes 16-40).  Every call takes them.
+ * other three at bytes 16-40).  Every call but the autotuner takes them.
  */
 #ifndef SZGB_H
 #define SZGB_H
@@ -136,9 +136,9 @@ size_t szgb_compress_bound(const szgb_params *p);
  * SZGB_ETRUNC reports that out_cap is too small.  opt_stats may be NULL.
  * Fails with SZGB_ENONFINITE on NaN/Inf input, SZGB_EINVAL on bad
  * parameters.  Layers 1..4 in every dimension: 3D fields with n = 3, 4 and
- * 4D fields run on the hyperplane kernels, 1D-3D fields otherwise on the
- * wavefront.  A 4D field's stream
- * says ndim = 4 and keeps shape[0] at header byte 120; its rows of shape[3]
+ * 4D fields run on the tiled hyperplane kernels (one launch per diagonal of
+ * tiles), 1D-3D fields otherwise on the wavefront.  A 4D field's stream says
+ * ndim = 4 and keeps shape[0] at header byte 120; its rows of shape[3]
  * points are coded as those of the (shape[0] shape[1]) x shape[2] x shape[3]
  * view, whose szgb_compress_bound it never exceeds. */
 int szgb_compress(szgb_ctx *ctx, const float *data, int data_on_device,
