@@ -121,6 +121,28 @@ def ncu_traffic(kernel):
     return val
 
 
+def host_link(torch, stream, xh, yh, reps=5):
+    """Host<->device copy rates (GB/s) of the field's pinned buffers: median
+    of `reps` copies each way, CUDA events on the copying stream."""
+    d = torch.empty(xh.shape, dtype=xh.dtype, device=stream.device)
+    out = {}
+    with torch.cuda.stream(stream):
+        for name, fn in (("h2d", lambda: d.copy_(xh, non_blocking=True)),
+                         ("d2h", lambda: yh.copy_(d, non_blocking=True))):
+            fn()
+            ts = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            out[name] = xh.numel() * xh.element_size() / (pct(ts, 50) / 1e3) / 1e9
+    del d
+    return out
+
+
 def pct(v, q):
     v = sorted(v)
     if not v:
@@ -849,6 +871,13 @@ def main():
         if i >= args.warmup:
             e2e_t.append(dt)
     e2e_val = ws * 2 * nbytes * len(e2e_t) / sum(e2e_t) / 1e9
+    link = host_link(torch, stream, xh, yh)
+    # the serial bound of one end-to-end compress + decompress: each call
+    # returns with its output on the host, so its copies cannot overlap the
+    # kernels (the field in, the stream out; the stream in, the field out)
+    t_serial = (nbytes / link["h2d"] + stream_bytes / link["d2h"] + stream_bytes / link["h2d"]
+                + nbytes / link["d2h"]) / 1e9 + (pct(tc2, 50) + pct(td2, 50)) / 1e3
+    e2e_bound = 2 * nbytes / t_serial / 1e9
 
     # roofline of the dominant kernel: live CUDA-event phase times
     peak, peak_kind = peaks()
@@ -895,12 +924,15 @@ def main():
         "cpu_baseline": cpu,
         "batched": batched,
         "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": nbytes + stream_bytes,
-                "d2h_bytes_per_step": stream_bytes + nbytes},
-        # kernels of this library per step: compress 11 (range, adapt, wavefront,
-        # histogram, codebook, row bits, 3 scan, metadata, encode), decompress 7
-        # (tables, row bytes, 3 scan, row decode, wavefront); the lattice variant
-        # compress 12, decompress 7 + 3 axis scans per layer
-        "gpu_launches": (18 if args.variant == "exact" else 19 + 3 * args.layers) * args.steps,
+                "d2h_bytes_per_step": stream_bytes + nbytes,
+                "host_link_gbs": {"h2d": link["h2d"], "d2h": link["d2h"]},
+                "serial_bound_gbs": e2e_bound},
+        # kernels of this library per step: compress 10 (range, adapt, wavefront,
+        # histogram, codebook, chunk bits, 2 scan, metadata, encode), decompress 5
+        # (2 scan, tables, chunk decode, wavefront); the lattice variant compress
+        # 11 (range, adapt, 2 lattice passes, then the same 7), decompress 5 +
+        # 3 axis scans per layer (2 scan, tables, chunk decode, finish)
+        "gpu_launches": (15 if args.variant == "exact" else 16 + 3 * args.layers) * args.steps,
         "clocks": clk,
         "wall_s_timed": t_wall,
     }

@@ -636,19 +636,42 @@ int launch_rowbits(const uint16_t* codes, uint64_t pitch, const float* x, uint64
 }
 
 // ---------------------------------------------------------------------------
-// exclusive scan of row byte counts -> row offsets (three phases)
+// exclusive scan of chunk byte counts -> chunk offsets.  One tile of 2048
+// entries: one kernel.  Up to kScanAddMax tiles: the tile scans, then one
+// kernel in which every tile adds the sum of the tiles before it (read from
+// the tile sums, which it reduces itself).  More tiles: the tile sums are
+// scanned by one warp in between (three kernels).  No kernel waits for another
+// block.
 
 constexpr int kScanTile = 2048;
+constexpr int kScanAddMax = 1024;
+
+// the payload's byte total is known: sizes of the stream's sections
+// (compression) or the payload length to check (decompression)
+__device__ __forceinline__ void scan_finalize(DevState* st, uint64_t rows, uint64_t acc, int finalize) {
+    st->payload = acc;
+    if (finalize) {
+        const unsigned tw = st->maxrow <= 0xffffu ? 2u : 4u;
+        st->table_width = tw;
+        st->cb_bytes = (3ull * st->nsym + 3) & ~3ull;
+        st->tab_bytes = ((uint64_t)tw * rows + 3) & ~3ull;
+        st->total = (uint64_t)kHeaderBytes + st->cb_bytes + st->tab_bytes + acc;
+        st->fits = st->total <= st->cap;
+        if (!st->fits) st->err |= kErrOverflow;
+    }
+}
 
 // in: the counts (tab == nullptr), or the stream's chunk table of `width`-byte
 // little-endian entries (4-byte aligned), whose values are also written to
 // counts_out.  A thread takes two consecutive entries; a warp-shuffle scan of
 // the thread sums, then of the warp sums, gives every entry its exclusive
-// prefix within the tile (two barriers).
+// prefix within the tile (two barriers).  A grid of one tile finalizes the
+// state itself (st != nullptr).
 __global__ void __launch_bounds__(1024) k_scan_local(const uint32_t* __restrict__ in, uint64_t n,
                                                      uint64_t* out, uint64_t* blocksums,
                                                      const uint8_t* __restrict__ tab, int width,
-                                                     uint32_t* __restrict__ counts_out) {
+                                                     uint32_t* __restrict__ counts_out, DevState* st,
+                                                     int finalize) {
     __shared__ uint64_t s_w[32];
     const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
     const uint64_t i0 = base + 2 * (uint64_t)threadIdx.x;
@@ -689,7 +712,10 @@ __global__ void __launch_bounds__(1024) k_scan_local(const uint32_t* __restrict_
             if (lane >= o) wi += y;
         }
         s_w[lane] = wi - w;
-        if (lane == 31) blocksums[blockIdx.x] = wi;
+        if (lane == 31) {
+            if (st) scan_finalize(st, n, wi, finalize);
+            else blocksums[blockIdx.x] = wi;
+        }
     }
     __syncthreads();
     const uint64_t excl = s_w[wid] + incl - t;
@@ -697,7 +723,8 @@ __global__ void __launch_bounds__(1024) k_scan_local(const uint32_t* __restrict_
     if (i0 + 1 < n) out[i0 + 1] = excl + v0;
 }
 
-// one warp: exclusive scan of the block sums, 32 at a time
+// one warp: exclusive scan of the block sums, 32 at a time (more than
+// kScanAddMax tiles)
 __global__ void __launch_bounds__(32) k_scan_blocks(uint64_t* blocksums, int nblocks, DevState* st,
                                                     uint64_t rows, int finalize) {
     const int lane = threadIdx.x;
@@ -713,36 +740,58 @@ __global__ void __launch_bounds__(32) k_scan_blocks(uint64_t* blocksums, int nbl
         if (b < nblocks) blocksums[b] = acc + incl - t;
         acc += __shfl_sync(0xffffffffu, incl, 31);
     }
-    if (lane == 0) {
-        if (finalize) {
-            st->payload = acc;
-            unsigned tw = st->maxrow <= 0xffffu ? 2u : 4u;
-            st->table_width = tw;
-            st->cb_bytes = (3ull * st->nsym + 3) & ~3ull;
-            st->tab_bytes = ((uint64_t)tw * rows + 3) & ~3ull;
-            st->total = (uint64_t)kHeaderBytes + st->cb_bytes + st->tab_bytes + acc;
-            st->fits = st->total <= st->cap;
-            if (!st->fits) st->err |= kErrOverflow;
-        } else {
-            st->payload = acc;
-        }
-    }
+    if (lane == 0) scan_finalize(st, rows, acc, finalize);
 }
 
-__global__ void __launch_bounds__(1024) k_scan_add(uint64_t* out, uint64_t n, const uint64_t* blocksums) {
-    const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
-    const uint64_t add = blocksums[blockIdx.x];
+// tile b's entries += the sum of tiles < b: blocksums already scanned
+// (st == nullptr), or the tile sums, reduced here over [0, b); the last tile
+// then finalizes the state
+__global__ void __launch_bounds__(1024) k_scan_add(uint64_t* out, uint64_t n, const uint64_t* blocksums,
+                                                   DevState* st, int finalize) {
+    __shared__ uint64_t s_w[32];
+    __shared__ uint64_t s_add;
+    const int b = (int)blockIdx.x;
+    if (!st) {
+        if (threadIdx.x == 0) s_add = blocksums[b];
+    } else {
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        uint64_t v = 0;
+        for (int i = threadIdx.x; i < b; i += blockDim.x) v += blocksums[i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) s_w[wid] = v;
+        __syncthreads();
+        if (wid == 0) {
+            v = s_w[lane];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) {
+                s_add = v;
+                if (b == (int)gridDim.x - 1) scan_finalize(st, n, v + blocksums[b], finalize);
+            }
+        }
+    }
+    __syncthreads();
+    const uint64_t base = (uint64_t)b * kScanTile;
+    const uint64_t add = s_add;
     for (int i = threadIdx.x; i < kScanTile; i += blockDim.x)
         if (base + i < n) out[base + i] += add;
 }
 
 int launch_scan_rows(const uint32_t* rowbytes, uint64_t rows, uint64_t* rowoff, uint64_t* blocksums,
                      DevState* st, int finalize_compress, cudaStream_t s, const uint8_t* table, int width) {
-    int nb = (int)((rows + kScanTile - 1) / kScanTile);
-    k_scan_local<<<nb, 1024, 0, s>>>(table ? nullptr : rowbytes, rows, rowoff, blocksums, table, width,
-                                     const_cast<uint32_t*>(rowbytes));
-    k_scan_blocks<<<1, 32, 0, s>>>(blocksums, nb, st, rows, finalize_compress);
-    k_scan_add<<<nb, 1024, 0, s>>>(rowoff, rows, blocksums);
+    const uint64_t nb = (rows + kScanTile - 1) / kScanTile;
+    const uint32_t* in = table ? nullptr : rowbytes;
+    uint32_t* counts_out = const_cast<uint32_t*>(rowbytes);
+    if (nb <= 1) {
+        k_scan_local<<<1, 1024, 0, s>>>(in, rows, rowoff, blocksums, table, width, counts_out, st,
+                                        finalize_compress);
+    } else if (nb <= (uint64_t)kScanAddMax) {
+        k_scan_local<<<(unsigned)nb, 1024, 0, s>>>(in, rows, rowoff, blocksums, table, width, counts_out, nullptr, 0);
+        k_scan_add<<<(unsigned)nb, 1024, 0, s>>>(rowoff, rows, blocksums, st, finalize_compress);
+    } else {
+        k_scan_local<<<(unsigned)nb, 1024, 0, s>>>(in, rows, rowoff, blocksums, table, width, counts_out, nullptr, 0);
+        k_scan_blocks<<<1, 32, 0, s>>>(blocksums, (int)nb, st, rows, finalize_compress);
+        k_scan_add<<<(unsigned)nb, 1024, 0, s>>>(rowoff, rows, blocksums, nullptr, 0);
+    }
     return cudaGetLastError() == cudaSuccess ? 0 : SZGB_ECUDA;
 }
 

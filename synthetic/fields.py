@@ -169,6 +169,17 @@ def linear_field(shape, coef=(0.5, -0.25, 0.125), c0=1.0) -> np.ndarray:
     return f.astype(np.float32)
 
 
+def walk3d(n0: int, n1: int, n2: int, seed: int, step: float = 0.01) -> np.ndarray:
+    """Seeded random walk along the fastest axis, in [0, 1]: a cheap field of
+    any shape (many short rows without a spectral transform)."""
+    rng = np.random.default_rng(seed)
+    g = np.cumsum(rng.standard_normal((n0, n1, n2), dtype=np.float32) * np.float32(step), axis=2)
+    g += rng.standard_normal((n0, n1, 1), dtype=np.float32)
+    g -= g.min()
+    g /= max(float(g.max()), 1e-30)
+    return np.ascontiguousarray(g, dtype=np.float32)
+
+
 def cache_dir() -> str:
     d = os.environ.get("SZGB_SYNTH_CACHE") or os.path.join(
         os.environ.get("TMPDIR", "/tmp"), "szgb_synth")

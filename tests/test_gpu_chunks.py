@@ -130,3 +130,30 @@ def test_invalid_chunk_rejected(env):
         with pytest.raises(szgb.SzgbError) as e:
             ctx.compress(xd, eb_rel=1e-3, m=8, chunk_points=C)
         assert e.value.code == szgb.EINVAL
+
+
+# chunk counts around the chunk-offset scan's tile of 2048 entries and its
+# 1024-tile limit for the two-kernel form: one tile (partial and full), two
+# tiles, and 1028 tiles (the three-kernel form)
+SCAN_CASES = [
+    ("1-tile-partial", lambda: fields.grf2d(40, 100, seed=101), dict(chunk_points=32), 160),
+    ("1-tile-full", lambda: fields.grf2d(64, 1024, seed=102), dict(chunk_points=32), 2048),
+    ("2-tiles", lambda: fields.grf2d(2049, 32, seed=103), dict(), 2049),
+    ("1028-tiles", lambda: fields.walk3d(1028, 2048, 8, seed=104), dict(), 1028 * 2048),
+]
+
+
+@pytest.mark.parametrize("name,gen,ckw,nchunks", SCAN_CASES, ids=[c[0] for c in SCAN_CASES])
+def test_chunk_offset_scan_sizes(env, szo, name, gen, ckw, nchunks):
+    torch, szgb, ctx = env
+    x = np.ascontiguousarray(gen())
+    kw = dict(eb_rel=1e-4, m=0, **ckw)
+    ref, rec, _ = szo.compress(x, want_aux=True, **kw)
+    rows = int(np.prod(x.shape[:-1]))
+    C = ckw.get("chunk_points", 0)
+    per_row = -(-x.shape[-1] // C) if 0 < C < x.shape[-1] else 1
+    assert rows * per_row == nchunks
+    s, st = ctx.compress(torch.from_numpy(x).cuda(), **kw)
+    assert np.array_equal(s.cpu().numpy(), ref)
+    y = ctx.decompress(s)
+    assert np.array_equal(_bits(y.cpu().numpy()), _bits(rec))
