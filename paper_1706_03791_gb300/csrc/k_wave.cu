@@ -129,6 +129,13 @@ __device__ __forceinline__ bool halo_tagged(const uint64_t (&w)[4]) {
 }
 
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+// The tensor map of an item lives in the argument table in global memory,
+// which the host rewrites between launches (another field, or the other
+// direction's map at the same address): order this thread's tensor-map
+// accesses after those writes before its first tiled copy.
+__device__ __forceinline__ void fence_tensormap_acquire(const void* tmap) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmap) : "memory");
+}
 
 // ---------------------------------------------------------------------------
 // The kernel.  ND = 1, 2 (row topology) or 3 (plane x row); NL = layers;
@@ -681,6 +688,7 @@ __device__ __forceinline__ void wave_item(const WaveArgs& A, const int item, uns
         }
         // staging warp; prologue: x tiles up to sweep kPFX
         int u_issued = kPFX;  // latest sweep whose x tiles were issued
+        if (tma_x && lane == 0) fence_tensormap_acquire(&A.tm_x);
         for (int u = 0; u <= kPFX; u++) issue_x(u);
         cp_async_commit();
         cp_async_wait<0>();

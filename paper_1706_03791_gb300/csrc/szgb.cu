@@ -964,25 +964,27 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
     size_t nprog = 0, total_items = 0;
     for (int f = 0; f < count; f++) nprog += (size_t)nitems[f], total_items += (size_t)nitems[f];
 
-    // device scratch
-    DevState* st;
-    unsigned *tickets, *prog_all;
-    uint32_t *hist_all, *order;
-    char* wargs;
-    Arena A;
-    A.add(&st, count);
-    A.add(&tickets, kMaxLayers);
-    A.add(&prog_all, nprog);
-    A.add(&hist_all, (size_t)count * 65536);
-    A.add(&wargs, (size_t)count * wsz);
-    A.add(&order, 2 * total_items);
+    // pinned host tables: initial states, wavefront arguments, order,
+    // codebook arguments; the final states come back after them.  The device
+    // copy of the tables has the same layout, so that one copy moves them.
+    const size_t cbsz = codebook_args_bytes();
+    const size_t o_st = 0, o_w = align_up((size_t)count * sizeof(DevState), 256);
+    const size_t o_ord = align_up(o_w + (size_t)count * wsz, 256);
+    const size_t o_cb = align_up(o_ord + 8 * total_items, 256);
+    const size_t o_out = align_up(o_cb + (size_t)count * cbsz, 256);
+    // what every pass starts from zero, in one region cleared by one memset:
+    // tickets, item progress words, histograms, halo buffers
     size_t nhalo = 0;
     for (int f = 0; f < count; f++) nhalo += P[f].hrow + P[f].hplane;
-    float* halo_all;
-    A.add(&halo_all, nhalo);
-    const size_t cbsz = codebook_args_bytes();
-    char* cbargs;
-    A.add(&cbargs, (size_t)count * cbsz);
+    const size_t z_pr = align_up(4 * (size_t)kMaxLayers, 256);
+    const size_t z_hi = align_up(z_pr + 4 * nprog, 256);
+    const size_t z_ha = align_up(z_hi + 4 * (size_t)count * 65536, 256);
+    const size_t z_end = align_up(z_ha + 4 * nhalo, 256);
+    // device scratch
+    char *dtab, *zero;
+    Arena A;
+    A.add(&dtab, o_out);
+    A.add(&zero, z_end);
     for (int f = 0; f < count; f++) {
         CompPlan& q = P[f];
         A.add(&q.partials, 2 * (size_t)q.range_blocks);
@@ -1001,6 +1003,14 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
     }
     if ((rc = ensure_scratch(c, A.total))) return rc;
     A.bind(c->scratch);
+    DevState* const st = reinterpret_cast<DevState*>(dtab + o_st);
+    char* const wargs = dtab + o_w;
+    uint32_t* const order = reinterpret_cast<uint32_t*>(dtab + o_ord);
+    char* const cbargs = dtab + o_cb;
+    unsigned* const tickets = reinterpret_cast<unsigned*>(zero);
+    unsigned* const prog_all = reinterpret_cast<unsigned*>(zero + z_pr);
+    uint32_t* const hist_all = reinterpret_cast<uint32_t*>(zero + z_hi);
+    float* const halo_all = reinterpret_cast<float*>(zero + z_ha);
     {
         size_t po = 0, ho = 0;
         for (int f = 0; f < count; f++) {
@@ -1012,12 +1022,6 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
             ho += P[f].hrow + P[f].hplane;
         }
     }
-    // pinned host tables: initial states, wavefront arguments, order; the
-    // final states come back to the same place
-    const size_t o_st = 0, o_w = align_up((size_t)count * sizeof(DevState), 256);
-    const size_t o_ord = align_up(o_w + (size_t)count * wsz, 256);
-    const size_t o_cb = align_up(o_ord + 8 * total_items, 256);
-    const size_t o_out = align_up(o_cb + (size_t)count * cbsz, 256);
     if ((rc = ensure_pinned(c, o_out + (size_t)count * sizeof(DevState)))) return rc;
     char* H = static_cast<char*>(c->h_batch);
     DevState* h_init = reinterpret_cast<DevState*>(H + o_st);
@@ -1057,14 +1061,8 @@ int compress_batch_impl(szgb_ctx* c, int count, const float* const* data, const 
     cudaStream_t s = c->stream;
     auto enqueue = [&]() -> int {
         int r;
-        if (cudaMemcpyAsync(st, h_init, (size_t)count * sizeof(DevState), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemcpyAsync(wargs, H + o_w, (size_t)count * wsz, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemcpyAsync(order, h_order, 8 * total_items, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemsetAsync(tickets, 0, kMaxLayers * sizeof(unsigned), s) != cudaSuccess ||
-            cudaMemsetAsync(prog_all, 0, nprog * sizeof(unsigned), s) != cudaSuccess ||
-            cudaMemsetAsync(halo_all, 0, nhalo * 4, s) != cudaSuccess ||
-            cudaMemsetAsync(hist_all, 0, (size_t)count * 65536 * 4, s) != cudaSuccess ||
-            cudaMemcpyAsync(cbargs, H + o_cb, (size_t)count * cbsz, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        if (cudaMemcpyAsync(dtab, H, o_out, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemsetAsync(zero, 0, z_end, s) != cudaSuccess)
             return SZGB_ECUDA;
         fork_aux(c);
         for (int f = 0; f < count; f++) {
@@ -1205,26 +1203,26 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
     const size_t wsz = wave_args_bytes();
     size_t nprog = 0, total_items = 0;
     for (int f = 0; f < count; f++) nprog += (size_t)nitems[f], total_items += (size_t)nitems[f];
-    DevState* st;
-    unsigned *tickets, *prog_all;
-    uint32_t* order;
-    char* wargs;
-    Arena A;
-    A.add(&st, count);
-    A.add(&tickets, kMaxLayers);
-    A.add(&prog_all, nprog);
-    A.add(&wargs, (size_t)count * wsz);
-    A.add(&order, 2 * total_items);
+    // pinned host tables: initial states, wavefront arguments, order, decode
+    // and table arguments, decode block offsets; the final states come back
+    // after them.  The device copy has the same layout (one copy).
+    const size_t dsz = decode_args_bytes(), tsz = tables_args_bytes();
+    const size_t o_st = 0, o_w = align_up((size_t)count * sizeof(DevState), 256);
+    const size_t o_ord = align_up(o_w + (size_t)count * wsz, 256);
+    const size_t o_dec = align_up(o_ord + 8 * total_items, 256);
+    const size_t o_tab = align_up(o_dec + (size_t)count * dsz, 256);
+    const size_t o_blk = align_up(o_tab + (size_t)count * tsz, 256);
+    const size_t o_out = align_up(o_blk + 4 * ((size_t)count + 1), 256);
+    // tickets, item progress words and halo buffers: one region, one memset
     size_t nhalo = 0;
     for (int f = 0; f < count; f++) nhalo += P[f].hrow + P[f].hplane;
-    float* halo_all;
-    A.add(&halo_all, nhalo);
-    const size_t dsz = decode_args_bytes(), tsz = tables_args_bytes();
-    char *dargs, *targs;
-    uint32_t* dblk;
-    A.add(&dargs, (size_t)count * dsz);
-    A.add(&targs, (size_t)count * tsz);
-    A.add(&dblk, (size_t)count + 1);
+    const size_t z_pr = align_up(4 * (size_t)kMaxLayers, 256);
+    const size_t z_ha = align_up(z_pr + 4 * nprog, 256);
+    const size_t z_end = align_up(z_ha + 4 * nhalo, 256);
+    char *dtab, *zero;
+    Arena A;
+    A.add(&dtab, o_out);
+    A.add(&zero, z_end);
     for (int f = 0; f < count; f++) {
         DecPlan& q = P[f];
         A.add(&q.codes, q.rows * q.cpitch + 8);
@@ -1238,6 +1236,15 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
     }
     if ((rc = ensure_scratch(c, A.total))) return rc;
     A.bind(c->scratch);
+    DevState* const st = reinterpret_cast<DevState*>(dtab + o_st);
+    char* const wargs = dtab + o_w;
+    uint32_t* const order = reinterpret_cast<uint32_t*>(dtab + o_ord);
+    char* const dargs = dtab + o_dec;
+    char* const targs = dtab + o_tab;
+    uint32_t* const dblk = reinterpret_cast<uint32_t*>(dtab + o_blk);
+    unsigned* const tickets = reinterpret_cast<unsigned*>(zero);
+    unsigned* const prog_all = reinterpret_cast<unsigned*>(zero + z_pr);
+    float* const halo_all = reinterpret_cast<float*>(zero + z_ha);
     {
         size_t po = 0, ho = 0;
         for (int f = 0; f < count; f++) {
@@ -1248,12 +1255,6 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
             po += (size_t)nitems[f];
         }
     }
-    const size_t o_st = 0, o_w = align_up((size_t)count * sizeof(DevState), 256);
-    const size_t o_ord = align_up(o_w + (size_t)count * wsz, 256);
-    const size_t o_dec = align_up(o_ord + 8 * total_items, 256);
-    const size_t o_tab = align_up(o_dec + (size_t)count * dsz, 256);
-    const size_t o_blk = align_up(o_tab + (size_t)count * tsz, 256);
-    const size_t o_out = align_up(o_blk + 4 * ((size_t)count + 1), 256);
     if ((rc = ensure_pinned(c, o_out + (size_t)count * sizeof(DevState)))) return rc;
     char* Hb = static_cast<char*>(c->h_batch);
     DevState* h_init = reinterpret_cast<DevState*>(Hb + o_st);
@@ -1306,15 +1307,8 @@ int decompress_batch_impl(szgb_ctx* c, int count, const uint8_t* const* in, cons
     }
     auto enqueue = [&]() -> int {
         int r;
-        if (cudaMemcpyAsync(st, h_init, (size_t)count * sizeof(DevState), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemcpyAsync(wargs, Hb + o_w, (size_t)count * wsz, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemcpyAsync(order, h_order, 8 * total_items, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemsetAsync(tickets, 0, kMaxLayers * sizeof(unsigned), s) != cudaSuccess ||
-            cudaMemsetAsync(prog_all, 0, nprog * sizeof(unsigned), s) != cudaSuccess ||
-            cudaMemsetAsync(halo_all, 0, nhalo * 4, s) != cudaSuccess ||
-            cudaMemcpyAsync(dargs, Hb + o_dec, (size_t)count * dsz, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemcpyAsync(dblk, h_blk, 4 * ((size_t)count + 1), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemcpyAsync(targs, Hb + o_tab, (size_t)count * tsz, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        if (cudaMemcpyAsync(dtab, Hb, o_out, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemsetAsync(zero, 0, z_end, s) != cudaSuccess)
             return SZGB_ECUDA;
         // every field's chunk offsets (auxiliary streams) while the decoder
         // tables of every field are built in one launch (one CTA each)
